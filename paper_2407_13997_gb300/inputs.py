@@ -1,0 +1,94 @@
+"""Seeded synthetic workloads (shared by the tests, the bench and smoke).
+
+This module holds no arithmetic of the method: it only names the problem
+parameters and draws the random amplitudes of the divergence-free Fourier
+forcing, which both the CUDA path and the oracle then evaluate themselves.
+
+Fourier forcing: stream-function modes psi_j = sin(mx_j pi x) sin(my_j pi y),
+f = sum_j amp_j (d_y psi_j, -d_x psi_j), using the 8 lowest mode pairs ordered
+by (mx^2 + my^2, mx), amp_j = z_j / (mx_j^2 + my_j^2) with z_j ~ N(0, 1) from
+numpy.random.default_rng(seed) (amplitudes decaying as |k|^-2).
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+KIND_TAYLOR_GREEN = 0
+KIND_POLY = 1
+KIND_FOURIER = 2
+KIND_NAMES = {KIND_TAYLOR_GREEN: "taylor_green", KIND_POLY: "poly", KIND_FOURIER: "fourier"}
+
+FOURIER_MODES = ((1, 1), (1, 2), (2, 1), (2, 2), (1, 3), (3, 1), (2, 3), (3, 2))
+
+
+def fourier_forcing(seed, n_modes=8):
+    """(mx, my, amp) arrays of the seeded divergence-free Fourier forcing."""
+    rng = np.random.default_rng(seed)
+    z = rng.standard_normal(n_modes)
+    mx = np.array([m for m, _ in FOURIER_MODES[:n_modes]], dtype=np.int32)
+    my = np.array([n for _, n in FOURIER_MODES[:n_modes]], dtype=np.int32)
+    amp = z / (mx.astype(np.float64) ** 2 + my.astype(np.float64) ** 2)
+    return mx, my, amp
+
+
+@dataclass
+class Workload:
+    """One space-time solve: mesh n_fine -> n_coarse, Q_{k+1}^2/Q_k, DG(q), N slabs."""
+
+    name: str
+    n_fine: int
+    n_coarse: int
+    k: int
+    q: int
+    N: int
+    T: float
+    nu: float
+    conv: float
+    kind: int
+    steady: bool = False
+    mx: np.ndarray = field(default_factory=lambda: np.zeros(0, dtype=np.int32))
+    my: np.ndarray = field(default_factory=lambda: np.zeros(0, dtype=np.int32))
+    amp: np.ndarray = field(default_factory=lambda: np.zeros(0))
+
+    def ndofs(self, n=None):
+        n = self.n_fine if n is None else n
+        nv = n * (self.k + 1) + 1
+        np_ = n * self.k + 1
+        return self.N * (self.q + 1) * (2 * nv * nv + np_ * np_)
+
+
+def taylor_green_8x8():
+    """Plain FP64 parity workload: 8x8 Q2/Q1, DG(0), 8 slabs on [0, 1], nu = 1e-2,
+    decaying Taylor-Green data, coarsened to 2x2."""
+    return Workload("tg_q2q1_dg0_n8_N8", 8, 2, 1, 0, 8, 1.0, 1e-2, 1.0, KIND_TAYLOR_GREEN)
+
+
+def fourier_64x64_q3q2_dg1(seed=0):
+    """64x64 Q3/Q2, DG(1), 64 slabs on [0, 1], nu = 1e-3, seeded Fourier forcing,
+    no-slip walls, u(0) = 0, coarsened to 2x2 (11,665,792 space-time DoFs)."""
+    mx, my, amp = fourier_forcing(seed)
+    return Workload("fourier_q3q2_dg1_n64_N64", 64, 2, 2, 1, 64, 1.0, 1e-3, 1.0,
+                    KIND_FOURIER, False, mx, my, amp)
+
+
+def fourier_128x128_q2q1_dg0(seed=0):
+    """128x128 Q2/Q1, DG(0), 128 slabs, nu = 1e-3, seeded Fourier forcing."""
+    mx, my, amp = fourier_forcing(seed)
+    return Workload("fourier_q2q1_dg0_n128_N128", 128, 2, 1, 0, 128, 1.0, 1e-3, 1.0,
+                    KIND_FOURIER, False, mx, my, amp)
+
+
+def fourier_small(n=8, k=1, q=0, N=4, nu=1e-2, seed=0, T=1.0, n_coarse=2):
+    mx, my, amp = fourier_forcing(seed)
+    return Workload(f"fourier_k{k}_q{q}_n{n}_N{N}", n, n_coarse, k, q, N, T, nu, 1.0,
+                    KIND_FOURIER, False, mx, my, amp)
+
+
+def poly_small(n=4, k=1, q=1, N=3, nu=0.1, steady=False, n_coarse=2):
+    return Workload(f"poly_k{k}_q{q}_n{n}_N{N}", n, n_coarse, k, q, N, 1.0, nu, 1.0,
+                    KIND_POLY, steady)
+
+
+def seeded_vector(seed, size, scale=1.0):
+    """A reproducible N(0, scale^2) test vector."""
+    return scale * np.random.default_rng(seed).standard_normal(size)
