@@ -1,0 +1,210 @@
+/*
+ * wrmg.h -- C ABI of the GB300 space-time waveform-relaxation multigrid library.
+ *
+ * The library solves the space-time Taylor-Hood discretisation of the
+ * incompressible Navier-Stokes equations (Eq. nsfem; DG(q) in time, Def.
+ * "Temporal discretisation", Eq. dgintime) on the unit square,
+ *
+ *     u_t + conv (u.grad) u + grad p - nu lap u = f,   div u = 0,
+ *
+ * with Q_{k+1}^2 / Q_k elements on a uniform n x n quadrilateral mesh and N
+ * time slabs solved all at once, by inexact Newton with FGMRES preconditioned
+ * by V(2,2) waveform-relaxation multigrid cycles (Sec. 3, Algorithm Vcycle).
+ * The paper's form u_t + R u.grad u + grad phi - lap u = 0 is conv = R, nu = 1.
+ *
+ * Vectors.  Every vector argument is a caller-owned DEVICE pointer (cudaMalloc
+ * or a torch CUDA tensor) to FP64 data of length wr_ndofs(ctx, level) in the
+ * canonical layout
+ *
+ *     index = ((slab * (q+1) + a) * S + field_offset + y * nf + x)
+ *
+ * with S = 2 nv^2 + np^2, nv = n(k+1)+1 and np = nk+1 nodes per direction,
+ * fields u_x (offset 0), u_y (offset nv^2), Phi (offset 2 nv^2), x fastest,
+ * a = 0..q the temporal DoF of the slab (Lagrange basis at the right-Radau
+ * points; a = q is the slab end value).  The discrete pressure Phi follows the
+ * paper's sign +(Phi, div psi), i.e. it approximates minus the strong-form p.
+ * Exceptions: functions ending in _host take host pointers.
+ *
+ * Streams.  All work is enqueued on the CUDA stream given to wr_create.  Calls
+ * that return host scalars (norms, iteration counts) synchronise that stream;
+ * the others only enqueue.  A context must not be used from two host threads
+ * at once.
+ *
+ * Errors.  Every call returns a status (WR_OK on success).  No exception
+ * crosses the ABI; wr_last_error returns a description of the last failure.
+ * After WR_ERR_CUDA the context should be destroyed.
+ *
+ * Ownership.  A wr_ctx owns the level hierarchy, the linearisation point on
+ * every level, the stored patch factors, the Chebyshev eigen-estimates and the
+ * Krylov workspace; wr_destroy frees them.  The caller owns every vector.
+ */
+#ifndef WRMG_H
+#define WRMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define WR_OK 0
+#define WR_ERR_ARG 1            /* invalid argument (size, level, null pointer, unsupported k/q) */
+#define WR_ERR_NOMEM 2          /* device allocation failed                                     */
+#define WR_ERR_CUDA 3           /* a CUDA call or kernel launch failed                          */
+#define WR_ERR_NOT_CONVERGED 4  /* Newton or FGMRES reached its iteration limit                 */
+#define WR_ERR_TIMEOUT 5        /* a bounded device wait gave up                                */
+#define WR_ERR_NAN 6            /* a norm became NaN or Inf                                     */
+#define WR_ERR_STATE 7          /* call order violated (e.g. smoother before wr_linearise)      */
+
+/* problem data (wr_problem.kind) */
+#define WR_TAYLOR_GREEN 0  /* decaying Taylor-Green (Chorin) vortex, f = 0, exact Dirichlet data (conv = 1)  */
+#define WR_POLY 1          /* manufactured u = (y^2, x^2)(1+t) (or steady), p = x+y-1, with matching f       */
+#define WR_FOURIER 2       /* no-slip walls, u(0) = 0, f = sum amp_j curl(sin(mx_j pi x) sin(my_j pi y))     */
+
+/* arithmetic of the stored patch factors and of the smoother (wr_options.precision) */
+#define WR_FP64 0
+#define WR_FP32 1
+
+typedef struct wr_ctx wr_ctx;
+
+typedef struct {
+    int n_fine;     /* cells per direction on the finest level (power of two times n_coarse) */
+    int n_coarse;   /* cells per direction on the direct-solve level; must be 2              */
+    int k;          /* Taylor-Hood order: velocity Q_{k+1}, pressure Q_k; k = 1 or 2          */
+    int q;          /* DG(q) in time; q = 0 or 1                                             */
+    int n_slabs;    /* N time slabs of width T / N                                           */
+    double T, nu, conv;
+    int kind;       /* WR_TAYLOR_GREEN, WR_POLY or WR_FOURIER                                */
+    int steady;     /* WR_POLY only: time-constant u = (y^2, x^2)                            */
+    int n_modes;    /* WR_FOURIER: number of modes (<= 8), host arrays below                 */
+    const int *mx, *my;
+    const double *amp;
+} wr_problem;
+
+typedef struct {
+    int precision;          /* WR_FP64 (default) or WR_FP32 factors and smoother                */
+    int cheb_steps;         /* Chebyshev steps per relaxation (2: V(2,2))                        */
+    double cheb_lo, cheb_hi;/* Chebyshev interval [cheb_lo lam, cheb_hi lam] (0.25, 1.05)       */
+    int eig_steps;          /* Arnoldi steps of the eigen-estimate (10)                         */
+    double newton_rtol;     /* stop when ||F|| <= newton_rtol ||F_0|| (1e-8)                     */
+    int newton_maxit;       /* (20)                                                              */
+    int ew;                 /* 1: Eisenstat-Walker forcing terms; 0: fixed eta_fixed             */
+    double eta_fixed;       /* (1e-4)                                                            */
+    int gmres_restart;      /* (30)                                                              */
+    int gmres_maxit;        /* total FGMRES iterations per Newton step (200)                     */
+} wr_options;
+
+typedef struct {
+    int newton_its;            /* Newton steps taken                                       */
+    int gmres_its[64];         /* FGMRES iterations of each Newton step                    */
+    double residual_norms[65]; /* ||F|| before each Newton step and at the end             */
+    double setup_ms;           /* time in wr_linearise, summed                             */
+    double krylov_ms;          /* time in FGMRES, summed                                   */
+    int vcycles;               /* V-cycles applied                                          */
+} wr_stats;
+
+/* Fills *o with the defaults listed above. */
+void wr_default_options(wr_options *o);
+
+/* Creates a context: level hierarchy n_fine, n_fine/2, ..., n_coarse with the
+ * same time mesh on every level (Sec. 3, semi-coarsening) and all device
+ * storage for the stored-factor smoother.  cuda_stream is a cudaStream_t (NULL
+ * = default stream).  Host arrays in *p are copied.  Errors: WR_ERR_ARG for
+ * unsupported sizes, WR_ERR_NOMEM if the hierarchy does not fit. */
+int wr_create(wr_ctx **out, const wr_problem *p, const wr_options *o, void *cuda_stream);
+int wr_destroy(wr_ctx *c);
+const char *wr_last_error(const wr_ctx *c);
+
+/* Levels are numbered 0 (coarsest, n_coarse) .. L (finest). */
+int wr_num_levels(const wr_ctx *c, int *out);
+int wr_ndofs(const wr_ctx *c, int level, int64_t *out);
+/* Bytes of device memory the context holds. */
+int wr_device_bytes(const wr_ctx *c, int64_t *out);
+
+/* Global indices (host array, capacity >= 2 (2k+3)^2 (q+1) + (2k-1)^2 (q+1))
+ * of Vanka+star patch `patch` (= J (n+1) + I for vertex (I, J)) on `slab` of
+ * `level` (Sec. 3, NS relaxation; Fig. patches): velocity DoFs in the closure of
+ * the 2x2-cell vertex star, pressure DoFs of the open star, each at every
+ * temporal DoF of the slab; order: temporal DoF a, then u_x nodes (y-major),
+ * u_y nodes, pressure nodes; Dirichlet nodes dropped. *len receives the count. */
+int wr_patch_dofs(const wr_ctx *c, int level, int64_t patch, int slab, int64_t *idx_host, int *len);
+
+/* U = Dirichlet data g at every temporal node on the boundary, zero elsewhere. */
+int wr_initial_guess(wr_ctx *c, double *U);
+
+/* F = F(U), the nonlinear space-time residual of Eq. nsfem on the finest level
+ * (Dirichlet rows: U - g).  Sum-factorised, matrix-free, FP64. */
+int wr_residual(wr_ctx *c, const double *U, double *F);
+
+/* Linearises about W (finest level): injects W to every coarser level,
+ * assembles and factors every (patch, slab) block A_nn = J(W)[P_i, P_i] of the
+ * waveform patch systems (Eq. waveform_patch_solve; principal submatrices of
+ * the assembled space-time Jacobian), factors the coarse slab blocks and runs
+ * the 10-step Arnoldi eigen-estimate of M^{-1} J on every smoothed level. */
+int wr_linearise(wr_ctx *c, const double *W);
+/* Same without the eigen-estimates (they keep their previous values). */
+int wr_linearise_no_eig(wr_ctx *c, const double *W);
+int wr_get_lambda(const wr_ctx *c, int level, double *lam);
+int wr_set_lambda(wr_ctx *c, int level, double lam);
+
+/* y = J(W_level) x: the Newton linearisation of Eq. nsfem about the level's
+ * linearisation point, with Dirichlet rows and columns replaced by the
+ * identity.  Sum-factorised matrix-free FP64 (kernel (e)). x and y must not alias. */
+int wr_apply_jacobian(wr_ctx *c, int level, const double *x, double *y);
+
+/* y = M^{-1} r = sum_i R_i^T A_i^{-1} R_i r: the waveform Vanka+star relaxation
+ * (per-patch gather, forward substitution over slabs with the stored slab
+ * factors, additive scatter).  level >= 1.  r and y must not alias. */
+int wr_patch_apply(wr_ctx *c, int level, const double *r, double *y);
+
+/* One relaxation: cheb_steps Chebyshev steps for J x = b preconditioned by
+ * wr_patch_apply; zero_guess != 0 ignores (and overwrites) x. level >= 1. */
+int wr_smooth(wr_ctx *c, int level, const double *b, double *x, int zero_guess);
+
+/* xc = R xf = P^T xf from level fine_level to fine_level - 1 (Sec. 3,
+ * P = I (x) blockdiag(P_u, P_phi)); Dirichlet entries zero. */
+int wr_restrict(wr_ctx *c, int fine_level, const double *xf, double *xc);
+/* xf += P xc. */
+int wr_prolong_add(wr_ctx *c, int fine_level, const double *xc, double *xf);
+
+/* x = exact solve with level 0's J (block forward substitution over slabs,
+ * pressure pinned at vertex (0, 0) per temporal DoF, then made mean-free). */
+int wr_coarse_solve(wr_ctx *c, const double *b, double *x);
+
+/* x = one V(2,2) cycle (Algorithm Vcycle) for J_fine x = b from a zero guess. */
+int wr_vcycle(wr_ctx *c, const double *b, double *x);
+/* The same with HOST b and x: copies b in and x out on the context stream. */
+int wr_vcycle_host(wr_ctx *c, const double *b_host, double *x_host);
+
+/* Subtracts from every temporal DoF's pressure its mean int Phi (the null
+ * space of J under all-Dirichlet velocity). Works on the finest level. */
+int wr_project_pressure(wr_ctx *c, double *x);
+
+/* Newton-FGMRES-WRMG solve from U_inout (call wr_initial_guess first for the
+ * standard start) until ||F|| <= newton_rtol ||F_0||.  stats may be NULL.
+ * Returns WR_ERR_NOT_CONVERGED if newton_maxit is reached. */
+int wr_solve(wr_ctx *c, double *U_inout, wr_stats *stats);
+/* The same with a HOST U (copied in and out). */
+int wr_solve_host(wr_ctx *c, double *U_host, wr_stats *stats);
+
+/* Total kernel launches made by this library in this process (all contexts). */
+int wr_launch_count(int64_t *out);
+
+/* enable != 0 starts recording CUDA events on the context stream around every
+ * launch of the smoother-apply kernel (gather + forward substitution over
+ * slabs, steps (a)+(c)), per level; it clears earlier records. */
+int wr_profile(wr_ctx *c, int enable);
+/* Sum of the recorded smoother-apply kernel durations on `level` (ms) and the
+ * number of launches recorded; synchronises the stream. */
+int wr_profile_smoother(wr_ctx *c, int level, double *total_ms, int *launches);
+
+/* FP64 FMA throughput of this GPU, measured by a register-only kernel
+ * (TFLOP/s); the denominator for FP64-ALU-bound kernels. */
+int wr_measure_fp64_tflops(void *cuda_stream, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

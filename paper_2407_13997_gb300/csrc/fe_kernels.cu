@@ -1,0 +1,539 @@
+// Space-time residual F(U) and Jacobian action J(W) x of Eq. nsfem, sum-factorised
+// and matrix-free on the uniform quadrilateral mesh (hot-path step (e)), plus the
+// element convection matrices used by the patch assembly, boundary data and the
+// injection of the linearisation point to coarser levels.
+//
+// Element kernel: one warp per (cell, slab).  The warp stages the element's
+// nodal data in shared memory, interpolates every field to the (k+3)^2 Gauss
+// points by two 1D passes (x, then y), forms the pointwise coefficients of the
+// weak form, and contracts them against the test functions by the transposed
+// two passes.  Element results go to a per-element buffer that a second kernel
+// sums into the global vector in a fixed order (deterministic, no atomics).
+//
+// Per slab n and test psi = tau_a phi (velocity component c), chi (pressure):
+//   value coefficient  sum_b Kt[a,b] u_{c,b} - tau_a(0) u^-_c
+//                      + dt conv sum_{b,e} T3[a,b,e] (convection term)
+//                      - dt sum_g wt_g tau_a(t_g) f_c(t_g)               (F only)
+//   gradient coeff.    dt sum_b Wt[a,b] (nu grad u_{c,b} + Phi_b e_c)
+//   pressure coeff.    dt sum_b Wt[a,b] div u_b
+// with the convection term (U_b.grad) U_{c,e} for F and
+// (W_b.grad) x_{c,e} + (x_b.grad) W_{c,e} for J.
+#include <cmath>
+
+#include "wrmg_internal.h"
+
+namespace {
+
+template <int K, int Q>
+struct D {
+  static constexpr int NT = Q + 1, NVL = K + 2, NPL = K + 1, NQ = K + 3;
+  static constexpr int NVE = NVL * NVL, NPE = NPL * NPL, NQ2 = NQ * NQ;
+  static constexpr int ELEM = NT * (2 * NVE + NPE);
+};
+
+constexpr int kWarps = 4;  // elements per CTA
+
+__device__ __forceinline__ void exact_velocity(const PhysParams& ph, double x, double y, double t,
+                                               double& ux, double& uy) {
+  if (ph.kind == WR_TAYLOR_GREEN) {
+    const double e = exp(-2.0 * ph.nu * M_PI * M_PI * t);
+    ux = -cospi(x) * sinpi(y) * e;
+    uy = sinpi(x) * cospi(y) * e;
+  } else if (ph.kind == WR_POLY) {
+    const double s = ph.steady ? 1.0 : 1.0 + t;
+    ux = y * y * s;
+    uy = x * x * s;
+  } else {
+    ux = 0.0;
+    uy = 0.0;
+  }
+}
+
+__device__ __forceinline__ void forcing(const PhysParams& ph, double x, double y, double t, double& fx,
+                                        double& fy) {
+  if (ph.kind == WR_POLY) {
+    const double nu = ph.nu, c = ph.conv;
+    if (ph.steady) {
+      fx = 2.0 * c * x * x * y + 1.0 - 2.0 * nu;
+      fy = 2.0 * c * x * y * y + 1.0 - 2.0 * nu;
+    } else {
+      const double s = 1.0 + t;
+      fx = y * y + 2.0 * c * x * x * y * s * s + 1.0 - 2.0 * nu * s;
+      fy = x * x + 2.0 * c * x * y * y * s * s + 1.0 - 2.0 * nu * s;
+    }
+  } else if (ph.kind == WR_FOURIER) {
+    fx = 0.0;
+    fy = 0.0;
+    for (int m = 0; m < ph.n_modes; ++m) {
+      const double a = ph.amp[m] * M_PI;
+      const double sx = sinpi(ph.mx[m] * x), cx = cospi(ph.mx[m] * x);
+      const double sy = sinpi(ph.my[m] * y), cy = cospi(ph.my[m] * y);
+      fx += a * ph.my[m] * sx * cy;
+      fy -= a * ph.mx[m] * cx * sy;
+    }
+  } else {
+    fx = 0.0;
+    fy = 0.0;
+  }
+}
+
+__device__ __forceinline__ bool vel_dirichlet(const LevelGeom& g, int gx, int gy) {
+  return gx == 0 || gy == 0 || gx == g.nv - 1 || gy == g.nv - 1;
+}
+
+// Shared-memory workspace of one element (one warp).
+template <int K, int Q, bool LIN>
+struct ElemSmem {
+  using d = D<K, Q>;
+  // velocity fields: u(c,b) [2 NT], w(c,b) [2 NT, J only], u^-(c) [2]
+  static constexpr int FV = LIN ? 4 * d::NT + 2 : 2 * d::NT + 2;
+  static constexpr int FU = 0, FW = 2 * d::NT, FUP = LIN ? 4 * d::NT : 2 * d::NT;
+  double vn[FV][d::NVE];           // nodal velocity fields
+  double pn[d::NT][d::NPE];        // nodal pressure
+  double t1[FV][2][d::NVL][d::NQ]; // x-pass values / derivatives
+  double vq[FV][3][d::NQ2];        // value, d/dx, d/dy at Gauss points
+  double pq[d::NT][d::NQ2];
+  double cv[2 * d::NT][3][d::NQ2]; // output coefficients (value, x-grad, y-grad)
+  double cp[d::NT][d::NQ2];
+  double out[d::ELEM];
+};
+
+// One warp computes the element contribution of (cell, slab) for F (LIN = false)
+// or J x (LIN = true).  `x` is U for F.
+template <int K, int Q, bool LIN>
+__global__ void __launch_bounds__(32 * kWarps)
+element_kernel(LevelGeom g, FeTables T, PhysParams ph, const double* __restrict__ W,
+               const double* __restrict__ x, double* __restrict__ ye) {
+  using d = D<K, Q>;
+  using SM = ElemSmem<K, Q, LIN>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM& s = reinterpret_cast<SM*>(smem_raw)[threadIdx.x / 32];
+  const int lane = threadIdx.x & 31;
+  const int cell = blockIdx.x * kWarps + threadIdx.x / 32;
+  const int slab = blockIdx.y;
+  if (cell >= g.ncells()) return;
+  const int CI = cell % g.n, CJ = cell / g.n;
+  const double h = g.h, dt = g.dt;
+  const int nv = g.nv, np = g.np, S = g.S;
+  const int64_t nv2 = (int64_t)nv * nv;
+
+  // ---- gather nodal data
+  for (int it = lane; it < 2 * d::NVE; it += 32) {
+    const int c = it / d::NVE, l = it % d::NVE;
+    const int gx = CI * (K + 1) + l % d::NVL, gy = CJ * (K + 1) + l / d::NVL;
+    const int64_t sp = c * nv2 + (int64_t)gy * nv + gx;
+    const bool dir = vel_dirichlet(g, gx, gy);
+    for (int b = 0; b < d::NT; ++b) {
+      const int64_t off = ((int64_t)slab * d::NT + b) * S + sp;
+      s.vn[SM::FU + c * d::NT + b][l] = (LIN && dir) ? 0.0 : x[off];
+      if constexpr (LIN) s.vn[SM::FW + c * d::NT + b][l] = W[off];
+    }
+    double up;
+    if (slab > 0) {
+      const int64_t off = ((int64_t)(slab - 1) * d::NT + (d::NT - 1)) * S + sp;
+      up = (LIN && dir) ? 0.0 : x[off];
+    } else if (LIN) {
+      up = 0.0;
+    } else {
+      double ux, uy;
+      exact_velocity(ph, gx * (h / (K + 1)), gy * (h / (K + 1)), 0.0, ux, uy);
+      up = c == 0 ? ux : uy;
+    }
+    s.vn[SM::FUP + c][l] = up;
+  }
+  for (int it = lane; it < d::NT * d::NPE; it += 32) {
+    const int b = it / d::NPE, l = it % d::NPE;
+    const int px = CI * K + l % d::NPL, py = CJ * K + l / d::NPL;
+    s.pn[b][l] = x[((int64_t)slab * d::NT + b) * S + 2 * nv2 + (int64_t)py * np + px];
+  }
+  __syncwarp();
+
+  // ---- interpolation to Gauss points: x pass
+  for (int it = lane; it < SM::FV * d::NVL * d::NQ; it += 32) {
+    const int f = it / (d::NVL * d::NQ), r = it % (d::NVL * d::NQ);
+    const int j = r / d::NQ, qx = r % d::NQ;
+    double v = 0.0, dv = 0.0;
+#pragma unroll
+    for (int i = 0; i < d::NVL; ++i) {
+      const double u = s.vn[f][j * d::NVL + i];
+      v = fma(T.Bv[qx][i], u, v);
+      dv = fma(T.Dv[qx][i], u, dv);
+    }
+    s.t1[f][0][j][qx] = v;
+    s.t1[f][1][j][qx] = dv;
+  }
+  for (int it = lane; it < d::NT * d::NQ2; it += 32) {  // pressure values, direct 2D sum
+    const int b = it / d::NQ2, q = it % d::NQ2;
+    const int qy = q / d::NQ, qx = q % d::NQ;
+    double v = 0.0;
+#pragma unroll
+    for (int j = 0; j < d::NPL; ++j)
+#pragma unroll
+      for (int i = 0; i < d::NPL; ++i) v = fma(T.Bp[qy][j] * T.Bp[qx][i], s.pn[b][j * d::NPL + i], v);
+    s.pq[b][q] = v;
+  }
+  __syncwarp();
+  // y pass
+  const double ih = 1.0 / h;
+  for (int it = lane; it < SM::FV * d::NQ2; it += 32) {
+    const int f = it / d::NQ2, q = it % d::NQ2;
+    const int qy = q / d::NQ, qx = q % d::NQ;
+    double v = 0.0, vx = 0.0, vy = 0.0;
+#pragma unroll
+    for (int j = 0; j < d::NVL; ++j) {
+      v = fma(T.Bv[qy][j], s.t1[f][0][j][qx], v);
+      vx = fma(T.Bv[qy][j], s.t1[f][1][j][qx], vx);
+      vy = fma(T.Dv[qy][j], s.t1[f][0][j][qx], vy);
+    }
+    s.vq[f][0][q] = v;
+    s.vq[f][1][q] = vx * ih;
+    s.vq[f][2][q] = vy * ih;
+  }
+  __syncwarp();
+
+  // ---- pointwise coefficients
+  for (int q = lane; q < d::NQ2; q += 32) {
+    const int qy = q / d::NQ, qx = q % d::NQ;
+    const double om = T.wq[qx] * T.wq[qy] * h * h;
+    double fxg[WR_MAX_NTQ], fyg[WR_MAX_NTQ];
+    if constexpr (!LIN) {
+      const double xx = (CI + T.xq[qx]) * h, yy = (CJ + T.xq[qy]) * h;
+      for (int gq = 0; gq < Q + 2; ++gq)
+        forcing(ph, xx, yy, (slab + T.tq[gq]) * dt, fxg[gq], fyg[gq]);
+    }
+#pragma unroll
+    for (int a = 0; a < d::NT; ++a) {
+      double pw = 0.0, divw = 0.0;
+#pragma unroll
+      for (int b = 0; b < d::NT; ++b) {
+        pw = fma(T.Wt[a][b], s.pq[b][q], pw);
+        divw = fma(T.Wt[a][b], s.vq[SM::FU + 0 * d::NT + b][1][q] + s.vq[SM::FU + 1 * d::NT + b][2][q], divw);
+      }
+      s.cp[a][q] = om * dt * divw;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        double val = -T.tau0[a] * s.vq[SM::FUP + c][0][q];
+        double gx = 0.0, gy = 0.0, cv = 0.0;
+#pragma unroll
+        for (int b = 0; b < d::NT; ++b) {
+          const int fu = SM::FU + c * d::NT + b;
+          val = fma(T.Kt[a][b], s.vq[fu][0][q], val);
+          gx = fma(T.Wt[a][b], s.vq[fu][1][q], gx);
+          gy = fma(T.Wt[a][b], s.vq[fu][2][q], gy);
+#pragma unroll
+          for (int e = 0; e < d::NT; ++e) {
+            const double t3 = T.T3[a][b][e];
+            const int fe = SM::FU + c * d::NT + e;
+            if constexpr (LIN) {
+              const int wb = SM::FW + b, wb1 = SM::FW + d::NT + b;     // W_b components
+              const int ub = SM::FU + b, ub1 = SM::FU + d::NT + b;     // x_b components
+              const int we = SM::FW + c * d::NT + e;
+              const double term = s.vq[wb][0][q] * s.vq[fe][1][q] + s.vq[wb1][0][q] * s.vq[fe][2][q] +
+                                  s.vq[ub][0][q] * s.vq[we][1][q] + s.vq[ub1][0][q] * s.vq[we][2][q];
+              cv = fma(t3, term, cv);
+            } else {
+              const int ub = SM::FU + b, ub1 = SM::FU + d::NT + b;
+              const double term = s.vq[ub][0][q] * s.vq[fe][1][q] + s.vq[ub1][0][q] * s.vq[fe][2][q];
+              cv = fma(t3, term, cv);
+            }
+          }
+        }
+        val = fma(dt * ph.conv, cv, val);
+        if constexpr (!LIN) {
+          double fsum = 0.0;
+          for (int gq = 0; gq < Q + 2; ++gq) fsum += T.wtq[gq] * T.Tq[a][gq] * (c == 0 ? fxg[gq] : fyg[gq]);
+          val -= dt * fsum;
+        }
+        gx = dt * ph.nu * gx + (c == 0 ? dt * pw : 0.0);
+        gy = dt * ph.nu * gy + (c == 1 ? dt * pw : 0.0);
+        s.cv[c * d::NT + a][0][q] = om * val;
+        s.cv[c * d::NT + a][1][q] = om * gx * ih;
+        s.cv[c * d::NT + a][2][q] = om * gy * ih;
+      }
+    }
+  }
+  __syncwarp();
+
+  // ---- test contraction: y pass (reuse t1 for the 2 NT output fields)
+  for (int it = lane; it < 2 * d::NT * d::NVL * d::NQ; it += 32) {
+    const int f = it / (d::NVL * d::NQ), r = it % (d::NVL * d::NQ);
+    const int j = r / d::NQ, qx = r % d::NQ;
+    double a1 = 0.0, a2 = 0.0;
+#pragma unroll
+    for (int qy = 0; qy < d::NQ; ++qy) {
+      const int q = qy * d::NQ + qx;
+      a1 = fma(T.Bv[qy][j], s.cv[f][0][q], a1);
+      a1 = fma(T.Dv[qy][j], s.cv[f][2][q], a1);
+      a2 = fma(T.Bv[qy][j], s.cv[f][1][q], a2);
+    }
+    s.t1[f][0][j][qx] = a1;
+    s.t1[f][1][j][qx] = a2;
+  }
+  __syncwarp();
+  // x pass -> element output; layout a*(2 NVE + NPE) + c*NVE + l, then pressure
+  for (int it = lane; it < 2 * d::NT * d::NVE; it += 32) {
+    const int f = it / d::NVE, l = it % d::NVE;
+    const int c = f / d::NT, a = f % d::NT;
+    const int j = l / d::NVL, i = l % d::NVL;
+    double v = 0.0;
+#pragma unroll
+    for (int qx = 0; qx < d::NQ; ++qx) {
+      v = fma(T.Bv[qx][i], s.t1[f][0][j][qx], v);
+      v = fma(T.Dv[qx][i], s.t1[f][1][j][qx], v);
+    }
+    s.out[a * (2 * d::NVE + d::NPE) + c * d::NVE + l] = v;
+  }
+  for (int it = lane; it < d::NT * d::NPE; it += 32) {
+    const int a = it / d::NPE, l = it % d::NPE;
+    const int j = l / d::NPL, i = l % d::NPL;
+    double v = 0.0;
+    for (int qy = 0; qy < d::NQ; ++qy)
+      for (int qx = 0; qx < d::NQ; ++qx)
+        v = fma(T.Bp[qy][j] * T.Bp[qx][i], s.cp[a][qy * d::NQ + qx], v);
+    s.out[a * (2 * d::NVE + d::NPE) + 2 * d::NVE + l] = v;
+  }
+  __syncwarp();
+  double* dst = ye + ((int64_t)slab * g.ncells() + cell) * d::ELEM;
+  for (int it = lane; it < d::ELEM; it += 32) dst[it] = s.out[it];
+}
+
+// Sums element contributions into the global vector (fixed cell order) and sets
+// the Dirichlet rows: y = x for J, y = U - g for F.
+template <int K, int Q, bool LIN>
+__global__ void assemble_kernel(LevelGeom g, FeTables T, PhysParams ph, const double* __restrict__ ye,
+                                const double* __restrict__ x, double* __restrict__ y) {
+  using d = D<K, Q>;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= g.ndofs) return;
+  const int S = g.S, nv = g.nv, np = g.np;
+  const int64_t blk = idx / S;
+  const int sp = int(idx % S);
+  const int slab = int(blk / d::NT), a = int(blk % d::NT);
+  const int nv2 = nv * nv;
+  const int64_t base = (int64_t)slab * g.ncells();
+  double acc = 0.0;
+  if (sp < 2 * nv2) {
+    const int c = sp / nv2, t = sp % nv2;
+    const int gx = t % nv, gy = t / nv;
+    if (vel_dirichlet(g, gx, gy)) {
+      if (LIN) {
+        y[idx] = x[idx];
+      } else {
+        double ux, uy;
+        exact_velocity(ph, gx * (g.h / (K + 1)), gy * (g.h / (K + 1)), (slab + T.tnode[a]) * g.dt, ux, uy);
+        y[idx] = x[idx] - (c == 0 ? ux : uy);
+      }
+      return;
+    }
+    const int p = K + 1;
+    const int cx0 = (gx - 1) / p, cx1 = min(gx / p, g.n - 1);
+    const int cy0 = (gy - 1) / p, cy1 = min(gy / p, g.n - 1);
+    for (int cy = cy0; cy <= cy1; ++cy)
+      for (int cx = cx0; cx <= cx1; ++cx) {
+        const int l = (gy - cy * p) * d::NVL + (gx - cx * p);
+        acc += ye[(base + cy * g.n + cx) * d::ELEM + a * (2 * d::NVE + d::NPE) + c * d::NVE + l];
+      }
+  } else {
+    const int t = sp - 2 * nv2;
+    const int px = t % np, py = t / np;
+    const int p = K;
+    const int cx0 = px == 0 ? 0 : (px - 1) / p, cx1 = min(px / p, g.n - 1);
+    const int cy0 = py == 0 ? 0 : (py - 1) / p, cy1 = min(py / p, g.n - 1);
+    for (int cy = cy0; cy <= cy1; ++cy)
+      for (int cx = cx0; cx <= cx1; ++cx) {
+        const int l = (py - cy * p) * d::NPL + (px - cx * p);
+        acc += ye[(base + cy * g.n + cx) * d::ELEM + a * (2 * d::NVE + d::NPE) + 2 * d::NVE + l];
+      }
+  }
+  y[idx] = acc;
+}
+
+__global__ void boundary_kernel(LevelGeom g, FeTables T, PhysParams ph, double* __restrict__ U) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= g.ndofs) return;
+  const int S = g.S, nv = g.nv, nv2 = nv * nv;
+  const int64_t blk = idx / S;
+  const int sp = int(idx % S);
+  const int slab = int(blk / g.nt), a = int(blk % g.nt);
+  double v = 0.0;
+  if (sp < 2 * nv2) {
+    const int c = sp / nv2, t = sp % nv2;
+    const int gx = t % nv, gy = t / nv;
+    if (vel_dirichlet(g, gx, gy)) {
+      double ux, uy;
+      exact_velocity(ph, gx * (g.h / (g.k + 1)), gy * (g.h / (g.k + 1)), (slab + T.tnode[a]) * g.dt, ux, uy);
+      v = c == 0 ? ux : uy;
+    }
+  }
+  U[idx] = v;
+}
+
+// Element convection matrices about W (per time DoF e of W):
+//   Ce[slab][cell][e][c*2+d][i][j] = int phi_i [ delta_cd (W_e.grad) phi_j + phi_j d_d W_{e,c} ]
+template <int K, int Q>
+__global__ void __launch_bounds__(32 * kWarps)
+conv_elements_kernel(LevelGeom g, FeTables T, const double* __restrict__ W, double* __restrict__ Ce) {
+  using d = D<K, Q>;
+  struct Sm {
+    double wn[2 * d::NT][d::NVE];
+    double t1[2 * d::NT][2][d::NVL][d::NQ];
+    double wq[2 * d::NT][3][d::NQ2];
+  };
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Sm& s = reinterpret_cast<Sm*>(smem_raw)[threadIdx.x / 32];
+  const int lane = threadIdx.x & 31;
+  const int cell = blockIdx.x * kWarps + threadIdx.x / 32;
+  const int slab = blockIdx.y;
+  if (cell >= g.ncells()) return;
+  const int CI = cell % g.n, CJ = cell / g.n;
+  const int nv = g.nv;
+  const int64_t nv2 = (int64_t)nv * nv;
+  const double h = g.h, ih = 1.0 / h;
+  for (int it = lane; it < 2 * d::NT * d::NVE; it += 32) {
+    const int f = it / d::NVE, l = it % d::NVE;  // f = c*NT + e
+    const int c = f / d::NT, e = f % d::NT;
+    const int gx = CI * (K + 1) + l % d::NVL, gy = CJ * (K + 1) + l / d::NVL;
+    s.wn[f][l] = W[((int64_t)slab * d::NT + e) * g.S + c * nv2 + (int64_t)gy * nv + gx];
+  }
+  __syncwarp();
+  for (int it = lane; it < 2 * d::NT * d::NVL * d::NQ; it += 32) {
+    const int f = it / (d::NVL * d::NQ), r = it % (d::NVL * d::NQ);
+    const int j = r / d::NQ, qx = r % d::NQ;
+    double v = 0.0, dv = 0.0;
+    for (int i = 0; i < d::NVL; ++i) {
+      v = fma(T.Bv[qx][i], s.wn[f][j * d::NVL + i], v);
+      dv = fma(T.Dv[qx][i], s.wn[f][j * d::NVL + i], dv);
+    }
+    s.t1[f][0][j][qx] = v;
+    s.t1[f][1][j][qx] = dv;
+  }
+  __syncwarp();
+  for (int it = lane; it < 2 * d::NT * d::NQ2; it += 32) {
+    const int f = it / d::NQ2, q = it % d::NQ2;
+    const int qy = q / d::NQ, qx = q % d::NQ;
+    double v = 0.0, vx = 0.0, vy = 0.0;
+    for (int j = 0; j < d::NVL; ++j) {
+      v = fma(T.Bv[qy][j], s.t1[f][0][j][qx], v);
+      vx = fma(T.Bv[qy][j], s.t1[f][1][j][qx], vx);
+      vy = fma(T.Dv[qy][j], s.t1[f][0][j][qx], vy);
+    }
+    s.wq[f][0][q] = v;
+    s.wq[f][1][q] = vx * ih;
+    s.wq[f][2][q] = vy * ih;
+  }
+  __syncwarp();
+  double* dst = Ce + ((int64_t)slab * g.ncells() + cell) * (d::NT * 4 * d::NVE * d::NVE);
+  for (int it = lane; it < d::NT * d::NVE * d::NVE; it += 32) {
+    const int e = it / (d::NVE * d::NVE), r = it % (d::NVE * d::NVE);
+    const int i = r / d::NVE, j = r % d::NVE;
+    const int iy = i / d::NVL, ix = i % d::NVL, jy = j / d::NVL, jx = j % d::NVL;
+    double adv = 0.0, b00 = 0.0, b01 = 0.0, b10 = 0.0, b11 = 0.0;
+    for (int qy = 0; qy < d::NQ; ++qy)
+      for (int qx = 0; qx < d::NQ; ++qx) {
+        const int q = qy * d::NQ + qx;
+        const double om = T.wq[qx] * T.wq[qy] * h * h;
+        const double phi_i = T.Bv[qx][ix] * T.Bv[qy][iy];
+        const double phi_j = T.Bv[qx][jx] * T.Bv[qy][jy];
+        const double djx = T.Dv[qx][jx] * T.Bv[qy][jy] * ih;
+        const double djy = T.Bv[qx][jx] * T.Dv[qy][jy] * ih;
+        const double wi = om * phi_i;
+        const double wij = wi * phi_j;
+        adv = fma(wi, s.wq[0 * d::NT + e][0][q] * djx + s.wq[1 * d::NT + e][0][q] * djy, adv);
+        b00 = fma(wij, s.wq[0 * d::NT + e][1][q], b00);  // d_x W_x
+        b01 = fma(wij, s.wq[0 * d::NT + e][2][q], b01);  // d_y W_x
+        b10 = fma(wij, s.wq[1 * d::NT + e][1][q], b10);  // d_x W_y
+        b11 = fma(wij, s.wq[1 * d::NT + e][2][q], b11);  // d_y W_y
+      }
+    double* m = dst + (int64_t)e * 4 * d::NVE * d::NVE;
+    m[0 * d::NVE * d::NVE + r] = adv + b00;
+    m[1 * d::NVE * d::NVE + r] = b01;
+    m[2 * d::NVE * d::NVE + r] = b10;
+    m[3 * d::NVE * d::NVE + r] = adv + b11;
+  }
+}
+
+__global__ void inject_kernel(LevelGeom gf, LevelGeom gc, const double* __restrict__ Wf, double* __restrict__ Wc) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= gc.ndofs) return;
+  const int64_t blk = idx / gc.S;
+  const int sp = int(idx % gc.S);
+  const int nvc2 = gc.nv * gc.nv;
+  int64_t src;
+  if (sp < 2 * nvc2) {
+    const int c = sp / nvc2, t = sp % nvc2;
+    const int x = t % gc.nv, y = t / gc.nv;
+    src = c * (int64_t)gf.nv * gf.nv + (int64_t)(2 * y) * gf.nv + 2 * x;
+  } else {
+    const int t = sp - 2 * nvc2;
+    const int x = t % gc.np, y = t / gc.np;
+    src = 2 * (int64_t)gf.nv * gf.nv + (int64_t)(2 * y) * gf.np + 2 * x;
+  }
+  Wc[idx] = Wf[blk * gf.S + src];
+}
+
+template <int K, int Q, bool LIN>
+void run_element(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* W, const double* x,
+                 double* y, double* ye, cudaStream_t s) {
+  const size_t smem = sizeof(ElemSmem<K, Q, LIN>) * kWarps;
+  auto kern = element_kernel<K, Q, LIN>;
+  WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((g.ncells() + kWarps - 1) / kWarps, g.N);
+  kern<<<grid, 32 * kWarps, smem, s>>>(g, T, ph, W, x, ye);
+  WR_LAUNCH_CHECK();
+  const int threads = 256;
+  assemble_kernel<K, Q, LIN><<<(unsigned)((g.ndofs + threads - 1) / threads), threads, 0, s>>>(g, T, ph, ye, x, y);
+  WR_LAUNCH_CHECK();
+}
+
+template <bool LIN>
+void dispatch_element(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* W, const double* x,
+                      double* y, double* ye, cudaStream_t s) {
+  if (g.k == 1 && g.q == 0) run_element<1, 0, LIN>(g, T, ph, W, x, y, ye, s);
+  else if (g.k == 1 && g.q == 1) run_element<1, 1, LIN>(g, T, ph, W, x, y, ye, s);
+  else if (g.k == 2 && g.q == 0) run_element<2, 0, LIN>(g, T, ph, W, x, y, ye, s);
+  else if (g.k == 2 && g.q == 1) run_element<2, 1, LIN>(g, T, ph, W, x, y, ye, s);
+  else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
+}
+
+template <int K, int Q>
+void run_conv(const LevelGeom& g, const FeTables& T, const double* W, double* Ce, cudaStream_t s) {
+  using d = D<K, Q>;
+  const size_t smem = (sizeof(double) * (2 * d::NT * d::NVE + 2 * d::NT * 2 * d::NVL * d::NQ + 2 * d::NT * 3 * d::NQ2)) * kWarps;
+  auto kern = conv_elements_kernel<K, Q>;
+  WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((g.ncells() + kWarps - 1) / kWarps, g.N);
+  kern<<<grid, 32 * kWarps, smem, s>>>(g, T, W, Ce);
+  WR_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+void launch_residual(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* U, double* F,
+                     double* ye, cudaStream_t s) {
+  dispatch_element<false>(g, T, ph, nullptr, U, F, ye, s);
+}
+
+void launch_jacobian(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* W, const double* x,
+                     double* y, double* ye, cudaStream_t s) {
+  dispatch_element<true>(g, T, ph, W, x, y, ye, s);
+}
+
+void launch_boundary_values(const LevelGeom& g, const FeTables& T, const PhysParams& ph, double* U, cudaStream_t s) {
+  const int threads = 256;
+  boundary_kernel<<<(unsigned)((g.ndofs + threads - 1) / threads), threads, 0, s>>>(g, T, ph, U);
+  WR_LAUNCH_CHECK();
+}
+
+void launch_conv_elements(const LevelGeom& g, const FeTables& T, const double* W, double* Ce, cudaStream_t s) {
+  if (g.k == 1 && g.q == 0) run_conv<1, 0>(g, T, W, Ce, s);
+  else if (g.k == 1 && g.q == 1) run_conv<1, 1>(g, T, W, Ce, s);
+  else if (g.k == 2 && g.q == 0) run_conv<2, 0>(g, T, W, Ce, s);
+  else if (g.k == 2 && g.q == 1) run_conv<2, 1>(g, T, W, Ce, s);
+  else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
+}
+
+void launch_inject(const LevelGeom& gf, const LevelGeom& gc, const double* Wf, double* Wc, cudaStream_t s) {
+  const int threads = 256;
+  inject_kernel<<<(unsigned)((gc.ndofs + threads - 1) / threads), threads, 0, s>>>(gf, gc, Wf, Wc);
+  WR_LAUNCH_CHECK();
+}

@@ -1,0 +1,567 @@
+// Waveform Vanka+star relaxation (hot-path steps (a)-(d)) and the coarse-level
+// direct solve, which is the same block forward substitution on one block that
+// holds every free DoF.
+//
+// Patches (Sec. 3, NS relaxation; Fig. patches): one per vertex (I, J).  Velocity
+// slots form the (2k+3) x (2k+3) node grid of the closed 2x2-cell block around
+// the vertex (the closure of the vertex star), per component; pressure slots the
+// (2k-1) x (2k-1) grid of the open star.  Slots off the domain or on the
+// Dirichlet boundary are padding: identity rows and columns, zero data.
+//
+// (b) block_factor_kernel, one CTA per (patch, slab): assembles the slab
+//     diagonal block A_nn = J(W)[P_i, P_i] (principal submatrix of the
+//     assembled space-time Jacobian) directly in shared memory from the global
+//     1D mass/stiffness/divergence entries and the element convection matrices,
+//     then inverts it.  For DG(1) the block has 2x2 temporal sub-blocks of size
+//     ms <= 107; it is factored as
+//         A00^{-1},  X = A00^{-1} A01,  S = A11 - A10 X,  S^{-1}
+//     (block LU over the temporal DoFs, Gauss-Jordan with partial pivoting inside
+//     each block), which keeps every working matrix inside shared memory.
+// (a)+(c) block_apply_kernel, one CTA per patch, sequential over slabs:
+//     gathers r on the patch, adds the jump coupling tau_a(0) M_u y_{n-1}
+//     (Eq. waveform_patch_solve: A_{n,n-1} = -tau_a(0) M_u on the last temporal
+//     DoF's velocity), applies the stored factors (GEMVs streamed from HBM).
+// (d) scatter_kernel: every global DoF pulls the outputs of the patches that
+//     contain it in a fixed order (deterministic weighted additive scatter, w = 1).
+#include <cmath>
+
+#include "wrmg_internal.h"
+
+namespace {
+
+template <int K>
+struct PD {
+  static constexpr int NVG = 2 * K + 3, NPG = 2 * K - 1;
+  static constexpr int NVG2 = NVG * NVG;
+  static constexpr int MS = 2 * NVG2 + NPG * NPG;         // 51 (k = 1) or 107 (k = 2)
+  static constexpr int LD = (MS % 2) ? MS : MS + 1;       // odd leading dimension in smem
+  static constexpr int NVL = K + 2, NVE = NVL * NVL;
+};
+
+struct Slot {
+  int field;   // 0, 1 velocity component, 2 pressure
+  int gx, gy;  // global node
+  int sp;      // spatial index within a temporal block, -1 = padding
+};
+
+__device__ __forceinline__ void block_origin(const LevelGeom& g, const BlockSet& bs, int blk, int& vx0, int& vy0,
+                                             int& px0, int& py0) {
+  if (bs.kind == 0) {
+    const int I = blk % (g.n + 1), J = blk / (g.n + 1);
+    vx0 = (I - 1) * (g.k + 1);
+    vy0 = (J - 1) * (g.k + 1);
+    px0 = I * g.k - (g.k - 1);
+    py0 = J * g.k - (g.k - 1);
+  } else {
+    vx0 = vy0 = 1;
+    px0 = py0 = 0;
+  }
+}
+
+__device__ __forceinline__ Slot decode_slot(const LevelGeom& g, const BlockSet& bs, int blk, int s) {
+  int vx0, vy0, px0, py0;
+  block_origin(g, bs, blk, vx0, vy0, px0, py0);
+  const int nv2g = bs.nvg * bs.nvg;
+  Slot r;
+  r.sp = -1;
+  if (s < 2 * nv2g) {
+    r.field = s / nv2g;
+    const int t = s % nv2g;
+    r.gx = vx0 + t % bs.nvg;
+    r.gy = vy0 + t / bs.nvg;
+    if (r.gx >= 1 && r.gx <= g.nv - 2 && r.gy >= 1 && r.gy <= g.nv - 2)
+      r.sp = r.field * g.nv * g.nv + r.gy * g.nv + r.gx;
+  } else if (s < 2 * nv2g + bs.npg * bs.npg) {
+    r.field = 2;
+    const int t = s - 2 * nv2g;
+    r.gx = px0 + t % bs.npg;
+    r.gy = py0 + t / bs.npg;
+    const bool pinned = bs.kind == 1 && r.gx == 0 && r.gy == 0;
+    if (r.gx >= 0 && r.gx < g.np && r.gy >= 0 && r.gy < g.np && !pinned)
+      r.sp = 2 * g.nv * g.nv + r.gy * g.np + r.gx;
+  } else {
+    r.field = 3;
+    r.gx = r.gy = 0;
+  }
+  return r;
+}
+
+// cells [lo, hi] of the 1D mesh containing node g of a degree-p Lagrange space
+__device__ __forceinline__ int cell_lo(int g, int p) { return g == 0 ? 0 : (g - 1) / p; }
+__device__ __forceinline__ int cell_hi(int g, int p, int n) { return min(g / p, n - 1); }
+
+// global 1D velocity-velocity matrix entry sum_c ref[gi - pc][gj - pc]
+template <int K>
+__device__ __forceinline__ double vv1(const double (*ref)[WR_MAX_NVL], int n, int gi, int gj) {
+  const int p = K + 1;
+  const int lo = max(cell_lo(gi, p), cell_lo(gj, p)), hi = min(cell_hi(gi, p, n), cell_hi(gj, p, n));
+  double v = 0.0;
+  for (int c = lo; c <= hi; ++c) v += ref[gi - p * c][gj - p * c];
+  return v;
+}
+// global 1D pressure-velocity entry sum_c ref[pn - kc][vn - (k+1)c]
+template <int K>
+__device__ __forceinline__ double pv1(const double (*ref)[WR_MAX_NVL], int n, int pn, int vn) {
+  const int lo = max(cell_lo(pn, K), cell_lo(vn, K + 1)), hi = min(cell_hi(pn, K, n), cell_hi(vn, K + 1, n));
+  double v = 0.0;
+  for (int c = lo; c <= hi; ++c) v += ref[pn - K * c][vn - (K + 1) * c];
+  return v;
+}
+
+// Entry (a, b) temporal block, slots si, sj, of the slab diagonal block of J(W).
+template <int K, int Q>
+__device__ __noinline__ double jac_entry(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* __restrict__ Ce,
+                            int slab, const Slot& si, const Slot& sj, int a, int b) {
+  using pd = PD<K>;
+  constexpr int NT = Q + 1;
+  if (si.sp < 0 || sj.sp < 0) return 0.0;  // padding is handled by the callers
+  const double h = g.h, dt = g.dt;
+  const int n = g.n;
+  if (si.field < 2 && sj.field < 2) {
+    double v = 0.0;
+    if (si.field == sj.field) {
+      const double mx = h * vv1<K>(T.m1, n, si.gx, sj.gx), my = h * vv1<K>(T.m1, n, si.gy, sj.gy);
+      const double kx = vv1<K>(T.k1, n, si.gx, sj.gx) / h, ky = vv1<K>(T.k1, n, si.gy, sj.gy) / h;
+      v = T.Kt[a][b] * mx * my + dt * ph.nu * T.Wt[a][b] * (kx * my + mx * ky);
+    }
+    if (ph.conv != 0.0) {
+      const int p = K + 1;
+      const int cx0 = max(cell_lo(si.gx, p), cell_lo(sj.gx, p)), cx1 = min(cell_hi(si.gx, p, n), cell_hi(sj.gx, p, n));
+      const int cy0 = max(cell_lo(si.gy, p), cell_lo(sj.gy, p)), cy1 = min(cell_hi(si.gy, p, n), cell_hi(sj.gy, p, n));
+      double cv = 0.0;
+      for (int cy = cy0; cy <= cy1; ++cy)
+        for (int cx = cx0; cx <= cx1; ++cx) {
+          const int li = (si.gy - p * cy) * pd::NVL + (si.gx - p * cx);
+          const int lj = (sj.gy - p * cy) * pd::NVL + (sj.gx - p * cx);
+          const double* m = Ce + ((int64_t)slab * g.ncells() + cy * n + cx) * (NT * 4 * pd::NVE * pd::NVE) +
+                            (si.field * 2 + sj.field) * pd::NVE * pd::NVE + li * pd::NVE + lj;
+#pragma unroll
+          for (int e = 0; e < NT; ++e) cv += T.T3[a][b][e] * m[(int64_t)e * 4 * pd::NVE * pd::NVE];
+        }
+      v += dt * ph.conv * cv;
+    }
+    return v;
+  }
+  if (si.field == 2 && sj.field == 2) return 0.0;
+  // velocity component c at (vx, vy) against pressure node (px, py): int chi d_c phi
+  const Slot& sv = si.field < 2 ? si : sj;
+  const Slot& sp = si.field < 2 ? sj : si;
+  double gval;
+  if (sv.field == 0)
+    gval = pv1<K>(T.d1, n, sp.gx, sv.gx) * h * pv1<K>(T.c1, n, sp.gy, sv.gy);
+  else
+    gval = h * pv1<K>(T.c1, n, sp.gx, sv.gx) * pv1<K>(T.d1, n, sp.gy, sv.gy);
+  return dt * T.Wt[a][b] * gval;
+}
+
+// In-place Gauss-Jordan inversion with partial pivoting (largest |.|, lowest
+// row on ties) of the MS x MS row-major matrix A (leading dimension LD) in
+// shared memory.  Returns false (to all threads) if a zero pivot was met.
+template <int MS, int LD, int NTH>
+__device__ bool gauss_jordan(double* A, double* colbuf, int* perm, int* sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  bool ok = true;
+#pragma unroll 1
+  for (int p = 0; p < MS; ++p) {
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = MS;
+      for (int i = p + lane; i < MS; i += 32) {
+        const double v = fabs(A[i * LD + p]);
+        if (v > best) { best = v; bi = i; }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        sh[0] = bi;
+        perm[p] = bi;
+        if (!(best > 0.0)) sh[1] = 1;
+      }
+    }
+    __syncthreads();
+    const int r = sh[0];
+    if (r != p)
+      for (int j = tid; j < MS; j += NTH) {
+        const double t = A[p * LD + j];
+        A[p * LD + j] = A[r * LD + j];
+        A[r * LD + j] = t;
+      }
+    __syncthreads();
+    const double inv = 1.0 / A[p * LD + p];
+    for (int i = tid; i < MS; i += NTH) colbuf[i] = A[i * LD + p];
+    __syncthreads();
+    for (int j = tid; j < MS; j += NTH) A[p * LD + j] = (j == p) ? inv : A[p * LD + j] * inv;
+    __syncthreads();
+    for (int e = tid; e < MS * MS; e += NTH) {
+      const int i = e / MS, j = e - (e / MS) * MS;
+      if (i == p) continue;
+      if (j == p)
+        A[i * LD + j] = -colbuf[i] * inv;
+      else
+        A[i * LD + j] = fma(-colbuf[i], A[p * LD + j], A[i * LD + j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll 1
+  for (int p = MS - 1; p >= 0; --p) {
+    const int r = perm[p];
+    if (r != p)
+      for (int i = tid; i < MS; i += NTH) {
+        const double t = A[i * LD + p];
+        A[i * LD + p] = A[i * LD + r];
+        A[i * LD + r] = t;
+      }
+    __syncthreads();
+  }
+  ok = sh[1] == 0;
+  return ok;
+}
+
+template <int MS, int LD, int NTH, typename FT>
+__device__ void store_colmajor(const double* A, FT* dst) {
+  for (int e = threadIdx.x; e < MS * MS; e += NTH) {
+    const int j = e / MS, i = e - j * MS;
+    dst[e] = (FT)A[i * LD + j];
+  }
+}
+
+template <int K, int Q>
+__device__ void assemble_block(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* Ce, int slab,
+                               const Slot* slots, double* M, int a, int b, int nth) {
+  using pd = PD<K>;
+  for (int e = threadIdx.x; e < pd::MS * pd::MS; e += nth) {
+    const int i = e / pd::MS, j = e - i * pd::MS;
+    double v;
+    if (slots[i].sp < 0 || slots[j].sp < 0)
+      v = (i == j && a == b) ? 1.0 : 0.0;
+    else
+      v = jac_entry<K, Q>(g, T, ph, Ce, slab, slots[i], slots[j], a, b);
+    M[i * pd::LD + j] = v;
+  }
+}
+
+template <int K, int Q>
+__device__ void add_block(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* Ce, int slab,
+                          const Slot* slots, double* M, int a, int b, int nth) {
+  using pd = PD<K>;
+  for (int e = threadIdx.x; e < pd::MS * pd::MS; e += nth) {
+    const int i = e / pd::MS, j = e - i * pd::MS;
+    double v;
+    if (slots[i].sp < 0 || slots[j].sp < 0)
+      v = (i == j && a == b) ? 1.0 : 0.0;
+    else
+      v = jac_entry<K, Q>(g, T, ph, Ce, slab, slots[i], slots[j], a, b);
+    M[i * pd::LD + j] += v;
+  }
+}
+
+template <int K, int Q, typename FT, int NTH>
+__global__ void __launch_bounds__(NTH)
+block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const double* __restrict__ Ce,
+                    FT* __restrict__ factors, int* __restrict__ status) {
+  using pd = PD<K>;
+  constexpr int MS = pd::MS, LD = pd::LD;
+  constexpr int NE = (MS * MS + NTH - 1) / NTH;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* M1 = reinterpret_cast<double*>(smem_raw);
+  double* M2 = M1 + MS * LD;
+  double* colbuf = M2 + (Q == 1 ? MS * LD : 0);
+  Slot* slots = reinterpret_cast<Slot*>(colbuf + MS);
+  int* perm = reinterpret_cast<int*>(slots + MS);
+  int* sh = perm + MS;
+  const int blk = blockIdx.x, slab = blockIdx.y;
+  for (int s = threadIdx.x; s < MS; s += NTH) slots[s] = decode_slot(g, bs, blk, s);
+  if (threadIdx.x == 0) { sh[0] = 0; sh[1] = 0; }
+  __syncthreads();
+  FT* F = factors + ((int64_t)blk * g.N + slab) * (Q + 1) * (Q + 1) * MS * MS;
+  bool ok;
+  if constexpr (Q == 0) {
+    assemble_block<K, Q>(g, T, ph, Ce, slab, slots, M1, 0, 0, NTH);
+    __syncthreads();
+    ok = gauss_jordan<MS, LD, NTH>(M1, colbuf, perm, sh);
+    store_colmajor<MS, LD, NTH>(M1, F);
+  } else {
+    // A00^{-1}
+    assemble_block<K, Q>(g, T, ph, Ce, slab, slots, M1, 0, 0, NTH);
+    __syncthreads();
+    ok = gauss_jordan<MS, LD, NTH>(M1, colbuf, perm, sh);
+    store_colmajor<MS, LD, NTH>(M1, F);
+    // X = A00^{-1} A01
+    assemble_block<K, Q>(g, T, ph, Ce, slab, slots, M2, 0, 1, NTH);
+    __syncthreads();
+    double acc[NE];
+    int ioff[NE], jcol[NE];
+#pragma unroll
+    for (int t = 0; t < NE; ++t) {
+      const int e = threadIdx.x + t * NTH;
+      const int i = e < MS * MS ? e / MS : 0;
+      ioff[t] = i * LD;
+      jcol[t] = e < MS * MS ? e - i * MS : 0;
+      acc[t] = 0.0;
+    }
+#pragma unroll 1
+    for (int l = 0; l < MS; ++l)
+#pragma unroll
+      for (int t = 0; t < NE; ++t) acc[t] = fma(M1[ioff[t] + l], M2[l * LD + jcol[t]], acc[t]);
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < NE; ++t)
+      if (threadIdx.x + t * NTH < MS * MS) M2[ioff[t] + jcol[t]] = acc[t];
+    __syncthreads();
+    store_colmajor<MS, LD, NTH>(M2, F + 3 * MS * MS);
+    // A10
+    assemble_block<K, Q>(g, T, ph, Ce, slab, slots, M1, 1, 0, NTH);
+    __syncthreads();
+    store_colmajor<MS, LD, NTH>(M1, F + 1 * MS * MS);
+    // S = A11 - A10 X: the product in registers, then A11 added entry by entry
+#pragma unroll
+    for (int t = 0; t < NE; ++t) acc[t] = 0.0;
+#pragma unroll 1
+    for (int l = 0; l < MS; ++l)
+#pragma unroll
+      for (int t = 0; t < NE; ++t) acc[t] = fma(-M1[ioff[t] + l], M2[l * LD + jcol[t]], acc[t]);
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < NE; ++t)
+      if (threadIdx.x + t * NTH < MS * MS) M2[ioff[t] + jcol[t]] = acc[t];
+    __syncthreads();
+    add_block<K, Q>(g, T, ph, Ce, slab, slots, M2, 1, 1, NTH);
+    __syncthreads();
+    ok = gauss_jordan<MS, LD, NTH>(M2, colbuf, perm, sh) && ok;
+    store_colmajor<MS, LD, NTH>(M2, F + 2 * MS * MS);
+  }
+  if (!ok && threadIdx.x == 0) atomicExch(status, 1);
+}
+
+// y[i] (+)= sum_j F[j*MS + i] x[j] for thread i < MS (column-major factor block)
+template <int MS, typename FT>
+__device__ __forceinline__ FT gemv_row(const FT* __restrict__ F, const FT* x, int i) {
+  FT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  int j = 0;
+#pragma unroll 4
+  for (; j + 3 < MS; j += 4) {
+    a0 = fma(__ldcs(F + (j + 0) * MS + i), x[j + 0], a0);
+    a1 = fma(__ldcs(F + (j + 1) * MS + i), x[j + 1], a1);
+    a2 = fma(__ldcs(F + (j + 2) * MS + i), x[j + 2], a2);
+    a3 = fma(__ldcs(F + (j + 3) * MS + i), x[j + 3], a3);
+  }
+  for (; j < MS; ++j) a0 = fma(__ldcs(F + j * MS + i), x[j], a0);
+  return (a0 + a1) + (a2 + a3);
+}
+
+template <int K, int Q, typename FT>
+__global__ void __launch_bounds__(128)
+block_apply_kernel(LevelGeom g, FeTables T, BlockSet bs, const FT* __restrict__ factors, const double* __restrict__ r,
+                   double* __restrict__ out) {
+  using pd = PD<K>;
+  constexpr int MS = pd::MS, NT = Q + 1, NVG = pd::NVG, NVG2 = pd::NVG2;
+  __shared__ int sidx[MS];
+  __shared__ FT rhs[NT][MS];
+  __shared__ FT y[NT][MS];
+  __shared__ FT yp[2][NVG2];
+  __shared__ FT tm[2][NVG2];
+  __shared__ FT mx[NVG][NVG], my[NVG][NVG];
+  const int blk = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  int vx0, vy0, px0, py0;
+  block_origin(g, bs, blk, vx0, vy0, px0, py0);
+  const int nvg = bs.nvg;  // <= NVG
+  for (int s = tid; s < MS; s += nth) sidx[s] = decode_slot(g, bs, blk, s).sp;
+  for (int e = tid; e < NVG * NVG; e += nth) {
+    const int i = e / NVG, j = e % NVG;
+    const int xi = vx0 + i, xj = vx0 + j, yi = vy0 + i, yj = vy0 + j;
+    const bool vx = i < nvg && j < nvg && xi >= 1 && xi <= g.nv - 2 && xj >= 1 && xj <= g.nv - 2;
+    const bool vy = i < nvg && j < nvg && yi >= 1 && yi <= g.nv - 2 && yj >= 1 && yj <= g.nv - 2;
+    mx[i][j] = vx ? (FT)(g.h * vv1<K>(T.m1, g.n, xi, xj)) : (FT)0;
+    my[i][j] = vy ? (FT)(g.h * vv1<K>(T.m1, g.n, yi, yj)) : (FT)0;
+  }
+  for (int e = tid; e < 2 * NVG2; e += nth) (&yp[0][0])[e] = 0;
+  __syncthreads();
+  const int nv2g = nvg * nvg;
+  for (int slab = 0; slab < g.N; ++slab) {
+    // (a) gather
+    for (int e = tid; e < NT * MS; e += nth) {
+      const int a = e / MS, s = e % MS;
+      const int sp = sidx[s];
+      rhs[a][s] = sp >= 0 ? (FT)r[((int64_t)slab * NT + a) * g.S + sp] : (FT)0;
+    }
+    if (slab > 0) {
+      // jump coupling: rhs_a += tau_a(0) M_u y_{n-1, last} (tensor-product mass on the slot grid)
+      for (int e = tid; e < 2 * nv2g; e += nth) {
+        const int c = e / nv2g, t = e % nv2g, iy = t / nvg, jx = t % nvg;
+        FT acc = 0;
+        for (int jy = 0; jy < nvg; ++jy) acc = fma(my[iy][jy], yp[c][jy * nvg + jx], acc);
+        tm[c][t] = acc;
+      }
+      __syncthreads();
+      for (int e = tid; e < 2 * nv2g; e += nth) {
+        const int c = e / nv2g, t = e % nv2g, iy = t / nvg, ix = t % nvg;
+        FT acc = 0;
+        for (int jx = 0; jx < nvg; ++jx) acc = fma(mx[ix][jx], tm[c][iy * nvg + jx], acc);
+        const int s = c * nv2g + t;
+        if (sidx[s] >= 0)
+          for (int a = 0; a < NT; ++a) rhs[a][s] += (FT)T.tau0[a] * acc;
+      }
+    }
+    __syncthreads();
+    // (c) apply the stored slab factors
+    const FT* F = factors + ((int64_t)blk * g.N + slab) * NT * NT * MS * MS;
+    if constexpr (Q == 0) {
+      if (tid < MS) y[0][tid] = gemv_row<MS>(F, rhs[0], tid);
+      __syncthreads();
+    } else {
+      if (tid < MS) y[0][tid] = gemv_row<MS>(F, rhs[0], tid);                        // z0 = A00^{-1} r0
+      __syncthreads();
+      if (tid < MS) rhs[1][tid] -= gemv_row<MS>(F + 1 * MS * MS, y[0], tid);          // s1 = r1 - A10 z0
+      __syncthreads();
+      if (tid < MS) y[1][tid] = gemv_row<MS>(F + 2 * MS * MS, rhs[1], tid);          // y1 = S^{-1} s1
+      __syncthreads();
+      if (tid < MS) y[0][tid] -= gemv_row<MS>(F + 3 * MS * MS, y[1], tid);           // y0 = z0 - X y1
+      __syncthreads();
+    }
+    // output
+    for (int e = tid; e < NT * MS; e += nth) {
+      const int a = e / MS, s = e % MS;
+      if (bs.kind == 0) {
+        out[(((int64_t)blk * g.N + slab) * NT + a) * MS + s] = (double)y[a][s];
+      } else if (sidx[s] >= 0) {
+        out[((int64_t)slab * NT + a) * g.S + sidx[s]] = (double)y[a][s];
+      }
+    }
+    for (int e = tid; e < 2 * nv2g; e += nth) {
+      const int c = e / nv2g, t = e % nv2g;
+      yp[c][t] = y[NT - 1][c * nv2g + t];
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+__device__ __forceinline__ int ceildiv(int a, int b) { return -floordiv(-a, b); }
+
+template <int K, int Q>
+__global__ void scatter_kernel(LevelGeom g, const double* __restrict__ Yp, double* __restrict__ y) {
+  using pd = PD<K>;
+  constexpr int MS = pd::MS, NT = Q + 1;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= g.ndofs) return;
+  const int S = g.S, nv = g.nv, nv2 = nv * nv, n = g.n;
+  const int64_t blkt = idx / S;
+  const int sp = int(idx % S);
+  const int slab = int(blkt / NT), a = int(blkt % NT);
+  double acc = 0.0;
+  if (sp < 2 * nv2) {
+    const int c = sp / nv2, t = sp % nv2, gx = t % nv, gy = t / nv;
+    if (gx == 0 || gy == 0 || gx == nv - 1 || gy == nv - 1) { y[idx] = 0.0; return; }
+    const int p = K + 1;
+    const int I0 = max(0, ceildiv(gx, p) - 1), I1 = min(n, gx / p + 1);
+    const int J0 = max(0, ceildiv(gy, p) - 1), J1 = min(n, gy / p + 1);
+    for (int J = J0; J <= J1; ++J)
+      for (int I = I0; I <= I1; ++I) {
+        const int lx = gx - (I - 1) * p, ly = gy - (J - 1) * p;
+        const int s = c * pd::NVG2 + ly * pd::NVG + lx;
+        acc += Yp[(((int64_t)(J * (n + 1) + I) * g.N + slab) * NT + a) * MS + s];
+      }
+  } else {
+    const int t = sp - 2 * nv2, px = t % g.np, py = t / g.np;
+    const int I0 = max(0, ceildiv(px - K + 1, K)), I1 = min(n, floordiv(px + K - 1, K));
+    const int J0 = max(0, ceildiv(py - K + 1, K)), J1 = min(n, floordiv(py + K - 1, K));
+    for (int J = J0; J <= J1; ++J)
+      for (int I = I0; I <= I1; ++I) {
+        const int lx = px - (I * K - (K - 1)), ly = py - (J * K - (K - 1));
+        const int s = 2 * pd::NVG2 + ly * pd::NPG + lx;
+        acc += Yp[(((int64_t)(J * (n + 1) + I) * g.N + slab) * NT + a) * MS + s];
+      }
+  }
+  y[idx] = acc;
+}
+
+template <int K, int Q, typename FT>
+void run_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const BlockSet& bs, const double* Ce,
+                FT* factors, int* status, cudaStream_t s) {
+  using pd = PD<K>;
+  constexpr int NTH = K == 1 ? 256 : 512;
+  const size_t smem = sizeof(double) * ((Q == 1 ? 2 : 1) * pd::MS * pd::LD + pd::MS) + sizeof(Slot) * pd::MS +
+                      sizeof(int) * (pd::MS + 2);
+  auto kern = block_factor_kernel<K, Q, FT, NTH>;
+  WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int nblk = bs.kind == 0 ? g.npatch() : 1;
+  kern<<<dim3(nblk, g.N), NTH, smem, s>>>(g, T, ph, bs, Ce, factors, status);
+  WR_LAUNCH_CHECK();
+}
+
+template <int K, int Q, typename FT>
+void run_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs, const FT* factors, const double* r,
+               double* out, cudaStream_t s) {
+  using pd = PD<K>;
+  const int nth = ((pd::MS + 31) / 32) * 32;
+  const int nblk = bs.kind == 0 ? g.npatch() : 1;
+  block_apply_kernel<K, Q, FT><<<nblk, nth, 0, s>>>(g, T, bs, factors, r, out);
+  WR_LAUNCH_CHECK();
+}
+
+int* status_buffer() {
+  static int* st = nullptr;  // per process; reset before each factorisation
+  if (!st) WR_CUDA(cudaMalloc(&st, sizeof(int)));
+  return st;
+}
+
+}  // namespace
+
+void launch_block_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const BlockSet& bs,
+                         const double* Ce, void* factors, int precision, cudaStream_t s) {
+  int* st = status_buffer();
+  WR_CUDA(cudaMemsetAsync(st, 0, sizeof(int), s));
+#define WR_F(K_, Q_)                                                                                   \
+  if (g.k == K_ && g.q == Q_) {                                                                        \
+    if (precision == WR_FP32)                                                                          \
+      run_factor<K_, Q_, float>(g, T, ph, bs, Ce, static_cast<float*>(factors), st, s);                \
+    else                                                                                               \
+      run_factor<K_, Q_, double>(g, T, ph, bs, Ce, static_cast<double*>(factors), st, s);              \
+  } else
+  WR_F(1, 0) WR_F(1, 1) WR_F(2, 0) WR_F(2, 1) throw WrError(WR_ERR_ARG, "unsupported (k, q)");
+#undef WR_F
+  int h = 0;
+  WR_CUDA(cudaMemcpyAsync(&h, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+  WR_CUDA(cudaStreamSynchronize(s));
+  if (h) throw WrError(WR_ERR_NAN, "singular patch block (zero pivot) in the factorisation");
+}
+
+void launch_block_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs, const void* factors, int precision,
+                        const double* r, double* out, cudaStream_t s) {
+#define WR_A(K_, Q_)                                                                                          \
+  if (g.k == K_ && g.q == Q_) {                                                                               \
+    if (precision == WR_FP32)                                                                                 \
+      run_apply<K_, Q_, float>(g, T, bs, static_cast<const float*>(factors), r, out, s);                     \
+    else                                                                                                      \
+      run_apply<K_, Q_, double>(g, T, bs, static_cast<const double*>(factors), r, out, s);                   \
+  } else
+  WR_A(1, 0) WR_A(1, 1) WR_A(2, 0) WR_A(2, 1) throw WrError(WR_ERR_ARG, "unsupported (k, q)");
+#undef WR_A
+}
+
+void launch_scatter(const LevelGeom& g, const BlockSet& bs, const double* Yp, double* y, cudaStream_t s) {
+  (void)bs;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((g.ndofs + threads - 1) / threads);
+  if (g.k == 1 && g.q == 0) scatter_kernel<1, 0><<<blocks, threads, 0, s>>>(g, Yp, y);
+  else if (g.k == 1 && g.q == 1) scatter_kernel<1, 1><<<blocks, threads, 0, s>>>(g, Yp, y);
+  else if (g.k == 2 && g.q == 0) scatter_kernel<2, 0><<<blocks, threads, 0, s>>>(g, Yp, y);
+  else if (g.k == 2 && g.q == 1) scatter_kernel<2, 1><<<blocks, threads, 0, s>>>(g, Yp, y);
+  else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
+  WR_LAUNCH_CHECK();
+}
+
+namespace {
+__global__ void patch_slots_kernel(LevelGeom g, BlockSet bs, int blk, int* __restrict__ out) {
+  for (int s = threadIdx.x; s < bs.ms; s += blockDim.x) out[s] = decode_slot(g, bs, blk, s).sp;
+}
+}  // namespace
+
+// Spatial index of every slot of block `blk` as the kernels decode it (-1 = padding).
+void launch_patch_slots(const LevelGeom& g, const BlockSet& bs, int blk, int* out_sp, cudaStream_t s) {
+  patch_slots_kernel<<<1, 128, 0, s>>>(g, bs, blk, out_sp);
+  WR_LAUNCH_CHECK();
+}

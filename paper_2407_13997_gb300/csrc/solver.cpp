@@ -1,0 +1,781 @@
+// Host control plane of libwrmg: the level hierarchy, the V(2,2) cycle
+// (Algorithm Vcycle), Chebyshev(2) relaxation weights with the 10-step Arnoldi
+// eigen-estimate (Sec. 3), the coarse direct solve, FGMRES (restart 30, MGS,
+// Givens) and inexact Newton with Eisenstat-Walker forcing terms (Sec. 5).
+// Every vector operation runs in this library's kernels on the context stream;
+// only Krylov scalars (dot products, Hessenberg entries) come to the host.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <atomic>
+#include <memory>
+
+#include "wrmg_internal.h"
+
+void launch_patch_slots(const LevelGeom& g, const BlockSet& bs, int blk, int* out_sp, cudaStream_t s);
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+}  // namespace
+void wr_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+struct Level {
+  LevelGeom g;
+  BlockSet bs;
+  double* W = nullptr;
+  void* factors = nullptr;
+  double *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *z = nullptr, *t = nullptr;
+  double lam = 0.0;
+  bool lam_set = false;
+};
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct wr_ctx {
+  std::string err;
+  cudaStream_t s = nullptr;
+  wr_options opt;
+  PhysParams ph;
+  FeTables tab;
+  int k = 0, q = 0, N = 0;
+  double T = 1.0;
+  std::vector<Level> L;  // 0 = coarsest
+  BlockSet cbs;
+  double* cfactors = nullptr;
+  double *Ce = nullptr, *ye = nullptr, *Yp = nullptr;
+  std::vector<double*> V, Z;
+  double *F = nullptr, *w = nullptr, *hb = nullptr, *hx = nullptr;
+  double *partials = nullptr, *dres = nullptr, *hres = nullptr;
+  int* slots = nullptr;
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  bool linearised = false;
+  int vcycles = 0;
+  // CUDA-event timing of the smoother-apply kernel (per level), enabled by wr_profile
+  bool prof = false;
+  std::vector<std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+
+  cudaEvent_t next_event() {
+    if (ev_used == ev_pool.size()) {
+      cudaEvent_t e;
+      WR_CUDA(cudaEventCreate(&e));
+      ev_pool.push_back(e);
+    }
+    return ev_pool[ev_used++];
+  }
+
+  template <typename Tp>
+  Tp* alloc(size_t count) {
+    void* p = nullptr;
+    const size_t nb = std::max<size_t>(count * sizeof(Tp), 16);
+    cudaError_t e = cudaMalloc(&p, nb);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw WrError(WR_ERR_NOMEM, "cudaMalloc of " + std::to_string(nb) + " bytes failed (" + cudaGetErrorString(e) +
+                                      "); " + std::to_string(bytes) + " bytes already held");
+    }
+    allocs.push_back(p);
+    bytes += nb;
+    return static_cast<Tp*>(p);
+  }
+  ~wr_ctx() {
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    for (void* p : allocs) cudaFree(p);
+    if (hres) cudaFreeHost(hres);
+  }
+
+  Level& fine() { return L.back(); }
+  int top() const { return (int)L.size() - 1; }
+
+  double dot(int64_t n, const double* x, const double* y) {
+    vec_dot_dev(n, x, y, partials, dres, s);
+    WR_CUDA(cudaMemcpyAsync(hres, dres, sizeof(double), cudaMemcpyDeviceToHost, s));
+    WR_CUDA(cudaStreamSynchronize(s));
+    return *hres;
+  }
+  double norm(int64_t n, const double* x) { return std::sqrt(dot(n, x, x)); }
+
+  void jac(int l, const double* x, double* y) { launch_jacobian(L[l].g, tab, ph, L[l].W, x, y, ye, s); }
+
+  void patch_apply(int l, const double* r, double* y) {
+    if (!linearised) throw WrError(WR_ERR_STATE, "wr_linearise must be called first");
+    if (prof) {
+      cudaEvent_t e0 = next_event(), e1 = next_event();
+      WR_CUDA(cudaEventRecord(e0, s));
+      launch_block_apply(L[l].g, tab, L[l].bs, L[l].factors, opt.precision, r, Yp, s);
+      WR_CUDA(cudaEventRecord(e1, s));
+      prof_ev[l].push_back({e0, e1});
+    } else {
+      launch_block_apply(L[l].g, tab, L[l].bs, L[l].factors, opt.precision, r, Yp, s);
+    }
+    launch_scatter(L[l].g, L[l].bs, Yp, y, s);
+  }
+
+  void coarse_solve(const double* b, double* x) {
+    if (!linearised) throw WrError(WR_ERR_STATE, "wr_linearise must be called first");
+    const LevelGeom& g = L[0].g;
+    vec_zero(g.ndofs, x, s);
+    launch_block_apply(g, tab, cbs, cfactors, WR_FP64, b, x, s);
+    launch_project_pressure(g, tab, x, s);
+  }
+
+  // opt.cheb_steps steps of preconditioned Chebyshev iteration (Saad, Alg. 12.1)
+  void smooth(int l, const double* b, double* x, bool zero_guess) {
+    Level& lv = L[l];
+    const int64_t n = lv.g.ndofs;
+    if (!lv.lam_set) throw WrError(WR_ERR_STATE, "no eigen-estimate on this level");
+    const double a = opt.cheb_lo * lv.lam, bb = opt.cheb_hi * lv.lam;
+    const double theta = 0.5 * (bb + a), delta = 0.5 * (bb - a), sigma = theta / delta;
+    if (zero_guess) {
+      vec_zero(n, x, s);
+      vec_copy(n, b, lv.r, s);
+    } else {
+      jac(l, x, lv.t);
+      vec_copy(n, b, lv.r, s);
+      vec_axpby(n, -1.0, lv.t, 1.0, lv.r, s);
+    }
+    double rho = 1.0 / sigma;
+    patch_apply(l, lv.r, lv.d);
+    vec_scale(n, 1.0 / theta, lv.d, s);
+    for (int step = 0; step < opt.cheb_steps; ++step) {
+      vec_axpby(n, 1.0, lv.d, 1.0, x, s);
+      if (step == opt.cheb_steps - 1) break;
+      jac(l, x, lv.t);
+      vec_copy(n, b, lv.r, s);
+      vec_axpby(n, -1.0, lv.t, 1.0, lv.r, s);
+      patch_apply(l, lv.r, lv.z);
+      const double rho_new = 1.0 / (2.0 * sigma - rho);
+      vec_axpby(n, 2.0 * rho_new / delta, lv.z, rho_new * rho, lv.d, s);
+      rho = rho_new;
+    }
+  }
+
+  void vcycle(const double* b, double* x) {
+    const int T_ = top();
+    std::vector<const double*> bl(T_ + 1);
+    std::vector<double*> xl(T_ + 1);
+    for (int l = 0; l <= T_; ++l) {
+      bl[l] = L[l].b;
+      xl[l] = L[l].x;
+    }
+    bl[T_] = b;
+    xl[T_] = x;
+    for (int l = T_; l >= 1; --l) {
+      smooth(l, bl[l], xl[l], true);
+      jac(l, xl[l], L[l].t);
+      vec_copy(L[l].g.ndofs, bl[l], L[l].r, s);
+      vec_axpby(L[l].g.ndofs, -1.0, L[l].t, 1.0, L[l].r, s);
+      launch_restrict(L[l].g, L[l - 1].g, tab, L[l].r, L[l - 1].b, s);
+    }
+    coarse_solve(L[0].b, xl[0]);
+    for (int l = 1; l <= T_; ++l) {
+      launch_prolong_add(L[l].g, L[l - 1].g, tab, xl[l - 1], xl[l], s);
+      smooth(l, bl[l], xl[l], false);
+    }
+    ++vcycles;
+  }
+
+  void linearise(const double* W, bool eig) {
+    const int T_ = top();
+    vec_copy(L[T_].g.ndofs, W, L[T_].W, s);
+    for (int l = T_; l >= 1; --l) launch_inject(L[l].g, L[l - 1].g, L[l].W, L[l - 1].W, s);
+    for (int l = 1; l <= T_; ++l) {
+      if (ph.conv != 0.0) launch_conv_elements(L[l].g, tab, L[l].W, Ce, s);
+      launch_block_factor(L[l].g, tab, ph, L[l].bs, Ce, L[l].factors, opt.precision, s);
+    }
+    if (ph.conv != 0.0) launch_conv_elements(L[0].g, tab, L[0].W, Ce, s);
+    launch_block_factor(L[0].g, tab, ph, cbs, Ce, cfactors, WR_FP64, s);
+    linearised = true;
+    if (eig)
+      for (int l = 1; l <= T_; ++l) eigen_estimate(l);
+  }
+
+  // Largest real part of the Ritz values of opt.eig_steps Arnoldi (MGS) steps on M^{-1} J.
+  void eigen_estimate(int l) {
+    Level& lv = L[l];
+    const int64_t n = lv.g.ndofs;
+    const int m = opt.eig_steps;
+    std::vector<double> H((m + 1) * m, 0.0);
+    launch_splitmix_free(lv.g, (uint64_t)l, V[0], s);
+    vec_scale(n, 1.0 / norm(n, V[0]), V[0], s);
+    int mm = m;
+    for (int j = 0; j < m; ++j) {
+      jac(l, V[j], lv.t);
+      patch_apply(l, lv.t, V[j + 1]);
+      for (int i = 0; i <= j; ++i) {
+        const double hij = dot(n, V[j + 1], V[i]);
+        H[i * m + j] = hij;
+        vec_axpby(n, -hij, V[i], 1.0, V[j + 1], s);
+      }
+      const double hn = norm(n, V[j + 1]);
+      H[(j + 1) * m + j] = hn;
+      if (hn <= 1e-14 * std::fabs(H[j * m + j]) + 1e-300) {
+        mm = j + 1;
+        break;
+      }
+      vec_scale(n, 1.0 / hn, V[j + 1], s);
+    }
+    lv.lam = max_real_eigenvalue(H, mm, m);
+    lv.lam_set = true;
+  }
+
+  // Eigenvalues of the leading mm x mm block of the upper Hessenberg H (row
+  // stride ld) by the complex shifted QR algorithm with Wilkinson shifts and
+  // deflation (Golub & Van Loan, Sec. 7.5); returns the largest real part.
+  static double max_real_eigenvalue(const std::vector<double>& H, int mm, int ld) {
+    using cd = std::complex<double>;
+    std::vector<cd> A(mm * mm);
+    for (int i = 0; i < mm; ++i)
+      for (int j = 0; j < mm; ++j) A[i * mm + j] = H[i * ld + j];
+    auto at = [&](int i, int j) -> cd& { return A[i * mm + j]; };
+    int hi = mm - 1, its = 0;
+    std::vector<double> cs(mm);
+    std::vector<cd> sn(mm);
+    while (hi > 0 && its < 200 * mm) {
+      int lo = hi;
+      while (lo > 0 && std::abs(at(lo, lo - 1)) > 1e-15 * (std::abs(at(lo, lo)) + std::abs(at(lo - 1, lo - 1)))) --lo;
+      if (lo == hi) {
+        --hi;
+        its = 0;
+        continue;
+      }
+      const cd a = at(hi - 1, hi - 1), b = at(hi - 1, hi), c = at(hi, hi - 1), d = at(hi, hi);
+      const cd tr = a + d, det = a * d - b * c;
+      const cd disc = std::sqrt(tr * tr / 4.0 - det);
+      cd mu = (std::abs(tr / 2.0 + disc - d) < std::abs(tr / 2.0 - disc - d)) ? tr / 2.0 + disc : tr / 2.0 - disc;
+      if (its > 0 && its % 11 == 0) mu = d + cd(std::abs(at(hi, hi - 1)), 0.0);  // exceptional shift
+      for (int i = lo; i <= hi; ++i) at(i, i) -= mu;
+      for (int i = lo; i < hi; ++i) {
+        const cd x = at(i, i), y = at(i + 1, i);
+        const double r = std::sqrt(std::norm(x) + std::norm(y));
+        if (r == 0.0) { cs[i] = 1.0; sn[i] = 0.0; continue; }
+        if (std::abs(x) == 0.0) {
+          cs[i] = 0.0;
+          sn[i] = 1.0;
+        } else {
+          cs[i] = std::abs(x) / r;
+          sn[i] = (x / std::abs(x)) * std::conj(y) / r;
+        }
+        for (int j = i; j <= hi; ++j) {
+          const cd u = at(i, j), v = at(i + 1, j);
+          at(i, j) = cs[i] * u + sn[i] * v;
+          at(i + 1, j) = -std::conj(sn[i]) * u + cs[i] * v;
+        }
+      }
+      for (int i = lo; i < hi; ++i)
+        for (int kk = lo; kk <= std::min(i + 1, hi); ++kk) {
+          const cd u = at(kk, i), v = at(kk, i + 1);
+          at(kk, i) = u * cs[i] + v * std::conj(sn[i]);
+          at(kk, i + 1) = -u * sn[i] + v * cs[i];
+        }
+      for (int i = lo; i <= hi; ++i) at(i, i) += mu;
+      ++its;
+    }
+    double best = -1e300;
+    for (int i = 0; i < mm; ++i) best = std::max(best, at(i, i).real());
+    return best;
+  }
+
+  // Right-preconditioned FGMRES with zero initial guess; returns iterations.
+  int fgmres(const double* b, double* x, double tol) {
+    Level& fl = fine();
+    const int64_t n = fl.g.ndofs;
+    const int m = opt.gmres_restart;
+    vec_zero(n, x, s);
+    vec_copy(n, b, w, s);
+    double beta = norm(n, w);
+    int its = 0;
+    std::vector<double> H((m + 1) * m), cs(m), sn(m), gg(m + 1), y(m);
+    while (beta > tol && its < opt.gmres_maxit) {
+      vec_copy(n, w, V[0], s);
+      vec_scale(n, 1.0 / beta, V[0], s);
+      std::fill(H.begin(), H.end(), 0.0);
+      std::fill(gg.begin(), gg.end(), 0.0);
+      gg[0] = beta;
+      int jend = 0;
+      for (int j = 0; j < m; ++j) {
+        vcycle(V[j], Z[j]);
+        launch_project_pressure(fl.g, tab, Z[j], s);
+        jac(top(), Z[j], V[j + 1]);
+        for (int i = 0; i <= j; ++i) {
+          const double hij = dot(n, V[j + 1], V[i]);
+          H[i * m + j] = hij;
+          vec_axpby(n, -hij, V[i], 1.0, V[j + 1], s);
+        }
+        const double hn = norm(n, V[j + 1]);
+        H[(j + 1) * m + j] = hn;
+        if (hn != 0.0) vec_scale(n, 1.0 / hn, V[j + 1], s);
+        for (int i = 0; i < j; ++i) {
+          const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+          H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+          H[i * m + j] = t;
+        }
+        const double den = std::hypot(H[j * m + j], H[(j + 1) * m + j]);
+        cs[j] = H[j * m + j] / den;
+        sn[j] = H[(j + 1) * m + j] / den;
+        H[j * m + j] = den;
+        H[(j + 1) * m + j] = 0.0;
+        gg[j + 1] = -sn[j] * gg[j];
+        gg[j] = cs[j] * gg[j];
+        ++its;
+        jend = j + 1;
+        if (!std::isfinite(gg[j + 1])) throw WrError(WR_ERR_NAN, "FGMRES residual is not finite");
+        if (std::fabs(gg[j + 1]) <= tol || its >= opt.gmres_maxit) break;
+      }
+      for (int i = jend - 1; i >= 0; --i) {
+        double acc = gg[i];
+        for (int l2 = i + 1; l2 < jend; ++l2) acc -= H[i * m + l2] * y[l2];
+        y[i] = acc / H[i * m + i];
+      }
+      for (int i = 0; i < jend; ++i) vec_axpby(n, y[i], Z[i], 1.0, x, s);
+      jac(top(), x, w);
+      vec_axpby(n, 1.0, b, -1.0, w, s);  // w = b - J x
+      beta = norm(n, w);
+    }
+    return its;
+  }
+
+  int solve(double* U, wr_stats* st) {
+    Level& fl = fine();
+    const int64_t n = fl.g.ndofs;
+    wr_stats loc;
+    std::memset(&loc, 0, sizeof(loc));
+    launch_residual(fl.g, tab, ph, U, F, ye, s);
+    double fnorm = norm(n, F);
+    const double f0 = fnorm;
+    double eta = opt.ew ? 0.5 : opt.eta_fixed;
+    loc.residual_norms[0] = fnorm;
+    int status = WR_ERR_NOT_CONVERGED;
+    const int v0 = vcycles;
+    for (int it = 0; it < opt.newton_maxit && it < 64; ++it) {
+      if (!std::isfinite(fnorm)) {
+        status = WR_ERR_NAN;
+        break;
+      }
+      if (fnorm <= opt.newton_rtol * f0) {
+        status = WR_OK;
+        break;
+      }
+      double t0 = now_ms();
+      linearise(U, true);
+      WR_CUDA(cudaStreamSynchronize(s));
+      double t1 = now_ms();
+      loc.setup_ms += t1 - t0;
+      vec_scale(n, -1.0, F, s);
+      // FGMRES writes the Newton step into Z-independent scratch: reuse hx as the step
+      const int its = fgmres(F, hx, eta * fnorm);
+      WR_CUDA(cudaStreamSynchronize(s));
+      loc.krylov_ms += now_ms() - t1;
+      vec_axpby(n, 1.0, hx, 1.0, U, s);
+      launch_residual(fl.g, tab, ph, U, F, ye, s);
+      const double fnew = norm(n, F);
+      loc.gmres_its[loc.newton_its] = its;
+      loc.newton_its++;
+      loc.residual_norms[loc.newton_its] = fnew;
+      if (opt.ew) {
+        const double gamma = 0.9, alpha = 2.0;
+        double en = gamma * std::pow(fnew / fnorm, alpha);
+        const double safe = gamma * std::pow(eta, alpha);
+        if (safe > 0.1) en = std::max(en, safe);
+        eta = std::min(0.9, std::max(en, 0.5 * opt.newton_rtol * f0 / fnew));
+      }
+      fnorm = fnew;
+    }
+    if (status == WR_ERR_NOT_CONVERGED && std::isfinite(fnorm) && fnorm <= opt.newton_rtol * f0) status = WR_OK;
+    loc.vcycles = vcycles - v0;
+    if (st) *st = loc;
+    return status;
+  }
+};
+
+namespace {
+
+int fail(wr_ctx* c, const WrError& e) {
+  if (c) c->err = e.what();
+  return e.code;
+}
+
+template <typename Fn>
+int guarded(wr_ctx* c, Fn&& fn) {
+  try {
+    return fn();
+  } catch (const WrError& e) {
+    return fail(c, e);
+  } catch (const std::exception& e) {
+    if (c) c->err = e.what();
+    return WR_ERR_CUDA;
+  }
+}
+
+void need(bool cond, const char* msg) {
+  if (!cond) throw WrError(WR_ERR_ARG, msg);
+}
+
+void check_level(const wr_ctx* c, int level, int lo) {
+  need(level >= lo && level < (int)c->L.size(), "level out of range");
+}
+
+}  // namespace
+
+extern "C" {
+
+void wr_default_options(wr_options* o) {
+  if (!o) return;
+  o->precision = WR_FP64;
+  o->cheb_steps = 2;
+  o->cheb_lo = 0.25;
+  o->cheb_hi = 1.05;
+  o->eig_steps = 10;
+  o->newton_rtol = 1e-8;
+  o->newton_maxit = 20;
+  o->ew = 1;
+  o->eta_fixed = 1e-4;
+  o->gmres_restart = 30;
+  o->gmres_maxit = 200;
+}
+
+int wr_create(wr_ctx** out, const wr_problem* p, const wr_options* o, void* stream) {
+  if (!out || !p) return WR_ERR_ARG;
+  *out = nullptr;
+  auto c = std::make_unique<wr_ctx>();
+  int rc = guarded(c.get(), [&]() -> int {
+    need(p->k == 1 || p->k == 2, "k must be 1 or 2");
+    need(p->q == 0 || p->q == 1, "q must be 0 or 1");
+    need(p->n_coarse == 2, "n_coarse must be 2");
+    need(p->n_fine >= 4 && p->n_fine <= 4096, "n_fine out of range");
+    need(p->n_slabs >= 1 && p->T > 0.0, "need n_slabs >= 1 and T > 0");
+    int nf = p->n_fine;
+    while (nf > p->n_coarse && nf % 2 == 0) nf /= 2;
+    need(nf == p->n_coarse, "n_fine must be n_coarse times a power of two");
+    need(p->kind >= WR_TAYLOR_GREEN && p->kind <= WR_FOURIER, "unknown problem kind");
+    need(p->n_modes >= 0 && p->n_modes <= 8, "at most 8 Fourier modes");
+    need(p->n_modes == 0 || (p->mx && p->my && p->amp), "Fourier mode arrays missing");
+    if (o) c->opt = *o;
+    else wr_default_options(&c->opt);
+    need(c->opt.precision == WR_FP64 || c->opt.precision == WR_FP32, "precision must be WR_FP64 or WR_FP32");
+    need(c->opt.cheb_steps >= 1 && c->opt.eig_steps >= 1 && c->opt.eig_steps <= c->opt.gmres_restart,
+         "bad Chebyshev / eigen-estimate steps");
+    need(c->opt.gmres_restart >= 1 && c->opt.gmres_restart <= 200, "bad restart");
+    c->s = static_cast<cudaStream_t>(stream);
+    c->k = p->k; c->q = p->q; c->N = p->n_slabs; c->T = p->T;
+    c->ph.kind = p->kind; c->ph.steady = p->steady; c->ph.nu = p->nu; c->ph.conv = p->conv; c->ph.T = p->T;
+    c->ph.n_modes = p->n_modes;
+    for (int m = 0; m < p->n_modes; ++m) { c->ph.mx[m] = p->mx[m]; c->ph.my[m] = p->my[m]; c->ph.amp[m] = p->amp[m]; }
+    c->tab = build_tables(p->k, p->q);
+    std::vector<int> ns;
+    for (int n = p->n_coarse; n <= p->n_fine; n *= 2) ns.push_back(n);
+    const int ms = patch_ms(p->k), nt = p->q + 1;
+    const size_t fsz = c->opt.precision == WR_FP32 ? sizeof(float) : sizeof(double);
+    size_t max_ce = 0, max_ye = 0, max_yp = 0;
+    for (size_t l = 0; l < ns.size(); ++l) {
+      Level lv;
+      lv.g = make_geom(ns[l], p->k, p->q, p->n_slabs, p->T);
+      lv.bs.kind = 0;
+      lv.bs.nvg = patch_nvg(p->k);
+      lv.bs.npg = patch_npg(p->k);
+      lv.bs.ms = ms;
+      const int64_t nd = lv.g.ndofs;
+      lv.W = c->alloc<double>(nd);
+      lv.b = c->alloc<double>(nd);
+      lv.x = c->alloc<double>(nd);
+      lv.r = c->alloc<double>(nd);
+      lv.d = c->alloc<double>(nd);
+      lv.z = c->alloc<double>(nd);
+      lv.t = c->alloc<double>(nd);
+      const size_t nvl = p->k + 2, nvle = nvl * nvl, elem = nt * (2 * nvle + (p->k + 1) * (p->k + 1));
+      max_ce = std::max(max_ce, (size_t)p->n_slabs * lv.g.ncells() * nt * 4 * nvle * nvle);
+      max_ye = std::max(max_ye, (size_t)p->n_slabs * lv.g.ncells() * elem);
+      if (l >= 1) {
+        const size_t nf = (size_t)lv.g.npatch() * p->n_slabs * nt * nt * ms * ms;
+        void* f = nullptr;
+        if (fsz == sizeof(float)) f = c->alloc<float>(nf);
+        else f = c->alloc<double>(nf);
+        lv.factors = f;
+        max_yp = std::max(max_yp, (size_t)lv.g.npatch() * p->n_slabs * nt * ms);
+      }
+      c->L.push_back(lv);
+    }
+    c->cbs.kind = 1;
+    c->cbs.nvg = c->L[0].g.nv - 2;
+    c->cbs.npg = c->L[0].g.np;
+    c->cbs.ms = ms;
+    need(2 * c->cbs.nvg * c->cbs.nvg + c->cbs.npg * c->cbs.npg <= ms, "coarse block exceeds the slot layout");
+    c->cfactors = c->alloc<double>((size_t)p->n_slabs * nt * nt * ms * ms);
+    c->Ce = c->alloc<double>(p->conv != 0.0 ? max_ce : 1);
+    c->ye = c->alloc<double>(max_ye);
+    c->Yp = c->alloc<double>(max_yp);
+    const int64_t nfine = c->fine().g.ndofs;
+    const int nvec = std::max(c->opt.gmres_restart, c->opt.eig_steps) + 1;
+    for (int i = 0; i < nvec; ++i) c->V.push_back(c->alloc<double>(nfine));
+    for (int i = 0; i < c->opt.gmres_restart; ++i) c->Z.push_back(c->alloc<double>(nfine));
+    c->F = c->alloc<double>(nfine);
+    c->w = c->alloc<double>(nfine);
+    c->hb = c->alloc<double>(nfine);
+    c->hx = c->alloc<double>(nfine);
+    c->partials = c->alloc<double>(dot_partials_size());
+    c->dres = c->alloc<double>(1);
+    c->slots = c->alloc<int>(2 * ms);
+    WR_CUDA(cudaMallocHost(&c->hres, sizeof(double)));
+    return WR_OK;
+  });
+  if (rc != WR_OK) {
+    // keep the message reachable: the context is returned so wr_last_error works
+    *out = c.release();
+    return rc;
+  }
+  *out = c.release();
+  return WR_OK;
+}
+
+int wr_destroy(wr_ctx* c) {
+  delete c;
+  return WR_OK;
+}
+
+const char* wr_last_error(const wr_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int wr_num_levels(const wr_ctx* c, int* out) {
+  if (!c || !out) return WR_ERR_ARG;
+  *out = (int)c->L.size();
+  return WR_OK;
+}
+
+int wr_ndofs(const wr_ctx* c, int level, int64_t* out) {
+  if (!c || !out || level < 0 || level >= (int)c->L.size()) return WR_ERR_ARG;
+  *out = c->L[level].g.ndofs;
+  return WR_OK;
+}
+
+int wr_device_bytes(const wr_ctx* c, int64_t* out) {
+  if (!c || !out) return WR_ERR_ARG;
+  *out = c->bytes;
+  return WR_OK;
+}
+
+int wr_patch_dofs(const wr_ctx* cc, int level, int64_t patch, int slab, int64_t* idx, int* len) {
+  wr_ctx* c = const_cast<wr_ctx*>(cc);
+  return guarded(c, [&]() -> int {
+    need(c != nullptr && idx != nullptr && len != nullptr, "null argument");
+    check_level(c, level, 0);
+    const Level& lv = c->L[level];
+    need(patch >= 0 && patch < lv.g.npatch() && slab >= 0 && slab < lv.g.N, "patch or slab out of range");
+    const int ms = lv.bs.ms;
+    launch_patch_slots(lv.g, lv.bs, (int)patch, c->slots, c->s);
+    std::vector<int> sp(ms);
+    WR_CUDA(cudaMemcpyAsync(sp.data(), c->slots, sizeof(int) * ms, cudaMemcpyDeviceToHost, c->s));
+    WR_CUDA(cudaStreamSynchronize(c->s));
+    int cnt = 0;
+    for (int a = 0; a < lv.g.nt; ++a)
+      for (int s = 0; s < ms; ++s)
+        if (sp[s] >= 0) idx[cnt++] = ((int64_t)slab * lv.g.nt + a) * lv.g.S + sp[s];
+    *len = cnt;
+    return WR_OK;
+  });
+}
+
+int wr_initial_guess(wr_ctx* c, double* U) {
+  return guarded(c, [&]() -> int {
+    need(c && U, "null argument");
+    launch_boundary_values(c->fine().g, c->tab, c->ph, U, c->s);
+    return WR_OK;
+  });
+}
+
+int wr_residual(wr_ctx* c, const double* U, double* F) {
+  return guarded(c, [&]() -> int {
+    need(c && U && F && U != F, "null or aliased argument");
+    launch_residual(c->fine().g, c->tab, c->ph, U, F, c->ye, c->s);
+    return WR_OK;
+  });
+}
+
+int wr_linearise(wr_ctx* c, const double* W) {
+  return guarded(c, [&]() -> int {
+    need(c && W, "null argument");
+    c->linearise(W, true);
+    return WR_OK;
+  });
+}
+
+int wr_linearise_no_eig(wr_ctx* c, const double* W) {
+  return guarded(c, [&]() -> int {
+    need(c && W, "null argument");
+    c->linearise(W, false);
+    return WR_OK;
+  });
+}
+
+int wr_get_lambda(const wr_ctx* c, int level, double* lam) {
+  if (!c || !lam || level < 1 || level >= (int)c->L.size()) return WR_ERR_ARG;
+  if (!c->L[level].lam_set) return WR_ERR_STATE;
+  *lam = c->L[level].lam;
+  return WR_OK;
+}
+
+int wr_set_lambda(wr_ctx* c, int level, double lam) {
+  if (!c || level < 1 || level >= (int)c->L.size() || !(lam > 0.0)) return WR_ERR_ARG;
+  c->L[level].lam = lam;
+  c->L[level].lam_set = true;
+  return WR_OK;
+}
+
+int wr_apply_jacobian(wr_ctx* c, int level, const double* x, double* y) {
+  return guarded(c, [&]() -> int {
+    need(c && x && y && x != y, "null or aliased argument");
+    check_level(c, level, 0);
+    c->jac(level, x, y);
+    return WR_OK;
+  });
+}
+
+int wr_patch_apply(wr_ctx* c, int level, const double* r, double* y) {
+  return guarded(c, [&]() -> int {
+    need(c && r && y && r != y, "null or aliased argument");
+    check_level(c, level, 1);
+    c->patch_apply(level, r, y);
+    return WR_OK;
+  });
+}
+
+int wr_smooth(wr_ctx* c, int level, const double* b, double* x, int zero_guess) {
+  return guarded(c, [&]() -> int {
+    need(c && b && x && b != x, "null or aliased argument");
+    check_level(c, level, 1);
+    c->smooth(level, b, x, zero_guess != 0);
+    return WR_OK;
+  });
+}
+
+int wr_restrict(wr_ctx* c, int fine_level, const double* xf, double* xc) {
+  return guarded(c, [&]() -> int {
+    need(c && xf && xc, "null argument");
+    check_level(c, fine_level, 1);
+    launch_restrict(c->L[fine_level].g, c->L[fine_level - 1].g, c->tab, xf, xc, c->s);
+    return WR_OK;
+  });
+}
+
+int wr_prolong_add(wr_ctx* c, int fine_level, const double* xc, double* xf) {
+  return guarded(c, [&]() -> int {
+    need(c && xf && xc, "null argument");
+    check_level(c, fine_level, 1);
+    launch_prolong_add(c->L[fine_level].g, c->L[fine_level - 1].g, c->tab, xc, xf, c->s);
+    return WR_OK;
+  });
+}
+
+int wr_coarse_solve(wr_ctx* c, const double* b, double* x) {
+  return guarded(c, [&]() -> int {
+    need(c && b && x && b != x, "null or aliased argument");
+    c->coarse_solve(b, x);
+    return WR_OK;
+  });
+}
+
+int wr_vcycle(wr_ctx* c, const double* b, double* x) {
+  return guarded(c, [&]() -> int {
+    need(c && b && x && b != x, "null or aliased argument");
+    c->vcycle(b, x);
+    return WR_OK;
+  });
+}
+
+int wr_vcycle_host(wr_ctx* c, const double* b_host, double* x_host) {
+  return guarded(c, [&]() -> int {
+    need(c && b_host && x_host, "null argument");
+    const int64_t n = c->fine().g.ndofs;
+    WR_CUDA(cudaMemcpyAsync(c->hb, b_host, sizeof(double) * n, cudaMemcpyHostToDevice, c->s));
+    c->vcycle(c->hb, c->hx);
+    WR_CUDA(cudaMemcpyAsync(x_host, c->hx, sizeof(double) * n, cudaMemcpyDeviceToHost, c->s));
+    WR_CUDA(cudaStreamSynchronize(c->s));
+    return WR_OK;
+  });
+}
+
+int wr_project_pressure(wr_ctx* c, double* x) {
+  return guarded(c, [&]() -> int {
+    need(c && x, "null argument");
+    launch_project_pressure(c->fine().g, c->tab, x, c->s);
+    return WR_OK;
+  });
+}
+
+int wr_solve(wr_ctx* c, double* U, wr_stats* st) {
+  return guarded(c, [&]() -> int {
+    need(c && U, "null argument");
+    const int rc = c->solve(U, st);
+    if (rc == WR_ERR_NOT_CONVERGED) c->err = "Newton iteration limit reached";
+    if (rc == WR_ERR_NAN) c->err = "residual norm is not finite";
+    return rc;
+  });
+}
+
+int wr_solve_host(wr_ctx* c, double* U_host, wr_stats* st) {
+  return guarded(c, [&]() -> int {
+    need(c && U_host, "null argument");
+    const int64_t n = c->fine().g.ndofs;
+    WR_CUDA(cudaMemcpyAsync(c->hb, U_host, sizeof(double) * n, cudaMemcpyHostToDevice, c->s));
+    const int rc = c->solve(c->hb, st);
+    WR_CUDA(cudaMemcpyAsync(U_host, c->hb, sizeof(double) * n, cudaMemcpyDeviceToHost, c->s));
+    WR_CUDA(cudaStreamSynchronize(c->s));
+    if (rc == WR_ERR_NOT_CONVERGED) c->err = "Newton iteration limit reached";
+    return rc;
+  });
+}
+
+int wr_launch_count(int64_t* out) {
+  if (!out) return WR_ERR_ARG;
+  *out = g_launches.load();
+  return WR_OK;
+}
+
+int wr_profile(wr_ctx* c, int enable) {
+  return guarded(c, [&]() -> int {
+    need(c != nullptr, "null context");
+    WR_CUDA(cudaStreamSynchronize(c->s));
+    c->prof = enable != 0;
+    c->prof_ev.assign(c->L.size(), {});
+    c->ev_used = 0;
+    return WR_OK;
+  });
+}
+
+int wr_profile_smoother(wr_ctx* c, int level, double* total_ms, int* launches) {
+  return guarded(c, [&]() -> int {
+    need(c && total_ms && launches, "null argument");
+    check_level(c, level, 1);
+    need(level < (int)c->prof_ev.size(), "profiling not enabled");
+    WR_CUDA(cudaStreamSynchronize(c->s));
+    double tot = 0.0;
+    for (auto& pr : c->prof_ev[level]) {
+      float ms = 0.f;
+      WR_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+      tot += ms;
+    }
+    *total_ms = tot;
+    *launches = (int)c->prof_ev[level].size();
+    return WR_OK;
+  });
+}
+
+int wr_measure_fp64_tflops(void* stream, double* out) {
+  if (!out) return WR_ERR_ARG;
+  try {
+    *out = measure_fp64_tflops(static_cast<cudaStream_t>(stream));
+    return WR_OK;
+  } catch (const WrError& e) {
+    return e.code;
+  }
+}
+
+}  // extern "C"

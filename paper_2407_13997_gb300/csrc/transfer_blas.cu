@@ -1,0 +1,306 @@
+// Grid transfers (hot-path step (f)), pressure-mean projection, FP64 vector
+// kernels with deterministic reductions, and the FP64 throughput probe.
+//
+// Transfers (Sec. 3): P = I_t (x) blockdiag(P_u, P_phi), R = P^T, with
+// P_u = P1_v (x) P1_v per velocity component and P_phi = P1_p (x) P1_p, where
+// P1[f, c] is the coarse 1D Lagrange basis function c at fine node f.  Fine node
+// f lies in coarse cell min(f / 2p, nc - 1) at offset r = f - 2p cell, and its
+// weights on the coarse cell's p+1 nodes are the tabulated phi_l(r / 2p).
+// Dirichlet velocity rows and columns are zero (corrections vanish there).
+#include <cmath>
+
+#include "wrmg_internal.h"
+
+namespace {
+
+// weight of coarse node ic at fine node f (1D, degree p, nc coarse cells)
+__device__ __forceinline__ double w1d(const double* tab, int ld, int p, int nc, int f, int ic) {
+  const int c = min(f / (2 * p), nc - 1);
+  const int l = ic - p * c;
+  if (l < 0 || l > p) return 0.0;
+  return tab[(f - 2 * p * c) * ld + l];
+}
+
+__global__ void prolong_add_kernel(LevelGeom gf, LevelGeom gc, FeTables T, const double* __restrict__ xc,
+                                   double* __restrict__ xf) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= gf.ndofs) return;
+  const int64_t blk = idx / gf.S;
+  const int sp = int(idx % gf.S);
+  const int nvf2 = gf.nv * gf.nv, nvc2 = gc.nv * gc.nv;
+  const double* xcb = xc + blk * gc.S;
+  double acc = 0.0;
+  if (sp < 2 * nvf2) {
+    const int c = sp / nvf2, t = sp % nvf2, fx = t % gf.nv, fy = t / gf.nv;
+    if (fx == 0 || fy == 0 || fx == gf.nv - 1 || fy == gf.nv - 1) return;  // Dirichlet: P row is zero
+    const int p = gf.k + 1, nc = gc.n;
+    const int cx = min(fx / (2 * p), nc - 1), cy = min(fy / (2 * p), nc - 1);
+    const double* tx = T.pv[fx - 2 * p * cx];
+    const double* ty = T.pv[fy - 2 * p * cy];
+    for (int ly = 0; ly <= p; ++ly) {
+      const int Y = p * cy + ly;
+      if (ty[ly] == 0.0 || Y == 0 || Y == gc.nv - 1) continue;
+      for (int lx = 0; lx <= p; ++lx) {
+        const int X = p * cx + lx;
+        if (tx[lx] == 0.0 || X == 0 || X == gc.nv - 1) continue;
+        acc = fma(ty[ly] * tx[lx], xcb[c * nvc2 + Y * gc.nv + X], acc);
+      }
+    }
+  } else {
+    const int t = sp - 2 * nvf2, fx = t % gf.np, fy = t / gf.np;
+    const int p = gf.k, nc = gc.n;
+    const int cx = min(fx / (2 * p), nc - 1), cy = min(fy / (2 * p), nc - 1);
+    const double* tx = T.pp[fx - 2 * p * cx];
+    const double* ty = T.pp[fy - 2 * p * cy];
+    for (int ly = 0; ly <= p; ++ly) {
+      if (ty[ly] == 0.0) continue;
+      for (int lx = 0; lx <= p; ++lx) {
+        if (tx[lx] == 0.0) continue;
+        acc = fma(ty[ly] * tx[lx], xcb[2 * nvc2 + (p * cy + ly) * gc.np + p * cx + lx], acc);
+      }
+    }
+  }
+  xf[idx] += acc;
+}
+
+__global__ void restrict_kernel(LevelGeom gf, LevelGeom gc, FeTables T, const double* __restrict__ xf,
+                                double* __restrict__ xc) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= gc.ndofs) return;
+  const int64_t blk = idx / gc.S;
+  const int sp = int(idx % gc.S);
+  const int nvf2 = gf.nv * gf.nv, nvc2 = gc.nv * gc.nv;
+  const double* xfb = xf + blk * gf.S;
+  double acc = 0.0;
+  if (sp < 2 * nvc2) {
+    const int c = sp / nvc2, t = sp % nvc2, X = t % gc.nv, Y = t / gc.nv;
+    if (X == 0 || Y == 0 || X == gc.nv - 1 || Y == gc.nv - 1) { xc[idx] = 0.0; return; }
+    const int p = gf.k + 1, nc = gc.n;
+    // fine nodes in the coarse cells around X (support of the coarse basis function)
+    const int fx0 = 2 * p * max(0, (X - 1) / p), fx1 = min(2 * p * (min(X / p, nc - 1) + 1), gf.nv - 1);
+    const int fy0 = 2 * p * max(0, (Y - 1) / p), fy1 = min(2 * p * (min(Y / p, nc - 1) + 1), gf.nv - 1);
+    for (int fy = max(fy0, 1); fy <= min(fy1, gf.nv - 2); ++fy) {
+      const double wy = w1d(&T.pv[0][0], WR_MAX_NVL, p, nc, fy, Y);
+      if (wy == 0.0) continue;
+      for (int fx = max(fx0, 1); fx <= min(fx1, gf.nv - 2); ++fx) {
+        const double wx = w1d(&T.pv[0][0], WR_MAX_NVL, p, nc, fx, X);
+        if (wx == 0.0) continue;
+        acc = fma(wy * wx, xfb[c * nvf2 + fy * gf.nv + fx], acc);
+      }
+    }
+  } else {
+    const int t = sp - 2 * nvc2, X = t % gc.np, Y = t / gc.np;
+    const int p = gf.k, nc = gc.n;
+    const int fx0 = 2 * p * max(0, (X - 1) / p), fx1 = min(2 * p * (min(X / p, nc - 1) + 1), gf.np - 1);
+    const int fy0 = 2 * p * max(0, (Y - 1) / p), fy1 = min(2 * p * (min(Y / p, nc - 1) + 1), gf.np - 1);
+    for (int fy = fy0; fy <= fy1; ++fy) {
+      const double wy = w1d(&T.pp[0][0], WR_MAX_NPL, p, nc, fy, Y);
+      if (wy == 0.0) continue;
+      for (int fx = fx0; fx <= fx1; ++fx) {
+        const double wx = w1d(&T.pp[0][0], WR_MAX_NPL, p, nc, fx, X);
+        if (wx == 0.0) continue;
+        acc = fma(wy * wx, xfb[2 * nvf2 + fy * gf.np + fx], acc);
+      }
+    }
+  }
+  xc[idx] = acc;
+}
+
+// Pressure weight int chi_j of node g in 1D: h sum over cells containing g of mp1.
+__device__ __forceinline__ double pw1(const FeTables& T, int k, int n, double h, int g) {
+  const int lo = g == 0 ? 0 : (g - 1) / k, hi = min(g / k, n - 1);
+  double v = 0.0;
+  for (int c = lo; c <= hi; ++c) v += T.mp1[g - k * c];
+  return h * v;
+}
+
+// One CTA per temporal block: Phi -= (sum_j w_j Phi_j) / (sum_j w_j), fixed-order reduction.
+__global__ void project_pressure_kernel(LevelGeom g, FeTables T, double* __restrict__ x) {
+  __shared__ double sa[256], sb[256];
+  double* p = x + (int64_t)blockIdx.x * g.S + 2 * g.nv * g.nv;
+  const int np2 = g.np * g.np;
+  double a = 0.0, b = 0.0;
+  for (int j = threadIdx.x; j < np2; j += blockDim.x) {
+    const double w = pw1(T, g.k, g.n, g.h, j % g.np) * pw1(T, g.k, g.n, g.h, j / g.np);
+    a = fma(w, p[j], a);
+    b += w;
+  }
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sa[threadIdx.x] += sa[threadIdx.x + s];
+      sb[threadIdx.x] += sb[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  const double mean = sa[0] / sb[0];
+  for (int j = threadIdx.x; j < np2; j += blockDim.x) p[j] -= mean;
+}
+
+__global__ void zero_dirichlet_kernel(LevelGeom g, double* __restrict__ x) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= g.ndofs) return;
+  const int sp = int(idx % g.S), nv = g.nv, nv2 = nv * nv;
+  if (sp < 2 * nv2) {
+    const int t = sp % nv2, gx = t % nv, gy = t / nv;
+    if (gx == 0 || gy == 0 || gx == nv - 1 || gy == nv - 1) x[idx] = 0.0;
+  }
+}
+
+// uniform(-1, 1) from splitmix64 (Steele, Lea & Flood 2014), counter-based:
+// value i = mix(seed + (i+1) * 0x9E3779B97F4A7C15), top 53 bits; zero on Dirichlet DoFs.
+__global__ void splitmix_kernel(LevelGeom g, uint64_t seed, double* __restrict__ x) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= g.ndofs) return;
+  uint64_t z = seed + (uint64_t)(idx + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  u = 2.0 * u - 1.0;
+  const int sp = int(idx % g.S), nv = g.nv, nv2 = nv * nv;
+  if (sp < 2 * nv2) {
+    const int t = sp % nv2, gx = t % nv, gy = t / nv;
+    if (gx == 0 || gy == 0 || gx == nv - 1 || gy == nv - 1) u = 0.0;
+  }
+  x[idx] = u;
+}
+
+__global__ void axpby_kernel(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], b * y[i]);
+}
+__global__ void axpbypz_kernel(int64_t n, double a, const double* __restrict__ x, double b,
+                               const double* __restrict__ y, double c, double* __restrict__ z) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    z[i] = fma(a, x[i], fma(b, y[i], c * z[i]));
+}
+__global__ void copy_kernel(int64_t n, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[i];
+}
+__global__ void scale_kernel(int64_t n, double a, double* __restrict__ x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= a;
+}
+
+constexpr int kDotBlocks = 1024, kDotThreads = 256;
+
+// Deterministic dot: each block sums a fixed strided set in a fixed tree, then one block sums the partials.
+__global__ void dot_stage1(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
+                           double* __restrict__ partials) {
+  __shared__ double s[kDotThreads];
+  double a = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kDotThreads)
+    a = fma(x[i], y[i], a);
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int st = kDotThreads / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = s[0];
+}
+__global__ void dot_stage2(const double* __restrict__ partials, double* __restrict__ out) {
+  __shared__ double s[kDotThreads];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += kDotThreads) a += partials[i];
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int st = kDotThreads / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+// 8 independent FMA chains per thread, register only.
+__global__ void fp64_probe_kernel(double* out, int iters, double a, double b) {
+  double x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  out[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+inline unsigned grid_for(int64_t n, int threads) {
+  const int64_t b = (n + threads - 1) / threads;
+  return (unsigned)(b < 4 * 152 * 8 ? (b > 0 ? b : 1) : 4 * 152 * 8);
+}
+
+}  // namespace
+
+void launch_restrict(const LevelGeom& gf, const LevelGeom& gc, const FeTables& T, const double* xf, double* xc,
+                     cudaStream_t s) {
+  restrict_kernel<<<(unsigned)((gc.ndofs + 255) / 256), 256, 0, s>>>(gf, gc, T, xf, xc);
+  WR_LAUNCH_CHECK();
+}
+void launch_prolong_add(const LevelGeom& gf, const LevelGeom& gc, const FeTables& T, const double* xc, double* xf,
+                        cudaStream_t s) {
+  prolong_add_kernel<<<(unsigned)((gf.ndofs + 255) / 256), 256, 0, s>>>(gf, gc, T, xc, xf);
+  WR_LAUNCH_CHECK();
+}
+void launch_project_pressure(const LevelGeom& g, const FeTables& T, double* x, cudaStream_t s) {
+  project_pressure_kernel<<<g.N * g.nt, 256, 0, s>>>(g, T, x);
+  WR_LAUNCH_CHECK();
+}
+void launch_zero_dirichlet(const LevelGeom& g, double* x, cudaStream_t s) {
+  zero_dirichlet_kernel<<<(unsigned)((g.ndofs + 255) / 256), 256, 0, s>>>(g, x);
+  WR_LAUNCH_CHECK();
+}
+void launch_splitmix_free(const LevelGeom& g, uint64_t seed, double* x, cudaStream_t s) {
+  splitmix_kernel<<<(unsigned)((g.ndofs + 255) / 256), 256, 0, s>>>(g, seed, x);
+  WR_LAUNCH_CHECK();
+}
+void vec_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t s) {
+  axpby_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, a, x, b, y);
+  WR_LAUNCH_CHECK();
+}
+void vec_axpbypz(int64_t n, double a, const double* x, double b, const double* y, double c, double* z,
+                 cudaStream_t s) {
+  axpbypz_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, a, x, b, y, c, z);
+  WR_LAUNCH_CHECK();
+}
+void vec_copy(int64_t n, const double* x, double* y, cudaStream_t s) {
+  copy_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, x, y);
+  WR_LAUNCH_CHECK();
+}
+void vec_scale(int64_t n, double a, double* x, cudaStream_t s) {
+  scale_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, a, x);
+  WR_LAUNCH_CHECK();
+}
+void vec_zero(int64_t n, double* x, cudaStream_t s) { WR_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s)); }
+int dot_partials_size() { return kDotBlocks; }
+void vec_dot_dev(int64_t n, const double* x, const double* y, double* partials, double* out, cudaStream_t s) {
+  dot_stage1<<<kDotBlocks, kDotThreads, 0, s>>>(n, x, y, partials);
+  WR_LAUNCH_CHECK();
+  dot_stage2<<<1, kDotThreads, 0, s>>>(partials, out);
+  WR_LAUNCH_CHECK();
+}
+
+double measure_fp64_tflops(cudaStream_t s) {
+  int dev = 0, sms = 0;
+  WR_CUDA(cudaGetDevice(&dev));
+  WR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * 8, threads = 256, iters = 1 << 13;
+  double* out = nullptr;
+  WR_CUDA(cudaMalloc(&out, sizeof(double) * blocks * threads));
+  cudaEvent_t e0, e1;
+  WR_CUDA(cudaEventCreate(&e0));
+  WR_CUDA(cudaEventCreate(&e1));
+  fp64_probe_kernel<<<blocks, threads, 0, s>>>(out, iters, 0.999999, 1e-7);
+  WR_CUDA(cudaEventRecord(e0, s));
+  for (int r = 0; r < 5; ++r) fp64_probe_kernel<<<blocks, threads, 0, s>>>(out, iters, 0.999999, 1e-7);
+  WR_CUDA(cudaEventRecord(e1, s));
+  WR_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  WR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  const double flops = 5.0 * blocks * threads * (double)iters * 8 * 2;
+  return flops / (ms * 1e-3) / 1e12;
+}
