@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""Throughput of the waveform-relaxation multigrid cycle on one GB300 (or N replicas).
+
+A step is one V(2,2) waveform-Vanka cycle (Algorithm Vcycle) on the 64x64
+Taylor-Hood Q3/Q2, DG(1), 64-slab, nu = 1e-3 Fourier-forced workload
+(11,665,792 space-time DoFs, 6 levels), with the slab factors stored (step (b)
+is timed once, separately, as ``factor_ms``).  Every step runs the whole hot
+path: per-patch gathers and forward substitutions over slabs with the stored
+factors (a, c), additive scatters (d), matrix-free residuals (e) and grid
+transfers (f) on every level, plus the coarse direct solve.
+
+value = space-time DoFs per second per cycle, summed over ranks (each rank runs
+an independent replica; the method has no exchange step across GPUs on this
+path).  The working set (~134 GB of stored factors streamed every cycle) is far
+larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import resource
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "space-time DoF/s per waveform-Vanka V(2,2) cycle"
+UNIT = "DoF/s"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--n", type=int, default=64, help="mesh (smaller only for quick local checks)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload(args, seed=0):
+    from paper_2407_13997_gb300 import inputs
+    w = inputs.fourier_64x64_q3q2_dg1(seed)
+    if args.n != 64:
+        w.n_fine = args.n
+        w.name = w.name.replace("n64", f"n{args.n}")
+    return w
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", HBM_FALLBACK_GBS)), "measured"
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def smoother_algorithmic(ctx, w):
+    """Algorithmic bytes and FP64 flops of one finest-level smoother-apply launch:
+    every (patch, slab) streams its (q+1)^2 m^2 factor entries once (m = the
+    patch's true size, padding excluded), reads its m (q+1) right-hand side
+    values and writes as many outputs; 2 flops per factor entry."""
+    L = ctx.fine
+    n1 = w.n_fine + 1
+    sizes = [len(ctx.patch_dofs(L, p, 0)) for p in range(n1 * n1)]  # (q+1) * m per slab
+    ent = sum(s * s for s in sizes) * w.N
+    vec = sum(sizes) * w.N
+    return 8.0 * (ent + 2 * vec), 2.0 * ent
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch from a committed ncu summary, valid only while the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2407_13997_gb300", "csrc", "patch_kernels.cu")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    rec = d.get(kernel)
+    if not rec:
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return rec.get("dram_bytes_per_launch") if rec.get("source_sha256") == sha else None
+
+
+def cpu_baseline(w, steps=3):
+    """The oracle (FP64 CPU, test infrastructure) timed on this host: V(2,2) cycles
+    on the 16x16, 8-slab instance of the same Q3/Q2 DG(1) Fourier problem.  The
+    oracle's cost per DoF per cycle does not depend on the mesh (fixed patch size,
+    fixed stencils), so DoF/s per cycle carries over to the 64x64 workload."""
+    import numpy as np
+    from oracle.fem import Problem
+    from oracle.solver import Hierarchy, Options
+    from paper_2407_13997_gb300 import inputs
+    pb = Problem(kind="fourier", nu=w.nu, conv=w.conv, T=w.T, mx=w.mx, my=w.my, amp=w.amp)
+    ws = inputs.fourier_64x64_q3q2_dg1(0)
+    ws.n_fine, ws.N = 16, 8
+    h = Hierarchy(ws.n_fine, ws.n_coarse, ws.k, ws.q, ws.N, pb, Options())
+    W = inputs.forcing_shaped_iterate(ws)
+    h.linearise(W)
+    b = -h.fine.residual(W)
+    h.vcycle(b)
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        h.vcycle(b)
+    dt = time.perf_counter() - t0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    nd = h.fine.ndofs
+    return {"value": nd * steps / dt, "unit": UNIT, "cores": max(1, round(cpu / dt)), "kind": "oracle",
+            "sample": f"{steps} oracle V(2,2) cycles on the 16x16, 8-slab instance ({nd} DoFs) of the same "
+                      f"Q3/Q2 DG(1) Fourier problem, {dt / steps:.2f} s per cycle"}, nd, dt / steps
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    w = workload(args)
+    base, nd, sec = cpu_baseline(w, steps=max(1, args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "ndofs": w.ndofs(), "sample_ndofs": nd, "parallelism": "replicas"},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2407_13997_gb300 import inputs, wrmg
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = workload(args, seed=rank)
+    prec = wrmg.WR_FP32 if args.precision == "fp32" else wrmg.WR_FP64
+    ctx = wrmg.Context(w, wrmg.default_options(precision=prec))
+    stream = torch.cuda.current_stream()
+    D = ctx.ndofs()
+    W = torch.from_numpy(inputs.forcing_shaped_iterate(w)).cuda()
+    F = ctx.vector()
+    ctx.residual(W, F)
+    b = -F
+    x = ctx.vector()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.linearise(W, eig=False)
+    torch.cuda.synchronize()
+    factor_ms = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    ctx.linearise(W, eig=True)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    fp64_tflops = wrmg.measure_fp64_tflops(stream.cuda_stream)
+    for _ in range(args.warmup):
+        ctx.vcycle(b, x)
+    torch.cuda.synchronize()
+
+    ctx.profile(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = wrmg.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.vcycle(b, x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = wrmg.launch_count() - launches0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    sm_ms, sm_n = ctx.profile_smoother(ctx.fine)
+    ctx.profile(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = D * world * args.steps / (ms * 1e-3)
+
+    # end to end through the host-buffer ABI call: H2D of b, cycle, D2H of x every step
+    hb = torch.empty(D, dtype=torch.float64).pin_memory()
+    hx = torch.empty(D, dtype=torch.float64).pin_memory()
+    hb.copy_(b.cpu())
+    bn, xn = hb.numpy(), hx.numpy()
+    ctx.vcycle_host(bn, xn)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.vcycle_host(bn, xn)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    assert np.isfinite(xn).all()
+
+    alg_bytes, alg_flops = smoother_algorithmic(ctx, w)
+    avg_s = sm_ms / max(sm_n, 1) * 1e-3
+    hbm_peak, hbm_src = measured_peaks()
+    achieved_tf = alg_flops / avg_s / 1e12
+    achieved_gbs = alg_bytes / avg_s / 1e9
+    if prec == wrmg.WR_FP64:
+        roof = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_tflops, "unit": "TFLOP/s",
+                "frac": achieved_tf / fp64_tflops, "traffic": traffic_record("block_apply_kernel"),
+                "kernel": "block_apply_kernel (finest level)", "launches": sm_n, "avg_ms": avg_s * 1e3,
+                "peak_source": "FP64 FMA rate measured live by wr_measure_fp64_tflops",
+                "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src}}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_peak, "traffic": traffic_record("block_apply_kernel_fp32"),
+                "kernel": "block_apply_kernel (finest level, FP32 factors)", "launches": sm_n,
+                "avg_ms": avg_s * 1e3, "peak_source": hbm_src}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == wrmg.WR_FP64 else "f32 factors / f64 Krylov",
+            "data": "synthetic",
+            "config": {"workload": w.name, "ndofs": D, "n": w.n_fine, "k": w.k, "q": w.q, "N": w.N,
+                       "levels": ctx.num_levels, "factor_storage": args.precision,
+                       "device_bytes": ctx.device_bytes(),
+                       "l2": "no flush: ~134 GB of stored factors streamed per cycle >> 129 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "factor_ms": factor_ms, "setup_ms": setup_ms, "roofline": roof,
+            "e2e": {"value": D * world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * D,
+                    "d2h_bytes_per_step": 8 * D},
+            "gpu_launches": launches, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)[0]
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -92,3 +92,26 @@ def poly_small(n=4, k=1, q=1, N=3, nu=0.1, steady=False, n_coarse=2):
 def seeded_vector(seed, size, scale=1.0):
     """A reproducible N(0, scale^2) test vector."""
     return scale * np.random.default_rng(seed).standard_normal(size)
+
+
+def forcing_shaped_iterate(w, scale=1.0):
+    """A synthetic linearisation point with the structure of a forced flow: the
+    divergence-free field sum_j amp_j curl(psi_j) of the workload's Fourier modes
+    at the velocity nodes, normalised to max |u| = scale, zero on the walls and at
+    every temporal DoF, zero pressure (canonical layout)."""
+    nv = w.n_fine * (w.k + 1) + 1
+    np_ = w.n_fine * w.k + 1
+    x = np.linspace(0.0, 1.0, nv)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    ux = np.zeros_like(X)
+    uy = np.zeros_like(X)
+    for m, n, a in zip(w.mx, w.my, w.amp):
+        ux += a * n * np.pi * np.sin(m * np.pi * X) * np.cos(n * np.pi * Y)
+        uy -= a * m * np.pi * np.cos(m * np.pi * X) * np.sin(n * np.pi * Y)
+    wall = np.zeros_like(X, dtype=bool)
+    wall[0, :] = wall[-1, :] = wall[:, 0] = wall[:, -1] = True
+    ux[wall] = 0.0
+    uy[wall] = 0.0
+    mag = max(np.abs(ux).max(), np.abs(uy).max(), 1e-300)
+    blk = np.concatenate([ux.ravel(), uy.ravel(), np.zeros(np_ * np_)]) * (scale / mag)
+    return np.tile(blk, w.N * (w.q + 1))
