@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    ap.add_argument("--n", type=int, default=64, help="mesh (smaller only for quick local checks)")
+    ap.add_argument("--n", type=int, default=64, help="mesh (smaller only for profiling captures)")
+    ap.add_argument("--slabs", type=int, default=64, help="time slabs (fewer only for profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -54,9 +55,9 @@ def dist_info():
 def workload(args, seed=0):
     from paper_2407_13997_gb300 import inputs
     w = inputs.fourier_64x64_q3q2_dg1(seed)
-    if args.n != 64:
-        w.n_fine = args.n
-        w.name = w.name.replace("n64", f"n{args.n}")
+    if args.n != 64 or args.slabs != 64:
+        w.n_fine, w.N = args.n, args.slabs
+        w.name = f"fourier_q3q2_dg1_n{args.n}_N{args.slabs}"
     return w
 
 
@@ -81,7 +82,7 @@ class ClockSampler:
         self.proc = None
         self.lines = []
 
-    def start(self):
+    def start(self, wait_first=True):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -90,6 +91,11 @@ class ClockSampler:
             self.thread.start()
         except OSError:
             self.proc = None
+            return
+        t0 = time.time()
+        while wait_first and not self.lines and time.time() - t0 < 20:
+            time.sleep(0.05)
+        self.lines.clear()
 
     def _read(self):
         for line in self.proc.stdout:
@@ -226,14 +232,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
     fp64_tflops = wrmg.measure_fp64_tflops(stream.cuda_stream)
+    clocks = ClockSampler(local)
+    clocks.start()  # returns after the first sample, before the warm-up
+    ctx.profile(True)  # pre-creates the CUDA events
     for _ in range(args.warmup):
         ctx.vcycle(b, x)
     torch.cuda.synchronize()
-
-    ctx.profile(True)
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
+    ctx.profile(True)  # drop the warm-up records
+    clocks.lines.clear()
     launches0 = wrmg.launch_count()
     if dist:
         dist.barrier()

@@ -17,10 +17,11 @@
 //         A00^{-1},  X = A00^{-1} A01,  S = A11 - A10 X,  S^{-1}
 //     (block LU over the temporal DoFs, Gauss-Jordan with partial pivoting inside
 //     each block), which keeps every working matrix inside shared memory.
-// (a)+(c) block_apply_kernel, one CTA per patch, sequential over slabs:
-//     gathers r on the patch, adds the jump coupling tau_a(0) M_u y_{n-1}
-//     (Eq. waveform_patch_solve: A_{n,n-1} = -tau_a(0) M_u on the last temporal
-//     DoF's velocity), applies the stored factors (GEMVs streamed from HBM).
+// (a)+(c) block_apply_kernel, persistent CTAs, one patch at a time, sequential
+//     over slabs: gathers r on the patch, adds the jump coupling
+//     tau_a(0) M_u y_{n-1} (Eq. waveform_patch_solve: A_{n,n-1} = -tau_a(0) M_u on
+//     the last temporal DoF's velocity), applies the stored factors, which are
+//     streamed HBM -> shared memory by cp.async.bulk through an mbarrier ring.
 // (d) scatter_kernel: every global DoF pulls the outputs of the patches that
 //     contain it in a fixed order (deterministic weighted additive scatter, w = 1).
 #include <cmath>
@@ -276,7 +277,8 @@ block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const d
   for (int s = threadIdx.x; s < MS; s += NTH) slots[s] = decode_slot(g, bs, blk, s);
   if (threadIdx.x == 0) { sh[0] = 0; sh[1] = 0; }
   __syncthreads();
-  FT* F = factors + ((int64_t)blk * g.N + slab) * (Q + 1) * (Q + 1) * MS * MS;
+  constexpr int64_t BLK = (MS * MS + 16 / (int)sizeof(FT) - 1) / (16 / (int)sizeof(FT)) * (16 / (int)sizeof(FT));
+  FT* F = factors + ((int64_t)blk * g.N + slab) * (Q + 1) * (Q + 1) * BLK;
   bool ok;
   if constexpr (Q == 0) {
     assemble_block<K, Q>(g, T, ph, Ce, slab, slots, M1, 0, 0, NTH);
@@ -311,11 +313,11 @@ block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const d
     for (int t = 0; t < NE; ++t)
       if (threadIdx.x + t * NTH < MS * MS) M2[ioff[t] + jcol[t]] = acc[t];
     __syncthreads();
-    store_colmajor<MS, LD, NTH>(M2, F + 3 * MS * MS);
+    store_colmajor<MS, LD, NTH>(M2, F + 3 * BLK);
     // A10
     assemble_block<K, Q>(g, T, ph, Ce, slab, slots, M1, 1, 0, NTH);
     __syncthreads();
-    store_colmajor<MS, LD, NTH>(M1, F + 1 * MS * MS);
+    store_colmajor<MS, LD, NTH>(M1, F + 1 * BLK);
     // S = A11 - A10 X: the product in registers, then A11 added entry by entry
 #pragma unroll
     for (int t = 0; t < NE; ++t) acc[t] = 0.0;
@@ -331,110 +333,291 @@ block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const d
     add_block<K, Q>(g, T, ph, Ce, slab, slots, M2, 1, 1, NTH);
     __syncthreads();
     ok = gauss_jordan<MS, LD, NTH>(M2, colbuf, perm, sh) && ok;
-    store_colmajor<MS, LD, NTH>(M2, F + 2 * MS * MS);
+    store_colmajor<MS, LD, NTH>(M2, F + 2 * BLK);
   }
   if (!ok && threadIdx.x == 0) atomicExch(status, 1);
 }
 
-// y[i] (+)= sum_j F[j*MS + i] x[j] for thread i < MS (column-major factor block)
-template <int MS, typename FT>
-__device__ __forceinline__ FT gemv_row(const FT* __restrict__ F, const FT* x, int i) {
-  FT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-  int j = 0;
-#pragma unroll 4
-  for (; j + 3 < MS; j += 4) {
-    a0 = fma(__ldcs(F + (j + 0) * MS + i), x[j + 0], a0);
-    a1 = fma(__ldcs(F + (j + 1) * MS + i), x[j + 1], a1);
-    a2 = fma(__ldcs(F + (j + 2) * MS + i), x[j + 2], a2);
-    a3 = fma(__ldcs(F + (j + 3) * MS + i), x[j + 3], a3);
-  }
-  for (; j < MS; ++j) a0 = fma(__ldcs(F + j * MS + i), x[j], a0);
-  return (a0 + a1) + (a2 + a3);
+// ---------------------------------------------------------------- smoother apply
+// Persistent, warp-specialised.  CTA c owns patches c, c + gridDim.x, ...  A
+// patch's stored factors are one contiguous run of N (q+1)^2 column-major blocks
+// in the order they are consumed.  A producer warp streams them, in chunks of CC
+// columns, into a ring of NS shared-memory slots with cp.async.bulk; slot s has a
+// "full" mbarrier (transaction count = the chunk's bytes) and an "empty"
+// mbarrier on which every consumer warp arrives once it has read the chunk, so
+// the producer refills a slot as soon as it is free and about NS chunks stay in
+// flight.  Consumer thread (i, g) multiplies row i by the g-th sub-range of each
+// chunk's columns (G groups: 95-99% of the lanes issue FP64 FMAs, which bind on
+// GB300) with four independent accumulators; partial sums are combined in a fixed
+// order after a named barrier of the consumer warps.  The next slab's right-hand
+// side is prefetched into registers while the current slab's blocks are applied.
+// Every wait is bounded: on timeout the kernel sets *err, drains its own copies
+// in flight (bounded) and returns.
+template <int K, int Q, typename FT>
+struct ApplyCfg {
+  using pd = PD<K>;
+  static constexpr int MS = pd::MS, NT = Q + 1, NB = NT * NT;
+  static constexpr int G = K == 1 ? 5 : 4;                        // column groups per chunk
+  static constexpr int NCONS = (G * MS + 31) / 32 * 32;           // consumer threads: 256 or 448
+  static constexpr int NTH = NCONS + 32;                          // + one producer warp
+  static constexpr int GR = 16 / (int)sizeof(FT);                 // elements per 16-byte granule
+  static constexpr int BLK = (MS * MS + GR - 1) / GR * GR;        // padded block elements
+  static constexpr int BLK_BYTES = BLK * (int)sizeof(FT);
+  // chunk width: whole block for k = 1, 28 columns for k = 2 (a multiple of GR columns keeps
+  // every chunk boundary on a 16-byte granule)
+  static constexpr int CC = K == 1 ? (MS + GR - 1) / GR * GR : 28;
+  static constexpr int NCH = (MS + CC - 1) / CC;                  // chunks per block
+  static constexpr int SUB = (CC + G - 1) / G;                    // columns per group and chunk
+  static constexpr int LAST = BLK - (NCH - 1) * CC * MS;          // last chunk carries the padding
+  static constexpr int SLOT = CC * MS > LAST ? CC * MS : LAST;
+  static constexpr int SLOT_ELEMS = (SLOT + GR - 1) / GR * GR;
+  static constexpr int RING_BYTES = 176 * 1024;
+  static constexpr int NS = RING_BYTES / (SLOT_ELEMS * (int)sizeof(FT)) < 16
+                                ? RING_BYTES / (SLOT_ELEMS * (int)sizeof(FT))
+                                : 16;
+  static_assert((CC * MS * (int)sizeof(FT)) % 16 == 0, "chunk boundary off the 16-byte granule");
+  static_assert(NS >= 2, "ring too small");
+};
+
+template <int K, int Q, typename FT>
+struct ApplySmem {
+  using C = ApplyCfg<K, Q, FT>;
+  using pd = PD<K>;
+  unsigned long long full[C::NS];
+  unsigned long long empty[C::NS];
+  int abort_flag;  // written by any warp at any time
+  int decision;    // abort decision of the consumers, published by consumer thread 0 before a barrier
+  int issued;
+  int sidx[C::MS];
+  FT rhs[C::NT][C::MS];
+  FT y[C::NT][C::MS];
+  FT red[C::G][C::MS];
+  FT yp[2][pd::NVG2];
+  FT tm[2][pd::NVG2];
+  FT mx[pd::NVG][pd::NVG];
+  FT my[pd::NVG][pd::NVG];
+};
+
+constexpr int kSpinLimit = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < kSpinLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+template <int NCONS>
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(NCONS) : "memory");
 }
 
 template <int K, int Q, typename FT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(ApplyCfg<K, Q, FT>::NTH, 1)
 block_apply_kernel(LevelGeom g, FeTables T, BlockSet bs, const FT* __restrict__ factors, const double* __restrict__ r,
-                   double* __restrict__ out) {
+                   double* __restrict__ out, int nblk, int* __restrict__ err) {
+  using C = ApplyCfg<K, Q, FT>;
   using pd = PD<K>;
-  constexpr int MS = pd::MS, NT = Q + 1, NVG = pd::NVG, NVG2 = pd::NVG2;
-  __shared__ int sidx[MS];
-  __shared__ FT rhs[NT][MS];
-  __shared__ FT y[NT][MS];
-  __shared__ FT yp[2][NVG2];
-  __shared__ FT tm[2][NVG2];
-  __shared__ FT mx[NVG][NVG], my[NVG][NVG];
-  const int blk = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
-  int vx0, vy0, px0, py0;
-  block_origin(g, bs, blk, vx0, vy0, px0, py0);
-  const int nvg = bs.nvg;  // <= NVG
-  for (int s = tid; s < MS; s += nth) sidx[s] = decode_slot(g, bs, blk, s).sp;
-  for (int e = tid; e < NVG * NVG; e += nth) {
-    const int i = e / NVG, j = e % NVG;
-    const int xi = vx0 + i, xj = vx0 + j, yi = vy0 + i, yj = vy0 + j;
-    const bool vx = i < nvg && j < nvg && xi >= 1 && xi <= g.nv - 2 && xj >= 1 && xj <= g.nv - 2;
-    const bool vy = i < nvg && j < nvg && yi >= 1 && yi <= g.nv - 2 && yj >= 1 && yj <= g.nv - 2;
-    mx[i][j] = vx ? (FT)(g.h * vv1<K>(T.m1, g.n, xi, xj)) : (FT)0;
-    my[i][j] = vy ? (FT)(g.h * vv1<K>(T.m1, g.n, yi, yj)) : (FT)0;
+  constexpr int MS = C::MS, NT = C::NT, NB = C::NB, NS = C::NS, NVG = pd::NVG, NCH = C::NCH, NCONS = C::NCONS;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  FT* ring = reinterpret_cast<FT*>(smem_raw);
+  ApplySmem<K, Q, FT>& sm =
+      *reinterpret_cast<ApplySmem<K, Q, FT>*>(smem_raw + (size_t)NS * C::SLOT_ELEMS * sizeof(FT));
+  volatile int* abort_flag = &sm.abort_flag;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int npatch_cta = blockIdx.x < nblk ? (nblk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t blocks_pp = (int64_t)g.N * NB;         // blocks per patch
+  const int64_t total = npatch_cta * blocks_pp * NCH;  // chunks streamed by this CTA
+  if (tid == 0) {
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(smem_u32(&sm.full[i]), 1);
+      mbar_init(smem_u32(&sm.empty[i]), NCONS / 32);
+    }
+    sm.abort_flag = 0;
+    sm.decision = 0;
+    sm.issued = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int e = tid; e < 2 * NVG2; e += nth) (&yp[0][0])[e] = 0;
   __syncthreads();
-  const int nv2g = nvg * nvg;
-  for (int slab = 0; slab < g.N; ++slab) {
-    // (a) gather
-    for (int e = tid; e < NT * MS; e += nth) {
-      const int a = e / MS, s = e % MS;
-      const int sp = sidx[s];
-      rhs[a][s] = sp >= 0 ? (FT)r[((int64_t)slab * NT + a) * g.S + sp] : (FT)0;
-    }
-    if (slab > 0) {
-      // jump coupling: rhs_a += tau_a(0) M_u y_{n-1, last} (tensor-product mass on the slot grid)
-      for (int e = tid; e < 2 * nv2g; e += nth) {
-        const int c = e / nv2g, t = e % nv2g, iy = t / nvg, jx = t % nvg;
-        FT acc = 0;
-        for (int jy = 0; jy < nvg; ++jy) acc = fma(my[iy][jy], yp[c][jy * nvg + jx], acc);
-        tm[c][t] = acc;
-      }
-      __syncthreads();
-      for (int e = tid; e < 2 * nv2g; e += nth) {
-        const int c = e / nv2g, t = e % nv2g, iy = t / nvg, ix = t % nvg;
-        FT acc = 0;
-        for (int jx = 0; jx < nvg; ++jx) acc = fma(mx[ix][jx], tm[c][iy * nvg + jx], acc);
-        const int s = c * nv2g + t;
-        if (sidx[s] >= 0)
-          for (int a = 0; a < NT; ++a) rhs[a][s] += (FT)T.tau0[a] * acc;
-      }
-    }
-    __syncthreads();
-    // (c) apply the stored slab factors
-    const FT* F = factors + ((int64_t)blk * g.N + slab) * NT * NT * MS * MS;
-    if constexpr (Q == 0) {
-      if (tid < MS) y[0][tid] = gemv_row<MS>(F, rhs[0], tid);
-      __syncthreads();
-    } else {
-      if (tid < MS) y[0][tid] = gemv_row<MS>(F, rhs[0], tid);                        // z0 = A00^{-1} r0
-      __syncthreads();
-      if (tid < MS) rhs[1][tid] -= gemv_row<MS>(F + 1 * MS * MS, y[0], tid);          // s1 = r1 - A10 z0
-      __syncthreads();
-      if (tid < MS) y[1][tid] = gemv_row<MS>(F + 2 * MS * MS, rhs[1], tid);          // y1 = S^{-1} s1
-      __syncthreads();
-      if (tid < MS) y[0][tid] -= gemv_row<MS>(F + 3 * MS * MS, y[1], tid);           // y0 = z0 - X y1
-      __syncthreads();
-    }
-    // output
-    for (int e = tid; e < NT * MS; e += nth) {
-      const int a = e / MS, s = e % MS;
-      if (bs.kind == 0) {
-        out[(((int64_t)blk * g.N + slab) * NT + a) * MS + s] = (double)y[a][s];
-      } else if (sidx[s] >= 0) {
-        out[((int64_t)slab * NT + a) * g.S + sidx[s]] = (double)y[a][s];
+
+  if (tid >= NCONS) {  // ---------------- producer warp
+    if (lane == 0) {
+      for (int64_t s = 0; s < total; ++s) {
+        const int slot = (int)(s % NS);
+        const int64_t u = s / NS;
+        if (u > 0 && !mbar_wait_bounded(smem_u32(&sm.empty[slot]), (uint32_t)((u - 1) & 1))) {
+          *abort_flag = 1;
+          atomicExch(err, 1);
+          break;
+        }
+        if (*abort_flag) break;
+        const int64_t bi = s / NCH;  // CTA-local block index
+        const int k = (int)(s - bi * NCH);
+        const int t = (int)(bi / blocks_pp);
+        const int64_t q = bi - t * blocks_pp;
+        const int blk = blockIdx.x + t * gridDim.x;
+        const int64_t off = ((int64_t)blk * blocks_pp + q) * C::BLK + (int64_t)k * C::CC * MS;
+        const int elems = (k == NCH - 1) ? C::BLK - k * C::CC * MS : C::CC * MS;
+        const uint32_t bar = smem_u32(&sm.full[slot]);
+        const uint32_t bytes = (uint32_t)(elems * sizeof(FT));
+        mbar_expect_tx(bar, bytes);
+        bulk_g2s(smem_u32(ring + (size_t)slot * C::SLOT_ELEMS), factors + off, bytes, bar);
+        *(volatile int*)&sm.issued = (int)(s + 1 < 0x7fffffff ? s + 1 : 0x7fffffff);
       }
     }
-    for (int e = tid; e < 2 * nv2g; e += nth) {
-      const int c = e / nv2g, t = e % nv2g;
-      yp[c][t] = y[NT - 1][c * nv2g + t];
+    return;
+  }
+
+  // ---------------- consumer warps
+  int64_t ci = 0;  // next chunk to consume
+  const int nvg = bs.nvg, nv2g = nvg * nvg;
+  const bool gemv_thread = tid < C::G * MS;
+  const int row = tid % MS, grp = tid / MS;
+  bool aborted = false;
+  for (int t = 0; t < npatch_cta && !aborted; ++t) {
+    const int blk = blockIdx.x + t * gridDim.x;
+    int vx0, vy0, px0, py0;
+    block_origin(g, bs, blk, vx0, vy0, px0, py0);
+    for (int s = tid; s < MS; s += NCONS) sm.sidx[s] = decode_slot(g, bs, blk, s).sp;
+    for (int e = tid; e < NVG * NVG; e += NCONS) {
+      const int i = e / NVG, j = e % NVG;
+      const int xi = vx0 + i, xj = vx0 + j, yi = vy0 + i, yj = vy0 + j;
+      const bool okx = i < nvg && j < nvg && xi >= 1 && xi <= g.nv - 2 && xj >= 1 && xj <= g.nv - 2;
+      const bool oky = i < nvg && j < nvg && yi >= 1 && yi <= g.nv - 2 && yj >= 1 && yj <= g.nv - 2;
+      sm.mx[i][j] = okx ? (FT)(g.h * vv1<K>(T.m1, g.n, xi, xj)) : (FT)0;
+      sm.my[i][j] = oky ? (FT)(g.h * vv1<K>(T.m1, g.n, yi, yj)) : (FT)0;
     }
-    __syncthreads();
+    for (int e = tid; e < 2 * pd::NVG2; e += NCONS) (&sm.yp[0][0])[e] = 0;
+    consumer_sync<NCONS>();
+    // (a) gather of slab 0; later slabs come from the register prefetch
+    for (int e = tid; e < NT * MS; e += NCONS) {
+      const int a = e / MS, s = e % MS, sp = sm.sidx[s];
+      sm.rhs[a][s] = sp >= 0 ? (FT)r[(int64_t)a * g.S + sp] : (FT)0;
+    }
+    for (int slab = 0; slab < g.N && !aborted; ++slab) {
+      if (slab > 0) {
+        // jump coupling: rhs_a += tau_a(0) M_u y_{n-1, last} (tensor-product mass on the slot grid)
+        consumer_sync<NCONS>();
+        for (int e = tid; e < 2 * nv2g; e += NCONS) {
+          const int c = e / nv2g, tt = e % nv2g, iy = tt / nvg, jx = tt % nvg;
+          FT acc = 0;
+          for (int jy = 0; jy < nvg; ++jy) acc = fma(sm.my[iy][jy], sm.yp[c][jy * nvg + jx], acc);
+          sm.tm[c][tt] = acc;
+        }
+        consumer_sync<NCONS>();
+        for (int e = tid; e < 2 * nv2g; e += NCONS) {
+          const int c = e / nv2g, tt = e % nv2g, iy = tt / nvg, ix = tt % nvg;
+          FT acc = 0;
+          for (int jx = 0; jx < nvg; ++jx) acc = fma(sm.mx[ix][jx], sm.tm[c][iy * nvg + jx], acc);
+          const int s = c * nv2g + tt;
+          if (sm.sidx[s] >= 0)
+            for (int a = 0; a < NT; ++a) sm.rhs[a][s] += (FT)T.tau0[a] * acc;
+        }
+      }
+      consumer_sync<NCONS>();
+      // register prefetch of the next slab's right-hand side
+      FT pf = 0;
+      if (tid < NT * MS && slab + 1 < g.N) {
+        const int sp = sm.sidx[tid % MS];
+        if (sp >= 0) pf = (FT)r[((int64_t)(slab + 1) * NT + tid / MS) * g.S + sp];
+      }
+      // (c) the slab's stored blocks: Q = 0: y0 = A^{-1} r0;  Q = 1: z0 = A00^{-1} r0,
+      //     s1 = r1 - A10 z0, y1 = S^{-1} s1, y0 = z0 - X y1
+      for (int b = 0; b < NB; ++b) {
+        const FT* xv = (b == 0) ? sm.rhs[0] : (b == 1) ? sm.y[0] : (b == 2) ? sm.rhs[NT - 1] : sm.y[NT - 1];
+        FT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int k = 0; k < NCH; ++k) {
+          const int slot = (int)(ci % NS);
+          const bool ok = !aborted && mbar_wait_bounded(smem_u32(&sm.full[slot]), (uint32_t)((ci / NS) & 1));
+          if (!ok) {
+            aborted = true;
+            *abort_flag = 1;
+          }
+          if (ok && gemv_thread) {
+            const FT* A = ring + (size_t)slot * C::SLOT_ELEMS;
+            const int c0 = grp * C::SUB;
+            const int ncol = min(C::CC, MS - k * C::CC);
+            const int c1 = min(ncol, c0 + C::SUB);
+            const FT* xk = xv + k * C::CC;
+            int c = c0;
+            for (; c + 3 < c1; c += 4) {
+              a0 = fma(A[(c + 0) * MS + row], xk[c + 0], a0);
+              a1 = fma(A[(c + 1) * MS + row], xk[c + 1], a1);
+              a2 = fma(A[(c + 2) * MS + row], xk[c + 2], a2);
+              a3 = fma(A[(c + 3) * MS + row], xk[c + 3], a3);
+            }
+            for (; c < c1; ++c) a0 = fma(A[c * MS + row], xk[c], a0);
+          }
+          __syncwarp();
+          if (ok && lane == 0) mbar_arrive(smem_u32(&sm.empty[slot]));  // this warp is done with the slot
+          ++ci;
+        }
+        if (gemv_thread) sm.red[grp][row] = (a0 + a1) + (a2 + a3);
+        if (tid == 0) sm.decision = *abort_flag;  // one reader, so every consumer decides alike
+        consumer_sync<NCONS>();
+        if (sm.decision) {
+          aborted = true;
+          break;
+        }
+        if (tid < MS) {
+          FT sum = sm.red[0][tid];
+#pragma unroll
+          for (int h = 1; h < C::G; ++h) sum += sm.red[h][tid];
+          if (b == 0) sm.y[0][tid] = sum;
+          else if (b == 1) sm.rhs[NT - 1][tid] -= sum;
+          else if (b == 2) sm.y[NT - 1][tid] = sum;
+          else sm.y[0][tid] -= sum;
+        }
+        consumer_sync<NCONS>();
+      }
+      if (aborted) break;
+      // output, jump state, next right-hand side
+      for (int e = tid; e < NT * MS; e += NCONS) {
+        const int a = e / MS, s = e % MS;
+        if (bs.kind == 0) {
+          out[(((int64_t)blk * g.N + slab) * NT + a) * MS + s] = (double)sm.y[a][s];
+        } else if (sm.sidx[s] >= 0) {
+          out[((int64_t)slab * NT + a) * g.S + sm.sidx[s]] = (double)sm.y[a][s];
+        }
+      }
+      for (int e = tid; e < 2 * nv2g; e += NCONS) {
+        const int c = e / nv2g, tt = e % nv2g;
+        sm.yp[c][tt] = sm.y[NT - 1][c * nv2g + tt];
+      }
+      if (tid < NT * MS) sm.rhs[tid / MS][tid % MS] = pf;
+    }
+    consumer_sync<NCONS>();
+  }
+  if (aborted && tid == 0) {
+    // drain this CTA's own copies in flight (bounded), then report
+    // the last NS issued chunks are the latest copy into each slot
+    const int64_t issued = *(volatile int*)&sm.issued;
+    for (int64_t s = issued > NS ? issued - NS : 0; s < issued; ++s)
+      mbar_wait_bounded(smem_u32(&sm.full[(int)(s % NS)]), (uint32_t)((s / NS) & 1));
+    atomicExch(err, 1);
   }
 }
 
@@ -494,11 +677,22 @@ void run_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph, con
 
 template <int K, int Q, typename FT>
 void run_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs, const FT* factors, const double* r,
-               double* out, cudaStream_t s) {
-  using pd = PD<K>;
-  const int nth = ((pd::MS + 31) / 32) * 32;
+               double* out, int* err, cudaStream_t s) {
+  using C = ApplyCfg<K, Q, FT>;
+  const size_t smem = (size_t)C::NS * C::SLOT_ELEMS * sizeof(FT) + sizeof(ApplySmem<K, Q, FT>);
+  auto kern = block_apply_kernel<K, Q, FT>;
+  static int grid_cap = 0;  // persistent grid: CTAs resident on the whole GPU
+  if (grid_cap == 0) {
+    WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0, per_sm = 0;
+    WR_CUDA(cudaGetDevice(&dev));
+    WR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    WR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NTH, smem));
+    grid_cap = sms * (per_sm > 0 ? per_sm : 1);
+  }
   const int nblk = bs.kind == 0 ? g.npatch() : 1;
-  block_apply_kernel<K, Q, FT><<<nblk, nth, 0, s>>>(g, T, bs, factors, r, out);
+  const int grid = nblk < grid_cap ? nblk : grid_cap;
+  kern<<<grid, C::NTH, smem, s>>>(g, T, bs, factors, r, out, nblk, err);
   WR_LAUNCH_CHECK();
 }
 
@@ -530,13 +724,13 @@ void launch_block_factor(const LevelGeom& g, const FeTables& T, const PhysParams
 }
 
 void launch_block_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs, const void* factors, int precision,
-                        const double* r, double* out, cudaStream_t s) {
+                        const double* r, double* out, int* err, cudaStream_t s) {
 #define WR_A(K_, Q_)                                                                                          \
   if (g.k == K_ && g.q == Q_) {                                                                               \
     if (precision == WR_FP32)                                                                                 \
-      run_apply<K_, Q_, float>(g, T, bs, static_cast<const float*>(factors), r, out, s);                     \
+      run_apply<K_, Q_, float>(g, T, bs, static_cast<const float*>(factors), r, out, err, s);                     \
     else                                                                                                      \
-      run_apply<K_, Q_, double>(g, T, bs, static_cast<const double*>(factors), r, out, s);                   \
+      run_apply<K_, Q_, double>(g, T, bs, static_cast<const double*>(factors), r, out, err, s);                   \
   } else
   WR_A(1, 0) WR_A(1, 1) WR_A(2, 0) WR_A(2, 1) throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 #undef WR_A

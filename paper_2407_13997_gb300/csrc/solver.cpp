@@ -54,7 +54,9 @@ struct wr_ctx {
   std::vector<double*> V, Z;
   double *F = nullptr, *w = nullptr, *hb = nullptr, *hx = nullptr;
   double *partials = nullptr, *dres = nullptr, *hres = nullptr;
+  int* herr = nullptr;
   int* slots = nullptr;
+  int* derr = nullptr;  // device error flag of the bounded waits
   std::vector<void*> allocs;
   int64_t bytes = 0;
   bool linearised = false;
@@ -92,6 +94,7 @@ struct wr_ctx {
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
     if (hres) cudaFreeHost(hres);
+    if (herr) cudaFreeHost(herr);
   }
 
   Level& fine() { return L.back(); }
@@ -100,8 +103,15 @@ struct wr_ctx {
   double dot(int64_t n, const double* x, const double* y) {
     vec_dot_dev(n, x, y, partials, dres, s);
     WR_CUDA(cudaMemcpyAsync(hres, dres, sizeof(double), cudaMemcpyDeviceToHost, s));
+    WR_CUDA(cudaMemcpyAsync(herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
     WR_CUDA(cudaStreamSynchronize(s));
+    if (*herr) throw WrError(WR_ERR_TIMEOUT, "a bounded wait in the smoother kernel gave up");
     return *hres;
+  }
+  void check_device() {
+    WR_CUDA(cudaMemcpyAsync(herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    WR_CUDA(cudaStreamSynchronize(s));
+    if (*herr) throw WrError(WR_ERR_TIMEOUT, "a bounded wait in the smoother kernel gave up");
   }
   double norm(int64_t n, const double* x) { return std::sqrt(dot(n, x, x)); }
 
@@ -112,11 +122,11 @@ struct wr_ctx {
     if (prof) {
       cudaEvent_t e0 = next_event(), e1 = next_event();
       WR_CUDA(cudaEventRecord(e0, s));
-      launch_block_apply(L[l].g, tab, L[l].bs, L[l].factors, opt.precision, r, Yp, s);
+      launch_block_apply(L[l].g, tab, L[l].bs, L[l].factors, opt.precision, r, Yp, derr, s);
       WR_CUDA(cudaEventRecord(e1, s));
       prof_ev[l].push_back({e0, e1});
     } else {
-      launch_block_apply(L[l].g, tab, L[l].bs, L[l].factors, opt.precision, r, Yp, s);
+      launch_block_apply(L[l].g, tab, L[l].bs, L[l].factors, opt.precision, r, Yp, derr, s);
     }
     launch_scatter(L[l].g, L[l].bs, Yp, y, s);
   }
@@ -125,7 +135,7 @@ struct wr_ctx {
     if (!linearised) throw WrError(WR_ERR_STATE, "wr_linearise must be called first");
     const LevelGeom& g = L[0].g;
     vec_zero(g.ndofs, x, s);
-    launch_block_apply(g, tab, cbs, cfactors, WR_FP64, b, x, s);
+    launch_block_apply(g, tab, cbs, cfactors, WR_FP64, b, x, derr, s);
     launch_project_pressure(g, tab, x, s);
   }
 
@@ -496,7 +506,7 @@ int wr_create(wr_ctx** out, const wr_problem* p, const wr_options* o, void* stre
       max_ce = std::max(max_ce, (size_t)p->n_slabs * lv.g.ncells() * nt * 4 * nvle * nvle);
       max_ye = std::max(max_ye, (size_t)p->n_slabs * lv.g.ncells() * elem);
       if (l >= 1) {
-        const size_t nf = (size_t)lv.g.npatch() * p->n_slabs * nt * nt * ms * ms;
+        const size_t nf = (size_t)lv.g.npatch() * p->n_slabs * nt * nt * factor_block_elems(p->k, c->opt.precision);
         void* f = nullptr;
         if (fsz == sizeof(float)) f = c->alloc<float>(nf);
         else f = c->alloc<double>(nf);
@@ -510,7 +520,7 @@ int wr_create(wr_ctx** out, const wr_problem* p, const wr_options* o, void* stre
     c->cbs.npg = c->L[0].g.np;
     c->cbs.ms = ms;
     need(2 * c->cbs.nvg * c->cbs.nvg + c->cbs.npg * c->cbs.npg <= ms, "coarse block exceeds the slot layout");
-    c->cfactors = c->alloc<double>((size_t)p->n_slabs * nt * nt * ms * ms);
+    c->cfactors = c->alloc<double>((size_t)p->n_slabs * nt * nt * factor_block_elems(p->k, WR_FP64));
     c->Ce = c->alloc<double>(p->conv != 0.0 ? max_ce : 1);
     c->ye = c->alloc<double>(max_ye);
     c->Yp = c->alloc<double>(max_yp);
@@ -525,7 +535,11 @@ int wr_create(wr_ctx** out, const wr_problem* p, const wr_options* o, void* stre
     c->partials = c->alloc<double>(dot_partials_size());
     c->dres = c->alloc<double>(1);
     c->slots = c->alloc<int>(2 * ms);
+    c->derr = c->alloc<int>(1);
+    WR_CUDA(cudaMemset(c->derr, 0, sizeof(int)));
     WR_CUDA(cudaMallocHost(&c->hres, sizeof(double)));
+    WR_CUDA(cudaMallocHost(&c->herr, sizeof(int)));
+    *c->herr = 0;
     return WR_OK;
   });
   if (rc != WR_OK) {
@@ -697,7 +711,7 @@ int wr_vcycle_host(wr_ctx* c, const double* b_host, double* x_host) {
     WR_CUDA(cudaMemcpyAsync(c->hb, b_host, sizeof(double) * n, cudaMemcpyHostToDevice, c->s));
     c->vcycle(c->hb, c->hx);
     WR_CUDA(cudaMemcpyAsync(x_host, c->hx, sizeof(double) * n, cudaMemcpyDeviceToHost, c->s));
-    WR_CUDA(cudaStreamSynchronize(c->s));
+    c->check_device();
     return WR_OK;
   });
 }
@@ -746,6 +760,12 @@ int wr_profile(wr_ctx* c, int enable) {
     c->prof = enable != 0;
     c->prof_ev.assign(c->L.size(), {});
     c->ev_used = 0;
+    // create the events now so that none is created inside a timed region
+    while (c->prof && c->ev_pool.size() < 4096) {
+      cudaEvent_t e;
+      WR_CUDA(cudaEventCreate(&e));
+      c->ev_pool.push_back(e);
+    }
     return WR_OK;
   });
 }

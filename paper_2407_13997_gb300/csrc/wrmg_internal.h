@@ -100,6 +100,13 @@ inline LevelGeom make_geom(int n, int k, int q, int N, double T) {
 inline int patch_nvg(int k) { return 2 * k + 3; }
 inline int patch_npg(int k) { return 2 * k - 1; }
 inline int patch_ms(int k) { return 2 * patch_nvg(k) * patch_nvg(k) + patch_npg(k) * patch_npg(k); }
+// Elements of one stored ms x ms factor block, padded to a multiple of 16 bytes
+// (the granule of the bulk copies that stream the blocks into shared memory).
+inline int64_t factor_block_elems(int k, int precision) {
+  const int64_t e = (int64_t)patch_ms(k) * patch_ms(k);
+  const int64_t g = precision == WR_FP32 ? 4 : 2;
+  return (e + g - 1) / g * g;
+}
 
 // A dense block of the smoother or of the coarse solve: the velocity slots form
 // an nvg x nvg grid of global velocity nodes from (vx0, vy0), the pressure
@@ -129,7 +136,7 @@ void launch_block_factor(const LevelGeom& g, const FeTables& T, const PhysParams
                          cudaStream_t s);
 void launch_block_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs,
                         const void* factors, int precision, const double* r, double* out,
-                        cudaStream_t s);
+                        int* err, cudaStream_t s);
 void launch_scatter(const LevelGeom& g, const BlockSet& bs, const double* Yp, double* y,
                     cudaStream_t s);
 void launch_restrict(const LevelGeom& gf, const LevelGeom& gc, const FeTables& T,

@@ -1,0 +1,59 @@
+"""Precision form: FP32 stored patch factors and FP32 smoother arithmetic, with the
+residual, FGMRES (Arnoldi, Givens, least squares) and the coarse solve in FP64.
+
+The smoother itself is only FP32-accurate, so it is compared with the FP64 oracle
+at 2e-5 relative (FP32 rounding of inverses with condition numbers up to ~1e2);
+whole solves are run to a tight residual (1e-11) so that both the FP32-smoother
+solution and the FP64 oracle solution sit well inside the 1e-8 bound on the
+final solution that the precision form must meet.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.fem import Discretisation
+from oracle.patches import PatchSmoother
+from oracle.solver import Hierarchy, Options, newton_solve
+from oracle.transfer import injection
+from paper_2407_13997_gb300 import inputs, wrmg
+from tests.oracle_problems import oracle_problem
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.mark.parametrize("w", [inputs.fourier_small(n=8, k=1, q=0, N=3, nu=0.02),
+                               inputs.fourier_small(n=4, k=2, q=1, N=2, nu=0.01)], ids=["q2q1_dg0", "q3q2_dg1"])
+def test_fp32_smoother_close_to_fp64_oracle(w):
+    ctx = wrmg.Context(w, wrmg.default_options(precision=wrmg.WR_FP32))
+    d = Discretisation(w.n_fine, w.k, w.q, w.N, oracle_problem(w))
+    rng = np.random.default_rng(5)
+    W = 0.5 * rng.standard_normal(d.ndofs)
+    mask = d.dirichlet_mask()
+    W[mask] = d.boundary_values()[mask]
+    ctx.linearise(torch.from_numpy(W).cuda(), eig=False)
+    r = rng.standard_normal(d.ndofs)
+    y = ctx.vector()
+    ctx.patch_apply(ctx.fine, torch.from_numpy(r).cuda(), y)
+    ref = PatchSmoother(d, d.jacobian(W)).apply(r)
+    err = rel(y.cpu().numpy(), ref)
+    assert 1e-12 < err < 2e-5, err   # genuinely FP32, and FP32-accurate
+    ctx.close()
+
+
+@pytest.mark.parametrize("w", [inputs.taylor_green_8x8(), inputs.fourier_small(n=8, k=2, q=1, N=4, nu=1e-2)],
+                         ids=["tg_q2q1_dg0_n8_N8", "fourier_q3q2_dg1_n8_N4"])
+def test_fp32_smoother_solve_meets_1e8_against_fp64_oracle(w):
+    opts = wrmg.default_options(precision=wrmg.WR_FP32, newton_rtol=1e-11)
+    ctx = wrmg.Context(w, opts)
+    U = ctx.vector()
+    ctx.initial_guess(U)
+    st = ctx.solve(U)
+    hier = Hierarchy(w.n_fine, w.n_coarse, w.k, w.q, w.N, oracle_problem(w), Options(newton_rtol=1e-11))
+    ref = newton_solve(hier)
+    err = rel(U.cpu().numpy(), ref)
+    assert err <= 1e-8, (err, st)
+    ctx.close()
