@@ -128,17 +128,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def smoother_algorithmic(ctx, w):
-    """Algorithmic bytes and FP64 flops of one finest-level smoother-apply launch:
+def smoother_algorithmic(ctx, w, factor_bytes=8):
+    """Algorithmic bytes and flops of one finest-level smoother-apply launch:
     every (patch, slab) streams its (q+1)^2 m^2 factor entries once (m = the
-    patch's true size, padding excluded), reads its m (q+1) right-hand side
-    values and writes as many outputs; 2 flops per factor entry."""
+    patch's true size, padding excluded; factor_bytes per entry), reads its
+    m (q+1) FP64 right-hand side values and writes as many FP64 outputs;
+    2 flops per factor entry."""
     L = ctx.fine
     n1 = w.n_fine + 1
     sizes = [len(ctx.patch_dofs(L, p, 0)) for p in range(n1 * n1)]  # (q+1) * m per slab
     ent = sum(s * s for s in sizes) * w.N
     vec = sum(sizes) * w.N
-    return 8.0 * (ent + 2 * vec), 2.0 * ent
+    return factor_bytes * ent + 16.0 * vec, 2.0 * ent
 
 
 def traffic_record(kernel):
@@ -281,7 +282,7 @@ def run_ours(args):
         e2e_s = float(t.item())
     assert np.isfinite(xn).all()
 
-    alg_bytes, alg_flops = smoother_algorithmic(ctx, w)
+    alg_bytes, alg_flops = smoother_algorithmic(ctx, w, 8 if prec == wrmg.WR_FP64 else 4)
     avg_s = sm_ms / max(sm_n, 1) * 1e-3
     hbm_peak, hbm_src = measured_peaks()
     achieved_tf = alg_flops / avg_s / 1e12

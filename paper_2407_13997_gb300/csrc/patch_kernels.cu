@@ -109,89 +109,181 @@ __device__ __forceinline__ double pv1(const double (*ref)[WR_MAX_NVL], int n, in
   return v;
 }
 
-// Entry (a, b) temporal block, slots si, sj, of the slab diagonal block of J(W).
-template <int K, int Q>
-__device__ __noinline__ double jac_entry(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* __restrict__ Ce,
-                            int slab, const Slot& si, const Slot& sj, int a, int b) {
+// ---------------------------------------------------------------- factorisation
+// One CTA per (block, slab).  The slab diagonal block A_nn = J(W)[P_i, P_i] is
+// assembled in shared memory in two passes per temporal sub-block (a, b):
+//   1. the constant-coefficient part from per-patch tables of the global 1D
+//      matrices restricted to the slot grid (tensor products on the Cartesian
+//      mesh):  Kt[a,b] M + dt nu Wt[a,b] K  on velocity pairs of one component,
+//      dt Wt[a,b] (chi, d_c phi) on velocity-pressure pairs;
+//   2. the convection  dt conv sum_e T3[a,b,e] Ce_e  scattered cell by cell from
+//      the element convection matrices of every cell whose closure meets the
+//      slot grid (the 2x2 star and, for the principal submatrix, its ring of
+//      cells), with coalesced reads and no write conflicts.
+// The block is then inverted by Gauss-Jordan with partial pivoting (DG(0)), or,
+// for DG(1), factored as A00^{-1}, X = A00^{-1} A01, S = A11 - A10 X, S^{-1}.
+// CT is the arithmetic and storage type: double (plain form) or float
+// (precision form; FP32 runs at 58x the FP64 rate on GB300).
+
+template <int K>
+struct FactorTables {
+  static constexpr int NVG = 2 * K + 3, NPT = 2 * K + 1;  // slot-grid sizes (pressure: coarse block is larger)
+  double Mx[NVG][NVG], Kx[NVG][NVG], My[NVG][NVG], Ky[NVG][NVG];
+  double Dx[NPT][NVG], Cx[NPT][NVG], Dy[NPT][NVG], Cy[NPT][NVG];
+  signed char sf[PD<K>::MS];               // slot field 0/1 velocity, 2 pressure, -1 padding
+  signed char sx[PD<K>::MS], sy[PD<K>::MS];  // slot-grid coordinates
+};
+
+template <int K>
+__device__ void build_factor_tables(const LevelGeom& g, const FeTables& T, const BlockSet& bs, int blk,
+                                    FactorTables<K>& ft, int nth) {
   using pd = PD<K>;
-  constexpr int NT = Q + 1;
-  if (si.sp < 0 || sj.sp < 0) return 0.0;  // padding is handled by the callers
-  const double h = g.h, dt = g.dt;
-  const int n = g.n;
-  if (si.field < 2 && sj.field < 2) {
-    double v = 0.0;
-    if (si.field == sj.field) {
-      const double mx = h * vv1<K>(T.m1, n, si.gx, sj.gx), my = h * vv1<K>(T.m1, n, si.gy, sj.gy);
-      const double kx = vv1<K>(T.k1, n, si.gx, sj.gx) / h, ky = vv1<K>(T.k1, n, si.gy, sj.gy) / h;
-      v = T.Kt[a][b] * mx * my + dt * ph.nu * T.Wt[a][b] * (kx * my + mx * ky);
-    }
-    if (ph.conv != 0.0) {
-      const int p = K + 1;
-      const int cx0 = max(cell_lo(si.gx, p), cell_lo(sj.gx, p)), cx1 = min(cell_hi(si.gx, p, n), cell_hi(sj.gx, p, n));
-      const int cy0 = max(cell_lo(si.gy, p), cell_lo(sj.gy, p)), cy1 = min(cell_hi(si.gy, p, n), cell_hi(sj.gy, p, n));
-      double cv = 0.0;
-      for (int cy = cy0; cy <= cy1; ++cy)
-        for (int cx = cx0; cx <= cx1; ++cx) {
-          const int li = (si.gy - p * cy) * pd::NVL + (si.gx - p * cx);
-          const int lj = (sj.gy - p * cy) * pd::NVL + (sj.gx - p * cx);
-          const double* m = Ce + ((int64_t)slab * g.ncells() + cy * n + cx) * (NT * 4 * pd::NVE * pd::NVE) +
-                            (si.field * 2 + sj.field) * pd::NVE * pd::NVE + li * pd::NVE + lj;
-#pragma unroll
-          for (int e = 0; e < NT; ++e) cv += T.T3[a][b][e] * m[(int64_t)e * 4 * pd::NVE * pd::NVE];
-        }
-      v += dt * ph.conv * cv;
-    }
-    return v;
+  using TB = FactorTables<K>;
+  int vx0, vy0, px0, py0;
+  block_origin(g, bs, blk, vx0, vy0, px0, py0);
+  const double h = g.h;
+  for (int e = threadIdx.x; e < TB::NVG * TB::NVG; e += nth) {
+    const int i = e / TB::NVG, j = e % TB::NVG;
+    const int xi = min(max(vx0 + i, 0), g.nv - 1), xj = min(max(vx0 + j, 0), g.nv - 1);
+    const int yi = min(max(vy0 + i, 0), g.nv - 1), yj = min(max(vy0 + j, 0), g.nv - 1);
+    ft.Mx[i][j] = h * vv1<K>(T.m1, g.n, xi, xj);
+    ft.Kx[i][j] = vv1<K>(T.k1, g.n, xi, xj) / h;
+    ft.My[i][j] = h * vv1<K>(T.m1, g.n, yi, yj);
+    ft.Ky[i][j] = vv1<K>(T.k1, g.n, yi, yj) / h;
   }
-  if (si.field == 2 && sj.field == 2) return 0.0;
-  // velocity component c at (vx, vy) against pressure node (px, py): int chi d_c phi
-  const Slot& sv = si.field < 2 ? si : sj;
-  const Slot& sp = si.field < 2 ? sj : si;
-  double gval;
-  if (sv.field == 0)
-    gval = pv1<K>(T.d1, n, sp.gx, sv.gx) * h * pv1<K>(T.c1, n, sp.gy, sv.gy);
-  else
-    gval = h * pv1<K>(T.c1, n, sp.gx, sv.gx) * pv1<K>(T.d1, n, sp.gy, sv.gy);
-  return dt * T.Wt[a][b] * gval;
+  for (int e = threadIdx.x; e < TB::NPT * TB::NVG; e += nth) {
+    const int p = e / TB::NVG, v = e % TB::NVG;
+    const int pxg = min(max(px0 + p, 0), g.np - 1), pyg = min(max(py0 + p, 0), g.np - 1);
+    const int vxg = min(max(vx0 + v, 0), g.nv - 1), vyg = min(max(vy0 + v, 0), g.nv - 1);
+    ft.Dx[p][v] = pv1<K>(T.d1, g.n, pxg, vxg);
+    ft.Cx[p][v] = h * pv1<K>(T.c1, g.n, pxg, vxg);
+    ft.Dy[p][v] = pv1<K>(T.d1, g.n, pyg, vyg);
+    ft.Cy[p][v] = h * pv1<K>(T.c1, g.n, pyg, vyg);
+  }
+  for (int s = threadIdx.x; s < pd::MS; s += nth) {
+    const Slot sl = decode_slot(g, bs, blk, s);
+    if (sl.sp < 0) {
+      ft.sf[s] = -1;
+      ft.sx[s] = ft.sy[s] = 0;
+    } else if (sl.field < 2) {
+      ft.sf[s] = (signed char)sl.field;
+      ft.sx[s] = (signed char)(sl.gx - vx0);
+      ft.sy[s] = (signed char)(sl.gy - vy0);
+    } else {
+      ft.sf[s] = 2;
+      ft.sx[s] = (signed char)(sl.gx - px0);
+      ft.sy[s] = (signed char)(sl.gy - py0);
+    }
+  }
+}
+
+// M (+)= constant part of temporal sub-block (a, b); padding rows/columns get the identity on a == b.
+template <int K, int Q, typename CT, int LD, int NTH>
+__device__ void assemble_const(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const FactorTables<K>& ft,
+                               CT* M, int a, int b, bool add) {
+  constexpr int MS = PD<K>::MS;
+  const double kt = T.Kt[a][b], vis = g.dt * ph.nu * T.Wt[a][b], dw = g.dt * T.Wt[a][b];
+  for (int e = threadIdx.x; e < MS * MS; e += NTH) {
+    const int i = e / MS, j = e - (e / MS) * MS;
+    const int fi = ft.sf[i], fj = ft.sf[j];
+    double v = 0.0;
+    if (fi < 0 || fj < 0) {
+      v = (i == j && a == b) ? 1.0 : 0.0;
+    } else if (fi < 2 && fj < 2) {
+      if (fi == fj) {
+        const int ix = ft.sx[i], iy = ft.sy[i], jx = ft.sx[j], jy = ft.sy[j];
+        const double mx = ft.Mx[ix][jx], my = ft.My[iy][jy];
+        v = kt * mx * my + vis * (ft.Kx[ix][jx] * my + mx * ft.Ky[iy][jy]);
+      }
+    } else if (fi < 2 || fj < 2) {
+      const int sv = fi < 2 ? i : j, sq = fi < 2 ? j : i;
+      const int c = ft.sf[sv];
+      const int vx = ft.sx[sv], vy = ft.sy[sv], qx = ft.sx[sq], qy = ft.sy[sq];
+      v = dw * (c == 0 ? ft.Dx[qx][vx] * ft.Cy[qy][vy] : ft.Cx[qx][vx] * ft.Dy[qy][vy]);
+    }
+    if (add)
+      M[i * LD + j] += (CT)v;
+    else
+      M[i * LD + j] = (CT)v;
+  }
+}
+
+// M += dt conv sum_e T3[a,b,e] Ce_e, cell by cell (one cell per pass: no write conflicts).
+template <int K, int Q, typename CT, int LD, int NTH>
+__device__ void assemble_conv(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const BlockSet& bs,
+                              const double* __restrict__ Ce, int blk, int slab, const FactorTables<K>& ft, CT* M,
+                              int a, int b) {
+  using pd = PD<K>;
+  constexpr int NT = Q + 1, NVL = pd::NVL, NVE = pd::NVE, NVG = pd::NVG;
+  constexpr int MS = pd::MS;
+  int vx0, vy0, px0, py0;
+  block_origin(g, bs, blk, vx0, vy0, px0, py0);
+  const int nvg = bs.nvg;
+  // cells whose closure meets the slot grid
+  const int cx0 = max(0, (vx0 - 1) / (K + 1) - (vx0 - 1 < 0 ? 1 : 0)), cx1 = min(g.n - 1, (vx0 + nvg - 1) / (K + 1));
+  const int cy0 = max(0, (vy0 - 1) / (K + 1) - (vy0 - 1 < 0 ? 1 : 0)), cy1 = min(g.n - 1, (vy0 + nvg - 1) / (K + 1));
+  const double sc = g.dt * ph.conv;
+  double w[NT];
+#pragma unroll
+  for (int e = 0; e < NT; ++e) w[e] = sc * T.T3[a][b][e];
+  for (int cy = cy0; cy <= cy1; ++cy)
+    for (int cx = cx0; cx <= cx1; ++cx) {
+      const double* ce = Ce + ((int64_t)slab * g.ncells() + cy * g.n + cx) * (NT * 4 * NVE * NVE);
+      for (int e = threadIdx.x; e < 4 * NVE * NVE; e += NTH) {
+        const int cd = e / (NVE * NVE), r = e % (NVE * NVE);
+        const int li = r / NVE, lj = r % NVE;
+        const int ix = cx * (K + 1) + li % NVL - vx0, iy = cy * (K + 1) + li / NVL - vy0;
+        const int jx = cx * (K + 1) + lj % NVL - vx0, jy = cy * (K + 1) + lj / NVL - vy0;
+        if (ix < 0 || ix >= nvg || iy < 0 || iy >= nvg || jx < 0 || jx >= nvg || jy < 0 || jy >= nvg) continue;
+        const int si = (cd >> 1) * nvg * nvg + iy * nvg + ix, sj = (cd & 1) * nvg * nvg + jy * nvg + jx;
+        if (ft.sf[si] < 0 || ft.sf[sj] < 0) continue;
+        double v = 0.0;
+#pragma unroll
+        for (int ee = 0; ee < NT; ++ee) v += w[ee] * ce[(int64_t)ee * 4 * NVE * NVE + e];
+        M[si * LD + sj] += (CT)v;
+      }
+      __syncthreads();
+    }
+  (void)MS;
+  (void)NVG;
 }
 
 // In-place Gauss-Jordan inversion with partial pivoting (largest |.|, lowest
 // row on ties) of the MS x MS row-major matrix A (leading dimension LD) in
 // shared memory.  Returns false (to all threads) if a zero pivot was met.
-template <int MS, int LD, int NTH>
-__device__ bool gauss_jordan(double* A, double* colbuf, int* perm, int* sh) {
+template <int MS, int LD, int NTH, typename CT>
+__device__ bool gauss_jordan(CT* A, CT* colbuf, int* perm, int* sh) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  bool ok = true;
 #pragma unroll 1
   for (int p = 0; p < MS; ++p) {
     if (warp == 0) {
-      double best = -1.0;
+      CT best = -1;
       int bi = MS;
       for (int i = p + lane; i < MS; i += 32) {
-        const double v = fabs(A[i * LD + p]);
+        const CT v = fabs(A[i * LD + p]);
         if (v > best) { best = v; bi = i; }
       }
       for (int off = 16; off > 0; off >>= 1) {
-        const double ob = __shfl_down_sync(0xffffffffu, best, off);
+        const CT ob = __shfl_down_sync(0xffffffffu, best, off);
         const int oi = __shfl_down_sync(0xffffffffu, bi, off);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
       if (lane == 0) {
         sh[0] = bi;
         perm[p] = bi;
-        if (!(best > 0.0)) sh[1] = 1;
+        if (!(best > 0)) sh[1] = 1;
       }
     }
     __syncthreads();
     const int r = sh[0];
     if (r != p)
       for (int j = tid; j < MS; j += NTH) {
-        const double t = A[p * LD + j];
+        const CT t = A[p * LD + j];
         A[p * LD + j] = A[r * LD + j];
         A[r * LD + j] = t;
       }
     __syncthreads();
-    const double inv = 1.0 / A[p * LD + p];
+    const CT inv = CT(1) / A[p * LD + p];
     for (int i = tid; i < MS; i += NTH) colbuf[i] = A[i * LD + p];
     __syncthreads();
     for (int j = tid; j < MS; j += NTH) A[p * LD + j] = (j == p) ? inv : A[p * LD + j] * inv;
@@ -211,127 +303,100 @@ __device__ bool gauss_jordan(double* A, double* colbuf, int* perm, int* sh) {
     const int r = perm[p];
     if (r != p)
       for (int i = tid; i < MS; i += NTH) {
-        const double t = A[i * LD + p];
+        const CT t = A[i * LD + p];
         A[i * LD + p] = A[i * LD + r];
         A[i * LD + r] = t;
       }
     __syncthreads();
   }
-  ok = sh[1] == 0;
-  return ok;
+  return sh[1] == 0;
 }
 
-template <int MS, int LD, int NTH, typename FT>
-__device__ void store_colmajor(const double* A, FT* dst) {
+template <int MS, int LD, int NTH, typename CT>
+__device__ void store_colmajor(const CT* A, CT* dst) {
   for (int e = threadIdx.x; e < MS * MS; e += NTH) {
     const int j = e / MS, i = e - j * MS;
-    dst[e] = (FT)A[i * LD + j];
+    dst[e] = A[i * LD + j];
   }
 }
 
-template <int K, int Q>
-__device__ void assemble_block(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* Ce, int slab,
-                               const Slot* slots, double* M, int a, int b, int nth) {
-  using pd = PD<K>;
-  for (int e = threadIdx.x; e < pd::MS * pd::MS; e += nth) {
-    const int i = e / pd::MS, j = e - i * pd::MS;
-    double v;
-    if (slots[i].sp < 0 || slots[j].sp < 0)
-      v = (i == j && a == b) ? 1.0 : 0.0;
-    else
-      v = jac_entry<K, Q>(g, T, ph, Ce, slab, slots[i], slots[j], a, b);
-    M[i * pd::LD + j] = v;
+// C = sign * A B (+ C if accumulate) for MS x MS shared-memory matrices, result written over B.
+template <int MS, int LD, int NTH, typename CT>
+__device__ void gemm_into_b(const CT* A, CT* B, CT sign) {
+  constexpr int NE = (MS * MS + NTH - 1) / NTH;
+  CT acc[NE];
+  int ioff[NE], jcol[NE];
+#pragma unroll
+  for (int t = 0; t < NE; ++t) {
+    const int e = threadIdx.x + t * NTH;
+    const int i = e < MS * MS ? e / MS : 0;
+    ioff[t] = i * LD;
+    jcol[t] = e < MS * MS ? e - i * MS : 0;
+    acc[t] = 0;
   }
+#pragma unroll 1
+  for (int l = 0; l < MS; ++l)
+#pragma unroll
+    for (int t = 0; t < NE; ++t) acc[t] = fma(A[ioff[t] + l], B[l * LD + jcol[t]], acc[t]);
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < NE; ++t)
+    if (threadIdx.x + t * NTH < MS * MS) B[ioff[t] + jcol[t]] = sign * acc[t];
+  __syncthreads();
 }
 
-template <int K, int Q>
-__device__ void add_block(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* Ce, int slab,
-                          const Slot* slots, double* M, int a, int b, int nth) {
-  using pd = PD<K>;
-  for (int e = threadIdx.x; e < pd::MS * pd::MS; e += nth) {
-    const int i = e / pd::MS, j = e - i * pd::MS;
-    double v;
-    if (slots[i].sp < 0 || slots[j].sp < 0)
-      v = (i == j && a == b) ? 1.0 : 0.0;
-    else
-      v = jac_entry<K, Q>(g, T, ph, Ce, slab, slots[i], slots[j], a, b);
-    M[i * pd::LD + j] += v;
-  }
-}
-
-template <int K, int Q, typename FT, int NTH>
-__global__ void __launch_bounds__(NTH)
+template <int K, int Q, typename CT, int NTH>
+__global__ void __launch_bounds__(NTH, 1)
 block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const double* __restrict__ Ce,
-                    FT* __restrict__ factors, int* __restrict__ status) {
+                    CT* __restrict__ factors, int* __restrict__ status) {
   using pd = PD<K>;
   constexpr int MS = pd::MS, LD = pd::LD;
-  constexpr int NE = (MS * MS + NTH - 1) / NTH;
+  constexpr int G = 16 / (int)sizeof(CT);
+  constexpr int64_t BLK = (MS * MS + G - 1) / G * G;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* M1 = reinterpret_cast<double*>(smem_raw);
-  double* M2 = M1 + MS * LD;
-  double* colbuf = M2 + (Q == 1 ? MS * LD : 0);
-  Slot* slots = reinterpret_cast<Slot*>(colbuf + MS);
-  int* perm = reinterpret_cast<int*>(slots + MS);
+  CT* M1 = reinterpret_cast<CT*>(smem_raw);
+  CT* M2 = M1 + MS * LD;
+  CT* colbuf = M2 + (Q == 1 ? MS * LD : 0);
+  FactorTables<K>& ft = *reinterpret_cast<FactorTables<K>*>(
+      smem_raw + ((sizeof(CT) * ((Q == 1 ? 2 : 1) * MS * LD + MS) + 15) / 16) * 16);
+  int* perm = reinterpret_cast<int*>(&ft + 1);
   int* sh = perm + MS;
   const int blk = blockIdx.x, slab = blockIdx.y;
-  for (int s = threadIdx.x; s < MS; s += NTH) slots[s] = decode_slot(g, bs, blk, s);
+  build_factor_tables<K>(g, T, bs, blk, ft, NTH);
   if (threadIdx.x == 0) { sh[0] = 0; sh[1] = 0; }
   __syncthreads();
-  constexpr int64_t BLK = (MS * MS + 16 / (int)sizeof(FT) - 1) / (16 / (int)sizeof(FT)) * (16 / (int)sizeof(FT));
-  FT* F = factors + ((int64_t)blk * g.N + slab) * (Q + 1) * (Q + 1) * BLK;
+  const bool conv = ph.conv != 0.0;
+  CT* F = factors + ((int64_t)blk * g.N + slab) * (Q + 1) * (Q + 1) * BLK;
   bool ok;
   if constexpr (Q == 0) {
-    assemble_block<K, Q>(g, T, ph, Ce, slab, slots, M1, 0, 0, NTH);
+    assemble_const<K, Q, CT, LD, NTH>(g, T, ph, ft, M1, 0, 0, false);
     __syncthreads();
+    if (conv) assemble_conv<K, Q, CT, LD, NTH>(g, T, ph, bs, Ce, blk, slab, ft, M1, 0, 0);
     ok = gauss_jordan<MS, LD, NTH>(M1, colbuf, perm, sh);
     store_colmajor<MS, LD, NTH>(M1, F);
   } else {
     // A00^{-1}
-    assemble_block<K, Q>(g, T, ph, Ce, slab, slots, M1, 0, 0, NTH);
+    assemble_const<K, Q, CT, LD, NTH>(g, T, ph, ft, M1, 0, 0, false);
     __syncthreads();
+    if (conv) assemble_conv<K, Q, CT, LD, NTH>(g, T, ph, bs, Ce, blk, slab, ft, M1, 0, 0);
     ok = gauss_jordan<MS, LD, NTH>(M1, colbuf, perm, sh);
     store_colmajor<MS, LD, NTH>(M1, F);
     // X = A00^{-1} A01
-    assemble_block<K, Q>(g, T, ph, Ce, slab, slots, M2, 0, 1, NTH);
+    assemble_const<K, Q, CT, LD, NTH>(g, T, ph, ft, M2, 0, 1, false);
     __syncthreads();
-    double acc[NE];
-    int ioff[NE], jcol[NE];
-#pragma unroll
-    for (int t = 0; t < NE; ++t) {
-      const int e = threadIdx.x + t * NTH;
-      const int i = e < MS * MS ? e / MS : 0;
-      ioff[t] = i * LD;
-      jcol[t] = e < MS * MS ? e - i * MS : 0;
-      acc[t] = 0.0;
-    }
-#pragma unroll 1
-    for (int l = 0; l < MS; ++l)
-#pragma unroll
-      for (int t = 0; t < NE; ++t) acc[t] = fma(M1[ioff[t] + l], M2[l * LD + jcol[t]], acc[t]);
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < NE; ++t)
-      if (threadIdx.x + t * NTH < MS * MS) M2[ioff[t] + jcol[t]] = acc[t];
-    __syncthreads();
+    if (conv) assemble_conv<K, Q, CT, LD, NTH>(g, T, ph, bs, Ce, blk, slab, ft, M2, 0, 1);
+    gemm_into_b<MS, LD, NTH, CT>(M1, M2, CT(1));
     store_colmajor<MS, LD, NTH>(M2, F + 3 * BLK);
     // A10
-    assemble_block<K, Q>(g, T, ph, Ce, slab, slots, M1, 1, 0, NTH);
+    assemble_const<K, Q, CT, LD, NTH>(g, T, ph, ft, M1, 1, 0, false);
     __syncthreads();
+    if (conv) assemble_conv<K, Q, CT, LD, NTH>(g, T, ph, bs, Ce, blk, slab, ft, M1, 1, 0);
     store_colmajor<MS, LD, NTH>(M1, F + 1 * BLK);
-    // S = A11 - A10 X: the product in registers, then A11 added entry by entry
-#pragma unroll
-    for (int t = 0; t < NE; ++t) acc[t] = 0.0;
-#pragma unroll 1
-    for (int l = 0; l < MS; ++l)
-#pragma unroll
-      for (int t = 0; t < NE; ++t) acc[t] = fma(-M1[ioff[t] + l], M2[l * LD + jcol[t]], acc[t]);
+    // S = A11 - A10 X
+    gemm_into_b<MS, LD, NTH, CT>(M1, M2, CT(-1));
+    assemble_const<K, Q, CT, LD, NTH>(g, T, ph, ft, M2, 1, 1, true);
     __syncthreads();
-#pragma unroll
-    for (int t = 0; t < NE; ++t)
-      if (threadIdx.x + t * NTH < MS * MS) M2[ioff[t] + jcol[t]] = acc[t];
-    __syncthreads();
-    add_block<K, Q>(g, T, ph, Ce, slab, slots, M2, 1, 1, NTH);
-    __syncthreads();
+    if (conv) assemble_conv<K, Q, CT, LD, NTH>(g, T, ph, bs, Ce, blk, slab, ft, M2, 1, 1);
     ok = gauss_jordan<MS, LD, NTH>(M2, colbuf, perm, sh) && ok;
     store_colmajor<MS, LD, NTH>(M2, F + 2 * BLK);
   }
@@ -661,14 +726,14 @@ __global__ void scatter_kernel(LevelGeom g, const double* __restrict__ Yp, doubl
   y[idx] = acc;
 }
 
-template <int K, int Q, typename FT>
+template <int K, int Q, typename CT>
 void run_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const BlockSet& bs, const double* Ce,
-                FT* factors, int* status, cudaStream_t s) {
+                CT* factors, int* status, cudaStream_t s) {
   using pd = PD<K>;
   constexpr int NTH = K == 1 ? 256 : 512;
-  const size_t smem = sizeof(double) * ((Q == 1 ? 2 : 1) * pd::MS * pd::LD + pd::MS) + sizeof(Slot) * pd::MS +
-                      sizeof(int) * (pd::MS + 2);
-  auto kern = block_factor_kernel<K, Q, FT, NTH>;
+  const size_t mats = ((sizeof(CT) * ((Q == 1 ? 2 : 1) * pd::MS * pd::LD + pd::MS) + 15) / 16) * 16;
+  const size_t smem = mats + sizeof(FactorTables<K>) + sizeof(int) * (pd::MS + 2);
+  auto kern = block_factor_kernel<K, Q, CT, NTH>;
   WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int nblk = bs.kind == 0 ? g.npatch() : 1;
   kern<<<dim3(nblk, g.N), NTH, smem, s>>>(g, T, ph, bs, Ce, factors, status);
