@@ -321,42 +321,50 @@ class Discretisation:
 
     def residual(self, U):
         """Nonlinear space-time residual F(U) of Eq. nsfem (Dirichlet rows: U - g)."""
+        F = np.zeros(self.ndofs)
+        for n in range(self.N):
+            F[self.block(n, 0):self.block(n + 1, 0)] = self.residual_slab(U, n)
+        return F
+
+    def residual_slab(self, U, n):
+        """The rows of F(U) that belong to slab n (they read slabs n and n-1 of U)."""
         tm, dt, nu, cv = self.tm, self.dt, self.pb.nu, self.pb.conv
         nv2 = self.nv ** 2
-        F = np.zeros(self.ndofs)
-        u_prev = self.initial_velocity()
-        for n in range(self.N):
-            Un = self._slab(U, n)
-            # velocity values/gradients at quadrature points for each temporal DoF
-            fields = [[self._vel_at_q(Un[b, c * nv2:(c + 1) * nv2]) for c in range(2)]
-                      for b in range(self.nt)]
-            Fn = np.zeros((self.nt, self.S))
-            for a in range(self.nt):
-                r = np.zeros(self.S)
-                for b in range(self.nt):
-                    r += tm.Kt[a, b] * (self.Mv @ Un[b])
-                    r += dt * tm.Wt[a, b] * (nu * (self.Kv @ Un[b]) + self.G @ Un[b])
-                r -= tm.tau0[a] * (self.Mv @ u_prev)
-                for c in range(2):
-                    integrand = np.zeros_like(self.qpx)
-                    for b in range(self.nt):
-                        for e in range(self.nt):
-                            ub = fields[b]
-                            ue = fields[e][c]
-                            integrand += tm.T3[a, b, e] * (ub[0][0] * ue[1] + ub[1][0] * ue[2])
-                    loc = np.einsum("cq,iq,q->ci", integrand, self.Vv, self.wq2)
-                    vec = np.zeros(nv2)
-                    np.add.at(vec, self.cell_vnodes.ravel(), loc.ravel())
-                    r[c * nv2:(c + 1) * nv2] += dt * cv * vec
-                Fn[a] = r
-            Fn -= self.forcing_vector(n)
-            F[self.block(n, 0):self.block(n + 1, 0)] = Fn.ravel()
-            u_prev = Un[self.nt - 1].copy()
+        if n == 0:
+            u_prev = self.initial_velocity()
+        else:
+            u_prev = self._slab(U, n - 1)[self.nt - 1].copy()
             u_prev[self.off_p:] = 0.0
-        mask = self.dirichlet_mask()
-        g = self.boundary_values()
-        F[mask] = U[mask] - g[mask]
-        return F
+        Un = self._slab(U, n)
+        # velocity values/gradients at quadrature points for each temporal DoF
+        fields = [[self._vel_at_q(Un[b, c * nv2:(c + 1) * nv2]) for c in range(2)]
+                  for b in range(self.nt)]
+        Fn = np.zeros((self.nt, self.S))
+        for a in range(self.nt):
+            r = np.zeros(self.S)
+            for b in range(self.nt):
+                r += tm.Kt[a, b] * (self.Mv @ Un[b])
+                r += dt * tm.Wt[a, b] * (nu * (self.Kv @ Un[b]) + self.G @ Un[b])
+            r -= tm.tau0[a] * (self.Mv @ u_prev)
+            for c in range(2):
+                integrand = np.zeros_like(self.qpx)
+                for b in range(self.nt):
+                    for e in range(self.nt):
+                        ub = fields[b]
+                        ue = fields[e][c]
+                        integrand += tm.T3[a, b, e] * (ub[0][0] * ue[1] + ub[1][0] * ue[2])
+                loc = np.einsum("cq,iq,q->ci", integrand, self.Vv, self.wq2)
+                vec = np.zeros(nv2)
+                np.add.at(vec, self.cell_vnodes.ravel(), loc.ravel())
+                r[c * nv2:(c + 1) * nv2] += dt * cv * vec
+            Fn[a] = r
+        Fn -= self.forcing_vector(n)
+        Fn = Fn.ravel()
+        mask = np.tile(self.spatial_dirichlet(), self.nt)
+        g = self.boundary_values()[self.block(n, 0):self.block(n + 1, 0)]
+        Un = Un.ravel()
+        Fn[mask] = Un[mask] - g[mask]
+        return Fn
 
     def slab_blocks(self, W, slab):
         """(diagonal block, subdiagonal block) of J(W) for ``slab`` before the
@@ -387,6 +395,16 @@ class Discretisation:
         J = (Z @ J @ Z + sp.diags(mask.astype(np.float64))).tocsr()
         J.eliminate_zeros()
         return J
+
+    def jacobian_slab(self, W, n):
+        """(diagonal, subdiagonal) blocks of the rows of J(W) that belong to slab n,
+        with the same Dirichlet elimination as ``jacobian``."""
+        D, L = self.slab_blocks(W, n)
+        m = np.tile(self.spatial_dirichlet(), self.nt)
+        Z = sp.diags((~m).astype(np.float64))
+        D = (Z @ D @ Z + sp.diags(m.astype(np.float64))).tocsr()
+        L = (Z @ L @ Z).tocsr()
+        return D, L
 
     def initial_guess(self):
         """Boundary lift at every temporal node, zero interior, zero pressure."""

@@ -35,6 +35,12 @@ def interpolation_1d(n_coarse, p):
 
 def prolongation(fine, coarse):
     """Sparse global P from the coarse level's vectors to the fine level's."""
+    Ph = spatial_prolongation(fine, coarse)
+    return sp.kron(sp.identity(fine.N * fine.nt), Ph).tocsr()
+
+
+def spatial_prolongation(fine, coarse):
+    """P_h = blockdiag(P_u, P_u, P_phi) acting on one temporal block, Dirichlet rows and columns zero."""
     assert fine.n == 2 * coarse.n and fine.k == coarse.k and fine.q == coarse.q and fine.N == coarse.N
     k = fine.k
     P1v = sp.csr_matrix(interpolation_1d(coarse.n, k + 1))
@@ -46,7 +52,7 @@ def prolongation(fine, coarse):
     zc = sp.diags((~coarse.spatial_dirichlet()).astype(np.float64))
     Ph = (zf @ Ph @ zc).tocsr()
     Ph.eliminate_zeros()
-    return sp.kron(sp.identity(fine.N * fine.nt), Ph).tocsr()
+    return Ph
 
 
 def injection(fine, coarse, W):
