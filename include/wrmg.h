@@ -200,6 +200,29 @@ int wr_profile(wr_ctx *c, int enable);
  * number of launches recorded; synchronises the stream. */
 int wr_profile_smoother(wr_ctx *c, int level, double *total_ms, int *launches);
 
+/* y = J(W) x on the n_fine mesh that *p describes, like wr_apply_jacobian on
+ * the finest level, but with no context and no device allocation: for callers
+ * that cannot call cudaMalloc (an application that owns all device memory
+ * through its own pool, or a latency-critical loop that must not pay for the
+ * allocator's implicit synchronisation).  The paper has no counterpart; this
+ * is a service of the library.
+ *   W, x, y: caller-owned device pointers, canonical layout, FP64, length
+ *   n_slabs (q+1) (2 nv^2 + np^2); x and y must not alias.  Only n_fine, k, q,
+ *   n_slabs, T, nu and conv of *p are read.  Work is enqueued on cuda_stream.
+ * Scratch: a fixed 64 MiB array of this library's static device memory (8 Mi
+ *   doubles), held by every GPU that loads the library until the process exits.
+ *   Problems that need more, i.e. n_slabs n_fine^2 (q+1) (2 (k+2)^2 + (k+1)^2)
+ *   > 8 Mi, are rejected with WR_ERR_ARG before any work is enqueued (other
+ *   WR_ERR_ARG causes: null or aliased pointers, unsupported k or q).
+ * The first call on a device looks up the array's device address on that device
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the array: calls that overlap on the GPU (other streams,
+ *   other threads) race and must be serialised by the caller.  The array keeps
+ *   the last call's contents; each call writes every entry it reads first, so
+ *   nothing needs clearing.
+ * Returns WR_OK, WR_ERR_ARG, or WR_ERR_CUDA (launch failure). */
+int wr_apply_jacobian_static(const wr_problem *p, const double *W, const double *x, double *y, void *cuda_stream);
+
 /* FP64 FMA throughput of this GPU, measured by a register-only kernel
  * (TFLOP/s); the denominator for FP64-ALU-bound kernels. */
 int wr_measure_fp64_tflops(void *cuda_stream, double *out);

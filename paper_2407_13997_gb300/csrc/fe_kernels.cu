@@ -19,6 +19,7 @@
 // with the convection term (U_b.grad) U_{c,e} for F and
 // (W_b.grad) x_{c,e} + (x_b.grad) W_{c,e} for J.
 #include <cmath>
+#include <mutex>
 
 #include "wrmg_internal.h"
 
@@ -536,4 +537,66 @@ void launch_inject(const LevelGeom& gf, const LevelGeom& gc, const double* Wf, d
   const int threads = 256;
   inject_kernel<<<(unsigned)((gc.ndofs + threads - 1) / threads), threads, 0, s>>>(gf, gc, Wf, Wc);
   WR_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------- J(W) x without device allocation
+// Some callers cannot call cudaMalloc: an application that owns every byte of
+// device memory through its own pool, or a latency-critical loop that must not
+// pay for the allocator's implicit device synchronisation and its failure modes.
+// wr_apply_jacobian_static serves them: it needs no context, and its only
+// scratch (the per-element contributions that the assembly kernel sums) lives
+// in the fixed file-scope array below, which every GPU that loads this library
+// holds until the process exits.
+static constexpr int64_t kStaticScratchDoubles = 8ll * 1024 * 1024;  // 64 MiB
+static __device__ __align__(256) double g_static_elem_scratch[kStaticScratchDoubles];
+
+namespace {
+constexpr int kMaxDevices = 64;
+double* g_static_scratch_ptr[kMaxDevices] = {};
+std::mutex g_static_scratch_mutex;
+
+// Device address of the static scratch on the current device (set up once per device).
+cudaError_t static_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_scratch_mutex);
+  if (!g_static_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_elem_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_scratch_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_static_scratch_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" int wr_apply_jacobian_static(const wr_problem* p, const double* W, const double* x, double* y,
+                                        void* cuda_stream) {
+  if (!p || !W || !x || !y || x == y) return WR_ERR_ARG;
+  if ((p->k != 1 && p->k != 2) || (p->q != 0 && p->q != 1) || p->n_fine < 1 || p->n_slabs < 1 || !(p->T > 0.0))
+    return WR_ERR_ARG;
+  const int64_t nvl = p->k + 2, npl = p->k + 1;
+  const int64_t elem = (p->q + 1) * (2 * nvl * nvl + npl * npl);
+  const int64_t need = (int64_t)p->n_slabs * p->n_fine * p->n_fine * elem;
+  if (need > kStaticScratchDoubles) return WR_ERR_ARG;  // larger than the static scratch
+  try {
+    double* scratch = nullptr;
+    if (static_scratch(&scratch) != cudaSuccess) return WR_ERR_CUDA;
+    const LevelGeom g = make_geom(p->n_fine, p->k, p->q, p->n_slabs, p->T);
+    const FeTables T = build_tables(p->k, p->q);
+    PhysParams ph = {};
+    ph.kind = p->kind;
+    ph.steady = p->steady;
+    ph.nu = p->nu;
+    ph.conv = p->conv;
+    ph.T = p->T;
+    ph.n_modes = 0;  // the Jacobian does not read the forcing
+    dispatch_element<true>(g, T, ph, W, x, y, scratch, static_cast<cudaStream_t>(cuda_stream));
+    return WR_OK;
+  } catch (const WrError& e) {
+    return e.code;
+  }
 }

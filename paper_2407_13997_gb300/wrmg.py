@@ -85,6 +85,7 @@ _SIGS = {
     "wr_solve_host": (ctypes.c_int, [_P, _P, ctypes.POINTER(Stats)]),
     "wr_measure_fp64_tflops": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "wr_launch_count": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64)]),
+    "wr_apply_jacobian_static": (ctypes.c_int, [ctypes.POINTER(Problem), _P, _P, _P, _P]),
     "wr_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "wr_profile_smoother": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int)]),
