@@ -41,10 +41,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--n", type=int, default=64, help="mesh (smaller only for profiling captures)")
     ap.add_argument("--slabs", type=int, default=64, help="time slabs (fewer only for profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", default="cycle", choices=["cycle", "precision"],
+                    help="cycle: the V(2,2) throughput line (default); precision: the FP64/FP32/BF16 "
+                         "solves of the 128x128 Q2/Q1 DG(0) 128-slab workload")
     return ap.parse_args()
 
 
@@ -214,7 +217,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     w = workload(args, seed=rank)
-    prec = wrmg.WR_FP32 if args.precision == "fp32" else wrmg.WR_FP64
+    prec = {"fp64": wrmg.WR_FP64, "fp32": wrmg.WR_FP32, "bf16": wrmg.WR_BF16}[args.precision]
     ctx = wrmg.Context(w, wrmg.default_options(precision=prec))
     stream = torch.cuda.current_stream()
     D = ctx.ndofs()
@@ -282,7 +285,7 @@ def run_ours(args):
         e2e_s = float(t.item())
     assert np.isfinite(xn).all()
 
-    alg_bytes, alg_flops = smoother_algorithmic(ctx, w, 8 if prec == wrmg.WR_FP64 else 4)
+    alg_bytes, alg_flops = smoother_algorithmic(ctx, w, {wrmg.WR_FP64: 8, wrmg.WR_FP32: 4, wrmg.WR_BF16: 2}[prec])
     avg_s = sm_ms / max(sm_n, 1) * 1e-3
     hbm_peak, hbm_src = measured_peaks()
     achieved_tf = alg_flops / avg_s / 1e12
@@ -296,13 +299,15 @@ def run_ours(args):
                         "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src}}
     else:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved_gbs / hbm_peak, "traffic": traffic_record("block_apply_kernel_fp32"),
-                "kernel": "block_apply_kernel (finest level, FP32 factors)", "launches": sm_n,
+                "frac": achieved_gbs / hbm_peak, "traffic": traffic_record(f"block_apply_kernel_{args.precision}"),
+                "kernel": f"block_apply_kernel (finest level, {args.precision} factors)", "launches": sm_n,
                 "avg_ms": avg_s * 1e3, "peak_source": hbm_src}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if prec == wrmg.WR_FP64 else "f32 factors / f64 Krylov",
+            "vs_baseline": None,
+            "dtype": {wrmg.WR_FP64: "f64", wrmg.WR_FP32: "f32 factors+smoother / f64 residual+Krylov",
+                      wrmg.WR_BF16: "bf16 factors, f32 smoother / f64 residual+Krylov"}[prec],
             "data": "synthetic",
             "config": {"workload": w.name, "ndofs": D, "n": w.n_fine, "k": w.k, "q": w.q, "N": w.N,
                        "levels": ctx.num_levels, "factor_storage": args.precision,
@@ -322,10 +327,68 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_precision_form(args):
+    """Precision form on the 128x128 Q2/Q1 DG(0), 128-slab workload: the FP64 solve
+    (run to 1e-11, the reference), then FP32 and BF16 smoother solves to 1e-8 and to
+    1e-10; each reports its final error against the FP64 solution, its FGMRES
+    iterations, its V(2,2) cycle throughput and its solve time."""
+    import numpy as np
+    import torch
+    from paper_2407_13997_gb300 import inputs, wrmg
+    torch.cuda.set_device(0)
+    w = inputs.fourier_128x128_q2q1_dg0(0)
+    if args.n != 64:
+        w.n_fine = args.n
+    if args.slabs != 64:
+        w.N = args.slabs
+    out = {"form": "precision", "workload": w.name if args.n == 64 else f"fourier_q2q1_dg0_n{w.n_fine}_N{w.N}",
+           "ndofs": w.ndofs(), "variants": {}}
+    ref = None
+    for name, prec, rtol in [("fp64", wrmg.WR_FP64, 1e-11), ("fp32", wrmg.WR_FP32, 1e-8), ("fp32", wrmg.WR_FP32, 1e-10),
+                             ("bf16", wrmg.WR_BF16, 1e-8), ("bf16", wrmg.WR_BF16, 1e-10)]:
+        ctx = wrmg.Context(w, wrmg.default_options(precision=prec, newton_rtol=rtol))
+        U = ctx.vector()
+        ctx.initial_guess(U)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = ctx.solve(U)
+        torch.cuda.synchronize()
+        solve_s = time.perf_counter() - t0
+        # cycle throughput about the converged iterate
+        F = ctx.vector()
+        ctx.residual(U, F)
+        x = ctx.vector()
+        for _ in range(2):
+            ctx.vcycle(-F, x)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            ctx.vcycle(-F, x)
+        e1.record()
+        torch.cuda.synchronize()
+        cyc_ms = e0.elapsed_time(e1) / 5
+        u = U.cpu().numpy()
+        rec = {"newton": st["newton_its"], "fgmres": st["gmres"], "fgmres_total": sum(st["gmres"]),
+               "final_rel_residual": st["residuals"][-1] / st["residuals"][0], "solve_s": solve_s,
+               "setup_s": st["setup_ms"] / 1e3, "cycle_ms": cyc_ms, "dof_per_s_per_cycle": w.ndofs() / cyc_ms * 1e3,
+               "device_bytes": ctx.device_bytes(), "rtol": rtol}
+        if ref is None:
+            ref = u
+        else:
+            rec["rel_error_vs_fp64"] = float(np.abs(u - ref).max() / np.abs(ref).max())
+        out["variants"][f"{name}_rtol{rtol:g}"] = rec
+        ctx.close()
+        del U, F, x
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.form == "precision":
+        run_precision_form(args)
     else:
         run_ours(args)
 

@@ -64,14 +64,15 @@ extern "C" {
 #define WR_FOURIER 2       /* no-slip walls, u(0) = 0, f = sum amp_j curl(sin(mx_j pi x) sin(my_j pi y))     */
 
 /* arithmetic of the stored patch factors and of the smoother (wr_options.precision) */
-#define WR_FP64 0
-#define WR_FP32 1
+#define WR_FP64 0  /* FP64 factors and smoother (the plain method)                        */
+#define WR_FP32 1  /* FP32 factorisation, factors and smoother                              */
+#define WR_BF16 2  /* FP32 factorisation, BF16-stored factors, FP32 smoother arithmetic      */
 
 typedef struct wr_ctx wr_ctx;
 
 typedef struct {
-    int n_fine;     /* cells per direction on the finest level (power of two times n_coarse) */
-    int n_coarse;   /* cells per direction on the direct-solve level; must be 2              */
+    int n_fine;     /* cells per direction on the finest level (n_coarse times a power of 2) */
+    int n_coarse;   /* cells per direction on the direct-solve level: 2, or 3 when k = 1     */
     int k;          /* Taylor-Hood order: velocity Q_{k+1}, pressure Q_k; k = 1 or 2          */
     int q;          /* DG(q) in time; q = 0 or 1                                             */
     int n_slabs;    /* N time slabs of width T / N                                           */
@@ -84,7 +85,7 @@ typedef struct {
 } wr_problem;
 
 typedef struct {
-    int precision;          /* WR_FP64 (default) or WR_FP32 factors and smoother                */
+    int precision;          /* WR_FP64 (default), WR_FP32 or WR_BF16 factors and smoother         */
     int cheb_steps;         /* Chebyshev steps per relaxation (2: V(2,2))                        */
     double cheb_lo, cheb_hi;/* Chebyshev interval [cheb_lo lam, cheb_hi lam] (0.25, 1.05)       */
     int eig_steps;          /* Arnoldi steps of the eigen-estimate (10)                         */
@@ -188,6 +189,35 @@ int wr_project_pressure(wr_ctx *c, double *x);
 int wr_solve(wr_ctx *c, double *U_inout, wr_stats *stats);
 /* The same with a HOST U (copied in and out). */
 int wr_solve_host(wr_ctx *c, double *U_host, wr_stats *stats);
+
+/* ------------------------------------------------------------------ batching
+ * A wr_batch holds many independent space-time solves (uneven meshes, slab
+ * counts, viscosities and forcings; one k and one q for the whole batch) and
+ * advances them in lock step: every stage of the V-cycle is one launch for all
+ * members (the smoother one persistent launch over every member's patches),
+ * Newton and FGMRES keep per-member scalars, and members that converge leave
+ * the active set.  Member vectors are caller-owned device pointers in the
+ * canonical layout of that member's finest level.  The paper solves one
+ * problem at a time; batching is a service of this library. */
+typedef struct wr_batch wr_batch;
+int wr_batch_create(wr_batch **out, int n, const wr_problem *ps, const wr_options *o, void *cuda_stream);
+int wr_batch_destroy(wr_batch *b);
+const char *wr_batch_last_error(const wr_batch *b);
+int wr_batch_ndofs(const wr_batch *b, int member, int64_t *out);
+int wr_batch_device_bytes(const wr_batch *b, int64_t *out);
+/* U[m] = Dirichlet data of member m (like wr_initial_guess). */
+int wr_batch_initial_guess(wr_batch *b, double *const *U);
+/* Linearises every member about W[m] (factors and eigen-estimates). */
+int wr_batch_linearise(wr_batch *b, double *const *W);
+int wr_batch_get_lambda(const wr_batch *b, int member, int level, double *lam);
+/* x[m] = one V(2,2) cycle of member m for right-hand side b[m] (all members at once). */
+int wr_batch_vcycle(wr_batch *b, double *const *bin, double *const *xout);
+/* One V(2,2) cycle of every member on the batch's internal right-hand side
+ * (the last b given to wr_batch_vcycle); for throughput measurements. */
+int wr_batch_vcycle_resident(wr_batch *b);
+/* Newton-FGMRES-WRMG solve of every member from U[m] (in/out); st may be NULL
+ * or an array of n wr_stats.  WR_ERR_NOT_CONVERGED if any member hits newton_maxit. */
+int wr_batch_solve(wr_batch *b, double *const *U, wr_stats *st);
 
 /* Total kernel launches made by this library in this process (all contexts). */
 int wr_launch_count(int64_t *out);

@@ -102,17 +102,14 @@ struct ElemSmem {
 // One warp computes the element contribution of (cell, slab) for F (LIN = false)
 // or J x (LIN = true).  `x` is U for F.
 template <int K, int Q, bool LIN>
-__global__ void __launch_bounds__(32 * kWarps)
-element_kernel(LevelGeom g, FeTables T, PhysParams ph, const double* __restrict__ W,
-               const double* __restrict__ x, double* __restrict__ ye) {
+__device__ __forceinline__ void element_body(const LevelGeom& g, const FeTables& T, const PhysParams& ph,
+                                             const double* __restrict__ W, const double* __restrict__ x,
+                                             double* __restrict__ ye, int cell, int slab) {
   using d = D<K, Q>;
   using SM = ElemSmem<K, Q, LIN>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SM& s = reinterpret_cast<SM*>(smem_raw)[threadIdx.x / 32];
   const int lane = threadIdx.x & 31;
-  const int cell = blockIdx.x * kWarps + threadIdx.x / 32;
-  const int slab = blockIdx.y;
-  if (cell >= g.ncells()) return;
   const int CI = cell % g.n, CJ = cell / g.n;
   const double h = g.h, dt = g.dt;
   const int nv = g.nv, np = g.np, S = g.S;
@@ -298,14 +295,38 @@ element_kernel(LevelGeom g, FeTables T, PhysParams ph, const double* __restrict_
   for (int it = lane; it < d::ELEM; it += 32) dst[it] = s.out[it];
 }
 
+template <int K, int Q, bool LIN>
+__global__ void __launch_bounds__(32 * kWarps)
+element_kernel(LevelGeom g, FeTables T, PhysParams ph, const double* __restrict__ W,
+               const double* __restrict__ x, double* __restrict__ ye) {
+  const int cell = blockIdx.x * kWarps + threadIdx.x / 32;
+  if (cell >= g.ncells()) return;
+  element_body<K, Q, LIN>(g, T, ph, W, x, ye, cell, blockIdx.y);
+}
+
+// Batched: one CTA per (member, group of kWarps cells, slab); x and ye are arenas.
+template <int K, int Q, bool LIN>
+__global__ void __launch_bounds__(32 * kWarps)
+bt_element_kernel(const BatchSeg* __restrict__ segs, int nseg, FeTables T, const double* __restrict__ x,
+                  double* __restrict__ ye) {
+  const int m = batch_find<BU_ELEM>(segs, nseg, blockIdx.x);
+  const LevelGeom g = segs[m].g;
+  const PhysParams ph = segs[m].ph;
+  const int cb = (g.ncells() + kWarps - 1) / kWarps;
+  const int64_t lu = blockIdx.x - segs[m].u_elem;
+  const int slab = (int)(lu / cb);
+  const int cell = (int)(lu % cb) * kWarps + threadIdx.x / 32;
+  if (cell >= g.ncells()) return;
+  element_body<K, Q, LIN>(g, T, ph, segs[m].W, x + segs[m].off, ye + segs[m].off_ye, cell, slab);
+}
+
 // Sums element contributions into the global vector (fixed cell order) and sets
 // the Dirichlet rows: y = x for J, y = U - g for F.
 template <int K, int Q, bool LIN>
-__global__ void assemble_kernel(LevelGeom g, FeTables T, PhysParams ph, const double* __restrict__ ye,
-                                const double* __restrict__ x, double* __restrict__ y) {
+__device__ __forceinline__ void assemble_body(const LevelGeom& g, const FeTables& T, const PhysParams& ph,
+                                              const double* __restrict__ ye, const double* __restrict__ x,
+                                              double* __restrict__ y, int64_t idx) {
   using d = D<K, Q>;
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= g.ndofs) return;
   const int S = g.S, nv = g.nv, np = g.np;
   const int64_t blk = idx / S;
   const int sp = int(idx % S);
@@ -349,9 +370,28 @@ __global__ void assemble_kernel(LevelGeom g, FeTables T, PhysParams ph, const do
   y[idx] = acc;
 }
 
-__global__ void boundary_kernel(LevelGeom g, FeTables T, PhysParams ph, double* __restrict__ U) {
+template <int K, int Q, bool LIN>
+__global__ void assemble_kernel(LevelGeom g, FeTables T, PhysParams ph, const double* __restrict__ ye,
+                                const double* __restrict__ x, double* __restrict__ y) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= g.ndofs) return;
+  assemble_body<K, Q, LIN>(g, T, ph, ye, x, y, idx);
+}
+
+template <int K, int Q, bool LIN>
+__global__ void bt_assemble_kernel(const BatchSeg* __restrict__ segs, int nseg, int64_t dofs, FeTables T,
+                                   const double* __restrict__ ye, const double* __restrict__ x,
+                                   double* __restrict__ y) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= dofs) return;
+  const int m = batch_find<BU_DOF>(segs, nseg, u);
+  const LevelGeom g = segs[m].g;
+  const int64_t off = segs[m].off;
+  assemble_body<K, Q, LIN>(g, T, segs[m].ph, ye + segs[m].off_ye, x + off, y + off, u - segs[m].u_dof);
+}
+
+__device__ __forceinline__ void boundary_body(const LevelGeom& g, const FeTables& T, const PhysParams& ph,
+                                              double* __restrict__ U, int64_t idx) {
   const int S = g.S, nv = g.nv, nv2 = nv * nv;
   const int64_t blk = idx / S;
   const int sp = int(idx % S);
@@ -367,6 +407,21 @@ __global__ void boundary_kernel(LevelGeom g, FeTables T, PhysParams ph, double* 
     }
   }
   U[idx] = v;
+}
+
+__global__ void boundary_kernel(LevelGeom g, FeTables T, PhysParams ph, double* __restrict__ U) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= g.ndofs) return;
+  boundary_body(g, T, ph, U, idx);
+}
+
+__global__ void bt_boundary_kernel(const BatchSeg* __restrict__ segs, int nseg, int64_t dofs, FeTables T,
+                                   double* __restrict__ U) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= dofs) return;
+  const int m = batch_find<BU_DOF>(segs, nseg, u);
+  const LevelGeom g = segs[m].g;
+  boundary_body(g, T, segs[m].ph, U + segs[m].off, u - segs[m].u_dof);
 }
 
 // Element convection matrices about W (per time DoF e of W):
@@ -507,7 +562,49 @@ void run_conv(const LevelGeom& g, const FeTables& T, const double* W, double* Ce
   WR_LAUNCH_CHECK();
 }
 
+template <int K, int Q, bool LIN>
+void run_bt_element(const BatchSeg* segs, int nseg, int64_t units, int64_t dofs, const FeTables& T, const double* x,
+                    double* y, double* ye, cudaStream_t s) {
+  const size_t smem = sizeof(ElemSmem<K, Q, LIN>) * kWarps;
+  auto kern = bt_element_kernel<K, Q, LIN>;
+  WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (units > 0) {
+    kern<<<(unsigned)units, 32 * kWarps, smem, s>>>(segs, nseg, T, x, ye);
+    WR_LAUNCH_CHECK();
+  }
+  if (dofs > 0) {
+    bt_assemble_kernel<K, Q, LIN><<<(unsigned)((dofs + 255) / 256), 256, 0, s>>>(segs, nseg, dofs, T, ye, x, y);
+    WR_LAUNCH_CHECK();
+  }
+}
+
+template <bool LIN>
+void dispatch_bt_element(int k, int q, const BatchSeg* segs, int nseg, int64_t units, int64_t dofs,
+                         const FeTables& T, const double* x, double* y, double* ye, cudaStream_t s) {
+  if (k == 1 && q == 0) run_bt_element<1, 0, LIN>(segs, nseg, units, dofs, T, x, y, ye, s);
+  else if (k == 1 && q == 1) run_bt_element<1, 1, LIN>(segs, nseg, units, dofs, T, x, y, ye, s);
+  else if (k == 2 && q == 0) run_bt_element<2, 0, LIN>(segs, nseg, units, dofs, T, x, y, ye, s);
+  else if (k == 2 && q == 1) run_bt_element<2, 1, LIN>(segs, nseg, units, dofs, T, x, y, ye, s);
+  else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
+}
+
 }  // namespace
+
+void bt_jacobian(int k, int q, const BatchSeg* segs, int nseg, int64_t units, int64_t dofs, const FeTables& T,
+                 const double* x, double* y, double* ye, cudaStream_t s) {
+  dispatch_bt_element<true>(k, q, segs, nseg, units, dofs, T, x, y, ye, s);
+}
+
+void bt_residual(int k, int q, const BatchSeg* segs, int nseg, int64_t units, int64_t dofs, const FeTables& T,
+                 const double* U, double* F, double* ye, cudaStream_t s) {
+  dispatch_bt_element<false>(k, q, segs, nseg, units, dofs, T, U, F, ye, s);
+}
+
+void bt_boundary(const BatchSeg* segs, int nseg, int64_t dofs, const FeTables& T, double* U, cudaStream_t s) {
+  if (dofs <= 0) return;
+  bt_boundary_kernel<<<(unsigned)((dofs + 255) / 256), 256, 0, s>>>(segs, nseg, dofs, T, U);
+  WR_LAUNCH_CHECK();
+}
 
 void launch_residual(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* U, double* F,
                      double* ye, cudaStream_t s) {

@@ -24,15 +24,20 @@
 //     streamed HBM -> shared memory by cp.async.bulk through an mbarrier ring.
 // (d) scatter_kernel: every global DoF pulls the outputs of the patches that
 //     contain it in a fixed order (deterministic weighted additive scatter, w = 1).
+#include <cuda_bf16.h>
+
 #include <cmath>
 
 #include "wrmg_internal.h"
 
 namespace {
 
-template <int K>
+// Slot shape of a block: velocity grid NVG x NVG per component, pressure grid
+// NPG x NPG.  Patches: NVG = 2k+3, NPG = 2k-1; the coarse 2x2 block fits the
+// patch shape; the coarse 3x3 block of Q2/Q1 uses NPG = 4 (5x5 velocity, 66 slots).
+template <int K, int NPGX = 2 * K - 1>
 struct PD {
-  static constexpr int NVG = 2 * K + 3, NPG = 2 * K - 1;
+  static constexpr int NVG = 2 * K + 3, NPG = NPGX;
   static constexpr int NVG2 = NVG * NVG;
   static constexpr int MS = 2 * NVG2 + NPG * NPG;         // 51 (k = 1) or 107 (k = 2)
   static constexpr int LD = (MS % 2) ? MS : MS + 1;       // odd leading dimension in smem
@@ -125,20 +130,21 @@ __device__ __forceinline__ double pv1(const double (*ref)[WR_MAX_NVL], int n, in
 // CT is the arithmetic and storage type: double (plain form) or float
 // (precision form; FP32 runs at 58x the FP64 rate on GB300).
 
-template <int K>
+template <int K, int NPGX = 2 * K - 1>
 struct FactorTables {
-  static constexpr int NVG = 2 * K + 3, NPT = 2 * K + 1;  // slot-grid sizes (pressure: coarse block is larger)
+  static constexpr int NVG = 2 * K + 3;
+  static constexpr int NPT = 2 * K + 1 > NPGX ? 2 * K + 1 : NPGX;  // pressure rows (coarse blocks are larger)
   double Mx[NVG][NVG], Kx[NVG][NVG], My[NVG][NVG], Ky[NVG][NVG];
   double Dx[NPT][NVG], Cx[NPT][NVG], Dy[NPT][NVG], Cy[NPT][NVG];
-  signed char sf[PD<K>::MS];               // slot field 0/1 velocity, 2 pressure, -1 padding
-  signed char sx[PD<K>::MS], sy[PD<K>::MS];  // slot-grid coordinates
+  signed char sf[PD<K, NPGX>::MS];                   // slot field 0/1 velocity, 2 pressure, -1 padding
+  signed char sx[PD<K, NPGX>::MS], sy[PD<K, NPGX>::MS];  // slot-grid coordinates
 };
 
-template <int K>
+template <int K, int NPGX>
 __device__ void build_factor_tables(const LevelGeom& g, const FeTables& T, const BlockSet& bs, int blk,
-                                    FactorTables<K>& ft, int nth) {
-  using pd = PD<K>;
-  using TB = FactorTables<K>;
+                                    FactorTables<K, NPGX>& ft, int nth) {
+  using pd = PD<K, NPGX>;
+  using TB = FactorTables<K, NPGX>;
   int vx0, vy0, px0, py0;
   block_origin(g, bs, blk, vx0, vy0, px0, py0);
   const double h = g.h;
@@ -178,10 +184,10 @@ __device__ void build_factor_tables(const LevelGeom& g, const FeTables& T, const
 }
 
 // M (+)= constant part of temporal sub-block (a, b); padding rows/columns get the identity on a == b.
-template <int K, int Q, typename CT, int LD, int NTH>
-__device__ void assemble_const(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const FactorTables<K>& ft,
-                               CT* M, int a, int b, bool add) {
-  constexpr int MS = PD<K>::MS;
+template <int K, int Q, typename CT, int LD, int NTH, int NPGX>
+__device__ void assemble_const(const LevelGeom& g, const FeTables& T, const PhysParams& ph,
+                               const FactorTables<K, NPGX>& ft, CT* M, int a, int b, bool add) {
+  constexpr int MS = PD<K, NPGX>::MS;
   const double kt = T.Kt[a][b], vis = g.dt * ph.nu * T.Wt[a][b], dw = g.dt * T.Wt[a][b];
   for (int e = threadIdx.x; e < MS * MS; e += NTH) {
     const int i = e / MS, j = e - (e / MS) * MS;
@@ -209,11 +215,11 @@ __device__ void assemble_const(const LevelGeom& g, const FeTables& T, const Phys
 }
 
 // M += dt conv sum_e T3[a,b,e] Ce_e, cell by cell (one cell per pass: no write conflicts).
-template <int K, int Q, typename CT, int LD, int NTH>
+template <int K, int Q, typename CT, int LD, int NTH, int NPGX>
 __device__ void assemble_conv(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const BlockSet& bs,
-                              const double* __restrict__ Ce, int blk, int slab, const FactorTables<K>& ft, CT* M,
-                              int a, int b) {
-  using pd = PD<K>;
+                              const double* __restrict__ Ce, int blk, int slab, const FactorTables<K, NPGX>& ft,
+                              CT* M, int a, int b) {
+  using pd = PD<K, NPGX>;
   constexpr int NT = Q + 1, NVL = pd::NVL, NVE = pd::NVE, NVG = pd::NVG;
   constexpr int MS = pd::MS;
   int vx0, vy0, px0, py0;
@@ -312,11 +318,15 @@ __device__ bool gauss_jordan(CT* A, CT* colbuf, int* perm, int* sh) {
   return sh[1] == 0;
 }
 
-template <int MS, int LD, int NTH, typename CT>
-__device__ void store_colmajor(const CT* A, CT* dst) {
+__device__ __forceinline__ void narrow(double v, double& d) { d = v; }
+__device__ __forceinline__ void narrow(float v, float& d) { d = v; }
+__device__ __forceinline__ void narrow(float v, __nv_bfloat16& d) { d = __float2bfloat16_rn(v); }
+
+template <int MS, int LD, int NTH, typename CT, typename ST>
+__device__ void store_colmajor(const CT* A, ST* dst) {
   for (int e = threadIdx.x; e < MS * MS; e += NTH) {
     const int j = e / MS, i = e - j * MS;
-    dst[e] = A[i * LD + j];
+    narrow(A[i * LD + j], dst[e]);
   }
 }
 
@@ -345,58 +355,58 @@ __device__ void gemm_into_b(const CT* A, CT* B, CT sign) {
   __syncthreads();
 }
 
-template <int K, int Q, typename CT, int NTH>
+template <int K, int Q, typename CT, typename ST, int NTH, int NPGX>
 __global__ void __launch_bounds__(NTH, 1)
 block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const double* __restrict__ Ce,
-                    CT* __restrict__ factors, int* __restrict__ status) {
-  using pd = PD<K>;
+                    ST* __restrict__ factors, int* __restrict__ status) {
+  using pd = PD<K, NPGX>;
   constexpr int MS = pd::MS, LD = pd::LD;
-  constexpr int G = 16 / (int)sizeof(CT);
+  constexpr int G = 16 / (int)sizeof(ST);
   constexpr int64_t BLK = (MS * MS + G - 1) / G * G;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT* M1 = reinterpret_cast<CT*>(smem_raw);
   CT* M2 = M1 + MS * LD;
   CT* colbuf = M2 + (Q == 1 ? MS * LD : 0);
-  FactorTables<K>& ft = *reinterpret_cast<FactorTables<K>*>(
+  FactorTables<K, NPGX>& ft = *reinterpret_cast<FactorTables<K, NPGX>*>(
       smem_raw + ((sizeof(CT) * ((Q == 1 ? 2 : 1) * MS * LD + MS) + 15) / 16) * 16);
   int* perm = reinterpret_cast<int*>(&ft + 1);
   int* sh = perm + MS;
   const int blk = blockIdx.x, slab = blockIdx.y;
-  build_factor_tables<K>(g, T, bs, blk, ft, NTH);
+  build_factor_tables<K, NPGX>(g, T, bs, blk, ft, NTH);
   if (threadIdx.x == 0) { sh[0] = 0; sh[1] = 0; }
   __syncthreads();
   const bool conv = ph.conv != 0.0;
-  CT* F = factors + ((int64_t)blk * g.N + slab) * (Q + 1) * (Q + 1) * BLK;
+  ST* F = factors + ((int64_t)blk * g.N + slab) * (Q + 1) * (Q + 1) * BLK;
   bool ok;
   if constexpr (Q == 0) {
-    assemble_const<K, Q, CT, LD, NTH>(g, T, ph, ft, M1, 0, 0, false);
+    assemble_const<K, Q, CT, LD, NTH, NPGX>(g, T, ph, ft, M1, 0, 0, false);
     __syncthreads();
-    if (conv) assemble_conv<K, Q, CT, LD, NTH>(g, T, ph, bs, Ce, blk, slab, ft, M1, 0, 0);
+    if (conv) assemble_conv<K, Q, CT, LD, NTH, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M1, 0, 0);
     ok = gauss_jordan<MS, LD, NTH>(M1, colbuf, perm, sh);
     store_colmajor<MS, LD, NTH>(M1, F);
   } else {
     // A00^{-1}
-    assemble_const<K, Q, CT, LD, NTH>(g, T, ph, ft, M1, 0, 0, false);
+    assemble_const<K, Q, CT, LD, NTH, NPGX>(g, T, ph, ft, M1, 0, 0, false);
     __syncthreads();
-    if (conv) assemble_conv<K, Q, CT, LD, NTH>(g, T, ph, bs, Ce, blk, slab, ft, M1, 0, 0);
+    if (conv) assemble_conv<K, Q, CT, LD, NTH, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M1, 0, 0);
     ok = gauss_jordan<MS, LD, NTH>(M1, colbuf, perm, sh);
     store_colmajor<MS, LD, NTH>(M1, F);
     // X = A00^{-1} A01
-    assemble_const<K, Q, CT, LD, NTH>(g, T, ph, ft, M2, 0, 1, false);
+    assemble_const<K, Q, CT, LD, NTH, NPGX>(g, T, ph, ft, M2, 0, 1, false);
     __syncthreads();
-    if (conv) assemble_conv<K, Q, CT, LD, NTH>(g, T, ph, bs, Ce, blk, slab, ft, M2, 0, 1);
+    if (conv) assemble_conv<K, Q, CT, LD, NTH, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M2, 0, 1);
     gemm_into_b<MS, LD, NTH, CT>(M1, M2, CT(1));
     store_colmajor<MS, LD, NTH>(M2, F + 3 * BLK);
     // A10
-    assemble_const<K, Q, CT, LD, NTH>(g, T, ph, ft, M1, 1, 0, false);
+    assemble_const<K, Q, CT, LD, NTH, NPGX>(g, T, ph, ft, M1, 1, 0, false);
     __syncthreads();
-    if (conv) assemble_conv<K, Q, CT, LD, NTH>(g, T, ph, bs, Ce, blk, slab, ft, M1, 1, 0);
+    if (conv) assemble_conv<K, Q, CT, LD, NTH, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M1, 1, 0);
     store_colmajor<MS, LD, NTH>(M1, F + 1 * BLK);
     // S = A11 - A10 X
     gemm_into_b<MS, LD, NTH, CT>(M1, M2, CT(-1));
-    assemble_const<K, Q, CT, LD, NTH>(g, T, ph, ft, M2, 1, 1, true);
+    assemble_const<K, Q, CT, LD, NTH, NPGX>(g, T, ph, ft, M2, 1, 1, true);
     __syncthreads();
-    if (conv) assemble_conv<K, Q, CT, LD, NTH>(g, T, ph, bs, Ce, blk, slab, ft, M2, 1, 1);
+    if (conv) assemble_conv<K, Q, CT, LD, NTH, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M2, 1, 1);
     ok = gauss_jordan<MS, LD, NTH>(M2, colbuf, perm, sh) && ok;
     store_colmajor<MS, LD, NTH>(M2, F + 2 * BLK);
   }
@@ -418,9 +428,18 @@ block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const d
 // side is prefetched into registers while the current slab's blocks are applied.
 // Every wait is bounded: on timeout the kernel sets *err, drains its own copies
 // in flight (bounded) and returns.
-template <int K, int Q, typename FT>
+// Arithmetic type of the apply for each factor storage type: BF16 factors are
+// widened to FP32 on load.
+template <typename FT> struct ComputeType { using type = FT; };
+template <> struct ComputeType<__nv_bfloat16> { using type = float; };
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ float widen(float v) { return v; }
+__device__ __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <int K, int Q, typename FT, int NPGX = 2 * K - 1>
 struct ApplyCfg {
-  using pd = PD<K>;
+  using pd = PD<K, NPGX>;
+  using CT = typename ComputeType<FT>::type;
   static constexpr int MS = pd::MS, NT = Q + 1, NB = NT * NT;
   static constexpr int G = K == 1 ? 5 : 4;                        // column groups per chunk
   static constexpr int NCONS = (G * MS + 31) / 32 * 32;           // consumer threads: 256 or 448
@@ -430,7 +449,7 @@ struct ApplyCfg {
   static constexpr int BLK_BYTES = BLK * (int)sizeof(FT);
   // chunk width: whole block for k = 1, 28 columns for k = 2 (a multiple of GR columns keeps
   // every chunk boundary on a 16-byte granule)
-  static constexpr int CC = K == 1 ? (MS + GR - 1) / GR * GR : 28;
+  static constexpr int CC = K == 1 ? (MS + GR - 1) / GR * GR : (28 + GR - 1) / GR * GR;
   static constexpr int NCH = (MS + CC - 1) / CC;                  // chunks per block
   static constexpr int SUB = (CC + G - 1) / G;                    // columns per group and chunk
   static constexpr int LAST = BLK - (NCH - 1) * CC * MS;          // last chunk carries the padding
@@ -444,23 +463,24 @@ struct ApplyCfg {
   static_assert(NS >= 2, "ring too small");
 };
 
-template <int K, int Q, typename FT>
+template <int K, int Q, typename FT, int NPGX = 2 * K - 1>
 struct ApplySmem {
-  using C = ApplyCfg<K, Q, FT>;
-  using pd = PD<K>;
+  using C = ApplyCfg<K, Q, FT, NPGX>;
+  using pd = PD<K, NPGX>;
+  using CT = typename C::CT;
   unsigned long long full[C::NS];
   unsigned long long empty[C::NS];
   int abort_flag;  // written by any warp at any time
   int decision;    // abort decision of the consumers, published by consumer thread 0 before a barrier
   int issued;
   int sidx[C::MS];
-  FT rhs[C::NT][C::MS];
-  FT y[C::NT][C::MS];
-  FT red[C::G][C::MS];
-  FT yp[2][pd::NVG2];
-  FT tm[2][pd::NVG2];
-  FT mx[pd::NVG][pd::NVG];
-  FT my[pd::NVG][pd::NVG];
+  CT rhs[C::NT][C::MS];
+  CT y[C::NT][C::MS];
+  CT red[C::G][C::MS];
+  CT yp[2][pd::NVG2];
+  CT tm[2][pd::NVG2];
+  CT mx[pd::NVG][pd::NVG];
+  CT my[pd::NVG][pd::NVG];
 };
 
 constexpr int kSpinLimit = 1 << 22;
@@ -500,22 +520,31 @@ __device__ __forceinline__ void consumer_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(NCONS) : "memory");
 }
 
-template <int K, int Q, typename FT>
-__global__ void __launch_bounds__(ApplyCfg<K, Q, FT>::NTH, 1)
-block_apply_kernel(LevelGeom g, FeTables T, BlockSet bs, const FT* __restrict__ factors, const double* __restrict__ r,
-                   double* __restrict__ out, int nblk, int* __restrict__ err) {
-  using C = ApplyCfg<K, Q, FT>;
-  using pd = PD<K>;
+// One unit of work of the smoother apply: block `blk` of a level, with that
+// level's geometry, stored factors, right-hand side and output.
+template <typename FT>
+struct ApplyItem {
+  LevelGeom g;
+  BlockSet bs;
+  const FT* factors;
+  const double* r;
+  double* out;  // patch outputs [blk][slab][a][slot] (kind 0) or the global solution (kind 1)
+  int blk;
+};
+
+template <int K, int Q, typename FT, int NPGX, class Items>
+__device__ __forceinline__ void apply_persistent(const FeTables& T, const Items& items, int64_t nitems,
+                                                 int* __restrict__ err) {
+  using C = ApplyCfg<K, Q, FT, NPGX>;
+  using pd = PD<K, NPGX>;
+  using CT = typename C::CT;
   constexpr int MS = C::MS, NT = C::NT, NB = C::NB, NS = C::NS, NVG = pd::NVG, NCH = C::NCH, NCONS = C::NCONS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   FT* ring = reinterpret_cast<FT*>(smem_raw);
-  ApplySmem<K, Q, FT>& sm =
-      *reinterpret_cast<ApplySmem<K, Q, FT>*>(smem_raw + (size_t)NS * C::SLOT_ELEMS * sizeof(FT));
+  ApplySmem<K, Q, FT, NPGX>& sm =
+      *reinterpret_cast<ApplySmem<K, Q, FT, NPGX>*>(smem_raw + (size_t)NS * C::SLOT_ELEMS * sizeof(FT));
   volatile int* abort_flag = &sm.abort_flag;
   const int tid = threadIdx.x, lane = tid & 31;
-  const int npatch_cta = blockIdx.x < nblk ? (nblk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const int64_t blocks_pp = (int64_t)g.N * NB;         // blocks per patch
-  const int64_t total = npatch_cta * blocks_pp * NCH;  // chunks streamed by this CTA
   if (tid == 0) {
     for (int i = 0; i < NS; ++i) {
       mbar_init(smem_u32(&sm.full[i]), 1);
@@ -528,29 +557,36 @@ block_apply_kernel(LevelGeom g, FeTables T, BlockSet bs, const FT* __restrict__ 
   }
   __syncthreads();
 
-  if (tid >= NCONS) {  // ---------------- producer warp
+  if (tid >= NCONS) {  // ---------------- producer warp: walks the CTA's items and streams their chunks
     if (lane == 0) {
-      for (int64_t s = 0; s < total; ++s) {
-        const int slot = (int)(s % NS);
-        const int64_t u = s / NS;
-        if (u > 0 && !mbar_wait_bounded(smem_u32(&sm.empty[slot]), (uint32_t)((u - 1) & 1))) {
-          *abort_flag = 1;
-          atomicExch(err, 1);
-          break;
+      int64_t s = 0;
+      bool stop = false;
+      for (int64_t it = blockIdx.x; it < nitems && !stop; it += gridDim.x) {
+        const ApplyItem<FT> v = items(it);
+        const int64_t per_item = (int64_t)v.g.N * NB * NCH;
+        for (int64_t q = 0; q < per_item; ++q, ++s) {
+          const int slot = (int)(s % NS);
+          const int64_t u = s / NS;
+          if (u > 0 && !mbar_wait_bounded(smem_u32(&sm.empty[slot]), (uint32_t)((u - 1) & 1))) {
+            *abort_flag = 1;
+            atomicExch(err, 1);
+            stop = true;
+            break;
+          }
+          if (*abort_flag) {
+            stop = true;
+            break;
+          }
+          const int64_t bi = q / NCH;  // block index within the item
+          const int k = (int)(q - bi * NCH);
+          const int64_t off = ((int64_t)v.blk * v.g.N * NB + bi) * C::BLK + (int64_t)k * C::CC * MS;
+          const int elems = (k == NCH - 1) ? C::BLK - k * C::CC * MS : C::CC * MS;
+          const uint32_t bar = smem_u32(&sm.full[slot]);
+          const uint32_t bytes = (uint32_t)(elems * sizeof(FT));
+          mbar_expect_tx(bar, bytes);
+          bulk_g2s(smem_u32(ring + (size_t)slot * C::SLOT_ELEMS), v.factors + off, bytes, bar);
+          *(volatile int*)&sm.issued = (int)(s + 1 < 0x7fffffff ? s + 1 : 0x7fffffff);
         }
-        if (*abort_flag) break;
-        const int64_t bi = s / NCH;  // CTA-local block index
-        const int k = (int)(s - bi * NCH);
-        const int t = (int)(bi / blocks_pp);
-        const int64_t q = bi - t * blocks_pp;
-        const int blk = blockIdx.x + t * gridDim.x;
-        const int64_t off = ((int64_t)blk * blocks_pp + q) * C::BLK + (int64_t)k * C::CC * MS;
-        const int elems = (k == NCH - 1) ? C::BLK - k * C::CC * MS : C::CC * MS;
-        const uint32_t bar = smem_u32(&sm.full[slot]);
-        const uint32_t bytes = (uint32_t)(elems * sizeof(FT));
-        mbar_expect_tx(bar, bytes);
-        bulk_g2s(smem_u32(ring + (size_t)slot * C::SLOT_ELEMS), factors + off, bytes, bar);
-        *(volatile int*)&sm.issued = (int)(s + 1 < 0x7fffffff ? s + 1 : 0x7fffffff);
       }
     }
     return;
@@ -558,12 +594,17 @@ block_apply_kernel(LevelGeom g, FeTables T, BlockSet bs, const FT* __restrict__ 
 
   // ---------------- consumer warps
   int64_t ci = 0;  // next chunk to consume
-  const int nvg = bs.nvg, nv2g = nvg * nvg;
   const bool gemv_thread = tid < C::G * MS;
   const int row = tid % MS, grp = tid / MS;
   bool aborted = false;
-  for (int t = 0; t < npatch_cta && !aborted; ++t) {
-    const int blk = blockIdx.x + t * gridDim.x;
+  for (int64_t it = blockIdx.x; it < nitems && !aborted; it += gridDim.x) {
+    const ApplyItem<FT> v = items(it);
+    const LevelGeom& g = v.g;
+    const BlockSet& bs = v.bs;
+    const double* __restrict__ r = v.r;
+    double* __restrict__ out = v.out;
+    const int blk = v.blk;
+    const int nvg = bs.nvg, nv2g = nvg * nvg;
     int vx0, vy0, px0, py0;
     block_origin(g, bs, blk, vx0, vy0, px0, py0);
     for (int s = tid; s < MS; s += NCONS) sm.sidx[s] = decode_slot(g, bs, blk, s).sp;
@@ -572,15 +613,15 @@ block_apply_kernel(LevelGeom g, FeTables T, BlockSet bs, const FT* __restrict__ 
       const int xi = vx0 + i, xj = vx0 + j, yi = vy0 + i, yj = vy0 + j;
       const bool okx = i < nvg && j < nvg && xi >= 1 && xi <= g.nv - 2 && xj >= 1 && xj <= g.nv - 2;
       const bool oky = i < nvg && j < nvg && yi >= 1 && yi <= g.nv - 2 && yj >= 1 && yj <= g.nv - 2;
-      sm.mx[i][j] = okx ? (FT)(g.h * vv1<K>(T.m1, g.n, xi, xj)) : (FT)0;
-      sm.my[i][j] = oky ? (FT)(g.h * vv1<K>(T.m1, g.n, yi, yj)) : (FT)0;
+      sm.mx[i][j] = okx ? (CT)(g.h * vv1<K>(T.m1, g.n, xi, xj)) : (CT)0;
+      sm.my[i][j] = oky ? (CT)(g.h * vv1<K>(T.m1, g.n, yi, yj)) : (CT)0;
     }
     for (int e = tid; e < 2 * pd::NVG2; e += NCONS) (&sm.yp[0][0])[e] = 0;
     consumer_sync<NCONS>();
     // (a) gather of slab 0; later slabs come from the register prefetch
     for (int e = tid; e < NT * MS; e += NCONS) {
       const int a = e / MS, s = e % MS, sp = sm.sidx[s];
-      sm.rhs[a][s] = sp >= 0 ? (FT)r[(int64_t)a * g.S + sp] : (FT)0;
+      sm.rhs[a][s] = sp >= 0 ? (CT)r[(int64_t)a * g.S + sp] : (CT)0;
     }
     for (int slab = 0; slab < g.N && !aborted; ++slab) {
       if (slab > 0) {
@@ -588,32 +629,32 @@ block_apply_kernel(LevelGeom g, FeTables T, BlockSet bs, const FT* __restrict__ 
         consumer_sync<NCONS>();
         for (int e = tid; e < 2 * nv2g; e += NCONS) {
           const int c = e / nv2g, tt = e % nv2g, iy = tt / nvg, jx = tt % nvg;
-          FT acc = 0;
+          CT acc = 0;
           for (int jy = 0; jy < nvg; ++jy) acc = fma(sm.my[iy][jy], sm.yp[c][jy * nvg + jx], acc);
           sm.tm[c][tt] = acc;
         }
         consumer_sync<NCONS>();
         for (int e = tid; e < 2 * nv2g; e += NCONS) {
           const int c = e / nv2g, tt = e % nv2g, iy = tt / nvg, ix = tt % nvg;
-          FT acc = 0;
+          CT acc = 0;
           for (int jx = 0; jx < nvg; ++jx) acc = fma(sm.mx[ix][jx], sm.tm[c][iy * nvg + jx], acc);
           const int s = c * nv2g + tt;
           if (sm.sidx[s] >= 0)
-            for (int a = 0; a < NT; ++a) sm.rhs[a][s] += (FT)T.tau0[a] * acc;
+            for (int a = 0; a < NT; ++a) sm.rhs[a][s] += (CT)T.tau0[a] * acc;
         }
       }
       consumer_sync<NCONS>();
       // register prefetch of the next slab's right-hand side
-      FT pf = 0;
+      CT pf = 0;
       if (tid < NT * MS && slab + 1 < g.N) {
         const int sp = sm.sidx[tid % MS];
-        if (sp >= 0) pf = (FT)r[((int64_t)(slab + 1) * NT + tid / MS) * g.S + sp];
+        if (sp >= 0) pf = (CT)r[((int64_t)(slab + 1) * NT + tid / MS) * g.S + sp];
       }
       // (c) the slab's stored blocks: Q = 0: y0 = A^{-1} r0;  Q = 1: z0 = A00^{-1} r0,
       //     s1 = r1 - A10 z0, y1 = S^{-1} s1, y0 = z0 - X y1
       for (int b = 0; b < NB; ++b) {
-        const FT* xv = (b == 0) ? sm.rhs[0] : (b == 1) ? sm.y[0] : (b == 2) ? sm.rhs[NT - 1] : sm.y[NT - 1];
-        FT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        const CT* xv = (b == 0) ? sm.rhs[0] : (b == 1) ? sm.y[0] : (b == 2) ? sm.rhs[NT - 1] : sm.y[NT - 1];
+        CT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         for (int k = 0; k < NCH; ++k) {
           const int slot = (int)(ci % NS);
           const bool ok = !aborted && mbar_wait_bounded(smem_u32(&sm.full[slot]), (uint32_t)((ci / NS) & 1));
@@ -626,15 +667,15 @@ block_apply_kernel(LevelGeom g, FeTables T, BlockSet bs, const FT* __restrict__ 
             const int c0 = grp * C::SUB;
             const int ncol = min(C::CC, MS - k * C::CC);
             const int c1 = min(ncol, c0 + C::SUB);
-            const FT* xk = xv + k * C::CC;
+            const CT* xk = xv + k * C::CC;
             int c = c0;
             for (; c + 3 < c1; c += 4) {
-              a0 = fma(A[(c + 0) * MS + row], xk[c + 0], a0);
-              a1 = fma(A[(c + 1) * MS + row], xk[c + 1], a1);
-              a2 = fma(A[(c + 2) * MS + row], xk[c + 2], a2);
-              a3 = fma(A[(c + 3) * MS + row], xk[c + 3], a3);
+              a0 = fma(widen(A[(c + 0) * MS + row]), xk[c + 0], a0);
+              a1 = fma(widen(A[(c + 1) * MS + row]), xk[c + 1], a1);
+              a2 = fma(widen(A[(c + 2) * MS + row]), xk[c + 2], a2);
+              a3 = fma(widen(A[(c + 3) * MS + row]), xk[c + 3], a3);
             }
-            for (; c < c1; ++c) a0 = fma(A[c * MS + row], xk[c], a0);
+            for (; c < c1; ++c) a0 = fma(widen(A[c * MS + row]), xk[c], a0);
           }
           __syncwarp();
           if (ok && lane == 0) mbar_arrive(smem_u32(&sm.empty[slot]));  // this warp is done with the slot
@@ -648,7 +689,7 @@ block_apply_kernel(LevelGeom g, FeTables T, BlockSet bs, const FT* __restrict__ 
           break;
         }
         if (tid < MS) {
-          FT sum = sm.red[0][tid];
+          CT sum = sm.red[0][tid];
 #pragma unroll
           for (int h = 1; h < C::G; ++h) sum += sm.red[h][tid];
           if (b == 0) sm.y[0][tid] = sum;
@@ -677,7 +718,6 @@ block_apply_kernel(LevelGeom g, FeTables T, BlockSet bs, const FT* __restrict__ 
     consumer_sync<NCONS>();
   }
   if (aborted && tid == 0) {
-    // drain this CTA's own copies in flight (bounded), then report
     // the last NS issued chunks are the latest copy into each slot
     const int64_t issued = *(volatile int*)&sm.issued;
     for (int64_t s = issued > NS ? issued - NS : 0; s < issued; ++s)
@@ -686,15 +726,64 @@ block_apply_kernel(LevelGeom g, FeTables T, BlockSet bs, const FT* __restrict__ 
   }
 }
 
+template <typename FT>
+struct SingleItems {
+  LevelGeom g;
+  BlockSet bs;
+  const FT* factors;
+  const double* r;
+  double* out;
+  __device__ ApplyItem<FT> operator()(int64_t it) const { return {g, bs, factors, r, out, (int)it}; }
+};
+
+template <typename FT>
+struct BatchItems {
+  const BatchSeg* segs;
+  int nseg;
+  const double* r;   // arena of right-hand sides at this depth (kind 0)
+  double* yp;        // patch-output arena (kind 0)
+  bool coarse;       // kind 1: absolute per-member pointers xa / ya
+  __device__ ApplyItem<FT> operator()(int64_t it) const {
+    const int m = batch_find<BU_PATCH>(segs, nseg, it);
+    const BatchSeg& sg = segs[m];
+    ApplyItem<FT> v;
+    v.g = sg.g;
+    v.bs = sg.bs;
+    v.factors = static_cast<const FT*>(sg.factors);
+    v.blk = (int)(it - sg.u_patch);
+    if (coarse) {
+      v.r = sg.xa;
+      v.out = sg.ya;
+    } else {
+      v.r = r + sg.off;
+      v.out = yp + sg.off_yp;
+    }
+    return v;
+  }
+};
+
+template <int K, int Q, typename FT, int NPGX>
+__global__ void __launch_bounds__(ApplyCfg<K, Q, FT, NPGX>::NTH, 1)
+block_apply_kernel(LevelGeom g, FeTables T, BlockSet bs, const FT* __restrict__ factors, const double* __restrict__ r,
+                   double* __restrict__ out, int nblk, int* __restrict__ err) {
+  apply_persistent<K, Q, FT, NPGX>(T, SingleItems<FT>{g, bs, factors, r, out}, nblk, err);
+}
+
+template <int K, int Q, typename FT, int NPGX>
+__global__ void __launch_bounds__(ApplyCfg<K, Q, FT, NPGX>::NTH, 1)
+bt_block_apply_kernel(const BatchSeg* __restrict__ segs, int nseg, int64_t nitems, FeTables T,
+                      const double* __restrict__ r, double* __restrict__ yp, int coarse, int* __restrict__ err) {
+  apply_persistent<K, Q, FT, NPGX>(T, BatchItems<FT>{segs, nseg, r, yp, coarse != 0}, nitems, err);
+}
+
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 __device__ __forceinline__ int ceildiv(int a, int b) { return -floordiv(-a, b); }
 
 template <int K, int Q>
-__global__ void scatter_kernel(LevelGeom g, const double* __restrict__ Yp, double* __restrict__ y) {
+__device__ __forceinline__ void scatter_body(const LevelGeom& g, const double* __restrict__ Yp,
+                                             double* __restrict__ y, int64_t idx) {
   using pd = PD<K>;
   constexpr int MS = pd::MS, NT = Q + 1;
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= g.ndofs) return;
   const int S = g.S, nv = g.nv, nv2 = nv * nv, n = g.n;
   const int64_t blkt = idx / S;
   const int sp = int(idx % S);
@@ -726,26 +815,43 @@ __global__ void scatter_kernel(LevelGeom g, const double* __restrict__ Yp, doubl
   y[idx] = acc;
 }
 
-template <int K, int Q, typename CT>
+template <int K, int Q>
+__global__ void scatter_kernel(LevelGeom g, const double* __restrict__ Yp, double* __restrict__ y) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= g.ndofs) return;
+  scatter_body<K, Q>(g, Yp, y, idx);
+}
+
+template <int K, int Q>
+__global__ void bt_scatter_kernel(const BatchSeg* __restrict__ segs, int nseg, int64_t dofs,
+                                  const double* __restrict__ yp, double* __restrict__ y) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= dofs) return;
+  const int m = batch_find<BU_DOF>(segs, nseg, u);
+  const LevelGeom g = segs[m].g;
+  scatter_body<K, Q>(g, yp + segs[m].off_yp, y + segs[m].off, u - segs[m].u_dof);
+}
+
+template <int K, int Q, typename CT, typename ST, int NPGX = 2 * K - 1>
 void run_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const BlockSet& bs, const double* Ce,
-                CT* factors, int* status, cudaStream_t s) {
-  using pd = PD<K>;
+                ST* factors, int* status, cudaStream_t s) {
+  using pd = PD<K, NPGX>;
   constexpr int NTH = K == 1 ? 256 : 512;
   const size_t mats = ((sizeof(CT) * ((Q == 1 ? 2 : 1) * pd::MS * pd::LD + pd::MS) + 15) / 16) * 16;
-  const size_t smem = mats + sizeof(FactorTables<K>) + sizeof(int) * (pd::MS + 2);
-  auto kern = block_factor_kernel<K, Q, CT, NTH>;
+  const size_t smem = mats + sizeof(FactorTables<K, NPGX>) + sizeof(int) * (pd::MS + 2);
+  auto kern = block_factor_kernel<K, Q, CT, ST, NTH, NPGX>;
   WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int nblk = bs.kind == 0 ? g.npatch() : 1;
   kern<<<dim3(nblk, g.N), NTH, smem, s>>>(g, T, ph, bs, Ce, factors, status);
   WR_LAUNCH_CHECK();
 }
 
-template <int K, int Q, typename FT>
+template <int K, int Q, typename FT, int NPGX = 2 * K - 1>
 void run_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs, const FT* factors, const double* r,
                double* out, int* err, cudaStream_t s) {
-  using C = ApplyCfg<K, Q, FT>;
-  const size_t smem = (size_t)C::NS * C::SLOT_ELEMS * sizeof(FT) + sizeof(ApplySmem<K, Q, FT>);
-  auto kern = block_apply_kernel<K, Q, FT>;
+  using C = ApplyCfg<K, Q, FT, NPGX>;
+  const size_t smem = (size_t)C::NS * C::SLOT_ELEMS * sizeof(FT) + sizeof(ApplySmem<K, Q, FT, NPGX>);
+  auto kern = block_apply_kernel<K, Q, FT, NPGX>;
   static int grid_cap = 0;  // persistent grid: CTAs resident on the whole GPU
   if (grid_cap == 0) {
     WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -761,6 +867,27 @@ void run_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs, const 
   WR_LAUNCH_CHECK();
 }
 
+template <int K, int Q, typename FT, int NPGX = 2 * K - 1>
+void run_bt_apply(const BatchSeg* segs, int nseg, int64_t items, const FeTables& T, const double* r, double* yp,
+                  bool coarse, int* err, cudaStream_t s) {
+  using C = ApplyCfg<K, Q, FT, NPGX>;
+  const size_t smem = (size_t)C::NS * C::SLOT_ELEMS * sizeof(FT) + sizeof(ApplySmem<K, Q, FT, NPGX>);
+  auto kern = bt_block_apply_kernel<K, Q, FT, NPGX>;
+  static int grid_cap = 0;
+  if (grid_cap == 0) {
+    WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0, per_sm = 0;
+    WR_CUDA(cudaGetDevice(&dev));
+    WR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    WR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NTH, smem));
+    grid_cap = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  if (items <= 0) return;
+  const int grid = items < grid_cap ? (int)items : grid_cap;
+  kern<<<grid, C::NTH, smem, s>>>(segs, nseg, items, T, r, yp, coarse ? 1 : 0, err);
+  WR_LAUNCH_CHECK();
+}
+
 int* status_buffer() {
   static int* st = nullptr;  // per process; reset before each factorisation
   if (!st) WR_CUDA(cudaMalloc(&st, sizeof(int)));
@@ -773,12 +900,18 @@ void launch_block_factor(const LevelGeom& g, const FeTables& T, const PhysParams
                          const double* Ce, void* factors, int precision, cudaStream_t s) {
   int* st = status_buffer();
   WR_CUDA(cudaMemsetAsync(st, 0, sizeof(int), s));
-#define WR_F(K_, Q_)                                                                                   \
-  if (g.k == K_ && g.q == Q_) {                                                                        \
-    if (precision == WR_FP32)                                                                          \
-      run_factor<K_, Q_, float>(g, T, ph, bs, Ce, static_cast<float*>(factors), st, s);                \
-    else                                                                                               \
-      run_factor<K_, Q_, double>(g, T, ph, bs, Ce, static_cast<double*>(factors), st, s);              \
+#define WR_F(K_, Q_)                                                                                     \
+  if (g.k == K_ && g.q == Q_) {                                                                          \
+    if (precision == WR_FP32)                                                                            \
+      run_factor<K_, Q_, float, float>(g, T, ph, bs, Ce, static_cast<float*>(factors), st, s);           \
+    else if (precision == WR_BF16)                                                                       \
+      run_factor<K_, Q_, float, __nv_bfloat16>(g, T, ph, bs, Ce, static_cast<__nv_bfloat16*>(factors), st, s); \
+    else                                                                                                 \
+      run_factor<K_, Q_, double, double>(g, T, ph, bs, Ce, static_cast<double*>(factors), st, s);        \
+  } else
+  if (bs.kind == 1 && g.k == 1 && bs.npg == 4) {  // coarse 3x3 block of Q2/Q1 (FP64)
+    if (g.q == 0) run_factor<1, 0, double, double, 4>(g, T, ph, bs, Ce, static_cast<double*>(factors), st, s);
+    else run_factor<1, 1, double, double, 4>(g, T, ph, bs, Ce, static_cast<double*>(factors), st, s);
   } else
   WR_F(1, 0) WR_F(1, 1) WR_F(2, 0) WR_F(2, 1) throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 #undef WR_F
@@ -794,8 +927,14 @@ void launch_block_apply(const LevelGeom& g, const FeTables& T, const BlockSet& b
   if (g.k == K_ && g.q == Q_) {                                                                               \
     if (precision == WR_FP32)                                                                                 \
       run_apply<K_, Q_, float>(g, T, bs, static_cast<const float*>(factors), r, out, err, s);                     \
+    else if (precision == WR_BF16)                                                                            \
+      run_apply<K_, Q_, __nv_bfloat16>(g, T, bs, static_cast<const __nv_bfloat16*>(factors), r, out, err, s);     \
     else                                                                                                      \
       run_apply<K_, Q_, double>(g, T, bs, static_cast<const double*>(factors), r, out, err, s);                   \
+  } else
+  if (bs.kind == 1 && g.k == 1 && bs.npg == 4) {  // coarse 3x3 block of Q2/Q1 (FP64)
+    if (g.q == 0) run_apply<1, 0, double, 4>(g, T, bs, static_cast<const double*>(factors), r, out, err, s);
+    else run_apply<1, 1, double, 4>(g, T, bs, static_cast<const double*>(factors), r, out, err, s);
   } else
   WR_A(1, 0) WR_A(1, 1) WR_A(2, 0) WR_A(2, 1) throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 #undef WR_A
@@ -822,5 +961,41 @@ __global__ void patch_slots_kernel(LevelGeom g, BlockSet bs, int blk, int* __res
 // Spatial index of every slot of block `blk` as the kernels decode it (-1 = padding).
 void launch_patch_slots(const LevelGeom& g, const BlockSet& bs, int blk, int* out_sp, cudaStream_t s) {
   patch_slots_kernel<<<1, 128, 0, s>>>(g, bs, blk, out_sp);
+  WR_LAUNCH_CHECK();
+}
+
+void bt_block_apply(int k, int q, int precision, const BatchSeg* segs, int nseg, int64_t items, int64_t dofs,
+                    const FeTables& T, const double* r, double* out, double* yp, int* err, int coarse_n,
+                    cudaStream_t s) {
+  // coarse blocks (coarse_n = 2 or 3) are FP64; the 3x3 coarse block of Q2/Q1 uses its own slot shape
+  if (coarse_n == 3) {
+    if (k != 1) throw WrError(WR_ERR_ARG, "3x3 coarse blocks need k = 1");
+    if (q == 0) run_bt_apply<1, 0, double, 4>(segs, nseg, items, T, r, yp, true, err, s);
+    else run_bt_apply<1, 1, double, 4>(segs, nseg, items, T, r, yp, true, err, s);
+    return;
+  }
+  if (coarse_n == 2) {
+    if (k == 1 && q == 0) run_bt_apply<1, 0, double>(segs, nseg, items, T, r, yp, true, err, s);
+    else if (k == 1 && q == 1) run_bt_apply<1, 1, double>(segs, nseg, items, T, r, yp, true, err, s);
+    else if (k == 2 && q == 0) run_bt_apply<2, 0, double>(segs, nseg, items, T, r, yp, true, err, s);
+    else if (k == 2 && q == 1) run_bt_apply<2, 1, double>(segs, nseg, items, T, r, yp, true, err, s);
+    else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
+    return;
+  }
+#define WR_BA(K_, Q_)                                                                                    \
+  if (k == K_ && q == Q_) {                                                                              \
+    if (precision == WR_FP32) run_bt_apply<K_, Q_, float>(segs, nseg, items, T, r, yp, false, err, s);   \
+    else if (precision == WR_BF16)                                                                       \
+      run_bt_apply<K_, Q_, __nv_bfloat16>(segs, nseg, items, T, r, yp, false, err, s);                   \
+    else run_bt_apply<K_, Q_, double>(segs, nseg, items, T, r, yp, false, err, s);                       \
+  } else
+  WR_BA(1, 0) WR_BA(1, 1) WR_BA(2, 0) WR_BA(2, 1) throw WrError(WR_ERR_ARG, "unsupported (k, q)");
+#undef WR_BA
+  if (dofs <= 0) return;
+  const unsigned blocks = (unsigned)((dofs + 255) / 256);
+  if (k == 1 && q == 0) bt_scatter_kernel<1, 0><<<blocks, 256, 0, s>>>(segs, nseg, dofs, yp, out);
+  else if (k == 1 && q == 1) bt_scatter_kernel<1, 1><<<blocks, 256, 0, s>>>(segs, nseg, dofs, yp, out);
+  else if (k == 2 && q == 0) bt_scatter_kernel<2, 0><<<blocks, 256, 0, s>>>(segs, nseg, dofs, yp, out);
+  else bt_scatter_kernel<2, 1><<<blocks, 256, 0, s>>>(segs, nseg, dofs, yp, out);
   WR_LAUNCH_CHECK();
 }

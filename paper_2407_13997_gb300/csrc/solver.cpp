@@ -408,6 +408,10 @@ struct wr_ctx {
   }
 };
 
+double hessenberg_max_real_eig(const std::vector<double>& H, int mm, int ld) {
+  return wr_ctx::max_real_eigenvalue(H, mm, ld);
+}
+
 namespace {
 
 int fail(wr_ctx* c, const WrError& e) {
@@ -461,7 +465,7 @@ int wr_create(wr_ctx** out, const wr_problem* p, const wr_options* o, void* stre
   int rc = guarded(c.get(), [&]() -> int {
     need(p->k == 1 || p->k == 2, "k must be 1 or 2");
     need(p->q == 0 || p->q == 1, "q must be 0 or 1");
-    need(p->n_coarse == 2, "n_coarse must be 2");
+    need(p->n_coarse == 2 || (p->n_coarse == 3 && p->k == 1), "n_coarse must be 2 (or 3 for k = 1)");
     need(p->n_fine >= 4 && p->n_fine <= 4096, "n_fine out of range");
     need(p->n_slabs >= 1 && p->T > 0.0, "need n_slabs >= 1 and T > 0");
     int nf = p->n_fine;
@@ -472,7 +476,8 @@ int wr_create(wr_ctx** out, const wr_problem* p, const wr_options* o, void* stre
     need(p->n_modes == 0 || (p->mx && p->my && p->amp), "Fourier mode arrays missing");
     if (o) c->opt = *o;
     else wr_default_options(&c->opt);
-    need(c->opt.precision == WR_FP64 || c->opt.precision == WR_FP32, "precision must be WR_FP64 or WR_FP32");
+    need(c->opt.precision == WR_FP64 || c->opt.precision == WR_FP32 || c->opt.precision == WR_BF16,
+         "precision must be WR_FP64, WR_FP32 or WR_BF16");
     need(c->opt.cheb_steps >= 1 && c->opt.eig_steps >= 1 && c->opt.eig_steps <= c->opt.gmres_restart,
          "bad Chebyshev / eigen-estimate steps");
     need(c->opt.gmres_restart >= 1 && c->opt.gmres_restart <= 200, "bad restart");
@@ -485,7 +490,7 @@ int wr_create(wr_ctx** out, const wr_problem* p, const wr_options* o, void* stre
     std::vector<int> ns;
     for (int n = p->n_coarse; n <= p->n_fine; n *= 2) ns.push_back(n);
     const int ms = patch_ms(p->k), nt = p->q + 1;
-    const size_t fsz = c->opt.precision == WR_FP32 ? sizeof(float) : sizeof(double);
+    const size_t fsz = factor_elem_bytes(c->opt.precision);
     size_t max_ce = 0, max_ye = 0, max_yp = 0;
     for (size_t l = 0; l < ns.size(); ++l) {
       Level lv;
@@ -508,7 +513,8 @@ int wr_create(wr_ctx** out, const wr_problem* p, const wr_options* o, void* stre
       if (l >= 1) {
         const size_t nf = (size_t)lv.g.npatch() * p->n_slabs * nt * nt * factor_block_elems(p->k, c->opt.precision);
         void* f = nullptr;
-        if (fsz == sizeof(float)) f = c->alloc<float>(nf);
+        if (fsz == 2) f = c->alloc<uint16_t>(nf);
+        else if (fsz == 4) f = c->alloc<float>(nf);
         else f = c->alloc<double>(nf);
         lv.factors = f;
         max_yp = std::max(max_yp, (size_t)lv.g.npatch() * p->n_slabs * nt * ms);
@@ -518,9 +524,9 @@ int wr_create(wr_ctx** out, const wr_problem* p, const wr_options* o, void* stre
     c->cbs.kind = 1;
     c->cbs.nvg = c->L[0].g.nv - 2;
     c->cbs.npg = c->L[0].g.np;
-    c->cbs.ms = ms;
-    need(2 * c->cbs.nvg * c->cbs.nvg + c->cbs.npg * c->cbs.npg <= ms, "coarse block exceeds the slot layout");
-    c->cfactors = c->alloc<double>((size_t)p->n_slabs * nt * nt * factor_block_elems(p->k, WR_FP64));
+    c->cbs.ms = coarse_ms(p->k, p->n_coarse);
+    need(2 * c->cbs.nvg * c->cbs.nvg + c->cbs.npg * c->cbs.npg <= c->cbs.ms, "coarse block exceeds the slot layout");
+    c->cfactors = c->alloc<double>((size_t)p->n_slabs * nt * nt * block_elems(c->cbs.ms, WR_FP64));
     c->Ce = c->alloc<double>(p->conv != 0.0 ? max_ce : 1);
     c->ye = c->alloc<double>(max_ye);
     c->Yp = c->alloc<double>(max_yp);

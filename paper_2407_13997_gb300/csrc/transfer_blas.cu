@@ -21,10 +21,8 @@ __device__ __forceinline__ double w1d(const double* tab, int ld, int p, int nc, 
   return tab[(f - 2 * p * c) * ld + l];
 }
 
-__global__ void prolong_add_kernel(LevelGeom gf, LevelGeom gc, FeTables T, const double* __restrict__ xc,
-                                   double* __restrict__ xf) {
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= gf.ndofs) return;
+__device__ __forceinline__ void prolong_body(const LevelGeom& gf, const LevelGeom& gc, const FeTables& T,
+                                             const double* __restrict__ xc, double* __restrict__ xf, int64_t idx) {
   const int64_t blk = idx / gf.S;
   const int sp = int(idx % gf.S);
   const int nvf2 = gf.nv * gf.nv, nvc2 = gc.nv * gc.nv;
@@ -63,10 +61,15 @@ __global__ void prolong_add_kernel(LevelGeom gf, LevelGeom gc, FeTables T, const
   xf[idx] += acc;
 }
 
-__global__ void restrict_kernel(LevelGeom gf, LevelGeom gc, FeTables T, const double* __restrict__ xf,
-                                double* __restrict__ xc) {
+__global__ void prolong_add_kernel(LevelGeom gf, LevelGeom gc, FeTables T, const double* __restrict__ xc,
+                                   double* __restrict__ xf) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= gc.ndofs) return;
+  if (idx >= gf.ndofs) return;
+  prolong_body(gf, gc, T, xc, xf, idx);
+}
+
+__device__ __forceinline__ void restrict_body(const LevelGeom& gf, const LevelGeom& gc, const FeTables& T,
+                                              const double* __restrict__ xf, double* __restrict__ xc, int64_t idx) {
   const int64_t blk = idx / gc.S;
   const int sp = int(idx % gc.S);
   const int nvf2 = gf.nv * gf.nv, nvc2 = gc.nv * gc.nv;
@@ -106,6 +109,13 @@ __global__ void restrict_kernel(LevelGeom gf, LevelGeom gc, FeTables T, const do
   xc[idx] = acc;
 }
 
+__global__ void restrict_kernel(LevelGeom gf, LevelGeom gc, FeTables T, const double* __restrict__ xf,
+                                double* __restrict__ xc) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= gc.ndofs) return;
+  restrict_body(gf, gc, T, xf, xc, idx);
+}
+
 // Pressure weight int chi_j of node g in 1D: h sum over cells containing g of mp1.
 __device__ __forceinline__ double pw1(const FeTables& T, int k, int n, double h, int g) {
   const int lo = g == 0 ? 0 : (g - 1) / k, hi = min(g / k, n - 1);
@@ -115,9 +125,10 @@ __device__ __forceinline__ double pw1(const FeTables& T, int k, int n, double h,
 }
 
 // One CTA per temporal block: Phi -= (sum_j w_j Phi_j) / (sum_j w_j), fixed-order reduction.
-__global__ void project_pressure_kernel(LevelGeom g, FeTables T, double* __restrict__ x) {
+__device__ __forceinline__ void project_body(const LevelGeom& g, const FeTables& T, double* __restrict__ x,
+                                             int64_t tblk) {
   __shared__ double sa[256], sb[256];
-  double* p = x + (int64_t)blockIdx.x * g.S + 2 * g.nv * g.nv;
+  double* p = x + tblk * g.S + 2 * g.nv * g.nv;
   const int np2 = g.np * g.np;
   double a = 0.0, b = 0.0;
   for (int j = threadIdx.x; j < np2; j += blockDim.x) {
@@ -137,6 +148,10 @@ __global__ void project_pressure_kernel(LevelGeom g, FeTables T, double* __restr
   }
   const double mean = sa[0] / sb[0];
   for (int j = threadIdx.x; j < np2; j += blockDim.x) p[j] -= mean;
+}
+
+__global__ void project_pressure_kernel(LevelGeom g, FeTables T, double* __restrict__ x) {
+  project_body(g, T, x, blockIdx.x);
 }
 
 __global__ void zero_dirichlet_kernel(LevelGeom g, double* __restrict__ x) {
@@ -226,6 +241,103 @@ __global__ void fp64_probe_kernel(double* out, int iters, double a, double b) {
   out[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
 }
 
+// ---------------------------------------------------------------- batched variants
+__global__ void bt_restrict_kernel(const BatchSeg* __restrict__ segs, int nseg, int64_t dofsc, FeTables T,
+                                   const double* __restrict__ xf, double* __restrict__ xc) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= dofsc) return;
+  const int m = batch_find<BU_DOFC>(segs, nseg, u);
+  const LevelGeom gf = segs[m].g, gc = segs[m].gc;
+  restrict_body(gf, gc, T, xf + segs[m].off, xc + segs[m].offc, u - segs[m].u_dofc);
+}
+__global__ void bt_prolong_kernel(const BatchSeg* __restrict__ segs, int nseg, int64_t dofs, FeTables T,
+                                  const double* __restrict__ xc, double* __restrict__ xf) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= dofs) return;
+  const int m = batch_find<BU_DOF>(segs, nseg, u);
+  const LevelGeom gf = segs[m].g, gc = segs[m].gc;
+  prolong_body(gf, gc, T, xc + segs[m].offc, xf + segs[m].off, u - segs[m].u_dof);
+}
+__global__ void bt_project_kernel(const BatchSeg* __restrict__ segs, int nseg, FeTables T, double* __restrict__ x,
+                                  int absolute) {
+  const int m = batch_find<BU_TBLK>(segs, nseg, blockIdx.x);
+  const LevelGeom g = segs[m].g;
+  double* base = absolute ? segs[m].ya : x + segs[m].off;
+  project_body(g, T, base, blockIdx.x - segs[m].u_tblk);
+}
+__global__ void bt_splitmix_kernel(const BatchSeg* __restrict__ segs, int nseg, int64_t dofs,
+                                   const int64_t* __restrict__ seeds, double* __restrict__ x) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= dofs) return;
+  const int m = batch_find<BU_DOF>(segs, nseg, u);
+  const LevelGeom g = segs[m].g;
+  const int64_t idx = u - segs[m].u_dof;
+  uint64_t z = (uint64_t)seeds[m] + (uint64_t)(idx + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  double v = 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+  const int sp = int(idx % g.S), nv = g.nv, nv2 = nv * nv;
+  if (sp < 2 * nv2) {
+    const int t = sp % nv2, gx = t % nv, gy = t / nv;
+    if (gx == 0 || gy == 0 || gx == nv - 1 || gy == nv - 1) v = 0.0;
+  }
+  x[segs[m].off + idx] = v;
+}
+__global__ void bt_axpby_kernel(const BatchSeg* __restrict__ segs, int nseg, int64_t dofs, const double* __restrict__ a,
+                                double as, const double* __restrict__ x, const double* __restrict__ b, double bs_,
+                                double* __restrict__ y) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= dofs) return;
+  const int m = batch_find<BU_DOF>(segs, nseg, u);
+  const int64_t i = segs[m].off + (u - segs[m].u_dof);
+  const double am = a ? a[m] : as, bm = b ? b[m] : bs_;
+  y[i] = fma(am, x[i], bm * y[i]);
+}
+__global__ void bt_copy_kernel(const BatchSeg* __restrict__ segs, int nseg, int64_t dofs, const double* __restrict__ x,
+                               double* __restrict__ y) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= dofs) return;
+  const int m = batch_find<BU_DOF>(segs, nseg, u);
+  const int64_t i = segs[m].off + (u - segs[m].u_dof);
+  y[i] = x[i];
+}
+__global__ void bt_fill_abs_kernel(const BatchSeg* __restrict__ segs, int nseg, int64_t dofs, double v) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= dofs) return;
+  const int m = batch_find<BU_DOF>(segs, nseg, u);
+  segs[m].ya[u - segs[m].u_dof] = v;
+}
+constexpr int kBtDotBlocks = 64;
+// grid (kBtDotBlocks, nseg): fixed strided partial sums per member, then a fixed tree
+__global__ void bt_dot_stage1(const BatchSeg* __restrict__ segs, const double* __restrict__ x,
+                              const double* __restrict__ y, double* __restrict__ partials) {
+  __shared__ double sbuf[256];
+  const int m = blockIdx.y;
+  const int64_t n = segs[m].g.ndofs, off = segs[m].off;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)kBtDotBlocks * 256)
+    acc = fma(x[off + i], y[off + i], acc);
+  sbuf[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sbuf[threadIdx.x] += sbuf[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[m * kBtDotBlocks + blockIdx.x] = sbuf[0];
+}
+__global__ void bt_dot_stage2(const double* __restrict__ partials, double* __restrict__ out) {
+  __shared__ double sbuf[64];
+  const int m = blockIdx.x;
+  sbuf[threadIdx.x] = partials[m * kBtDotBlocks + threadIdx.x];
+  __syncthreads();
+  for (int st = 32; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sbuf[threadIdx.x] += sbuf[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[m] = sbuf[0];
+}
+
 inline unsigned grid_for(int64_t n, int threads) {
   const int64_t b = (n + threads - 1) / threads;
   return (unsigned)(b < 4 * 152 * 8 ? (b > 0 ? b : 1) : 4 * 152 * 8);
@@ -303,4 +415,55 @@ double measure_fp64_tflops(cudaStream_t s) {
   cudaFree(out);
   const double flops = 5.0 * blocks * threads * (double)iters * 8 * 2;
   return flops / (ms * 1e-3) / 1e12;
+}
+
+static unsigned nblocks(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+void bt_restrict(const BatchSeg* segs, int nseg, int64_t dofsc, const FeTables& T, const double* xf, double* xc,
+                 cudaStream_t s) {
+  if (dofsc <= 0) return;
+  bt_restrict_kernel<<<nblocks(dofsc), 256, 0, s>>>(segs, nseg, dofsc, T, xf, xc);
+  WR_LAUNCH_CHECK();
+}
+void bt_prolong_add(const BatchSeg* segs, int nseg, int64_t dofs, const FeTables& T, const double* xc, double* xf,
+                    cudaStream_t s) {
+  if (dofs <= 0) return;
+  bt_prolong_kernel<<<nblocks(dofs), 256, 0, s>>>(segs, nseg, dofs, T, xc, xf);
+  WR_LAUNCH_CHECK();
+}
+void bt_project_pressure(const BatchSeg* segs, int nseg, int64_t tblks, const FeTables& T, double* x, bool absolute,
+                         cudaStream_t s) {
+  if (tblks <= 0) return;
+  bt_project_kernel<<<(unsigned)tblks, 256, 0, s>>>(segs, nseg, T, x, absolute ? 1 : 0);
+  WR_LAUNCH_CHECK();
+}
+void bt_splitmix(const BatchSeg* segs, int nseg, int64_t dofs, const int64_t* seeds, double* x, cudaStream_t s) {
+  if (dofs <= 0) return;
+  bt_splitmix_kernel<<<nblocks(dofs), 256, 0, s>>>(segs, nseg, dofs, seeds, x);
+  WR_LAUNCH_CHECK();
+}
+void bt_axpby(const BatchSeg* segs, int nseg, int64_t dofs, const double* a, double as, const double* x,
+              const double* b, double bs_, double* y, cudaStream_t s) {
+  if (dofs <= 0) return;
+  bt_axpby_kernel<<<nblocks(dofs), 256, 0, s>>>(segs, nseg, dofs, a, as, x, b, bs_, y);
+  WR_LAUNCH_CHECK();
+}
+void bt_copy(const BatchSeg* segs, int nseg, int64_t dofs, const double* x, double* y, cudaStream_t s) {
+  if (dofs <= 0) return;
+  bt_copy_kernel<<<nblocks(dofs), 256, 0, s>>>(segs, nseg, dofs, x, y);
+  WR_LAUNCH_CHECK();
+}
+void bt_fill_abs(const BatchSeg* segs, int nseg, int64_t dofs, double v, cudaStream_t s) {
+  if (dofs <= 0) return;
+  bt_fill_abs_kernel<<<nblocks(dofs), 256, 0, s>>>(segs, nseg, dofs, v);
+  WR_LAUNCH_CHECK();
+}
+int bt_dot_blocks() { return kBtDotBlocks; }
+void bt_dot(const BatchSeg* segs, int nseg, const double* x, const double* y, double* partials, double* out,
+            cudaStream_t s) {
+  if (nseg <= 0) return;
+  bt_dot_stage1<<<dim3(kBtDotBlocks, nseg), 256, 0, s>>>(segs, x, y, partials);
+  WR_LAUNCH_CHECK();
+  bt_dot_stage2<<<nseg, kBtDotBlocks, 0, s>>>(partials, out);
+  WR_LAUNCH_CHECK();
 }

@@ -102,11 +102,16 @@ inline int patch_npg(int k) { return 2 * k - 1; }
 inline int patch_ms(int k) { return 2 * patch_nvg(k) * patch_nvg(k) + patch_npg(k) * patch_npg(k); }
 // Elements of one stored ms x ms factor block, padded to a multiple of 16 bytes
 // (the granule of the bulk copies that stream the blocks into shared memory).
-inline int64_t factor_block_elems(int k, int precision) {
-  const int64_t e = (int64_t)patch_ms(k) * patch_ms(k);
-  const int64_t g = precision == WR_FP32 ? 4 : 2;
+inline int factor_elem_bytes(int precision) { return precision == WR_FP32 ? 4 : precision == WR_BF16 ? 2 : 8; }
+inline int64_t block_elems(int ms, int precision) {
+  const int64_t e = (int64_t)ms * ms;
+  const int64_t g = precision == WR_FP32 ? 4 : precision == WR_BF16 ? 8 : 2;
   return (e + g - 1) / g * g;
 }
+inline int64_t factor_block_elems(int k, int precision) { return block_elems(patch_ms(k), precision); }
+// Slot count per temporal DoF of the coarse block: the patch shape holds the
+// 2x2 coarse mesh; the 3x3 coarse mesh of Q2/Q1 needs 2*5^2 + 4^2 = 66 slots.
+inline int coarse_ms(int k, int n_coarse) { return n_coarse == 2 ? patch_ms(k) : 2 * 25 + 16; }
 
 // A dense block of the smoother or of the coarse solve: the velocity slots form
 // an nvg x nvg grid of global velocity nodes from (vx0, vy0), the pressure
@@ -119,6 +124,51 @@ struct BlockSet {
 };
 
 FeTables build_tables(int k, int q);
+// Largest real part of the eigenvalues of the leading mm x mm block of an upper
+// Hessenberg matrix stored row-major with row stride ld (shifted complex QR).
+double hessenberg_max_real_eig(const std::vector<double>& H, int mm, int ld);
+
+// ---------------------------------------------------------------- batched launches
+// One member of a batched launch at one level depth (0 = every member's finest
+// level).  Vectors of all members at a depth live in one arena per role; a
+// member's vectors start at `off` (and at `offc` in the next-coarser depth's
+// arenas).  The u_* fields are exclusive prefix sums of the work units of the
+// members before this one, for each kind of batched kernel; kernels find their
+// member by binary search on the prefix that matches their unit.
+struct BatchSeg {
+  LevelGeom g;           // geometry at this depth
+  LevelGeom gc;          // geometry one level coarser (transfers); unused at the coarsest level
+  BlockSet bs;           // the patch set (kind 0) or the coarse block (kind 1)
+  PhysParams ph;
+  int member;
+  int64_t off, offc;     // vector offsets at this depth / the next coarser depth
+  int64_t off_ye, off_yp;// offsets in the element-contribution and patch-output scratch arenas
+  const double* W;       // linearisation point of this level
+  const void* factors;   // stored factors of this level (coarse factors for kind 1)
+  double* xa;            // absolute right-hand side pointer (coarse-solve tables)
+  double* ya;            // absolute output pointer (coarse-solve tables)
+  int64_t u_elem, u_dof, u_dofc, u_patch, u_tblk;  // prefixes: element units, DoFs, coarse DoFs, patches, temporal blocks
+};
+
+enum BatchUnit { BU_ELEM = 0, BU_DOF = 1, BU_DOFC = 2, BU_PATCH = 3, BU_TBLK = 4 };
+
+// last member whose prefix of `kind` is <= u (members with no units are skipped by construction)
+#ifdef __CUDACC__
+template <int KIND>
+__device__ __forceinline__ int batch_find(const BatchSeg* __restrict__ segs, int nseg, int64_t u) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int64_t b = KIND == BU_ELEM ? segs[mid].u_elem : KIND == BU_DOF ? segs[mid].u_dof
+                    : KIND == BU_DOFC ? segs[mid].u_dofc : KIND == BU_PATCH ? segs[mid].u_patch : segs[mid].u_tblk;
+    if (b <= u) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+#endif
+
+// element units of a member level: ceil(cells / 4) x slabs (4 = elements per element-kernel CTA)
+inline int64_t elem_units(const LevelGeom& g) { return (int64_t)((g.ncells() + 3) / 4) * g.N; }
 
 // ---------------------------------------------------------------- kernels
 void launch_residual(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* U,
@@ -159,3 +209,31 @@ int dot_partials_size();
 void vec_dot_dev(int64_t n, const double* x, const double* y, double* partials, double* out,
                  cudaStream_t s);
 double measure_fp64_tflops(cudaStream_t s);
+
+// batched kernels (one launch for every member in `segs`; base pointers are arenas)
+void bt_jacobian(int k, int q, const BatchSeg* segs, int nseg, int64_t units, int64_t dofs, const FeTables& T,
+                 const double* x, double* y, double* ye, cudaStream_t s);
+void bt_residual(int k, int q, const BatchSeg* segs, int nseg, int64_t units, int64_t dofs, const FeTables& T,
+                 const double* U, double* F, double* ye, cudaStream_t s);
+// coarse_n = 0: patch smoother (scatter into `out`); 2 or 3: coarse block solves of that coarse mesh
+void bt_block_apply(int k, int q, int precision, const BatchSeg* segs, int nseg, int64_t items, int64_t dofs,
+                    const FeTables& T, const double* r, double* out, double* yp, int* err, int coarse_n,
+                    cudaStream_t s);
+void bt_restrict(const BatchSeg* segs, int nseg, int64_t dofsc, const FeTables& T, const double* xf, double* xc,
+                 cudaStream_t s);
+void bt_prolong_add(const BatchSeg* segs, int nseg, int64_t dofs, const FeTables& T, const double* xc, double* xf,
+                    cudaStream_t s);
+void bt_project_pressure(const BatchSeg* segs, int nseg, int64_t tblks, const FeTables& T, double* x, bool absolute,
+                         cudaStream_t s);
+void bt_splitmix(const BatchSeg* segs, int nseg, int64_t dofs, const int64_t* seeds, double* x, cudaStream_t s);
+void bt_boundary(const BatchSeg* segs, int nseg, int64_t dofs, const FeTables& T, double* U, cudaStream_t s);
+// y = a_m x + b_m y per member (a_m, b_m device arrays indexed by segment, or scalars if null)
+void bt_axpby(const BatchSeg* segs, int nseg, int64_t dofs, const double* a, double as, const double* x,
+              const double* b, double bs_, double* y, cudaStream_t s);
+void bt_copy(const BatchSeg* segs, int nseg, int64_t dofs, const double* x, double* y, cudaStream_t s);
+// per-member dot products into out[nseg]; partials holds nseg * bt_dot_blocks() doubles
+// segs[m].ya[i] = v for i < segs[m].g.ndofs (absolute pointers; BU_DOF prefix)
+void bt_fill_abs(const BatchSeg* segs, int nseg, int64_t dofs, double v, cudaStream_t s);
+int bt_dot_blocks();
+void bt_dot(const BatchSeg* segs, int nseg, const double* x, const double* y, double* partials, double* out,
+            cudaStream_t s);

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libwrmg.so")
 
 WR_OK = 0
 WR_ERR_ARG, WR_ERR_NOMEM, WR_ERR_CUDA, WR_ERR_NOT_CONVERGED, WR_ERR_TIMEOUT, WR_ERR_NAN, WR_ERR_STATE = range(1, 8)
-WR_FP64, WR_FP32 = 0, 1
+WR_FP64, WR_FP32, WR_BF16 = 0, 1, 2
 _STATUS = {1: "WR_ERR_ARG", 2: "WR_ERR_NOMEM", 3: "WR_ERR_CUDA", 4: "WR_ERR_NOT_CONVERGED",
            5: "WR_ERR_TIMEOUT", 6: "WR_ERR_NAN", 7: "WR_ERR_STATE"}
 
@@ -86,6 +86,18 @@ _SIGS = {
     "wr_measure_fp64_tflops": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "wr_launch_count": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64)]),
     "wr_apply_jacobian_static": (ctypes.c_int, [ctypes.POINTER(Problem), _P, _P, _P, _P]),
+    "wr_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(Problem),
+                                       ctypes.POINTER(Options), _P]),
+    "wr_batch_destroy": (ctypes.c_int, [_P]),
+    "wr_batch_last_error": (ctypes.c_char_p, [_P]),
+    "wr_batch_ndofs": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
+    "wr_batch_device_bytes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "wr_batch_initial_guess": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p)]),
+    "wr_batch_linearise": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p)]),
+    "wr_batch_get_lambda": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "wr_batch_vcycle": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p)]),
+    "wr_batch_vcycle_resident": (ctypes.c_int, [_P]),
+    "wr_batch_solve": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Stats)]),
     "wr_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "wr_profile_smoother": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int)]),

@@ -25,8 +25,9 @@ CASES = [
     inputs.fourier_small(n=4, k=1, q=1, N=3, nu=0.02),
     inputs.fourier_small(n=4, k=2, q=1, N=2, nu=0.01),
     inputs.fourier_small(n=4, k=2, q=0, N=2, nu=0.05),
+    inputs.fourier_small(n=12, k=1, q=1, N=2, nu=0.02, n_coarse=3),   # 3x3 coarse block
 ]
-IDS = [w.name for w in CASES]
+IDS = [w.name + f"_c{w.n_coarse}" for w in CASES]
 
 
 def rel(a, b):
