@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--n", type=int, default=64, help="mesh (smaller only for profiling captures)")
     ap.add_argument("--slabs", type=int, default=64, help="time slabs (fewer only for profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="cycle", choices=["cycle", "precision"],
+    ap.add_argument("--members", type=int, default=256, help="batch form: number of solves")
+    ap.add_argument("--form", default="cycle", choices=["cycle", "precision", "batch"],
                     help="cycle: the V(2,2) throughput line (default); precision: the FP64/FP32/BF16 "
                          "solves of the 128x128 Q2/Q1 DG(0) 128-slab workload")
     return ap.parse_args()
@@ -383,12 +384,87 @@ def run_precision_form(args):
     print(json.dumps(out), flush=True)
 
 
+def run_batch_form(args):
+    """Batching form: independent Q2/Q1 DG(0) solves of uneven sizes in one lock-step
+    batch (FP32 smoother, FP64 residual and Krylov).  Reports the batched V(2,2)
+    cycle throughput (DoFs of every member per second), the batched solve to 1e-8
+    (solves/s), and the plain FP64 method run request by request on a sample."""
+    import numpy as np
+    import torch
+    from paper_2407_13997_gb300 import inputs, wrmg
+    torch.cuda.set_device(0)
+    ws = inputs.batching_workloads(args.members, seed=1)
+    total = sum(w.ndofs() for w in ws)
+    out = {"form": "batch", "members": len(ws), "total_ndofs": total,
+           "mesh_mix": {str(n): sum(1 for w in ws if w.n_fine == n) for n in (8, 16, 24, 32, 48)}}
+    t0 = time.perf_counter()
+    batch = wrmg.Batch(ws, wrmg.default_options(precision=wrmg.WR_FP32))
+    torch.cuda.synchronize()
+    out["create_s"] = time.perf_counter() - t0
+    out["device_bytes"] = batch.device_bytes()
+    Ws = [torch.from_numpy(inputs.forcing_shaped_iterate(w)).cuda() for w in ws]
+    t0 = time.perf_counter()
+    batch.linearise(Ws)
+    torch.cuda.synchronize()
+    out["linearise_s"] = time.perf_counter() - t0
+    rng = np.random.default_rng(2)
+    bs = [torch.from_numpy(rng.standard_normal(w.ndofs())).cuda() for w in ws]
+    xs = batch.vectors()
+    batch.vcycle(bs, xs)
+    for _ in range(2):
+        batch.vcycle_resident()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = wrmg.launch_count()
+    e0.record()
+    for _ in range(args.steps):
+        batch.vcycle_resident()
+    e1.record()
+    torch.cuda.synchronize()
+    cyc = e0.elapsed_time(e1) / args.steps
+    out["cycle_ms"] = cyc
+    out["dof_per_s_per_cycle"] = total / cyc * 1e3
+    out["launches_per_cycle"] = (wrmg.launch_count() - launches0) / args.steps
+    del Ws, bs, xs
+    Us = batch.vectors()
+    batch.initial_guess(Us)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = batch.solve(Us, check=False)
+    torch.cuda.synchronize()
+    solve_s = time.perf_counter() - t0
+    conv = [s["residuals"][-1] <= 1e-8 * s["residuals"][0] for s in st]
+    out["batched_solve"] = {"seconds": solve_s, "solves_per_s": len(ws) / solve_s, "converged": int(sum(conv)),
+                            "newton_max": max(s["newton_its"] for s in st),
+                            "fgmres_total_mean": float(np.mean([sum(s["gmres"]) for s in st]))}
+    batch.close()
+    del Us
+    torch.cuda.empty_cache()
+    # the plain FP64 method, request by request, on a seeded sample of the same draws
+    sample = ws[:max(1, min(8, len(ws)))]
+    t0 = time.perf_counter()
+    for w in sample:
+        ctx = wrmg.Context(w)
+        U = ctx.vector()
+        ctx.initial_guess(U)
+        ctx.solve(U, check=False)
+        ctx.close()
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t0
+    out["sequential_fp64"] = {"sample": len(sample), "seconds": seq, "solves_per_s": len(sample) / seq,
+                              "ndofs_sample": sum(w.ndofs() for w in sample)}
+    out["solves_per_s_ratio_batched_vs_sequential_fp64"] = out["batched_solve"]["solves_per_s"] / (len(sample) / seq)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.form == "precision":
         run_precision_form(args)
+    elif args.form == "batch":
+        run_batch_form(args)
     else:
         run_ours(args)
 

@@ -115,3 +115,20 @@ def forcing_shaped_iterate(w, scale=1.0):
     mag = max(np.abs(ux).max(), np.abs(uy).max(), 1e-300)
     blk = np.concatenate([ux.ravel(), uy.ravel(), np.zeros(np_ * np_)]) * (scale / mag)
     return np.tile(blk, w.N * (w.q + 1))
+
+
+def batching_workloads(count=256, seed=1):
+    """Independent Q2/Q1 DG(0) solves with uneven sizes: n uniform in {8, 16, 24, 32, 48}
+    (24 and 48 coarsen to 3x3), N uniform in {8, 16, 32, 64}, nu log-uniform in
+    [1e-3, 1e-1], each with its own Fourier forcing seed (1000 * seed + i)."""
+    rng = np.random.default_rng(seed)
+    ns = rng.choice([8, 16, 24, 32, 48], size=count)
+    Ns = rng.choice([8, 16, 32, 64], size=count)
+    nus = 10.0 ** rng.uniform(-3.0, -1.0, size=count)
+    out = []
+    for i in range(count):
+        n = int(ns[i])
+        mx, my, amp = fourier_forcing(1000 * seed + i)
+        out.append(Workload(f"batch{seed}_{i}_n{n}_N{int(Ns[i])}", n, 3 if n % 3 == 0 else 2, 1, 0, int(Ns[i]),
+                            1.0, float(nus[i]), 1.0, KIND_FOURIER, False, mx, my, amp))
+    return out

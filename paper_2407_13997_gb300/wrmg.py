@@ -298,3 +298,97 @@ class Context:
         if check:
             self._check(rc)
         return st.as_dict()
+
+
+class Batch:
+    """Many independent solves advanced in lock step (one k and q per batch)."""
+
+    def __init__(self, workloads, options=None, stream=None):
+        import torch
+        lib = load()
+        self._lib = lib
+        self.workloads = list(workloads)
+        n = len(self.workloads)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self._keep = []
+        probs = (Problem * n)()
+        for i, w in enumerate(self.workloads):
+            mx = np.ascontiguousarray(w.mx, dtype=np.int32)
+            my = np.ascontiguousarray(w.my, dtype=np.int32)
+            amp = np.ascontiguousarray(w.amp, dtype=np.float64)
+            self._keep += [mx, my, amp]
+            probs[i] = Problem(w.n_fine, w.n_coarse, w.k, w.q, w.N, w.T, w.nu, w.conv, w.kind, int(w.steady),
+                               len(amp), mx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                               my.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                               amp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        self.options = options if options is not None else default_options()
+        h = ctypes.c_void_p()
+        rc = lib.wr_batch_create(ctypes.byref(h), n, probs, ctypes.byref(self.options), ctypes.c_void_p(stream))
+        self._h = h
+        if rc != WR_OK:
+            msg = lib.wr_batch_last_error(h).decode() if h.value else "wr_batch_create failed"
+            if h.value:
+                lib.wr_batch_destroy(h)
+            self._h = ctypes.c_void_p()
+            raise WrmgError(rc, msg)
+        self.n = n
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.wr_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != WR_OK:
+            raise WrmgError(rc, self._lib.wr_batch_last_error(self._h).decode())
+
+    @staticmethod
+    def _ptrs(ts):
+        for t in ts:
+            _ptr(t)
+        return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+    def ndofs(self, m):
+        out = ctypes.c_int64()
+        self._check(self._lib.wr_batch_ndofs(self._h, m, ctypes.byref(out)))
+        return out.value
+
+    def device_bytes(self):
+        out = ctypes.c_int64()
+        self._check(self._lib.wr_batch_device_bytes(self._h, ctypes.byref(out)))
+        return out.value
+
+    def vectors(self):
+        import torch
+        return [torch.zeros(self.ndofs(m), dtype=torch.float64, device="cuda") for m in range(self.n)]
+
+    def initial_guess(self, Us):
+        self._check(self._lib.wr_batch_initial_guess(self._h, self._ptrs(Us)))
+
+    def linearise(self, Ws):
+        self._check(self._lib.wr_batch_linearise(self._h, self._ptrs(Ws)))
+
+    def get_lambda(self, m, level):
+        out = ctypes.c_double()
+        self._check(self._lib.wr_batch_get_lambda(self._h, m, level, ctypes.byref(out)))
+        return out.value
+
+    def vcycle(self, bs, xs):
+        self._check(self._lib.wr_batch_vcycle(self._h, self._ptrs(bs), self._ptrs(xs)))
+
+    def vcycle_resident(self):
+        self._check(self._lib.wr_batch_vcycle_resident(self._h))
+
+    def solve(self, Us, check=True):
+        st = (Stats * self.n)()
+        rc = self._lib.wr_batch_solve(self._h, self._ptrs(Us), st)
+        if check:
+            self._check(rc)
+        return [s.as_dict() for s in st]
