@@ -191,9 +191,21 @@ class Discretisation:
         return sp.coo_matrix((vals.ravel(), (r, c)), shape=shape).tocsr()
 
     def _linear_matrices(self):
-        """Spatial S x S matrices: velocity mass Mv, velocity stiffness Kv and the
-        symmetric pressure coupling G (rows of velocity tests against pressure
-        trials: (chi_j, d_c phi_i); rows of pressure tests: its transpose)."""
+        """Spatial S x S matrices of the whole mesh: velocity mass Mv, velocity
+        stiffness Kv and the symmetric pressure coupling G (rows of velocity tests
+        against pressure trials: (chi_j, d_c phi_i); rows of pressure tests: its
+        transpose)."""
+        self.Mv, self.Kv, self.G = self.linear_matrices_on(np.arange(self.n * self.n))
+        w = self.wq2
+        nc = self.n * self.n
+        Mp = self._assemble(self.cell_pnodes, self.cell_pnodes,
+                            np.broadcast_to(np.einsum("iq,jq,q->ij", self.Vp, self.Vp, w),
+                                            (nc, (self.k + 1) ** 2, (self.k + 1) ** 2)),
+                            (self.np_ ** 2, self.np_ ** 2))
+        self.pressure_weights = np.asarray(Mp.sum(axis=1)).ravel()   # int chi_j
+
+    def linear_matrices_on(self, cells):
+        """(Mv, Kv, G) assembled over the cells with ids in ``cells`` only."""
         S, nv2 = self.S, self.nv ** 2
         w = self.wq2
         Me = np.einsum("iq,jq,q->ij", self.Vv, self.Vv, w)
@@ -201,26 +213,18 @@ class Discretisation:
             "iq,jq,q->ij", self.Dyv, self.Dyv, w)
         Gx = np.einsum("iq,jq,q->ij", self.Dxv, self.Vp, w)   # (vel i, pres j)
         Gy = np.einsum("iq,jq,q->ij", self.Dyv, self.Vp, w)
-        nc = self.n * self.n
-        mats = {}
+        cells = np.asarray(cells, dtype=np.int64)
+        nc = len(cells)
         blocks_M, blocks_K, blocks_G = [], [], []
         for c in range(2):
-            rv = self.cell_vnodes + c * nv2
+            rv = self.cell_vnodes[cells] + c * nv2
             blocks_M.append(self._assemble(rv, rv, np.broadcast_to(Me, (nc,) + Me.shape), (S, S)))
             blocks_K.append(self._assemble(rv, rv, np.broadcast_to(Ke, (nc,) + Ke.shape), (S, S)))
             Ge = Gx if c == 0 else Gy
-            rp = self.cell_pnodes + self.off_p
+            rp = self.cell_pnodes[cells] + self.off_p
             blocks_G.append(self._assemble(rv, rp, np.broadcast_to(Ge, (nc,) + Ge.shape), (S, S)))
-        self.Mv = blocks_M[0] + blocks_M[1]
-        self.Kv = blocks_K[0] + blocks_K[1]
         G = blocks_G[0] + blocks_G[1]
-        self.G = (G + G.T).tocsr()
-        Mp = self._assemble(self.cell_pnodes, self.cell_pnodes,
-                            np.broadcast_to(np.einsum("iq,jq,q->ij", self.Vp, self.Vp, w),
-                                            (nc, (self.k + 1) ** 2, (self.k + 1) ** 2)),
-                            (self.np_ ** 2, self.np_ ** 2))
-        self.pressure_weights = np.asarray(Mp.sum(axis=1)).ravel()   # int chi_j
-        del mats
+        return blocks_M[0] + blocks_M[1], blocks_K[0] + blocks_K[1], (G + G.T).tocsr()
 
     # ------------------------------------------------------------ fields at quadrature points
     def _vel_at_q(self, uc):
@@ -229,13 +233,15 @@ class Discretisation:
         loc = uc[self.cell_vnodes]
         return loc @ self.Vv, loc @ self.Dxv, loc @ self.Dyv
 
-    def convection_matrix(self, w):
+    def convection_matrix(self, w, cells=None):
         """Spatial S x S matrix of the linearised convection about the spatial
         velocity field w (a spatial block): rows (c, i), cols (d, j),
-        int phi_i [ delta_cd (w.grad) phi_j + phi_j d_d w_c ]."""
+        int phi_i [ delta_cd (w.grad) phi_j + phi_j d_d w_c ]; over every cell, or
+        over the cells with ids in ``cells`` only."""
         S, nv2 = self.S, self.nv ** 2
-        wx, wxx, wxy = self._vel_at_q(w[:nv2])
-        wy, wyx, wyy = self._vel_at_q(w[nv2:2 * nv2])
+        cells = np.arange(self.n * self.n) if cells is None else np.asarray(cells, dtype=np.int64)
+        wx, wxx, wxy = (f[cells] for f in self._vel_at_q(w[:nv2]))
+        wy, wyx, wyy = (f[cells] for f in self._vel_at_q(w[nv2:2 * nv2]))
         W = self.wq2
         adv = wx[:, None, :] * self.Dxv[None] + wy[:, None, :] * self.Dyv[None]   # (cell, j, q)
         base = np.einsum("iq,cjq,q->cij", self.Vv, adv, W)
@@ -247,7 +253,8 @@ class Discretisation:
                 vals = mass_w(grads[c][d])
                 if c == d:
                     vals = vals + base
-                A = self._assemble(self.cell_vnodes + c * nv2, self.cell_vnodes + d * nv2, vals, (S, S))
+                A = self._assemble(self.cell_vnodes[cells] + c * nv2, self.cell_vnodes[cells] + d * nv2, vals,
+                                   (S, S))
                 out = A if out is None else out + A
         return out
 
@@ -377,6 +384,21 @@ class Discretisation:
         E = np.zeros((self.nt, self.nt))
         E[:, self.nt - 1] = -tm.tau0
         L = sp.kron(E, self.Mv)
+        return D.tocsr(), L.tocsr()
+
+    def local_slab_blocks(self, W, slab, cells):
+        """``slab_blocks`` assembled over the cells with ids in ``cells`` only: the
+        space-time problem restricted to those cells (used for the patch matrix
+        assembled over a patch's own cells)."""
+        tm, dt, nu, cv = self.tm, self.dt, self.pb.nu, self.pb.conv
+        Wn = self._slab(W, slab)
+        Mv, Kv, G = self.linear_matrices_on(cells)
+        D = sp.kron(tm.Kt, Mv) + dt * (nu * sp.kron(tm.Wt, Kv) + sp.kron(tm.Wt, G))
+        for c in range(self.nt):
+            D = D + dt * cv * sp.kron(tm.T3[:, :, c], self.convection_matrix(Wn[c], cells))
+        E = np.zeros((self.nt, self.nt))
+        E[:, self.nt - 1] = -tm.tau0
+        L = sp.kron(E, Mv)
         return D.tocsr(), L.tocsr()
 
     def jacobian(self, W):

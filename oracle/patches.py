@@ -13,13 +13,15 @@ and the list is compacted.
 Patch-local order, per slab: temporal DoF a outermost, then the u_x nodes
 (y-major, x fastest), then u_y, then the pressure nodes.  Patch id = J*(n+1)+I.
 
-Patch matrix: the principal submatrix A_i = J[P_i, P_i] of the assembled
-space-time Jacobian (PCASM-style reading).  Because J is block lower
+Patch matrix: by default the principal submatrix A_i = J[P_i, P_i] of the
+assembled space-time Jacobian (PCASM-style reading (A)); optionally (reading
+(B)) the space-time Jacobian assembled over the patch's own 2 x 2 cells only,
+restricted to P_i (subdiagonal included).  Because J is block lower
 bidiagonal in slabs, the patch system is the block lower bidiagonal system of
 Eq. waveform_patch_solve and is solved by forward substitution over slabs,
 y_n = A_nn^{-1} (r_n - A_{n,n-1} y_{n-1}), each A_nn by dense LU with partial
 pivoting.  The relaxation is M^{-1} r = sum_i R_i^T (w_i * A_i^{-1} R_i r),
-w = 1 (plain additive).
+w = 1 (plain additive) or w = 1 / (number of patches holding the DoF).
 """
 import numpy as np
 import scipy.linalg as sla
@@ -56,19 +58,56 @@ def patch_dofs(disc, patch, slab):
     return np.concatenate([disc.block(slab, a) + sidx for a in range(disc.nt)])
 
 
-class PatchSmoother:
-    """The waveform Vanka+star relaxation M^{-1} for one level's J."""
+def patch_cells(disc, patch):
+    """Ids (J * n + I) of the cells of the 2 x 2 block around the patch's vertex."""
+    n1 = disc.n + 1
+    I, J = patch % n1, patch // n1
+    return np.array([cy * disc.n + cx for cy in (J - 1, J) for cx in (I - 1, I)
+                     if 0 <= cx < disc.n and 0 <= cy < disc.n], dtype=np.int64)
 
-    def __init__(self, disc, J):
+
+def multiplicity_weights(disc):
+    """w = 1 / (number of patches whose index list holds the DoF); 0 on Dirichlet DoFs."""
+    count = np.zeros(disc.ndofs)
+    for i in range((disc.n + 1) ** 2):
+        for s in range(disc.N):
+            count[patch_dofs(disc, i, s)] += 1.0
+    w = np.zeros(disc.ndofs)
+    w[count > 0] = 1.0 / count[count > 0]
+    return w
+
+
+class PatchSmoother:
+    """The waveform Vanka+star relaxation M^{-1} for one level's J.
+
+    local=False: patch matrices are principal submatrices of J (reading (A));
+    local=True: they are assembled over each patch's own cells about the
+    iterate W (reading (B)); W is then required."""
+
+    def __init__(self, disc, J, local=False, W=None):
         self.disc, self.J = disc, J
         self.npatch = (disc.n + 1) ** 2
         self.idx = [[patch_dofs(disc, i, s) for s in range(disc.N)] for i in range(self.npatch)]
-        # dense diagonal blocks A_nn (principal submatrices), factored by partial-pivot LU
-        self.lu = [[sla.lu_factor(J[ix][:, ix].toarray(), check_finite=False) for ix in row]
-                   for row in self.idx]
-        # subdiagonal blocks A_{n,n-1} of the patch system
-        self.sub = [[None] + [J[row[s]][:, row[s - 1]].toarray() for s in range(1, disc.N)]
-                    for row in self.idx]
+        if not local:
+            diag = [[J[ix][:, ix].toarray() for ix in row] for row in self.idx]
+            sub = [[None] + [J[row[s]][:, row[s - 1]].toarray() for s in range(1, disc.N)] for row in self.idx]
+        else:
+            diag, sub = [], []
+            for i, row in enumerate(self.idx):
+                cells = patch_cells(disc, i)
+                # patch indices within one slab's (q+1) S block
+                loc = row[0] - disc.block(0, 0)
+                drow, srow = [], [None]
+                for s in range(disc.N):
+                    D, L = disc.local_slab_blocks(W, s, cells)
+                    drow.append(D[loc][:, loc].toarray())
+                    if s > 0:
+                        srow.append(L[loc][:, loc].toarray())
+                diag.append(drow)
+                sub.append(srow)
+        # dense diagonal blocks A_nn factored by partial-pivot LU; subdiagonal blocks A_{n,n-1}
+        self.lu = [[sla.lu_factor(A, check_finite=False) for A in row] for row in diag]
+        self.sub = sub
 
     def patch_solve(self, i, r):
         """y_i = A_i^{-1} R_i r by forward substitution over slabs (Eq. waveform_patch_solve)."""
