@@ -45,8 +45,14 @@ def parse():
     ap.add_argument("--n", type=int, default=64, help="mesh (smaller only for profiling captures)")
     ap.add_argument("--slabs", type=int, default=64, help="time slabs (fewer only for profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--members", type=int, default=256, help="batch form: number of solves")
-    ap.add_argument("--form", default="cycle", choices=["cycle", "precision", "batch"],
+    ap.add_argument("--members", type=int, default=None,
+                    help="batch form: number of solves (256); serve form: number of requests (32)")
+    ap.add_argument("--rates", default="10,100,500", help="serve form: Poisson arrival rates (requests/s)")
+    ap.add_argument("--inflight", type=int, default=8, help="serve form: solves in flight at most")
+    ap.add_argument("--budget-gb", type=float, default=96.0, help="serve form: device-memory budget")
+    ap.add_argument("--full-mix", action="store_true",
+                    help="serve form: draw n and N from {16, 32, 64} (default {16, 32})")
+    ap.add_argument("--form", default="cycle", choices=["cycle", "precision", "batch", "serve"],
                     help="cycle: the V(2,2) throughput line (default); precision: the FP64/FP32/BF16 "
                          "solves of the 128x128 Q2/Q1 DG(0) 128-slab workload")
     return ap.parse_args()
@@ -393,7 +399,7 @@ def run_batch_form(args):
     import torch
     from paper_2407_13997_gb300 import inputs, wrmg
     torch.cuda.set_device(0)
-    ws = inputs.batching_workloads(args.members, seed=1)
+    ws = inputs.batching_workloads(args.members or 256, seed=1)
     total = sum(w.ndofs() for w in ws)
     out = {"form": "batch", "members": len(ws), "total_ndofs": total,
            "mesh_mix": {str(n): sum(1 for w in ws if w.n_fine == n) for n in (8, 16, 24, 32, 48)}}
@@ -457,6 +463,96 @@ def run_batch_form(args):
     print(json.dumps(out), flush=True)
 
 
+def run_serve_form(args):
+    """Serving form: a seeded Poisson stream of solve requests (Q2/Q1 DG(0) or Q3/Q2
+    DG(1), nu log-uniform in [1e-3, 1e-1]) served by the native request loop with
+    FP32 factors and FP64 Newton/Krylov to rtol 1e-8, against the plain FP64 method
+    run request by request.  The FP64 arm is timed request by request (context
+    set-up, solve and the host copy of the solution) and its latencies follow from
+    those service times and the same arrivals through a single FIFO server."""
+    import numpy as np
+    import torch
+    from paper_2407_13997_gb300 import inputs, wrmg
+    torch.cuda.set_device(0)
+    grid = (16, 32, 64) if args.full_mix else (16, 32)
+    reqs = inputs.serving_workloads(args.members or 32, seed=2, ns=grid, slabs=grid)
+    rates = [float(r) for r in args.rates.split(",")]
+    o32 = wrmg.default_options(precision=wrmg.WR_FP32, newton_rtol=1e-8)
+    o64 = wrmg.default_options(precision=wrmg.WR_FP64, newton_rtol=1e-8)
+    out = {"form": "serve", "requests": len(reqs), "mesh_and_slab_grid": list(grid),
+           "total_ndofs": sum(w.ndofs() for w in reqs), "inflight_cap": args.inflight,
+           "budget_bytes": int(args.budget_gb * 2 ** 30), "options": "FP32 factors, FP64 Newton/FGMRES, rtol 1e-8"}
+    warm = inputs.serving_workloads(2, seed=99, ns=(16,), slabs=(16,))
+    for w in warm:                                    # module loading and first-launch set-up
+        for o in (o32, o64):
+            ctx = wrmg.Context(w, o)
+            U = ctx.vector()
+            ctx.initial_guess(U)
+            ctx.solve(U, check=False)
+            ctx.close()
+    torch.cuda.synchronize()
+    # plain FP64, request by request
+    service, refs = [], []
+    for w in reqs:
+        t0 = time.perf_counter()
+        ctx = wrmg.Context(w, o64)
+        U = ctx.vector()
+        ctx.initial_guess(U)
+        ctx.solve(U, check=False)
+        refs.append(U.cpu().numpy())
+        ctx.close()
+        service.append(time.perf_counter() - t0)
+        del U
+    torch.cuda.empty_cache()
+    out["sequential_fp64"] = {"service_s_total": sum(service), "service_s_median": statistics.median(service),
+                              "solves_per_s_saturated": len(reqs) / sum(service), "rates": {}}
+    out["rates"] = {}
+    errs = []
+    for rate in rates:
+        arr = inputs.poisson_arrivals(len(reqs), rate, seed=2)
+        end, lat = 0.0, []
+        for a, sv_t in zip(arr, service):             # the FIFO single server of the FP64 arm
+            end = max(a, end) + sv_t
+            lat.append(end - a)
+        out["sequential_fp64"]["rates"][str(int(rate))] = {
+            "solves_per_s": len(reqs) / (end - arr[0]), "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99))}
+        sv = wrmg.Server(out["budget_bytes"], args.inflight, o32)
+        tickets = [None] * len(reqs)
+
+        def feeder():
+            t0 = time.perf_counter()
+            for i, (a, w) in enumerate(zip(arr, reqs)):
+                dt = t0 + a - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                tickets[i] = sv.submit(w)
+
+        t_start = time.perf_counter()
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        res = [sv.poll(t) for t in tickets]
+        t_end = time.perf_counter()
+        st = sv.stats()
+        sv.close()
+        lat = [r[3] for r in res]
+        ok = sum(1 for r in res if r[0] == wrmg.WR_OK)
+        for r, ref in zip(res, refs):
+            if r[1] is not None:
+                errs.append(float(np.abs(r[1] - ref).max() / max(np.abs(ref).max(), 1e-300)))
+        out["rates"][str(int(rate))] = {
+            "solves_per_s": len(reqs) / (t_end - t_start - arr[0]), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "converged": ok, "peak_inflight": st["peak_inflight"],
+            "peak_bytes": st["peak_bytes"], "newton_total": sum(r[2]["newton_its"] for r in res),
+            "fgmres_total": sum(sum(r[2]["gmres"]) for r in res)}
+    out["max_rel_diff_vs_fp64_solution"] = max(errs) if errs else None
+    top = str(int(max(rates)))
+    out["solves_per_s_ratio_vs_sequential_fp64"] = (out["rates"][top]["solves_per_s"] /
+                                                    out["sequential_fp64"]["rates"][top]["solves_per_s"])
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -465,6 +561,8 @@ def main():
         run_precision_form(args)
     elif args.form == "batch":
         run_batch_form(args)
+    elif args.form == "serve":
+        run_serve_form(args)
     else:
         run_ours(args)
 

@@ -68,6 +68,15 @@ extern "C" {
 #define WR_FP32 1  /* FP32 factorisation, factors and smoother                              */
 #define WR_BF16 2  /* FP32 factorisation, BF16-stored factors, FP32 smoother arithmetic      */
 
+/* the patch matrix of the Vanka+star relaxation (wr_options.patch_assembly; Sec. 3
+ * defines the patch by its DoFs and leaves the matrix to the assembled operator) */
+#define WR_PATCH_SUBMATRIX 0  /* A_i = J[P_i, P_i], the principal submatrix of the assembled J   */
+#define WR_PATCH_LOCAL 1      /* the space-time Jacobian assembled over the patch's own 2x2
+                                 cells, restricted to P_i (diagonal and subdiagonal blocks)      */
+/* the additive scatter's weights (wr_options.scatter_weight) */
+#define WR_WEIGHT_ONE 0           /* y = sum_i R_i^T y_i (plain additive Schwarz)               */
+#define WR_WEIGHT_MULTIPLICITY 1  /* y = sum_i R_i^T (y_i / number of patches holding the DoF)  */
+
 typedef struct wr_ctx wr_ctx;
 
 typedef struct {
@@ -95,6 +104,8 @@ typedef struct {
     double eta_fixed;       /* (1e-4)                                                            */
     int gmres_restart;      /* (30)                                                              */
     int gmres_maxit;        /* total FGMRES iterations per Newton step (200)                     */
+    int patch_assembly;     /* WR_PATCH_SUBMATRIX (default) or WR_PATCH_LOCAL                    */
+    int scatter_weight;     /* WR_WEIGHT_ONE (default) or WR_WEIGHT_MULTIPLICITY                 */
 } wr_options;
 
 typedef struct {
@@ -115,6 +126,8 @@ void wr_default_options(wr_options *o);
  * = default stream).  Host arrays in *p are copied.  Errors: WR_ERR_ARG for
  * unsupported sizes, WR_ERR_NOMEM if the hierarchy does not fit. */
 int wr_create(wr_ctx **out, const wr_problem *p, const wr_options *o, void *cuda_stream);
+/* Device bytes wr_create would allocate for (*p, *o), without allocating. */
+int wr_estimate_bytes(const wr_problem *p, const wr_options *o, int64_t *out);
 int wr_destroy(wr_ctx *c);
 const char *wr_last_error(const wr_ctx *c);
 
@@ -218,6 +231,37 @@ int wr_batch_vcycle_resident(wr_batch *b);
 /* Newton-FGMRES-WRMG solve of every member from U[m] (in/out); st may be NULL
  * or an array of n wr_stats.  WR_ERR_NOT_CONVERGED if any member hits newton_maxit. */
 int wr_batch_solve(wr_batch *b, double *const *U, wr_stats *st);
+
+/* ------------------------------------------------------------------ serving
+ * A wr_server solves a stream of independent space-time problems.  Requests
+ * wait in arrival (FIFO) order; the head request is admitted as soon as fewer
+ * than max_inflight solves run and its device bytes (wr_estimate_bytes plus its
+ * solution vector) fit in what remains of mem_budget_bytes.  Each admitted
+ * request runs on its own host thread, CUDA stream and context (allocated on
+ * admission, freed on completion), so the solves in flight overlap on the GPU
+ * and a completion admits the next request at once.  A request larger than
+ * the whole budget completes with WR_ERR_NOMEM.  Results are the same as a
+ * wr_solve of that problem alone (deterministic kernels, per-stream state).
+ * The paper solves one problem at a time; serving is a service of this library.
+ *   o: the options every request is solved with (NULL: wr_default_options).
+ *   The server uses the device current at wr_server_create. */
+typedef struct wr_server wr_server;
+int wr_server_create(wr_server **out, int64_t mem_budget_bytes, int max_inflight, const wr_options *o);
+/* Waits for the solves in flight; requests still queued complete with WR_ERR_STATE. */
+int wr_server_destroy(wr_server *sv);
+/* Queues *p (copied, forcing modes included); U0_host is NULL (start from the
+ * Dirichlet data, like wr_initial_guess) or a host iterate of the finest
+ * level's length (copied).  *ticket identifies the request for wr_server_poll. */
+int wr_server_submit(wr_server *sv, const wr_problem *p, const double *U0_host, uint64_t *ticket);
+/* wait == 0: WR_ERR_STATE while the request is queued or running.  Once it has
+ * completed (wait != 0 blocks until then): copies the host solution into U_host
+ * (may be NULL), its statistics into *st and its latency, submission to
+ * completion in ms, into *latency_ms (either may be NULL), forgets the ticket
+ * and returns the solve's status (WR_OK, WR_ERR_NOT_CONVERGED, WR_ERR_NOMEM...).
+ * Unknown tickets: WR_ERR_ARG. */
+int wr_server_poll(wr_server *sv, uint64_t ticket, int wait, double *U_host, wr_stats *st, double *latency_ms);
+/* Largest device bytes admitted at once and largest number of solves in flight so far. */
+int wr_server_stats(wr_server *sv, int64_t *peak_bytes, int *peak_inflight);
 
 /* Total kernel launches made by this library in this process (all contexts). */
 int wr_launch_count(int64_t *out);

@@ -69,7 +69,7 @@ struct wr_batch {
   double *F = nullptr, *w = nullptr, *step = nullptr, *U = nullptr, *vb = nullptr, *vx = nullptr;
   double *partials = nullptr, *dres = nullptr, *hres = nullptr, *hcoef = nullptr, *dcoef = nullptr;
   int64_t* dseeds = nullptr;
-  int *derr = nullptr, *herr = nullptr;
+  int *derr = nullptr, *herr = nullptr, *fstat = nullptr;
   std::vector<char> active;
   std::vector<Table> smooth;  // per depth: members with a smoothing level there
   Table coarse2, coarse3, fine;
@@ -104,6 +104,8 @@ struct wr_batch {
     bs.nvg = patch_nvg(k);
     bs.npg = patch_npg(k);
     bs.ms = patch_ms(k);
+    bs.local = opt.patch_assembly == WR_PATCH_LOCAL;
+    bs.weighted = opt.scatter_weight == WR_WEIGHT_MULTIPLICITY;
     return bs;
   }
   int64_t elem_size() const { return (int64_t)nt * (2 * (k + 2) * (k + 2) + (k + 1) * (k + 1)); }
@@ -305,10 +307,10 @@ struct wr_batch {
       for (int l = M.L; l >= 1; --l) launch_inject(M.g[l], M.g[l - 1], M.W[l], M.W[l - 1], s);
       for (int l = 1; l <= M.L; ++l) {
         if (M.ph.conv != 0.0) launch_conv_elements(M.g[l], tab, M.W[l], Ce, s);
-        launch_block_factor(M.g[l], tab, M.ph, patch_set(), Ce, M.factors[l], opt.precision, s);
+        launch_block_factor(M.g[l], tab, M.ph, patch_set(), Ce, M.factors[l], opt.precision, fstat, s);
       }
       if (M.ph.conv != 0.0) launch_conv_elements(M.g[0], tab, M.W[0], Ce, s);
-      launch_block_factor(M.g[0], tab, M.ph, M.cbs, Ce, M.cf, WR_FP64, s);
+      launch_block_factor(M.g[0], tab, M.ph, M.cbs, Ce, M.cf, WR_FP64, fstat, s);
     }
     build_tables();
     for (int d = 0; d < D; ++d) eigen_depth(d);
@@ -596,6 +598,10 @@ int wr_batch_create(wr_batch** out, int n, const wr_problem* ps, const wr_option
     if (o) b->opt = *o;
     else wr_default_options(&b->opt);
     bneed(b->opt.precision >= WR_FP64 && b->opt.precision <= WR_BF16, "bad precision");
+    bneed(b->opt.patch_assembly == WR_PATCH_SUBMATRIX || b->opt.patch_assembly == WR_PATCH_LOCAL,
+          "bad patch_assembly");
+    bneed(b->opt.scatter_weight == WR_WEIGHT_ONE || b->opt.scatter_weight == WR_WEIGHT_MULTIPLICITY,
+          "bad scatter_weight");
     bneed(b->opt.cheb_steps >= 1 && 2 * b->opt.cheb_steps <= kCoefRows, "bad Chebyshev steps");
     bneed(b->opt.eig_steps >= 1 && b->opt.eig_steps <= b->opt.gmres_restart, "bad eigen-estimate steps");
     b->s = static_cast<cudaStream_t>(stream);
@@ -705,6 +711,7 @@ int wr_batch_create(wr_batch** out, int n, const wr_problem* ps, const wr_option
     b->dcoef = b->alloc<double>(2 * (size_t)n);
     b->dseeds = b->alloc<int64_t>(n);
     b->derr = b->alloc<int>(1);
+    b->fstat = b->alloc<int>(1);
     WR_CUDA(cudaMemsetAsync(b->derr, 0, sizeof(int), b->s));
     WR_CUDA(cudaMallocHost(&b->hres, sizeof(double) * n));
     WR_CUDA(cudaMallocHost(&b->hcoef, sizeof(double) * 2 * n));

@@ -64,6 +64,19 @@ __device__ __forceinline__ void block_origin(const LevelGeom& g, const BlockSet&
   }
 }
 
+// 1D cell range [c0, c0 + 1] of the 2x2 cell block of a patch (kind 0) along one
+// direction, from the block's first velocity node v0 = (I - 1)(k + 1); the whole
+// mesh when the patch system is the principal submatrix or the block is not a patch.
+__device__ __forceinline__ void own_cells(const LevelGeom& g, const BlockSet& bs, int v0, int& c0, int& c1) {
+  if (bs.kind == 0 && bs.local) {
+    c0 = v0 / (g.k + 1);  // exact: v0 is a multiple of k + 1 (c0 = -1 for I = 0)
+    c1 = c0 + 1;
+  } else {
+    c0 = 0;
+    c1 = 1 << 30;
+  }
+}
+
 __device__ __forceinline__ Slot decode_slot(const LevelGeom& g, const BlockSet& bs, int blk, int s) {
   int vx0, vy0, px0, py0;
   block_origin(g, bs, blk, vx0, vy0, px0, py0);
@@ -96,11 +109,14 @@ __device__ __forceinline__ Slot decode_slot(const LevelGeom& g, const BlockSet& 
 __device__ __forceinline__ int cell_lo(int g, int p) { return g == 0 ? 0 : (g - 1) / p; }
 __device__ __forceinline__ int cell_hi(int g, int p, int n) { return min(g / p, n - 1); }
 
-// global 1D velocity-velocity matrix entry sum_c ref[gi - pc][gj - pc]
+// global 1D velocity-velocity matrix entry sum_c ref[gi - pc][gj - pc], over the
+// cells c in [clo, chi] only (the whole mesh by default)
 template <int K>
-__device__ __forceinline__ double vv1(const double (*ref)[WR_MAX_NVL], int n, int gi, int gj) {
+__device__ __forceinline__ double vv1(const double (*ref)[WR_MAX_NVL], int n, int gi, int gj, int clo = 0,
+                                      int chi = 1 << 30) {
   const int p = K + 1;
-  const int lo = max(cell_lo(gi, p), cell_lo(gj, p)), hi = min(cell_hi(gi, p, n), cell_hi(gj, p, n));
+  const int lo = max(max(cell_lo(gi, p), cell_lo(gj, p)), clo);
+  const int hi = min(min(cell_hi(gi, p, n), cell_hi(gj, p, n)), chi);
   double v = 0.0;
   for (int c = lo; c <= hi; ++c) v += ref[gi - p * c][gj - p * c];
   return v;
@@ -148,14 +164,17 @@ __device__ void build_factor_tables(const LevelGeom& g, const FeTables& T, const
   int vx0, vy0, px0, py0;
   block_origin(g, bs, blk, vx0, vy0, px0, py0);
   const double h = g.h;
+  int cx0, cx1, cy0, cy1;
+  own_cells(g, bs, vx0, cx0, cx1);
+  own_cells(g, bs, vy0, cy0, cy1);
   for (int e = threadIdx.x; e < TB::NVG * TB::NVG; e += nth) {
     const int i = e / TB::NVG, j = e % TB::NVG;
     const int xi = min(max(vx0 + i, 0), g.nv - 1), xj = min(max(vx0 + j, 0), g.nv - 1);
     const int yi = min(max(vy0 + i, 0), g.nv - 1), yj = min(max(vy0 + j, 0), g.nv - 1);
-    ft.Mx[i][j] = h * vv1<K>(T.m1, g.n, xi, xj);
-    ft.Kx[i][j] = vv1<K>(T.k1, g.n, xi, xj) / h;
-    ft.My[i][j] = h * vv1<K>(T.m1, g.n, yi, yj);
-    ft.Ky[i][j] = vv1<K>(T.k1, g.n, yi, yj) / h;
+    ft.Mx[i][j] = h * vv1<K>(T.m1, g.n, xi, xj, cx0, cx1);
+    ft.Kx[i][j] = vv1<K>(T.k1, g.n, xi, xj, cx0, cx1) / h;
+    ft.My[i][j] = h * vv1<K>(T.m1, g.n, yi, yj, cy0, cy1);
+    ft.Ky[i][j] = vv1<K>(T.k1, g.n, yi, yj, cy0, cy1) / h;
   }
   for (int e = threadIdx.x; e < TB::NPT * TB::NVG; e += nth) {
     const int p = e / TB::NVG, v = e % TB::NVG;
@@ -225,9 +244,19 @@ __device__ void assemble_conv(const LevelGeom& g, const FeTables& T, const PhysP
   int vx0, vy0, px0, py0;
   block_origin(g, bs, blk, vx0, vy0, px0, py0);
   const int nvg = bs.nvg;
-  // cells whose closure meets the slot grid
-  const int cx0 = max(0, (vx0 - 1) / (K + 1) - (vx0 - 1 < 0 ? 1 : 0)), cx1 = min(g.n - 1, (vx0 + nvg - 1) / (K + 1));
-  const int cy0 = max(0, (vy0 - 1) / (K + 1) - (vy0 - 1 < 0 ? 1 : 0)), cy1 = min(g.n - 1, (vy0 + nvg - 1) / (K + 1));
+  // cells whose closure meets the slot grid (only the patch's own 2x2 cells when
+  // the patch system is assembled over them)
+  int cx0 = max(0, (vx0 - 1) / (K + 1) - (vx0 - 1 < 0 ? 1 : 0)), cx1 = min(g.n - 1, (vx0 + nvg - 1) / (K + 1));
+  int cy0 = max(0, (vy0 - 1) / (K + 1) - (vy0 - 1 < 0 ? 1 : 0)), cy1 = min(g.n - 1, (vy0 + nvg - 1) / (K + 1));
+  if (bs.kind == 0 && bs.local) {
+    int a0, a1;
+    own_cells(g, bs, vx0, a0, a1);
+    cx0 = max(cx0, a0);
+    cx1 = min(cx1, a1);
+    own_cells(g, bs, vy0, a0, a1);
+    cy0 = max(cy0, a0);
+    cy1 = min(cy1, a1);
+  }
   const double sc = g.dt * ph.conv;
   double w[NT];
 #pragma unroll
@@ -608,13 +637,16 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
     int vx0, vy0, px0, py0;
     block_origin(g, bs, blk, vx0, vy0, px0, py0);
     for (int s = tid; s < MS; s += NCONS) sm.sidx[s] = decode_slot(g, bs, blk, s).sp;
+    int cx0, cx1, cy0, cy1;
+    own_cells(g, bs, vx0, cx0, cx1);
+    own_cells(g, bs, vy0, cy0, cy1);
     for (int e = tid; e < NVG * NVG; e += NCONS) {
       const int i = e / NVG, j = e % NVG;
       const int xi = vx0 + i, xj = vx0 + j, yi = vy0 + i, yj = vy0 + j;
       const bool okx = i < nvg && j < nvg && xi >= 1 && xi <= g.nv - 2 && xj >= 1 && xj <= g.nv - 2;
       const bool oky = i < nvg && j < nvg && yi >= 1 && yi <= g.nv - 2 && yj >= 1 && yj <= g.nv - 2;
-      sm.mx[i][j] = okx ? (CT)(g.h * vv1<K>(T.m1, g.n, xi, xj)) : (CT)0;
-      sm.my[i][j] = oky ? (CT)(g.h * vv1<K>(T.m1, g.n, yi, yj)) : (CT)0;
+      sm.mx[i][j] = okx ? (CT)(g.h * vv1<K>(T.m1, g.n, xi, xj, cx0, cx1)) : (CT)0;
+      sm.my[i][j] = oky ? (CT)(g.h * vv1<K>(T.m1, g.n, yi, yj, cy0, cy1)) : (CT)0;
     }
     for (int e = tid; e < 2 * pd::NVG2; e += NCONS) (&sm.yp[0][0])[e] = 0;
     consumer_sync<NCONS>();
@@ -781,7 +813,7 @@ __device__ __forceinline__ int ceildiv(int a, int b) { return -floordiv(-a, b); 
 
 template <int K, int Q>
 __device__ __forceinline__ void scatter_body(const LevelGeom& g, const double* __restrict__ Yp,
-                                             double* __restrict__ y, int64_t idx) {
+                                             double* __restrict__ y, int64_t idx, int weighted) {
   using pd = PD<K>;
   constexpr int MS = pd::MS, NT = Q + 1;
   const int S = g.S, nv = g.nv, nv2 = nv * nv, n = g.n;
@@ -789,6 +821,7 @@ __device__ __forceinline__ void scatter_body(const LevelGeom& g, const double* _
   const int sp = int(idx % S);
   const int slab = int(blkt / NT), a = int(blkt % NT);
   double acc = 0.0;
+  int cnt = 0;  // number of patches holding the DoF
   if (sp < 2 * nv2) {
     const int c = sp / nv2, t = sp % nv2, gx = t % nv, gy = t / nv;
     if (gx == 0 || gy == 0 || gx == nv - 1 || gy == nv - 1) { y[idx] = 0.0; return; }
@@ -800,6 +833,7 @@ __device__ __forceinline__ void scatter_body(const LevelGeom& g, const double* _
         const int lx = gx - (I - 1) * p, ly = gy - (J - 1) * p;
         const int s = c * pd::NVG2 + ly * pd::NVG + lx;
         acc += Yp[(((int64_t)(J * (n + 1) + I) * g.N + slab) * NT + a) * MS + s];
+        ++cnt;
       }
   } else {
     const int t = sp - 2 * nv2, px = t % g.np, py = t / g.np;
@@ -810,16 +844,17 @@ __device__ __forceinline__ void scatter_body(const LevelGeom& g, const double* _
         const int lx = px - (I * K - (K - 1)), ly = py - (J * K - (K - 1));
         const int s = 2 * pd::NVG2 + ly * pd::NPG + lx;
         acc += Yp[(((int64_t)(J * (n + 1) + I) * g.N + slab) * NT + a) * MS + s];
+        ++cnt;
       }
   }
-  y[idx] = acc;
+  y[idx] = (weighted && cnt > 0) ? acc / cnt : acc;
 }
 
 template <int K, int Q>
-__global__ void scatter_kernel(LevelGeom g, const double* __restrict__ Yp, double* __restrict__ y) {
+__global__ void scatter_kernel(LevelGeom g, const double* __restrict__ Yp, double* __restrict__ y, int weighted) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= g.ndofs) return;
-  scatter_body<K, Q>(g, Yp, y, idx);
+  scatter_body<K, Q>(g, Yp, y, idx, weighted);
 }
 
 template <int K, int Q>
@@ -829,7 +864,7 @@ __global__ void bt_scatter_kernel(const BatchSeg* __restrict__ segs, int nseg, i
   if (u >= dofs) return;
   const int m = batch_find<BU_DOF>(segs, nseg, u);
   const LevelGeom g = segs[m].g;
-  scatter_body<K, Q>(g, yp + segs[m].off_yp, y + segs[m].off, u - segs[m].u_dof);
+  scatter_body<K, Q>(g, yp + segs[m].off_yp, y + segs[m].off, u - segs[m].u_dof, segs[m].bs.weighted);
 }
 
 template <int K, int Q, typename CT, typename ST, int NPGX = 2 * K - 1>
@@ -846,21 +881,26 @@ void run_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph, con
   WR_LAUNCH_CHECK();
 }
 
+// CTAs of `kern` resident on the whole GPU at `smem` bytes of dynamic shared memory
+// (also raises the kernel's dynamic shared memory limit to `smem`).
+template <typename Kern>
+int persistent_grid(Kern kern, int nth, size_t smem) {
+  WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, sms = 0, per_sm = 0;
+  WR_CUDA(cudaGetDevice(&dev));
+  WR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  WR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nth, smem));
+  return sms * (per_sm > 0 ? per_sm : 1);
+}
+
 template <int K, int Q, typename FT, int NPGX = 2 * K - 1>
 void run_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs, const FT* factors, const double* r,
                double* out, int* err, cudaStream_t s) {
   using C = ApplyCfg<K, Q, FT, NPGX>;
   const size_t smem = (size_t)C::NS * C::SLOT_ELEMS * sizeof(FT) + sizeof(ApplySmem<K, Q, FT, NPGX>);
   auto kern = block_apply_kernel<K, Q, FT, NPGX>;
-  static int grid_cap = 0;  // persistent grid: CTAs resident on the whole GPU
-  if (grid_cap == 0) {
-    WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0, sms = 0, per_sm = 0;
-    WR_CUDA(cudaGetDevice(&dev));
-    WR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    WR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NTH, smem));
-    grid_cap = sms * (per_sm > 0 ? per_sm : 1);
-  }
+  // persistent grid: CTAs resident on the whole GPU (computed once; thread-safe static)
+  static const int grid_cap = persistent_grid(kern, C::NTH, smem);
   const int nblk = bs.kind == 0 ? g.npatch() : 1;
   const int grid = nblk < grid_cap ? nblk : grid_cap;
   kern<<<grid, C::NTH, smem, s>>>(g, T, bs, factors, r, out, nblk, err);
@@ -873,32 +913,18 @@ void run_bt_apply(const BatchSeg* segs, int nseg, int64_t items, const FeTables&
   using C = ApplyCfg<K, Q, FT, NPGX>;
   const size_t smem = (size_t)C::NS * C::SLOT_ELEMS * sizeof(FT) + sizeof(ApplySmem<K, Q, FT, NPGX>);
   auto kern = bt_block_apply_kernel<K, Q, FT, NPGX>;
-  static int grid_cap = 0;
-  if (grid_cap == 0) {
-    WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0, sms = 0, per_sm = 0;
-    WR_CUDA(cudaGetDevice(&dev));
-    WR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    WR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NTH, smem));
-    grid_cap = sms * (per_sm > 0 ? per_sm : 1);
-  }
+  static const int grid_cap = persistent_grid(kern, C::NTH, smem);
   if (items <= 0) return;
   const int grid = items < grid_cap ? (int)items : grid_cap;
   kern<<<grid, C::NTH, smem, s>>>(segs, nseg, items, T, r, yp, coarse ? 1 : 0, err);
   WR_LAUNCH_CHECK();
 }
 
-int* status_buffer() {
-  static int* st = nullptr;  // per process; reset before each factorisation
-  if (!st) WR_CUDA(cudaMalloc(&st, sizeof(int)));
-  return st;
-}
 
 }  // namespace
 
 void launch_block_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const BlockSet& bs,
-                         const double* Ce, void* factors, int precision, cudaStream_t s) {
-  int* st = status_buffer();
+                         const double* Ce, void* factors, int precision, int* st, cudaStream_t s) {
   WR_CUDA(cudaMemsetAsync(st, 0, sizeof(int), s));
 #define WR_F(K_, Q_)                                                                                     \
   if (g.k == K_ && g.q == Q_) {                                                                          \
@@ -941,13 +967,12 @@ void launch_block_apply(const LevelGeom& g, const FeTables& T, const BlockSet& b
 }
 
 void launch_scatter(const LevelGeom& g, const BlockSet& bs, const double* Yp, double* y, cudaStream_t s) {
-  (void)bs;
-  const int threads = 256;
+  const int threads = 256, wt = bs.weighted;
   const unsigned blocks = (unsigned)((g.ndofs + threads - 1) / threads);
-  if (g.k == 1 && g.q == 0) scatter_kernel<1, 0><<<blocks, threads, 0, s>>>(g, Yp, y);
-  else if (g.k == 1 && g.q == 1) scatter_kernel<1, 1><<<blocks, threads, 0, s>>>(g, Yp, y);
-  else if (g.k == 2 && g.q == 0) scatter_kernel<2, 0><<<blocks, threads, 0, s>>>(g, Yp, y);
-  else if (g.k == 2 && g.q == 1) scatter_kernel<2, 1><<<blocks, threads, 0, s>>>(g, Yp, y);
+  if (g.k == 1 && g.q == 0) scatter_kernel<1, 0><<<blocks, threads, 0, s>>>(g, Yp, y, wt);
+  else if (g.k == 1 && g.q == 1) scatter_kernel<1, 1><<<blocks, threads, 0, s>>>(g, Yp, y, wt);
+  else if (g.k == 2 && g.q == 0) scatter_kernel<2, 0><<<blocks, threads, 0, s>>>(g, Yp, y, wt);
+  else if (g.k == 2 && g.q == 1) scatter_kernel<2, 1><<<blocks, threads, 0, s>>>(g, Yp, y, wt);
   else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
   WR_LAUNCH_CHECK();
 }

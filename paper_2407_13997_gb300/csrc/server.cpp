@@ -1,0 +1,232 @@
+// Serving form: a request loop over independent space-time solves.
+//
+// Requests queue in arrival order.  A scheduler thread admits the request at the
+// head of the queue as soon as an in-flight slot is free and its device memory
+// (wr_estimate_bytes plus its solution vector) fits in the remaining budget;
+// a request larger than the whole budget is refused.  Every admitted request
+// runs on a worker thread with its own CUDA stream and context, so its level
+// hierarchy, factors and Krylov state stay on the device for the whole solve,
+// and the kernels of all in-flight solves overlap on the GPU.  When a solve
+// completes its memory and slot are released and the scheduler admits the next
+// requests at once (continuous admission, no waves).  Each solve runs the same
+// deterministic kernels on its own stream, so its result does not depend on
+// what else is in flight.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "wrmg_internal.h"
+
+namespace {
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+  uint64_t id = 0;
+  wr_problem p;
+  std::vector<int> mx, my;
+  std::vector<double> amp;
+  std::vector<double> U0;  // optional initial iterate (host)
+  std::vector<double> U;   // result (host)
+  wr_stats st;
+  int status = WR_ERR_STATE;  // WR_ERR_STATE while queued or running
+  bool done = false;
+  int64_t bytes = 0, ndofs = 0;
+  double t_submit = 0, t_start = 0, t_end = 0;
+};
+
+}  // namespace
+
+struct wr_server {
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<std::shared_ptr<Request>> queue;
+  std::map<uint64_t, std::shared_ptr<Request>> reqs;
+  std::vector<std::thread> workers;
+  std::thread scheduler;
+  wr_options opt;
+  int64_t budget = 0, used = 0, peak_used = 0;
+  int max_inflight = 1, inflight = 0, peak_inflight = 0, device = 0;
+  uint64_t next_id = 1;
+  bool stopping = false;
+  std::string err;
+
+  void run_one(std::shared_ptr<Request> r) {
+    cudaSetDevice(device);
+    cudaStream_t s = nullptr;
+    wr_ctx* c = nullptr;
+    double* dU = nullptr;
+    int rc = WR_OK;
+    std::memset(&r->st, 0, sizeof(r->st));
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) rc = WR_ERR_CUDA;
+    if (rc == WR_OK) rc = create_context(&c, &r->p, &opt, s, true);
+    if (rc == WR_OK && cudaMallocAsync(&dU, sizeof(double) * r->ndofs, s) != cudaSuccess) rc = WR_ERR_NOMEM;
+    if (rc == WR_OK) {
+      if (!r->U0.empty()) {
+        if (cudaMemcpyAsync(dU, r->U0.data(), sizeof(double) * r->ndofs, cudaMemcpyHostToDevice, s) != cudaSuccess)
+          rc = WR_ERR_CUDA;
+      } else {
+        rc = wr_initial_guess(c, dU);
+      }
+    }
+    if (rc == WR_OK) rc = wr_solve(c, dU, &r->st);
+    if (rc == WR_OK || rc == WR_ERR_NOT_CONVERGED) {
+      r->U.resize(r->ndofs);
+      if (cudaMemcpyAsync(r->U.data(), dU, sizeof(double) * r->ndofs, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        rc = WR_ERR_CUDA;
+    }
+    if (dU) cudaFreeAsync(dU, s);
+    if (c) wr_destroy(c);
+    if (s) cudaStreamDestroy(s);
+    std::lock_guard<std::mutex> lock(mu);
+    r->status = rc;
+    r->t_end = now_ms();
+    r->done = true;
+    used -= r->bytes;
+    --inflight;
+    cv.notify_all();
+  }
+
+  void schedule() {
+    std::unique_lock<std::mutex> lock(mu);
+    while (true) {
+      cv.wait(lock, [&] {
+        if (stopping) return true;
+        if (queue.empty()) return false;
+        const auto& h = queue.front();
+        return h->bytes > budget || (inflight < max_inflight && used + h->bytes <= budget);
+      });
+      if (stopping && queue.empty()) return;
+      if (stopping) {  // refuse what is still queued
+        for (auto& r : queue) {
+          r->status = WR_ERR_STATE;
+          r->done = true;
+        }
+        queue.clear();
+        cv.notify_all();
+        return;
+      }
+      auto r = queue.front();
+      queue.pop_front();
+      if (r->bytes > budget) {
+        r->status = WR_ERR_NOMEM;
+        r->t_end = now_ms();
+        r->done = true;
+        cv.notify_all();
+        continue;
+      }
+      used += r->bytes;
+      ++inflight;
+      peak_used = std::max(peak_used, used);
+      peak_inflight = std::max(peak_inflight, inflight);
+      r->t_start = now_ms();
+      workers.emplace_back([this, r] { run_one(r); });
+    }
+  }
+};
+
+extern "C" {
+
+int wr_server_create(wr_server** out, int64_t mem_budget_bytes, int max_inflight, const wr_options* o) {
+  if (!out || mem_budget_bytes <= 0 || max_inflight < 1) return WR_ERR_ARG;
+  auto sv = std::make_unique<wr_server>();
+  if (o) sv->opt = *o;
+  else wr_default_options(&sv->opt);
+  sv->budget = mem_budget_bytes;
+  sv->max_inflight = max_inflight;
+  if (cudaGetDevice(&sv->device) != cudaSuccess) return WR_ERR_CUDA;
+  // keep freed blocks in this process's default pool up to the budget, so that
+  // admissions after completions reuse them instead of mapping memory afresh
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, sv->device) == cudaSuccess) {
+    uint64_t keep = (uint64_t)mem_budget_bytes;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  wr_server* raw = sv.get();
+  sv->scheduler = std::thread([raw] { raw->schedule(); });
+  *out = sv.release();
+  return WR_OK;
+}
+
+int wr_server_destroy(wr_server* sv) {
+  if (!sv) return WR_ERR_ARG;
+  {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    sv->stopping = true;
+    sv->cv.notify_all();
+  }
+  if (sv->scheduler.joinable()) sv->scheduler.join();
+  for (auto& t : sv->workers)
+    if (t.joinable()) t.join();
+  delete sv;
+  return WR_OK;
+}
+
+int wr_server_submit(wr_server* sv, const wr_problem* p, const double* U0_host, uint64_t* ticket) {
+  if (!sv || !p || !ticket) return WR_ERR_ARG;
+  auto r = std::make_shared<Request>();
+  r->p = *p;
+  if (p->n_modes > 0) {
+    if (!p->mx || !p->my || !p->amp || p->n_modes > 8) return WR_ERR_ARG;
+    r->mx.assign(p->mx, p->mx + p->n_modes);
+    r->my.assign(p->my, p->my + p->n_modes);
+    r->amp.assign(p->amp, p->amp + p->n_modes);
+    r->p.mx = r->mx.data();
+    r->p.my = r->my.data();
+    r->p.amp = r->amp.data();
+  }
+  int64_t est = 0;
+  const int rc = wr_estimate_bytes(&r->p, &sv->opt, &est);
+  if (rc != WR_OK) return rc;
+  const LevelGeom g = make_geom(p->n_fine, p->k, p->q, p->n_slabs, p->T);
+  r->ndofs = g.ndofs;
+  r->bytes = est + (int64_t)sizeof(double) * r->ndofs;
+  if (U0_host) r->U0.assign(U0_host, U0_host + r->ndofs);
+  std::lock_guard<std::mutex> lock(sv->mu);
+  if (sv->stopping) return WR_ERR_STATE;
+  r->id = sv->next_id++;
+  r->t_submit = now_ms();
+  sv->reqs[r->id] = r;
+  sv->queue.push_back(r);
+  *ticket = r->id;
+  sv->cv.notify_all();
+  return WR_OK;
+}
+
+// Returns WR_ERR_STATE while the request is queued or running (wait == 0), else the
+// solve's status; on completion copies the solution (U_host may be NULL), the
+// statistics and the latency (submit to completion, ms) and forgets the ticket.
+int wr_server_poll(wr_server* sv, uint64_t ticket, int wait, double* U_host, wr_stats* st, double* latency_ms) {
+  if (!sv) return WR_ERR_ARG;
+  std::unique_lock<std::mutex> lock(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return WR_ERR_ARG;
+  auto r = it->second;
+  if (wait) sv->cv.wait(lock, [&] { return r->done; });
+  if (!r->done) return WR_ERR_STATE;
+  if (U_host && !r->U.empty()) std::memcpy(U_host, r->U.data(), sizeof(double) * r->ndofs);
+  if (st) *st = r->st;
+  if (latency_ms) *latency_ms = r->t_end - r->t_submit;
+  sv->reqs.erase(it);
+  return r->status;
+}
+
+// Peak device bytes admitted at once and peak number of solves in flight so far.
+int wr_server_stats(wr_server* sv, int64_t* peak_bytes, int* peak_inflight) {
+  if (!sv) return WR_ERR_ARG;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  if (peak_bytes) *peak_bytes = sv->peak_used;
+  if (peak_inflight) *peak_inflight = sv->peak_inflight;
+  return WR_OK;
+}
+
+}  // extern "C"

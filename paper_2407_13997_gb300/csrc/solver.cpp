@@ -56,7 +56,8 @@ struct wr_ctx {
   double *partials = nullptr, *dres = nullptr, *hres = nullptr;
   int* herr = nullptr;
   int* slots = nullptr;
-  int* derr = nullptr;  // device error flag of the bounded waits
+  int* derr = nullptr;   // device error flag of the bounded waits
+  int* fstat = nullptr;  // device zero-pivot flag of the factorisation
   std::vector<void*> allocs;
   int64_t bytes = 0;
   bool linearised = false;
@@ -76,11 +77,20 @@ struct wr_ctx {
     return ev_pool[ev_used++];
   }
 
+  bool dry = false;  // count the allocations of wr_create without making them
+  // allocate from the stream-ordered pool on s (no device-wide synchronisation
+  // in cudaMalloc/cudaFree while other streams run; used by the server)
+  bool stream_ordered = false;
+
   template <typename Tp>
   Tp* alloc(size_t count) {
     void* p = nullptr;
     const size_t nb = std::max<size_t>(count * sizeof(Tp), 16);
-    cudaError_t e = cudaMalloc(&p, nb);
+    if (dry) {
+      bytes += nb;
+      return reinterpret_cast<Tp*>(uintptr_t(256));
+    }
+    cudaError_t e = stream_ordered ? cudaMallocAsync(&p, nb, s) : cudaMalloc(&p, nb);
     if (e != cudaSuccess) {
       cudaGetLastError();
       throw WrError(WR_ERR_NOMEM, "cudaMalloc of " + std::to_string(nb) + " bytes failed (" + cudaGetErrorString(e) +
@@ -92,7 +102,12 @@ struct wr_ctx {
   }
   ~wr_ctx() {
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
-    for (void* p : allocs) cudaFree(p);
+    if (stream_ordered) {
+      for (void* p : allocs) cudaFreeAsync(p, s);
+      cudaStreamSynchronize(s);
+    } else {
+      for (void* p : allocs) cudaFree(p);
+    }
     if (hres) cudaFreeHost(hres);
     if (herr) cudaFreeHost(herr);
   }
@@ -201,10 +216,10 @@ struct wr_ctx {
     for (int l = T_; l >= 1; --l) launch_inject(L[l].g, L[l - 1].g, L[l].W, L[l - 1].W, s);
     for (int l = 1; l <= T_; ++l) {
       if (ph.conv != 0.0) launch_conv_elements(L[l].g, tab, L[l].W, Ce, s);
-      launch_block_factor(L[l].g, tab, ph, L[l].bs, Ce, L[l].factors, opt.precision, s);
+      launch_block_factor(L[l].g, tab, ph, L[l].bs, Ce, L[l].factors, opt.precision, fstat, s);
     }
     if (ph.conv != 0.0) launch_conv_elements(L[0].g, tab, L[0].W, Ce, s);
-    launch_block_factor(L[0].g, tab, ph, cbs, Ce, cfactors, WR_FP64, s);
+    launch_block_factor(L[0].g, tab, ph, cbs, Ce, cfactors, WR_FP64, fstat, s);
     linearised = true;
     if (eig)
       for (int l = 1; l <= T_; ++l) eigen_estimate(l);
@@ -456,13 +471,33 @@ void wr_default_options(wr_options* o) {
   o->eta_fixed = 1e-4;
   o->gmres_restart = 30;
   o->gmres_maxit = 200;
+  o->patch_assembly = WR_PATCH_SUBMATRIX;
+  o->scatter_weight = WR_WEIGHT_ONE;
 }
+
+static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, void* stream);
 
 int wr_create(wr_ctx** out, const wr_problem* p, const wr_options* o, void* stream) {
   if (!out || !p) return WR_ERR_ARG;
   *out = nullptr;
   auto c = std::make_unique<wr_ctx>();
-  int rc = guarded(c.get(), [&]() -> int {
+  const int rc = create_impl(c.get(), p, o, stream);
+  *out = c.release();
+  return rc;
+}
+
+int wr_estimate_bytes(const wr_problem* p, const wr_options* o, int64_t* out) {
+  if (!p || !out) return WR_ERR_ARG;
+  wr_ctx c;
+  c.dry = true;
+  const int rc = create_impl(&c, p, o, nullptr);
+  *out = c.bytes;
+  return rc;
+}
+
+static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, void* stream) {
+  wr_ctx* c = cptr;
+  int rc = guarded(c, [&]() -> int {
     need(p->k == 1 || p->k == 2, "k must be 1 or 2");
     need(p->q == 0 || p->q == 1, "q must be 0 or 1");
     need(p->n_coarse == 2 || (p->n_coarse == 3 && p->k == 1), "n_coarse must be 2 (or 3 for k = 1)");
@@ -481,6 +516,10 @@ int wr_create(wr_ctx** out, const wr_problem* p, const wr_options* o, void* stre
     need(c->opt.cheb_steps >= 1 && c->opt.eig_steps >= 1 && c->opt.eig_steps <= c->opt.gmres_restart,
          "bad Chebyshev / eigen-estimate steps");
     need(c->opt.gmres_restart >= 1 && c->opt.gmres_restart <= 200, "bad restart");
+    need(c->opt.patch_assembly == WR_PATCH_SUBMATRIX || c->opt.patch_assembly == WR_PATCH_LOCAL,
+         "patch_assembly must be WR_PATCH_SUBMATRIX or WR_PATCH_LOCAL");
+    need(c->opt.scatter_weight == WR_WEIGHT_ONE || c->opt.scatter_weight == WR_WEIGHT_MULTIPLICITY,
+         "scatter_weight must be WR_WEIGHT_ONE or WR_WEIGHT_MULTIPLICITY");
     c->s = static_cast<cudaStream_t>(stream);
     c->k = p->k; c->q = p->q; c->N = p->n_slabs; c->T = p->T;
     c->ph.kind = p->kind; c->ph.steady = p->steady; c->ph.nu = p->nu; c->ph.conv = p->conv; c->ph.T = p->T;
@@ -499,6 +538,8 @@ int wr_create(wr_ctx** out, const wr_problem* p, const wr_options* o, void* stre
       lv.bs.nvg = patch_nvg(p->k);
       lv.bs.npg = patch_npg(p->k);
       lv.bs.ms = ms;
+      lv.bs.local = c->opt.patch_assembly == WR_PATCH_LOCAL;
+      lv.bs.weighted = c->opt.scatter_weight == WR_WEIGHT_MULTIPLICITY;
       const int64_t nd = lv.g.ndofs;
       lv.W = c->alloc<double>(nd);
       lv.b = c->alloc<double>(nd);
@@ -542,19 +583,15 @@ int wr_create(wr_ctx** out, const wr_problem* p, const wr_options* o, void* stre
     c->dres = c->alloc<double>(1);
     c->slots = c->alloc<int>(2 * ms);
     c->derr = c->alloc<int>(1);
+    c->fstat = c->alloc<int>(1);
+    if (c->dry) return WR_OK;
     WR_CUDA(cudaMemset(c->derr, 0, sizeof(int)));
     WR_CUDA(cudaMallocHost(&c->hres, sizeof(double)));
     WR_CUDA(cudaMallocHost(&c->herr, sizeof(int)));
     *c->herr = 0;
     return WR_OK;
   });
-  if (rc != WR_OK) {
-    // keep the message reachable: the context is returned so wr_last_error works
-    *out = c.release();
-    return rc;
-  }
-  *out = c.release();
-  return WR_OK;
+  return rc;  // on failure the context is still returned, so wr_last_error works
 }
 
 int wr_destroy(wr_ctx* c) {
@@ -805,3 +842,13 @@ int wr_measure_fp64_tflops(void* stream, double* out) {
 }
 
 }  // extern "C"
+
+int create_context(wr_ctx** out, const wr_problem* p, const wr_options* o, void* stream, bool stream_ordered) {
+  if (!out || !p) return WR_ERR_ARG;
+  *out = nullptr;
+  auto c = std::make_unique<wr_ctx>();
+  c->stream_ordered = stream_ordered;
+  const int rc = create_impl(c.get(), p, o, stream);
+  *out = c.release();
+  return rc;
+}

@@ -121,6 +121,8 @@ inline int coarse_ms(int k, int n_coarse) { return n_coarse == 2 ? patch_ms(k) :
 struct BlockSet {
   int kind;  // 0: one Vanka+star patch per vertex; 1: the single coarse block
   int nvg, npg, ms;  // ms = padded slot count per temporal DoF (leading dimension)
+  int local = 0;     // kind 0: 1 = patch system assembled over the patch's own cells
+  int weighted = 0;  // kind 0: 1 = scatter weight 1 / (number of patches holding the DoF)
 };
 
 FeTables build_tables(int k, int q);
@@ -181,8 +183,9 @@ void launch_conv_elements(const LevelGeom& g, const FeTables& T, const double* W
                           cudaStream_t s);
 void launch_inject(const LevelGeom& gf, const LevelGeom& gc, const double* Wf, double* Wc,
                    cudaStream_t s);
+// st: a device int of the caller's (zero-pivot flag), read back after the launch
 void launch_block_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph,
-                         const BlockSet& bs, const double* Ce, void* factors, int precision,
+                         const BlockSet& bs, const double* Ce, void* factors, int precision, int* st,
                          cudaStream_t s);
 void launch_block_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs,
                         const void* factors, int precision, const double* r, double* out,
@@ -237,3 +240,9 @@ void bt_fill_abs(const BatchSeg* segs, int nseg, int64_t dofs, double v, cudaStr
 int bt_dot_blocks();
 void bt_dot(const BatchSeg* segs, int nseg, const double* x, const double* y, double* partials, double* out,
             cudaStream_t s);
+
+// wr_create with the option of allocating the context's device memory from the
+// stream-ordered pool on `stream` (cudaMallocAsync / cudaFreeAsync), so that
+// creating and destroying a context never synchronises the whole device while
+// other streams run.
+int create_context(wr_ctx** out, const wr_problem* p, const wr_options* o, void* stream, bool stream_ordered);

@@ -132,3 +132,28 @@ def batching_workloads(count=256, seed=1):
         out.append(Workload(f"batch{seed}_{i}_n{n}_N{int(Ns[i])}", n, 3 if n % 3 == 0 else 2, 1, 0, int(Ns[i]),
                             1.0, float(nus[i]), 1.0, KIND_FOURIER, False, mx, my, amp))
     return out
+
+
+def serving_workloads(count=32, seed=2, ns=(16, 32, 64), slabs=(16, 32, 64)):
+    """Space-time solve requests of the serving stream: Q2/Q1 DG(0) or Q3/Q2 DG(1)
+    with equal probability, n uniform in `ns`, N uniform in `slabs`, nu log-uniform
+    in [1e-3, 1e-1], Fourier forcing seeded 5000 * seed + i, coarsened to 2x2."""
+    rng = np.random.default_rng(seed)
+    kinds = rng.integers(0, 2, size=count)
+    ns_ = rng.choice(list(ns), size=count)
+    Ns = rng.choice(list(slabs), size=count)
+    nus = 10.0 ** rng.uniform(-3.0, -1.0, size=count)
+    out = []
+    for i in range(count):
+        k, q = (1, 0) if kinds[i] == 0 else (2, 1)
+        n, N = int(ns_[i]), int(Ns[i])
+        mx, my, amp = fourier_forcing(5000 * seed + i)
+        out.append(Workload(f"serve{seed}_{i}_q{k + 1}q{k}_dg{q}_n{n}_N{N}", n, 2, k, q, N, 1.0, float(nus[i]), 1.0,
+                            KIND_FOURIER, False, mx, my, amp))
+    return out
+
+
+def poisson_arrivals(count, rate, seed=2):
+    """Arrival times (s) of a Poisson stream of `rate` requests per second."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=count))

@@ -16,6 +16,8 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libwrmg.so")
 WR_OK = 0
 WR_ERR_ARG, WR_ERR_NOMEM, WR_ERR_CUDA, WR_ERR_NOT_CONVERGED, WR_ERR_TIMEOUT, WR_ERR_NAN, WR_ERR_STATE = range(1, 8)
 WR_FP64, WR_FP32, WR_BF16 = 0, 1, 2
+WR_PATCH_SUBMATRIX, WR_PATCH_LOCAL = 0, 1
+WR_WEIGHT_ONE, WR_WEIGHT_MULTIPLICITY = 0, 1
 _STATUS = {1: "WR_ERR_ARG", 2: "WR_ERR_NOMEM", 3: "WR_ERR_CUDA", 4: "WR_ERR_NOT_CONVERGED",
            5: "WR_ERR_TIMEOUT", 6: "WR_ERR_NAN", 7: "WR_ERR_STATE"}
 
@@ -38,7 +40,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("cheb_steps", ctypes.c_int), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("eig_steps", ctypes.c_int), ("newton_rtol", ctypes.c_double),
                 ("newton_maxit", ctypes.c_int), ("ew", ctypes.c_int), ("eta_fixed", ctypes.c_double),
-                ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int)]
+                ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
+                ("patch_assembly", ctypes.c_int), ("scatter_weight", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -59,6 +62,8 @@ _P = ctypes.c_void_p
 _SIGS = {
     "wr_default_options": (None, [ctypes.POINTER(Options)]),
     "wr_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Problem), ctypes.POINTER(Options), _P]),
+    "wr_estimate_bytes": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.POINTER(Options),
+                                         ctypes.POINTER(ctypes.c_int64)]),
     "wr_destroy": (ctypes.c_int, [_P]),
     "wr_last_error": (ctypes.c_char_p, [_P]),
     "wr_num_levels": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
@@ -98,6 +103,13 @@ _SIGS = {
     "wr_batch_vcycle": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p)]),
     "wr_batch_vcycle_resident": (ctypes.c_int, [_P]),
     "wr_batch_solve": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Stats)]),
+    "wr_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int,
+                                        ctypes.POINTER(Options)]),
+    "wr_server_destroy": (ctypes.c_int, [_P]),
+    "wr_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(Problem), _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "wr_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int, _P, ctypes.POINTER(Stats),
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "wr_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]),
     "wr_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "wr_profile_smoother": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int)]),
@@ -155,6 +167,28 @@ def measure_fp64_tflops(stream=None):
 def launch_count():
     out = ctypes.c_int64()
     load().wr_launch_count(ctypes.byref(out))
+    return out.value
+
+
+def _problem(w):
+    """(Problem, arrays kept alive) for a workload description."""
+    mx = np.ascontiguousarray(w.mx, dtype=np.int32)
+    my = np.ascontiguousarray(w.my, dtype=np.int32)
+    amp = np.ascontiguousarray(w.amp, dtype=np.float64)
+    p = Problem(w.n_fine, w.n_coarse, w.k, w.q, w.N, w.T, w.nu, w.conv, w.kind, int(w.steady), len(amp),
+                mx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), my.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                amp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return p, (mx, my, amp)
+
+
+def estimate_bytes(workload, options=None):
+    """Device bytes a Context for `workload` would allocate (nothing is allocated)."""
+    p, keep = _problem(workload)
+    o = options if options is not None else default_options()
+    out = ctypes.c_int64()
+    rc = load().wr_estimate_bytes(ctypes.byref(p), ctypes.byref(o), ctypes.byref(out))
+    if rc != WR_OK:
+        raise WrmgError(rc, "wr_estimate_bytes failed")
     return out.value
 
 
@@ -392,3 +426,65 @@ class Batch:
         if check:
             self._check(rc)
         return [s.as_dict() for s in st]
+
+
+class Server:
+    """A request loop over independent solves: FIFO admission under a device
+    memory budget and an in-flight cap; each admitted request runs on its own
+    native worker thread, CUDA stream and context."""
+
+    def __init__(self, mem_budget_bytes, max_inflight, options=None):
+        lib = load()
+        self._lib = lib
+        self.options = options if options is not None else default_options()
+        h = ctypes.c_void_p()
+        rc = lib.wr_server_create(ctypes.byref(h), int(mem_budget_bytes), int(max_inflight),
+                                  ctypes.byref(self.options))
+        if rc != WR_OK:
+            raise WrmgError(rc, "wr_server_create failed")
+        self._h = h
+        self._ndofs = {}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.wr_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, workload, U0=None):
+        """Queues one solve; returns its ticket.  U0: optional host float64 iterate."""
+        p, keep = _problem(workload)
+        ptr = None
+        if U0 is not None:
+            U0 = np.ascontiguousarray(U0, dtype=np.float64)
+            ptr = ctypes.c_void_p(U0.ctypes.data)
+        t = ctypes.c_uint64()
+        rc = self._lib.wr_server_submit(self._h, ctypes.byref(p), ptr, ctypes.byref(t))
+        if rc != WR_OK:
+            raise WrmgError(rc, "wr_server_submit failed")
+        self._ndofs[t.value] = workload.ndofs()
+        return t.value
+
+    def poll(self, ticket, wait=True, want_solution=True):
+        """None while the request runs (wait=False); else (status, U or None, stats, latency_ms)."""
+        n = self._ndofs[ticket]
+        U = np.empty(n, dtype=np.float64) if want_solution else None
+        st = Stats()
+        lat = ctypes.c_double()
+        rc = self._lib.wr_server_poll(self._h, ctypes.c_uint64(ticket), int(bool(wait)),
+                                      ctypes.c_void_p(U.ctypes.data) if U is not None else None,
+                                      ctypes.byref(st), ctypes.byref(lat))
+        if rc == WR_ERR_STATE and not wait:
+            return None
+        del self._ndofs[ticket]
+        return rc, U, st.as_dict(), lat.value
+
+    def stats(self):
+        b, n = ctypes.c_int64(), ctypes.c_int()
+        self._lib.wr_server_stats(self._h, ctypes.byref(b), ctypes.byref(n))
+        return {"peak_bytes": b.value, "peak_inflight": n.value}

@@ -46,3 +46,25 @@ def test_binding_covers_the_header_and_loads(libpath):
     assert set(wrmg.exported_symbols()) == set(declared_functions())
     o = wrmg.default_options()
     assert o.cheb_steps == 2 and o.eig_steps == 10 and abs(o.cheb_lo - 0.25) < 1e-15 and o.gmres_restart == 30
+
+
+def test_allocation_estimate_runs_on_the_host(libpath):
+    # the dry run of wr_create makes no CUDA call, so it works without a GPU
+    from paper_2407_13997_gb300 import inputs, wrmg
+    w = inputs.fourier_64x64_q3q2_dg1()
+    e = {p: wrmg.estimate_bytes(w, wrmg.default_options(precision=p)) for p in (wrmg.WR_FP64, wrmg.WR_FP32,
+                                                                                 wrmg.WR_BF16)}
+    # the fine-level factors alone: one (q+1) MS x (q+1) MS block per patch and slab, MS = 107 for k = 2
+    npatch, ms, nt = 65 * 65, 107, 2
+    fine_factors = npatch * w.N * (nt * ms) ** 2
+    assert e[wrmg.WR_FP64] > 8 * fine_factors
+    assert e[wrmg.WR_FP64] > e[wrmg.WR_FP32] > e[wrmg.WR_BF16] > 2 * fine_factors
+    assert e[wrmg.WR_FP64] - e[wrmg.WR_FP32] > 4 * fine_factors
+    # doubling the slab count roughly doubles everything that scales with N
+    w2 = inputs.fourier_64x64_q3q2_dg1()
+    w2.N = 128
+    assert 1.9 < wrmg.estimate_bytes(w2) / e[wrmg.WR_FP64] < 2.05
+    bad = inputs.fourier_small(n=8, k=1, q=0, N=3, nu=0.02)
+    bad.k = 3
+    with pytest.raises(wrmg.WrmgError):
+        wrmg.estimate_bytes(bad)
