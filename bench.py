@@ -42,8 +42,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"])
-    ap.add_argument("--n", type=int, default=64, help="mesh (smaller only for profiling captures)")
-    ap.add_argument("--slabs", type=int, default=64, help="time slabs (fewer only for profiling captures)")
+    ap.add_argument("--workload", default="q3q2", choices=["q3q2", "q2q1"],
+                    help="cycle form: q3q2 = 64x64 Q3/Q2 DG(1) 64 slabs (default); "
+                         "q2q1 = 128x128 Q2/Q1 DG(0) 128 slabs")
+    ap.add_argument("--n", type=int, default=None, help="mesh (smaller only for profiling captures)")
+    ap.add_argument("--slabs", type=int, default=None, help="time slabs (fewer only for profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--members", type=int, default=None,
                     help="batch form: number of solves (256); serve form: number of requests (32)")
@@ -52,7 +55,7 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=96.0, help="serve form: device-memory budget")
     ap.add_argument("--full-mix", action="store_true",
                     help="serve form: draw n and N from {16, 32, 64} (default {16, 32})")
-    ap.add_argument("--form", default="cycle", choices=["cycle", "precision", "batch", "serve"],
+    ap.add_argument("--form", default="cycle", choices=["cycle", "precision", "batch", "serve", "smoother"],
                     help="cycle: the V(2,2) throughput line (default); precision: the FP64/FP32/BF16 "
                          "solves of the 128x128 Q2/Q1 DG(0) 128-slab workload")
     return ap.parse_args()
@@ -64,10 +67,18 @@ def dist_info():
 
 def workload(args, seed=0):
     from paper_2407_13997_gb300 import inputs
+    if args.workload == "q2q1":
+        w = inputs.fourier_128x128_q2q1_dg0(seed)
+        n, N = args.n or 128, args.slabs or 128
+        if (n, N) != (128, 128):
+            w.n_fine, w.N = n, N
+            w.name = f"fourier_q2q1_dg0_n{n}_N{N}"
+        return w
     w = inputs.fourier_64x64_q3q2_dg1(seed)
-    if args.n != 64 or args.slabs != 64:
-        w.n_fine, w.N = args.n, args.slabs
-        w.name = f"fourier_q3q2_dg1_n{args.n}_N{args.slabs}"
+    n, N = args.n or 64, args.slabs or 64
+    if (n, N) != (64, 64):
+        w.n_fine, w.N = n, N
+        w.name = f"fourier_q3q2_dg1_n{n}_N{N}"
     return w
 
 
@@ -256,10 +267,12 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")  # ncu --nvtx --nvtx-include timed/ lists these launches only
     e0.record(stream)
     for _ in range(args.steps):
         ctx.vcycle(b, x)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -319,7 +332,8 @@ def run_ours(args):
             "config": {"workload": w.name, "ndofs": D, "n": w.n_fine, "k": w.k, "q": w.q, "N": w.N,
                        "levels": ctx.num_levels, "factor_storage": args.precision,
                        "device_bytes": ctx.device_bytes(),
-                       "l2": "no flush: ~134 GB of stored factors streamed per cycle >> 129 MB L2",
+                       "l2": f"no flush: {ctx.device_bytes() / 1e9:.0f} GB on the device, the stored factors "
+                             "streamed every cycle >> 129 MB L2",
                        "parallelism": f"replicas x{world}"},
             "factor_ms": factor_ms, "setup_ms": setup_ms, "roofline": roof,
             "e2e": {"value": D * world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * D,
@@ -344,11 +358,10 @@ def run_precision_form(args):
     from paper_2407_13997_gb300 import inputs, wrmg
     torch.cuda.set_device(0)
     w = inputs.fourier_128x128_q2q1_dg0(0)
-    if args.n != 64:
-        w.n_fine = args.n
-    if args.slabs != 64:
-        w.N = args.slabs
-    out = {"form": "precision", "workload": w.name if args.n == 64 else f"fourier_q2q1_dg0_n{w.n_fine}_N{w.N}",
+    if args.n or args.slabs:
+        w.n_fine, w.N = args.n or w.n_fine, args.slabs or w.N
+        w.name = f"fourier_q2q1_dg0_n{w.n_fine}_N{w.N}"
+    out = {"form": "precision", "workload": w.name,
            "ndofs": w.ndofs(), "variants": {}}
     ref = None
     for name, prec, rtol in [("fp64", wrmg.WR_FP64, 1e-11), ("fp32", wrmg.WR_FP32, 1e-8), ("fp32", wrmg.WR_FP32, 1e-10),
@@ -553,6 +566,50 @@ def run_serve_form(args):
     print(json.dumps(out), flush=True)
 
 
+def run_smoother_form(args):
+    """The finest-level smoother apply alone (gather, forward substitution over slabs
+    with the stored factors, scatter), K timed launches after W warm-ups: the burst
+    roofline of the dominant kernel, and the command the ncu captures run."""
+    import torch
+    from paper_2407_13997_gb300 import inputs, wrmg
+    torch.cuda.set_device(0)
+    w = workload(args)
+    prec = {"fp64": wrmg.WR_FP64, "fp32": wrmg.WR_FP32, "bf16": wrmg.WR_BF16}[args.precision]
+    ctx = wrmg.Context(w, wrmg.default_options(precision=prec))
+    W = torch.from_numpy(inputs.forcing_shaped_iterate(w)).cuda()
+    ctx.linearise(W, eig=False)
+    L = ctx.fine
+    r = torch.from_numpy(inputs.seeded_vector(3, ctx.ndofs(L))).cuda()
+    y = ctx.vector(L)
+    stream = torch.cuda.current_stream()
+    fp64_tflops = wrmg.measure_fp64_tflops(stream.cuda_stream)
+    ctx.profile(True)
+    for _ in range(args.warmup):
+        ctx.patch_apply(L, r, y)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.patch_apply(L, r, y)
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    sm_ms, sm_n = ctx.profile_smoother(L)
+    alg_bytes, alg_flops = smoother_algorithmic(ctx, w, {wrmg.WR_FP64: 8, wrmg.WR_FP32: 4, wrmg.WR_BF16: 2}[prec])
+    avg_s = sm_ms / max(sm_n, 1) * 1e-3
+    hbm_peak, hbm_src = measured_peaks()
+    out = {"form": "smoother", "workload": w.name, "precision": args.precision, "launches": sm_n,
+           "apply_kernel_ms": avg_s * 1e3, "apply_with_scatter_ms": e0.elapsed_time(e1) / args.steps,
+           "algorithmic_bytes": alg_bytes, "algorithmic_flops": alg_flops,
+           "achieved_gbs": alg_bytes / avg_s / 1e9, "hbm_frac": alg_bytes / avg_s / 1e9 / hbm_peak,
+           "hbm_peak_source": hbm_src, "achieved_tflops": alg_flops / avg_s / 1e12,
+           "fp64_peak_tflops": fp64_tflops, "fp64_frac": alg_flops / avg_s / 1e12 / fp64_tflops}
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -563,6 +620,8 @@ def main():
         run_batch_form(args)
     elif args.form == "serve":
         run_serve_form(args)
+    elif args.form == "smoother":
+        run_smoother_form(args)
     else:
         run_ours(args)
 

@@ -77,6 +77,18 @@ extern "C" {
 #define WR_WEIGHT_ONE 0           /* y = sum_i R_i^T y_i (plain additive Schwarz)               */
 #define WR_WEIGHT_MULTIPLICITY 1  /* y = sum_i R_i^T (y_i / number of patches holding the DoF)  */
 
+/* the slab factors of step (b) (wr_options.store_factors): stored at linearisation
+ * and streamed by every smoother apply, or recomputed in place: every apply on a
+ * recomputing level rebuilds the convection element matrices and the factors of
+ * a window of recompute_slabs slabs into one shared window buffer, applies them,
+ * and moves to the next window (the forward substitution carries the jump state
+ * across windows).  Results are bitwise those of the stored form. */
+#define WR_RECOMPUTE 0   /* every smoothed level recomputes                                      */
+#define WR_STORE 1       /* every smoothed level stores                                          */
+#define WR_STORE_AUTO 2  /* the fewest finest levels recompute such that the context fits
+                            memory_budget_mb (wr_estimate_bytes with memory_budget_mb = 0
+                            assumes every level stored)                                          */
+
 typedef struct wr_ctx wr_ctx;
 
 typedef struct {
@@ -106,6 +118,10 @@ typedef struct {
     int gmres_maxit;        /* total FGMRES iterations per Newton step (200)                     */
     int patch_assembly;     /* WR_PATCH_SUBMATRIX (default) or WR_PATCH_LOCAL                    */
     int scatter_weight;     /* WR_WEIGHT_ONE (default) or WR_WEIGHT_MULTIPLICITY                 */
+    int store_factors;      /* WR_STORE (default), WR_RECOMPUTE or WR_STORE_AUTO                  */
+    int recompute_slabs;    /* slabs per recompute window (0: ceil(N / 16))                      */
+    int memory_budget_mb;   /* WR_STORE_AUTO: device MiB the context may take (0: 92% of the
+                               device's free memory at wr_create)                              */
 } wr_options;
 
 typedef struct {
@@ -136,6 +152,9 @@ int wr_num_levels(const wr_ctx *c, int *out);
 int wr_ndofs(const wr_ctx *c, int level, int64_t *out);
 /* Bytes of device memory the context holds. */
 int wr_device_bytes(const wr_ctx *c, int64_t *out);
+/* Smoothed level (1 .. num_levels - 1): *stored = 1 if its factors are stored,
+ * 0 if recomputed per apply; *window_slabs = the slabs per recompute window (N when stored). */
+int wr_factor_storage(const wr_ctx *c, int level, int *stored, int *window_slabs);
 
 /* Global indices (host array, capacity >= 2 (2k+3)^2 (q+1) + (2k-1)^2 (q+1))
  * of Vanka+star patch `patch` (= J (n+1) + I for vertex (I, J)) on `slab` of

@@ -484,7 +484,12 @@ struct ApplyCfg {
   static constexpr int LAST = BLK - (NCH - 1) * CC * MS;          // last chunk carries the padding
   static constexpr int SLOT = CC * MS > LAST ? CC * MS : LAST;
   static constexpr int SLOT_ELEMS = (SLOT + GR - 1) / GR * GR;
-  static constexpr int RING_BYTES = 176 * 1024;
+  // Q2/Q1 patch blocks are small (51 x 51 per temporal pair): a 64 KB ring and three
+  // CTAs per SM hide the per-slab barriers and the jump-coupling latency of one CTA
+  // behind the others; larger blocks take one CTA per SM and a 176 KB ring.
+  static constexpr bool SMALL = K == 1 && NPGX == 2 * K - 1;
+  static constexpr int MINB = SMALL ? 3 : 1;                      // CTAs per SM
+  static constexpr int RING_BYTES = (SMALL ? 64 : 176) * 1024;
   static constexpr int NS = RING_BYTES / (SLOT_ELEMS * (int)sizeof(FT)) < 16
                                 ? RING_BYTES / (SLOT_ELEMS * (int)sizeof(FT))
                                 : 16;
@@ -557,8 +562,11 @@ struct ApplyItem {
   BlockSet bs;
   const FT* factors;
   const double* r;
-  double* out;  // patch outputs [blk][slab][a][slot] (kind 0) or the global solution (kind 1)
+  double* out;  // patch outputs [slab][blk][a][slot] (kind 0) or the global solution (kind 1)
   int blk;
+  // kind 0 only: patch outputs of the slab before this item's first slab (the
+  // jump state when the slabs are processed in windows), or null (zero state)
+  const double* prev;
 };
 
 template <int K, int Q, typename FT, int NPGX, class Items>
@@ -648,7 +656,12 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
       sm.mx[i][j] = okx ? (CT)(g.h * vv1<K>(T.m1, g.n, xi, xj, cx0, cx1)) : (CT)0;
       sm.my[i][j] = oky ? (CT)(g.h * vv1<K>(T.m1, g.n, yi, yj, cy0, cy1)) : (CT)0;
     }
-    for (int e = tid; e < 2 * pd::NVG2; e += NCONS) (&sm.yp[0][0])[e] = 0;
+    for (int e = tid; e < 2 * pd::NVG2; e += NCONS) {
+      const int c = e / pd::NVG2, tt = e % pd::NVG2;
+      sm.yp[c][tt] = (v.prev && bs.kind == 0 && tt < nv2g)
+                         ? (CT)v.prev[((int64_t)blk * NT + NT - 1) * MS + c * nv2g + tt]
+                         : (CT)0;
+    }
     consumer_sync<NCONS>();
     // (a) gather of slab 0; later slabs come from the register prefetch
     for (int e = tid; e < NT * MS; e += NCONS) {
@@ -736,7 +749,7 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
       for (int e = tid; e < NT * MS; e += NCONS) {
         const int a = e / MS, s = e % MS;
         if (bs.kind == 0) {
-          out[(((int64_t)blk * g.N + slab) * NT + a) * MS + s] = (double)sm.y[a][s];
+          out[(((int64_t)slab * g.npatch() + blk) * NT + a) * MS + s] = (double)sm.y[a][s];
         } else if (sm.sidx[s] >= 0) {
           out[((int64_t)slab * NT + a) * g.S + sm.sidx[s]] = (double)sm.y[a][s];
         }
@@ -765,7 +778,8 @@ struct SingleItems {
   const FT* factors;
   const double* r;
   double* out;
-  __device__ ApplyItem<FT> operator()(int64_t it) const { return {g, bs, factors, r, out, (int)it}; }
+  const double* prev;
+  __device__ ApplyItem<FT> operator()(int64_t it) const { return {g, bs, factors, r, out, (int)it, prev}; }
 };
 
 template <typename FT>
@@ -783,6 +797,7 @@ struct BatchItems {
     v.bs = sg.bs;
     v.factors = static_cast<const FT*>(sg.factors);
     v.blk = (int)(it - sg.u_patch);
+    v.prev = nullptr;
     if (coarse) {
       v.r = sg.xa;
       v.out = sg.ya;
@@ -795,14 +810,14 @@ struct BatchItems {
 };
 
 template <int K, int Q, typename FT, int NPGX>
-__global__ void __launch_bounds__(ApplyCfg<K, Q, FT, NPGX>::NTH, 1)
+__global__ void __launch_bounds__(ApplyCfg<K, Q, FT, NPGX>::NTH, ApplyCfg<K, Q, FT, NPGX>::MINB)
 block_apply_kernel(LevelGeom g, FeTables T, BlockSet bs, const FT* __restrict__ factors, const double* __restrict__ r,
-                   double* __restrict__ out, int nblk, int* __restrict__ err) {
-  apply_persistent<K, Q, FT, NPGX>(T, SingleItems<FT>{g, bs, factors, r, out}, nblk, err);
+                   double* __restrict__ out, int nblk, int* __restrict__ err, const double* __restrict__ prev) {
+  apply_persistent<K, Q, FT, NPGX>(T, SingleItems<FT>{g, bs, factors, r, out, prev}, nblk, err);
 }
 
 template <int K, int Q, typename FT, int NPGX>
-__global__ void __launch_bounds__(ApplyCfg<K, Q, FT, NPGX>::NTH, 1)
+__global__ void __launch_bounds__(ApplyCfg<K, Q, FT, NPGX>::NTH, ApplyCfg<K, Q, FT, NPGX>::MINB)
 bt_block_apply_kernel(const BatchSeg* __restrict__ segs, int nseg, int64_t nitems, FeTables T,
                       const double* __restrict__ r, double* __restrict__ yp, int coarse, int* __restrict__ err) {
   apply_persistent<K, Q, FT, NPGX>(T, BatchItems<FT>{segs, nseg, r, yp, coarse != 0}, nitems, err);
@@ -816,7 +831,7 @@ __device__ __forceinline__ void scatter_body(const LevelGeom& g, const double* _
                                              double* __restrict__ y, int64_t idx, int weighted) {
   using pd = PD<K>;
   constexpr int MS = pd::MS, NT = Q + 1;
-  const int S = g.S, nv = g.nv, nv2 = nv * nv, n = g.n;
+  const int S = g.S, nv = g.nv, nv2 = nv * nv, n = g.n, np1 = n + 1;
   const int64_t blkt = idx / S;
   const int sp = int(idx % S);
   const int slab = int(blkt / NT), a = int(blkt % NT);
@@ -832,7 +847,7 @@ __device__ __forceinline__ void scatter_body(const LevelGeom& g, const double* _
       for (int I = I0; I <= I1; ++I) {
         const int lx = gx - (I - 1) * p, ly = gy - (J - 1) * p;
         const int s = c * pd::NVG2 + ly * pd::NVG + lx;
-        acc += Yp[(((int64_t)(J * (n + 1) + I) * g.N + slab) * NT + a) * MS + s];
+        acc += Yp[(((int64_t)slab * np1 * np1 + J * np1 + I) * NT + a) * MS + s];
         ++cnt;
       }
   } else {
@@ -843,7 +858,7 @@ __device__ __forceinline__ void scatter_body(const LevelGeom& g, const double* _
       for (int I = I0; I <= I1; ++I) {
         const int lx = px - (I * K - (K - 1)), ly = py - (J * K - (K - 1));
         const int s = 2 * pd::NVG2 + ly * pd::NPG + lx;
-        acc += Yp[(((int64_t)(J * (n + 1) + I) * g.N + slab) * NT + a) * MS + s];
+        acc += Yp[(((int64_t)slab * np1 * np1 + J * np1 + I) * NT + a) * MS + s];
         ++cnt;
       }
   }
@@ -895,7 +910,7 @@ int persistent_grid(Kern kern, int nth, size_t smem) {
 
 template <int K, int Q, typename FT, int NPGX = 2 * K - 1>
 void run_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs, const FT* factors, const double* r,
-               double* out, int* err, cudaStream_t s) {
+               double* out, int* err, const double* prev, cudaStream_t s) {
   using C = ApplyCfg<K, Q, FT, NPGX>;
   const size_t smem = (size_t)C::NS * C::SLOT_ELEMS * sizeof(FT) + sizeof(ApplySmem<K, Q, FT, NPGX>);
   auto kern = block_apply_kernel<K, Q, FT, NPGX>;
@@ -903,7 +918,7 @@ void run_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs, const 
   static const int grid_cap = persistent_grid(kern, C::NTH, smem);
   const int nblk = bs.kind == 0 ? g.npatch() : 1;
   const int grid = nblk < grid_cap ? nblk : grid_cap;
-  kern<<<grid, C::NTH, smem, s>>>(g, T, bs, factors, r, out, nblk, err);
+  kern<<<grid, C::NTH, smem, s>>>(g, T, bs, factors, r, out, nblk, err, prev);
   WR_LAUNCH_CHECK();
 }
 
@@ -924,8 +939,8 @@ void run_bt_apply(const BatchSeg* segs, int nseg, int64_t items, const FeTables&
 }  // namespace
 
 void launch_block_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const BlockSet& bs,
-                         const double* Ce, void* factors, int precision, int* st, cudaStream_t s) {
-  WR_CUDA(cudaMemsetAsync(st, 0, sizeof(int), s));
+                         const double* Ce, void* factors, int precision, int* st, cudaStream_t s, bool check) {
+  if (check) WR_CUDA(cudaMemsetAsync(st, 0, sizeof(int), s));
 #define WR_F(K_, Q_)                                                                                     \
   if (g.k == K_ && g.q == Q_) {                                                                          \
     if (precision == WR_FP32)                                                                            \
@@ -941,6 +956,7 @@ void launch_block_factor(const LevelGeom& g, const FeTables& T, const PhysParams
   } else
   WR_F(1, 0) WR_F(1, 1) WR_F(2, 0) WR_F(2, 1) throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 #undef WR_F
+  if (!check) return;
   int h = 0;
   WR_CUDA(cudaMemcpyAsync(&h, st, sizeof(int), cudaMemcpyDeviceToHost, s));
   WR_CUDA(cudaStreamSynchronize(s));
@@ -948,19 +964,19 @@ void launch_block_factor(const LevelGeom& g, const FeTables& T, const PhysParams
 }
 
 void launch_block_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs, const void* factors, int precision,
-                        const double* r, double* out, int* err, cudaStream_t s) {
+                        const double* r, double* out, int* err, cudaStream_t s, const double* prev) {
 #define WR_A(K_, Q_)                                                                                          \
   if (g.k == K_ && g.q == Q_) {                                                                               \
     if (precision == WR_FP32)                                                                                 \
-      run_apply<K_, Q_, float>(g, T, bs, static_cast<const float*>(factors), r, out, err, s);                     \
+      run_apply<K_, Q_, float>(g, T, bs, static_cast<const float*>(factors), r, out, err, prev, s);                     \
     else if (precision == WR_BF16)                                                                            \
-      run_apply<K_, Q_, __nv_bfloat16>(g, T, bs, static_cast<const __nv_bfloat16*>(factors), r, out, err, s);     \
+      run_apply<K_, Q_, __nv_bfloat16>(g, T, bs, static_cast<const __nv_bfloat16*>(factors), r, out, err, prev, s);     \
     else                                                                                                      \
-      run_apply<K_, Q_, double>(g, T, bs, static_cast<const double*>(factors), r, out, err, s);                   \
+      run_apply<K_, Q_, double>(g, T, bs, static_cast<const double*>(factors), r, out, err, prev, s);                   \
   } else
   if (bs.kind == 1 && g.k == 1 && bs.npg == 4) {  // coarse 3x3 block of Q2/Q1 (FP64)
-    if (g.q == 0) run_apply<1, 0, double, 4>(g, T, bs, static_cast<const double*>(factors), r, out, err, s);
-    else run_apply<1, 1, double, 4>(g, T, bs, static_cast<const double*>(factors), r, out, err, s);
+    if (g.q == 0) run_apply<1, 0, double, 4>(g, T, bs, static_cast<const double*>(factors), r, out, err, prev, s);
+    else run_apply<1, 1, double, 4>(g, T, bs, static_cast<const double*>(factors), r, out, err, prev, s);
   } else
   WR_A(1, 0) WR_A(1, 1) WR_A(2, 0) WR_A(2, 1) throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 #undef WR_A

@@ -27,7 +27,9 @@ struct Level {
   LevelGeom g;
   BlockSet bs;
   double* W = nullptr;
-  void* factors = nullptr;
+  void* factors = nullptr;  // stored factors (null when the level recomputes them per apply)
+  bool recompute = false;   // factors recomputed in windows of `nw` slabs at every smoother apply
+  int nw = 0;
   double *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *z = nullptr, *t = nullptr;
   double lam = 0.0;
   bool lam_set = false;
@@ -78,6 +80,9 @@ struct wr_ctx {
   }
 
   bool dry = false;  // count the allocations of wr_create without making them
+  // levels (from the finest down) that recompute their factors; -1 = decide from the options
+  int forced_recompute = -1;
+  void* fwin = nullptr;  // factor window of the recomputing levels
   // allocate from the stream-ordered pool on s (no device-wide synchronisation
   // in cudaMalloc/cudaFree while other streams run; used by the server)
   bool stream_ordered = false;
@@ -132,8 +137,52 @@ struct wr_ctx {
 
   void jac(int l, const double* x, double* y) { launch_jacobian(L[l].g, tab, ph, L[l].W, x, y, ye, s); }
 
+  // Recomputing levels: per window of slabs, the convection element matrices and
+  // the slab factors are rebuilt into the window buffer and applied at once; the
+  // forward substitution carries the jump state across windows through the
+  // previous slab's patch outputs.
+  void factor_window(int l, int s0, int nwc, bool check) {
+    Level& lv = L[l];
+    LevelGeom gw = lv.g;
+    gw.N = nwc;
+    gw.ndofs = (int64_t)nwc * gw.nt * gw.S;
+    if (ph.conv != 0.0) launch_conv_elements(gw, tab, lv.W + (int64_t)s0 * gw.nt * gw.S, Ce, s);
+    launch_block_factor(gw, tab, ph, lv.bs, Ce, fwin, opt.precision, fstat, s, check);
+  }
+
+  void patch_apply_windows(int l, const double* r, double* y) {
+    Level& lv = L[l];
+    const LevelGeom& g = lv.g;
+    const int64_t slab_out = (int64_t)g.npatch() * g.nt * lv.bs.ms;
+    for (int s0 = 0; s0 < g.N; s0 += lv.nw) {
+      const int nwc = std::min(lv.nw, g.N - s0);
+      factor_window(l, s0, nwc, false);
+      LevelGeom gw = g;
+      gw.N = nwc;
+      gw.ndofs = (int64_t)nwc * gw.nt * gw.S;
+      const double* prev = s0 > 0 ? Yp + (s0 - 1) * slab_out : nullptr;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (prof) {
+        e0 = next_event();
+        e1 = next_event();
+        WR_CUDA(cudaEventRecord(e0, s));
+      }
+      launch_block_apply(gw, tab, lv.bs, fwin, opt.precision, r + (int64_t)s0 * g.nt * g.S, Yp + s0 * slab_out, derr,
+                         s, prev);
+      if (prof) {
+        WR_CUDA(cudaEventRecord(e1, s));
+        prof_ev[l].push_back({e0, e1});
+      }
+    }
+    launch_scatter(g, lv.bs, Yp, y, s);
+  }
+
   void patch_apply(int l, const double* r, double* y) {
     if (!linearised) throw WrError(WR_ERR_STATE, "wr_linearise must be called first");
+    if (L[l].recompute) {
+      patch_apply_windows(l, r, y);
+      return;
+    }
     if (prof) {
       cudaEvent_t e0 = next_event(), e1 = next_event();
       WR_CUDA(cudaEventRecord(e0, s));
@@ -215,6 +264,10 @@ struct wr_ctx {
     vec_copy(L[T_].g.ndofs, W, L[T_].W, s);
     for (int l = T_; l >= 1; --l) launch_inject(L[l].g, L[l - 1].g, L[l].W, L[l - 1].W, s);
     for (int l = 1; l <= T_; ++l) {
+      if (L[l].recompute) {  // one pass over the windows checks every block for a zero pivot
+        for (int s0 = 0; s0 < L[l].g.N; s0 += L[l].nw) factor_window(l, s0, std::min(L[l].nw, L[l].g.N - s0), true);
+        continue;
+      }
       if (ph.conv != 0.0) launch_conv_elements(L[l].g, tab, L[l].W, Ce, s);
       launch_block_factor(L[l].g, tab, ph, L[l].bs, Ce, L[l].factors, opt.precision, fstat, s);
     }
@@ -473,6 +526,9 @@ void wr_default_options(wr_options* o) {
   o->gmres_maxit = 200;
   o->patch_assembly = WR_PATCH_SUBMATRIX;
   o->scatter_weight = WR_WEIGHT_ONE;
+  o->store_factors = WR_STORE;
+  o->recompute_slabs = 0;
+  o->memory_budget_mb = 0;
 }
 
 static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, void* stream);
@@ -520,6 +576,10 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
          "patch_assembly must be WR_PATCH_SUBMATRIX or WR_PATCH_LOCAL");
     need(c->opt.scatter_weight == WR_WEIGHT_ONE || c->opt.scatter_weight == WR_WEIGHT_MULTIPLICITY,
          "scatter_weight must be WR_WEIGHT_ONE or WR_WEIGHT_MULTIPLICITY");
+    need(c->opt.store_factors == WR_STORE || c->opt.store_factors == WR_RECOMPUTE ||
+             c->opt.store_factors == WR_STORE_AUTO,
+         "store_factors must be WR_STORE, WR_RECOMPUTE or WR_STORE_AUTO");
+    need(c->opt.recompute_slabs >= 0 && c->opt.memory_budget_mb >= 0, "bad recompute_slabs / memory_budget_mb");
     c->s = static_cast<cudaStream_t>(stream);
     c->k = p->k; c->q = p->q; c->N = p->n_slabs; c->T = p->T;
     c->ph.kind = p->kind; c->ph.steady = p->steady; c->ph.nu = p->nu; c->ph.conv = p->conv; c->ph.T = p->T;
@@ -530,7 +590,39 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
     for (int n = p->n_coarse; n <= p->n_fine; n *= 2) ns.push_back(n);
     const int ms = patch_ms(p->k), nt = p->q + 1;
     const size_t fsz = factor_elem_bytes(c->opt.precision);
-    size_t max_ce = 0, max_ye = 0, max_yp = 0;
+    const int nsmooth = (int)ns.size() - 1;
+    const int nw = c->opt.recompute_slabs > 0 ? std::min(c->opt.recompute_slabs, p->n_slabs)
+                                              : std::max(1, (p->n_slabs + 15) / 16);
+    // how many of the finest smoothed levels recompute their factors
+    int nrec = 0;
+    if (c->forced_recompute >= 0) {
+      nrec = c->forced_recompute;
+    } else if (c->opt.store_factors == WR_RECOMPUTE) {
+      nrec = nsmooth;
+    } else if (c->opt.store_factors == WR_STORE_AUTO) {
+      // the fewest recomputing levels whose allocations fit the budget (store all
+      // when no budget is given and no device may be queried, as in a dry run)
+      int64_t budget = (int64_t)c->opt.memory_budget_mb << 20;
+      if (budget == 0 && !c->dry) {
+        size_t fr = 0, tot = 0;
+        WR_CUDA(cudaMemGetInfo(&fr, &tot));
+        budget = (int64_t)(0.92 * (double)fr);
+      }
+      nrec = 0;
+      if (budget > 0) {
+        nrec = nsmooth;
+        for (int r = 0; r <= nsmooth; ++r) {
+          wr_ctx t;
+          t.dry = true;
+          t.forced_recompute = r;
+          if (create_impl(&t, p, &c->opt, nullptr) == WR_OK && t.bytes <= budget) {
+            nrec = r;
+            break;
+          }
+        }
+      }
+    }
+    size_t max_ce = 0, max_ye = 0, max_yp = 0, max_fw = 0;
     for (size_t l = 0; l < ns.size(); ++l) {
       Level lv;
       lv.g = make_geom(ns[l], p->k, p->q, p->n_slabs, p->T);
@@ -549,15 +641,21 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
       lv.z = c->alloc<double>(nd);
       lv.t = c->alloc<double>(nd);
       const size_t nvl = p->k + 2, nvle = nvl * nvl, elem = nt * (2 * nvle + (p->k + 1) * (p->k + 1));
-      max_ce = std::max(max_ce, (size_t)p->n_slabs * lv.g.ncells() * nt * 4 * nvle * nvle);
+      lv.recompute = l >= 1 && (int)l > nsmooth - nrec;
+      lv.nw = lv.recompute ? nw : p->n_slabs;
+      max_ce = std::max(max_ce, (size_t)lv.nw * lv.g.ncells() * nt * 4 * nvle * nvle);
       max_ye = std::max(max_ye, (size_t)p->n_slabs * lv.g.ncells() * elem);
       if (l >= 1) {
-        const size_t nf = (size_t)lv.g.npatch() * p->n_slabs * nt * nt * factor_block_elems(p->k, c->opt.precision);
-        void* f = nullptr;
-        if (fsz == 2) f = c->alloc<uint16_t>(nf);
-        else if (fsz == 4) f = c->alloc<float>(nf);
-        else f = c->alloc<double>(nf);
-        lv.factors = f;
+        const size_t per_slab = (size_t)lv.g.npatch() * nt * nt * factor_block_elems(p->k, c->opt.precision);
+        if (lv.recompute) {
+          max_fw = std::max(max_fw, per_slab * nw);
+        } else {
+          void* f = nullptr;
+          if (fsz == 2) f = c->alloc<uint16_t>(per_slab * p->n_slabs);
+          else if (fsz == 4) f = c->alloc<float>(per_slab * p->n_slabs);
+          else f = c->alloc<double>(per_slab * p->n_slabs);
+          lv.factors = f;
+        }
         max_yp = std::max(max_yp, (size_t)lv.g.npatch() * p->n_slabs * nt * ms);
       }
       c->L.push_back(lv);
@@ -568,6 +666,11 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
     c->cbs.ms = coarse_ms(p->k, p->n_coarse);
     need(2 * c->cbs.nvg * c->cbs.nvg + c->cbs.npg * c->cbs.npg <= c->cbs.ms, "coarse block exceeds the slot layout");
     c->cfactors = c->alloc<double>((size_t)p->n_slabs * nt * nt * block_elems(c->cbs.ms, WR_FP64));
+    if (max_fw > 0) {
+      if (fsz == 2) c->fwin = c->alloc<uint16_t>(max_fw);
+      else if (fsz == 4) c->fwin = c->alloc<float>(max_fw);
+      else c->fwin = c->alloc<double>(max_fw);
+    }
     c->Ce = c->alloc<double>(p->conv != 0.0 ? max_ce : 1);
     c->ye = c->alloc<double>(max_ye);
     c->Yp = c->alloc<double>(max_yp);
@@ -610,6 +713,13 @@ int wr_num_levels(const wr_ctx* c, int* out) {
 int wr_ndofs(const wr_ctx* c, int level, int64_t* out) {
   if (!c || !out || level < 0 || level >= (int)c->L.size()) return WR_ERR_ARG;
   *out = c->L[level].g.ndofs;
+  return WR_OK;
+}
+
+int wr_factor_storage(const wr_ctx* c, int level, int* stored, int* window_slabs) {
+  if (!c || level < 1 || level >= (int)c->L.size()) return WR_ERR_ARG;
+  if (stored) *stored = c->L[level].recompute ? 0 : 1;
+  if (window_slabs) *window_slabs = c->L[level].nw;
   return WR_OK;
 }
 

@@ -183,13 +183,18 @@ void launch_conv_elements(const LevelGeom& g, const FeTables& T, const double* W
                           cudaStream_t s);
 void launch_inject(const LevelGeom& gf, const LevelGeom& gc, const double* Wf, double* Wc,
                    cudaStream_t s);
-// st: a device int of the caller's (zero-pivot flag), read back after the launch
+// st: a device int of the caller's (zero-pivot flag); with check it is cleared
+// before and read back after the launch (a host synchronisation), else left as is
 void launch_block_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph,
                          const BlockSet& bs, const double* Ce, void* factors, int precision, int* st,
-                         cudaStream_t s);
+                         cudaStream_t s, bool check = true);
+// Patch blocks (kind 0) write [slab][patch][a][slot] outputs to out; the coarse
+// block (kind 1) writes the solution.  A window of slabs is g with N = window
+// length, r and out offset to the window's first slab, factors of the window,
+// and prev = the patch outputs of the slab before it (null: zero jump state).
 void launch_block_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs,
                         const void* factors, int precision, const double* r, double* out,
-                        int* err, cudaStream_t s);
+                        int* err, cudaStream_t s, const double* prev = nullptr);
 void launch_scatter(const LevelGeom& g, const BlockSet& bs, const double* Yp, double* y,
                     cudaStream_t s);
 void launch_restrict(const LevelGeom& gf, const LevelGeom& gc, const FeTables& T,

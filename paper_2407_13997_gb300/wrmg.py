@@ -18,6 +18,7 @@ WR_ERR_ARG, WR_ERR_NOMEM, WR_ERR_CUDA, WR_ERR_NOT_CONVERGED, WR_ERR_TIMEOUT, WR_
 WR_FP64, WR_FP32, WR_BF16 = 0, 1, 2
 WR_PATCH_SUBMATRIX, WR_PATCH_LOCAL = 0, 1
 WR_WEIGHT_ONE, WR_WEIGHT_MULTIPLICITY = 0, 1
+WR_RECOMPUTE, WR_STORE, WR_STORE_AUTO = 0, 1, 2
 _STATUS = {1: "WR_ERR_ARG", 2: "WR_ERR_NOMEM", 3: "WR_ERR_CUDA", 4: "WR_ERR_NOT_CONVERGED",
            5: "WR_ERR_TIMEOUT", 6: "WR_ERR_NAN", 7: "WR_ERR_STATE"}
 
@@ -41,7 +42,9 @@ class Options(ctypes.Structure):
                 ("cheb_hi", ctypes.c_double), ("eig_steps", ctypes.c_int), ("newton_rtol", ctypes.c_double),
                 ("newton_maxit", ctypes.c_int), ("ew", ctypes.c_int), ("eta_fixed", ctypes.c_double),
                 ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
-                ("patch_assembly", ctypes.c_int), ("scatter_weight", ctypes.c_int)]
+                ("patch_assembly", ctypes.c_int), ("scatter_weight", ctypes.c_int),
+                ("store_factors", ctypes.c_int), ("recompute_slabs", ctypes.c_int),
+                ("memory_budget_mb", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -69,6 +72,7 @@ _SIGS = {
     "wr_num_levels": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "wr_ndofs": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
     "wr_device_bytes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "wr_factor_storage": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "wr_patch_dofs": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int)]),
     "wr_initial_guess": (ctypes.c_int, [_P, _P]),
@@ -253,6 +257,12 @@ class Context:
         out = ctypes.c_int64()
         self._check(self._lib.wr_device_bytes(self._h, ctypes.byref(out)))
         return out.value
+
+    def factor_storage(self, level):
+        """(stored, window_slabs) of a smoothed level."""
+        st, nw = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.wr_factor_storage(self._h, level, ctypes.byref(st), ctypes.byref(nw)))
+        return bool(st.value), nw.value
 
     def vector(self, level=None):
         import torch

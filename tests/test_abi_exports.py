@@ -68,3 +68,22 @@ def test_allocation_estimate_runs_on_the_host(libpath):
     bad.k = 3
     with pytest.raises(wrmg.WrmgError):
         wrmg.estimate_bytes(bad)
+
+
+def test_store_or_recompute_plan_on_the_host(libpath):
+    """The planner of wr_create (run dry by wr_estimate_bytes): recomputing the
+    factors needs far less memory than storing them, and the automatic choice keeps
+    the fewest recomputing levels that fit the budget."""
+    from paper_2407_13997_gb300 import inputs, wrmg
+    w = inputs.fourier_64x64_q3q2_dg1()
+    est = lambda **kw: wrmg.estimate_bytes(w, wrmg.default_options(**kw))
+    store = est(store_factors=wrmg.WR_STORE)
+    rec = est(store_factors=wrmg.WR_RECOMPUTE, recompute_slabs=4)
+    assert rec < store / 4
+    mib = lambda b: int(b // (1 << 20)) + 1
+    assert est(store_factors=wrmg.WR_STORE_AUTO) == store                     # no budget given: store
+    assert est(store_factors=wrmg.WR_STORE_AUTO, memory_budget_mb=mib(store)) == store
+    mid = (store + rec) // 2
+    auto = est(store_factors=wrmg.WR_STORE_AUTO, memory_budget_mb=mib(mid), recompute_slabs=4)
+    assert rec <= auto <= mid + (1 << 20)
+    assert est(store_factors=wrmg.WR_STORE_AUTO, memory_budget_mb=1, recompute_slabs=4) == rec

@@ -211,3 +211,35 @@ def test_smoother_variants_match_oracle(w, assembly, weight):
     ctx.vcycle(cuda(b), x)
     assert torch.isfinite(x).all()
     s.ctx.close()
+
+
+@pytest.mark.parametrize("w", [CASES[0], CASES[1], CASES[2]], ids=[IDS[0], IDS[1], IDS[2]])
+@pytest.mark.parametrize("window", [1, 2])
+@pytest.mark.parametrize("prec", [wrmg.WR_FP64, wrmg.WR_FP32], ids=["fp64", "fp32"])
+def test_recomputed_factors_give_the_stored_result_bitwise(w, window, prec):
+    """Factors recomputed in windows of slabs at every apply (ragged last window
+    included) are the stored factors, so the smoother, the eigen-estimates and the
+    V-cycle are bitwise those of the stored form."""
+    st = Setup(w, options=wrmg.default_options(precision=prec))
+    rc = wrmg.Context(w, wrmg.default_options(precision=prec, store_factors=wrmg.WR_RECOMPUTE,
+                                              recompute_slabs=window))
+    W = cuda(st.W[-1])
+    st.ctx.linearise(W, eig=True)
+    rc.linearise(W, eig=True)
+    for l in range(1, st.ctx.num_levels):
+        assert rc.factor_storage(l) == (False, window)
+        assert st.ctx.factor_storage(l) == (True, w.N)
+        assert rc.get_lambda(l) == st.ctx.get_lambda(l)
+        r = cuda(st.rng.standard_normal(st.ctx.ndofs(l)))
+        y1, y2 = st.ctx.vector(l), rc.vector(l)
+        st.ctx.patch_apply(l, r, y1)
+        rc.patch_apply(l, r, y2)
+        assert torch.equal(y1, y2), l
+    b = cuda(st.rng.standard_normal(st.ctx.ndofs()))
+    x1, x2 = st.ctx.vector(), rc.vector()
+    st.ctx.vcycle(b, x1)
+    rc.vcycle(b, x2)
+    assert torch.equal(x1, x2)
+    assert rc.device_bytes() < st.ctx.device_bytes() or w.N <= window
+    st.ctx.close()
+    rc.close()
