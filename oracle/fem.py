@@ -57,6 +57,7 @@ class Problem:
     nu: float = 1e-2
     conv: float = 1.0
     T: float = 1.0
+    t0: float = 0.0          # time at the start of slab 0: the slabs cover [t0, t0 + T]
     steady: bool = False
     mx: np.ndarray = field(default_factory=lambda: np.zeros(0, dtype=np.int64))
     my: np.ndarray = field(default_factory=lambda: np.zeros(0, dtype=np.int64))
@@ -115,6 +116,8 @@ class Discretisation:
         self.ndofs = N * self.nt * self.S
         self.off_p = 2 * self.nv ** 2
         self.tm = TimeMatrices(q)
+        # u(t0) for the jump of slab 0: the exact data unless a spatial block is set here
+        self.initial_state = None
         self._tables()
         self._linear_matrices()
 
@@ -149,7 +152,7 @@ class Discretisation:
         return (np.linspace(0, 1, self.nv), np.linspace(0, 1, self.np_))
 
     def time_nodes(self, slab):
-        return (slab + self.tm.nodes) * self.dt
+        return self.pb.t0 + (slab + self.tm.nodes) * self.dt
 
     # ------------------------------------------------------------ element tables
     def _tables(self):
@@ -277,10 +280,17 @@ class Discretisation:
         return g
 
     def initial_velocity(self):
-        """Spatial block holding the nodal interpolant of u(0) (pressure part zero)."""
+        """Spatial block holding u(t0) (pressure part zero): the velocity part of
+        ``initial_state`` when it is set (e.g. the end state of a previous time
+        step), else the nodal interpolant of the exact u(t0)."""
+        nv2 = self.nv ** 2
+        if self.initial_state is not None:
+            u0 = np.zeros(self.S)
+            u0[:2 * nv2] = self.initial_state[:2 * nv2]
+            return u0
         xv, _ = self.node_coords()
         X, Y = np.meshgrid(xv, xv, indexing="xy")
-        ux, uy = self.pb.exact_velocity(X, Y, 0.0)
+        ux, uy = self.pb.exact_velocity(X, Y, self.pb.t0)
         u0 = np.zeros(self.S)
         nv2 = self.nv ** 2
         u0[:nv2] = np.broadcast_to(ux, X.shape).ravel()
@@ -310,7 +320,7 @@ class Discretisation:
         out = np.zeros((self.nt, self.S))
         nv2 = self.nv ** 2
         for g, (sg, wg) in enumerate(zip(tm.tq, tm.wq)):
-            t = (slab + sg) * self.dt
+            t = self.pb.t0 + (slab + sg) * self.dt
             fx, fy = self.pb.forcing(self.qpx, self.qpy, t)
             fx = np.broadcast_to(fx, self.qpx.shape)
             fy = np.broadcast_to(fy, self.qpy.shape)

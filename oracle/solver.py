@@ -31,6 +31,8 @@
 Parity unpinned by the paper (fixed by convention only): the EW constants, the
 Arnoldi start vector and the FGMRES restart length.
 """
+import dataclasses
+
 import numpy as np
 import scipy.linalg as sla
 
@@ -299,3 +301,31 @@ def newton_solve(hier, U0=None, stats=None):
     if stats is not None:
         stats.update(hist)
     return U
+
+
+def timestepping_solve(n_fine, n_coarse, k, q, N, problem, opts=None, stats=None):
+    """The timestepping comparator (Sec. 5): the N slabs of ``problem`` solved one
+    after another, each as the one-slab space-time problem on
+    [t0 + n dt, t0 + (n + 1) dt] whose slab-0 jump takes the previous step's end
+    state (the last temporal DoF of its slab), with the same Newton-FGMRES-V-cycle
+    solver coupling across one time element only.  Because the space-time system
+    is block lower bidiagonal in slabs, its solution is the all-at-once one.
+    Returns the N-slab global vector; stats (if given) gets per-step histories."""
+    dt = problem.T / N
+    prev = None
+    out = []
+    steps = []
+    for n in range(N):
+        pb = dataclasses.replace(problem, t0=problem.t0 + n * dt, T=dt)
+        hier = Hierarchy(n_fine, n_coarse, k, q, 1, pb, opts)
+        if prev is not None:
+            hier.fine.initial_state = prev
+        st = {}
+        U = newton_solve(hier, stats=st)
+        steps.append(st)
+        out.append(U)
+        d = hier.fine
+        prev = U[d.block(0, d.nt - 1):d.block(0, d.nt - 1) + d.S].copy()
+    if stats is not None:
+        stats["steps"] = steps
+    return np.concatenate(out)

@@ -5,7 +5,7 @@ import scipy.sparse as sp
 
 from oracle.fem import Discretisation, Problem
 from oracle.solver import (CoarseSolver, Hierarchy, Options, arnoldi_ritz_max, chebyshev, fgmres,
-                           newton_solve, splitmix64_raw, splitmix64_uniform)
+                           newton_solve, splitmix64_raw, splitmix64_uniform, timestepping_solve)
 from tests.test_oracle_fem import direct_solve
 
 
@@ -108,3 +108,34 @@ def test_taylor_green_config_solves_to_tolerance_and_is_accurate():
     off = d.block(d.N - 1, 0)
     err = np.abs(U[off:off + d.off_p] - ex[off:off + d.off_p]).max()
     assert err < 0.02, err
+
+
+@pytest.mark.parametrize("kind,k,q", [("taylor_green", 1, 1), ("poly", 2, 1), ("taylor_green", 1, 0)])
+def test_timestepping_reaches_the_all_at_once_solution(kind, k, q):
+    """The space-time system is block lower bidiagonal in slabs (causal), so solving
+    slab after slab with the previous end state as initial data must give the
+    all-at-once discrete solution; the time offset enters the boundary data (Taylor-
+    Green) and the forcing (poly), the end state the jump.  Both are taken from the
+    brute-force direct Newton of the whole space-time system."""
+    pb = Problem(kind=kind, nu=0.05, conv=1.0, T=0.6)
+    N = 3
+    ref = direct_solve(Discretisation(4, k, q, N, pb), tol=1e-13)
+    U = timestepping_solve(4, 2, k, q, N, pb, Options(newton_rtol=1e-13, ew=False, eta_fixed=1e-12))
+    assert np.abs(U - ref).max() < 1e-9 * np.abs(ref).max()
+    # the first step alone is the one-slab problem on [0, T/N] with the exact initial data
+    d1 = Discretisation(4, k, q, 1, Problem(kind=kind, nu=0.05, conv=1.0, T=0.2))
+    first = direct_solve(d1, tol=1e-13)
+    assert np.abs(U[:d1.ndofs] - first).max() < 1e-9 * np.abs(first).max()
+
+
+def test_shifted_problem_uses_its_start_time():
+    """A one-slab problem starting at t0 has the boundary data and the initial state
+    of the exact Taylor-Green solution at t0 and its nodes (closed form)."""
+    pb = Problem(kind="taylor_green", nu=0.05, conv=1.0, T=0.2, t0=0.4)
+    d = Discretisation(4, 1, 1, 1, pb)
+    xv, _ = d.node_coords()
+    X, Y = np.meshgrid(xv, xv, indexing="xy")
+    e = np.exp(-2 * 0.05 * np.pi ** 2 * 0.4)
+    u0 = d.initial_velocity()
+    assert np.allclose(u0[:d.nv ** 2], (-np.cos(np.pi * X) * np.sin(np.pi * Y) * e).ravel(), atol=1e-15)
+    assert np.allclose(d.time_nodes(0), 0.4 + 0.2 * d.tm.nodes)
