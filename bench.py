@@ -17,6 +17,7 @@ larger than L2, so no flush is needed between steps.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -55,7 +56,7 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=96.0, help="serve form: device-memory budget")
     ap.add_argument("--full-mix", action="store_true",
                     help="serve form: draw n and N from {16, 32, 64} (default {16, 32})")
-    ap.add_argument("--form", default="cycle", choices=["cycle", "precision", "batch", "serve", "smoother"],
+    ap.add_argument("--form", default="cycle", choices=["cycle", "precision", "batch", "serve", "smoother", "timestepping"],
                     help="cycle: the V(2,2) throughput line (default); precision: the FP64/FP32/BF16 "
                          "solves of the 128x128 Q2/Q1 DG(0) 128-slab workload")
     return ap.parse_args()
@@ -505,19 +506,21 @@ def run_serve_form(args):
             ctx.close()
     torch.cuda.synchronize()
     # plain FP64, request by request
-    service, refs = [], []
+    service, refs, seq_status = [], [], []
     for w in reqs:
         t0 = time.perf_counter()
         ctx = wrmg.Context(w, o64)
         U = ctx.vector()
         ctx.initial_guess(U)
-        ctx.solve(U, check=False)
+        st = ctx.solve(U, check=False)
         refs.append(U.cpu().numpy())
         ctx.close()
         service.append(time.perf_counter() - t0)
+        seq_status.append(st["status"])
         del U
     torch.cuda.empty_cache()
-    out["sequential_fp64"] = {"service_s_total": sum(service), "service_s_median": statistics.median(service),
+    out["sequential_fp64"] = {"converged": sum(1 for c in seq_status if c == wrmg.WR_OK),
+                              "service_s_total": sum(service), "service_s_median": statistics.median(service),
                               "solves_per_s_saturated": len(reqs) / sum(service), "rates": {}}
     out["rates"] = {}
     errs = []
@@ -551,14 +554,20 @@ def run_serve_form(args):
         sv.close()
         lat = [r[3] for r in res]
         ok = sum(1 for r in res if r[0] == wrmg.WR_OK)
-        for r, ref in zip(res, refs):
-            if r[1] is not None:
+        for r, ref, c64 in zip(res, refs, seq_status):
+            if r[1] is not None and r[0] == wrmg.WR_OK and c64 == wrmg.WR_OK:
                 errs.append(float(np.abs(r[1] - ref).max() / max(np.abs(ref).max(), 1e-300)))
+        out.setdefault("per_request", [{"name": w.name, "nu": w.nu, "fp64_status": c, "fp64_s": t}
+                                       for w, c, t in zip(reqs, seq_status, service)])
+        for pr, r in zip(out["per_request"], res):
+            pr[f"served_status_{int(rate)}"] = r[0]
+            pr[f"served_latency_ms_{int(rate)}"] = r[3]
         out["rates"][str(int(rate))] = {
             "solves_per_s": len(reqs) / (t_end - t_start - arr[0]), "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "converged": ok, "peak_inflight": st["peak_inflight"],
             "peak_bytes": st["peak_bytes"], "newton_total": sum(r[2]["newton_its"] for r in res),
             "fgmres_total": sum(sum(r[2]["gmres"]) for r in res)}
+    # over the requests both arms solved to 1e-8
     out["max_rel_diff_vs_fp64_solution"] = max(errs) if errs else None
     top = str(int(max(rates)))
     out["solves_per_s_ratio_vs_sequential_fp64"] = (out["rates"][top]["solves_per_s"] /
@@ -610,6 +619,59 @@ def run_smoother_form(args):
     print(json.dumps(out), flush=True)
 
 
+def run_timestepping_form(args):
+    """Timestepping comparator on the Chorin problem (R = 10, t in [0, 0.1]): the
+    all-at-once WRMG solve against N one-slab solves in sequence (the same
+    Newton-FGMRES-multigrid machinery coupling one time element), for
+    Q2/Q1 and Q3/Q2 with DG(0) and DG(1) and N = 10, 20, 40; solve times (context
+    set-up excluded, every linearisation included), iterations, and the largest
+    difference between the two discrete solutions."""
+    import torch
+    from paper_2407_13997_gb300 import inputs, wrmg
+    torch.cuda.set_device(0)
+    n = args.n or 32
+    out = {"form": "timestepping", "problem": "chorin R=10, nu=1, t in [0, 0.1]", "n": n, "runs": []}
+    warm = inputs.chorin(8, 1, 0, 2)
+    for w in (warm, dataclasses.replace(warm, N=1, T=warm.T / warm.N)):
+        ctx = wrmg.Context(w)
+        U = ctx.vector()
+        ctx.initial_guess(U)
+        ctx.solve(U, check=False)
+        ctx.close()
+    for k, q in ((1, 0), (1, 1), (2, 0), (2, 1)):
+        for N in (10, 20, 40):
+            w = inputs.chorin(n, k, q, N)
+            ctx = wrmg.Context(w)
+            U = ctx.vector()
+            ctx.initial_guess(U)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = ctx.solve(U, check=False)
+            torch.cuda.synchronize()
+            t_wrmg = time.perf_counter() - t0
+            ctx.close()
+            one = dataclasses.replace(w, N=1, T=w.T / N)
+            c1 = wrmg.Context(one)
+            Ut = torch.zeros(w.ndofs(), dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sts = c1.solve_timestepping(Ut, N, check=False)
+            torch.cuda.synchronize()
+            t_ts = time.perf_counter() - t0
+            c1.close()
+            diff = float((Ut - U).abs().max() / U.abs().max())
+            out["runs"].append({
+                "space": f"Q{k + 1}/Q{k}", "time": f"DG({q})", "N": N, "ndofs": w.ndofs(),
+                "wrmg": {"status": st["status"], "seconds": t_wrmg, "newton": st["newton_its"],
+                         "fgmres_total": sum(st["gmres"])},
+                "timestepping": {"status": sts["status"], "seconds": t_ts,
+                                 "newton_per_step": sts["newton_its"] / N,
+                                 "fgmres_per_step": sum(sts["gmres_per_step"][:N]) / min(N, 64)},
+                "max_rel_diff": diff})
+            del U, Ut
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -622,6 +684,8 @@ def main():
         run_serve_form(args)
     elif args.form == "smoother":
         run_smoother_form(args)
+    elif args.form == "timestepping":
+        run_timestepping_form(args)
     else:
         run_ours(args)
 

@@ -103,6 +103,7 @@ typedef struct {
     int n_modes;    /* WR_FOURIER: number of modes (<= 8), host arrays below                 */
     const int *mx, *my;
     const double *amp;
+    double t0;      /* time at the start of slab 0: the slabs cover [t0, t0 + T] (0)           */
 } wr_problem;
 
 typedef struct {
@@ -221,6 +222,26 @@ int wr_project_pressure(wr_ctx *c, double *x);
 int wr_solve(wr_ctx *c, double *U_inout, wr_stats *stats);
 /* The same with a HOST U (copied in and out). */
 int wr_solve_host(wr_ctx *c, double *U_host, wr_stats *stats);
+
+/* Sets the velocity that the slab-0 jump term of the residual takes as u(t0)
+ * (Eq. nsfem's U_0^-): u0 is a device spatial block of the finest level (S = 2 nv^2
+ * + np^2 doubles, canonical field order; its pressure part is ignored), copied;
+ * NULL restores the problem's own initial data (the exact u(t0), or zero). */
+int wr_set_initial_state(wr_ctx *c, const double *u0);
+
+/* The timestepping comparator (Sec. 5): the context must have n_slabs = 1 (one
+ * time element of width T starting at the problem's t0); step i solves that
+ * element moved to [t0 + i T, t0 + (i + 1) T] with Newton-FGMRES-WRMG, taking as
+ * initial state the end state of step i - 1 (the last temporal DoF of its slab;
+ * step 0 takes the state of wr_set_initial_state, or the problem's own data).
+ * U: device array of n_steps one-slab solutions in sequence (n_steps (q+1) S
+ * doubles, together the canonical layout of the n_steps-slab problem); it is
+ * overwritten (each step starts from its boundary lift).  st (may be NULL):
+ * newton_its, vcycles, setup_ms and krylov_ms summed over the steps;
+ * gmres_its[i] = FGMRES iterations of step i and residual_norms[i] = its final
+ * ||F|| (i < 64).  Returns the first failing step's status, else WR_OK; the
+ * context keeps the state of the last step (wr_set_initial_state resets it). */
+int wr_solve_timestepping(wr_ctx *c, int n_steps, double *U, wr_stats *st);
 
 /* ------------------------------------------------------------------ batching
  * A wr_batch holds many independent space-time solves (uneven meshes, slab

@@ -628,6 +628,7 @@ int wr_batch_create(wr_batch** out, int n, const wr_problem* ps, const wr_option
       M.L = L;
       M.ph.kind = p.kind; M.ph.steady = p.steady; M.ph.nu = p.nu; M.ph.conv = p.conv; M.ph.T = p.T;
       M.ph.n_modes = p.n_modes;
+      M.ph.t0 = p.t0;
       for (int i = 0; i < p.n_modes; ++i) { M.ph.mx[i] = p.mx[i]; M.ph.my[i] = p.my[i]; M.ph.amp[i] = p.amp[i]; }
       for (int l = 0, nn = p.n_coarse; l <= L; ++l, nn *= 2) M.g.push_back(make_geom(nn, p.k, p.q, p.n_slabs, p.T));
       M.lam.assign(L + 1, 0.0);

@@ -132,9 +132,11 @@ __device__ __forceinline__ void element_body(const LevelGeom& g, const FeTables&
       up = (LIN && dir) ? 0.0 : x[off];
     } else if (LIN) {
       up = 0.0;
+    } else if (ph.u0) {
+      up = ph.u0[sp];
     } else {
       double ux, uy;
-      exact_velocity(ph, gx * (h / (K + 1)), gy * (h / (K + 1)), 0.0, ux, uy);
+      exact_velocity(ph, gx * (h / (K + 1)), gy * (h / (K + 1)), ph.t0, ux, uy);
       up = c == 0 ? ux : uy;
     }
     s.vn[SM::FUP + c][l] = up;
@@ -197,7 +199,7 @@ __device__ __forceinline__ void element_body(const LevelGeom& g, const FeTables&
     if constexpr (!LIN) {
       const double xx = (CI + T.xq[qx]) * h, yy = (CJ + T.xq[qy]) * h;
       for (int gq = 0; gq < Q + 2; ++gq)
-        forcing(ph, xx, yy, (slab + T.tq[gq]) * dt, fxg[gq], fyg[gq]);
+        forcing(ph, xx, yy, ph.t0 + (slab + T.tq[gq]) * dt, fxg[gq], fyg[gq]);
     }
 #pragma unroll
     for (int a = 0; a < d::NT; ++a) {
@@ -342,7 +344,7 @@ __device__ __forceinline__ void assemble_body(const LevelGeom& g, const FeTables
         y[idx] = x[idx];
       } else {
         double ux, uy;
-        exact_velocity(ph, gx * (g.h / (K + 1)), gy * (g.h / (K + 1)), (slab + T.tnode[a]) * g.dt, ux, uy);
+        exact_velocity(ph, gx * (g.h / (K + 1)), gy * (g.h / (K + 1)), ph.t0 + (slab + T.tnode[a]) * g.dt, ux, uy);
         y[idx] = x[idx] - (c == 0 ? ux : uy);
       }
       return;
@@ -402,7 +404,8 @@ __device__ __forceinline__ void boundary_body(const LevelGeom& g, const FeTables
     const int gx = t % nv, gy = t / nv;
     if (vel_dirichlet(g, gx, gy)) {
       double ux, uy;
-      exact_velocity(ph, gx * (g.h / (g.k + 1)), gy * (g.h / (g.k + 1)), (slab + T.tnode[a]) * g.dt, ux, uy);
+      exact_velocity(ph, gx * (g.h / (g.k + 1)), gy * (g.h / (g.k + 1)), ph.t0 + (slab + T.tnode[a]) * g.dt, ux,
+                     uy);
       v = c == 0 ? ux : uy;
     }
   }

@@ -60,6 +60,8 @@ struct wr_ctx {
   int* slots = nullptr;
   int* derr = nullptr;   // device error flag of the bounded waits
   int* fstat = nullptr;  // device zero-pivot flag of the factorisation
+  double t0 = 0.0;       // the problem's start time
+  double* u0 = nullptr;  // slab-0 initial state set by wr_set_initial_state (a finest-level spatial block)
   std::vector<void*> allocs;
   int64_t bytes = 0;
   bool linearised = false;
@@ -584,6 +586,8 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
     c->k = p->k; c->q = p->q; c->N = p->n_slabs; c->T = p->T;
     c->ph.kind = p->kind; c->ph.steady = p->steady; c->ph.nu = p->nu; c->ph.conv = p->conv; c->ph.T = p->T;
     c->ph.n_modes = p->n_modes;
+    c->ph.t0 = p->t0;
+    c->t0 = p->t0;
     for (int m = 0; m < p->n_modes; ++m) { c->ph.mx[m] = p->mx[m]; c->ph.my[m] = p->my[m]; c->ph.amp[m] = p->amp[m]; }
     c->tab = build_tables(p->k, p->q);
     std::vector<int> ns;
@@ -687,8 +691,11 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
     c->slots = c->alloc<int>(2 * ms);
     c->derr = c->alloc<int>(1);
     c->fstat = c->alloc<int>(1);
+    c->u0 = c->alloc<double>(c->fine().g.S);
     if (c->dry) return WR_OK;
-    WR_CUDA(cudaMemset(c->derr, 0, sizeof(int)));
+    // on the context's stream: its memory may come from the stream-ordered pool
+    WR_CUDA(cudaMemsetAsync(c->derr, 0, sizeof(int), c->s));
+    WR_CUDA(cudaStreamSynchronize(c->s));
     WR_CUDA(cudaMallocHost(&c->hres, sizeof(double)));
     WR_CUDA(cudaMallocHost(&c->herr, sizeof(int)));
     *c->herr = 0;
@@ -884,6 +891,55 @@ int wr_solve(wr_ctx* c, double* U, wr_stats* st) {
     if (rc == WR_ERR_NOT_CONVERGED) c->err = "Newton iteration limit reached";
     if (rc == WR_ERR_NAN) c->err = "residual norm is not finite";
     return rc;
+  });
+}
+
+int wr_set_initial_state(wr_ctx* c, const double* u0) {
+  return guarded(c, [&]() -> int {
+    need(c != nullptr, "null context");
+    if (!u0) {
+      c->ph.u0 = nullptr;
+      return WR_OK;
+    }
+    WR_CUDA(cudaMemcpyAsync(c->u0, u0, sizeof(double) * c->fine().g.S, cudaMemcpyDeviceToDevice, c->s));
+    c->ph.u0 = c->u0;
+    return WR_OK;
+  });
+}
+
+int wr_solve_timestepping(wr_ctx* c, int n_steps, double* U, wr_stats* st) {
+  return guarded(c, [&]() -> int {
+    need(c && U && n_steps >= 1, "null argument or n_steps < 1");
+    need(c->N == 1, "the timestepping comparator needs a one-slab context");
+    const LevelGeom& g = c->fine().g;
+    const int64_t step = g.ndofs, last = (int64_t)(g.nt - 1) * g.S;
+    wr_stats tot;
+    std::memset(&tot, 0, sizeof(tot));
+    int status = WR_OK;
+    for (int i = 0; i < n_steps; ++i) {
+      double* Ui = U + i * step;
+      c->ph.t0 = c->t0 + i * c->T;
+      if (i > 0) {  // the previous step's end state, held in the context's own buffer
+        WR_CUDA(cudaMemcpyAsync(c->u0, Ui - step + last, sizeof(double) * g.S, cudaMemcpyDeviceToDevice, c->s));
+        c->ph.u0 = c->u0;
+      }
+      launch_boundary_values(g, c->tab, c->ph, Ui, c->s);
+      wr_stats si;
+      const int rc = c->solve(Ui, &si);
+      tot.newton_its += si.newton_its;
+      tot.vcycles += si.vcycles;
+      tot.setup_ms += si.setup_ms;
+      tot.krylov_ms += si.krylov_ms;
+      if (i < 64) {
+        for (int j = 0; j < si.newton_its && j < 64; ++j) tot.gmres_its[i] += si.gmres_its[j];
+        tot.residual_norms[i] = si.residual_norms[si.newton_its < 64 ? si.newton_its : 64];
+      }
+      if (rc != WR_OK && status == WR_OK) status = rc;
+    }
+    c->ph.t0 = c->t0;
+    if (st) *st = tot;
+    if (status == WR_ERR_NOT_CONVERGED) c->err = "Newton iteration limit reached in a time step";
+    return status;
   });
 }
 

@@ -74,6 +74,8 @@ struct PhysParams {
   int n_modes;
   int mx[8], my[8];
   double amp[8];
+  double t0 = 0.0;              // time at the start of slab 0
+  const double* u0 = nullptr;   // slab-0 initial velocity: a spatial block (device), or null = exact u(t0)
 };
 
 struct LevelGeom {

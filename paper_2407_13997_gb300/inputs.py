@@ -49,6 +49,7 @@ class Workload:
     mx: np.ndarray = field(default_factory=lambda: np.zeros(0, dtype=np.int32))
     my: np.ndarray = field(default_factory=lambda: np.zeros(0, dtype=np.int32))
     amp: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    t0: float = 0.0  # time at the start of slab 0
 
     def ndofs(self, n=None):
         n = self.n_fine if n is None else n
@@ -61,6 +62,13 @@ def taylor_green_8x8():
     """Plain FP64 parity workload: 8x8 Q2/Q1, DG(0), 8 slabs on [0, 1], nu = 1e-2,
     decaying Taylor-Green data, coarsened to 2x2."""
     return Workload("tg_q2q1_dg0_n8_N8", 8, 2, 1, 0, 8, 1.0, 1e-2, 1.0, KIND_TAYLOR_GREEN)
+
+
+def chorin(n=16, k=1, q=0, N=10, R=10.0):
+    """The Chorin (Taylor-Green) test problem of Sec. 4 in its Reynolds-number form:
+    nu = 1, convection R, t in [0, 0.1], exact velocity data on the whole boundary,
+    n x n mesh coarsened to 2 x 2, N slabs."""
+    return Workload(f"chorin_R{R:g}_q{k + 1}q{k}_dg{q}_n{n}_N{N}", n, 2, k, q, N, 0.1, 1.0, R, KIND_TAYLOR_GREEN)
 
 
 def fourier_64x64_q3q2_dg1(seed=0):

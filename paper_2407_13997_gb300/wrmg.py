@@ -34,7 +34,8 @@ class Problem(ctypes.Structure):
                 ("n_slabs", ctypes.c_int), ("T", ctypes.c_double), ("nu", ctypes.c_double),
                 ("conv", ctypes.c_double), ("kind", ctypes.c_int), ("steady", ctypes.c_int),
                 ("n_modes", ctypes.c_int), ("mx", ctypes.POINTER(ctypes.c_int)),
-                ("my", ctypes.POINTER(ctypes.c_int)), ("amp", ctypes.POINTER(ctypes.c_double))]
+                ("my", ctypes.POINTER(ctypes.c_int)), ("amp", ctypes.POINTER(ctypes.c_double)),
+                ("t0", ctypes.c_double)]
 
 
 class Options(ctypes.Structure):
@@ -92,6 +93,8 @@ _SIGS = {
     "wr_project_pressure": (ctypes.c_int, [_P, _P]),
     "wr_solve": (ctypes.c_int, [_P, _P, ctypes.POINTER(Stats)]),
     "wr_solve_host": (ctypes.c_int, [_P, _P, ctypes.POINTER(Stats)]),
+    "wr_set_initial_state": (ctypes.c_int, [_P, _P]),
+    "wr_solve_timestepping": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(Stats)]),
     "wr_measure_fp64_tflops": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "wr_launch_count": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64)]),
     "wr_apply_jacobian_static": (ctypes.c_int, [ctypes.POINTER(Problem), _P, _P, _P, _P]),
@@ -181,7 +184,7 @@ def _problem(w):
     amp = np.ascontiguousarray(w.amp, dtype=np.float64)
     p = Problem(w.n_fine, w.n_coarse, w.k, w.q, w.N, w.T, w.nu, w.conv, w.kind, int(w.steady), len(amp),
                 mx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), my.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                amp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+                amp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), getattr(w, "t0", 0.0))
     return p, (mx, my, amp)
 
 
@@ -214,7 +217,7 @@ class Context:
                     workload.nu, workload.conv, workload.kind, int(workload.steady), len(self._amp),
                     self._mx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                     self._my.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                    self._amp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+                    self._amp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), getattr(workload, "t0", 0.0))
         self.options = options if options is not None else default_options()
         h = ctypes.c_void_p()
         rc = lib.wr_create(ctypes.byref(h), ctypes.byref(p), ctypes.byref(self.options), ctypes.c_void_p(stream))
@@ -330,11 +333,29 @@ class Context:
         return ms.value, n.value
 
     def solve(self, U, check=True):
+        """Newton solve in place; the returned statistics carry the status code."""
         st = Stats()
         rc = self._lib.wr_solve(self._h, _ptr(U), ctypes.byref(st))
         if check:
             self._check(rc)
-        return st.as_dict()
+        d = st.as_dict()
+        d["status"] = rc
+        return d
+
+    def set_initial_state(self, u0):
+        """u0: a CUDA float64 spatial block of the finest level (length S), or None."""
+        self._check(self._lib.wr_set_initial_state(self._h, _ptr(u0) if u0 is not None else None))
+
+    def solve_timestepping(self, U, n_steps, check=True):
+        """The timestepping comparator on a one-slab context; U holds n_steps slabs."""
+        st = Stats()
+        rc = self._lib.wr_solve_timestepping(self._h, int(n_steps), _ptr(U), ctypes.byref(st))
+        if check:
+            self._check(rc)
+        n = min(int(n_steps), 64)
+        return {"status": rc, "newton_its": st.newton_its, "vcycles": st.vcycles, "setup_ms": st.setup_ms,
+                "krylov_ms": st.krylov_ms, "gmres_per_step": list(st.gmres_its[:n]),
+                "final_residual_per_step": list(st.residual_norms[:n])}
 
     def solve_host(self, U, check=True):
         st = Stats()
@@ -365,7 +386,7 @@ class Batch:
             probs[i] = Problem(w.n_fine, w.n_coarse, w.k, w.q, w.N, w.T, w.nu, w.conv, w.kind, int(w.steady),
                                len(amp), mx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                my.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                               amp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+                               amp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), getattr(w, "t0", 0.0))
         self.options = options if options is not None else default_options()
         h = ctypes.c_void_p()
         rc = lib.wr_batch_create(ctypes.byref(h), n, probs, ctypes.byref(self.options), ctypes.c_void_p(stream))

@@ -5,4 +5,4 @@ from paper_2407_13997_gb300.inputs import KIND_NAMES
 
 def oracle_problem(w):
     return Problem(kind=KIND_NAMES[w.kind], nu=w.nu, conv=w.conv, T=w.T, steady=w.steady,
-                   mx=w.mx, my=w.my, amp=w.amp)
+                   mx=w.mx, my=w.my, amp=w.amp, t0=w.t0)
