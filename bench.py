@@ -228,6 +228,7 @@ def run_ours(args):
     import numpy as np
     import torch
     from paper_2407_13997_gb300 import inputs, wrmg
+    from paper_2407_13997_gb300.replicas import max_over_ranks
 
     rank, world, local = dist_info()
     torch.cuda.set_device(local)
@@ -282,10 +283,7 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     sm_ms, sm_n = ctx.profile_smoother(ctx.fine)
     ctx.profile(False)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     value = D * world * args.steps / (ms * 1e-3)
 
     # end to end through the host-buffer ABI call: H2D of b, cycle, D2H of x every step
@@ -300,10 +298,7 @@ def run_ours(args):
     for _ in range(args.steps):
         ctx.vcycle_host(bn, xn)
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
     assert np.isfinite(xn).all()
 
     alg_bytes, alg_flops = smoother_algorithmic(ctx, w, {wrmg.WR_FP64: 8, wrmg.WR_FP32: 4, wrmg.WR_BF16: 2}[prec])
@@ -412,11 +407,20 @@ def run_batch_form(args):
     import numpy as np
     import torch
     from paper_2407_13997_gb300 import inputs, wrmg
-    torch.cuda.set_device(0)
-    ws = inputs.batching_workloads(args.members or 256, seed=1)
+    from paper_2407_13997_gb300.replicas import max_over_ranks, shard, sum_over_ranks
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:  # each rank runs its own shard of the members; no data-path collective
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    all_ws = inputs.batching_workloads(args.members or 256, seed=1)
+    ws = [all_ws[i] for i in shard([w.ndofs() for w in all_ws], rank, world)]
     total = sum(w.ndofs() for w in ws)
-    out = {"form": "batch", "members": len(ws), "total_ndofs": total,
-           "mesh_mix": {str(n): sum(1 for w in ws if w.n_fine == n) for n in (8, 16, 24, 32, 48)}}
+    job_total = sum(w.ndofs() for w in all_ws)
+    out = {"form": "batch", "members": len(all_ws), "total_ndofs": job_total, "n_gpus": world,
+           "scaling": "strong (members sharded over GPUs)" if world > 1 else None,
+           "mesh_mix": {str(n): sum(1 for w in all_ws if w.n_fine == n) for n in (8, 16, 24, 32, 48)}}
     t0 = time.perf_counter()
     batch = wrmg.Batch(ws, wrmg.default_options(precision=wrmg.WR_FP32))
     torch.cuda.synchronize()
@@ -436,32 +440,41 @@ def run_batch_form(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = wrmg.launch_count()
+    if dist:
+        dist.barrier()
     e0.record()
     for _ in range(args.steps):
         batch.vcycle_resident()
     e1.record()
     torch.cuda.synchronize()
-    cyc = e0.elapsed_time(e1) / args.steps
+    cyc = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
     out["cycle_ms"] = cyc
-    out["dof_per_s_per_cycle"] = total / cyc * 1e3
+    out["dof_per_s_per_cycle"] = job_total / cyc * 1e3
     out["launches_per_cycle"] = (wrmg.launch_count() - launches0) / args.steps
     del Ws, bs, xs
     Us = batch.vectors()
     batch.initial_guess(Us)
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     st = batch.solve(Us, check=False)
     torch.cuda.synchronize()
-    solve_s = time.perf_counter() - t0
+    solve_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     conv = [s["residuals"][-1] <= 1e-8 * s["residuals"][0] for s in st]
-    out["batched_solve"] = {"seconds": solve_s, "solves_per_s": len(ws) / solve_s, "converged": int(sum(conv)),
+    nconv = int(sum_over_ranks(sum(conv), dist, "cuda"))
+    out["batched_solve"] = {"seconds": solve_s, "solves_per_s": len(all_ws) / solve_s, "converged": nconv,
                             "newton_max": max(s["newton_its"] for s in st),
                             "fgmres_total_mean": float(np.mean([sum(s["gmres"]) for s in st]))}
     batch.close()
     del Us
     torch.cuda.empty_cache()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
     # the plain FP64 method, request by request, on a seeded sample of the same draws
-    sample = ws[:max(1, min(8, len(ws)))]
+    sample = all_ws[:max(1, min(8, len(all_ws)))]
     t0 = time.perf_counter()
     for w in sample:
         ctx = wrmg.Context(w)
@@ -475,6 +488,8 @@ def run_batch_form(args):
                               "ndofs_sample": sum(w.ndofs() for w in sample)}
     out["solves_per_s_ratio_batched_vs_sequential_fp64"] = out["batched_solve"]["solves_per_s"] / (len(sample) / seq)
     print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
 
 def run_serve_form(args):
