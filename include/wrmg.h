@@ -57,6 +57,7 @@ extern "C" {
 #define WR_ERR_TIMEOUT 5        /* a bounded device wait gave up                                */
 #define WR_ERR_NAN 6            /* a norm became NaN or Inf                                     */
 #define WR_ERR_STATE 7          /* call order violated (e.g. smoother before wr_linearise)      */
+#define WR_ERR_CANCELLED 8      /* a served request was cancelled (wr_server_cancel)            */
 
 /* problem data (wr_problem.kind) */
 #define WR_TAYLOR_GREEN 0  /* decaying Taylor-Green (Chorin) vortex, f = 0, exact Dirichlet data (conv = 1)  */
@@ -302,6 +303,21 @@ int wr_server_submit(wr_server *sv, const wr_problem *p, const double *U0_host, 
 int wr_server_poll(wr_server *sv, uint64_t ticket, int wait, double *U_host, wr_stats *st, double *latency_ms);
 /* Largest device bytes admitted at once and largest number of solves in flight so far. */
 int wr_server_stats(wr_server *sv, int64_t *peak_bytes, int *peak_inflight);
+/* Cancels a request: a queued one completes at once, a running one at its next
+ * Newton step or FGMRES iteration; either way with WR_ERR_CANCELLED (poll it as
+ * usual).  A completed request is unaffected.  Unknown tickets: WR_ERR_ARG. */
+int wr_server_cancel(wr_server *sv, uint64_t ticket);
+
+/* ------------------------------------------------------------------ failure detection
+ * Host-side fault injection and a self-test of the device-side bounded waits; the
+ * GPU is never faulted, trapped or hung.  Neither has a counterpart in the paper. */
+/* The nth device allocation made by a context or batch from now on fails with
+ * WR_ERR_NOMEM, as if the device were full (0 switches the injection off). */
+int wr_inject_alloc_failure(int64_t nth);
+/* Runs the smoother kernels' bounded wait on an mbarrier that nothing completes,
+ * in a one-warp kernel on cuda_stream: *timed_out = 1 when the wait gave up (as it
+ * must), *waited_ms = how long it waited (about the 2 s limit). */
+int wr_selftest_bounded_wait(void *cuda_stream, int *timed_out, double *waited_ms);
 
 /* Total kernel launches made by this library in this process (all contexts). */
 int wr_launch_count(int64_t *out);

@@ -81,6 +81,8 @@ struct wr_batch {
   Tp* alloc(size_t count) {
     void* p = nullptr;
     const size_t nb = std::max<size_t>(count * sizeof(Tp), 16);
+    if (g_fail_alloc.load() > 0 && g_fail_alloc.fetch_sub(1) == 1)
+      throw WrError(WR_ERR_NOMEM, "injected allocation failure (wr_inject_alloc_failure)");
     cudaError_t e = cudaMalloc(&p, nb);
     if (e != cudaSuccess) {
       cudaGetLastError();

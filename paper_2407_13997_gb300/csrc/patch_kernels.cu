@@ -517,7 +517,16 @@ struct ApplySmem {
   CT my[pd::NVG][pd::NVG];
 };
 
-constexpr int kSpinLimit = 1 << 22;
+// Every wait of the apply kernels is bounded in time: after kWaitLimitNs of the
+// global nanosecond timer (checked every 256 polls) the wait gives up, the
+// kernel raises the error flag, drains its own copies in flight and returns.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -545,9 +554,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < kSpinLimit; ++it)
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-  return false;
+    if ((it & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+  }
 }
 template <int NCONS>
 __device__ __forceinline__ void consumer_sync() {
@@ -1038,5 +1050,25 @@ void bt_block_apply(int k, int q, int precision, const BatchSeg* segs, int nseg,
   else if (k == 1 && q == 1) bt_scatter_kernel<1, 1><<<blocks, 256, 0, s>>>(segs, nseg, dofs, yp, out);
   else if (k == 2 && q == 0) bt_scatter_kernel<2, 0><<<blocks, 256, 0, s>>>(segs, nseg, dofs, yp, out);
   else bt_scatter_kernel<2, 1><<<blocks, 256, 0, s>>>(segs, nseg, dofs, yp, out);
+  WR_LAUNCH_CHECK();
+}
+
+
+// ---------------------------------------------------------------- self-test of the bounded wait
+// One thread initialises an mbarrier that nothing ever completes and waits on it
+// with the apply kernels' bounded wait; it must give up and report it.
+__global__ void bounded_wait_selftest_kernel(int* timed_out, unsigned long long* ns) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(smem_u32(&bar), 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  const unsigned long long t0 = global_ns();
+  const bool ok = mbar_wait_bounded(smem_u32(&bar), 0);
+  *ns = global_ns() - t0;
+  *timed_out = ok ? 0 : 1;
+}
+
+void launch_bounded_wait_selftest(int* timed_out, unsigned long long* ns, cudaStream_t s) {
+  bounded_wait_selftest_kernel<<<1, 32, 0, s>>>(timed_out, ns);
   WR_LAUNCH_CHECK();
 }

@@ -13,6 +13,7 @@
 // what else is in flight.
 #include <chrono>
 #include <condition_variable>
+#include <atomic>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -39,6 +40,7 @@ struct Request {
   wr_stats st;
   int status = WR_ERR_STATE;  // WR_ERR_STATE while queued or running
   bool done = false;
+  std::atomic<int> cancel{0};
   int64_t bytes = 0, ndofs = 0;
   double t_submit = 0, t_start = 0, t_end = 0;
 };
@@ -67,7 +69,9 @@ struct wr_server {
     int rc = WR_OK;
     std::memset(&r->st, 0, sizeof(r->st));
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) rc = WR_ERR_CUDA;
+    if (rc == WR_OK && r->cancel.load()) rc = WR_ERR_CANCELLED;
     if (rc == WR_OK) rc = create_context(&c, &r->p, &opt, s, true);
+    if (c) set_cancel_flag(c, &r->cancel);
     if (rc == WR_OK && cudaMallocAsync(&dU, sizeof(double) * r->ndofs, s) != cudaSuccess) rc = WR_ERR_NOMEM;
     if (rc == WR_OK) {
       if (!r->U0.empty()) {
@@ -218,6 +222,26 @@ int wr_server_poll(wr_server* sv, uint64_t ticket, int wait, double* U_host, wr_
   if (latency_ms) *latency_ms = r->t_end - r->t_submit;
   sv->reqs.erase(it);
   return r->status;
+}
+
+int wr_server_cancel(wr_server* sv, uint64_t ticket) {
+  if (!sv) return WR_ERR_ARG;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return WR_ERR_ARG;
+  auto r = it->second;
+  if (r->done) return WR_OK;
+  r->cancel.store(1);
+  for (auto q = sv->queue.begin(); q != sv->queue.end(); ++q)
+    if (*q == r) {  // still queued: complete it now
+      sv->queue.erase(q);
+      r->status = WR_ERR_CANCELLED;
+      r->t_end = now_ms();
+      r->done = true;
+      sv->cv.notify_all();
+      break;
+    }
+  return WR_OK;
 }
 
 // Peak device bytes admitted at once and peak number of solves in flight so far.

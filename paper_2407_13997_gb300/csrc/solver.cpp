@@ -21,6 +21,9 @@ std::atomic<int64_t> g_launches{0};
 }  // namespace
 void wr_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// host-side fault injection: the n-th device allocation from now on fails (0 = off)
+std::atomic<int64_t> g_fail_alloc{0};
+
 namespace {
 
 struct Level {
@@ -88,6 +91,11 @@ struct wr_ctx {
   // allocate from the stream-ordered pool on s (no device-wide synchronisation
   // in cudaMalloc/cudaFree while other streams run; used by the server)
   bool stream_ordered = false;
+  const std::atomic<int>* cancel = nullptr;  // set by the server: stop the solve at the next check
+
+  void check_cancel() const {
+    if (cancel && cancel->load()) throw WrError(WR_ERR_CANCELLED, "the request was cancelled");
+  }
 
   template <typename Tp>
   Tp* alloc(size_t count) {
@@ -97,6 +105,8 @@ struct wr_ctx {
       bytes += nb;
       return reinterpret_cast<Tp*>(uintptr_t(256));
     }
+    if (g_fail_alloc.load() > 0 && g_fail_alloc.fetch_sub(1) == 1)
+      throw WrError(WR_ERR_NOMEM, "injected allocation failure (wr_inject_alloc_failure)");
     cudaError_t e = stream_ordered ? cudaMallocAsync(&p, nb, s) : cudaMalloc(&p, nb);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -384,6 +394,7 @@ struct wr_ctx {
       gg[0] = beta;
       int jend = 0;
       for (int j = 0; j < m; ++j) {
+        check_cancel();
         vcycle(V[j], Z[j]);
         launch_project_pressure(fl.g, tab, Z[j], s);
         jac(top(), Z[j], V[j + 1]);
@@ -438,6 +449,7 @@ struct wr_ctx {
     int status = WR_ERR_NOT_CONVERGED;
     const int v0 = vcycles;
     for (int it = 0; it < opt.newton_maxit && it < 64; ++it) {
+      check_cancel();
       if (!std::isfinite(fnorm)) {
         status = WR_ERR_NAN;
         break;
@@ -1018,3 +1030,38 @@ int create_context(wr_ctx** out, const wr_problem* p, const wr_options* o, void*
   *out = c.release();
   return rc;
 }
+
+void set_cancel_flag(wr_ctx* c, const std::atomic<int>* flag) { c->cancel = flag; }
+
+extern "C" {
+
+int wr_inject_alloc_failure(int64_t nth) {
+  if (nth < 0) return WR_ERR_ARG;
+  g_fail_alloc.store(nth);
+  return WR_OK;
+}
+
+int wr_selftest_bounded_wait(void* stream, int* timed_out, double* waited_ms) {
+  if (!timed_out || !waited_ms) return WR_ERR_ARG;
+  try {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void* d = nullptr;
+    WR_CUDA(cudaMalloc(&d, 16));
+    std::unique_ptr<void, void (*)(void*)> hold(d, [](void* q) { cudaFree(q); });
+    int* flag = static_cast<int*>(d);
+    unsigned long long* ns = reinterpret_cast<unsigned long long*>(static_cast<char*>(d) + 8);
+    launch_bounded_wait_selftest(flag, ns, s);
+    int h = 0;
+    unsigned long long hn = 0;
+    WR_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    WR_CUDA(cudaMemcpyAsync(&hn, ns, sizeof(hn), cudaMemcpyDeviceToHost, s));
+    WR_CUDA(cudaStreamSynchronize(s));
+    *timed_out = h;
+    *waited_ms = hn * 1e-6;
+    return WR_OK;
+  } catch (const WrError& e) {
+    return e.code;
+  }
+}
+
+}  // extern "C"

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <stdexcept>
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -253,3 +254,13 @@ void bt_dot(const BatchSeg* segs, int nseg, const double* x, const double* y, do
 // creating and destroying a context never synchronises the whole device while
 // other streams run.
 int create_context(wr_ctx** out, const wr_problem* p, const wr_options* o, void* stream, bool stream_ordered);
+
+// The apply kernels' bounded wait on an mbarrier that never completes: *timed_out = 1
+// and *ns = the time waited (device pointers).
+void launch_bounded_wait_selftest(int* timed_out, unsigned long long* ns, cudaStream_t s);
+
+// The server's per-request cancel flag: the context's solve stops with
+// WR_ERR_CANCELLED at its next Newton step or FGMRES iteration once it is set.
+void set_cancel_flag(wr_ctx* c, const std::atomic<int>* flag);
+// Host-side fault injection counter (wr_inject_alloc_failure).
+extern std::atomic<int64_t> g_fail_alloc;

@@ -14,13 +14,14 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libwrmg.so")
 
 WR_OK = 0
-WR_ERR_ARG, WR_ERR_NOMEM, WR_ERR_CUDA, WR_ERR_NOT_CONVERGED, WR_ERR_TIMEOUT, WR_ERR_NAN, WR_ERR_STATE = range(1, 8)
+WR_ERR_ARG, WR_ERR_NOMEM, WR_ERR_CUDA, WR_ERR_NOT_CONVERGED, WR_ERR_TIMEOUT, WR_ERR_NAN, WR_ERR_STATE, \
+    WR_ERR_CANCELLED = range(1, 9)
 WR_FP64, WR_FP32, WR_BF16 = 0, 1, 2
 WR_PATCH_SUBMATRIX, WR_PATCH_LOCAL = 0, 1
 WR_WEIGHT_ONE, WR_WEIGHT_MULTIPLICITY = 0, 1
 WR_RECOMPUTE, WR_STORE, WR_STORE_AUTO = 0, 1, 2
 _STATUS = {1: "WR_ERR_ARG", 2: "WR_ERR_NOMEM", 3: "WR_ERR_CUDA", 4: "WR_ERR_NOT_CONVERGED",
-           5: "WR_ERR_TIMEOUT", 6: "WR_ERR_NAN", 7: "WR_ERR_STATE"}
+           5: "WR_ERR_TIMEOUT", 6: "WR_ERR_NAN", 7: "WR_ERR_STATE", 8: "WR_ERR_CANCELLED"}
 
 
 class WrmgError(RuntimeError):
@@ -117,6 +118,9 @@ _SIGS = {
     "wr_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int, _P, ctypes.POINTER(Stats),
                                       ctypes.POINTER(ctypes.c_double)]),
     "wr_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]),
+    "wr_server_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "wr_inject_alloc_failure": (ctypes.c_int, [ctypes.c_int64]),
+    "wr_selftest_bounded_wait": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "wr_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "wr_profile_smoother": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int)]),
@@ -169,6 +173,20 @@ def measure_fp64_tflops(stream=None):
     if rc != WR_OK:
         raise WrmgError(rc, "FP64 probe failed")
     return out.value
+
+
+def inject_alloc_failure(nth):
+    """Host-side fault injection: the nth device allocation from now on fails (0 = off)."""
+    load().wr_inject_alloc_failure(int(nth))
+
+
+def selftest_bounded_wait(stream=None):
+    """(timed_out, waited_ms) of the smoother kernels' bounded wait on a barrier nothing completes."""
+    t, ms = ctypes.c_int(), ctypes.c_double()
+    rc = load().wr_selftest_bounded_wait(ctypes.c_void_p(stream or 0), ctypes.byref(t), ctypes.byref(ms))
+    if rc != WR_OK:
+        raise WrmgError(rc, "bounded-wait self-test failed to run")
+    return bool(t.value), ms.value
 
 
 def launch_count():
@@ -514,6 +532,11 @@ class Server:
             return None
         del self._ndofs[ticket]
         return rc, U, st.as_dict(), lat.value
+
+    def cancel(self, ticket):
+        rc = self._lib.wr_server_cancel(self._h, ctypes.c_uint64(ticket))
+        if rc != WR_OK:
+            raise WrmgError(rc, "wr_server_cancel failed")
 
     def stats(self):
         b, n = ctypes.c_int64(), ctypes.c_int()
