@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=96.0, help="serve form: device-memory budget")
     ap.add_argument("--full-mix", action="store_true",
                     help="serve form: draw n and N from {16, 32, 64} (default {16, 32})")
-    ap.add_argument("--form", default="cycle", choices=["cycle", "precision", "batch", "serve", "smoother", "timestepping"],
+    ap.add_argument("--form", default="cycle", choices=["cycle", "precision", "batch", "serve", "smoother", "timestepping", "lid"],
                     help="cycle: the V(2,2) throughput line (default); precision: the FP64/FP32/BF16 "
                          "solves of the 128x128 Q2/Q1 DG(0) 128-slab workload")
     return ap.parse_args()
@@ -687,6 +687,37 @@ def run_timestepping_form(args):
     print(json.dumps(out), flush=True)
 
 
+def run_lid_form(args):
+    """Lid-driven cavity (Sec. 4, Table lid): Q2/Q1 DG(0), t in [0, 0.02], N = 20,
+    R = 1, 10, 100, on 16x16 and 32x32 meshes; whole WRMG solve times (context
+    set-up excluded) and Newton (FGMRES) counts."""
+    import torch
+    from paper_2407_13997_gb300 import inputs, wrmg
+    torch.cuda.set_device(0)
+    out = {"form": "lid", "runs": []}
+    warm = inputs.lid_cavity(8, 1, 0, 4, 10.0)
+    ctx = wrmg.Context(warm)
+    U = ctx.vector()
+    ctx.initial_guess(U)
+    ctx.solve(U, check=False)
+    ctx.close()
+    for n in (16, 32):
+        for R in (1.0, 10.0, 100.0):
+            w = inputs.lid_cavity(n, 1, 0, 20, R)
+            ctx = wrmg.Context(w)
+            U = ctx.vector()
+            ctx.initial_guess(U)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = ctx.solve(U, check=False)
+            torch.cuda.synchronize()
+            out["runs"].append({"n": n, "R": R, "ndofs": w.ndofs(), "status": st["status"],
+                                "seconds": time.perf_counter() - t0, "newton": st["newton_its"],
+                                "fgmres_total": sum(st["gmres"])})
+            ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -701,6 +732,8 @@ def main():
         run_smoother_form(args)
     elif args.form == "timestepping":
         run_timestepping_form(args)
+    elif args.form == "lid":
+        run_lid_form(args)
     else:
         run_ours(args)
 

@@ -63,6 +63,8 @@ extern "C" {
 #define WR_TAYLOR_GREEN 0  /* decaying Taylor-Green (Chorin) vortex, f = 0, exact Dirichlet data (conv = 1)  */
 #define WR_POLY 1          /* manufactured u = (y^2, x^2)(1+t) (or steady), p = x+y-1, with matching f       */
 #define WR_FOURIER 2       /* no-slip walls, u(0) = 0, f = sum amp_j curl(sin(mx_j pi x) sin(my_j pi y))     */
+#define WR_LID 3           /* lid-driven cavity (Sec. 4): u = (1, 0) on the open top edge, 0 on the other walls
+                              and the top corners, u(0) = 0, f = 0                                         */
 
 /* arithmetic of the stored patch factors and of the smoother (wr_options.precision) */
 #define WR_FP64 0  /* FP64 factors and smoother (the plain method)                        */
@@ -99,7 +101,7 @@ typedef struct {
     int q;          /* DG(q) in time; q = 0 or 1                                             */
     int n_slabs;    /* N time slabs of width T / N                                           */
     double T, nu, conv;
-    int kind;       /* WR_TAYLOR_GREEN, WR_POLY or WR_FOURIER                                */
+    int kind;       /* WR_TAYLOR_GREEN, WR_POLY, WR_FOURIER or WR_LID                        */
     int steady;     /* WR_POLY only: time-constant u = (y^2, x^2)                            */
     int n_modes;    /* WR_FOURIER: number of modes (<= 8), host arrays below                 */
     const int *mx, *my;

@@ -50,7 +50,10 @@ class Problem:
               the discrete space for k >= 1, so the discrete solution is exact;
           'fourier' -- no-slip walls, u(0) = 0, time-independent divergence-free
               forcing f = sum_j amp_j (d_y psi_j, -d_x psi_j),
-              psi_j = sin(mx_j pi x) sin(my_j pi y).
+              psi_j = sin(mx_j pi x) sin(my_j pi y);
+          'lid' -- lid-driven cavity (Sec. 4): u = (1, 0) on the open top edge
+              y = 1, 0 < x < 1, zero on the other walls and at the two top
+              corners, u(0) = 0, f = 0 (no exact solution).
     """
 
     kind: str = "taylor_green"
@@ -72,6 +75,13 @@ class Problem:
             s = 1.0 if self.steady else 1.0 + t
             return y * y * s, x * x * s
         return 0.0 * x, 0.0 * y
+
+    def boundary_velocity(self, x, y, t):
+        """The Dirichlet data on the boundary nodes (x, y at the nodes)."""
+        if self.kind == "lid":
+            lid = (y == 1.0) & (x > 0.0) & (x < 1.0)
+            return np.where(lid, 1.0, 0.0) + 0.0 * x, 0.0 * x
+        return self.exact_velocity(x, y, t)
 
     def exact_pressure(self, x, y, t):
         """Strong-form pressure p (the discrete Phi approximates -p)."""
@@ -271,7 +281,7 @@ class Discretisation:
         nv2 = self.nv ** 2
         for n in range(self.N):
             for a, t in enumerate(self.time_nodes(n)):
-                ux, uy = self.pb.exact_velocity(X, Y, t)
+                ux, uy = self.pb.boundary_velocity(X, Y, t)
                 blk = np.zeros(self.S)
                 blk[:nv2] = np.broadcast_to(ux, X.shape).ravel()
                 blk[nv2:2 * nv2] = np.broadcast_to(uy, X.shape).ravel()

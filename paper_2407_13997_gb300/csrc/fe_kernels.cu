@@ -50,6 +50,19 @@ __device__ __forceinline__ void exact_velocity(const PhysParams& ph, double x, d
   }
 }
 
+// Dirichlet data at velocity node (gx, gy) of a level with nv nodes per direction:
+// the exact solution, except for the lid-driven cavity (u = (1, 0) on the open top
+// edge, zero on the other walls and at the top corners).
+__device__ __forceinline__ void dirichlet_velocity(const PhysParams& ph, int gx, int gy, int nv, double hn, double t,
+                                                   double& ux, double& uy) {
+  if (ph.kind == WR_LID) {
+    ux = (gy == nv - 1 && gx > 0 && gx < nv - 1) ? 1.0 : 0.0;
+    uy = 0.0;
+  } else {
+    exact_velocity(ph, gx * hn, gy * hn, t, ux, uy);
+  }
+}
+
 __device__ __forceinline__ void forcing(const PhysParams& ph, double x, double y, double t, double& fx,
                                         double& fy) {
   if (ph.kind == WR_POLY) {
@@ -344,7 +357,7 @@ __device__ __forceinline__ void assemble_body(const LevelGeom& g, const FeTables
         y[idx] = x[idx];
       } else {
         double ux, uy;
-        exact_velocity(ph, gx * (g.h / (K + 1)), gy * (g.h / (K + 1)), ph.t0 + (slab + T.tnode[a]) * g.dt, ux, uy);
+        dirichlet_velocity(ph, gx, gy, nv, g.h / (K + 1), ph.t0 + (slab + T.tnode[a]) * g.dt, ux, uy);
         y[idx] = x[idx] - (c == 0 ? ux : uy);
       }
       return;
@@ -404,8 +417,7 @@ __device__ __forceinline__ void boundary_body(const LevelGeom& g, const FeTables
     const int gx = t % nv, gy = t / nv;
     if (vel_dirichlet(g, gx, gy)) {
       double ux, uy;
-      exact_velocity(ph, gx * (g.h / (g.k + 1)), gy * (g.h / (g.k + 1)), ph.t0 + (slab + T.tnode[a]) * g.dt, ux,
-                     uy);
+      dirichlet_velocity(ph, gx, gy, nv, g.h / (g.k + 1), ph.t0 + (slab + T.tnode[a]) * g.dt, ux, uy);
       v = c == 0 ? ux : uy;
     }
   }

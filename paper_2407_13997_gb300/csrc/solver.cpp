@@ -576,7 +576,7 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
     int nf = p->n_fine;
     while (nf > p->n_coarse && nf % 2 == 0) nf /= 2;
     need(nf == p->n_coarse, "n_fine must be n_coarse times a power of two");
-    need(p->kind >= WR_TAYLOR_GREEN && p->kind <= WR_FOURIER, "unknown problem kind");
+    need(p->kind >= WR_TAYLOR_GREEN && p->kind <= WR_LID, "unknown problem kind");
     need(p->n_modes >= 0 && p->n_modes <= 8, "at most 8 Fourier modes");
     need(p->n_modes == 0 || (p->mx && p->my && p->amp), "Fourier mode arrays missing");
     if (o) c->opt = *o;

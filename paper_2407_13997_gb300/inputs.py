@@ -16,7 +16,8 @@ import numpy as np
 KIND_TAYLOR_GREEN = 0
 KIND_POLY = 1
 KIND_FOURIER = 2
-KIND_NAMES = {KIND_TAYLOR_GREEN: "taylor_green", KIND_POLY: "poly", KIND_FOURIER: "fourier"}
+KIND_LID = 3
+KIND_NAMES = {KIND_TAYLOR_GREEN: "taylor_green", KIND_POLY: "poly", KIND_FOURIER: "fourier", KIND_LID: "lid"}
 
 FOURIER_MODES = ((1, 1), (1, 2), (2, 1), (2, 2), (1, 3), (3, 1), (2, 3), (3, 2))
 
@@ -69,6 +70,12 @@ def chorin(n=16, k=1, q=0, N=10, R=10.0):
     nu = 1, convection R, t in [0, 0.1], exact velocity data on the whole boundary,
     n x n mesh coarsened to 2 x 2, N slabs."""
     return Workload(f"chorin_R{R:g}_q{k + 1}q{k}_dg{q}_n{n}_N{N}", n, 2, k, q, N, 0.1, 1.0, R, KIND_TAYLOR_GREEN)
+
+
+def lid_cavity(n=16, k=1, q=0, N=20, R=10.0, T=0.02):
+    """The lid-driven cavity of Sec. 4 in Reynolds-number form (nu = 1, convection
+    R), started from rest, t in [0, T], n x n mesh coarsened to 2 x 2, N slabs."""
+    return Workload(f"lid_R{R:g}_q{k + 1}q{k}_dg{q}_n{n}_N{N}", n, 2, k, q, N, T, 1.0, R, KIND_LID)
 
 
 def fourier_64x64_q3q2_dg1(seed=0):

@@ -158,3 +158,47 @@ def test_discrete_solution_is_discretely_divergence_free():
     F = d.residual(U)
     for blk in range(d.N * d.nt):
         assert np.abs(F[blk * d.S + d.off_p:(blk + 1) * d.S]).max() < 1e-12
+
+
+def _centre_stream_function(d, blk):
+    """psi(1/2, y) = int_0^y u_x(1/2, s) ds of the Q2 velocity (exact per cell)."""
+    nv = d.nv
+    col = blk[:nv * nv].reshape(nv, nv)[:, (nv - 1) // 2]
+    H = 1.0 / d.n
+    ys, psi, acc = [0.0], [0.0], 0.0
+    for cell in range(d.n):
+        P = np.polyint(np.polyfit([0, H / 2, H], col[2 * cell:2 * cell + 3], 2))
+        for s in np.linspace(0, H, 41)[1:]:
+            ys.append(cell * H + s)
+            psi.append(acc + np.polyval(P, s))
+        acc += np.polyval(P, H)
+    return np.array(ys), np.array(psi)
+
+
+def test_lid_driven_cavity_data_and_steady_stokes_limit():
+    """Lid data: u_x = 1 only on the open top edge.  Stokes (conv = 0) run long
+    enough to be steady: the velocity is mirror-symmetric about x = 1/2 and the
+    centre-line stream function has the classical Stokes-cavity minimum
+    psi = -0.100076 at y = 0.7643 (the textbook value for the square cavity)."""
+    pb = Problem(kind="lid", nu=1.0, conv=0.0, T=4.0)
+    d = Discretisation(16, 1, 0, 4, pb)
+    g = d.boundary_values()
+    nv, nv2 = d.nv, d.nv ** 2
+    blk0 = g[:d.S]
+    top = np.zeros((nv, nv))
+    top[nv - 1, 1:nv - 1] = 1.0
+    assert np.array_equal(blk0[:nv2].reshape(nv, nv), top) and not blk0[nv2:].any()
+    assert not d.initial_velocity().any()
+    U = direct_solve(d, tol=1e-13)
+    blk = U[d.block(d.N - 1, 0):d.block(d.N - 1, 0) + d.S]
+    ux = blk[:nv2].reshape(nv, nv)
+    uy = blk[nv2:2 * nv2].reshape(nv, nv)
+    assert np.abs(ux - ux[:, ::-1]).max() < 1e-10 and np.abs(uy + uy[:, ::-1]).max() < 1e-10
+    ys, psi = _centre_stream_function(d, blk)
+    i = int(np.argmin(psi))
+    assert abs(psi[i] + 0.100076) < 2e-4 and abs(ys[i] - 0.7643) < 0.01
+    # convection breaks the mirror symmetry
+    d2 = Discretisation(8, 1, 0, 2, Problem(kind="lid", nu=1.0, conv=100.0, T=0.5))
+    U2 = direct_solve(d2, tol=1e-12)
+    u2 = U2[d2.block(1, 0):d2.block(1, 0) + d2.nv ** 2].reshape(d2.nv, d2.nv)
+    assert np.abs(u2 - u2[:, ::-1]).max() > 1e-4
