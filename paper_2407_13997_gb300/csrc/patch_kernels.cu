@@ -680,8 +680,9 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
       const int a = e / MS, s = e % MS, sp = sm.sidx[s];
       sm.rhs[a][s] = sp >= 0 ? (CT)r[(int64_t)a * g.S + sp] : (CT)0;
     }
+    const bool carry = v.prev != nullptr && bs.kind == 0;  // jump state from before the window
     for (int slab = 0; slab < g.N && !aborted; ++slab) {
-      if (slab > 0) {
+      if (slab > 0 || carry) {
         // jump coupling: rhs_a += tau_a(0) M_u y_{n-1, last} (tensor-product mass on the slot grid)
         consumer_sync<NCONS>();
         for (int e = tid; e < 2 * nv2g; e += NCONS) {
