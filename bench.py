@@ -164,15 +164,16 @@ def smoother_algorithmic(ctx, w, factor_bytes=8):
     return factor_bytes * ent + 16.0 * vec, 2.0 * ent
 
 
-def traffic_record(kernel):
-    """DRAM bytes per launch from a committed ncu summary, valid only while the kernel source is unchanged."""
+def traffic_record(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from a committed ncu summary,
+    valid only while the kernel source is unchanged (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_2407_13997_gb300", "csrc", "patch_kernels.cu")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    rec = d.get(kernel)
+    rec = d.get(f"{kernel}/{workload}")
     if not rec:
         return None
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
@@ -308,14 +309,14 @@ def run_ours(args):
     achieved_gbs = alg_bytes / avg_s / 1e9
     if prec == wrmg.WR_FP64:
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_tflops, "unit": "TFLOP/s",
-                "frac": achieved_tf / fp64_tflops, "traffic": traffic_record("block_apply_kernel"),
+                "frac": achieved_tf / fp64_tflops, "traffic": traffic_record("block_apply_kernel", w.name),
                 "kernel": "block_apply_kernel (finest level)", "launches": sm_n, "avg_ms": avg_s * 1e3,
                 "peak_source": "FP64 FMA rate measured live by wr_measure_fp64_tflops",
                 "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                         "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src}}
     else:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved_gbs / hbm_peak, "traffic": traffic_record(f"block_apply_kernel_{args.precision}"),
+                "frac": achieved_gbs / hbm_peak, "traffic": traffic_record(f"block_apply_kernel_{args.precision}", w.name),
                 "kernel": f"block_apply_kernel (finest level, {args.precision} factors)", "launches": sm_n,
                 "avg_ms": avg_s * 1e3, "peak_source": hbm_src}
 
