@@ -282,7 +282,9 @@ int wr_batch_solve(wr_batch *b, double *const *U, wr_stats *st);
  * solution vector) fit in what remains of mem_budget_bytes.  Each admitted
  * request runs on its own host thread, CUDA stream and context (allocated on
  * admission, freed on completion), so the solves in flight overlap on the GPU
- * and a completion admits the next request at once.  A request larger than
+ * and a completion admits the next request at once.  Smaller requests run on
+ * higher-priority streams (one level per factor 4 in DoFs), so the GPU starts their
+ * kernels first when SMs free up.  A request larger than
  * the whole budget completes with WR_ERR_NOMEM.  Results are the same as a
  * wr_solve of that problem alone (deterministic kernels, per-stream state).
  * The paper solves one problem at a time; serving is a service of this library.

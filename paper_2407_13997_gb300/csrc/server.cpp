@@ -61,6 +61,18 @@ struct wr_server {
   bool stopping = false;
   std::string err;
 
+  // Smaller solves get higher stream priority (the block scheduler then starts their
+  // CTAs first whenever SMs free up), so short requests are not stuck behind the
+  // persistent kernels of long ones: one priority level per factor 4 in DoFs above
+  // 16 Ki DoFs, clamped to the device's range.
+  int prio_least = 0, prio_greatest = 0;
+  int priority_of(int64_t ndofs) const {
+    int lvl = 0;
+    for (int64_t d = ndofs >> 14; d > 1 && lvl < 32; d >>= 2) ++lvl;
+    const int p = prio_greatest + lvl;  // greatest priority is numerically smallest
+    return p < prio_least ? p : prio_least;
+  }
+
   void run_one(std::shared_ptr<Request> r) {
     cudaSetDevice(device);
     cudaStream_t s = nullptr;
@@ -68,7 +80,8 @@ struct wr_server {
     double* dU = nullptr;
     int rc = WR_OK;
     std::memset(&r->st, 0, sizeof(r->st));
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) rc = WR_ERR_CUDA;
+    if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, priority_of(r->ndofs)) != cudaSuccess)
+      rc = WR_ERR_CUDA;
     if (rc == WR_OK && r->cancel.load()) rc = WR_ERR_CANCELLED;
     if (rc == WR_OK) rc = create_context(&c, &r->p, &opt, s, true);
     if (c) set_cancel_flag(c, &r->cancel);
@@ -148,6 +161,7 @@ int wr_server_create(wr_server** out, int64_t mem_budget_bytes, int max_inflight
   sv->budget = mem_budget_bytes;
   sv->max_inflight = max_inflight;
   if (cudaGetDevice(&sv->device) != cudaSuccess) return WR_ERR_CUDA;
+  if (cudaDeviceGetStreamPriorityRange(&sv->prio_least, &sv->prio_greatest) != cudaSuccess) return WR_ERR_CUDA;
   // keep freed blocks in this process's default pool up to the budget, so that
   // admissions after completions reuse them instead of mapping memory afresh
   cudaMemPool_t pool;
