@@ -271,6 +271,11 @@ int wr_batch_vcycle(wr_batch *b, double *const *bin, double *const *xout);
 /* One V(2,2) cycle of every member on the batch's internal right-hand side
  * (the last b given to wr_batch_vcycle); for throughput measurements. */
 int wr_batch_vcycle_resident(wr_batch *b);
+/* enable != 0 (the default): every batched V-cycle runs as one CUDA graph, captured
+ * anew whenever the active members or the Chebyshev intervals change (the cycle's
+ * kernels and arguments are the eager ones, so results are bitwise the same);
+ * 0: every kernel is launched eagerly. */
+int wr_batch_set_graphs(wr_batch *b, int enable);
 /* Newton-FGMRES-WRMG solve of every member from U[m] (in/out); st may be NULL
  * or an array of n wr_stats.  WR_ERR_NOT_CONVERGED if any member hits newton_maxit. */
 int wr_batch_solve(wr_batch *b, double *const *U, wr_stats *st);

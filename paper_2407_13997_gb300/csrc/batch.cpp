@@ -94,6 +94,7 @@ struct wr_batch {
     return static_cast<Tp*>(p);
   }
   ~wr_batch() {
+    drop_graph();
     for (void* p : allocs) cudaFree(p);
     if (hres) cudaFreeHost(hres);
     if (hcoef) cudaFreeHost(hcoef);
@@ -166,6 +167,7 @@ struct wr_batch {
   }
 
   void build_tables() {
+    ++table_ver;
     smooth.resize(D);
     for (int d = 0; d < D; ++d) {
       reset(smooth[d]);
@@ -189,6 +191,7 @@ struct wr_batch {
 
   // per-segment Chebyshev coefficients of every smoothing table (rows: 1/theta, then (c1, c2) per step)
   void upload_chebyshev() {
+    ++table_ver;  // the graph reads the coefficient arrays; re-capture after a change
     const int steps = opt.cheb_steps;
     for (int d = 0; d < D; ++d) {
       Table& t = smooth[d];
@@ -275,6 +278,56 @@ struct wr_batch {
                      t == &coarse3 ? 3 : 2, s);
       bt_project_pressure(t->d, t->n, t->tblks, tab, nullptr, true, s);
     }
+  }
+
+  // The V-cycle of the current tables as one CUDA graph: it reads vb and writes vx
+  // (depth-0 arenas), is captured after the tables or the Chebyshev coefficients
+  // change (an eager cycle runs first, so every kernel's one-time set-up is done),
+  // and replays as one launch.
+  cudaGraphExec_t gexec = nullptr;
+  int64_t table_ver = 0, graph_ver = -1, graph_kernels = 0;
+  bool use_graphs = true;
+
+  void drop_graph() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+    graph_ver = -1;
+  }
+
+  void vcycle_graph() {
+    if (!use_graphs) {
+      vcycle(vb, vx);
+      return;
+    }
+    if (graph_ver != table_ver) {
+      drop_graph();
+      vcycle(vb, vx);  // eager: one-time kernel attributes, and this call's result
+      cudaGraph_t graph = nullptr;
+      int64_t before = 0;
+      wr_launch_count(&before);
+      WR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      vcycle(vb, vx);
+      const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+      int64_t after = 0;
+      wr_launch_count(&after);
+      wr_uncount_launches(after - before);  // captured, not launched
+      if (ce != cudaSuccess || !graph) throw WrError(WR_ERR_CUDA, "V-cycle graph capture failed");
+      const cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) throw WrError(WR_ERR_CUDA, "V-cycle graph instantiation failed");
+      graph_kernels = after - before;
+      graph_ver = table_ver;
+      return;
+    }
+    WR_CUDA(cudaGraphLaunch(gexec, s));
+    wr_count_launches(graph_kernels);
+  }
+
+  // one V(2,2) cycle of every active member through the graph: x0 = V-cycle(b0)
+  void vcycle_via_graph(const double* b0, double* x0) {
+    bt_copy(fine.d, fine.n, fine.dofs, b0, vb, s);
+    vcycle_graph();
+    bt_copy(fine.d, fine.n, fine.dofs, vx, x0, s);
   }
 
   // one V(2,2) cycle of every active member: b0, x0 are depth-0 arena vectors
@@ -403,7 +456,7 @@ struct wr_batch {
       for (; j < R; ++j) {
         Table& ta = fine;
         if (!ta.n) break;
-        vcycle(V[j], Z[j]);
+        vcycle_via_graph(V[j], Z[j]);
         bt_project_pressure(ta.d, ta.n, ta.tblks, tab, Z[j], false, s);
         jac(ta, Z[j], V[j + 1]);
         c.assign(ta.n, 0.0);
@@ -779,7 +832,7 @@ int wr_batch_vcycle(wr_batch* b, double* const* bin, double* const* xout) {
     for (int m = 0; m < b->B; ++m)
       WR_CUDA(cudaMemcpyAsync(b->vb + b->off[0][m], bin[m], sizeof(double) * b->mem[m].g[b->mem[m].L].ndofs,
                               cudaMemcpyDeviceToDevice, b->s));
-    b->vcycle(b->vb, b->vx);
+    b->vcycle_graph();
     for (int m = 0; m < b->B; ++m)
       WR_CUDA(cudaMemcpyAsync(xout[m], b->vx + b->off[0][m], sizeof(double) * b->mem[m].g[b->mem[m].L].ndofs,
                               cudaMemcpyDeviceToDevice, b->s));
@@ -792,7 +845,7 @@ int wr_batch_vcycle_resident(wr_batch* b) {
   return bguard(b, [&]() -> int {
     bneed(b != nullptr, "null argument");
     if (!b->linearised) throw WrError(WR_ERR_STATE, "wr_batch_linearise must be called first");
-    b->vcycle(b->vb, b->vx);
+    b->vcycle_graph();
     return WR_OK;
   });
 }
@@ -830,3 +883,10 @@ int wr_batch_solve(wr_batch* b, double* const* U, wr_stats* st) {
 }
 
 }  // extern "C"
+
+extern "C" int wr_batch_set_graphs(wr_batch* b, int enable) {
+  if (!b) return WR_ERR_ARG;
+  b->use_graphs = enable != 0;
+  b->drop_graph();
+  return WR_OK;
+}

@@ -20,6 +20,8 @@ namespace {
 std::atomic<int64_t> g_launches{0};
 }  // namespace
 void wr_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void wr_count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void wr_uncount_launches(int64_t n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 
 // host-side fault injection: the n-th device allocation from now on fails (0 = off)
 std::atomic<int64_t> g_fail_alloc{0};

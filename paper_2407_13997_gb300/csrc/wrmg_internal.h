@@ -37,6 +37,8 @@ struct WrError : std::runtime_error {
   } while (0)
 // Every kernel launch of the library is followed by WR_LAUNCH_CHECK, which also counts it.
 void wr_count_launch();
+void wr_count_launches(int64_t n);    // kernels of a replayed CUDA graph
+void wr_uncount_launches(int64_t n);  // kernels captured into a graph, not launched
 #define WR_LAUNCH_CHECK()        \
   do {                           \
     wr_count_launch();           \

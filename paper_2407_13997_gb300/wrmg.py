@@ -110,6 +110,7 @@ _SIGS = {
     "wr_batch_get_lambda": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "wr_batch_vcycle": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p)]),
     "wr_batch_vcycle_resident": (ctypes.c_int, [_P]),
+    "wr_batch_set_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
     "wr_batch_solve": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Stats)]),
     "wr_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int,
                                         ctypes.POINTER(Options)]),
@@ -465,6 +466,9 @@ class Batch:
 
     def vcycle(self, bs, xs):
         self._check(self._lib.wr_batch_vcycle(self._h, self._ptrs(bs), self._ptrs(xs)))
+
+    def set_graphs(self, enable):
+        self._check(self._lib.wr_batch_set_graphs(self._h, int(bool(enable))))
 
     def vcycle_resident(self):
         self._check(self._lib.wr_batch_vcycle_resident(self._h))

@@ -93,3 +93,36 @@ def test_batched_solve_matches_single_solves_and_is_the_same_alone_and_in_the_mi
     assert rel(Ua[0], Us[2]) < 1e-10
     alone.close()
     batch.close()
+
+
+def test_graph_replay_equals_eager_cycles_bitwise():
+    """The batched V-cycle captured as one CUDA graph (re-captured when the active
+    set changes) gives bitwise the eager cycle's result, and its kernels are counted
+    once per replay."""
+    ws = members_q2q1()
+    rng = np.random.default_rng(5)
+    Ws = [torch.from_numpy(inputs.forcing_shaped_iterate(w)).cuda() for w in ws]
+    bs = [torch.from_numpy(rng.standard_normal(w.ndofs())).cuda() for w in ws]
+    out = []
+    for graphs in (True, False):
+        batch = wrmg.Batch(ws)
+        batch.set_graphs(graphs)
+        batch.linearise(Ws)
+        xs = batch.vectors()
+        for _ in range(3):                       # capture, then replays
+            batch.vcycle(bs, xs)
+        torch.cuda.synchronize()
+        n0 = wrmg.launch_count()
+        batch.vcycle(bs, xs)
+        torch.cuda.synchronize()
+        per_cycle = wrmg.launch_count() - n0
+        Us = batch.vectors()
+        batch.initial_guess(Us)
+        st = batch.solve(Us, check=False)
+        out.append((xs, per_cycle, Us, [s["gmres"] for s in st]))
+        batch.close()
+    (xg, ng, Ug, gg), (xe, ne, Ue, ge) = out
+    assert all(torch.equal(a, b) for a, b in zip(xg, xe))
+    assert ng == ne > 10
+    assert gg == ge
+    assert all(torch.equal(a, b) for a, b in zip(Ug, Ue))
