@@ -329,6 +329,7 @@ def run_ours(args):
             "config": {"workload": w.name, "ndofs": D, "n": w.n_fine, "k": w.k, "q": w.q, "N": w.N,
                        "levels": ctx.num_levels, "factor_storage": args.precision,
                        "device_bytes": ctx.device_bytes(),
+                       "apply_tiles": [ctx.apply_tile(l) for l in range(1, ctx.num_levels)],
                        "l2": f"no flush: {ctx.device_bytes() / 1e9:.0f} GB on the device, the stored factors "
                              "streamed every cycle >> 129 MB L2",
                        "parallelism": f"replicas x{world}"},

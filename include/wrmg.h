@@ -126,6 +126,9 @@ typedef struct {
     int recompute_slabs;    /* slabs per recompute window (0: ceil(N / 16))                      */
     int memory_budget_mb;   /* WR_STORE_AUTO: device MiB the context may take (0: 92% of the
                                device's free memory at wr_create)                              */
+    int autotune;           /* 1 (default): at the first linearisation, time the smoother-apply
+                               tile variants on every level's stored factors and keep the
+                               fastest (cached per shape for the process); 0: fixed tiles     */
 } wr_options;
 
 typedef struct {
@@ -159,6 +162,9 @@ int wr_device_bytes(const wr_ctx *c, int64_t *out);
 /* Smoothed level (1 .. num_levels - 1): *stored = 1 if its factors are stored,
  * 0 if recomputed per apply; *window_slabs = the slabs per recompute window (N when stored). */
 int wr_factor_storage(const wr_ctx *c, int level, int *stored, int *window_slabs);
+/* The smoother-apply tile of a smoothed level chosen by the autotuner (0 .. 2), or -1
+ * before the first linearisation or with autotune = 0 (the fixed tile of k is used). */
+int wr_apply_tile(const wr_ctx *c, int level, int *variant);
 
 /* Global indices (host array, capacity >= 2 (2k+3)^2 (q+1) + (2k-1)^2 (q+1))
  * of Vanka+star patch `patch` (= J (n+1) + I for vertex (I, J)) on `slab` of

@@ -239,8 +239,8 @@ struct wr_batch {
   void jac(const Table& t, const double* x, double* y) {
     if (t.n) bt_jacobian(k, q, t.d, t.n, t.units, t.dofs, tab, x, y, ye, s);
   }
-  void papply(const Table& t, const double* r, double* y) {
-    if (t.n) bt_block_apply(k, q, opt.precision, t.d, t.n, t.items, t.dofs, tab, r, y, yp, derr, 0, s);
+  void papply(const Table& t, int d, const double* r, double* y) {
+    if (t.n) bt_block_apply(k, q, opt.precision, t.d, t.n, t.items, t.dofs, tab, r, y, yp, derr, 0, s, depth_variant[d]);
   }
   void residual_b_minus(const Table& t, const double* b, double* x, double* tmp, double* r) {
     jac(t, x, tmp);
@@ -258,13 +258,13 @@ struct wr_batch {
     } else {
       residual_b_minus(t, b, x, a.t, a.r);
     }
-    papply(t, a.r, a.d);
+    papply(t, d, a.r, a.d);
     bt_axpby(t.d, t.n, t.dofs, nullptr, 0.0, a.d, t.coef, 0.0, a.d, s);  // d = M^{-1} r / theta
     for (int st = 0; st < opt.cheb_steps; ++st) {
       bt_axpby(t.d, t.n, t.dofs, nullptr, 1.0, a.d, nullptr, 1.0, x, s);
       if (st == opt.cheb_steps - 1) break;
       residual_b_minus(t, b, x, a.t, a.r);
-      papply(t, a.r, a.z);
+      papply(t, d, a.r, a.z);
       const int row = 2 * (st + 1);
       bt_axpby(t.d, t.n, t.dofs, t.coef + (size_t)row * B, 0.0, a.z, t.coef + (size_t)(row - 1) * B, 0.0, a.d, s);
     }
@@ -284,6 +284,7 @@ struct wr_batch {
   // (depth-0 arenas), is captured after the tables or the Chebyshev coefficients
   // change (an eager cycle runs first, so every kernel's one-time set-up is done),
   // and replays as one launch.
+  std::vector<int> depth_variant = std::vector<int>(16, -1);  // tuned apply tile per depth
   cudaGraphExec_t gexec = nullptr;
   int64_t table_ver = 0, graph_ver = -1, graph_kernels = 0;
   bool use_graphs = true;
@@ -368,6 +369,16 @@ struct wr_batch {
       launch_block_factor(M.g[0], tab, M.ph, M.cbs, Ce, M.cf, WR_FP64, fstat, s);
     }
     build_tables();
+    if (opt.autotune)
+      for (int d = 0; d < D; ++d) {
+        Table& t = smooth[d];
+        if (!t.n || depth_variant[d] >= 0) continue;
+        bt_axpby(t.d, t.n, t.dofs, nullptr, 0.0, ar[d].x, nullptr, 0.0, ar[d].x, s);
+        const TuneKey key{1, k, q, opt.precision, t.items, 0};
+        depth_variant[d] = tune_apply_variant(key, s, [&](int v) {
+          bt_block_apply(k, q, opt.precision, t.d, t.n, t.items, t.dofs, tab, ar[d].x, ar[d].d, yp, derr, 0, s, v);
+        });
+      }
     for (int d = 0; d < D; ++d) eigen_depth(d);
     linearised = true;
     upload_chebyshev();
@@ -390,7 +401,7 @@ struct wr_batch {
     bt_axpby(t.d, t.n, t.dofs, nullptr, 0.0, V[0], coefs(c), 0.0, V[0], s);
     for (int j = 0; j < mdim; ++j) {
       jac(t, V[j], ar[d].t);
-      papply(t, ar[d].t, V[j + 1]);
+      papply(t, d, ar[d].t, V[j + 1]);
       for (int i = 0; i <= j; ++i) {
         std::vector<double> h = dots(t, V[j + 1], V[i]);
         for (int e = 0; e < t.n; ++e) {
@@ -694,6 +705,7 @@ int wr_batch_create(wr_batch** out, int n, const wr_problem* ps, const wr_option
       D = std::max(D, L + 1);
     }
     b->D = D;
+    b->depth_variant.assign(D, -1);
     b->off.assign(D, std::vector<int64_t>(n, -1));
     b->off_ye.assign(D, std::vector<int64_t>(n, -1));
     b->off_yp.assign(D, std::vector<int64_t>(n, -1));

@@ -465,13 +465,31 @@ __device__ __forceinline__ double widen(double v) { return v; }
 __device__ __forceinline__ float widen(float v) { return v; }
 __device__ __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-template <int K, int Q, typename FT, int NPGX = 2 * K - 1>
+// Tile variants of the smoother apply (chosen per level by the autotuner): column
+// groups per chunk G, CTAs per SM and the shared-memory ring that streams the
+// factor chunks.  Variants of one K with the same G sum in the same order.
+//   Q2/Q1 (K = 1): G = 5 with 1, 2 or 3 CTAs per SM (176 / 96 / 64 KB rings);
+//   Q3/Q2 (K = 2): G = 4 with one 480-thread CTA per SM (176 KB), or G = 2 with
+//                  two or three 256-thread CTAs per SM (96 / 64 KB).
+// The coarse 3x3 block (NPGX != 2K - 1) always takes variant 0.
+constexpr int kApplyVariants = 3;
+// without tuning: three 64 KB CTAs per SM for Q2/Q1, one 480-thread CTA for Q3/Q2
+inline int default_apply_variant(int k) { return k == 1 ? 2 : 0; }
+template <int K, int V>
+struct ApplyTile {
+  static constexpr int G = K == 1 ? 5 : (V == 0 ? 4 : 2);
+  static constexpr int MINB = V + 1;
+  static constexpr int RING_KB = V == 0 ? 176 : V == 1 ? 96 : 64;
+};
+
+template <int K, int Q, typename FT, int NPGX = 2 * K - 1, int V = 0>
 struct ApplyCfg {
   using pd = PD<K, NPGX>;
   using CT = typename ComputeType<FT>::type;
+  using TL = ApplyTile<K, NPGX == 2 * K - 1 ? V : 0>;
   static constexpr int MS = pd::MS, NT = Q + 1, NB = NT * NT;
-  static constexpr int G = K == 1 ? 5 : 4;                        // column groups per chunk
-  static constexpr int NCONS = (G * MS + 31) / 32 * 32;           // consumer threads: 256 or 448
+  static constexpr int G = TL::G;                                 // column groups per chunk
+  static constexpr int NCONS = (G * MS + 31) / 32 * 32;           // consumer threads
   static constexpr int NTH = NCONS + 32;                          // + one producer warp
   static constexpr int GR = 16 / (int)sizeof(FT);                 // elements per 16-byte granule
   static constexpr int BLK = (MS * MS + GR - 1) / GR * GR;        // padded block elements
@@ -484,12 +502,8 @@ struct ApplyCfg {
   static constexpr int LAST = BLK - (NCH - 1) * CC * MS;          // last chunk carries the padding
   static constexpr int SLOT = CC * MS > LAST ? CC * MS : LAST;
   static constexpr int SLOT_ELEMS = (SLOT + GR - 1) / GR * GR;
-  // Q2/Q1 patch blocks are small (51 x 51 per temporal pair): a 64 KB ring and three
-  // CTAs per SM hide the per-slab barriers and the jump-coupling latency of one CTA
-  // behind the others; larger blocks take one CTA per SM and a 176 KB ring.
-  static constexpr bool SMALL = K == 1 && NPGX == 2 * K - 1;
-  static constexpr int MINB = SMALL ? 3 : 1;                      // CTAs per SM
-  static constexpr int RING_BYTES = (SMALL ? 64 : 176) * 1024;
+  static constexpr int MINB = TL::MINB;                           // CTAs per SM
+  static constexpr int RING_BYTES = TL::RING_KB * 1024;
   static constexpr int NS = RING_BYTES / (SLOT_ELEMS * (int)sizeof(FT)) < 16
                                 ? RING_BYTES / (SLOT_ELEMS * (int)sizeof(FT))
                                 : 16;
@@ -497,9 +511,9 @@ struct ApplyCfg {
   static_assert(NS >= 2, "ring too small");
 };
 
-template <int K, int Q, typename FT, int NPGX = 2 * K - 1>
+template <int K, int Q, typename FT, int NPGX = 2 * K - 1, int V = 0>
 struct ApplySmem {
-  using C = ApplyCfg<K, Q, FT, NPGX>;
+  using C = ApplyCfg<K, Q, FT, NPGX, V>;
   using pd = PD<K, NPGX>;
   using CT = typename C::CT;
   unsigned long long full[C::NS];
@@ -581,17 +595,17 @@ struct ApplyItem {
   const double* prev;
 };
 
-template <int K, int Q, typename FT, int NPGX, class Items>
+template <int K, int Q, typename FT, int NPGX, int V, class Items>
 __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items& items, int64_t nitems,
                                                  int* __restrict__ err) {
-  using C = ApplyCfg<K, Q, FT, NPGX>;
+  using C = ApplyCfg<K, Q, FT, NPGX, V>;
   using pd = PD<K, NPGX>;
   using CT = typename C::CT;
   constexpr int MS = C::MS, NT = C::NT, NB = C::NB, NS = C::NS, NVG = pd::NVG, NCH = C::NCH, NCONS = C::NCONS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   FT* ring = reinterpret_cast<FT*>(smem_raw);
-  ApplySmem<K, Q, FT, NPGX>& sm =
-      *reinterpret_cast<ApplySmem<K, Q, FT, NPGX>*>(smem_raw + (size_t)NS * C::SLOT_ELEMS * sizeof(FT));
+  ApplySmem<K, Q, FT, NPGX, V>& sm =
+      *reinterpret_cast<ApplySmem<K, Q, FT, NPGX, V>*>(smem_raw + (size_t)NS * C::SLOT_ELEMS * sizeof(FT));
   volatile int* abort_flag = &sm.abort_flag;
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid == 0) {
@@ -822,18 +836,18 @@ struct BatchItems {
   }
 };
 
-template <int K, int Q, typename FT, int NPGX>
-__global__ void __launch_bounds__(ApplyCfg<K, Q, FT, NPGX>::NTH, ApplyCfg<K, Q, FT, NPGX>::MINB)
+template <int K, int Q, typename FT, int NPGX, int V>
+__global__ void __launch_bounds__(ApplyCfg<K, Q, FT, NPGX, V>::NTH, ApplyCfg<K, Q, FT, NPGX, V>::MINB)
 block_apply_kernel(LevelGeom g, FeTables T, BlockSet bs, const FT* __restrict__ factors, const double* __restrict__ r,
                    double* __restrict__ out, int nblk, int* __restrict__ err, const double* __restrict__ prev) {
-  apply_persistent<K, Q, FT, NPGX>(T, SingleItems<FT>{g, bs, factors, r, out, prev}, nblk, err);
+  apply_persistent<K, Q, FT, NPGX, V>(T, SingleItems<FT>{g, bs, factors, r, out, prev}, nblk, err);
 }
 
-template <int K, int Q, typename FT, int NPGX>
-__global__ void __launch_bounds__(ApplyCfg<K, Q, FT, NPGX>::NTH, ApplyCfg<K, Q, FT, NPGX>::MINB)
+template <int K, int Q, typename FT, int NPGX, int V>
+__global__ void __launch_bounds__(ApplyCfg<K, Q, FT, NPGX, V>::NTH, ApplyCfg<K, Q, FT, NPGX, V>::MINB)
 bt_block_apply_kernel(const BatchSeg* __restrict__ segs, int nseg, int64_t nitems, FeTables T,
                       const double* __restrict__ r, double* __restrict__ yp, int coarse, int* __restrict__ err) {
-  apply_persistent<K, Q, FT, NPGX>(T, BatchItems<FT>{segs, nseg, r, yp, coarse != 0}, nitems, err);
+  apply_persistent<K, Q, FT, NPGX, V>(T, BatchItems<FT>{segs, nseg, r, yp, coarse != 0}, nitems, err);
 }
 
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
@@ -921,12 +935,12 @@ int persistent_grid(Kern kern, int nth, size_t smem) {
   return sms * (per_sm > 0 ? per_sm : 1);
 }
 
-template <int K, int Q, typename FT, int NPGX = 2 * K - 1>
+template <int K, int Q, typename FT, int NPGX = 2 * K - 1, int V = 0>
 void run_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs, const FT* factors, const double* r,
                double* out, int* err, const double* prev, cudaStream_t s) {
-  using C = ApplyCfg<K, Q, FT, NPGX>;
-  const size_t smem = (size_t)C::NS * C::SLOT_ELEMS * sizeof(FT) + sizeof(ApplySmem<K, Q, FT, NPGX>);
-  auto kern = block_apply_kernel<K, Q, FT, NPGX>;
+  using C = ApplyCfg<K, Q, FT, NPGX, V>;
+  const size_t smem = (size_t)C::NS * C::SLOT_ELEMS * sizeof(FT) + sizeof(ApplySmem<K, Q, FT, NPGX, V>);
+  auto kern = block_apply_kernel<K, Q, FT, NPGX, V>;
   // persistent grid: CTAs resident on the whole GPU (computed once; thread-safe static)
   static const int grid_cap = persistent_grid(kern, C::NTH, smem);
   const int nblk = bs.kind == 0 ? g.npatch() : 1;
@@ -935,12 +949,12 @@ void run_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs, const 
   WR_LAUNCH_CHECK();
 }
 
-template <int K, int Q, typename FT, int NPGX = 2 * K - 1>
+template <int K, int Q, typename FT, int NPGX = 2 * K - 1, int V = 0>
 void run_bt_apply(const BatchSeg* segs, int nseg, int64_t items, const FeTables& T, const double* r, double* yp,
                   bool coarse, int* err, cudaStream_t s) {
-  using C = ApplyCfg<K, Q, FT, NPGX>;
-  const size_t smem = (size_t)C::NS * C::SLOT_ELEMS * sizeof(FT) + sizeof(ApplySmem<K, Q, FT, NPGX>);
-  auto kern = bt_block_apply_kernel<K, Q, FT, NPGX>;
+  using C = ApplyCfg<K, Q, FT, NPGX, V>;
+  const size_t smem = (size_t)C::NS * C::SLOT_ELEMS * sizeof(FT) + sizeof(ApplySmem<K, Q, FT, NPGX, V>);
+  auto kern = bt_block_apply_kernel<K, Q, FT, NPGX, V>;
   static const int grid_cap = persistent_grid(kern, C::NTH, smem);
   if (items <= 0) return;
   const int grid = items < grid_cap ? (int)items : grid_cap;
@@ -948,6 +962,24 @@ void run_bt_apply(const BatchSeg* segs, int nseg, int64_t items, const FeTables&
   WR_LAUNCH_CHECK();
 }
 
+
+template <int K, int Q, typename FT>
+void apply_variant(int variant, const LevelGeom& g, const FeTables& T, const BlockSet& bs, const FT* factors,
+                   const double* r, double* out, int* err, const double* prev, cudaStream_t s) {
+  if (variant < 0) variant = default_apply_variant(K);
+  if (variant == 0) run_apply<K, Q, FT, 2 * K - 1, 0>(g, T, bs, factors, r, out, err, prev, s);
+  else if (variant == 1) run_apply<K, Q, FT, 2 * K - 1, 1>(g, T, bs, factors, r, out, err, prev, s);
+  else run_apply<K, Q, FT, 2 * K - 1, 2>(g, T, bs, factors, r, out, err, prev, s);
+}
+
+template <int K, int Q, typename FT>
+void bt_apply_variant(int variant, const BatchSeg* segs, int nseg, int64_t items, const FeTables& T,
+                      const double* r, double* yp, int* err, cudaStream_t s) {
+  if (variant < 0) variant = default_apply_variant(K);
+  if (variant == 0) run_bt_apply<K, Q, FT, 2 * K - 1, 0>(segs, nseg, items, T, r, yp, false, err, s);
+  else if (variant == 1) run_bt_apply<K, Q, FT, 2 * K - 1, 1>(segs, nseg, items, T, r, yp, false, err, s);
+  else run_bt_apply<K, Q, FT, 2 * K - 1, 2>(segs, nseg, items, T, r, yp, false, err, s);
+}
 
 }  // namespace
 
@@ -977,15 +1009,19 @@ void launch_block_factor(const LevelGeom& g, const FeTables& T, const PhysParams
 }
 
 void launch_block_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs, const void* factors, int precision,
-                        const double* r, double* out, int* err, cudaStream_t s, const double* prev) {
-#define WR_A(K_, Q_)                                                                                          \
-  if (g.k == K_ && g.q == Q_) {                                                                               \
-    if (precision == WR_FP32)                                                                                 \
-      run_apply<K_, Q_, float>(g, T, bs, static_cast<const float*>(factors), r, out, err, prev, s);                     \
-    else if (precision == WR_BF16)                                                                            \
-      run_apply<K_, Q_, __nv_bfloat16>(g, T, bs, static_cast<const __nv_bfloat16*>(factors), r, out, err, prev, s);     \
-    else                                                                                                      \
-      run_apply<K_, Q_, double>(g, T, bs, static_cast<const double*>(factors), r, out, err, prev, s);                   \
+                        const double* r, double* out, int* err, cudaStream_t s, const double* prev, int variant) {
+#define WR_A(K_, Q_)                                                                                   \
+  if (g.k == K_ && g.q == Q_) {                                                                        \
+    if (bs.kind == 1) {                                                                                \
+      run_apply<K_, Q_, double>(g, T, bs, static_cast<const double*>(factors), r, out, err, prev, s);  \
+    } else if (precision == WR_FP32) {                                                                 \
+      apply_variant<K_, Q_, float>(variant, g, T, bs, static_cast<const float*>(factors), r, out, err, prev, s); \
+    } else if (precision == WR_BF16) {                                                                 \
+      apply_variant<K_, Q_, __nv_bfloat16>(variant, g, T, bs, static_cast<const __nv_bfloat16*>(factors), r, out, \
+                                           err, prev, s);                                              \
+    } else {                                                                                           \
+      apply_variant<K_, Q_, double>(variant, g, T, bs, static_cast<const double*>(factors), r, out, err, prev, s); \
+    }                                                                                                  \
   } else
   if (bs.kind == 1 && g.k == 1 && bs.npg == 4) {  // coarse 3x3 block of Q2/Q1 (FP64)
     if (g.q == 0) run_apply<1, 0, double, 4>(g, T, bs, static_cast<const double*>(factors), r, out, err, prev, s);
@@ -1020,7 +1056,7 @@ void launch_patch_slots(const LevelGeom& g, const BlockSet& bs, int blk, int* ou
 
 void bt_block_apply(int k, int q, int precision, const BatchSeg* segs, int nseg, int64_t items, int64_t dofs,
                     const FeTables& T, const double* r, double* out, double* yp, int* err, int coarse_n,
-                    cudaStream_t s) {
+                    cudaStream_t s, int variant) {
   // coarse blocks (coarse_n = 2 or 3) are FP64; the 3x3 coarse block of Q2/Q1 uses its own slot shape
   if (coarse_n == 3) {
     if (k != 1) throw WrError(WR_ERR_ARG, "3x3 coarse blocks need k = 1");
@@ -1038,10 +1074,10 @@ void bt_block_apply(int k, int q, int precision, const BatchSeg* segs, int nseg,
   }
 #define WR_BA(K_, Q_)                                                                                    \
   if (k == K_ && q == Q_) {                                                                              \
-    if (precision == WR_FP32) run_bt_apply<K_, Q_, float>(segs, nseg, items, T, r, yp, false, err, s);   \
+    if (precision == WR_FP32) bt_apply_variant<K_, Q_, float>(variant, segs, nseg, items, T, r, yp, err, s); \
     else if (precision == WR_BF16)                                                                       \
-      run_bt_apply<K_, Q_, __nv_bfloat16>(segs, nseg, items, T, r, yp, false, err, s);                   \
-    else run_bt_apply<K_, Q_, double>(segs, nseg, items, T, r, yp, false, err, s);                       \
+      bt_apply_variant<K_, Q_, __nv_bfloat16>(variant, segs, nseg, items, T, r, yp, err, s);             \
+    else bt_apply_variant<K_, Q_, double>(variant, segs, nseg, items, T, r, yp, err, s);                 \
   } else
   WR_BA(1, 0) WR_BA(1, 1) WR_BA(2, 0) WR_BA(2, 1) throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 #undef WR_BA

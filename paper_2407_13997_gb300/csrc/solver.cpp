@@ -10,7 +10,10 @@
 #include <complex>
 #include <cstring>
 #include <atomic>
+#include <functional>
+#include <map>
 #include <memory>
+#include <mutex>
 
 #include "wrmg_internal.h"
 
@@ -26,6 +29,47 @@ void wr_uncount_launches(int64_t n) { g_launches.fetch_sub(n, std::memory_order_
 // host-side fault injection: the n-th device allocation from now on fails (0 = off)
 std::atomic<int64_t> g_fail_alloc{0};
 
+// Autotuner of the smoother-apply tile: every variant is timed on the level's own
+// stored factors (one warm-up and two timed launches, CUDA events on the stream)
+// and the fastest is kept.  The choice is cached for the process per key, so every
+// context and batch of one shape and precision uses the same tile (and therefore
+// the same summation order) from then on.
+namespace {
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+}  // namespace
+
+int tune_apply_variant(const TuneKey& key, cudaStream_t s, const std::function<void(int)>& launch) {
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) return it->second;
+  }
+  cudaEvent_t e0, e1;
+  WR_CUDA(cudaEventCreate(&e0));
+  WR_CUDA(cudaEventCreate(&e1));
+  int best = -1;
+  float best_ms = 0.f;
+  for (int v = 0; v < kApplyTileVariants; ++v) {
+    launch(v);
+    WR_CUDA(cudaEventRecord(e0, s));
+    launch(v);
+    launch(v);
+    WR_CUDA(cudaEventRecord(e1, s));
+    WR_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    WR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (best < 0 || ms < best_ms) {
+      best = v;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  return g_tuned.emplace(key, best).first->second;  // a concurrent tuner may have won: keep its choice
+}
+
 namespace {
 
 struct Level {
@@ -35,6 +79,7 @@ struct Level {
   void* factors = nullptr;  // stored factors (null when the level recomputes them per apply)
   bool recompute = false;   // factors recomputed in windows of `nw` slabs at every smoother apply
   int nw = 0;
+  int variant = -1;         // apply tile chosen by the autotuner (-1: not yet, the default of k)
   double *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *z = nullptr, *t = nullptr;
   double lam = 0.0;
   bool lam_set = false;
@@ -200,11 +245,11 @@ struct wr_ctx {
     if (prof) {
       cudaEvent_t e0 = next_event(), e1 = next_event();
       WR_CUDA(cudaEventRecord(e0, s));
-      launch_block_apply(L[l].g, tab, L[l].bs, L[l].factors, opt.precision, r, Yp, derr, s);
+      launch_block_apply(L[l].g, tab, L[l].bs, L[l].factors, opt.precision, r, Yp, derr, s, nullptr, L[l].variant);
       WR_CUDA(cudaEventRecord(e1, s));
       prof_ev[l].push_back({e0, e1});
     } else {
-      launch_block_apply(L[l].g, tab, L[l].bs, L[l].factors, opt.precision, r, Yp, derr, s);
+      launch_block_apply(L[l].g, tab, L[l].bs, L[l].factors, opt.precision, r, Yp, derr, s, nullptr, L[l].variant);
     }
     launch_scatter(L[l].g, L[l].bs, Yp, y, s);
   }
@@ -288,6 +333,16 @@ struct wr_ctx {
     if (ph.conv != 0.0) launch_conv_elements(L[0].g, tab, L[0].W, Ce, s);
     launch_block_factor(L[0].g, tab, ph, cbs, Ce, cfactors, WR_FP64, fstat, s);
     linearised = true;
+    if (opt.autotune)
+      for (int l = 1; l <= T_; ++l)
+        if (!L[l].recompute && L[l].variant < 0) {
+          Level& lv = L[l];
+          vec_zero(lv.g.ndofs, lv.x, s);
+          const TuneKey key{0, k, q, opt.precision, (int64_t)lv.g.npatch(), lv.g.N};
+          lv.variant = tune_apply_variant(key, s, [&](int v) {
+            launch_block_apply(lv.g, tab, lv.bs, lv.factors, opt.precision, lv.x, Yp, derr, s, nullptr, v);
+          });
+        }
     if (eig)
       for (int l = 1; l <= T_; ++l) eigen_estimate(l);
   }
@@ -543,6 +598,7 @@ void wr_default_options(wr_options* o) {
   o->patch_assembly = WR_PATCH_SUBMATRIX;
   o->scatter_weight = WR_WEIGHT_ONE;
   o->store_factors = WR_STORE;
+  o->autotune = 1;
   o->recompute_slabs = 0;
   o->memory_budget_mb = 0;
 }
@@ -734,6 +790,12 @@ int wr_num_levels(const wr_ctx* c, int* out) {
 int wr_ndofs(const wr_ctx* c, int level, int64_t* out) {
   if (!c || !out || level < 0 || level >= (int)c->L.size()) return WR_ERR_ARG;
   *out = c->L[level].g.ndofs;
+  return WR_OK;
+}
+
+int wr_apply_tile(const wr_ctx* c, int level, int* variant) {
+  if (!c || !variant || level < 1 || level >= (int)c->L.size()) return WR_ERR_ARG;
+  *variant = c->L[level].variant;
   return WR_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <stdexcept>
 #include <atomic>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -197,9 +198,12 @@ void launch_block_factor(const LevelGeom& g, const FeTables& T, const PhysParams
 // block (kind 1) writes the solution.  A window of slabs is g with N = window
 // length, r and out offset to the window's first slab, factors of the window,
 // and prev = the patch outputs of the slab before it (null: zero jump state).
+// variant: the apply tile (0 .. 2, -1 = the default of k; patch blocks only), chosen
+// per level by the autotuner
 void launch_block_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs,
                         const void* factors, int precision, const double* r, double* out,
-                        int* err, cudaStream_t s, const double* prev = nullptr);
+                        int* err, cudaStream_t s, const double* prev = nullptr, int variant = -1);
+constexpr int kApplyTileVariants = 3;
 void launch_scatter(const LevelGeom& g, const BlockSet& bs, const double* Yp, double* y,
                     cudaStream_t s);
 void launch_restrict(const LevelGeom& gf, const LevelGeom& gc, const FeTables& T,
@@ -231,7 +235,7 @@ void bt_residual(int k, int q, const BatchSeg* segs, int nseg, int64_t units, in
 // coarse_n = 0: patch smoother (scatter into `out`); 2 or 3: coarse block solves of that coarse mesh
 void bt_block_apply(int k, int q, int precision, const BatchSeg* segs, int nseg, int64_t items, int64_t dofs,
                     const FeTables& T, const double* r, double* out, double* yp, int* err, int coarse_n,
-                    cudaStream_t s);
+                    cudaStream_t s, int variant = -1);
 void bt_restrict(const BatchSeg* segs, int nseg, int64_t dofsc, const FeTables& T, const double* xf, double* xc,
                  cudaStream_t s);
 void bt_prolong_add(const BatchSeg* segs, int nseg, int64_t dofs, const FeTables& T, const double* xc, double* xf,
@@ -266,3 +270,20 @@ void launch_bounded_wait_selftest(int* timed_out, unsigned long long* ns, cudaSt
 void set_cancel_flag(wr_ctx* c, const std::atomic<int>* flag);
 // Host-side fault injection counter (wr_inject_alloc_failure).
 extern std::atomic<int64_t> g_fail_alloc;
+
+// Key of a tuned smoother-apply tile: kind (0 context level, 1 batch depth), k, q,
+// precision, blocks per launch, slabs.
+struct TuneKey {
+  int kind, k, q, precision;
+  int64_t blocks;
+  int slabs;
+  bool operator<(const TuneKey& o) const {
+    if (kind != o.kind) return kind < o.kind;
+    if (k != o.k) return k < o.k;
+    if (q != o.q) return q < o.q;
+    if (precision != o.precision) return precision < o.precision;
+    if (blocks != o.blocks) return blocks < o.blocks;
+    return slabs < o.slabs;
+  }
+};
+int tune_apply_variant(const TuneKey& key, cudaStream_t s, const std::function<void(int)>& launch);

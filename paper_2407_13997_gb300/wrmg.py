@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
                 ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
                 ("patch_assembly", ctypes.c_int), ("scatter_weight", ctypes.c_int),
                 ("store_factors", ctypes.c_int), ("recompute_slabs", ctypes.c_int),
-                ("memory_budget_mb", ctypes.c_int)]
+                ("memory_budget_mb", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -75,6 +75,7 @@ _SIGS = {
     "wr_ndofs": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
     "wr_device_bytes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "wr_factor_storage": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "wr_apply_tile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "wr_patch_dofs": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int)]),
     "wr_initial_guess": (ctypes.c_int, [_P, _P]),
@@ -285,6 +286,11 @@ class Context:
         st, nw = ctypes.c_int(), ctypes.c_int()
         self._check(self._lib.wr_factor_storage(self._h, level, ctypes.byref(st), ctypes.byref(nw)))
         return bool(st.value), nw.value
+
+    def apply_tile(self, level):
+        v = ctypes.c_int()
+        self._check(self._lib.wr_apply_tile(self._h, level, ctypes.byref(v)))
+        return v.value
 
     def vector(self, level=None):
         import torch
