@@ -1,0 +1,90 @@
+"""Pins for the oracle's heat-equation waveform relaxation (CPU only)."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle.heat import (HeatDiscretisation, HeatHierarchy, HeatProblem, HeatSmoother, global_1d, heat_patch_dofs,
+                         heat_patch_spatial, heat_solve)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_spatial_matrices_integrate_polynomials_exactly(k):
+    """Q_k reproduces polynomials of degree k in each variable: 1^T M 1 = |Omega| = 1,
+    K 1 = 0, x^T K x = int |grad x|^2 = 1, 1^T M x^k = 1/(k+1), and
+    (x y)^T K (x y) = int (y^2 + x^2) = 2/3."""
+    d = HeatDiscretisation(4, k, 0, 1, HeatProblem())
+    x = d.node_coords()
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    one = np.ones(d.S)
+    assert abs(one @ d.M @ one - 1.0) < 1e-13
+    assert np.abs(d.K @ one).max() < 1e-12
+    xv = X.ravel()
+    assert abs(xv @ d.K @ xv - 1.0) < 1e-12
+    assert abs(one @ d.M @ xv ** k - 1.0 / (k + 1)) < 1e-13
+    xy = (X * Y).ravel()
+    assert abs(xy @ d.K @ xy - 2.0 / 3.0) < 1e-12
+    M1, K1 = global_1d(3, k)
+    assert np.allclose(M1, M1.T) and np.allclose(K1, K1.T)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_vertex_star_patches_are_open_stars(k):
+    """Interior patch: (2k-1)^2 nodes strictly inside the 2x2 cell block; boundary
+    vertices keep the boundary nodes of their star; every node lies in a patch."""
+    d = HeatDiscretisation(4, k, 1, 2, HeatProblem())
+    x = d.node_coords()
+    h = 1.0 / d.n
+    covered = np.zeros(d.S, dtype=bool)
+    for J in range(d.n + 1):
+        for I in range(d.n + 1):
+            idx = heat_patch_spatial(d, I, J)
+            geo = [gy * d.nv + gx for gy in range(d.nv) for gx in range(d.nv)
+                   if (I - 1) * h + 1e-12 < x[gx] < (I + 1) * h - 1e-12
+                   and (J - 1) * h + 1e-12 < x[gy] < (J + 1) * h - 1e-12]
+            assert np.array_equal(idx, geo)
+            covered[idx] = True
+    assert len(heat_patch_spatial(d, 2, 2)) == (2 * k - 1) ** 2
+    assert covered.all()
+
+
+@pytest.mark.parametrize("q", [0, 1])
+def test_eigenfunction_decay_converges(q):
+    """u0 = cos(pi x) is a Neumann eigenfunction: u = exp(-nu pi^2 t) cos(pi x).  With a
+    fine Q3 mesh the end-value error is the time error, O(dt^(2q+1)) (Radau IIA)."""
+    errs = []
+    for N in (4, 8):
+        pb = HeatProblem(nu=1.0, T=0.2, u0="cos")
+        d = HeatDiscretisation(8, 3, q, N, pb)
+        U = spla.spsolve(d.jacobian().tocsc(), d.rhs())
+        end = U[d.block(N - 1, d.nt - 1):d.block(N - 1, d.nt - 1) + d.S]
+        x = d.node_coords()
+        X, Y = np.meshgrid(x, x, indexing="xy")
+        errs.append(np.abs(end - pb.exact(X, Y, 0.2).ravel()).max())
+    rate = np.log2(errs[0] / errs[1])
+    assert abs(rate - (2 * q + 1)) < 0.35, (errs, rate)
+
+
+@pytest.mark.parametrize("n,k,q,N", [(2, 1, 0, 3), (2, 2, 1, 2), (4, 1, 1, 2)])
+def test_smoother_equals_sum_of_explicit_space_time_patch_inverses(n, k, q, N):
+    d = HeatDiscretisation(n, k, q, N, HeatProblem())
+    J = d.jacobian()
+    sm = HeatSmoother(d, J)
+    r = np.random.default_rng(3).standard_normal(d.ndofs)
+    ref = np.zeros(d.ndofs)
+    for i in range((n + 1) ** 2):
+        ix = np.concatenate([heat_patch_dofs(d, i, s) for s in range(N)])
+        ref[ix] += np.linalg.inv(J[ix][:, ix].toarray()) @ r[ix]
+    assert np.abs(sm.apply(r) - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("k,q", [(1, 0), (2, 1), (3, 1)])
+def test_fgmres_wrmg_reaches_the_direct_solution_in_few_iterations(k, q):
+    """FGMRES preconditioned by one WRMG V(2,2) cycle reaches the direct space-time
+    solution; the paper reports 3 iterations to 1e-6 for its heat problems."""
+    hier = HeatHierarchy(8, 2, k, q, 20, HeatProblem(nu=1.0, T=0.02))
+    U, its = heat_solve(hier, rtol=1e-6, atol=1e-6)
+    ref = spla.spsolve(hier.J[-1].tocsc(), hier.fine.rhs())
+    assert np.abs(U - ref).max() < 1e-4 * np.abs(ref).max()   # residual 1e-6 times the condition
+    assert its <= 5, its   # the paper reports 3 on its triangle meshes
+    U2, its2 = heat_solve(hier, rtol=1e-12, atol=0.0)
+    assert np.abs(U2 - ref).max() < 1e-10 * np.abs(ref).max()
