@@ -65,6 +65,13 @@ extern "C" {
 #define WR_FOURIER 2       /* no-slip walls, u(0) = 0, f = sum amp_j curl(sin(mx_j pi x) sin(my_j pi y))     */
 #define WR_LID 3           /* lid-driven cavity (Sec. 4): u = (1, 0) on the open top edge, 0 on the other walls
                               and the top corners, u(0) = 0, f = 0                                         */
+/* The heat equation (Def. heat): u_t - nu lap u = 0, natural boundary conditions, continuous Q_k
+ * (k = 1, 2, 3) x DG(q); one scalar field, canonical index (slab (q+1) + a) S + y nv + x with
+ * nv = n k + 1, S = nv^2; vertex-star (open-star) patches; n_coarse = 2.  The problem is linear:
+ * wr_solve with newton_maxit = 1, ew = 0 and eta_fixed = the FGMRES tolerance is the paper's
+ * FGMRES-WRMG solve (Sec. 5).  Only the FP64 smoother exists for it. */
+#define WR_HEAT 4          /* u(0) = sin(pi x) + cos(2 pi y) (Sec. 5)                                      */
+#define WR_HEAT_EIGEN 5    /* u(0) = cos(pi x): u = exp(-nu pi^2 t) cos(pi x) exactly                      */
 
 /* arithmetic of the stored patch factors and of the smoother (wr_options.precision) */
 #define WR_FP64 0  /* FP64 factors and smoother (the plain method)                        */
@@ -101,7 +108,7 @@ typedef struct {
     int q;          /* DG(q) in time; q = 0 or 1                                             */
     int n_slabs;    /* N time slabs of width T / N                                           */
     double T, nu, conv;
-    int kind;       /* WR_TAYLOR_GREEN, WR_POLY, WR_FOURIER or WR_LID                        */
+    int kind;       /* WR_TAYLOR_GREEN, WR_POLY, WR_FOURIER, WR_LID, WR_HEAT or WR_HEAT_EIGEN */
     int steady;     /* WR_POLY only: time-constant u = (y^2, x^2)                            */
     int n_modes;    /* WR_FOURIER: number of modes (<= 8), host arrays below                 */
     const int *mx, *my;

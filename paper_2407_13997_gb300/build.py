@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libwrmg.so")
-SOURCES = ["tables.cpp", "fe_kernels.cu", "patch_kernels.cu", "transfer_blas.cu", "solver.cpp", "batch.cpp", "server.cpp"]
+SOURCES = ["tables.cpp", "fe_kernels.cu", "patch_kernels.cu", "transfer_blas.cu", "solver.cpp", "batch.cpp", "server.cpp", "heat.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", CSRC]

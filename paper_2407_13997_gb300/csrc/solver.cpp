@@ -110,6 +110,7 @@ struct wr_ctx {
   int* slots = nullptr;
   int* derr = nullptr;   // device error flag of the bounded waits
   int* fstat = nullptr;  // device zero-pivot flag of the factorisation
+  bool heat = false;     // the heat equation (one scalar field) instead of Navier-Stokes
   double t0 = 0.0;       // the problem's start time
   double* u0 = nullptr;  // slab-0 initial state set by wr_set_initial_state (a finest-level spatial block)
   std::vector<void*> allocs;
@@ -194,7 +195,25 @@ struct wr_ctx {
   }
   double norm(int64_t n, const double* x) { return std::sqrt(dot(n, x, x)); }
 
-  void jac(int l, const double* x, double* y) { launch_jacobian(L[l].g, tab, ph, L[l].W, x, y, ye, s); }
+  void jac(int l, const double* x, double* y) {
+    if (heat) heat_jacobian(L[l].g, tab, ph, x, y, s);
+    else launch_jacobian(L[l].g, tab, ph, L[l].W, x, y, ye, s);
+  }
+  void restrict_to(int l, const double* xf, double* xc) {
+    if (heat) heat_restrict(L[l].g, L[l - 1].g, tab, xf, xc, s);
+    else launch_restrict(L[l].g, L[l - 1].g, tab, xf, xc, s);
+  }
+  void prolong_add(int l, const double* xc, double* xf) {
+    if (heat) heat_prolong_add(L[l].g, L[l - 1].g, tab, xc, xf, s);
+    else launch_prolong_add(L[l].g, L[l - 1].g, tab, xc, xf, s);
+  }
+  void project(const LevelGeom& g, double* x) {
+    if (!heat) launch_project_pressure(g, tab, x, s);  // the heat operator has no null space
+  }
+  void residual(const double* U, double* Fo) {
+    if (heat) heat_residual(fine().g, tab, ph, U, Fo, s);
+    else launch_residual(fine().g, tab, ph, U, Fo, ye, s);
+  }
 
   // Recomputing levels: per window of slabs, the convection element matrices and
   // the slab factors are rebuilt into the window buffer and applied at once; the
@@ -238,6 +257,20 @@ struct wr_ctx {
 
   void patch_apply(int l, const double* r, double* y) {
     if (!linearised) throw WrError(WR_ERR_STATE, "wr_linearise must be called first");
+    if (heat) {
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (prof) {
+        e0 = next_event();
+        e1 = next_event();
+        WR_CUDA(cudaEventRecord(e0, s));
+      }
+      heat_patch_apply(L[l].g, tab, static_cast<const double*>(L[l].factors), r, Yp, y, s);
+      if (prof) {
+        WR_CUDA(cudaEventRecord(e1, s));
+        prof_ev[l].push_back({e0, e1});
+      }
+      return;
+    }
     if (L[l].recompute) {
       patch_apply_windows(l, r, y);
       return;
@@ -258,6 +291,10 @@ struct wr_ctx {
     if (!linearised) throw WrError(WR_ERR_STATE, "wr_linearise must be called first");
     const LevelGeom& g = L[0].g;
     vec_zero(g.ndofs, x, s);
+    if (heat) {
+      heat_coarse_apply(g, tab, cfactors, b, x, s);
+      return;
+    }
     launch_block_apply(g, tab, cbs, cfactors, WR_FP64, b, x, derr, s);
     launch_project_pressure(g, tab, x, s);
   }
@@ -308,11 +345,11 @@ struct wr_ctx {
       jac(l, xl[l], L[l].t);
       vec_copy(L[l].g.ndofs, bl[l], L[l].r, s);
       vec_axpby(L[l].g.ndofs, -1.0, L[l].t, 1.0, L[l].r, s);
-      launch_restrict(L[l].g, L[l - 1].g, tab, L[l].r, L[l - 1].b, s);
+      restrict_to(l, L[l].r, L[l - 1].b);
     }
     coarse_solve(L[0].b, xl[0]);
     for (int l = 1; l <= T_; ++l) {
-      launch_prolong_add(L[l].g, L[l - 1].g, tab, xl[l - 1], xl[l], s);
+      prolong_add(l, xl[l - 1], xl[l]);
       smooth(l, bl[l], xl[l], false);
     }
     ++vcycles;
@@ -320,6 +357,14 @@ struct wr_ctx {
 
   void linearise(const double* W, bool eig) {
     const int T_ = top();
+    if (heat) {  // linear: the blocks do not depend on W
+      for (int l = 1; l <= T_; ++l) heat_factor(L[l].g, tab, ph, false, static_cast<double*>(L[l].factors), fstat, s);
+      heat_factor(L[0].g, tab, ph, true, cfactors, fstat, s);
+      linearised = true;
+      if (eig)
+        for (int l = 1; l <= T_; ++l) eigen_estimate(l);
+      return;
+    }
     vec_copy(L[T_].g.ndofs, W, L[T_].W, s);
     for (int l = T_; l >= 1; --l) launch_inject(L[l].g, L[l - 1].g, L[l].W, L[l - 1].W, s);
     for (int l = 1; l <= T_; ++l) {
@@ -353,7 +398,8 @@ struct wr_ctx {
     const int64_t n = lv.g.ndofs;
     const int m = opt.eig_steps;
     std::vector<double> H((m + 1) * m, 0.0);
-    launch_splitmix_free(lv.g, (uint64_t)l, V[0], s);
+    if (heat) heat_splitmix(lv.g.ndofs, (uint64_t)l, V[0], s);
+    else launch_splitmix_free(lv.g, (uint64_t)l, V[0], s);
     vec_scale(n, 1.0 / norm(n, V[0]), V[0], s);
     int mm = m;
     for (int j = 0; j < m; ++j) {
@@ -453,7 +499,7 @@ struct wr_ctx {
       for (int j = 0; j < m; ++j) {
         check_cancel();
         vcycle(V[j], Z[j]);
-        launch_project_pressure(fl.g, tab, Z[j], s);
+        project(fl.g, Z[j]);
         jac(top(), Z[j], V[j + 1]);
         for (int i = 0; i <= j; ++i) {
           const double hij = dot(n, V[j + 1], V[i]);
@@ -498,7 +544,7 @@ struct wr_ctx {
     const int64_t n = fl.g.ndofs;
     wr_stats loc;
     std::memset(&loc, 0, sizeof(loc));
-    launch_residual(fl.g, tab, ph, U, F, ye, s);
+    residual(U, F);
     double fnorm = norm(n, F);
     const double f0 = fnorm;
     double eta = opt.ew ? 0.5 : opt.eta_fixed;
@@ -526,7 +572,7 @@ struct wr_ctx {
       WR_CUDA(cudaStreamSynchronize(s));
       loc.krylov_ms += now_ms() - t1;
       vec_axpby(n, 1.0, hx, 1.0, U, s);
-      launch_residual(fl.g, tab, ph, U, F, ye, s);
+      residual(U, F);
       const double fnew = norm(n, F);
       loc.gmres_its[loc.newton_its] = its;
       loc.newton_its++;
@@ -623,10 +669,72 @@ int wr_estimate_bytes(const wr_problem* p, const wr_options* o, int64_t* out) {
   return rc;
 }
 
+// The heat equation's hierarchy: FP64 stored inverses of every (patch, slab) block,
+// the whole-mesh coarse block, and the same Krylov workspace as Navier-Stokes.
+static int create_heat(wr_ctx* c, const wr_problem* p) {
+  c->heat = true;
+  c->opt.precision = WR_FP64;
+  c->opt.store_factors = WR_STORE;
+  c->opt.autotune = 0;
+  c->tab = build_tables(p->k - 1, p->q);  // the degree-k tables are the Navier-Stokes velocity ones of k - 1
+  const int m = heat_block_size(p->k, p->q, false), mc = heat_block_size(p->k, p->q, true);
+  size_t max_yp = 1;
+  for (int n = p->n_coarse; n <= p->n_fine; n *= 2) {
+    Level lv;
+    lv.g = make_heat_geom(n, p->k, p->q, p->n_slabs, p->T);
+    lv.bs.kind = 0;
+    lv.bs.nvg = lv.bs.npg = 0;
+    lv.bs.ms = m;
+    const int64_t nd = lv.g.ndofs;
+    lv.W = c->alloc<double>(1);
+    lv.b = c->alloc<double>(nd);
+    lv.x = c->alloc<double>(nd);
+    lv.r = c->alloc<double>(nd);
+    lv.d = c->alloc<double>(nd);
+    lv.z = c->alloc<double>(nd);
+    lv.t = c->alloc<double>(nd);
+    if (n > p->n_coarse) {
+      lv.factors = c->alloc<double>((size_t)lv.g.npatch() * p->n_slabs * m * m);
+      max_yp = std::max(max_yp, (size_t)lv.g.npatch() * p->n_slabs * m);
+    }
+    lv.nw = p->n_slabs;
+    c->L.push_back(lv);
+  }
+  c->cbs.kind = 1;
+  c->cbs.ms = mc;
+  c->cfactors = c->alloc<double>((size_t)p->n_slabs * mc * mc);
+  c->Ce = c->alloc<double>(1);
+  c->ye = c->alloc<double>(1);
+  c->Yp = c->alloc<double>(max_yp);
+  const int64_t nfine = c->fine().g.ndofs;
+  const int nvec = std::max(c->opt.gmres_restart, c->opt.eig_steps) + 1;
+  for (int i = 0; i < nvec; ++i) c->V.push_back(c->alloc<double>(nfine));
+  for (int i = 0; i < c->opt.gmres_restart; ++i) c->Z.push_back(c->alloc<double>(nfine));
+  c->F = c->alloc<double>(nfine);
+  c->w = c->alloc<double>(nfine);
+  c->hb = c->alloc<double>(nfine);
+  c->hx = c->alloc<double>(nfine);
+  c->partials = c->alloc<double>(dot_partials_size());
+  c->dres = c->alloc<double>(1);
+  c->derr = c->alloc<int>(1);
+  c->fstat = c->alloc<int>(1);
+  c->u0 = c->alloc<double>(c->fine().g.S);
+  c->slots = c->alloc<int>(32);
+  if (c->dry) return WR_OK;
+  WR_CUDA(cudaMemsetAsync(c->derr, 0, sizeof(int), c->s));
+  WR_CUDA(cudaStreamSynchronize(c->s));
+  WR_CUDA(cudaMallocHost(&c->hres, sizeof(double)));
+  WR_CUDA(cudaMallocHost(&c->herr, sizeof(int)));
+  *c->herr = 0;
+  return WR_OK;
+}
+
 static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, void* stream) {
   wr_ctx* c = cptr;
   int rc = guarded(c, [&]() -> int {
-    need(p->k == 1 || p->k == 2, "k must be 1 or 2");
+    const bool heat = p->kind == WR_HEAT || p->kind == WR_HEAT_EIGEN;
+    need(p->k == 1 || p->k == 2 || (heat && p->k == 3), "k must be 1 or 2 (1, 2 or 3 for the heat equation)");
+    need(!heat || p->n_coarse == 2, "the heat equation coarsens to 2x2");
     need(p->q == 0 || p->q == 1, "q must be 0 or 1");
     need(p->n_coarse == 2 || (p->n_coarse == 3 && p->k == 1), "n_coarse must be 2 (or 3 for k = 1)");
     need(p->n_fine >= 4 && p->n_fine <= 4096, "n_fine out of range");
@@ -634,7 +742,7 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
     int nf = p->n_fine;
     while (nf > p->n_coarse && nf % 2 == 0) nf /= 2;
     need(nf == p->n_coarse, "n_fine must be n_coarse times a power of two");
-    need(p->kind >= WR_TAYLOR_GREEN && p->kind <= WR_LID, "unknown problem kind");
+    need(p->kind >= WR_TAYLOR_GREEN && p->kind <= WR_HEAT_EIGEN, "unknown problem kind");
     need(p->n_modes >= 0 && p->n_modes <= 8, "at most 8 Fourier modes");
     need(p->n_modes == 0 || (p->mx && p->my && p->amp), "Fourier mode arrays missing");
     if (o) c->opt = *o;
@@ -659,6 +767,7 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
     c->ph.t0 = p->t0;
     c->t0 = p->t0;
     for (int m = 0; m < p->n_modes; ++m) { c->ph.mx[m] = p->mx[m]; c->ph.my[m] = p->my[m]; c->ph.amp[m] = p->amp[m]; }
+    if (heat) return create_heat(c, p);
     c->tab = build_tables(p->k, p->q);
     std::vector<int> ns;
     for (int n = p->n_coarse; n <= p->n_fine; n *= 2) ns.push_back(n);
@@ -819,6 +928,19 @@ int wr_patch_dofs(const wr_ctx* cc, int level, int64_t patch, int slab, int64_t*
     check_level(c, level, 0);
     const Level& lv = c->L[level];
     need(patch >= 0 && patch < lv.g.npatch() && slab >= 0 && slab < lv.g.N, "patch or slab out of range");
+    if (c->heat) {
+      need(level >= 1, "the heat equation's coarsest level has no patches");
+      const int np = heat_patch_slots(lv.g, (int)patch, c->slots, c->s);
+      std::vector<int> sp(np);
+      WR_CUDA(cudaMemcpyAsync(sp.data(), c->slots, sizeof(int) * np, cudaMemcpyDeviceToHost, c->s));
+      WR_CUDA(cudaStreamSynchronize(c->s));
+      int cnt = 0;
+      for (int a = 0; a < lv.g.nt; ++a)
+        for (int s = 0; s < np; ++s)
+          if (sp[s] >= 0) idx[cnt++] = ((int64_t)slab * lv.g.nt + a) * lv.g.S + sp[s];
+      *len = cnt;
+      return WR_OK;
+    }
     const int ms = lv.bs.ms;
     launch_patch_slots(lv.g, lv.bs, (int)patch, c->slots, c->s);
     std::vector<int> sp(ms);
@@ -836,7 +958,8 @@ int wr_patch_dofs(const wr_ctx* cc, int level, int64_t patch, int slab, int64_t*
 int wr_initial_guess(wr_ctx* c, double* U) {
   return guarded(c, [&]() -> int {
     need(c && U, "null argument");
-    launch_boundary_values(c->fine().g, c->tab, c->ph, U, c->s);
+    if (c->heat) vec_zero(c->fine().g.ndofs, U, c->s);  // natural boundary conditions: start from zero
+    else launch_boundary_values(c->fine().g, c->tab, c->ph, U, c->s);
     return WR_OK;
   });
 }
@@ -844,7 +967,7 @@ int wr_initial_guess(wr_ctx* c, double* U) {
 int wr_residual(wr_ctx* c, const double* U, double* F) {
   return guarded(c, [&]() -> int {
     need(c && U && F && U != F, "null or aliased argument");
-    launch_residual(c->fine().g, c->tab, c->ph, U, F, c->ye, c->s);
+    c->residual(U, F);
     return WR_OK;
   });
 }
@@ -910,7 +1033,7 @@ int wr_restrict(wr_ctx* c, int fine_level, const double* xf, double* xc) {
   return guarded(c, [&]() -> int {
     need(c && xf && xc, "null argument");
     check_level(c, fine_level, 1);
-    launch_restrict(c->L[fine_level].g, c->L[fine_level - 1].g, c->tab, xf, xc, c->s);
+    c->restrict_to(fine_level, xf, xc);
     return WR_OK;
   });
 }
@@ -919,7 +1042,7 @@ int wr_prolong_add(wr_ctx* c, int fine_level, const double* xc, double* xf) {
   return guarded(c, [&]() -> int {
     need(c && xf && xc, "null argument");
     check_level(c, fine_level, 1);
-    launch_prolong_add(c->L[fine_level].g, c->L[fine_level - 1].g, c->tab, xc, xf, c->s);
+    c->prolong_add(fine_level, xc, xf);
     return WR_OK;
   });
 }
@@ -955,7 +1078,7 @@ int wr_vcycle_host(wr_ctx* c, const double* b_host, double* x_host) {
 int wr_project_pressure(wr_ctx* c, double* x) {
   return guarded(c, [&]() -> int {
     need(c && x, "null argument");
-    launch_project_pressure(c->fine().g, c->tab, x, c->s);
+    c->project(c->fine().g, x);
     return WR_OK;
   });
 }
@@ -999,7 +1122,8 @@ int wr_solve_timestepping(wr_ctx* c, int n_steps, double* U, wr_stats* st) {
         WR_CUDA(cudaMemcpyAsync(c->u0, Ui - step + last, sizeof(double) * g.S, cudaMemcpyDeviceToDevice, c->s));
         c->ph.u0 = c->u0;
       }
-      launch_boundary_values(g, c->tab, c->ph, Ui, c->s);
+      if (c->heat) vec_zero(g.ndofs, Ui, c->s);
+      else launch_boundary_values(g, c->tab, c->ph, Ui, c->s);
       wr_stats si;
       const int rc = c->solve(Ui, &si);
       tot.newton_its += si.newton_its;

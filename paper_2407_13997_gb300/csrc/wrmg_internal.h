@@ -287,3 +287,25 @@ struct TuneKey {
   }
 };
 int tune_apply_variant(const TuneKey& key, cudaStream_t s, const std::function<void(int)>& launch);
+
+// ---------------------------------------------------------------- heat equation (heat.cu)
+LevelGeom make_heat_geom(int n, int k, int q, int N, double T);
+int heat_block_size(int k, int q, bool coarse);  // slots per (block, slab): (q+1) PX^2
+void heat_jacobian(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* x, double* y,
+                   cudaStream_t s);
+void heat_residual(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* x, double* y,
+                   cudaStream_t s);
+// inverts every (patch, slab) block (coarse: the single whole-mesh block); st as in launch_block_factor
+void heat_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph, bool coarse, double* f, int* st,
+                 cudaStream_t s);
+void heat_patch_apply(const LevelGeom& g, const FeTables& T, const double* f, const double* r, double* Yp, double* y,
+                      cudaStream_t s);
+void heat_coarse_apply(const LevelGeom& g, const FeTables& T, const double* f, const double* b, double* x,
+                       cudaStream_t s);
+void heat_restrict(const LevelGeom& gf, const LevelGeom& gc, const FeTables& T, const double* xf, double* xc,
+                   cudaStream_t s);
+void heat_prolong_add(const LevelGeom& gf, const LevelGeom& gc, const FeTables& T, const double* xc, double* xf,
+                      cudaStream_t s);
+void heat_splitmix(int64_t n, uint64_t seed, double* x, cudaStream_t s);
+// slot -> node index (-1 outside the domain) of heat patch blk into d_out; returns the slot count
+int heat_patch_slots(const LevelGeom& g, int blk, int* d_out, cudaStream_t s);

@@ -17,6 +17,8 @@ KIND_TAYLOR_GREEN = 0
 KIND_POLY = 1
 KIND_FOURIER = 2
 KIND_LID = 3
+KIND_HEAT = 4          # heat equation, u(0) = sin(pi x) + cos(2 pi y)
+KIND_HEAT_EIGEN = 5    # heat equation, u(0) = cos(pi x)
 KIND_NAMES = {KIND_TAYLOR_GREEN: "taylor_green", KIND_POLY: "poly", KIND_FOURIER: "fourier", KIND_LID: "lid"}
 
 FOURIER_MODES = ((1, 1), (1, 2), (2, 1), (2, 2), (1, 3), (3, 1), (2, 3), (3, 2))
@@ -54,6 +56,8 @@ class Workload:
 
     def ndofs(self, n=None):
         n = self.n_fine if n is None else n
+        if self.kind in (KIND_HEAT, KIND_HEAT_EIGEN):  # one scalar Q_k field
+            return self.N * (self.q + 1) * (n * self.k + 1) ** 2
         nv = n * (self.k + 1) + 1
         np_ = n * self.k + 1
         return self.N * (self.q + 1) * (2 * nv * nv + np_ * np_)
@@ -76,6 +80,14 @@ def lid_cavity(n=16, k=1, q=0, N=20, R=10.0, T=0.02):
     """The lid-driven cavity of Sec. 4 in Reynolds-number form (nu = 1, convection
     R), started from rest, t in [0, T], n x n mesh coarsened to 2 x 2, N slabs."""
     return Workload(f"lid_R{R:g}_q{k + 1}q{k}_dg{q}_n{n}_N{N}", n, 2, k, q, N, T, 1.0, R, KIND_LID)
+
+
+def heat(n=16, k=1, q=0, N=20, nu=1.0, T=0.02, eigen=False):
+    """The heat equation of Sec. 5: u_t - nu lap u = 0, natural boundary conditions,
+    u(0) = sin(pi x) + cos(2 pi y) (eigen: cos(pi x)), t in [0, T], Q_k x DG(q), N slabs,
+    n x n mesh coarsened to 2 x 2."""
+    return Workload(f"heat_q{k}_dg{q}_n{n}_N{N}", n, 2, k, q, N, T, nu, 0.0,
+                    KIND_HEAT_EIGEN if eigen else KIND_HEAT)
 
 
 def fourier_64x64_q3q2_dg1(seed=0):
