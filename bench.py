@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=96.0, help="serve form: device-memory budget")
     ap.add_argument("--full-mix", action="store_true",
                     help="serve form: draw n and N from {16, 32, 64} (default {16, 32})")
-    ap.add_argument("--form", default="cycle", choices=["cycle", "precision", "batch", "serve", "smoother", "timestepping", "lid"],
+    ap.add_argument("--form", default="cycle", choices=["cycle", "precision", "batch", "serve", "smoother", "timestepping", "lid", "heat"],
                     help="cycle: the V(2,2) throughput line (default); precision: the FP64/FP32/BF16 "
                          "solves of the 128x128 Q2/Q1 DG(0) 128-slab workload")
     return ap.parse_args()
@@ -720,6 +720,78 @@ def run_lid_form(args):
     print(json.dumps(out), flush=True)
 
 
+def run_heat_form(args):
+    """Heat equation (Sec. 5, Tables heat:time3/4): u_t - lap u = 0 with natural
+    boundary conditions, u(0) = sin(pi x) + cos(2 pi y), t in [0, 0.02], N = 20;
+    Q_k x DG(q) for k = 1, 2, 3 and q = 0, 1 on the n x n mesh (--n, default 64);
+    FGMRES-WRMG to a residual of max(1e-6 ||b||, 1e-6) (the paper's criterion),
+    against the timestepping comparator with the same criterion per step.  Times
+    exclude context set-up and include the factorisation and eigen-estimates."""
+    import torch
+    from paper_2407_13997_gb300 import inputs, wrmg
+    torch.cuda.set_device(0)
+    n = args.n or 64
+    out = {"form": "heat", "n": n, "N": 20, "t": [0.0, 0.02], "runs": []}
+
+    def options_for(w):
+        ctx = wrmg.Context(w)
+        U0, F = ctx.vector(), ctx.vector()
+        ctx.residual(U0, F)           # F(0) = -b
+        bn = float(F.norm())
+        ctx.close()
+        eta = max(1e-6, 1e-6 / bn) if bn > 0 else 1e-6
+        return wrmg.default_options(newton_maxit=1, ew=0, eta_fixed=eta, newton_rtol=eta)
+
+    warm = inputs.heat(8, 1, 0, 4)
+    ctx = wrmg.Context(warm, options_for(warm))
+    U = ctx.vector()
+    ctx.solve(U, check=False)
+    ctx.close()
+    for k in (1, 2, 3):
+        for q in (0, 1):
+            w = inputs.heat(n, k, q, 20)
+            o = options_for(w)
+            ctx = wrmg.Context(w, o)
+            U = ctx.vector()
+            ctx.initial_guess(U)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = ctx.solve(U, check=False)
+            torch.cuda.synchronize()
+            t_wrmg = time.perf_counter() - t0
+            # one V(2,2) cycle with the operators ready
+            b = ctx.vector()
+            ctx.residual(ctx.vector(), b)
+            x = ctx.vector()
+            for _ in range(2):
+                ctx.vcycle(b, x)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(5):
+                ctx.vcycle(b, x)
+            e1.record()
+            torch.cuda.synchronize()
+            cyc = e0.elapsed_time(e1) / 5
+            ctx.close()
+            one = dataclasses.replace(w, N=1, T=w.T / 20)
+            c1 = wrmg.Context(one, options_for(one))
+            Ut = torch.zeros(w.ndofs(), dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sts = c1.solve_timestepping(Ut, 20, check=False)
+            torch.cuda.synchronize()
+            t_ts = time.perf_counter() - t0
+            c1.close()
+            out["runs"].append({"space": f"Q{k}", "time": f"DG({q})", "ndofs": w.ndofs(),
+                                "wrmg": {"status": st["status"], "seconds": t_wrmg, "fgmres": sum(st["gmres"]),
+                                         "vcycle_ms": cyc, "dof_per_s_per_cycle": w.ndofs() / cyc * 1e3},
+                                "timestepping": {"status": sts["status"], "seconds": t_ts,
+                                                 "fgmres_per_step": sum(sts["gmres_per_step"][:20]) / 20},
+                                "max_rel_diff": float((Ut - U).abs().max() / U.abs().max())})
+            del U, Ut, b, x
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -736,6 +808,8 @@ def main():
         run_timestepping_form(args)
     elif args.form == "lid":
         run_lid_form(args)
+    elif args.form == "heat":
+        run_heat_form(args)
     else:
         run_ours(args)
 
