@@ -95,6 +95,7 @@ struct wr_batch {
   }
   ~wr_batch() {
     drop_graph();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     for (void* p : allocs) cudaFree(p);
     if (hres) cudaFreeHost(hres);
     if (hcoef) cudaFreeHost(hcoef);
@@ -286,6 +287,7 @@ struct wr_batch {
   // and replays as one launch.
   std::vector<int> depth_variant = std::vector<int>(16, -1);  // tuned apply tile per depth
   cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap_stream = nullptr;
   int64_t table_ver = 0, graph_ver = -1, graph_kernels = 0;
   bool use_graphs = true;
 
@@ -303,12 +305,24 @@ struct wr_batch {
     if (graph_ver != table_ver) {
       drop_graph();
       vcycle(vb, vx);  // eager: one-time kernel attributes, and this call's result
+      // capture on a private stream (the caller's may be the legacy default stream,
+      // which cannot capture); the graph is launched on the caller's stream
+      if (!cap_stream) WR_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
       cudaGraph_t graph = nullptr;
       int64_t before = 0;
       wr_launch_count(&before);
-      WR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      vcycle(vb, vx);
-      const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+      WR_CUDA(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+      std::swap(s, cap_stream);
+      try {
+        vcycle(vb, vx);
+      } catch (...) {
+        std::swap(s, cap_stream);
+        cudaStreamEndCapture(cap_stream, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+      }
+      std::swap(s, cap_stream);
+      const cudaError_t ce = cudaStreamEndCapture(cap_stream, &graph);
       int64_t after = 0;
       wr_launch_count(&after);
       wr_uncount_launches(after - before);  // captured, not launched
