@@ -136,6 +136,13 @@ typedef struct {
     int autotune;           /* 1 (default): at the first linearisation, time the smoother-apply
                                tile variants on every level's stored factors and keep the
                                fastest (cached per shape for the process); 0: fixed tiles     */
+    int time_parallel;      /* parallel-in-time patch solve (Sec. 5's partitioned forward
+                               substitution): 1 (default) on the smoothed levels whose patches
+                               fill at most half of the GPU, 2 on every stored level (4
+                               chunks), 0 off.  Each level's slabs split into chunks swept
+                               at once from zero states, the chunk-boundary states chained
+                               by transfer matrices built at linearisation, and the chunks
+                               swept again from their incoming states                        */
 } wr_options;
 
 typedef struct {

@@ -593,6 +593,7 @@ struct ApplyItem {
   // kind 0 only: patch outputs of the slab before this item's first slab (the
   // jump state when the slabs are processed in windows), or null (zero state)
   const double* prev;
+  int fN, s0;  // the factor array's slabs per block and this item's first slab in it (g.N slabs from s0)
 };
 
 template <int K, int Q, typename FT, int NPGX, int V, class Items>
@@ -642,7 +643,7 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
           }
           const int64_t bi = q / NCH;  // block index within the item
           const int k = (int)(q - bi * NCH);
-          const int64_t off = ((int64_t)v.blk * v.g.N * NB + bi) * C::BLK + (int64_t)k * C::CC * MS;
+          const int64_t off = (((int64_t)v.blk * v.fN + v.s0) * NB + bi) * C::BLK + (int64_t)k * C::CC * MS;
           const int elems = (k == NCH - 1) ? C::BLK - k * C::CC * MS : C::CC * MS;
           const uint32_t bar = smem_u32(&sm.full[slot]);
           const uint32_t bytes = (uint32_t)(elems * sizeof(FT));
@@ -798,6 +799,11 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
   }
 }
 
+// The blocks of one level, optionally split into chunks of Lc slabs (time-parallel
+// solve): item it is chunk c_first + it / nblk of block it % nblk.  prev_mode 0: zero
+// jump state; 1: chunk c starts from the state after chunk c - 1 (prev[c - 1], one
+// [block][a][slot] slab of outputs per chunk; chunk 0 from zero); 2: every item
+// starts from the same state prev.
 template <typename FT>
 struct SingleItems {
   LevelGeom g;
@@ -806,7 +812,31 @@ struct SingleItems {
   const double* r;
   double* out;
   const double* prev;
-  __device__ ApplyItem<FT> operator()(int64_t it) const { return {g, bs, factors, r, out, (int)it, prev}; }
+  int nblk = 1, nchunk = 1, Lc = 0, c_first = 0, prev_mode = 0;
+  __device__ ApplyItem<FT> operator()(int64_t it) const {
+    ApplyItem<FT> v;
+    v.g = g;
+    v.bs = bs;
+    v.factors = factors;
+    v.fN = g.N;
+    if (nchunk == 1) {
+      v.r = r;
+      v.out = out;
+      v.blk = (int)it;
+      v.prev = prev;
+      v.s0 = 0;
+      return v;
+    }
+    const int c = c_first + (int)(it / nblk);
+    v.blk = (int)(it % nblk);
+    v.s0 = c * Lc;
+    v.g.N = min(Lc, g.N - v.s0);
+    const int64_t slab_out = (int64_t)g.npatch() * g.nt * bs.ms;
+    v.r = r + (int64_t)v.s0 * g.nt * g.S;
+    v.out = out + v.s0 * slab_out;
+    v.prev = prev_mode == 1 ? (c > 0 ? prev + (int64_t)(c - 1) * slab_out : nullptr) : prev_mode == 2 ? prev : nullptr;
+    return v;
+  }
 };
 
 template <typename FT>
@@ -825,6 +855,8 @@ struct BatchItems {
     v.factors = static_cast<const FT*>(sg.factors);
     v.blk = (int)(it - sg.u_patch);
     v.prev = nullptr;
+    v.fN = sg.g.N;
+    v.s0 = 0;
     if (coarse) {
       v.r = sg.xa;
       v.out = sg.ya;
@@ -838,9 +870,8 @@ struct BatchItems {
 
 template <int K, int Q, typename FT, int NPGX, int V>
 __global__ void __launch_bounds__(ApplyCfg<K, Q, FT, NPGX, V>::NTH, ApplyCfg<K, Q, FT, NPGX, V>::MINB)
-block_apply_kernel(LevelGeom g, FeTables T, BlockSet bs, const FT* __restrict__ factors, const double* __restrict__ r,
-                   double* __restrict__ out, int nblk, int* __restrict__ err, const double* __restrict__ prev) {
-  apply_persistent<K, Q, FT, NPGX, V>(T, SingleItems<FT>{g, bs, factors, r, out, prev}, nblk, err);
+block_apply_kernel(LevelGeom g, FeTables T, SingleItems<FT> items, int64_t nitems, int* __restrict__ err) {
+  apply_persistent<K, Q, FT, NPGX, V>(T, items, nitems, err);
 }
 
 template <int K, int Q, typename FT, int NPGX, int V>
@@ -937,15 +968,28 @@ int persistent_grid(Kern kern, int nth, size_t smem) {
 
 template <int K, int Q, typename FT, int NPGX = 2 * K - 1, int V = 0>
 void run_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs, const FT* factors, const double* r,
-               double* out, int* err, const double* prev, cudaStream_t s) {
+               double* out, int* err, const double* prev, cudaStream_t s, const ChunkPlan* cp = nullptr) {
   using C = ApplyCfg<K, Q, FT, NPGX, V>;
   const size_t smem = (size_t)C::NS * C::SLOT_ELEMS * sizeof(FT) + sizeof(ApplySmem<K, Q, FT, NPGX, V>);
   auto kern = block_apply_kernel<K, Q, FT, NPGX, V>;
   // persistent grid: CTAs resident on the whole GPU (computed once; thread-safe static)
   static const int grid_cap = persistent_grid(kern, C::NTH, smem);
   const int nblk = bs.kind == 0 ? g.npatch() : 1;
-  const int grid = nblk < grid_cap ? nblk : grid_cap;
-  kern<<<grid, C::NTH, smem, s>>>(g, T, bs, factors, r, out, nblk, err, prev);
+  SingleItems<FT> items{g, bs, factors, r, out, prev};
+  items.nblk = nblk;
+  items.prev_mode = prev ? 2 : 0;
+  int64_t nitems = nblk;
+  if (cp && cp->nchunk > 1) {
+    items.nchunk = cp->nchunk;
+    items.Lc = cp->Lc;
+    items.c_first = cp->c_first;
+    items.prev_mode = cp->prev_mode;
+    items.prev = cp->prev;
+    nitems = (int64_t)nblk * (cp->nchunk - cp->c_first);
+  }
+  const int grid = nitems < grid_cap ? (int)nitems : grid_cap;
+  if (nitems <= 0) return;
+  kern<<<grid, C::NTH, smem, s>>>(g, T, items, nitems, err);
   WR_LAUNCH_CHECK();
 }
 
@@ -965,11 +1009,12 @@ void run_bt_apply(const BatchSeg* segs, int nseg, int64_t items, const FeTables&
 
 template <int K, int Q, typename FT>
 void apply_variant(int variant, const LevelGeom& g, const FeTables& T, const BlockSet& bs, const FT* factors,
-                   const double* r, double* out, int* err, const double* prev, cudaStream_t s) {
+                   const double* r, double* out, int* err, const double* prev, cudaStream_t s,
+                   const ChunkPlan* cp) {
   if (variant < 0) variant = default_apply_variant(K);
-  if (variant == 0) run_apply<K, Q, FT, 2 * K - 1, 0>(g, T, bs, factors, r, out, err, prev, s);
-  else if (variant == 1) run_apply<K, Q, FT, 2 * K - 1, 1>(g, T, bs, factors, r, out, err, prev, s);
-  else run_apply<K, Q, FT, 2 * K - 1, 2>(g, T, bs, factors, r, out, err, prev, s);
+  if (variant == 0) run_apply<K, Q, FT, 2 * K - 1, 0>(g, T, bs, factors, r, out, err, prev, s, cp);
+  else if (variant == 1) run_apply<K, Q, FT, 2 * K - 1, 1>(g, T, bs, factors, r, out, err, prev, s, cp);
+  else run_apply<K, Q, FT, 2 * K - 1, 2>(g, T, bs, factors, r, out, err, prev, s, cp);
 }
 
 template <int K, int Q, typename FT>
@@ -1009,18 +1054,19 @@ void launch_block_factor(const LevelGeom& g, const FeTables& T, const PhysParams
 }
 
 void launch_block_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs, const void* factors, int precision,
-                        const double* r, double* out, int* err, cudaStream_t s, const double* prev, int variant) {
+                        const double* r, double* out, int* err, cudaStream_t s, const double* prev, int variant,
+                        const ChunkPlan* cp) {
 #define WR_A(K_, Q_)                                                                                   \
   if (g.k == K_ && g.q == Q_) {                                                                        \
     if (bs.kind == 1) {                                                                                \
       run_apply<K_, Q_, double>(g, T, bs, static_cast<const double*>(factors), r, out, err, prev, s);  \
     } else if (precision == WR_FP32) {                                                                 \
-      apply_variant<K_, Q_, float>(variant, g, T, bs, static_cast<const float*>(factors), r, out, err, prev, s); \
+      apply_variant<K_, Q_, float>(variant, g, T, bs, static_cast<const float*>(factors), r, out, err, prev, s, cp); \
     } else if (precision == WR_BF16) {                                                                 \
       apply_variant<K_, Q_, __nv_bfloat16>(variant, g, T, bs, static_cast<const __nv_bfloat16*>(factors), r, out, \
-                                           err, prev, s);                                              \
+                                           err, prev, s, cp);                                          \
     } else {                                                                                           \
-      apply_variant<K_, Q_, double>(variant, g, T, bs, static_cast<const double*>(factors), r, out, err, prev, s); \
+      apply_variant<K_, Q_, double>(variant, g, T, bs, static_cast<const double*>(factors), r, out, err, prev, s, cp); \
     }                                                                                                  \
   } else
   if (bs.kind == 1 && g.k == 1 && bs.npg == 4) {  // coarse 3x3 block of Q2/Q1 (FP64)
@@ -1107,5 +1153,81 @@ __global__ void bounded_wait_selftest_kernel(int* timed_out, unsigned long long*
 
 void launch_bounded_wait_selftest(int* timed_out, unsigned long long* ns, cudaStream_t s) {
   bounded_wait_selftest_kernel<<<1, 32, 0, s>>>(timed_out, ns);
+  WR_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------- time-parallel patch solve
+// The partitioned forward substitution of Sec. 5's cost model: each patch's slabs are
+// split into chunks; (A) every chunk is swept from a zero jump state, all chunks at
+// once; (B) the chunk-end states are chained through the chunks' transfer matrices
+// T_c (the chunk's response to a unit incoming velocity state, built at setup by
+// sweeps from unit states): carry_c = e_c + T_c carry_{c-1}; (C) every chunk but the
+// first is swept again from its incoming state.
+
+__global__ void cr_unit_kernel(int64_t n, int nt, int ms, int j, double* __restrict__ buf) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int s = int(idx % ms), a = int((idx / ms) % nt);
+  buf[idx] = (a == nt - 1 && s == j) ? 1.0 : 0.0;
+}
+
+__global__ void cr_gather_kernel(int npatch, int nchunk, int Lc, int N, int nt, int ms, int mv, int j,
+                                 const double* __restrict__ Yp, double* __restrict__ Tm) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)npatch * nchunk * mv) return;
+  const int i = int(idx % mv);
+  const int64_t bc = idx / mv;
+  const int c = int(bc % nchunk), blk = int(bc / nchunk);
+  const int e = min((c + 1) * Lc, N) - 1;
+  Tm[(((int64_t)blk * nchunk + c) * mv + i) * mv + j] = Yp[(((int64_t)e * npatch + blk) * nt + nt - 1) * ms + i];
+}
+
+// one CTA per patch, one thread per velocity slot of the state
+__global__ void cr_carry_kernel(int npatch, int nchunk, int Lc, int N, int nt, int ms, int mv,
+                                const double* __restrict__ Tm, const double* __restrict__ Yp,
+                                double* __restrict__ carry) {
+  extern __shared__ double st[];  // mv doubles
+  const int blk = blockIdx.x, i = threadIdx.x;
+  if (i < mv) st[i] = 0.0;
+  __syncthreads();
+  const int64_t slab_out = (int64_t)npatch * nt * ms;
+  for (int c = 0; c + 1 < nchunk; ++c) {
+    const int e = min((c + 1) * Lc, N) - 1;
+    double v = 0.0;
+    if (i < mv) {
+      v = Yp[(((int64_t)e * npatch + blk) * nt + nt - 1) * ms + i];
+      const double* T = Tm + ((int64_t)blk * nchunk + c) * mv * mv + (int64_t)i * mv;
+      for (int jj = 0; jj < mv; ++jj) v = fma(T[jj], st[jj], v);
+    }
+    __syncthreads();
+    if (i < mv) {
+      st[i] = v;
+      carry[c * slab_out + ((int64_t)blk * nt + nt - 1) * ms + i] = v;
+    }
+    __syncthreads();
+  }
+}
+
+void cr_unit_state(const LevelGeom& g, const BlockSet& bs, int j, double* buf, cudaStream_t s) {
+  const int64_t n = (int64_t)g.npatch() * g.nt * bs.ms;
+  cr_unit_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, g.nt, bs.ms, j, buf);
+  WR_LAUNCH_CHECK();
+}
+
+void cr_gather_column(const LevelGeom& g, const BlockSet& bs, int nchunk, int Lc, int j, const double* Yp,
+                      double* Tm, cudaStream_t s) {
+  const int mv = 2 * bs.nvg * bs.nvg;
+  const int64_t n = (int64_t)g.npatch() * nchunk * mv;
+  cr_gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g.npatch(), nchunk, Lc, g.N, g.nt, bs.ms, mv, j, Yp,
+                                                               Tm);
+  WR_LAUNCH_CHECK();
+}
+
+void cr_carry(const LevelGeom& g, const BlockSet& bs, int nchunk, int Lc, const double* Tm, const double* Yp,
+              double* carry, cudaStream_t s) {
+  const int mv = 2 * bs.nvg * bs.nvg;
+  const int nth = (mv + 31) / 32 * 32;
+  cr_carry_kernel<<<g.npatch(), nth, sizeof(double) * mv, s>>>(g.npatch(), nchunk, Lc, g.N, g.nt, bs.ms, mv, Tm, Yp,
+                                                                carry);
   WR_LAUNCH_CHECK();
 }

@@ -80,6 +80,10 @@ struct Level {
   bool recompute = false;   // factors recomputed in windows of `nw` slabs at every smoother apply
   int nw = 0;
   int variant = -1;         // apply tile chosen by the autotuner (-1: not yet, the default of k)
+  // time-parallel patch solve: nchunk chunks of Lc slabs, chunk transfer matrices Tm,
+  // chunk-boundary states carry (nchunk = 1: the plain sweep over all slabs)
+  int nchunk = 1, Lc = 0;
+  double *Tm = nullptr, *carry = nullptr;
   double *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *z = nullptr, *t = nullptr;
   double lam = 0.0;
   bool lam_set = false;
@@ -255,6 +259,51 @@ struct wr_ctx {
     launch_scatter(g, lv.bs, Yp, y, s);
   }
 
+  // (A) every chunk from a zero state, (B) chain the chunk-end states, (C) every chunk
+  // but the first again from its incoming state; then the scatter
+  void patch_apply_time_parallel(int l, const double* r, double* y) {
+    Level& lv = L[l];
+    ChunkPlan a;
+    a.nchunk = lv.nchunk;
+    a.Lc = lv.Lc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (prof) {
+      e0 = next_event();
+      e1 = next_event();
+      WR_CUDA(cudaEventRecord(e0, s));
+    }
+    launch_block_apply(lv.g, tab, lv.bs, lv.factors, opt.precision, r, Yp, derr, s, nullptr, lv.variant, &a);
+    cr_carry(lv.g, lv.bs, lv.nchunk, lv.Lc, lv.Tm, Yp, lv.carry, s);
+    ChunkPlan c = a;
+    c.c_first = 1;
+    c.prev_mode = 1;
+    c.prev = lv.carry;
+    launch_block_apply(lv.g, tab, lv.bs, lv.factors, opt.precision, r, Yp, derr, s, nullptr, lv.variant, &c);
+    if (prof) {
+      WR_CUDA(cudaEventRecord(e1, s));
+      prof_ev[l].push_back({e0, e1});
+    }
+    launch_scatter(lv.g, lv.bs, Yp, y, s);
+  }
+
+  // Chunk transfer matrices: column j of every T_c is the chunk-end state of a sweep
+  // with a zero right-hand side from the unit incoming state j.
+  void build_transfer_matrices(int l) {
+    Level& lv = L[l];
+    const int mv = 2 * lv.bs.nvg * lv.bs.nvg;
+    vec_zero(lv.g.ndofs, lv.x, s);
+    ChunkPlan u;
+    u.nchunk = lv.nchunk;
+    u.Lc = lv.Lc;
+    u.prev_mode = 2;
+    u.prev = lv.carry;  // the unit state lives in the first carry slab during set-up
+    for (int j = 0; j < mv; ++j) {
+      cr_unit_state(lv.g, lv.bs, j, lv.carry, s);
+      launch_block_apply(lv.g, tab, lv.bs, lv.factors, opt.precision, lv.x, Yp, derr, s, nullptr, lv.variant, &u);
+      cr_gather_column(lv.g, lv.bs, lv.nchunk, lv.Lc, j, Yp, lv.Tm, s);
+    }
+  }
+
   void patch_apply(int l, const double* r, double* y) {
     if (!linearised) throw WrError(WR_ERR_STATE, "wr_linearise must be called first");
     if (heat) {
@@ -273,6 +322,10 @@ struct wr_ctx {
     }
     if (L[l].recompute) {
       patch_apply_windows(l, r, y);
+      return;
+    }
+    if (L[l].nchunk > 1) {
+      patch_apply_time_parallel(l, r, y);
       return;
     }
     if (prof) {
@@ -380,7 +433,7 @@ struct wr_ctx {
     linearised = true;
     if (opt.autotune)
       for (int l = 1; l <= T_; ++l)
-        if (!L[l].recompute && L[l].variant < 0) {
+        if (!L[l].recompute && L[l].variant < 0 && L[l].nchunk == 1) {
           Level& lv = L[l];
           vec_zero(lv.g.ndofs, lv.x, s);
           const TuneKey key{0, k, q, opt.precision, (int64_t)lv.g.npatch(), lv.g.N};
@@ -388,6 +441,8 @@ struct wr_ctx {
             launch_block_apply(lv.g, tab, lv.bs, lv.factors, opt.precision, lv.x, Yp, derr, s, nullptr, v);
           });
         }
+    for (int l = 1; l <= T_; ++l)
+      if (L[l].nchunk > 1) build_transfer_matrices(l);
     if (eig)
       for (int l = 1; l <= T_; ++l) eigen_estimate(l);
   }
@@ -645,6 +700,7 @@ void wr_default_options(wr_options* o) {
   o->scatter_weight = WR_WEIGHT_ONE;
   o->store_factors = WR_STORE;
   o->autotune = 1;
+  o->time_parallel = 1;
   o->recompute_slabs = 0;
   o->memory_budget_mb = 0;
 }
@@ -842,6 +898,33 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
         max_yp = std::max(max_yp, (size_t)lv.g.npatch() * p->n_slabs * nt * ms);
       }
       c->L.push_back(lv);
+    }
+    // time-parallel patch solve on the smoothed levels with too few patches to fill the
+    // GPU: about one chunk per free CTA slot, at least 2 and at most N / 2 chunks
+    int cap = 152 * (p->k == 1 ? 3 : 1);
+    if (!c->dry) {
+      int dev = 0, sms = 0;
+      WR_CUDA(cudaGetDevice(&dev));
+      WR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      cap = sms * (p->k == 1 ? 3 : 1);
+    }
+    for (size_t l = 1; l < c->L.size(); ++l) {
+      Level& lv = c->L[l];
+      if (lv.recompute || c->opt.time_parallel == 0 || p->n_slabs < 4) continue;
+      const int np_ = lv.g.npatch();
+      int C = 1;
+      if (c->opt.time_parallel == 2) C = std::min(4, p->n_slabs / 2);
+      else if (2 * np_ <= cap) C = std::min(cap / np_, p->n_slabs / 2);
+      if (C < 2) continue;
+      lv.Lc = (p->n_slabs + C - 1) / C;
+      lv.nchunk = (p->n_slabs + lv.Lc - 1) / lv.Lc;
+      if (lv.nchunk < 2) {
+        lv.nchunk = 1;
+        continue;
+      }
+      const int mv = 2 * lv.bs.nvg * lv.bs.nvg;
+      lv.Tm = c->alloc<double>((size_t)np_ * lv.nchunk * mv * mv);
+      lv.carry = c->alloc<double>((size_t)lv.nchunk * np_ * nt * ms);
     }
     c->cbs.kind = 1;
     c->cbs.nvg = c->L[0].g.nv - 2;

@@ -198,11 +198,29 @@ void launch_block_factor(const LevelGeom& g, const FeTables& T, const PhysParams
 // block (kind 1) writes the solution.  A window of slabs is g with N = window
 // length, r and out offset to the window's first slab, factors of the window,
 // and prev = the patch outputs of the slab before it (null: zero jump state).
+// Time-parallel split of a patch-block apply (patch blocks only): the items are the
+// chunks c_first .. nchunk - 1 of Lc slabs of every block; prev_mode 0: zero jump
+// state, 1: chunk c starts from prev + (c - 1) * (one slab of patch outputs), 2: every
+// chunk starts from the state prev.
+struct ChunkPlan {
+  int nchunk = 1, Lc = 0, c_first = 0, prev_mode = 0;
+  const double* prev = nullptr;
+};
 // variant: the apply tile (0 .. 2, -1 = the default of k; patch blocks only), chosen
 // per level by the autotuner
 void launch_block_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs,
                         const void* factors, int precision, const double* r, double* out,
-                        int* err, cudaStream_t s, const double* prev = nullptr, int variant = -1);
+                        int* err, cudaStream_t s, const double* prev = nullptr, int variant = -1,
+                        const ChunkPlan* cp = nullptr);
+// Time-parallel patch solve helpers (patch_kernels.cu); mv = 2 nvg^2 velocity slots.
+// buf = the state with 1 at velocity slot j of the last temporal DoF of every patch
+void cr_unit_state(const LevelGeom& g, const BlockSet& bs, int j, double* buf, cudaStream_t s);
+// Tm[(blk, c)][:, j] = the chunk-end velocity state of every chunk in the patch outputs Yp
+void cr_gather_column(const LevelGeom& g, const BlockSet& bs, int nchunk, int Lc, int j, const double* Yp,
+                      double* Tm, cudaStream_t s);
+// carry[c] = e_c + T_c carry[c - 1] for c = 0 .. nchunk - 2 (e_c: chunk-end states in Yp)
+void cr_carry(const LevelGeom& g, const BlockSet& bs, int nchunk, int Lc, const double* Tm, const double* Yp,
+              double* carry, cudaStream_t s);
 constexpr int kApplyTileVariants = 3;
 void launch_scatter(const LevelGeom& g, const BlockSet& bs, const double* Yp, double* y,
                     cudaStream_t s);

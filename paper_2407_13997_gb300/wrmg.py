@@ -46,7 +46,8 @@ class Options(ctypes.Structure):
                 ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
                 ("patch_assembly", ctypes.c_int), ("scatter_weight", ctypes.c_int),
                 ("store_factors", ctypes.c_int), ("recompute_slabs", ctypes.c_int),
-                ("memory_budget_mb", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("memory_budget_mb", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("time_parallel", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -221,9 +221,9 @@ def test_recomputed_factors_give_the_stored_result_bitwise(w, window, prec):
     included) are the stored factors, so the smoother, the eigen-estimates and the
     V-cycle are bitwise those of the stored form."""
     # fixed apply tiles on both sides (tuned tiles may sum in another order)
-    st = Setup(w, options=wrmg.default_options(precision=prec, autotune=0))
+    st = Setup(w, options=wrmg.default_options(precision=prec, autotune=0, time_parallel=0))
     rc = wrmg.Context(w, wrmg.default_options(precision=prec, store_factors=wrmg.WR_RECOMPUTE,
-                                              recompute_slabs=window, autotune=0))
+                                              recompute_slabs=window, autotune=0, time_parallel=0))
     W = cuda(st.W[-1])
     st.ctx.linearise(W, eig=True)
     rc.linearise(W, eig=True)
@@ -244,3 +244,31 @@ def test_recomputed_factors_give_the_stored_result_bitwise(w, window, prec):
     assert rc.device_bytes() < st.ctx.device_bytes() or w.N <= window
     st.ctx.close()
     rc.close()
+
+
+@pytest.mark.parametrize("w", [CASES[0], CASES[1], CASES[2], CASES[4]], ids=[IDS[0], IDS[1], IDS[2], IDS[4]])
+def test_time_parallel_patch_solve_matches_oracle(w):
+    """The partitioned (parallel-in-time) forward substitution over slabs on every
+    level: the smoother and the V-cycle match the oracle to 1e-10, and the sweep over
+    all slabs to 1e-12."""
+    s = Setup(w, options=wrmg.default_options(time_parallel=2))
+    seq = wrmg.Context(w, wrmg.default_options(time_parallel=0))
+    W = cuda(s.W[-1])
+    s.ctx.linearise(W, eig=True)
+    seq.linearise(W, eig=True)
+    for l in range(1, len(s.discs)):
+        d = s.discs[l]
+        sm = PatchSmoother(d, d.jacobian(s.W[l]))
+        r = s.rng.standard_normal(d.ndofs)
+        y, y2 = s.ctx.vector(l), seq.vector(l)
+        s.ctx.patch_apply(l, cuda(r), y)
+        seq.patch_apply(l, cuda(r), y2)
+        assert rel(y.cpu().numpy(), sm.apply(r)) < 1e-10, l
+        assert rel(y.cpu().numpy(), y2.cpu().numpy()) < 1e-12, l
+    b = s.rng.standard_normal(s.discs[-1].ndofs)
+    x, x2 = s.ctx.vector(), seq.vector()
+    s.ctx.vcycle(cuda(b), x)
+    seq.vcycle(cuda(b), x2)
+    assert rel(x.cpu().numpy(), x2.cpu().numpy()) < 1e-10
+    s.ctx.close()
+    seq.close()
