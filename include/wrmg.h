@@ -136,6 +136,9 @@ typedef struct {
     int autotune;           /* 1 (default): at the first linearisation, time the smoother-apply
                                tile variants on every level's stored factors and keep the
                                fastest (cached per shape for the process); 0: fixed tiles     */
+    int apply_tile;         /* -1 (default): the autotuner's (or the fixed) choice; 0 .. 3 force
+                               a smoother-apply tile on every level (0-2: one CTA per patch,
+                               1, 2 or 3 CTAs per SM; 3: one warp per patch)                 */
     int time_parallel;      /* parallel-in-time patch solve (Sec. 5's partitioned forward
                                substitution): 1 (default) on the smoothed levels whose patches
                                fill at most half of the GPU, 2 on every stored level (4

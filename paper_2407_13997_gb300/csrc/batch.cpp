@@ -678,6 +678,7 @@ int wr_batch_create(wr_batch** out, int n, const wr_problem* ps, const wr_option
     if (o) b->opt = *o;
     else wr_default_options(&b->opt);
     bneed(b->opt.precision >= WR_FP64 && b->opt.precision <= WR_BF16, "bad precision");
+    bneed(b->opt.apply_tile >= -1 && b->opt.apply_tile < kApplyTileVariants, "bad apply_tile");
     bneed(b->opt.patch_assembly == WR_PATCH_SUBMATRIX || b->opt.patch_assembly == WR_PATCH_LOCAL,
           "bad patch_assembly");
     bneed(b->opt.scatter_weight == WR_WEIGHT_ONE || b->opt.scatter_weight == WR_WEIGHT_MULTIPLICITY,
@@ -719,7 +720,7 @@ int wr_batch_create(wr_batch** out, int n, const wr_problem* ps, const wr_option
       D = std::max(D, L + 1);
     }
     b->D = D;
-    b->depth_variant.assign(D, -1);
+    b->depth_variant.assign(D, b->opt.apply_tile);
     b->off.assign(D, std::vector<int64_t>(n, -1));
     b->off_ye.assign(D, std::vector<int64_t>(n, -1));
     b->off_yp.assign(D, std::vector<int64_t>(n, -1));

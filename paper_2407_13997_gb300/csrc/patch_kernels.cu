@@ -472,7 +472,7 @@ __device__ __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162floa
 //   Q3/Q2 (K = 2): G = 4 with one 480-thread CTA per SM (176 KB), or G = 2 with
 //                  two or three 256-thread CTAs per SM (96 / 64 KB).
 // The coarse 3x3 block (NPGX != 2K - 1) always takes variant 0.
-constexpr int kApplyVariants = 3;
+constexpr int kApplyVariants = 4;  // tiles 0-2: CTA per block; tile 3: warp per block
 // without tuning: three 64 KB CTAs per SM for Q2/Q1, one 480-thread CTA for Q3/Q2
 inline int default_apply_variant(int k) { return k == 1 ? 2 : 0; }
 template <int K, int V>
@@ -868,6 +868,150 @@ struct BatchItems {
   }
 };
 
+// ---------------------------------------------------------------- warp-per-patch apply (tile 3)
+// Each warp owns one item at a time: it streams the item's factor blocks straight
+// from global memory (column-major blocks: for a column, the warp's lanes read
+// consecutive rows, R rows per lane) and needs no block-wide barrier, only warp
+// synchronisation between the phases of a slab.  The arithmetic per row is the
+// CTA tile's with one group (G = 1): one running sum per row over all columns.
+constexpr int kWarpTileWarps = 8;
+
+template <int K, int Q, typename FT>
+struct WarpSmem {
+  using pd = PD<K>;
+  using CT = typename ComputeType<FT>::type;
+  static constexpr int MS = pd::MS, NT = Q + 1;
+  CT rhs[NT][MS];
+  CT y[NT][MS];
+  CT yp[2][pd::NVG2];
+  CT tm[2][pd::NVG2];
+  CT mx[pd::NVG][pd::NVG];
+  CT my[pd::NVG][pd::NVG];
+  int sidx[MS];
+};
+
+template <int K, int Q, typename FT, class Items>
+__device__ __forceinline__ void warp_apply(const FeTables& T, const Items& items, int64_t nitems) {
+  using pd = PD<K>;
+  using CT = typename ComputeType<FT>::type;
+  using C = ApplyCfg<K, Q, FT>;
+  constexpr int MS = pd::MS, NT = Q + 1, NB = NT * NT, NVG = pd::NVG, R = (MS + 31) / 32;
+  extern __shared__ __align__(16) unsigned char wsm_raw[];  // kWarpTileWarps WarpSmem (dynamic: > 48 KB for k = 2)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  WarpSmem<K, Q, FT>& sm = reinterpret_cast<WarpSmem<K, Q, FT>*>(wsm_raw)[w];
+  const int64_t nwarps = (int64_t)gridDim.x * kWarpTileWarps;
+  for (int64_t it = (int64_t)blockIdx.x * kWarpTileWarps + w; it < nitems; it += nwarps) {
+    const ApplyItem<FT> v = items(it);
+    const LevelGeom& g = v.g;
+    const BlockSet& bs = v.bs;
+    const int blk = v.blk, nvg = bs.nvg, nv2g = nvg * nvg;
+    int vx0, vy0, px0, py0;
+    block_origin(g, bs, blk, vx0, vy0, px0, py0);
+    for (int s = lane; s < MS; s += 32) sm.sidx[s] = decode_slot(g, bs, blk, s).sp;
+    int cx0, cx1, cy0, cy1;
+    own_cells(g, bs, vx0, cx0, cx1);
+    own_cells(g, bs, vy0, cy0, cy1);
+    for (int e = lane; e < NVG * NVG; e += 32) {
+      const int i = e / NVG, j = e % NVG;
+      const int xi = vx0 + i, xj = vx0 + j, yi = vy0 + i, yj = vy0 + j;
+      const bool okx = i < nvg && j < nvg && xi >= 1 && xi <= g.nv - 2 && xj >= 1 && xj <= g.nv - 2;
+      const bool oky = i < nvg && j < nvg && yi >= 1 && yi <= g.nv - 2 && yj >= 1 && yj <= g.nv - 2;
+      sm.mx[i][j] = okx ? (CT)(g.h * vv1<K>(T.m1, g.n, xi, xj, cx0, cx1)) : (CT)0;
+      sm.my[i][j] = oky ? (CT)(g.h * vv1<K>(T.m1, g.n, yi, yj, cy0, cy1)) : (CT)0;
+    }
+    const bool carry = v.prev != nullptr;
+    for (int e = lane; e < 2 * pd::NVG2; e += 32) {
+      const int c = e / pd::NVG2, tt = e % pd::NVG2;
+      sm.yp[c][tt] = (carry && tt < nv2g) ? (CT)v.prev[((int64_t)blk * NT + NT - 1) * MS + c * nv2g + tt] : (CT)0;
+    }
+    __syncwarp();
+    for (int e = lane; e < NT * MS; e += 32) {
+      const int a = e / MS, s = e % MS, sp = sm.sidx[s];
+      sm.rhs[a][s] = sp >= 0 ? (CT)v.r[(int64_t)a * g.S + sp] : (CT)0;
+    }
+    for (int slab = 0; slab < g.N; ++slab) {
+      __syncwarp();
+      if (slab > 0 || carry) {
+        for (int e = lane; e < 2 * nv2g; e += 32) {
+          const int c = e / nv2g, tt = e % nv2g, iy = tt / nvg, jx = tt % nvg;
+          CT acc = 0;
+          for (int jy = 0; jy < nvg; ++jy) acc = fma(sm.my[iy][jy], sm.yp[c][jy * nvg + jx], acc);
+          sm.tm[c][tt] = acc;
+        }
+        __syncwarp();
+        for (int e = lane; e < 2 * nv2g; e += 32) {
+          const int c = e / nv2g, tt = e % nv2g, iy = tt / nvg, ix = tt % nvg;
+          CT acc = 0;
+          for (int jx = 0; jx < nvg; ++jx) acc = fma(sm.mx[ix][jx], sm.tm[c][iy * nvg + jx], acc);
+          const int s = c * nv2g + tt;
+          if (sm.sidx[s] >= 0)
+            for (int a = 0; a < NT; ++a) sm.rhs[a][s] += (CT)T.tau0[a] * acc;
+        }
+        __syncwarp();
+      }
+      // register prefetch of the next slab's right-hand side
+      CT pf[(NT * MS + 31) / 32];
+#pragma unroll
+      for (int u = 0; u < (NT * MS + 31) / 32; ++u) {
+        const int e = lane + 32 * u;
+        pf[u] = 0;
+        if (e < NT * MS && slab + 1 < g.N) {
+          const int sp = sm.sidx[e % MS];
+          if (sp >= 0) pf[u] = (CT)v.r[((int64_t)(slab + 1) * NT + e / MS) * g.S + sp];
+        }
+      }
+      // Q = 0: y0 = A^{-1} r0;  Q = 1: z0 = A00^{-1} r0, s1 = r1 - A10 z0, y1 = S^{-1} s1, y0 = z0 - X y1
+      for (int b = 0; b < NB; ++b) {
+        const CT* xv = (b == 0) ? sm.rhs[0] : (b == 1) ? sm.y[0] : (b == 2) ? sm.rhs[NT - 1] : sm.y[NT - 1];
+        const FT* A = v.factors + (((int64_t)blk * v.fN + v.s0 + slab) * NB + b) * C::BLK;
+        CT acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = 0;
+#pragma unroll 4
+        for (int c = 0; c < MS; ++c) {
+          const CT xc = xv[c];
+          const FT* col = A + (int64_t)c * MS;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int row = lane + 32 * r;
+            if (row < MS) acc[r] = fma(widen(__ldg(col + row)), xc, acc[r]);
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int row = lane + 32 * r;
+          if (row >= MS) continue;
+          if (b == 0) sm.y[0][row] = acc[r];
+          else if (b == 1) sm.rhs[NT - 1][row] -= acc[r];
+          else if (b == 2) sm.y[NT - 1][row] = acc[r];
+          else sm.y[0][row] -= acc[r];
+        }
+        __syncwarp();
+      }
+      for (int e = lane; e < NT * MS; e += 32) {
+        const int a = e / MS, s = e % MS;
+        if (bs.kind == 0) {
+          v.out[(((int64_t)slab * g.npatch() + blk) * NT + a) * MS + s] = (double)sm.y[a][s];
+        } else if (sm.sidx[s] >= 0) {
+          v.out[((int64_t)slab * NT + a) * g.S + sm.sidx[s]] = (double)sm.y[a][s];
+        }
+      }
+      for (int e = lane; e < 2 * nv2g; e += 32) {
+        const int c = e / nv2g, tt = e % nv2g;
+        sm.yp[c][tt] = sm.y[NT - 1][c * nv2g + tt];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < (NT * MS + 31) / 32; ++u) {
+        const int e = lane + 32 * u;
+        if (e < NT * MS) sm.rhs[e / MS][e % MS] = pf[u];
+      }
+    }
+    __syncwarp();
+  }
+}
+
 template <int K, int Q, typename FT, int NPGX, int V>
 __global__ void __launch_bounds__(ApplyCfg<K, Q, FT, NPGX, V>::NTH, ApplyCfg<K, Q, FT, NPGX, V>::MINB)
 block_apply_kernel(LevelGeom g, FeTables T, SingleItems<FT> items, int64_t nitems, int* __restrict__ err) {
@@ -879,6 +1023,19 @@ __global__ void __launch_bounds__(ApplyCfg<K, Q, FT, NPGX, V>::NTH, ApplyCfg<K, 
 bt_block_apply_kernel(const BatchSeg* __restrict__ segs, int nseg, int64_t nitems, FeTables T,
                       const double* __restrict__ r, double* __restrict__ yp, int coarse, int* __restrict__ err) {
   apply_persistent<K, Q, FT, NPGX, V>(T, BatchItems<FT>{segs, nseg, r, yp, coarse != 0}, nitems, err);
+}
+
+template <int K, int Q, typename FT>
+__global__ void __launch_bounds__(32 * kWarpTileWarps)
+warp_apply_kernel(FeTables T, SingleItems<FT> items, int64_t nitems) {
+  warp_apply<K, Q, FT>(T, items, nitems);
+}
+
+template <int K, int Q, typename FT>
+__global__ void __launch_bounds__(32 * kWarpTileWarps)
+bt_warp_apply_kernel(const BatchSeg* __restrict__ segs, int nseg, int64_t nitems, FeTables T,
+                     const double* __restrict__ r, double* __restrict__ yp) {
+  warp_apply<K, Q, FT>(T, BatchItems<FT>{segs, nseg, r, yp, false}, nitems);
 }
 
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
@@ -1008,11 +1165,51 @@ void run_bt_apply(const BatchSeg* segs, int nseg, int64_t items, const FeTables&
 
 
 template <int K, int Q, typename FT>
+void run_warp_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs, const FT* factors, const double* r,
+                    double* out, const double* prev, cudaStream_t s, const ChunkPlan* cp) {
+  auto kern = warp_apply_kernel<K, Q, FT>;
+  const size_t smem = sizeof(WarpSmem<K, Q, FT>) * kWarpTileWarps;
+  static const int grid_cap = persistent_grid(kern, 32 * kWarpTileWarps, smem);
+  const int nblk = g.npatch();
+  SingleItems<FT> items{g, bs, factors, r, out, prev};
+  items.nblk = nblk;
+  items.prev_mode = prev ? 2 : 0;
+  int64_t nitems = nblk;
+  if (cp && cp->nchunk > 1) {
+    items.nchunk = cp->nchunk;
+    items.Lc = cp->Lc;
+    items.c_first = cp->c_first;
+    items.prev_mode = cp->prev_mode;
+    items.prev = cp->prev;
+    nitems = (int64_t)nblk * (cp->nchunk - cp->c_first);
+  }
+  if (nitems <= 0) return;
+  const int64_t want = (nitems + kWarpTileWarps - 1) / kWarpTileWarps;
+  const int grid = want < grid_cap ? (int)want : grid_cap;
+  kern<<<grid, 32 * kWarpTileWarps, smem, s>>>(T, items, nitems);
+  WR_LAUNCH_CHECK();
+}
+
+template <int K, int Q, typename FT>
+void run_bt_warp_apply(const BatchSeg* segs, int nseg, int64_t items, const FeTables& T, const double* r, double* yp,
+                       cudaStream_t s) {
+  auto kern = bt_warp_apply_kernel<K, Q, FT>;
+  const size_t smem = sizeof(WarpSmem<K, Q, FT>) * kWarpTileWarps;
+  static const int grid_cap = persistent_grid(kern, 32 * kWarpTileWarps, smem);
+  if (items <= 0) return;
+  const int64_t want = (items + kWarpTileWarps - 1) / kWarpTileWarps;
+  const int grid = want < grid_cap ? (int)want : grid_cap;
+  kern<<<grid, 32 * kWarpTileWarps, smem, s>>>(segs, nseg, items, T, r, yp);
+  WR_LAUNCH_CHECK();
+}
+
+template <int K, int Q, typename FT>
 void apply_variant(int variant, const LevelGeom& g, const FeTables& T, const BlockSet& bs, const FT* factors,
                    const double* r, double* out, int* err, const double* prev, cudaStream_t s,
                    const ChunkPlan* cp) {
   if (variant < 0) variant = default_apply_variant(K);
-  if (variant == 0) run_apply<K, Q, FT, 2 * K - 1, 0>(g, T, bs, factors, r, out, err, prev, s, cp);
+  if (variant == 3) run_warp_apply<K, Q, FT>(g, T, bs, factors, r, out, prev, s, cp);
+  else if (variant == 0) run_apply<K, Q, FT, 2 * K - 1, 0>(g, T, bs, factors, r, out, err, prev, s, cp);
   else if (variant == 1) run_apply<K, Q, FT, 2 * K - 1, 1>(g, T, bs, factors, r, out, err, prev, s, cp);
   else run_apply<K, Q, FT, 2 * K - 1, 2>(g, T, bs, factors, r, out, err, prev, s, cp);
 }
@@ -1021,7 +1218,8 @@ template <int K, int Q, typename FT>
 void bt_apply_variant(int variant, const BatchSeg* segs, int nseg, int64_t items, const FeTables& T,
                       const double* r, double* yp, int* err, cudaStream_t s) {
   if (variant < 0) variant = default_apply_variant(K);
-  if (variant == 0) run_bt_apply<K, Q, FT, 2 * K - 1, 0>(segs, nseg, items, T, r, yp, false, err, s);
+  if (variant == 3) run_bt_warp_apply<K, Q, FT>(segs, nseg, items, T, r, yp, s);
+  else if (variant == 0) run_bt_apply<K, Q, FT, 2 * K - 1, 0>(segs, nseg, items, T, r, yp, false, err, s);
   else if (variant == 1) run_bt_apply<K, Q, FT, 2 * K - 1, 1>(segs, nseg, items, T, r, yp, false, err, s);
   else run_bt_apply<K, Q, FT, 2 * K - 1, 2>(segs, nseg, items, T, r, yp, false, err, s);
 }

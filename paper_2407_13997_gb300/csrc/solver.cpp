@@ -700,6 +700,7 @@ void wr_default_options(wr_options* o) {
   o->scatter_weight = WR_WEIGHT_ONE;
   o->store_factors = WR_STORE;
   o->autotune = 1;
+  o->apply_tile = -1;
   o->time_parallel = 1;
   o->recompute_slabs = 0;
   o->memory_budget_mb = 0;
@@ -816,6 +817,7 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
              c->opt.store_factors == WR_STORE_AUTO,
          "store_factors must be WR_STORE, WR_RECOMPUTE or WR_STORE_AUTO");
     need(c->opt.recompute_slabs >= 0 && c->opt.memory_budget_mb >= 0, "bad recompute_slabs / memory_budget_mb");
+    need(c->opt.apply_tile >= -1 && c->opt.apply_tile < kApplyTileVariants, "apply_tile must be -1 .. 3");
     c->s = static_cast<cudaStream_t>(stream);
     c->k = p->k; c->q = p->q; c->N = p->n_slabs; c->T = p->T;
     c->ph.kind = p->kind; c->ph.steady = p->steady; c->ph.nu = p->nu; c->ph.conv = p->conv; c->ph.T = p->T;
@@ -899,6 +901,8 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
       }
       c->L.push_back(lv);
     }
+    if (c->opt.apply_tile >= 0)
+      for (auto& lv : c->L) lv.variant = c->opt.apply_tile;
     // time-parallel patch solve on the smoothed levels with too few patches to fill the
     // GPU: about one chunk per free CTA slot, at least 2 and at most N / 2 chunks
     int cap = 152 * (p->k == 1 ? 3 : 1);

@@ -206,7 +206,7 @@ struct ChunkPlan {
   int nchunk = 1, Lc = 0, c_first = 0, prev_mode = 0;
   const double* prev = nullptr;
 };
-// variant: the apply tile (0 .. 2, -1 = the default of k; patch blocks only), chosen
+// variant: the apply tile (0 .. 3, -1 = the default of k; patch blocks only), chosen
 // per level by the autotuner
 void launch_block_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs,
                         const void* factors, int precision, const double* r, double* out,
@@ -221,7 +221,7 @@ void cr_gather_column(const LevelGeom& g, const BlockSet& bs, int nchunk, int Lc
 // carry[c] = e_c + T_c carry[c - 1] for c = 0 .. nchunk - 2 (e_c: chunk-end states in Yp)
 void cr_carry(const LevelGeom& g, const BlockSet& bs, int nchunk, int Lc, const double* Tm, const double* Yp,
               double* carry, cudaStream_t s);
-constexpr int kApplyTileVariants = 3;
+constexpr int kApplyTileVariants = 4;
 void launch_scatter(const LevelGeom& g, const BlockSet& bs, const double* Yp, double* y,
                     cudaStream_t s);
 void launch_restrict(const LevelGeom& gf, const LevelGeom& gc, const FeTables& T,

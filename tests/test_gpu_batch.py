@@ -126,3 +126,23 @@ def test_graph_replay_equals_eager_cycles_bitwise():
     assert ng == ne > 10
     assert gg == ge
     assert all(torch.equal(a, b) for a, b in zip(Ug, Ue))
+
+
+@pytest.mark.parametrize("tile", [2, 3])
+def test_batched_apply_tiles_match_single_instances(tile):
+    ws = members_q2q1()
+    rng = np.random.default_rng(8)
+    Ws = [torch.from_numpy(inputs.forcing_shaped_iterate(w)).cuda() for w in ws]
+    batch = wrmg.Batch(ws, wrmg.default_options(apply_tile=tile))
+    batch.linearise(Ws)
+    bs = [torch.from_numpy(rng.standard_normal(w.ndofs())).cuda() for w in ws]
+    xs = batch.vectors()
+    batch.vcycle(bs, xs)
+    for m, w in enumerate(ws):
+        ctx = wrmg.Context(w, wrmg.default_options(apply_tile=tile, time_parallel=0))
+        ctx.linearise(Ws[m], eig=True)
+        x = ctx.vector()
+        ctx.vcycle(bs[m].clone(), x)
+        assert rel(xs[m], x) < 1e-10, m
+        ctx.close()
+    batch.close()
