@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--rates", default="10,100,500", help="serve form: Poisson arrival rates (requests/s)")
     ap.add_argument("--inflight", type=int, default=8, help="serve form: solves in flight at most")
     ap.add_argument("--budget-gb", type=float, default=96.0, help="serve form: device-memory budget")
+    ap.add_argument("--time-parallel", type=int, default=None,
+                    help="smoother form: also time the parallel-in-time patch solve (1 = auto, 2 = forced)")
     ap.add_argument("--full-mix", action="store_true",
                     help="serve form: draw n and N from {16, 32, 64} (default {16, 32})")
     ap.add_argument("--form", default="cycle", choices=["cycle", "precision", "batch", "serve", "smoother", "timestepping", "lid", "heat"],
@@ -626,7 +628,24 @@ def run_smoother_form(args):
     alg_bytes, alg_flops = smoother_algorithmic(ctx, w, {wrmg.WR_FP64: 8, wrmg.WR_FP32: 4, wrmg.WR_BF16: 2}[prec])
     avg_s = sm_ms / max(sm_n, 1) * 1e-3
     hbm_peak, hbm_src = measured_peaks()
+    tp = None
+    if args.time_parallel:
+        # the same apply with the slabs split into chunks solved in parallel (all phases timed)
+        ctx2 = wrmg.Context(w, wrmg.default_options(precision=prec, time_parallel=args.time_parallel))
+        ctx2.linearise(W, eig=False)
+        for _ in range(args.warmup):
+            ctx2.patch_apply(L, r, y)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            ctx2.patch_apply(L, r, y)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        tp = {"apply_with_scatter_ms": f0.elapsed_time(f1) / args.steps, "mode": args.time_parallel}
+        ctx2.close()
     out = {"form": "smoother", "workload": w.name, "precision": args.precision, "launches": sm_n,
+           "time_parallel": tp,
            "apply_kernel_ms": avg_s * 1e3, "apply_with_scatter_ms": e0.elapsed_time(e1) / args.steps,
            "algorithmic_bytes": alg_bytes, "algorithmic_flops": alg_flops,
            "achieved_gbs": alg_bytes / avg_s / 1e9, "hbm_frac": alg_bytes / avg_s / 1e9 / hbm_peak,

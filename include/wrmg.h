@@ -140,9 +140,9 @@ typedef struct {
                                a smoother-apply tile on every level (0-2: one CTA per patch,
                                1, 2 or 3 CTAs per SM; 3: one warp per patch)                 */
     int time_parallel;      /* parallel-in-time patch solve (Sec. 5's partitioned forward
-                               substitution): 1 (default) on the smoothed levels whose patches
-                               fill at most half of the GPU, 2 on every stored level (4
-                               chunks), 0 off.  Each level's slabs split into chunks swept
+                               substitution): 1 on the smoothed levels whose patches fill at
+                               most half of the GPU, 2 on every stored level (4 chunks), 0
+                               (default) off.  Each level's slabs split into chunks swept
                                at once from zero states, the chunk-boundary states chained
                                by transfer matrices built at linearisation, and the chunks
                                swept again from their incoming states                        */

@@ -701,7 +701,7 @@ void wr_default_options(wr_options* o) {
   o->store_factors = WR_STORE;
   o->autotune = 1;
   o->apply_tile = -1;
-  o->time_parallel = 1;
+  o->time_parallel = 0;
   o->recompute_slabs = 0;
   o->memory_budget_mb = 0;
 }
