@@ -139,6 +139,9 @@ typedef struct {
     int apply_tile;         /* -1 (default): the autotuner's (or the fixed) choice; 0 .. 3 force
                                a smoother-apply tile on every level (0-2: one CTA per patch,
                                1, 2 or 3 CTAs per SM; 3: one warp per patch)                 */
+    double newton_divtol;   /* stop (WR_ERR_NOT_CONVERGED) once ||F|| > newton_divtol ||F_0|| (1e6; 0: never) */
+    int newton_stall;       /* stop once FGMRES has used gmres_maxit in this many consecutive
+                               Newton steps (3; 0: never)                                     */
     int time_parallel;      /* parallel-in-time patch solve (Sec. 5's partitioned forward
                                substitution): 1 on the smoothed levels whose patches fill at
                                most half of the GPU, 2 on every stored level (4 chunks), 0

@@ -64,12 +64,15 @@ def splitmix64_uniform(seed, count):
 class Options:
     def __init__(self, cheb_steps=2, cheb_lo=0.25, cheb_hi=1.05, eig_steps=10,
                  newton_rtol=1e-8, newton_maxit=20, ew=True, eta_fixed=1e-4,
-                 restart=30, gmres_maxit=200):
+                 restart=30, gmres_maxit=200, newton_divtol=1e6, newton_stall=3):
         self.cheb_steps, self.cheb_lo, self.cheb_hi = cheb_steps, cheb_lo, cheb_hi
         self.eig_steps = eig_steps
         self.newton_rtol, self.newton_maxit = newton_rtol, newton_maxit
         self.ew, self.eta_fixed = ew, eta_fixed
         self.restart, self.gmres_maxit = restart, gmres_maxit
+        # give up on divergence (||F|| > divtol ||F_0||) or after `stall` consecutive
+        # Newton steps whose FGMRES used all its iterations (0 switches either off)
+        self.newton_divtol, self.newton_stall = newton_divtol, newton_stall
 
 
 class CoarseSolver:
@@ -277,13 +280,18 @@ def newton_solve(hier, U0=None, stats=None):
     f0 = fnorm = np.linalg.norm(F)
     eta = 0.5 if opts.ew else opts.eta_fixed
     hist = {"residuals": [fnorm], "gmres": [], "eta": []}
+    stalls = 0
     for _ in range(opts.newton_maxit):
         if fnorm <= opts.newton_rtol * f0:
+            break
+        if (opts.newton_divtol > 0 and fnorm > opts.newton_divtol * f0) or \
+                (opts.newton_stall > 0 and stalls >= opts.newton_stall):
             break
         hier.linearise(U)
         J = hier.levels[-1].J
         delta, its = fgmres(lambda v: J @ v, hier.precondition, -F, eta * fnorm,
                             opts.restart, opts.gmres_maxit)
+        stalls = stalls + 1 if its >= opts.gmres_maxit else 0
         U = U + delta
         F = disc.residual(U)
         fnew = np.linalg.norm(F)

@@ -601,9 +601,16 @@ struct wr_batch {
       }
     }
     int status = WR_OK;
+    std::vector<int> stalls(B, 0);  // consecutive Newton steps whose FGMRES ran out of iterations
     for (int it = 0; it < opt.newton_maxit && it < 64; ++it) {
-      for (int m = 0; m < B; ++m)
-        if (active[m] && (!(fnorm[m] > opt.newton_rtol * f0[m]) || !std::isfinite(fnorm[m]))) active[m] = 0;
+      for (int m = 0; m < B; ++m) {
+        if (!active[m]) continue;
+        const bool done = !(fnorm[m] > opt.newton_rtol * f0[m]) || !std::isfinite(fnorm[m]);
+        // a member that diverges or whose FGMRES stagnates leaves the batch early
+        const bool gave_up = (opt.newton_divtol > 0.0 && fnorm[m] > opt.newton_divtol * f0[m]) ||
+                             (opt.newton_stall > 0 && stalls[m] >= opt.newton_stall);
+        if (done || gave_up) active[m] = 0;
+      }
       build_tables();
       if (!fine.n) break;
       const double t0 = now_ms();
@@ -629,6 +636,7 @@ struct wr_batch {
         S.setup_ms += t1 - t0;
         S.krylov_ms += t2 - t1;
         S.vcycles += its[m];
+        stalls[m] = its[m] >= opt.gmres_maxit ? stalls[m] + 1 : 0;
         if (opt.ew) {
           const double gamma = 0.9, alpha = 2.0;
           double en = gamma * std::pow(fnew / fnorm[m], alpha);

@@ -594,6 +594,13 @@ struct wr_ctx {
     return its;
   }
 
+  // Newton gives up early (WR_ERR_NOT_CONVERGED) once ||F|| exceeds newton_divtol ||F_0||
+  // (divergence) or FGMRES has exhausted gmres_maxit in newton_stall consecutive steps.
+  bool newton_gave_up(double fnorm, double f0, int stalls) const {
+    if (opt.newton_divtol > 0.0 && fnorm > opt.newton_divtol * f0) return true;
+    return opt.newton_stall > 0 && stalls >= opt.newton_stall;
+  }
+
   int solve(double* U, wr_stats* st) {
     Level& fl = fine();
     const int64_t n = fl.g.ndofs;
@@ -606,6 +613,7 @@ struct wr_ctx {
     loc.residual_norms[0] = fnorm;
     int status = WR_ERR_NOT_CONVERGED;
     const int v0 = vcycles;
+    int stalls = 0;  // consecutive Newton steps whose FGMRES ran out of iterations
     for (int it = 0; it < opt.newton_maxit && it < 64; ++it) {
       check_cancel();
       if (!std::isfinite(fnorm)) {
@@ -616,6 +624,7 @@ struct wr_ctx {
         status = WR_OK;
         break;
       }
+      if (newton_gave_up(fnorm, f0, stalls)) break;  // diverged or stagnated
       double t0 = now_ms();
       linearise(U, true);
       WR_CUDA(cudaStreamSynchronize(s));
@@ -626,6 +635,7 @@ struct wr_ctx {
       const int its = fgmres(F, hx, eta * fnorm);
       WR_CUDA(cudaStreamSynchronize(s));
       loc.krylov_ms += now_ms() - t1;
+      stalls = its >= opt.gmres_maxit ? stalls + 1 : 0;
       vec_axpby(n, 1.0, hx, 1.0, U, s);
       residual(U, F);
       const double fnew = norm(n, F);
@@ -702,6 +712,8 @@ void wr_default_options(wr_options* o) {
   o->autotune = 1;
   o->apply_tile = -1;
   o->time_parallel = 0;
+  o->newton_divtol = 1e6;
+  o->newton_stall = 3;
   o->recompute_slabs = 0;
   o->memory_budget_mb = 0;
 }

@@ -47,7 +47,8 @@ class Options(ctypes.Structure):
                 ("patch_assembly", ctypes.c_int), ("scatter_weight", ctypes.c_int),
                 ("store_factors", ctypes.c_int), ("recompute_slabs", ctypes.c_int),
                 ("memory_budget_mb", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("apply_tile", ctypes.c_int), ("time_parallel", ctypes.c_int)]
+                ("apply_tile", ctypes.c_int), ("newton_divtol", ctypes.c_double), ("newton_stall", ctypes.c_int),
+                ("time_parallel", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

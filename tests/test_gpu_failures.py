@@ -69,3 +69,23 @@ def test_cancelled_requests_queued_and_running():
     assert r_wait[0] == wrmg.WR_ERR_CANCELLED
     assert r_run[0] in (wrmg.WR_ERR_CANCELLED, wrmg.WR_OK)   # it may finish before the flag is seen
     assert r_keep[0] == wrmg.WR_OK
+
+
+def test_newton_safeguards_match_the_oracle():
+    """Divergence and FGMRES-stagnation safeguards stop Newton where the oracle's do."""
+    from oracle.fem import Problem
+    from oracle.solver import Hierarchy, Options, newton_solve
+    w = inputs.fourier_small(n=4, k=1, q=0, N=2, nu=0.02)
+    from tests.oracle_problems import oracle_problem
+    for gpu_opts, ora_opts in [(dict(newton_divtol=0.5), dict(newton_divtol=0.5)),
+                               (dict(gmres_maxit=1, newton_stall=2), dict(gmres_maxit=1, newton_stall=2))]:
+        ctx = wrmg.Context(w, wrmg.default_options(**gpu_opts))
+        U = ctx.vector()
+        ctx.initial_guess(U)
+        st = ctx.solve(U, check=False)
+        ost = {}
+        newton_solve(Hierarchy(w.n_fine, w.n_coarse, w.k, w.q, w.N, oracle_problem(w), Options(**ora_opts)),
+                     stats=ost)
+        assert st["status"] == wrmg.WR_ERR_NOT_CONVERGED
+        assert st["gmres"] == ost["gmres"]
+        ctx.close()

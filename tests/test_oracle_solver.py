@@ -139,3 +139,19 @@ def test_shifted_problem_uses_its_start_time():
     u0 = d.initial_velocity()
     assert np.allclose(u0[:d.nv ** 2], (-np.cos(np.pi * X) * np.sin(np.pi * Y) * e).ravel(), atol=1e-15)
     assert np.allclose(d.time_nodes(0), 0.4 + 0.2 * d.tm.nodes)
+
+
+def test_newton_gives_up_on_divergence_and_on_fgmres_stagnation():
+    """The safeguards stop Newton early: a divergence tolerance below 1 stops before
+    the first step; an FGMRES limit of one iteration exhausts every inner solve, so
+    Newton stops after `newton_stall` steps."""
+    pb = Problem(kind="taylor_green", nu=0.02, conv=1.0, T=0.5)
+    st = {}
+    newton_solve(Hierarchy(4, 2, 1, 0, 2, pb, Options(newton_divtol=0.5)), stats=st)
+    assert st["gmres"] == []
+    st = {}
+    newton_solve(Hierarchy(4, 2, 1, 0, 2, pb, Options(gmres_maxit=1, newton_stall=2)), stats=st)
+    assert st["gmres"] == [1, 1]
+    st = {}
+    U = newton_solve(Hierarchy(4, 2, 1, 0, 2, pb, Options()), stats=st)
+    assert st["residuals"][-1] <= 1e-8 * st["residuals"][0]
