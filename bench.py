@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--rates", default="10,100,500", help="serve form: Poisson arrival rates (requests/s)")
     ap.add_argument("--inflight", type=int, default=8, help="serve form: solves in flight at most")
     ap.add_argument("--budget-gb", type=float, default=96.0, help="serve form: device-memory budget")
+    ap.add_argument("--tile", type=int, default=-1,
+                    help="cycle and smoother forms: force a smoother-apply tile 0..3 (default: autotuned)")
     ap.add_argument("--time-parallel", type=int, default=None,
                     help="smoother form: also time the parallel-in-time patch solve (1 = auto, 2 = forced)")
     ap.add_argument("--full-mix", action="store_true",
@@ -241,7 +243,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     w = workload(args, seed=rank)
     prec = {"fp64": wrmg.WR_FP64, "fp32": wrmg.WR_FP32, "bf16": wrmg.WR_BF16}[args.precision]
-    ctx = wrmg.Context(w, wrmg.default_options(precision=prec))
+    ctx = wrmg.Context(w, wrmg.default_options(precision=prec, apply_tile=args.tile))
     stream = torch.cuda.current_stream()
     D = ctx.ndofs()
     W = torch.from_numpy(inputs.forcing_shaped_iterate(w)).cuda()
@@ -603,7 +605,7 @@ def run_smoother_form(args):
     torch.cuda.set_device(0)
     w = workload(args)
     prec = {"fp64": wrmg.WR_FP64, "fp32": wrmg.WR_FP32, "bf16": wrmg.WR_BF16}[args.precision]
-    ctx = wrmg.Context(w, wrmg.default_options(precision=prec))
+    ctx = wrmg.Context(w, wrmg.default_options(precision=prec, apply_tile=args.tile))
     W = torch.from_numpy(inputs.forcing_shaped_iterate(w)).cuda()
     ctx.linearise(W, eig=False)
     L = ctx.fine
@@ -645,7 +647,7 @@ def run_smoother_form(args):
         tp = {"apply_with_scatter_ms": f0.elapsed_time(f1) / args.steps, "mode": args.time_parallel}
         ctx2.close()
     out = {"form": "smoother", "workload": w.name, "precision": args.precision, "launches": sm_n,
-           "time_parallel": tp,
+           "apply_tile": ctx.apply_tile(L), "time_parallel": tp,
            "apply_kernel_ms": avg_s * 1e3, "apply_with_scatter_ms": e0.elapsed_time(e1) / args.steps,
            "algorithmic_bytes": alg_bytes, "algorithmic_flops": alg_flops,
            "achieved_gbs": alg_bytes / avg_s / 1e9, "hbm_frac": alg_bytes / avg_s / 1e9 / hbm_peak,
