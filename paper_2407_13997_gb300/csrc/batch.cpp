@@ -239,12 +239,17 @@ struct wr_batch {
 
   void jac(const Table& t, const double* x, double* y) {
     if (t.n) bt_jacobian(k, q, t.d, t.n, t.units, t.dofs, tab, x, y, ye, s);
+  }  // inside the preconditioner: single-precision element arithmetic in the reduced-precision forms
+  void jac_inner(const Table& t, const double* x, double* y) {
+    if (opt.precision == WR_FP64) jac(t, x, y);
+    else if (t.n) bt_jacobian_f32(k, q, t.d, t.n, t.units, t.dofs, tab, x, y, ye, s);
   }
+
   void papply(const Table& t, int d, const double* r, double* y) {
     if (t.n) bt_block_apply(k, q, opt.precision, t.d, t.n, t.items, t.dofs, tab, r, y, yp, derr, 0, s, depth_variant[d]);
   }
   void residual_b_minus(const Table& t, const double* b, double* x, double* tmp, double* r) {
-    jac(t, x, tmp);
+    jac_inner(t, x, tmp);
     bt_copy(t.d, t.n, t.dofs, b, r, s);
     bt_axpby(t.d, t.n, t.dofs, nullptr, -1.0, tmp, nullptr, 1.0, r, s);
   }
@@ -414,7 +419,7 @@ struct wr_batch {
     for (int i = 0; i < t.n; ++i) c[i] = 1.0 / std::sqrt(nrm[i]);
     bt_axpby(t.d, t.n, t.dofs, nullptr, 0.0, V[0], coefs(c), 0.0, V[0], s);
     for (int j = 0; j < mdim; ++j) {
-      jac(t, V[j], ar[d].t);
+      jac_inner(t, V[j], ar[d].t);
       papply(t, d, ar[d].t, V[j + 1]);
       for (int i = 0; i <= j; ++i) {
         std::vector<double> h = dots(t, V[j + 1], V[i]);

@@ -310,6 +310,243 @@ __device__ __forceinline__ void element_body(const LevelGeom& g, const FeTables&
   for (int it = lane; it < d::ELEM; it += 32) dst[it] = s.out[it];
 }
 
+// ---------------------------------------------------------------- FP32 Jacobian action
+// J(W) x in single precision for the reduced-precision forms, where it only feeds the
+// smoother's residuals inside the V-cycle (the Newton residual and the outer FGMRES
+// keep the FP64 kernel above).  Same algorithm as element_body<.., LIN = true>, with
+// the reference tables staged once per CTA as floats; element results stay FP64 in
+// the per-element buffer, so the assembly is unchanged.
+template <int K, int Q>
+struct TabF {
+  using d = D<K, Q>;
+  float Bv[d::NQ][d::NVL], Dv[d::NQ][d::NVL], Bp[d::NQ][d::NPL], wq[d::NQ];
+  float Kt[d::NT][d::NT], Wt[d::NT][d::NT], T3[d::NT][d::NT][d::NT], tau0[d::NT];
+};
+
+template <int K, int Q>
+struct ElemSmemF {
+  using d = D<K, Q>;
+  static constexpr int FV = 4 * d::NT + 2;
+  static constexpr int FU = 0, FW = 2 * d::NT, FUP = 4 * d::NT;
+  float vn[FV][d::NVE];
+  float pn[d::NT][d::NPE];
+  float t1[FV][2][d::NVL][d::NQ];
+  float vq[FV][3][d::NQ2];
+  float pq[d::NT][d::NQ2];
+  float cv[2 * d::NT][3][d::NQ2];
+  float cp[d::NT][d::NQ2];
+  float out[d::ELEM];
+};
+
+template <int K, int Q>
+__device__ __forceinline__ void stage_tab_f(const FeTables& T, TabF<K, Q>& tb) {
+  using d = D<K, Q>;
+  for (int e = threadIdx.x; e < d::NQ * d::NVL; e += blockDim.x) {
+    const int q = e / d::NVL, i = e % d::NVL;
+    tb.Bv[q][i] = (float)T.Bv[q][i];
+    tb.Dv[q][i] = (float)T.Dv[q][i];
+  }
+  for (int e = threadIdx.x; e < d::NQ * d::NPL; e += blockDim.x) tb.Bp[e / d::NPL][e % d::NPL] = (float)T.Bp[e / d::NPL][e % d::NPL];
+  for (int e = threadIdx.x; e < d::NQ; e += blockDim.x) tb.wq[e] = (float)T.wq[e];
+  for (int e = threadIdx.x; e < d::NT * d::NT * d::NT; e += blockDim.x) {
+    const int a = e / (d::NT * d::NT), b = (e / d::NT) % d::NT, c = e % d::NT;
+    tb.T3[a][b][c] = (float)T.T3[a][b][c];
+    if (c == 0) {
+      tb.Kt[a][b] = (float)T.Kt[a][b];
+      tb.Wt[a][b] = (float)T.Wt[a][b];
+    }
+  }
+  for (int e = threadIdx.x; e < d::NT; e += blockDim.x) tb.tau0[e] = (float)T.tau0[e];
+}
+
+template <int K, int Q>
+__device__ __forceinline__ void element_body_f32(const LevelGeom& g, const TabF<K, Q>& tb, const PhysParams& ph,
+                                                 const double* __restrict__ W, const double* __restrict__ x,
+                                                 double* __restrict__ ye, ElemSmemF<K, Q>& s, int cell, int slab) {
+  using d = D<K, Q>;
+  using SM = ElemSmemF<K, Q>;
+  const int lane = threadIdx.x & 31;
+  const int CI = cell % g.n, CJ = cell / g.n;
+  const float h = (float)g.h, dt = (float)g.dt;
+  const int nv = g.nv, np = g.np, S = g.S;
+  const int64_t nv2 = (int64_t)nv * nv;
+  for (int it = lane; it < 2 * d::NVE; it += 32) {
+    const int c = it / d::NVE, l = it % d::NVE;
+    const int gx = CI * (K + 1) + l % d::NVL, gy = CJ * (K + 1) + l / d::NVL;
+    const int64_t sp = c * nv2 + (int64_t)gy * nv + gx;
+    const bool dir = vel_dirichlet(g, gx, gy);
+    for (int b = 0; b < d::NT; ++b) {
+      const int64_t off = ((int64_t)slab * d::NT + b) * S + sp;
+      s.vn[SM::FU + c * d::NT + b][l] = dir ? 0.f : (float)x[off];
+      s.vn[SM::FW + c * d::NT + b][l] = (float)W[off];
+    }
+    float up = 0.f;
+    if (slab > 0 && !dir) up = (float)x[((int64_t)(slab - 1) * d::NT + (d::NT - 1)) * S + sp];
+    s.vn[SM::FUP + c][l] = up;
+  }
+  for (int it = lane; it < d::NT * d::NPE; it += 32) {
+    const int b = it / d::NPE, l = it % d::NPE;
+    const int px = CI * K + l % d::NPL, py = CJ * K + l / d::NPL;
+    s.pn[b][l] = (float)x[((int64_t)slab * d::NT + b) * S + 2 * nv2 + (int64_t)py * np + px];
+  }
+  __syncwarp();
+  for (int it = lane; it < SM::FV * d::NVL * d::NQ; it += 32) {
+    const int f = it / (d::NVL * d::NQ), r = it % (d::NVL * d::NQ);
+    const int j = r / d::NQ, qx = r % d::NQ;
+    float v = 0.f, dv = 0.f;
+#pragma unroll
+    for (int i = 0; i < d::NVL; ++i) {
+      const float u = s.vn[f][j * d::NVL + i];
+      v = fmaf(tb.Bv[qx][i], u, v);
+      dv = fmaf(tb.Dv[qx][i], u, dv);
+    }
+    s.t1[f][0][j][qx] = v;
+    s.t1[f][1][j][qx] = dv;
+  }
+  for (int it = lane; it < d::NT * d::NQ2; it += 32) {
+    const int b = it / d::NQ2, q = it % d::NQ2;
+    const int qy = q / d::NQ, qx = q % d::NQ;
+    float v = 0.f;
+#pragma unroll
+    for (int j = 0; j < d::NPL; ++j)
+#pragma unroll
+      for (int i = 0; i < d::NPL; ++i) v = fmaf(tb.Bp[qy][j] * tb.Bp[qx][i], s.pn[b][j * d::NPL + i], v);
+    s.pq[b][q] = v;
+  }
+  __syncwarp();
+  const float ih = 1.f / h;
+  for (int it = lane; it < SM::FV * d::NQ2; it += 32) {
+    const int f = it / d::NQ2, q = it % d::NQ2;
+    const int qy = q / d::NQ, qx = q % d::NQ;
+    float v = 0.f, vx = 0.f, vy = 0.f;
+#pragma unroll
+    for (int j = 0; j < d::NVL; ++j) {
+      v = fmaf(tb.Bv[qy][j], s.t1[f][0][j][qx], v);
+      vx = fmaf(tb.Bv[qy][j], s.t1[f][1][j][qx], vx);
+      vy = fmaf(tb.Dv[qy][j], s.t1[f][0][j][qx], vy);
+    }
+    s.vq[f][0][q] = v;
+    s.vq[f][1][q] = vx * ih;
+    s.vq[f][2][q] = vy * ih;
+  }
+  __syncwarp();
+  const float nu = (float)ph.nu, conv = (float)ph.conv;
+  for (int q = lane; q < d::NQ2; q += 32) {
+    const int qy = q / d::NQ, qx = q % d::NQ;
+    const float om = tb.wq[qx] * tb.wq[qy] * h * h;
+#pragma unroll
+    for (int a = 0; a < d::NT; ++a) {
+      float pw = 0.f, divw = 0.f;
+#pragma unroll
+      for (int b = 0; b < d::NT; ++b) {
+        pw = fmaf(tb.Wt[a][b], s.pq[b][q], pw);
+        divw = fmaf(tb.Wt[a][b], s.vq[SM::FU + 0 * d::NT + b][1][q] + s.vq[SM::FU + 1 * d::NT + b][2][q], divw);
+      }
+      s.cp[a][q] = om * dt * divw;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        float val = -tb.tau0[a] * s.vq[SM::FUP + c][0][q];
+        float gx = 0.f, gy = 0.f, cv = 0.f;
+#pragma unroll
+        for (int b = 0; b < d::NT; ++b) {
+          const int fu = SM::FU + c * d::NT + b;
+          val = fmaf(tb.Kt[a][b], s.vq[fu][0][q], val);
+          gx = fmaf(tb.Wt[a][b], s.vq[fu][1][q], gx);
+          gy = fmaf(tb.Wt[a][b], s.vq[fu][2][q], gy);
+#pragma unroll
+          for (int e = 0; e < d::NT; ++e) {
+            const int fe = SM::FU + c * d::NT + e;
+            const int wb = SM::FW + b, wb1 = SM::FW + d::NT + b;
+            const int ub = SM::FU + b, ub1 = SM::FU + d::NT + b;
+            const int we = SM::FW + c * d::NT + e;
+            const float term = s.vq[wb][0][q] * s.vq[fe][1][q] + s.vq[wb1][0][q] * s.vq[fe][2][q] +
+                               s.vq[ub][0][q] * s.vq[we][1][q] + s.vq[ub1][0][q] * s.vq[we][2][q];
+            cv = fmaf(tb.T3[a][b][e], term, cv);
+          }
+        }
+        val = fmaf(dt * conv, cv, val);
+        gx = dt * nu * gx + (c == 0 ? dt * pw : 0.f);
+        gy = dt * nu * gy + (c == 1 ? dt * pw : 0.f);
+        s.cv[c * d::NT + a][0][q] = om * val;
+        s.cv[c * d::NT + a][1][q] = om * gx * ih;
+        s.cv[c * d::NT + a][2][q] = om * gy * ih;
+      }
+    }
+  }
+  __syncwarp();
+  for (int it = lane; it < 2 * d::NT * d::NVL * d::NQ; it += 32) {
+    const int f = it / (d::NVL * d::NQ), r = it % (d::NVL * d::NQ);
+    const int j = r / d::NQ, qx = r % d::NQ;
+    float a1 = 0.f, a2 = 0.f;
+#pragma unroll
+    for (int qy = 0; qy < d::NQ; ++qy) {
+      const int q = qy * d::NQ + qx;
+      a1 = fmaf(tb.Bv[qy][j], s.cv[f][0][q], a1);
+      a1 = fmaf(tb.Dv[qy][j], s.cv[f][2][q], a1);
+      a2 = fmaf(tb.Bv[qy][j], s.cv[f][1][q], a2);
+    }
+    s.t1[f][0][j][qx] = a1;
+    s.t1[f][1][j][qx] = a2;
+  }
+  __syncwarp();
+  for (int it = lane; it < 2 * d::NT * d::NVE; it += 32) {
+    const int f = it / d::NVE, l = it % d::NVE;
+    const int c = f / d::NT, a = f % d::NT;
+    const int j = l / d::NVL, i = l % d::NVL;
+    float v = 0.f;
+#pragma unroll
+    for (int qx = 0; qx < d::NQ; ++qx) {
+      v = fmaf(tb.Bv[qx][i], s.t1[f][0][j][qx], v);
+      v = fmaf(tb.Dv[qx][i], s.t1[f][1][j][qx], v);
+    }
+    s.out[a * (2 * d::NVE + d::NPE) + c * d::NVE + l] = v;
+  }
+  for (int it = lane; it < d::NT * d::NPE; it += 32) {
+    const int a = it / d::NPE, l = it % d::NPE;
+    const int j = l / d::NPL, i = l % d::NPL;
+    float v = 0.f;
+    for (int qy = 0; qy < d::NQ; ++qy)
+      for (int qx = 0; qx < d::NQ; ++qx) v = fmaf(tb.Bp[qy][j] * tb.Bp[qx][i], s.cp[a][qy * d::NQ + qx], v);
+    s.out[a * (2 * d::NVE + d::NPE) + 2 * d::NVE + l] = v;
+  }
+  __syncwarp();
+  double* dst = ye + ((int64_t)slab * g.ncells() + cell) * d::ELEM;
+  for (int it = lane; it < d::ELEM; it += 32) dst[it] = (double)s.out[it];
+}
+
+template <int K, int Q>
+__global__ void __launch_bounds__(32 * kWarps)
+element_f32_kernel(LevelGeom g, FeTables T, PhysParams ph, const double* __restrict__ W,
+                   const double* __restrict__ x, double* __restrict__ ye) {
+  __shared__ TabF<K, Q> tb;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  stage_tab_f<K, Q>(T, tb);
+  __syncthreads();
+  const int cell = blockIdx.x * kWarps + threadIdx.x / 32;
+  if (cell >= g.ncells()) return;
+  element_body_f32<K, Q>(g, tb, ph, W, x, ye, reinterpret_cast<ElemSmemF<K, Q>*>(smem_raw)[threadIdx.x / 32], cell,
+                         blockIdx.y);
+}
+
+// Batched FP32 Jacobian: one CTA per (member, group of kWarps cells, slab).
+template <int K, int Q>
+__global__ void __launch_bounds__(32 * kWarps)
+bt_element_f32_kernel(const BatchSeg* __restrict__ segs, int nseg, FeTables T, const double* __restrict__ x,
+                      double* __restrict__ ye) {
+  __shared__ TabF<K, Q> tb;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  stage_tab_f<K, Q>(T, tb);
+  __syncthreads();
+  const int m = batch_find<BU_ELEM>(segs, nseg, blockIdx.x);
+  const LevelGeom g = segs[m].g;
+  const int cb = (g.ncells() + kWarps - 1) / kWarps;
+  const int64_t local = blockIdx.x - segs[m].u_elem;
+  const int slab = (int)(local / cb), cell = (int)(local % cb) * kWarps + threadIdx.x / 32;
+  if (cell >= g.ncells()) return;
+  element_body_f32<K, Q>(g, tb, segs[m].ph, segs[m].W, x + segs[m].off, ye + segs[m].off_ye,
+                         reinterpret_cast<ElemSmemF<K, Q>*>(smem_raw)[threadIdx.x / 32], cell, slab);
+}
+
 template <int K, int Q, bool LIN>
 __global__ void __launch_bounds__(32 * kWarps)
 element_kernel(LevelGeom g, FeTables T, PhysParams ph, const double* __restrict__ W,
@@ -593,6 +830,35 @@ void run_bt_element(const BatchSeg* segs, int nseg, int64_t units, int64_t dofs,
   }
 }
 
+template <int K, int Q>
+void run_element_f32(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* W, const double* x,
+                     double* y, double* ye, cudaStream_t s) {
+  const size_t smem = sizeof(ElemSmemF<K, Q>) * kWarps;
+  auto kern = element_f32_kernel<K, Q>;
+  WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((g.ncells() + kWarps - 1) / kWarps, g.N);
+  kern<<<grid, 32 * kWarps, smem, s>>>(g, T, ph, W, x, ye);
+  WR_LAUNCH_CHECK();
+  assemble_kernel<K, Q, true><<<(unsigned)((g.ndofs + 255) / 256), 256, 0, s>>>(g, T, ph, ye, x, y);
+  WR_LAUNCH_CHECK();
+}
+
+template <int K, int Q>
+void run_bt_element_f32(const BatchSeg* segs, int nseg, int64_t units, int64_t dofs, const FeTables& T,
+                        const double* x, double* y, double* ye, cudaStream_t s) {
+  const size_t smem = sizeof(ElemSmemF<K, Q>) * kWarps;
+  auto kern = bt_element_f32_kernel<K, Q>;
+  WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (units > 0) {
+    kern<<<(unsigned)units, 32 * kWarps, smem, s>>>(segs, nseg, T, x, ye);
+    WR_LAUNCH_CHECK();
+  }
+  if (dofs > 0) {
+    bt_assemble_kernel<K, Q, true><<<(unsigned)((dofs + 255) / 256), 256, 0, s>>>(segs, nseg, dofs, T, ye, x, y);
+    WR_LAUNCH_CHECK();
+  }
+}
+
 template <bool LIN>
 void dispatch_bt_element(int k, int q, const BatchSeg* segs, int nseg, int64_t units, int64_t dofs,
                          const FeTables& T, const double* x, double* y, double* ye, cudaStream_t s) {
@@ -608,6 +874,15 @@ void dispatch_bt_element(int k, int q, const BatchSeg* segs, int nseg, int64_t u
 void bt_jacobian(int k, int q, const BatchSeg* segs, int nseg, int64_t units, int64_t dofs, const FeTables& T,
                  const double* x, double* y, double* ye, cudaStream_t s) {
   dispatch_bt_element<true>(k, q, segs, nseg, units, dofs, T, x, y, ye, s);
+}
+
+void bt_jacobian_f32(int k, int q, const BatchSeg* segs, int nseg, int64_t units, int64_t dofs, const FeTables& T,
+                     const double* x, double* y, double* ye, cudaStream_t s) {
+  if (k == 1 && q == 0) run_bt_element_f32<1, 0>(segs, nseg, units, dofs, T, x, y, ye, s);
+  else if (k == 1 && q == 1) run_bt_element_f32<1, 1>(segs, nseg, units, dofs, T, x, y, ye, s);
+  else if (k == 2 && q == 0) run_bt_element_f32<2, 0>(segs, nseg, units, dofs, T, x, y, ye, s);
+  else if (k == 2 && q == 1) run_bt_element_f32<2, 1>(segs, nseg, units, dofs, T, x, y, ye, s);
+  else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 }
 
 void bt_residual(int k, int q, const BatchSeg* segs, int nseg, int64_t units, int64_t dofs, const FeTables& T,
@@ -629,6 +904,15 @@ void launch_residual(const LevelGeom& g, const FeTables& T, const PhysParams& ph
 void launch_jacobian(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* W, const double* x,
                      double* y, double* ye, cudaStream_t s) {
   dispatch_element<true>(g, T, ph, W, x, y, ye, s);
+}
+
+void launch_jacobian_f32(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* W, const double* x,
+                         double* y, double* ye, cudaStream_t s) {
+  if (g.k == 1 && g.q == 0) run_element_f32<1, 0>(g, T, ph, W, x, y, ye, s);
+  else if (g.k == 1 && g.q == 1) run_element_f32<1, 1>(g, T, ph, W, x, y, ye, s);
+  else if (g.k == 2 && g.q == 0) run_element_f32<2, 0>(g, T, ph, W, x, y, ye, s);
+  else if (g.k == 2 && g.q == 1) run_element_f32<2, 1>(g, T, ph, W, x, y, ye, s);
+  else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 }
 
 void launch_boundary_values(const LevelGeom& g, const FeTables& T, const PhysParams& ph, double* U, cudaStream_t s) {

@@ -203,6 +203,13 @@ struct wr_ctx {
     if (heat) heat_jacobian(L[l].g, tab, ph, x, y, s);
     else launch_jacobian(L[l].g, tab, ph, L[l].W, x, y, ye, s);
   }
+  // J inside the preconditioner (smoother residuals, the residual restricted to the
+  // next level, eigen-estimates): single-precision element arithmetic in the
+  // reduced-precision forms; the Newton residual and the outer FGMRES use jac().
+  void jac_inner(int l, const double* x, double* y) {
+    if (!heat && opt.precision != WR_FP64) launch_jacobian_f32(L[l].g, tab, ph, L[l].W, x, y, ye, s);
+    else jac(l, x, y);
+  }
   void restrict_to(int l, const double* xf, double* xc) {
     if (heat) heat_restrict(L[l].g, L[l - 1].g, tab, xf, xc, s);
     else launch_restrict(L[l].g, L[l - 1].g, tab, xf, xc, s);
@@ -363,7 +370,7 @@ struct wr_ctx {
       vec_zero(n, x, s);
       vec_copy(n, b, lv.r, s);
     } else {
-      jac(l, x, lv.t);
+      jac_inner(l, x, lv.t);
       vec_copy(n, b, lv.r, s);
       vec_axpby(n, -1.0, lv.t, 1.0, lv.r, s);
     }
@@ -373,7 +380,7 @@ struct wr_ctx {
     for (int step = 0; step < opt.cheb_steps; ++step) {
       vec_axpby(n, 1.0, lv.d, 1.0, x, s);
       if (step == opt.cheb_steps - 1) break;
-      jac(l, x, lv.t);
+      jac_inner(l, x, lv.t);
       vec_copy(n, b, lv.r, s);
       vec_axpby(n, -1.0, lv.t, 1.0, lv.r, s);
       patch_apply(l, lv.r, lv.z);
@@ -395,7 +402,7 @@ struct wr_ctx {
     xl[T_] = x;
     for (int l = T_; l >= 1; --l) {
       smooth(l, bl[l], xl[l], true);
-      jac(l, xl[l], L[l].t);
+      jac_inner(l, xl[l], L[l].t);
       vec_copy(L[l].g.ndofs, bl[l], L[l].r, s);
       vec_axpby(L[l].g.ndofs, -1.0, L[l].t, 1.0, L[l].r, s);
       restrict_to(l, L[l].r, L[l - 1].b);
@@ -458,7 +465,7 @@ struct wr_ctx {
     vec_scale(n, 1.0 / norm(n, V[0]), V[0], s);
     int mm = m;
     for (int j = 0; j < m; ++j) {
-      jac(l, V[j], lv.t);
+      jac_inner(l, V[j], lv.t);
       patch_apply(l, lv.t, V[j + 1]);
       for (int i = 0; i <= j; ++i) {
         const double hij = dot(n, V[j + 1], V[i]);

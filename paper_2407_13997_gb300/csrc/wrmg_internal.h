@@ -183,6 +183,10 @@ void launch_residual(const LevelGeom& g, const FeTables& T, const PhysParams& ph
                      double* F, double* ye, cudaStream_t s);
 void launch_jacobian(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* W,
                      const double* x, double* y, double* ye, cudaStream_t s);
+// J(W) x with single-precision element arithmetic (FP64 vectors and assembly): the
+// smoother's residuals inside the V-cycle of the reduced-precision forms
+void launch_jacobian_f32(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* W,
+                         const double* x, double* y, double* ye, cudaStream_t s);
 void launch_boundary_values(const LevelGeom& g, const FeTables& T, const PhysParams& ph, double* U,
                             cudaStream_t s);
 void launch_conv_elements(const LevelGeom& g, const FeTables& T, const double* W, double* Ce,
@@ -248,6 +252,8 @@ double measure_fp64_tflops(cudaStream_t s);
 // batched kernels (one launch for every member in `segs`; base pointers are arenas)
 void bt_jacobian(int k, int q, const BatchSeg* segs, int nseg, int64_t units, int64_t dofs, const FeTables& T,
                  const double* x, double* y, double* ye, cudaStream_t s);
+void bt_jacobian_f32(int k, int q, const BatchSeg* segs, int nseg, int64_t units, int64_t dofs, const FeTables& T,
+                     const double* x, double* y, double* ye, cudaStream_t s);
 void bt_residual(int k, int q, const BatchSeg* segs, int nseg, int64_t units, int64_t dofs, const FeTables& T,
                  const double* U, double* F, double* ye, cudaStream_t s);
 // coarse_n = 0: patch smoother (scatter into `out`); 2 or 3: coarse block solves of that coarse mesh

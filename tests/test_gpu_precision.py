@@ -62,3 +62,28 @@ def test_reduced_precision_solve_meets_1e8_against_fp64_oracle(w, prec):
     err = rel(U.cpu().numpy(), ref)
     assert err <= 1e-8, (err, st)
     ctx.close()
+
+
+@pytest.mark.parametrize("w", [inputs.fourier_small(n=8, k=1, q=0, N=3, nu=0.02),
+                               inputs.fourier_small(n=8, k=2, q=1, N=2, nu=0.01)], ids=["q2q1_dg0", "q3q2_dg1"])
+def test_fp32_form_vcycle_close_to_fp64_oracle(w):
+    """In the FP32 form every operator inside the V-cycle (the patch smoother and the
+    Jacobian actions of the Chebyshev residuals and of the restricted residual) is
+    single precision; the cycle stays FP32-accurate against the FP64 oracle's."""
+    ctx = wrmg.Context(w, wrmg.default_options(precision=wrmg.WR_FP32))
+    hier = Hierarchy(w.n_fine, w.n_coarse, w.k, w.q, w.N, oracle_problem(w), Options())
+    rng = np.random.default_rng(9)
+    d = hier.fine
+    W = 0.5 * rng.standard_normal(d.ndofs)
+    mask = d.dirichlet_mask()
+    W[mask] = d.boundary_values()[mask]
+    hier.linearise(W)
+    ctx.linearise(torch.from_numpy(W).cuda(), eig=False)
+    for l in range(1, len(hier.levels)):
+        ctx.set_lambda(l, hier.levels[l].lam)
+    b = rng.standard_normal(d.ndofs) * hier.levels[-1].free
+    x = ctx.vector()
+    ctx.vcycle(torch.from_numpy(b).cuda(), x)
+    err = rel(x.cpu().numpy(), hier.vcycle(b))
+    assert 1e-12 < err < 1e-4, err
+    ctx.close()
