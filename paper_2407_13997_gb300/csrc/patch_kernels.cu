@@ -347,6 +347,112 @@ __device__ bool gauss_jordan(CT* A, CT* colbuf, int* perm, int* sh) {
   return sh[1] == 0;
 }
 
+// Register-tiled Gauss-Jordan inversion with partial pivoting, the same elimination
+// as gauss_jordan above without moving rows: thread (ty, tx) of a (NTH/32) x 32 grid
+// holds rows ty + TY u and columns tx + 32 v of A in registers for the whole
+// inversion.  Per pivot column p: the column goes to shared memory, every warp picks
+// the pivot row (largest |.| among rows not yet used, lowest row on ties), the warp
+// that owns that row publishes it scaled, and every thread updates its own entries
+// (two block barriers per pivot; the column and row buffers alternate between
+// pivots, and the used-row flags change only after the second barrier).  The inverse is read back with the pivot order undone:
+// inv(A)[i][r_q] = X[r_i][q] for the pivot rows r.  A is MS x MS row-major with
+// leading dimension LD in shared memory, overwritten with inv(A).  Returns false (to
+// all threads) if a zero pivot was met.
+template <int MS, int LD, int NTH, typename CT>
+__device__ bool gauss_jordan_reg(CT* A) {
+  constexpr int TY = NTH / 32, RU = (MS + TY - 1) / TY, CV = (MS + 31) / 32;
+  __shared__ CT colb[2][MS], rowb[2][MS];
+  __shared__ int used[MS], prow[MS], pstep[MS], zero_pivot;
+  const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
+  CT a[RU][CV];
+#pragma unroll
+  for (int u = 0; u < RU; ++u)
+#pragma unroll
+    for (int v = 0; v < CV; ++v) {
+      const int i = ty + TY * u, j = lane + 32 * v;
+      a[u][v] = (i < MS && j < MS) ? A[i * LD + j] : CT(0);
+    }
+  for (int i = tid; i < MS; i += NTH) used[i] = 0;
+  if (tid == 0) zero_pivot = 0;
+  __syncthreads();
+#pragma unroll 1
+  for (int p = 0; p < MS; ++p) {
+    const int bsel = p & 1;
+    // column p to shared memory (owned by the lanes with lane == p % 32)
+    if (lane == (p & 31)) {
+      const int vp = p >> 5;
+#pragma unroll
+      for (int u = 0; u < RU; ++u) {
+        CT val = CT(0);
+#pragma unroll
+        for (int v = 0; v < CV; ++v) val = (v == vp) ? a[u][v] : val;
+        const int i = ty + TY * u;
+        if (i < MS) colb[bsel][i] = val;
+      }
+    }
+    __syncthreads();
+    // every warp finds the same pivot row
+    CT best = CT(-1);
+    int bi = MS;
+    for (int i = lane; i < MS; i += 32) {
+      const CT v = used[i] ? CT(-1) : fabs(colb[bsel][i]);
+      if (v > best) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const CT ob = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    const int r = bi;
+    const CT inv = CT(1) / colb[bsel][r];
+    // the owner warp of row r publishes it scaled by the inverse pivot
+    if (ty == r % TY) {
+      const int ur = r / TY;
+#pragma unroll
+      for (int v = 0; v < CV; ++v) {
+        CT val = CT(0);
+#pragma unroll
+        for (int u = 0; u < RU; ++u) val = (u == ur) ? a[u][v] : val;
+        const int j = lane + 32 * v;
+        if (j < MS) rowb[bsel][j] = (j == p) ? inv : val * inv;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+      const int i = ty + TY * u;
+      const CT f = i < MS ? colb[bsel][i] : CT(0);
+#pragma unroll
+      for (int v = 0; v < CV; ++v) {
+        const int j = lane + 32 * v;
+        const CT rj = j < MS ? rowb[bsel][j] : CT(0);
+        const CT nv = (i == r) ? rj : ((j == p) ? -f * rj : fma(-f, rj, a[u][v]));
+        a[u][v] = nv;
+      }
+    }
+    // bookkeeping after the second barrier, so that no warp's search of this pivot sees it
+    if (tid == 0) {
+      used[r] = 1;
+      prow[p] = r;
+      pstep[r] = p;
+      if (!(best > CT(0))) zero_pivot = 1;
+    }
+  }
+  __syncthreads();
+  // undo the pivot order: inv(A)[pstep[row]][prow[col]] = X[row][col]
+#pragma unroll
+  for (int u = 0; u < RU; ++u)
+#pragma unroll
+    for (int v = 0; v < CV; ++v) {
+      const int i = ty + TY * u, j = lane + 32 * v;
+      if (i < MS && j < MS) A[pstep[i] * LD + prow[j]] = a[u][v];
+    }
+  __syncthreads();
+  return zero_pivot == 0;
+}
+
+
 __device__ __forceinline__ void narrow(double v, double& d) { d = v; }
 __device__ __forceinline__ void narrow(float v, float& d) { d = v; }
 __device__ __forceinline__ void narrow(float v, __nv_bfloat16& d) { d = __float2bfloat16_rn(v); }
@@ -411,14 +517,14 @@ block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const d
     assemble_const<K, Q, CT, LD, NTH, NPGX>(g, T, ph, ft, M1, 0, 0, false);
     __syncthreads();
     if (conv) assemble_conv<K, Q, CT, LD, NTH, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M1, 0, 0);
-    ok = gauss_jordan<MS, LD, NTH>(M1, colbuf, perm, sh);
+    ok = gauss_jordan_reg<MS, LD, NTH>(M1);
     store_colmajor<MS, LD, NTH>(M1, F);
   } else {
     // A00^{-1}
     assemble_const<K, Q, CT, LD, NTH, NPGX>(g, T, ph, ft, M1, 0, 0, false);
     __syncthreads();
     if (conv) assemble_conv<K, Q, CT, LD, NTH, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M1, 0, 0);
-    ok = gauss_jordan<MS, LD, NTH>(M1, colbuf, perm, sh);
+    ok = gauss_jordan_reg<MS, LD, NTH>(M1);
     store_colmajor<MS, LD, NTH>(M1, F);
     // X = A00^{-1} A01
     assemble_const<K, Q, CT, LD, NTH, NPGX>(g, T, ph, ft, M2, 0, 1, false);
@@ -436,7 +542,7 @@ block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const d
     assemble_const<K, Q, CT, LD, NTH, NPGX>(g, T, ph, ft, M2, 1, 1, true);
     __syncthreads();
     if (conv) assemble_conv<K, Q, CT, LD, NTH, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M2, 1, 1);
-    ok = gauss_jordan<MS, LD, NTH>(M2, colbuf, perm, sh) && ok;
+    ok = gauss_jordan_reg<MS, LD, NTH>(M2) && ok;
     store_colmajor<MS, LD, NTH>(M2, F + 2 * BLK);
   }
   if (!ok && threadIdx.x == 0) atomicExch(status, 1);
