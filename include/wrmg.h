@@ -66,8 +66,10 @@ extern "C" {
 #define WR_LID 3           /* lid-driven cavity (Sec. 4): u = (1, 0) on the open top edge, 0 on the other walls
                               and the top corners, u(0) = 0, f = 0                                         */
 /* The heat equation (Def. heat): u_t - nu lap u = 0, natural boundary conditions, continuous Q_k
- * (k = 1, 2, 3) x DG(q); one scalar field, canonical index (slab (q+1) + a) S + y nv + x with
- * nv = n k + 1, S = nv^2; vertex-star (open-star) patches; n_coarse = 2.  The problem is linear:
+ * (k = 1, 2, 3) x DG(q) (q = 0..3, the degrees of Sec. 5); one scalar field, canonical index
+ * (slab (q+1) + a) S + y nv + x with nv = n k + 1, S = nv^2; vertex-star (open-star) patches;
+ * n_coarse = 2, or 1 (required for k = 3, q = 3, whose 2x2 coarse block, 196 x 196 in FP64, does
+ * not fit in shared memory; wr_create returns WR_ERR_ARG for it).  The problem is linear:
  * wr_solve with newton_maxit = 1, ew = 0 and eta_fixed = the FGMRES tolerance is the paper's
  * FGMRES-WRMG solve (Sec. 5).  Only the FP64 smoother exists for it. */
 #define WR_HEAT 4          /* u(0) = sin(pi x) + cos(2 pi y) (Sec. 5)                                      */
@@ -103,9 +105,11 @@ typedef struct wr_ctx wr_ctx;
 
 typedef struct {
     int n_fine;     /* cells per direction on the finest level (n_coarse times a power of 2) */
-    int n_coarse;   /* cells per direction on the direct-solve level: 2, or 3 when k = 1     */
-    int k;          /* Taylor-Hood order: velocity Q_{k+1}, pressure Q_k; k = 1 or 2          */
-    int q;          /* DG(q) in time; q = 0 or 1                                             */
+    int n_coarse;   /* cells per direction on the direct-solve level: 2, or 3 when k = 1
+                       (heat: 1 or 2)                                                        */
+    int k;          /* Taylor-Hood order: velocity Q_{k+1}, pressure Q_k; k = 1 or 2
+                       (heat: Q_k, k = 1, 2, 3)                                              */
+    int q;          /* DG(q) in time; q = 0 or 1 (heat: 0..3)                                */
     int n_slabs;    /* N time slabs of width T / N                                           */
     double T, nu, conv;
     int kind;       /* WR_TAYLOR_GREEN, WR_POLY, WR_FOURIER, WR_LID, WR_HEAT or WR_HEAT_EIGEN */

@@ -1,7 +1,8 @@
 // Heat-equation waveform relaxation on the GPU (Def. heat, Sec. 3, Sec. 5).
 //
-// u_t - nu lap u = 0 with natural boundary conditions, DG(q) in time (right-Radau
-// Lagrange basis), continuous Q_k (k = 1, 2, 3) on an n x n mesh.  One scalar
+// u_t - nu lap u = 0 with natural boundary conditions, DG(q) in time (q = 0..3,
+// right-Radau Lagrange basis), continuous Q_k (k = 1, 2, 3) on an n x n mesh (the
+// degrees of the paper's heat experiments, Sec. 5).  One scalar
 // field per temporal DoF: the canonical index is (slab (q+1) + a) S + y nv + x with
 // nv = n k + 1, S = nv^2.  Every operator is a tensor product of global 1D
 // matrices on the Cartesian mesh:
@@ -11,8 +12,8 @@
 // vertex (I, J) holds the nodes of its open star, a (2k-1)^2 window starting at
 // node ((I-1)k+1, (J-1)k+1) (clipped to the domain); its slab blocks are the
 // principal submatrices of J, inverted per (patch, slab) and applied by forward
-// substitution over slabs.  The coarsest level (2x2 cells) is one block holding
-// every node.  Levels coarsen in space only; transfers are the tensor products of
+// substitution over slabs.  The coarsest level (2x2 cells, or 1x1 where the 2x2
+// block would not fit in shared memory) is one block holding every node.  Levels coarsen in space only; transfers are the tensor products of
 // the 1D degree-k Lagrange interpolation.
 #include "wrmg_internal.h"
 
@@ -82,11 +83,12 @@ __global__ void heat_op_kernel(LevelGeom g, FeTables T, PhysParams ph, const dou
 }
 
 // Block layout: PX x PX node window per temporal DoF, slot = a PX^2 + ly PX + lx;
-// slots outside the domain are padding (identity rows and columns).
-template <int K, int PX>
+// slots outside the domain are padding (identity rows and columns).  WHOLE: the
+// block of the coarsest level (PX = n k + 1, every node); else a vertex-star patch.
+template <int K, int PX, bool WHOLE>
 struct HeatBlock {
   __device__ static void origin(const LevelGeom& g, int blk, int& x0, int& y0) {
-    if (PX == 2 * K - 1) {  // vertex-star patch
+    if (!WHOLE) {  // vertex-star patch
       const int I = blk % (g.n + 1), J = blk / (g.n + 1);
       x0 = (I - 1) * K + 1;
       y0 = (J - 1) * K + 1;
@@ -98,7 +100,7 @@ struct HeatBlock {
 
 // Inverts the slab block of (block, slab): assembled in shared memory, Gauss-Jordan
 // with partial pivoting (largest |.|, lowest row on ties), stored column-major.
-template <int K, int Q, int PX, int NTH>
+template <int K, int Q, int PX, bool WHOLE, int NTH>
 __global__ void __launch_bounds__(NTH) heat_factor_kernel(LevelGeom g, FeTables T, PhysParams ph,
                                                           double* __restrict__ factors, int* __restrict__ status) {
   constexpr int NT = Q + 1, P2 = PX * PX, M = NT * P2;
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(NTH) heat_factor_kernel(LevelGeom g, FeTables 
   __shared__ int piv;
   const int blk = blockIdx.x, slab = blockIdx.y, tid = threadIdx.x;
   int x0, y0;
-  HeatBlock<K, PX>::origin(g, blk, x0, y0);
+  HeatBlock<K, PX, WHOLE>::origin(g, blk, x0, y0);
   const int nv = g.nv;
   const double h = g.h, ih = 1.0 / h, cdt = g.dt * ph.nu;
   for (int e = tid; e < M * M; e += NTH) {
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(NTH) heat_factor_kernel(LevelGeom g, FeTables 
 // Forward substitution over slabs for one block per CTA: rhs = r_n - L y_{n-1},
 // y_n = A_nn^{-1} rhs; L = -tau(0) (x) M restricted to the block's nodes.
 // Patches write [slab][block][slot] outputs; the coarse block writes the solution.
-template <int K, int Q, int PX, int NTH>
+template <int K, int Q, int PX, bool WHOLE, int NTH>
 __global__ void __launch_bounds__(NTH) heat_apply_kernel(LevelGeom g, FeTables T, const double* __restrict__ factors,
                                                          const double* __restrict__ r, double* __restrict__ out,
                                                          int nblk) {
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(NTH) heat_apply_kernel(LevelGeom g, FeTables T
   __shared__ int node[P2];
   const int blk = blockIdx.x, tid = threadIdx.x;
   int x0, y0;
-  HeatBlock<K, PX>::origin(g, blk, x0, y0);
+  HeatBlock<K, PX, WHOLE>::origin(g, blk, x0, y0);
   const int nv = g.nv;
   for (int s = tid; s < P2; s += NTH) {
     const int ix = x0 + s % PX, iy = y0 + s / PX;
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(NTH) heat_apply_kernel(LevelGeom g, FeTables T
     __syncthreads();
     for (int i = tid; i < M; i += NTH) {
       const int a = i / P2, si = i % P2;
-      if (PX == 2 * K - 1) {
+      if (!WHOLE) {
         out[((int64_t)slab * nblk + blk) * M + i] = yv[i];
       } else if (node[si] >= 0) {
         out[((int64_t)slab * NT + a) * g.S + node[si]] = yv[i];
@@ -334,30 +336,43 @@ __global__ void heat_patch_slots_kernel(LevelGeom g, int blk, int* __restrict__ 
   const int s = threadIdx.x;
   if (s >= PX * PX) return;
   int x0, y0;
-  HeatBlock<K, PX>::origin(g, blk, x0, y0);
+  HeatBlock<K, PX, false>::origin(g, blk, x0, y0);
   const int ix = x0 + s % PX, iy = y0 + s / PX;
   out[s] = (ix >= 0 && ix < g.nv && iy >= 0 && iy < g.nv) ? iy * g.nv + ix : -1;
 }
 
 unsigned grid_of(int64_t n) { return (unsigned)((n + 255) / 256); }
 
-template <int K, int Q, int PX>
+// The factor kernel holds one M x M FP64 block (+ a column) in shared memory.
+constexpr size_t kHeatSmemLimit = 227 * 1024;
+constexpr size_t heat_factor_smem(int m) { return sizeof(double) * ((size_t)m * m + m); }
+constexpr int heat_threads(int m) { return m <= 32 ? 32 : (m <= 64 ? 64 : (m <= 128 ? 128 : 256)); }
+
+template <int K, int Q, int PX, bool WHOLE>
 void run_heat_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph, int nblk, double* f, int* st,
                      cudaStream_t s) {
-  constexpr int M = (Q + 1) * PX * PX, NTH = M <= 32 ? 32 : (M <= 64 ? 64 : 128);
-  const size_t smem = sizeof(double) * ((size_t)M * M + M);
-  auto kern = heat_factor_kernel<K, Q, PX, NTH>;
-  WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<dim3(nblk, g.N), NTH, smem, s>>>(g, T, ph, f, st);
-  WR_LAUNCH_CHECK();
+  constexpr int M = (Q + 1) * PX * PX, NTH = heat_threads(M);
+  if constexpr (heat_factor_smem(M) > kHeatSmemLimit) {
+    throw WrError(WR_ERR_ARG, "heat: the coarse block does not fit in shared memory (use a 1x1 coarsest mesh)");
+  } else {
+    const size_t smem = heat_factor_smem(M);
+    auto kern = heat_factor_kernel<K, Q, PX, WHOLE, NTH>;
+    WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<dim3(nblk, g.N), NTH, smem, s>>>(g, T, ph, f, st);
+    WR_LAUNCH_CHECK();
+  }
 }
 
-template <int K, int Q, int PX>
+template <int K, int Q, int PX, bool WHOLE>
 void run_heat_apply(const LevelGeom& g, const FeTables& T, const double* f, const double* r, double* out, int nblk,
                     cudaStream_t s) {
-  constexpr int M = (Q + 1) * PX * PX, NTH = M <= 32 ? 32 : (M <= 64 ? 64 : 128);
-  heat_apply_kernel<K, Q, PX, NTH><<<nblk, NTH, 0, s>>>(g, T, f, r, out, nblk);
-  WR_LAUNCH_CHECK();
+  constexpr int M = (Q + 1) * PX * PX, NTH = heat_threads(M);
+  if constexpr (heat_factor_smem(M) > kHeatSmemLimit) {
+    throw WrError(WR_ERR_ARG, "heat: the coarse block does not fit in shared memory (use a 1x1 coarsest mesh)");
+  } else {
+    heat_apply_kernel<K, Q, PX, WHOLE, NTH><<<nblk, NTH, 0, s>>>(g, T, f, r, out, nblk);
+    WR_LAUNCH_CHECK();
+  }
 }
 
 }  // namespace
@@ -374,10 +389,12 @@ LevelGeom make_heat_geom(int n, int k, int q, int N, double T) {
   return g;
 }
 
-int heat_block_size(int k, int q, bool coarse) {
-  const int px = coarse ? 2 * k + 1 : 2 * k - 1;
+int heat_block_size(int k, int q, int n_whole) {
+  const int px = n_whole > 0 ? n_whole * k + 1 : 2 * k - 1;
   return (q + 1) * px * px;
 }
+
+bool heat_block_fits(int k, int q, int n_whole) { return heat_factor_smem(heat_block_size(k, q, n_whole)) <= kHeatSmemLimit; }
 
 #define HEAT_KQ(stmt)                                                       \
   if (g.k == 1 && g.q == 0) { constexpr int K = 1, Q = 0; stmt; }           \
@@ -386,7 +403,13 @@ int heat_block_size(int k, int q, bool coarse) {
   else if (g.k == 2 && g.q == 1) { constexpr int K = 2, Q = 1; stmt; }      \
   else if (g.k == 3 && g.q == 0) { constexpr int K = 3, Q = 0; stmt; }      \
   else if (g.k == 3 && g.q == 1) { constexpr int K = 3, Q = 1; stmt; }      \
-  else throw WrError(WR_ERR_ARG, "heat: k must be 1..3 and q 0 or 1");
+  else if (g.k == 1 && g.q == 2) { constexpr int K = 1, Q = 2; stmt; }      \
+  else if (g.k == 1 && g.q == 3) { constexpr int K = 1, Q = 3; stmt; }      \
+  else if (g.k == 2 && g.q == 2) { constexpr int K = 2, Q = 2; stmt; }      \
+  else if (g.k == 2 && g.q == 3) { constexpr int K = 2, Q = 3; stmt; }      \
+  else if (g.k == 3 && g.q == 2) { constexpr int K = 3, Q = 2; stmt; }      \
+  else if (g.k == 3 && g.q == 3) { constexpr int K = 3, Q = 3; stmt; }      \
+  else throw WrError(WR_ERR_ARG, "heat: k must be 1..3 and q 0..3");
 
 void heat_jacobian(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* x, double* y,
                    cudaStream_t s) {
@@ -403,10 +426,14 @@ void heat_residual(const LevelGeom& g, const FeTables& T, const PhysParams& ph, 
 void heat_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph, bool coarse, double* f, int* st,
                  cudaStream_t s) {
   WR_CUDA(cudaMemsetAsync(st, 0, sizeof(int), s));
-  if (coarse) {
-    HEAT_KQ((run_heat_factor<K, Q, 2 * K + 1>(g, T, ph, 1, f, st, s)));
+  if (coarse && g.n == 2) {
+    HEAT_KQ((run_heat_factor<K, Q, 2 * K + 1, true>(g, T, ph, 1, f, st, s)));
+  } else if (coarse && g.n == 1) {
+    HEAT_KQ((run_heat_factor<K, Q, K + 1, true>(g, T, ph, 1, f, st, s)));
+  } else if (coarse) {
+    throw WrError(WR_ERR_ARG, "heat: the coarsest mesh must be 1x1 or 2x2");
   } else {
-    HEAT_KQ((run_heat_factor<K, Q, 2 * K - 1>(g, T, ph, g.npatch(), f, st, s)));
+    HEAT_KQ((run_heat_factor<K, Q, 2 * K - 1, false>(g, T, ph, g.npatch(), f, st, s)));
   }
   int h = 0;
   WR_CUDA(cudaMemcpyAsync(&h, st, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -416,14 +443,20 @@ void heat_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph, bo
 
 void heat_patch_apply(const LevelGeom& g, const FeTables& T, const double* f, const double* r, double* Yp, double* y,
                       cudaStream_t s) {
-  HEAT_KQ((run_heat_apply<K, Q, 2 * K - 1>(g, T, f, r, Yp, g.npatch(), s)));
+  HEAT_KQ((run_heat_apply<K, Q, 2 * K - 1, false>(g, T, f, r, Yp, g.npatch(), s)));
   HEAT_KQ((heat_scatter_kernel<K, Q><<<grid_of(g.ndofs), 256, 0, s>>>(g, Yp, y)));
   WR_LAUNCH_CHECK();
 }
 
 void heat_coarse_apply(const LevelGeom& g, const FeTables& T, const double* f, const double* b, double* x,
                        cudaStream_t s) {
-  HEAT_KQ((run_heat_apply<K, Q, 2 * K + 1>(g, T, f, b, x, 1, s)));
+  if (g.n == 2) {
+    HEAT_KQ((run_heat_apply<K, Q, 2 * K + 1, true>(g, T, f, b, x, 1, s)));
+  } else if (g.n == 1) {
+    HEAT_KQ((run_heat_apply<K, Q, K + 1, true>(g, T, f, b, x, 1, s)));
+  } else {
+    throw WrError(WR_ERR_ARG, "heat: the coarsest mesh must be 1x1 or 2x2");
+  }
 }
 
 void heat_restrict(const LevelGeom& gf, const LevelGeom& gc, const FeTables& T, const double* xf, double* xc,

@@ -753,7 +753,7 @@ static int create_heat(wr_ctx* c, const wr_problem* p) {
   c->opt.store_factors = WR_STORE;
   c->opt.autotune = 0;
   c->tab = build_tables(p->k - 1, p->q);  // the degree-k tables are the Navier-Stokes velocity ones of k - 1
-  const int m = heat_block_size(p->k, p->q, false), mc = heat_block_size(p->k, p->q, true);
+  const int m = heat_block_size(p->k, p->q, 0), mc = heat_block_size(p->k, p->q, p->n_coarse);
   size_t max_yp = 1;
   for (int n = p->n_coarse; n <= p->n_fine; n *= 2) {
     Level lv;
@@ -810,9 +810,15 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
   int rc = guarded(c, [&]() -> int {
     const bool heat = p->kind == WR_HEAT || p->kind == WR_HEAT_EIGEN;
     need(p->k == 1 || p->k == 2 || (heat && p->k == 3), "k must be 1 or 2 (1, 2 or 3 for the heat equation)");
-    need(!heat || p->n_coarse == 2, "the heat equation coarsens to 2x2");
-    need(p->q == 0 || p->q == 1, "q must be 0 or 1");
-    need(p->n_coarse == 2 || (p->n_coarse == 3 && p->k == 1), "n_coarse must be 2 (or 3 for k = 1)");
+    need(heat ? (p->q >= 0 && p->q <= 3) : (p->q == 0 || p->q == 1),
+         "q must be 0 or 1 (0..3 for the heat equation)");
+    if (heat) {
+      need(p->n_coarse == 1 || p->n_coarse == 2, "the heat equation coarsens to 1x1 or 2x2");
+      need(heat_block_fits(p->k, p->q, p->n_coarse),
+           "the coarse heat block does not fit in shared memory: coarsen to 1x1");
+    } else {
+      need(p->n_coarse == 2 || (p->n_coarse == 3 && p->k == 1), "n_coarse must be 2 (or 3 for k = 1)");
+    }
     need(p->n_fine >= 4 && p->n_fine <= 4096, "n_fine out of range");
     need(p->n_slabs >= 1 && p->T > 0.0, "need n_slabs >= 1 and T > 0");
     int nf = p->n_fine;

@@ -115,7 +115,7 @@ FeTables build_tables(int k, int q) {
   }
   // time
   radau01(q, T.tnode);
-  double tx[WR_MAX_NQ], tw[WR_MAX_NQ];
+  double tx[WR_MAX_NT + 2], tw[WR_MAX_NT + 2];
   const int ntg = q + 3;  // exact for the degree-3q integrands below
   gauss01(ntg, tx, tw);
   double v0[WR_MAX_NT];

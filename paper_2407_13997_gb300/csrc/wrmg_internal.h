@@ -17,12 +17,13 @@
 #define WR_HD
 #endif
 
-// Compile-time bounds: k <= 2 (Q3/Q2), q <= 1 (DG(1)).
+// Compile-time bounds: Navier-Stokes k <= 2 (Q3/Q2) and q <= 1 (DG(1)); the heat
+// equation k <= 3 (Q3) and q <= 3 (DG(3)).
 #define WR_MAX_NQ 5   // Gauss points per direction, k + 3
 #define WR_MAX_NVL 4  // velocity nodes per cell and direction, k + 2
 #define WR_MAX_NPL 3  // pressure nodes per cell and direction, k + 1
-#define WR_MAX_NT 2   // temporal DoFs per slab, q + 1
-#define WR_MAX_NTQ 3  // Gauss points in time for the forcing, q + 2
+#define WR_MAX_NT 4   // temporal DoFs per slab, q + 1
+#define WR_MAX_NTQ 5  // Gauss points in time for the forcing, q + 2
 
 struct WrError : std::runtime_error {
   int code;
@@ -314,7 +315,8 @@ int tune_apply_variant(const TuneKey& key, cudaStream_t s, const std::function<v
 
 // ---------------------------------------------------------------- heat equation (heat.cu)
 LevelGeom make_heat_geom(int n, int k, int q, int N, double T);
-int heat_block_size(int k, int q, bool coarse);  // slots per (block, slab): (q+1) PX^2
+int heat_block_size(int k, int q, int n_whole);  // slots per (block, slab): (q+1) PX^2; n_whole = 0: a patch
+bool heat_block_fits(int k, int q, int n_whole);  // the block's FP64 inversion fits in shared memory
 void heat_jacobian(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* x, double* y,
                    cudaStream_t s);
 void heat_residual(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* x, double* y,

@@ -82,11 +82,14 @@ def lid_cavity(n=16, k=1, q=0, N=20, R=10.0, T=0.02):
     return Workload(f"lid_R{R:g}_q{k + 1}q{k}_dg{q}_n{n}_N{N}", n, 2, k, q, N, T, 1.0, R, KIND_LID)
 
 
-def heat(n=16, k=1, q=0, N=20, nu=1.0, T=0.02, eigen=False):
+def heat(n=16, k=1, q=0, N=20, nu=1.0, T=0.02, eigen=False, n_coarse=None):
     """The heat equation of Sec. 5: u_t - nu lap u = 0, natural boundary conditions,
-    u(0) = sin(pi x) + cos(2 pi y) (eigen: cos(pi x)), t in [0, T], Q_k x DG(q), N slabs,
-    n x n mesh coarsened to 2 x 2."""
-    return Workload(f"heat_q{k}_dg{q}_n{n}_N{N}", n, 2, k, q, N, T, nu, 0.0,
+    u(0) = sin(pi x) + cos(2 pi y) (eigen: cos(pi x)), t in [0, T], Q_k x DG(q) (k = 1..3,
+    q = 0..3), N slabs, n x n mesh coarsened to 2 x 2 (1 x 1 for k = q = 3, whose 2 x 2
+    coarse block is too large for the GPU's direct solve)."""
+    if n_coarse is None:
+        n_coarse = 1 if (k == 3 and q == 3) else 2
+    return Workload(f"heat_q{k}_dg{q}_n{n}_N{N}", n, n_coarse, k, q, N, T, nu, 0.0,
                     KIND_HEAT_EIGEN if eigen else KIND_HEAT)
 
 

@@ -87,3 +87,25 @@ def test_store_or_recompute_plan_on_the_host(libpath):
     auto = est(store_factors=wrmg.WR_STORE_AUTO, memory_budget_mb=mib(mid), recompute_slabs=4)
     assert rec <= auto <= mid + (1 << 20)
     assert est(store_factors=wrmg.WR_STORE_AUTO, memory_budget_mb=1, recompute_slabs=4) == rec
+
+
+def test_heat_degrees_and_coarse_mesh_checks_on_the_host(libpath):
+    """The heat equation takes Q_k x DG(q) for k = 1..3, q = 0..3 (Sec. 5); its stored
+    factors are one (q+1)(2k-1)^2 block per patch and slab, FP64.  The k = q = 3 coarse
+    block of a 2x2 mesh (196 x 196) does not fit the direct solve and is refused; the 1x1
+    coarse mesh is taken instead.  Navier-Stokes stays at q <= 1."""
+    from paper_2407_13997_gb300 import inputs, wrmg
+    for k in (1, 2, 3):
+        for q in (0, 1, 2, 3):
+            w = inputs.heat(n=16, k=k, q=q, N=4)
+            m = (q + 1) * (2 * k - 1) ** 2
+            fine_factors = 17 * 17 * 4 * m * m * 8
+            assert wrmg.estimate_bytes(w) > fine_factors
+    assert inputs.heat(k=3, q=3).n_coarse == 1
+    bad = inputs.heat(n=16, k=3, q=3, N=4, n_coarse=2)
+    with pytest.raises(wrmg.WrmgError):
+        wrmg.estimate_bytes(bad)
+    ns = inputs.fourier_small(n=8, k=1, q=0, N=3)
+    ns.q = 2
+    with pytest.raises(wrmg.WrmgError):
+        wrmg.estimate_bytes(ns)

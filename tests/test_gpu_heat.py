@@ -2,7 +2,7 @@
 patch index tables bit-exact, operator and transfers 1e-12/1e-13, smoother,
 coarse solve, eigen-estimates and V-cycle 1e-10, the FGMRES-WRMG solve with the
 same iteration count and 1e-10 on the solution, and the timestepping comparator
-equal to the all-at-once solve."""
+equal to the all-at-once solve; Q_k (k = 1..3) x DG(q) (q = 0..3)."""
 import dataclasses
 
 import numpy as np
@@ -17,7 +17,11 @@ from oracle.solver import Options
 from paper_2407_13997_gb300 import inputs, wrmg
 
 CASES = [inputs.heat(n=8, k=1, q=0, N=5), inputs.heat(n=8, k=2, q=1, N=4), inputs.heat(n=4, k=3, q=1, N=3),
-         inputs.heat(n=8, k=3, q=0, N=3, eigen=True)]
+         inputs.heat(n=8, k=3, q=0, N=3, eigen=True),
+         # DG(2) and DG(3) in time (Sec. 5's temporal degrees); k = q = 3 coarsens to 1x1,
+         # k = 3, q = 2 takes the largest 2x2 coarse block (147 x 147)
+         inputs.heat(n=8, k=1, q=2, N=3), inputs.heat(n=4, k=2, q=3, N=3), inputs.heat(n=4, k=3, q=3, N=2),
+         inputs.heat(n=4, k=3, q=2, N=2)]
 IDS = [w.name + ("_eig" if w.kind == inputs.KIND_HEAT_EIGEN else "") for w in CASES]
 
 

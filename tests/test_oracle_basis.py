@@ -15,6 +15,19 @@ def test_radau_nodes_match_textbook_abscissae():
     assert np.allclose(radau_right_nodes(2), [(4 - s6) / 10, (4 + s6) / 10, 1.0], atol=1e-14)
 
 
+def test_radau_nodes_integrate_to_degree_2q():
+    """The (q+1)-point right-Radau rule (weights from the Lagrange basis) integrates
+    polynomials of degree 2q exactly on [0, 1] and no higher (Hairer & Wanner, Sec. IV.5)."""
+    for q in range(4):
+        nodes = radau_right_nodes(q)
+        xs, ws = gauss_legendre(q + 2)
+        V, _ = lagrange(nodes, xs)
+        w = V @ ws                      # int of each Lagrange basis function
+        for d in range(2 * q + 1):
+            assert abs(w @ nodes ** d - 1.0 / (d + 1)) < 1e-13, (q, d)
+        assert abs(w @ nodes ** (2 * q + 1) - 1.0 / (2 * q + 2)) > 1e-6, q
+
+
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_lagrange_reproduces_polynomials_and_derivatives(p):
     rng = np.random.default_rng(p)
@@ -45,7 +58,7 @@ def pade_stability(j, k, z):
     return num / den
 
 
-@pytest.mark.parametrize("q", [0, 1, 2])
+@pytest.mark.parametrize("q", [0, 1, 2, 3])
 def test_dg_in_time_end_value_is_radau_iia_stability_function(q):
     """For y' = lam y the DG(q) slab system (Eq. dgintime) reads
     (Kt - z Wt) U = tau(0) y0 with z = lam dt; its end value U_q must be the
