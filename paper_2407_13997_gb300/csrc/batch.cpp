@@ -381,10 +381,10 @@ struct wr_batch {
                               cudaMemcpyDeviceToDevice, s));
       for (int l = M.L; l >= 1; --l) launch_inject(M.g[l], M.g[l - 1], M.W[l], M.W[l - 1], s);
       for (int l = 1; l <= M.L; ++l) {
-        if (M.ph.conv != 0.0) launch_conv_elements(M.g[l], tab, M.W[l], Ce, s);
+        if (M.ph.conv != 0.0) launch_conv_elements(M.g[l], tab, M.W[l], Ce, opt.precision, s);
         launch_block_factor(M.g[l], tab, M.ph, patch_set(), Ce, M.factors[l], opt.precision, fstat, s);
       }
-      if (M.ph.conv != 0.0) launch_conv_elements(M.g[0], tab, M.W[0], Ce, s);
+      if (M.ph.conv != 0.0) launch_conv_elements(M.g[0], tab, M.W[0], Ce, WR_FP64, s);
       launch_block_factor(M.g[0], tab, M.ph, M.cbs, Ce, M.cf, WR_FP64, fstat, s);
     }
     build_tables();

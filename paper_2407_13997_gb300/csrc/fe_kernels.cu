@@ -678,15 +678,38 @@ __global__ void bt_boundary_kernel(const BatchSeg* __restrict__ segs, int nseg, 
 
 // Element convection matrices about W (per time DoF e of W):
 //   Ce[slab][cell][e][c*2+d][i][j] = int phi_i [ delta_cd (W_e.grad) phi_j + phi_j d_d W_{e,c} ]
-template <int K, int Q>
+// One warp per (cell, slab).  W and its gradient are interpolated to the Gauss
+// points by sum factorisation; the matrices are sum-factorised too: with
+// phi_i = b_ix(x) b_iy(y) every integrand is a weight product in x times one in y
+// times a field F at the quadrature point, so the x sums come first,
+//   P_F[ix][jx][qy] = sum_qx w_qx b_ix(qx) c_jx(qx) F(qx, qy)   (c = b', or b),
+// and each entry is then a sum over qy (NQ terms instead of NQ^2 per entry).
+// CT is the arithmetic and storage type: double for the FP64 factorisation, float
+// for the FP32/BF16 ones (whose blocks are assembled in FP32).
+template <int K, int Q, typename CT>
 __global__ void __launch_bounds__(32 * kWarps)
-conv_elements_kernel(LevelGeom g, FeTables T, const double* __restrict__ W, double* __restrict__ Ce) {
+conv_elements_kernel(LevelGeom g, FeTables T, const double* __restrict__ W, CT* __restrict__ Ce) {
   using d = D<K, Q>;
+  constexpr int NT = d::NT, NVL = d::NVL, NQ = d::NQ, NVE = d::NVE, NQ2 = d::NQ2;
   struct Sm {
-    double wn[2 * d::NT][d::NVE];
-    double t1[2 * d::NT][2][d::NVL][d::NQ];
-    double wq[2 * d::NT][3][d::NQ2];
+    CT wn[2 * NT][NVE];
+    CT t1[2 * NT][2][NVL][NQ];
+    CT wq[2 * NT][3][NQ2];
+    CT P[6][NVL][NVL][NQ];
   };
+  __shared__ CT bv[NQ][NVL], dv[NQ][NVL];
+  __shared__ CT ww[2][NVL][NVL][NQ];  // w_q b_i(q) b'_j(q) and w_q b_i(q) b_j(q)
+  for (int e = threadIdx.x; e < NQ * NVL; e += blockDim.x) {
+    const int q = e / NVL, i = e % NVL;
+    bv[q][i] = (CT)T.Bv[q][i];
+    dv[q][i] = (CT)T.Dv[q][i];
+  }
+  for (int e = threadIdx.x; e < NVL * NVL * NQ; e += blockDim.x) {
+    const int i = e / (NVL * NQ), j = (e / NQ) % NVL, q = e % NQ;
+    ww[0][i][j][q] = (CT)(T.wq[q] * T.Bv[q][i] * T.Dv[q][j]);
+    ww[1][i][j][q] = (CT)(T.wq[q] * T.Bv[q][i] * T.Bv[q][j]);
+  }
+  __syncthreads();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Sm& s = reinterpret_cast<Sm*>(smem_raw)[threadIdx.x / 32];
   const int lane = threadIdx.x & 31;
@@ -696,67 +719,79 @@ conv_elements_kernel(LevelGeom g, FeTables T, const double* __restrict__ W, doub
   const int CI = cell % g.n, CJ = cell / g.n;
   const int nv = g.nv;
   const int64_t nv2 = (int64_t)nv * nv;
-  const double h = g.h, ih = 1.0 / h;
-  for (int it = lane; it < 2 * d::NT * d::NVE; it += 32) {
-    const int f = it / d::NVE, l = it % d::NVE;  // f = c*NT + e
-    const int c = f / d::NT, e = f % d::NT;
-    const int gx = CI * (K + 1) + l % d::NVL, gy = CJ * (K + 1) + l / d::NVL;
-    s.wn[f][l] = W[((int64_t)slab * d::NT + e) * g.S + c * nv2 + (int64_t)gy * nv + gx];
+  const CT h = (CT)g.h, ih = (CT)(1.0 / g.h);
+  for (int it = lane; it < 2 * NT * NVE; it += 32) {
+    const int f = it / NVE, l = it % NVE;  // f = c*NT + e
+    const int c = f / NT, e = f % NT;
+    const int gx = CI * (K + 1) + l % NVL, gy = CJ * (K + 1) + l / NVL;
+    s.wn[f][l] = (CT)W[((int64_t)slab * NT + e) * g.S + c * nv2 + (int64_t)gy * nv + gx];
   }
   __syncwarp();
-  for (int it = lane; it < 2 * d::NT * d::NVL * d::NQ; it += 32) {
-    const int f = it / (d::NVL * d::NQ), r = it % (d::NVL * d::NQ);
-    const int j = r / d::NQ, qx = r % d::NQ;
-    double v = 0.0, dv = 0.0;
-    for (int i = 0; i < d::NVL; ++i) {
-      v = fma(T.Bv[qx][i], s.wn[f][j * d::NVL + i], v);
-      dv = fma(T.Dv[qx][i], s.wn[f][j * d::NVL + i], dv);
+  for (int it = lane; it < 2 * NT * NVL * NQ; it += 32) {
+    const int f = it / (NVL * NQ), r = it % (NVL * NQ);
+    const int j = r / NQ, qx = r % NQ;
+    CT v = 0, dvv = 0;
+    for (int i = 0; i < NVL; ++i) {
+      v = fma(bv[qx][i], s.wn[f][j * NVL + i], v);
+      dvv = fma(dv[qx][i], s.wn[f][j * NVL + i], dvv);
     }
     s.t1[f][0][j][qx] = v;
-    s.t1[f][1][j][qx] = dv;
+    s.t1[f][1][j][qx] = dvv;
   }
   __syncwarp();
-  for (int it = lane; it < 2 * d::NT * d::NQ2; it += 32) {
-    const int f = it / d::NQ2, q = it % d::NQ2;
-    const int qy = q / d::NQ, qx = q % d::NQ;
-    double v = 0.0, vx = 0.0, vy = 0.0;
-    for (int j = 0; j < d::NVL; ++j) {
-      v = fma(T.Bv[qy][j], s.t1[f][0][j][qx], v);
-      vx = fma(T.Bv[qy][j], s.t1[f][1][j][qx], vx);
-      vy = fma(T.Dv[qy][j], s.t1[f][0][j][qx], vy);
+  for (int it = lane; it < 2 * NT * NQ2; it += 32) {
+    const int f = it / NQ2, q = it % NQ2;
+    const int qy = q / NQ, qx = q % NQ;
+    CT v = 0, vx = 0, vy = 0;
+    for (int j = 0; j < NVL; ++j) {
+      v = fma(bv[qy][j], s.t1[f][0][j][qx], v);
+      vx = fma(bv[qy][j], s.t1[f][1][j][qx], vx);
+      vy = fma(dv[qy][j], s.t1[f][0][j][qx], vy);
     }
     s.wq[f][0][q] = v;
     s.wq[f][1][q] = vx * ih;
     s.wq[f][2][q] = vy * ih;
   }
   __syncwarp();
-  double* dst = Ce + ((int64_t)slab * g.ncells() + cell) * (d::NT * 4 * d::NVE * d::NVE);
-  for (int it = lane; it < d::NT * d::NVE * d::NVE; it += 32) {
-    const int e = it / (d::NVE * d::NVE), r = it % (d::NVE * d::NVE);
-    const int i = r / d::NVE, j = r % d::NVE;
-    const int iy = i / d::NVL, ix = i % d::NVL, jy = j / d::NVL, jx = j % d::NVL;
-    double adv = 0.0, b00 = 0.0, b01 = 0.0, b10 = 0.0, b11 = 0.0;
-    for (int qy = 0; qy < d::NQ; ++qy)
-      for (int qx = 0; qx < d::NQ; ++qx) {
-        const int q = qy * d::NQ + qx;
-        const double om = T.wq[qx] * T.wq[qy] * h * h;
-        const double phi_i = T.Bv[qx][ix] * T.Bv[qy][iy];
-        const double phi_j = T.Bv[qx][jx] * T.Bv[qy][jy];
-        const double djx = T.Dv[qx][jx] * T.Bv[qy][jy] * ih;
-        const double djy = T.Bv[qx][jx] * T.Dv[qy][jy] * ih;
-        const double wi = om * phi_i;
-        const double wij = wi * phi_j;
-        adv = fma(wi, s.wq[0 * d::NT + e][0][q] * djx + s.wq[1 * d::NT + e][0][q] * djy, adv);
-        b00 = fma(wij, s.wq[0 * d::NT + e][1][q], b00);  // d_x W_x
-        b01 = fma(wij, s.wq[0 * d::NT + e][2][q], b01);  // d_y W_x
-        b10 = fma(wij, s.wq[1 * d::NT + e][1][q], b10);  // d_x W_y
-        b11 = fma(wij, s.wq[1 * d::NT + e][2][q], b11);  // d_y W_y
+  CT* dst = Ce + ((int64_t)slab * g.ncells() + cell) * (NT * 4 * NVE * NVE);
+  for (int e = 0; e < NT; ++e) {
+    // x sums; fields: 0 W_x (against b'_jx), 1 W_y, 2 d_x W_x, 3 d_y W_x, 4 d_x W_y, 5 d_y W_y
+    for (int it = lane; it < 6 * NVL * NVL * NQ; it += 32) {
+      const int f = it / (NVL * NVL * NQ), r = it % (NVL * NVL * NQ);
+      const int ix = r / (NVL * NQ), jx = (r / NQ) % NVL, qy = r % NQ;
+      const int c = f == 0 ? 0 : f == 1 ? 1 : (f - 2) / 2;
+      const int comp = f < 2 ? 0 : 1 + (f - 2) % 2;
+      const CT* fld = &s.wq[c * NT + e][comp][qy * NQ];
+      const CT* wt = &ww[f == 0 ? 0 : 1][ix][jx][0];
+      CT acc = 0;
+#pragma unroll
+      for (int qx = 0; qx < NQ; ++qx) acc = fma(wt[qx], fld[qx], acc);
+      s.P[f][ix][jx][qy] = acc;
+    }
+    __syncwarp();
+    CT* m = dst + (int64_t)e * 4 * NVE * NVE;
+    for (int it = lane; it < NVE * NVE; it += 32) {
+      const int i = it / NVE, j = it % NVE;
+      const int iy = i / NVL, ix = i % NVL, jy = j / NVL, jx = j % NVL;
+      CT adv = 0, b00 = 0, b01 = 0, b10 = 0, b11 = 0;
+#pragma unroll
+      for (int qy = 0; qy < NQ; ++qy) {
+        const CT wb = ww[1][iy][jy][qy], wd = ww[0][iy][jy][qy];
+        adv = fma(wb, s.P[0][ix][jx][qy], fma(wd, s.P[1][ix][jx][qy], adv));
+        b00 = fma(wb, s.P[2][ix][jx][qy], b00);
+        b01 = fma(wb, s.P[3][ix][jx][qy], b01);
+        b10 = fma(wb, s.P[4][ix][jx][qy], b10);
+        b11 = fma(wb, s.P[5][ix][jx][qy], b11);
       }
-    double* m = dst + (int64_t)e * 4 * d::NVE * d::NVE;
-    m[0 * d::NVE * d::NVE + r] = adv + b00;
-    m[1 * d::NVE * d::NVE + r] = b01;
-    m[2 * d::NVE * d::NVE + r] = b10;
-    m[3 * d::NVE * d::NVE + r] = adv + b11;
+      // cell weights: h^2 for the area, 1/h for the derivative of phi_j in the advection
+      adv *= h;
+      const CT h2 = h * h;
+      m[0 * NVE * NVE + it] = adv + h2 * b00;
+      m[1 * NVE * NVE + it] = h2 * b01;
+      m[2 * NVE * NVE + it] = h2 * b10;
+      m[3 * NVE * NVE + it] = adv + h2 * b11;
+    }
+    __syncwarp();
   }
 }
 
@@ -803,11 +838,12 @@ void dispatch_element(const LevelGeom& g, const FeTables& T, const PhysParams& p
   else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 }
 
-template <int K, int Q>
-void run_conv(const LevelGeom& g, const FeTables& T, const double* W, double* Ce, cudaStream_t s) {
+template <int K, int Q, typename CT>
+void run_conv(const LevelGeom& g, const FeTables& T, const double* W, CT* Ce, cudaStream_t s) {
   using d = D<K, Q>;
-  const size_t smem = (sizeof(double) * (2 * d::NT * d::NVE + 2 * d::NT * 2 * d::NVL * d::NQ + 2 * d::NT * 3 * d::NQ2)) * kWarps;
-  auto kern = conv_elements_kernel<K, Q>;
+  const size_t smem = sizeof(CT) * (2 * d::NT * d::NVE + 2 * d::NT * 2 * d::NVL * d::NQ + 2 * d::NT * 3 * d::NQ2 +
+                                    6 * d::NVL * d::NVL * d::NQ) * kWarps;
+  auto kern = conv_elements_kernel<K, Q, CT>;
   WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((g.ncells() + kWarps - 1) / kWarps, g.N);
   kern<<<grid, 32 * kWarps, smem, s>>>(g, T, W, Ce);
@@ -921,12 +957,23 @@ void launch_boundary_values(const LevelGeom& g, const FeTables& T, const PhysPar
   WR_LAUNCH_CHECK();
 }
 
-void launch_conv_elements(const LevelGeom& g, const FeTables& T, const double* W, double* Ce, cudaStream_t s) {
-  if (g.k == 1 && g.q == 0) run_conv<1, 0>(g, T, W, Ce, s);
-  else if (g.k == 1 && g.q == 1) run_conv<1, 1>(g, T, W, Ce, s);
-  else if (g.k == 2 && g.q == 0) run_conv<2, 0>(g, T, W, Ce, s);
-  else if (g.k == 2 && g.q == 1) run_conv<2, 1>(g, T, W, Ce, s);
-  else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
+void launch_conv_elements(const LevelGeom& g, const FeTables& T, const double* W, void* Ce, int precision,
+                          cudaStream_t s) {
+  if (precision == WR_FP64) {
+    double* c = static_cast<double*>(Ce);
+    if (g.k == 1 && g.q == 0) run_conv<1, 0>(g, T, W, c, s);
+    else if (g.k == 1 && g.q == 1) run_conv<1, 1>(g, T, W, c, s);
+    else if (g.k == 2 && g.q == 0) run_conv<2, 0>(g, T, W, c, s);
+    else if (g.k == 2 && g.q == 1) run_conv<2, 1>(g, T, W, c, s);
+    else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
+  } else {
+    float* c = static_cast<float*>(Ce);
+    if (g.k == 1 && g.q == 0) run_conv<1, 0>(g, T, W, c, s);
+    else if (g.k == 1 && g.q == 1) run_conv<1, 1>(g, T, W, c, s);
+    else if (g.k == 2 && g.q == 0) run_conv<2, 0>(g, T, W, c, s);
+    else if (g.k == 2 && g.q == 1) run_conv<2, 1>(g, T, W, c, s);
+    else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
+  }
 }
 
 void launch_inject(const LevelGeom& gf, const LevelGeom& gc, const double* Wf, double* Wc, cudaStream_t s) {

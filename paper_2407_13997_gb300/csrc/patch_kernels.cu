@@ -146,46 +146,58 @@ __device__ __forceinline__ double pv1(const double (*ref)[WR_MAX_NVL], int n, in
 // CT is the arithmetic and storage type: double (plain form) or float
 // (precision form; FP32 runs at 58x the FP64 rate on GB300).
 
-template <int K, int NPGX = 2 * K - 1>
+// The threads that build one block: the whole CTA, or one warp of it.
+struct CtaGroup {
+  int t, n;  // this thread's index in the group, group size
+  __device__ void sync() const { __syncthreads(); }
+};
+struct WarpGroup {
+  int t, n;
+  __device__ void sync() const { __syncwarp(); }
+};
+
+// Per-block tables of the global 1D matrices on the slot grid, in the assembly's
+// arithmetic type VT (computed in FP64, rounded once to VT).
+template <int K, int NPGX = 2 * K - 1, typename VT = double>
 struct FactorTables {
   static constexpr int NVG = 2 * K + 3;
   static constexpr int NPT = 2 * K + 1 > NPGX ? 2 * K + 1 : NPGX;  // pressure rows (coarse blocks are larger)
-  double Mx[NVG][NVG], Kx[NVG][NVG], My[NVG][NVG], Ky[NVG][NVG];
-  double Dx[NPT][NVG], Cx[NPT][NVG], Dy[NPT][NVG], Cy[NPT][NVG];
+  VT Mx[NVG][NVG], Kx[NVG][NVG], My[NVG][NVG], Ky[NVG][NVG];
+  VT Dx[NPT][NVG], Cx[NPT][NVG], Dy[NPT][NVG], Cy[NPT][NVG];
   signed char sf[PD<K, NPGX>::MS];                   // slot field 0/1 velocity, 2 pressure, -1 padding
   signed char sx[PD<K, NPGX>::MS], sy[PD<K, NPGX>::MS];  // slot-grid coordinates
 };
 
-template <int K, int NPGX>
+template <int K, int NPGX, typename VT, class Grp>
 __device__ void build_factor_tables(const LevelGeom& g, const FeTables& T, const BlockSet& bs, int blk,
-                                    FactorTables<K, NPGX>& ft, int nth) {
+                                    FactorTables<K, NPGX, VT>& ft, const Grp& gr) {
   using pd = PD<K, NPGX>;
-  using TB = FactorTables<K, NPGX>;
+  using TB = FactorTables<K, NPGX, VT>;
   int vx0, vy0, px0, py0;
   block_origin(g, bs, blk, vx0, vy0, px0, py0);
   const double h = g.h;
   int cx0, cx1, cy0, cy1;
   own_cells(g, bs, vx0, cx0, cx1);
   own_cells(g, bs, vy0, cy0, cy1);
-  for (int e = threadIdx.x; e < TB::NVG * TB::NVG; e += nth) {
+  for (int e = gr.t; e < TB::NVG * TB::NVG; e += gr.n) {
     const int i = e / TB::NVG, j = e % TB::NVG;
     const int xi = min(max(vx0 + i, 0), g.nv - 1), xj = min(max(vx0 + j, 0), g.nv - 1);
     const int yi = min(max(vy0 + i, 0), g.nv - 1), yj = min(max(vy0 + j, 0), g.nv - 1);
-    ft.Mx[i][j] = h * vv1<K>(T.m1, g.n, xi, xj, cx0, cx1);
-    ft.Kx[i][j] = vv1<K>(T.k1, g.n, xi, xj, cx0, cx1) / h;
-    ft.My[i][j] = h * vv1<K>(T.m1, g.n, yi, yj, cy0, cy1);
-    ft.Ky[i][j] = vv1<K>(T.k1, g.n, yi, yj, cy0, cy1) / h;
+    ft.Mx[i][j] = (VT)(h * vv1<K>(T.m1, g.n, xi, xj, cx0, cx1));
+    ft.Kx[i][j] = (VT)(vv1<K>(T.k1, g.n, xi, xj, cx0, cx1) / h);
+    ft.My[i][j] = (VT)(h * vv1<K>(T.m1, g.n, yi, yj, cy0, cy1));
+    ft.Ky[i][j] = (VT)(vv1<K>(T.k1, g.n, yi, yj, cy0, cy1) / h);
   }
-  for (int e = threadIdx.x; e < TB::NPT * TB::NVG; e += nth) {
+  for (int e = gr.t; e < TB::NPT * TB::NVG; e += gr.n) {
     const int p = e / TB::NVG, v = e % TB::NVG;
     const int pxg = min(max(px0 + p, 0), g.np - 1), pyg = min(max(py0 + p, 0), g.np - 1);
     const int vxg = min(max(vx0 + v, 0), g.nv - 1), vyg = min(max(vy0 + v, 0), g.nv - 1);
-    ft.Dx[p][v] = pv1<K>(T.d1, g.n, pxg, vxg);
-    ft.Cx[p][v] = h * pv1<K>(T.c1, g.n, pxg, vxg);
-    ft.Dy[p][v] = pv1<K>(T.d1, g.n, pyg, vyg);
-    ft.Cy[p][v] = h * pv1<K>(T.c1, g.n, pyg, vyg);
+    ft.Dx[p][v] = (VT)pv1<K>(T.d1, g.n, pxg, vxg);
+    ft.Cx[p][v] = (VT)(h * pv1<K>(T.c1, g.n, pxg, vxg));
+    ft.Dy[p][v] = (VT)pv1<K>(T.d1, g.n, pyg, vyg);
+    ft.Cy[p][v] = (VT)(h * pv1<K>(T.c1, g.n, pyg, vyg));
   }
-  for (int s = threadIdx.x; s < pd::MS; s += nth) {
+  for (int s = gr.t; s < pd::MS; s += gr.n) {
     const Slot sl = decode_slot(g, bs, blk, s);
     if (sl.sp < 0) {
       ft.sf[s] = -1;
@@ -203,21 +215,22 @@ __device__ void build_factor_tables(const LevelGeom& g, const FeTables& T, const
 }
 
 // M (+)= constant part of temporal sub-block (a, b); padding rows/columns get the identity on a == b.
-template <int K, int Q, typename CT, int LD, int NTH, int NPGX>
+// Arithmetic in CT (FP64 for the plain form, FP32 for the reduced-precision ones).
+template <int K, int Q, typename CT, int LD, int NPGX, class Grp>
 __device__ void assemble_const(const LevelGeom& g, const FeTables& T, const PhysParams& ph,
-                               const FactorTables<K, NPGX>& ft, CT* M, int a, int b, bool add) {
+                               const FactorTables<K, NPGX, CT>& ft, CT* M, int a, int b, bool add, const Grp& gr) {
   constexpr int MS = PD<K, NPGX>::MS;
-  const double kt = T.Kt[a][b], vis = g.dt * ph.nu * T.Wt[a][b], dw = g.dt * T.Wt[a][b];
-  for (int e = threadIdx.x; e < MS * MS; e += NTH) {
+  const CT kt = (CT)T.Kt[a][b], vis = (CT)(g.dt * ph.nu * T.Wt[a][b]), dw = (CT)(g.dt * T.Wt[a][b]);
+  for (int e = gr.t; e < MS * MS; e += gr.n) {
     const int i = e / MS, j = e - (e / MS) * MS;
     const int fi = ft.sf[i], fj = ft.sf[j];
-    double v = 0.0;
+    CT v = 0;
     if (fi < 0 || fj < 0) {
-      v = (i == j && a == b) ? 1.0 : 0.0;
+      v = (i == j && a == b) ? CT(1) : CT(0);
     } else if (fi < 2 && fj < 2) {
       if (fi == fj) {
         const int ix = ft.sx[i], iy = ft.sy[i], jx = ft.sx[j], jy = ft.sy[j];
-        const double mx = ft.Mx[ix][jx], my = ft.My[iy][jy];
+        const CT mx = ft.Mx[ix][jx], my = ft.My[iy][jy];
         v = kt * mx * my + vis * (ft.Kx[ix][jx] * my + mx * ft.Ky[iy][jy]);
       }
     } else if (fi < 2 || fj < 2) {
@@ -227,17 +240,17 @@ __device__ void assemble_const(const LevelGeom& g, const FeTables& T, const Phys
       v = dw * (c == 0 ? ft.Dx[qx][vx] * ft.Cy[qy][vy] : ft.Cx[qx][vx] * ft.Dy[qy][vy]);
     }
     if (add)
-      M[i * LD + j] += (CT)v;
+      M[i * LD + j] += v;
     else
-      M[i * LD + j] = (CT)v;
+      M[i * LD + j] = v;
   }
 }
 
 // M += dt conv sum_e T3[a,b,e] Ce_e, cell by cell (one cell per pass: no write conflicts).
-template <int K, int Q, typename CT, int LD, int NTH, int NPGX>
+template <int K, int Q, typename CT, int LD, int NPGX, class Grp>
 __device__ void assemble_conv(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const BlockSet& bs,
-                              const double* __restrict__ Ce, int blk, int slab, const FactorTables<K, NPGX>& ft,
-                              CT* M, int a, int b) {
+                              const CT* __restrict__ Ce, int blk, int slab, const FactorTables<K, NPGX, CT>& ft,
+                              CT* M, int a, int b, const Grp& gr) {
   using pd = PD<K, NPGX>;
   constexpr int NT = Q + 1, NVL = pd::NVL, NVE = pd::NVE, NVG = pd::NVG;
   constexpr int MS = pd::MS;
@@ -258,13 +271,13 @@ __device__ void assemble_conv(const LevelGeom& g, const FeTables& T, const PhysP
     cy1 = min(cy1, a1);
   }
   const double sc = g.dt * ph.conv;
-  double w[NT];
+  CT w[NT];
 #pragma unroll
-  for (int e = 0; e < NT; ++e) w[e] = sc * T.T3[a][b][e];
+  for (int e = 0; e < NT; ++e) w[e] = (CT)(sc * T.T3[a][b][e]);
   for (int cy = cy0; cy <= cy1; ++cy)
     for (int cx = cx0; cx <= cx1; ++cx) {
-      const double* ce = Ce + ((int64_t)slab * g.ncells() + cy * g.n + cx) * (NT * 4 * NVE * NVE);
-      for (int e = threadIdx.x; e < 4 * NVE * NVE; e += NTH) {
+      const CT* ce = Ce + ((int64_t)slab * g.ncells() + cy * g.n + cx) * (NT * 4 * NVE * NVE);
+      for (int e = gr.t; e < 4 * NVE * NVE; e += gr.n) {
         const int cd = e / (NVE * NVE), r = e % (NVE * NVE);
         const int li = r / NVE, lj = r % NVE;
         const int ix = cx * (K + 1) + li % NVL - vx0, iy = cy * (K + 1) + li / NVL - vy0;
@@ -272,12 +285,12 @@ __device__ void assemble_conv(const LevelGeom& g, const FeTables& T, const PhysP
         if (ix < 0 || ix >= nvg || iy < 0 || iy >= nvg || jx < 0 || jx >= nvg || jy < 0 || jy >= nvg) continue;
         const int si = (cd >> 1) * nvg * nvg + iy * nvg + ix, sj = (cd & 1) * nvg * nvg + jy * nvg + jx;
         if (ft.sf[si] < 0 || ft.sf[sj] < 0) continue;
-        double v = 0.0;
+        CT v = 0;
 #pragma unroll
         for (int ee = 0; ee < NT; ++ee) v += w[ee] * ce[(int64_t)ee * 4 * NVE * NVE + e];
-        M[si * LD + sj] += (CT)v;
+        M[si * LD + sj] += v;
       }
-      __syncthreads();
+      gr.sync();
     }
   (void)MS;
   (void)NVG;
@@ -507,7 +520,7 @@ __device__ void gemm_into_b(const CT* A, CT* B, CT sign) {
 
 template <int K, int Q, typename CT, typename ST, int NTH, int NPGX>
 __global__ void __launch_bounds__(NTH, 1)
-block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const double* __restrict__ Ce,
+block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const CT* __restrict__ Ce,
                     ST* __restrict__ factors, int* __restrict__ status) {
   using pd = PD<K, NPGX>;
   constexpr int MS = pd::MS, LD = pd::LD;
@@ -517,50 +530,160 @@ block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const d
   CT* M1 = reinterpret_cast<CT*>(smem_raw);
   CT* M2 = M1 + MS * LD;
   CT* colbuf = M2 + (Q == 1 ? MS * LD : 0);
-  FactorTables<K, NPGX>& ft = *reinterpret_cast<FactorTables<K, NPGX>*>(
-      smem_raw + ((sizeof(CT) * ((Q == 1 ? 2 : 1) * MS * LD + MS) + 15) / 16) * 16);
+  using FT = FactorTables<K, NPGX, CT>;
+  FT& ft = *reinterpret_cast<FT*>(smem_raw + ((sizeof(CT) * ((Q == 1 ? 2 : 1) * MS * LD + MS) + 15) / 16) * 16);
   int* perm = reinterpret_cast<int*>(&ft + 1);
   int* sh = perm + MS;
   const int blk = blockIdx.x, slab = blockIdx.y;
-  build_factor_tables<K, NPGX>(g, T, bs, blk, ft, NTH);
+  const CtaGroup gr{(int)threadIdx.x, NTH};
+  build_factor_tables<K, NPGX>(g, T, bs, blk, ft, gr);
   if (threadIdx.x == 0) { sh[0] = 0; sh[1] = 0; }
   __syncthreads();
   const bool conv = ph.conv != 0.0;
   ST* F = factors + ((int64_t)blk * g.N + slab) * (Q + 1) * (Q + 1) * BLK;
   bool ok;
   if constexpr (Q == 0) {
-    assemble_const<K, Q, CT, LD, NTH, NPGX>(g, T, ph, ft, M1, 0, 0, false);
+    assemble_const<K, Q, CT, LD, NPGX>(g, T, ph, ft, M1, 0, 0, false, gr);
     __syncthreads();
-    if (conv) assemble_conv<K, Q, CT, LD, NTH, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M1, 0, 0);
+    if (conv) assemble_conv<K, Q, CT, LD, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M1, 0, 0, gr);
     ok = invert_block<MS, LD, NTH>(M1, colbuf, perm, sh);
     store_colmajor<MS, LD, NTH>(M1, F);
   } else {
     // A00^{-1}
-    assemble_const<K, Q, CT, LD, NTH, NPGX>(g, T, ph, ft, M1, 0, 0, false);
+    assemble_const<K, Q, CT, LD, NPGX>(g, T, ph, ft, M1, 0, 0, false, gr);
     __syncthreads();
-    if (conv) assemble_conv<K, Q, CT, LD, NTH, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M1, 0, 0);
+    if (conv) assemble_conv<K, Q, CT, LD, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M1, 0, 0, gr);
     ok = invert_block<MS, LD, NTH>(M1, colbuf, perm, sh);
     store_colmajor<MS, LD, NTH>(M1, F);
     // X = A00^{-1} A01
-    assemble_const<K, Q, CT, LD, NTH, NPGX>(g, T, ph, ft, M2, 0, 1, false);
+    assemble_const<K, Q, CT, LD, NPGX>(g, T, ph, ft, M2, 0, 1, false, gr);
     __syncthreads();
-    if (conv) assemble_conv<K, Q, CT, LD, NTH, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M2, 0, 1);
+    if (conv) assemble_conv<K, Q, CT, LD, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M2, 0, 1, gr);
     gemm_into_b<MS, LD, NTH, CT>(M1, M2, CT(1));
     store_colmajor<MS, LD, NTH>(M2, F + 3 * BLK);
     // A10
-    assemble_const<K, Q, CT, LD, NTH, NPGX>(g, T, ph, ft, M1, 1, 0, false);
+    assemble_const<K, Q, CT, LD, NPGX>(g, T, ph, ft, M1, 1, 0, false, gr);
     __syncthreads();
-    if (conv) assemble_conv<K, Q, CT, LD, NTH, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M1, 1, 0);
+    if (conv) assemble_conv<K, Q, CT, LD, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M1, 1, 0, gr);
     store_colmajor<MS, LD, NTH>(M1, F + 1 * BLK);
     // S = A11 - A10 X
     gemm_into_b<MS, LD, NTH, CT>(M1, M2, CT(-1));
-    assemble_const<K, Q, CT, LD, NTH, NPGX>(g, T, ph, ft, M2, 1, 1, true);
+    assemble_const<K, Q, CT, LD, NPGX>(g, T, ph, ft, M2, 1, 1, true, gr);
     __syncthreads();
-    if (conv) assemble_conv<K, Q, CT, LD, NTH, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M2, 1, 1);
+    if (conv) assemble_conv<K, Q, CT, LD, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M2, 1, 1, gr);
     ok = invert_block<MS, LD, NTH>(M2, colbuf, perm, sh) && ok;
     store_colmajor<MS, LD, NTH>(M2, F + 2 * BLK);
   }
   if (!ok && threadIdx.x == 0) atomicExch(status, 1);
+}
+
+// Q2/Q1 DG(0) blocks (51 x 51) of the reduced-precision forms: one warp per
+// (patch, slab), WPB warps per CTA, no barrier wider than a warp.  The warp builds
+// its tables and assembles its block in FP32 in its own shared-memory tile (the
+// same assembly as the CTA kernel, lane-strided), then inverts it in registers by
+// the Gauss-Jordan elimination of gauss_jordan_reg (no row moves; pivot = largest
+// |.| among the rows not yet used, lowest row on ties): lane l holds rows l and
+// l + 32.  Each step eliminates the current first column and appends the new
+// column of the inverse at the end (every row shifts left by one), so the pivot
+// column is always register 0, the column loop unrolls with constant register
+// indices and the step loop stays rolled.  After MS steps a row holds the row of
+// X with its columns in step order; the pivot order is undone in the column-major
+// store: inv(A)[step of row i][pivot row of step j] = X[i][j].
+template <typename ST>
+struct FactorWarpSmem {
+  static constexpr int MS = PD<1, 1>::MS, LD = PD<1, 1>::LD;
+  float M[MS * LD];
+  FactorTables<1, 1, float> ft;
+  int prow[MS];
+};
+
+template <typename ST, int WPB>
+__global__ void __launch_bounds__(32 * WPB)
+block_factor_warp_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const float* __restrict__ Ce,
+                         ST* __restrict__ factors, int* __restrict__ status) {
+  constexpr int K = 1, Q = 0, NPGX = 1;
+  using SM = FactorWarpSmem<ST>;
+  constexpr int MS = SM::MS, LD = SM::LD;
+  static_assert(MS > 32 && MS <= 64, "two rows per lane");
+  constexpr int G = 16 / (int)sizeof(ST);
+  constexpr int64_t BLK = (MS * MS + G - 1) / G * G;
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  SM& sm = reinterpret_cast<SM*>(smem_raw)[w];
+  const int nblk = g.npatch();
+  const int64_t item = (int64_t)blockIdx.x * WPB + w;  // slab-major: neighbouring warps share cells
+  if (item >= (int64_t)nblk * g.N) return;             // the whole warp leaves
+  const int blk = (int)(item % nblk), slab = (int)(item / nblk);
+  const WarpGroup gr{lane, 32};
+  build_factor_tables<K, NPGX>(g, T, bs, blk, sm.ft, gr);
+  __syncwarp();
+  assemble_const<K, Q, float, LD, NPGX>(g, T, ph, sm.ft, sm.M, 0, 0, false, gr);
+  __syncwarp();
+  if (ph.conv != 0.0) assemble_conv<K, Q, float, LD, NPGX>(g, T, ph, bs, Ce, blk, slab, sm.ft, sm.M, 0, 0, gr);
+  __syncwarp();
+  const bool two = lane + 32 < MS;
+  float a0[MS], a1[MS];
+#pragma unroll
+  for (int j = 0; j < MS; ++j) {
+    a0[j] = sm.M[lane * LD + j];
+    a1[j] = two ? sm.M[(lane + 32) * LD + j] : 0.f;
+  }
+  unsigned used = two ? 0u : 2u;  // bit 0: row lane, bit 1: row lane + 32 (absent rows count as used)
+  int step0 = 0, step1 = 0;
+  bool zero = false;
+#pragma unroll 1
+  for (int p = 0; p < MS; ++p) {
+    const float v0 = (used & 1u) ? -1.f : fabsf(a0[0]);
+    const float v1 = (used & 2u) ? -1.f : fabsf(a1[0]);
+    float best = v0;
+    int bi = lane;
+    if (v1 > v0) {
+      best = v1;
+      bi = lane + 32;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float ob = __shfl_xor_sync(FULL, best, off);
+      const int oi = __shfl_xor_sync(FULL, bi, off);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    zero |= !(best > 0.f);
+    const int owner = bi & 31;
+    const bool hi = bi >= 32;
+    const bool r0 = !hi && lane == owner, r1 = hi && lane == owner;
+    const float f0 = a0[0], f1 = a1[0];
+    const float inv = 1.f / __shfl_sync(FULL, hi ? f1 : f0, owner);
+#pragma unroll
+    for (int j = 1; j < MS; ++j) {
+      const float rj = __shfl_sync(FULL, hi ? a1[j] : a0[j], owner) * inv;
+      a0[j - 1] = r0 ? rj : fmaf(-f0, rj, a0[j]);
+      a1[j - 1] = r1 ? rj : fmaf(-f1, rj, a1[j]);
+    }
+    a0[MS - 1] = r0 ? inv : -f0 * inv;
+    a1[MS - 1] = r1 ? inv : -f1 * inv;
+    if (r0) {
+      used |= 1u;
+      step0 = p;
+    }
+    if (r1) {
+      used |= 2u;
+      step1 = p;
+    }
+    if (lane == 0) sm.prow[p] = bi;
+  }
+  __syncwarp();
+  ST* F = factors + ((int64_t)blk * g.N + slab) * BLK;
+#pragma unroll
+  for (int j = 0; j < MS; ++j) {
+    const int col = sm.prow[j];
+    narrow(a0[j], F[col * MS + step0]);
+    if (two) narrow(a1[j], F[col * MS + step1]);
+  }
+  if (zero && lane == 0) atomicExch(status, 1);
 }
 
 // ---------------------------------------------------------------- smoother apply
@@ -1219,16 +1342,28 @@ __global__ void bt_scatter_kernel(const BatchSeg* __restrict__ segs, int nseg, i
 }
 
 template <int K, int Q, typename CT, typename ST, int NPGX = 2 * K - 1>
-void run_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const BlockSet& bs, const double* Ce,
+void run_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const BlockSet& bs, const CT* Ce,
                 ST* factors, int* status, cudaStream_t s) {
   using pd = PD<K, NPGX>;
   constexpr int NTH = K == 1 ? 256 : 512;
   const size_t mats = ((sizeof(CT) * ((Q == 1 ? 2 : 1) * pd::MS * pd::LD + pd::MS) + 15) / 16) * 16;
-  const size_t smem = mats + sizeof(FactorTables<K, NPGX>) + sizeof(int) * (pd::MS + 2);
+  const size_t smem = mats + sizeof(FactorTables<K, NPGX, CT>) + sizeof(int) * (pd::MS + 2);
   auto kern = block_factor_kernel<K, Q, CT, ST, NTH, NPGX>;
   WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int nblk = bs.kind == 0 ? g.npatch() : 1;
   kern<<<dim3(nblk, g.N), NTH, smem, s>>>(g, T, ph, bs, Ce, factors, status);
+  WR_LAUNCH_CHECK();
+}
+
+template <typename ST>
+void run_factor_warp(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const BlockSet& bs, const float* Ce,
+                     ST* factors, int* status, cudaStream_t s) {
+  constexpr int WPB = 4;
+  const size_t smem = sizeof(FactorWarpSmem<ST>) * WPB;
+  auto kern = block_factor_warp_kernel<ST, WPB>;
+  WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t items = (int64_t)g.npatch() * g.N;
+  kern<<<(unsigned)((items + WPB - 1) / WPB), 32 * WPB, smem, s>>>(g, T, ph, bs, Ce, factors, status);
   WR_LAUNCH_CHECK();
 }
 
@@ -1348,20 +1483,26 @@ void bt_apply_variant(int variant, const BatchSeg* segs, int nseg, int64_t items
 }  // namespace
 
 void launch_block_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const BlockSet& bs,
-                         const double* Ce, void* factors, int precision, int* st, cudaStream_t s, bool check) {
+                         const void* Ce, void* factors, int precision, int* st, cudaStream_t s, bool check) {
   if (check) WR_CUDA(cudaMemsetAsync(st, 0, sizeof(int), s));
+  const double* Cd = static_cast<const double*>(Ce);
+  const float* Cf = static_cast<const float*>(Ce);
 #define WR_F(K_, Q_)                                                                                     \
   if (g.k == K_ && g.q == Q_) {                                                                          \
     if (precision == WR_FP32)                                                                            \
-      run_factor<K_, Q_, float, float>(g, T, ph, bs, Ce, static_cast<float*>(factors), st, s);           \
+      run_factor<K_, Q_, float, float>(g, T, ph, bs, Cf, static_cast<float*>(factors), st, s);           \
     else if (precision == WR_BF16)                                                                       \
-      run_factor<K_, Q_, float, __nv_bfloat16>(g, T, ph, bs, Ce, static_cast<__nv_bfloat16*>(factors), st, s); \
+      run_factor<K_, Q_, float, __nv_bfloat16>(g, T, ph, bs, Cf, static_cast<__nv_bfloat16*>(factors), st, s); \
     else                                                                                                 \
-      run_factor<K_, Q_, double, double>(g, T, ph, bs, Ce, static_cast<double*>(factors), st, s);        \
+      run_factor<K_, Q_, double, double>(g, T, ph, bs, Cd, static_cast<double*>(factors), st, s);        \
   } else
   if (bs.kind == 1 && g.k == 1 && bs.npg == 4) {  // coarse 3x3 block of Q2/Q1 (FP64)
-    if (g.q == 0) run_factor<1, 0, double, double, 4>(g, T, ph, bs, Ce, static_cast<double*>(factors), st, s);
-    else run_factor<1, 1, double, double, 4>(g, T, ph, bs, Ce, static_cast<double*>(factors), st, s);
+    if (g.q == 0) run_factor<1, 0, double, double, 4>(g, T, ph, bs, Cd, static_cast<double*>(factors), st, s);
+    else run_factor<1, 1, double, double, 4>(g, T, ph, bs, Cd, static_cast<double*>(factors), st, s);
+  } else if (bs.kind == 0 && g.k == 1 && g.q == 0 && precision == WR_FP32) {  // a warp per block
+    run_factor_warp<float>(g, T, ph, bs, Cf, static_cast<float*>(factors), st, s);
+  } else if (bs.kind == 0 && g.k == 1 && g.q == 0 && precision == WR_BF16) {
+    run_factor_warp<__nv_bfloat16>(g, T, ph, bs, Cf, static_cast<__nv_bfloat16*>(factors), st, s);
   } else
   WR_F(1, 0) WR_F(1, 1) WR_F(2, 0) WR_F(2, 1) throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 #undef WR_F

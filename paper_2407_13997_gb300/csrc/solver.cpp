@@ -235,7 +235,7 @@ struct wr_ctx {
     LevelGeom gw = lv.g;
     gw.N = nwc;
     gw.ndofs = (int64_t)nwc * gw.nt * gw.S;
-    if (ph.conv != 0.0) launch_conv_elements(gw, tab, lv.W + (int64_t)s0 * gw.nt * gw.S, Ce, s);
+    if (ph.conv != 0.0) launch_conv_elements(gw, tab, lv.W + (int64_t)s0 * gw.nt * gw.S, Ce, opt.precision, s);
     launch_block_factor(gw, tab, ph, lv.bs, Ce, fwin, opt.precision, fstat, s, check);
   }
 
@@ -432,10 +432,10 @@ struct wr_ctx {
         for (int s0 = 0; s0 < L[l].g.N; s0 += L[l].nw) factor_window(l, s0, std::min(L[l].nw, L[l].g.N - s0), true);
         continue;
       }
-      if (ph.conv != 0.0) launch_conv_elements(L[l].g, tab, L[l].W, Ce, s);
+      if (ph.conv != 0.0) launch_conv_elements(L[l].g, tab, L[l].W, Ce, opt.precision, s);
       launch_block_factor(L[l].g, tab, ph, L[l].bs, Ce, L[l].factors, opt.precision, fstat, s);
     }
-    if (ph.conv != 0.0) launch_conv_elements(L[0].g, tab, L[0].W, Ce, s);
+    if (ph.conv != 0.0) launch_conv_elements(L[0].g, tab, L[0].W, Ce, WR_FP64, s);
     launch_block_factor(L[0].g, tab, ph, cbs, Ce, cfactors, WR_FP64, fstat, s);
     linearised = true;
     if (opt.autotune)

@@ -190,14 +190,17 @@ void launch_jacobian_f32(const LevelGeom& g, const FeTables& T, const PhysParams
                          const double* x, double* y, double* ye, cudaStream_t s);
 void launch_boundary_values(const LevelGeom& g, const FeTables& T, const PhysParams& ph, double* U,
                             cudaStream_t s);
-void launch_conv_elements(const LevelGeom& g, const FeTables& T, const double* W, double* Ce,
+// Element convection matrices about W, in FP64 (precision WR_FP64) or FP32 (the
+// reduced-precision factorisations, which assemble their blocks in FP32).
+void launch_conv_elements(const LevelGeom& g, const FeTables& T, const double* W, void* Ce, int precision,
                           cudaStream_t s);
 void launch_inject(const LevelGeom& gf, const LevelGeom& gc, const double* Wf, double* Wc,
                    cudaStream_t s);
 // st: a device int of the caller's (zero-pivot flag); with check it is cleared
-// before and read back after the launch (a host synchronisation), else left as is
+// before and read back after the launch (a host synchronisation), else left as is.
+// Ce: the element convection matrices of launch_conv_elements in the same precision.
 void launch_block_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph,
-                         const BlockSet& bs, const double* Ce, void* factors, int precision, int* st,
+                         const BlockSet& bs, const void* Ce, void* factors, int precision, int* st,
                          cudaStream_t s, bool check = true);
 // Patch blocks (kind 0) write [slab][patch][a][slot] outputs to out; the coarse
 // block (kind 1) writes the solution.  A window of slabs is g with N = window
