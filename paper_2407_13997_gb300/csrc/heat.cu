@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(NTH) heat_factor_kernel(LevelGeom g, FeTables 
   __syncthreads();
   double* col = sA + M * M;
   __shared__ int perm[M];
+  __shared__ double pinv;  // the pivot's reciprocal, formed once per step
   bool singular = false;
   for (int p = 0; p < M; ++p) {
     if (tid == 0) {
@@ -141,6 +142,7 @@ __global__ void __launch_bounds__(NTH) heat_factor_kernel(LevelGeom g, FeTables 
         }
       piv = best;
       perm[p] = best;
+      pinv = 1.0 / sA[best * M + p];
     }
     __syncthreads();
     const int r = piv;
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(NTH) heat_factor_kernel(LevelGeom g, FeTables 
     __syncthreads();
     const double d = sA[p * M + p];
     if (!(fabs(d) > 0.0)) singular = true;
-    const double inv = 1.0 / d;
+    const double inv = pinv;
     for (int i = tid; i < M; i += NTH) col[i] = sA[i * M + p];
     __syncthreads();
     for (int j = tid; j < M; j += NTH) sA[p * M + j] = (j == p ? 1.0 : sA[p * M + j]) * inv;

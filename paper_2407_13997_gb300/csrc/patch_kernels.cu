@@ -298,10 +298,14 @@ __device__ void assemble_conv(const LevelGeom& g, const FeTables& T, const PhysP
 
 // In-place Gauss-Jordan inversion with partial pivoting (largest |.|, lowest
 // row on ties) of the MS x MS row-major matrix A (leading dimension LD) in
-// shared memory.  Returns false (to all threads) if a zero pivot was met.
+// shared memory.  Returns false (to all threads) if a zero pivot was met.  The
+// pivot's reciprocal is formed once, by the thread that picks the pivot, and
+// read by the others from shared memory (a division per thread would cost the
+// FP64 pipe as much as the step's elimination on GB300).
 template <int MS, int LD, int NTH, typename CT>
 __device__ bool gauss_jordan(CT* A, CT* colbuf, int* perm, int* sh) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ CT pinv;
 #pragma unroll 1
   for (int p = 0; p < MS; ++p) {
     if (warp == 0) {
@@ -320,6 +324,7 @@ __device__ bool gauss_jordan(CT* A, CT* colbuf, int* perm, int* sh) {
         sh[0] = bi;
         perm[p] = bi;
         if (!(best > 0)) sh[1] = 1;
+        pinv = CT(1) / A[bi * LD + p];  // the pivot, before the row exchange
       }
     }
     __syncthreads();
@@ -331,7 +336,7 @@ __device__ bool gauss_jordan(CT* A, CT* colbuf, int* perm, int* sh) {
         A[r * LD + j] = t;
       }
     __syncthreads();
-    const CT inv = CT(1) / A[p * LD + p];
+    const CT inv = pinv;
     for (int i = tid; i < MS; i += NTH) colbuf[i] = A[i * LD + p];
     __syncthreads();
     for (int j = tid; j < MS; j += NTH) A[p * LD + j] = (j == p) ? inv : A[p * LD + j] * inv;
