@@ -547,20 +547,35 @@ bt_element_f32_kernel(const BatchSeg* __restrict__ segs, int nseg, FeTables T, c
                          reinterpret_cast<ElemSmemF<K, Q>*>(smem_raw)[threadIdx.x / 32], cell, slab);
 }
 
+// The reference tables are copied once per CTA into shared memory: element_body
+// indexes them with lane-dependent indices, which kernel-parameter space serves one
+// address at a time.  T is a grid constant, so its address is taken without a copy.
+__device__ __forceinline__ void stage_fe_tables(const FeTables& T, FeTables& Ts) {
+  const double* src = reinterpret_cast<const double*>(&T);
+  double* dst = reinterpret_cast<double*>(&Ts);
+  for (int i = threadIdx.x; i < (int)(sizeof(FeTables) / sizeof(double)); i += blockDim.x) dst[i] = src[i];
+}
+
 template <int K, int Q, bool LIN>
 __global__ void __launch_bounds__(32 * kWarps)
-element_kernel(LevelGeom g, FeTables T, PhysParams ph, const double* __restrict__ W,
+element_kernel(LevelGeom g, const __grid_constant__ FeTables T, PhysParams ph, const double* __restrict__ W,
                const double* __restrict__ x, double* __restrict__ ye) {
+  __shared__ FeTables Ts;
+  stage_fe_tables(T, Ts);
+  __syncthreads();
   const int cell = blockIdx.x * kWarps + threadIdx.x / 32;
   if (cell >= g.ncells()) return;
-  element_body<K, Q, LIN>(g, T, ph, W, x, ye, cell, blockIdx.y);
+  element_body<K, Q, LIN>(g, Ts, ph, W, x, ye, cell, blockIdx.y);
 }
 
 // Batched: one CTA per (member, group of kWarps cells, slab); x and ye are arenas.
 template <int K, int Q, bool LIN>
 __global__ void __launch_bounds__(32 * kWarps)
-bt_element_kernel(const BatchSeg* __restrict__ segs, int nseg, FeTables T, const double* __restrict__ x,
-                  double* __restrict__ ye) {
+bt_element_kernel(const BatchSeg* __restrict__ segs, int nseg, const __grid_constant__ FeTables T,
+                  const double* __restrict__ x, double* __restrict__ ye) {
+  __shared__ FeTables Ts;
+  stage_fe_tables(T, Ts);
+  __syncthreads();
   const int m = batch_find<BU_ELEM>(segs, nseg, blockIdx.x);
   const LevelGeom g = segs[m].g;
   const PhysParams ph = segs[m].ph;
@@ -569,7 +584,7 @@ bt_element_kernel(const BatchSeg* __restrict__ segs, int nseg, FeTables T, const
   const int slab = (int)(lu / cb);
   const int cell = (int)(lu % cb) * kWarps + threadIdx.x / 32;
   if (cell >= g.ncells()) return;
-  element_body<K, Q, LIN>(g, T, ph, segs[m].W, x + segs[m].off, ye + segs[m].off_ye, cell, slab);
+  element_body<K, Q, LIN>(g, Ts, ph, segs[m].W, x + segs[m].off, ye + segs[m].off_ye, cell, slab);
 }
 
 // Sums element contributions into the global vector (fixed cell order) and sets

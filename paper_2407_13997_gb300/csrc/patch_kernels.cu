@@ -701,7 +701,7 @@ block_factor_warp_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, co
 // the producer refills a slot as soon as it is free and about NS chunks stay in
 // flight.  Consumer thread (i, g) multiplies row i by the g-th sub-range of each
 // chunk's columns (G groups: 95-99% of the lanes issue FP64 FMAs, which bind on
-// GB300) with four independent accumulators; partial sums are combined in a fixed
+// GB300) with one accumulator (FP64) or four (FP32/BF16); partial sums are combined in a fixed
 // order after a named barrier of the consumer warps.  The next slab's right-hand
 // side is prefetched into registers while the current slab's blocks are applied.
 // Every wait is bounded: on timeout the kernel sets *err, drains its own copies
@@ -991,19 +991,27 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
             const int c1 = min(ncol, c0 + C::SUB);
             const CT* xk = xv + k * C::CC;
             int c = c0;
-            for (; c + 3 < c1; c += 4) {
-              a0 = fma(widen(A[(c + 0) * MS + row]), xk[c + 0], a0);
-              a1 = fma(widen(A[(c + 1) * MS + row]), xk[c + 1], a1);
-              a2 = fma(widen(A[(c + 2) * MS + row]), xk[c + 2], a2);
-              a3 = fma(widen(A[(c + 3) * MS + row]), xk[c + 3], a3);
+            if constexpr (sizeof(CT) == 8) {
+              // FP64: the SM's FP64 pipe (2 FMA/clk on GB300) bounds the GEMV, not the
+              // dependency chain of one thread, so a single accumulator spares the
+              // three combining additions per block
+#pragma unroll 4
+              for (; c < c1; ++c) a0 = fma(widen(A[c * MS + row]), xk[c], a0);
+            } else {
+              for (; c + 3 < c1; c += 4) {
+                a0 = fma(widen(A[(c + 0) * MS + row]), xk[c + 0], a0);
+                a1 = fma(widen(A[(c + 1) * MS + row]), xk[c + 1], a1);
+                a2 = fma(widen(A[(c + 2) * MS + row]), xk[c + 2], a2);
+                a3 = fma(widen(A[(c + 3) * MS + row]), xk[c + 3], a3);
+              }
+              for (; c < c1; ++c) a0 = fma(widen(A[c * MS + row]), xk[c], a0);
             }
-            for (; c < c1; ++c) a0 = fma(widen(A[c * MS + row]), xk[c], a0);
           }
           __syncwarp();
           if (ok && lane == 0) mbar_arrive(smem_u32(&sm.empty[slot]));  // this warp is done with the slot
           ++ci;
         }
-        if (gemv_thread) sm.red[grp][row] = (a0 + a1) + (a2 + a3);
+        if (gemv_thread) sm.red[grp][row] = sizeof(CT) == 8 ? a0 : (a0 + a1) + (a2 + a3);
         if (tid == 0) sm.decision = *abort_flag;  // one reader, so every consumer decides alike
         consumer_sync<NCONS>();
         if (sm.decision) {
