@@ -60,7 +60,8 @@ def parse():
                     help="smoother form: also time the parallel-in-time patch solve (1 = auto, 2 = forced)")
     ap.add_argument("--full-mix", action="store_true",
                     help="serve form: draw n and N from {16, 32, 64} (default {16, 32})")
-    ap.add_argument("--form", default="cycle", choices=["cycle", "precision", "batch", "serve", "smoother", "timestepping", "lid", "heat"],
+    ap.add_argument("--form", default="cycle", choices=["cycle", "precision", "batch", "serve", "smoother", "timestepping", "lid", "heat",
+                                                        "setup"],
                     help="cycle: the V(2,2) throughput line (default); precision: the FP64/FP32/BF16 "
                          "solves of the 128x128 Q2/Q1 DG(0) 128-slab workload")
     return ap.parse_args()
@@ -814,6 +815,46 @@ def run_heat_form(args):
     print(json.dumps(out), flush=True)
 
 
+def run_setup_form(args):
+    """Linearisation (step (b) and the eigen-estimates) in FP64 and FP32 on the
+    --workload (q2q1: 128x128 Q2/Q1 DG(0), 128 slabs; q3q2: 64x64 Q3/Q2 DG(1), 64
+    slabs; --n/--slabs resize it): the first call (with
+    the apply-tile tuning), the factorisation alone (convection matrices and the
+    block inversions of every level) and factorisation + eigen-estimates.  The FP32
+    factorisation + eigen-estimates call sits in the NVTX range `timed` (the ncu
+    launch-list command).  FLOP rate: the inversions' algorithmic FMAs (m^3 per
+    DG(0) block; 4 m^3 per DG(1) block: two inversions and two products) x 2 over
+    the factorisation-alone time."""
+    import torch
+    from paper_2407_13997_gb300 import inputs, wrmg
+    torch.cuda.set_device(0)
+    w = workload(args)
+    ms = 51 if w.k == 1 else 107
+    blocks = sum((n + 1) ** 2 for n in [w.n_fine >> l for l in range(20)] if n > w.n_coarse) * w.N
+    flops = 2.0 * blocks * ms ** 3 * (1 if w.q == 0 else 4)
+    out = {"form": "setup", "workload": w.name, "ndofs": w.ndofs(), "blocks": blocks, "block_size": ms * (w.q + 1),
+           "algorithmic_flops": flops}
+    for name, prec in (("fp64", wrmg.WR_FP64), ("fp32", wrmg.WR_FP32)):
+        ctx = wrmg.Context(w, wrmg.default_options(precision=prec))
+        W = torch.from_numpy(inputs.forcing_shaped_iterate(w)).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter(); ctx.linearise(W, eig=False); torch.cuda.synchronize()
+        first = time.perf_counter() - t0
+        t0 = time.perf_counter(); ctx.linearise(W, eig=False); torch.cuda.synchronize()
+        fac = time.perf_counter() - t0
+        if name == "fp32":
+            torch.cuda.nvtx.range_push("timed")
+        t0 = time.perf_counter(); ctx.linearise(W, eig=True); torch.cuda.synchronize()
+        full = time.perf_counter() - t0
+        if name == "fp32":
+            torch.cuda.nvtx.range_pop()
+        out[name] = {"first_s": first, "factor_s": fac, "factor_eig_s": full, "factor_tflops": flops / fac / 1e12}
+        ctx.close()
+        del W
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -832,6 +873,8 @@ def main():
         run_lid_form(args)
     elif args.form == "heat":
         run_heat_form(args)
+    elif args.form == "setup":
+        run_setup_form(args)
     else:
         run_ours(args)
 
