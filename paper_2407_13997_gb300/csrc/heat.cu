@@ -34,11 +34,35 @@ __device__ __forceinline__ double heat_initial(const PhysParams& ph, double x, d
   return sinpi(x) + cospi(2.0 * y);
 }
 
+// The reference tables the heat kernels index with thread-dependent indices, copied
+// once per CTA into shared memory (kernel-parameter space serves one address at a time).
+struct HeatTab {
+  double m1[WR_MAX_NVL][WR_MAX_NVL], k1[WR_MAX_NVL][WR_MAX_NVL];
+  double Kt[WR_MAX_NT][WR_MAX_NT], Wt[WR_MAX_NT][WR_MAX_NT], tau0[WR_MAX_NT];
+};
+
+__device__ __forceinline__ void stage_heat_tab(const FeTables& T, HeatTab& t) {
+  for (int e = threadIdx.x; e < WR_MAX_NVL * WR_MAX_NVL; e += blockDim.x) {
+    const int i = e / WR_MAX_NVL, j = e % WR_MAX_NVL;
+    t.m1[i][j] = T.m1[i][j];
+    t.k1[i][j] = T.k1[i][j];
+  }
+  for (int e = threadIdx.x; e < WR_MAX_NT * WR_MAX_NT; e += blockDim.x) {
+    const int a = e / WR_MAX_NT, b = e % WR_MAX_NT;
+    t.Kt[a][b] = T.Kt[a][b];
+    t.Wt[a][b] = T.Wt[a][b];
+  }
+  for (int a = threadIdx.x; a < WR_MAX_NT; a += blockDim.x) t.tau0[a] = T.tau0[a];
+}
+
 // y = J x (RES = false) or F(x) = J x - b (RES = true: the slab-0 initial-data term).
 template <int K, int Q, bool RES>
-__global__ void heat_op_kernel(LevelGeom g, FeTables T, PhysParams ph, const double* __restrict__ x,
+__global__ void heat_op_kernel(LevelGeom g, FeTables Tp, PhysParams ph, const double* __restrict__ x,
                                double* __restrict__ y) {
   constexpr int NT = Q + 1;
+  __shared__ HeatTab T;
+  stage_heat_tab(Tp, T);
+  __syncthreads();
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= g.ndofs) return;
   const int nv = g.nv, S = g.S;
@@ -101,11 +125,14 @@ struct HeatBlock {
 // Inverts the slab block of (block, slab): assembled in shared memory, Gauss-Jordan
 // with partial pivoting (largest |.|, lowest row on ties), stored column-major.
 template <int K, int Q, int PX, bool WHOLE, int NTH>
-__global__ void __launch_bounds__(NTH) heat_factor_kernel(LevelGeom g, FeTables T, PhysParams ph,
+__global__ void __launch_bounds__(NTH) heat_factor_kernel(LevelGeom g, FeTables Tp, PhysParams ph,
                                                           double* __restrict__ factors, int* __restrict__ status) {
   constexpr int NT = Q + 1, P2 = PX * PX, M = NT * P2;
   extern __shared__ __align__(16) double sA[];  // M x M row-major, then one pivot column
   __shared__ int piv;
+  __shared__ HeatTab T;
+  stage_heat_tab(Tp, T);
+  __syncthreads();
   const int blk = blockIdx.x, slab = blockIdx.y, tid = threadIdx.x;
   int x0, y0;
   HeatBlock<K, PX, WHOLE>::origin(g, blk, x0, y0);
@@ -132,17 +159,29 @@ __global__ void __launch_bounds__(NTH) heat_factor_kernel(LevelGeom g, FeTables 
   __shared__ double pinv;  // the pivot's reciprocal, formed once per step
   bool singular = false;
   for (int p = 0; p < M; ++p) {
-    if (tid == 0) {
-      int best = p;
-      double bv = fabs(sA[p * M + p]);
-      for (int i = p + 1; i < M; ++i)
-        if (fabs(sA[i * M + p]) > bv) {
-          bv = fabs(sA[i * M + p]);
-          best = i;
+    if (tid < 32) {  // warp 0: largest |.| (compared as sign-cleared bit patterns), lowest row on ties
+      unsigned long long best = 0;
+      int bi = M;
+      for (int i = p + tid; i < M; i += 32) {
+        const unsigned long long v = (unsigned long long)__double_as_longlong(sA[i * M + p]) & 0x7fffffffffffffffull;
+        if (v > best || bi == M) {
+          best = v;
+          bi = i;
         }
-      piv = best;
-      perm[p] = best;
-      pinv = 1.0 / sA[best * M + p];
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (tid == 0) {
+        piv = bi;
+        perm[p] = bi;
+        pinv = 1.0 / sA[bi * M + p];
+      }
     }
     __syncthreads();
     const int r = piv;
@@ -191,12 +230,15 @@ __global__ void __launch_bounds__(NTH) heat_factor_kernel(LevelGeom g, FeTables 
 // y_n = A_nn^{-1} rhs; L = -tau(0) (x) M restricted to the block's nodes.
 // Patches write [slab][block][slot] outputs; the coarse block writes the solution.
 template <int K, int Q, int PX, bool WHOLE, int NTH>
-__global__ void __launch_bounds__(NTH) heat_apply_kernel(LevelGeom g, FeTables T, const double* __restrict__ factors,
+__global__ void __launch_bounds__(NTH) heat_apply_kernel(LevelGeom g, FeTables Tp, const double* __restrict__ factors,
                                                          const double* __restrict__ r, double* __restrict__ out,
                                                          int nblk) {
   constexpr int NT = Q + 1, P2 = PX * PX, M = NT * P2;
-  __shared__ double rhs[M], yv[M], ylast[P2], m1x[PX][PX], m1y[PX][PX];
+  __shared__ double rhs[M], yv[M], ylast[P2], tj[P2], mj[P2], m1x[PX][PX], m1y[PX][PX];
   __shared__ int node[P2];
+  __shared__ HeatTab T;
+  stage_heat_tab(Tp, T);
+  __syncthreads();
   const int blk = blockIdx.x, tid = threadIdx.x;
   int x0, y0;
   HeatBlock<K, PX, WHOLE>::origin(g, blk, x0, y0);
@@ -214,14 +256,26 @@ __global__ void __launch_bounds__(NTH) heat_apply_kernel(LevelGeom g, FeTables T
   }
   __syncthreads();
   for (int slab = 0; slab < g.N; ++slab) {
+    if (slab > 0) {  // jump term M y_{n-1, last} on the block's nodes, one tensor direction at a time
+      for (int e = tid; e < P2; e += NTH) {
+        const int ly = e / PX, jx = e % PX;
+        double t = 0.0;
+        for (int jy = 0; jy < PX; ++jy) t = fma(m1y[ly][jy], ylast[jy * PX + jx], t);
+        tj[e] = t;
+      }
+      __syncthreads();
+      for (int e = tid; e < P2; e += NTH) {
+        const int ly = e / PX, lx = e % PX;
+        double m = 0.0;
+        for (int jx = 0; jx < PX; ++jx) m = fma(m1x[lx][jx], tj[ly * PX + jx], m);
+        mj[e] = m;
+      }
+      __syncthreads();
+    }
     for (int i = tid; i < M; i += NTH) {
       const int a = i / P2, si = i % P2, nd = node[si];
       double v = nd >= 0 ? r[((int64_t)slab * NT + a) * g.S + nd] : 0.0;
-      if (slab > 0 && nd >= 0) {
-        double m = 0.0;
-        for (int sj = 0; sj < P2; ++sj) m = fma(m1y[si / PX][sj / PX] * m1x[si % PX][sj % PX], ylast[sj], m);
-        v = fma(T.tau0[a], m, v);
-      }
+      if (slab > 0 && nd >= 0) v = fma(T.tau0[a], mj[si], v);
       rhs[i] = v;
     }
     __syncthreads();
