@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--inflight", type=int, default=8, help="serve form: solves in flight at most")
     ap.add_argument("--budget-gb", type=float, default=96.0, help="serve form: device-memory budget")
     ap.add_argument("--tile", type=int, default=-1,
-                    help="cycle and smoother forms: force a smoother-apply tile 0..3 (default: autotuned)")
+                    help="cycle and smoother forms: force a smoother-apply tile 0..4 (default: autotuned)")
     ap.add_argument("--time-parallel", type=int, default=None,
                     help="smoother form: also time the parallel-in-time patch solve (1 = auto, 2 = forced)")
     ap.add_argument("--full-mix", action="store_true",

@@ -140,9 +140,11 @@ typedef struct {
     int autotune;           /* 1 (default): at the first linearisation, time the smoother-apply
                                tile variants on every level's stored factors and keep the
                                fastest (cached per shape for the process); 0: fixed tiles     */
-    int apply_tile;         /* -1 (default): the autotuner's (or the fixed) choice; 0 .. 3 force
+    int apply_tile;         /* -1 (default): the autotuner's (or the fixed) choice; 0 .. 4 force
                                a smoother-apply tile on every level (0-2: one CTA per patch,
-                               1, 2 or 3 CTAs per SM; 3: one warp per patch)                 */
+                               1, 2 or 3 CTAs per SM; 3: one warp per patch; 4: one warp per
+                               patch, each slab's block bulk-copied to shared memory two slabs
+                               ahead (Q2/Q1 DG(0); tile 3 elsewhere))                         */
     double newton_divtol;   /* stop (WR_ERR_NOT_CONVERGED) once ||F|| > newton_divtol ||F_0|| (1e6; 0: never) */
     int newton_stall;       /* stop once FGMRES has used gmres_maxit in this many consecutive
                                Newton steps (3; 0: never)                                     */

@@ -732,7 +732,7 @@ __device__ __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162floa
 //   Q3/Q2 (K = 2): G = 4 with one 480-thread CTA per SM (176 KB), or G = 2 with
 //                  two or three 256-thread CTAs per SM (96 / 64 KB).
 // The coarse 3x3 block (NPGX != 2K - 1) always takes variant 0.
-constexpr int kApplyVariants = 4;  // tiles 0-2: CTA per block; tile 3: warp per block
+constexpr int kApplyVariants = 5;  // tiles 0-2: CTA per block; 3: warp per block; 4: warp per block, bulk copies
 // without tuning: three 64 KB CTAs per SM for Q2/Q1, one 480-thread CTA for Q3/Q2
 inline int default_apply_variant(int k) { return k == 1 ? 2 : 0; }
 template <int K, int V>
@@ -1306,6 +1306,205 @@ bt_warp_apply_kernel(const BatchSeg* __restrict__ segs, int nseg, int64_t nitems
   warp_apply<K, Q, FT>(T, BatchItems<FT>{segs, nseg, r, yp, false}, nitems);
 }
 
+// Tile 4 (Q2/Q1 DG(0) only): a warp per patch as in tile 3, with each slab's block
+// (one contiguous column-major m x m block) brought into the warp's shared memory by
+// a single bulk copy (cp.async.bulk completing on an mbarrier), two slabs ahead of
+// its use.  Tile 3 keeps a few column loads in flight per warp and waits for them
+// slab after slab; here a whole block is in flight while the one before it is
+// applied.  The GEMV reads the block in the same order as tile 3 (bitwise the same
+// result).  Every wait is bounded: on timeout the warp raises *err, waits (bounded)
+// for its own copies still in flight and leaves.
+constexpr int kWarpBulkWarps = 4;
+
+template <typename FT>
+struct alignas(16) WarpBulkSmem {
+  static constexpr int MS = PD<1>::MS;
+  static constexpr int GR = 16 / (int)sizeof(FT);
+  static constexpr int BLK = (MS * MS + GR - 1) / GR * GR;  // the stored block, padded to 16 bytes
+  FT buf[2][BLK];
+  unsigned long long full[2];
+  WarpSmem<1, 0, FT> w;
+};
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+template <typename FT, class Items>
+__device__ __forceinline__ void warp_apply_bulk(const FeTables& T, const Items& items, int64_t nitems,
+                                                int* __restrict__ err) {
+  constexpr int K = 1;
+  using pd = PD<K>;
+  using CT = typename ComputeType<FT>::type;
+  using SB = WarpBulkSmem<FT>;
+  constexpr int MS = pd::MS, NVG = pd::NVG, R = (MS + 31) / 32, RP = (MS + 31) / 32;
+  constexpr uint32_t BYTES = (uint32_t)(SB::BLK * sizeof(FT));
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(128) unsigned char wsm_raw[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  SB& sb = reinterpret_cast<SB*>(wsm_raw)[w];
+  WarpSmem<1, 0, FT>& sm = sb.w;
+  if (lane == 0) {
+    mbar_init(smem_u32(&sb.full[0]), 1);
+    mbar_init(smem_u32(&sb.full[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  // completed uses of each buffer (the parity of its next wait) and copies in flight, as
+  // bit 0 (buffer 0) and bit 1 (buffer 1) -- scalars, so that nothing goes to local memory
+  uint32_t used0 = 0u, used1 = 0u, pending = 0u;
+  bool aborted = false;
+  const int64_t nwarps = (int64_t)gridDim.x * kWarpBulkWarps;
+  for (int64_t it = (int64_t)blockIdx.x * kWarpBulkWarps + w; it < nitems && !aborted; it += nwarps) {
+    const ApplyItem<FT> v = items(it);
+    const LevelGeom& g = v.g;
+    const BlockSet& bs = v.bs;
+    const int blk = v.blk, nvg = bs.nvg, nv2g = nvg * nvg;
+    const FT* fblk = v.factors + ((int64_t)blk * v.fN + v.s0) * SB::BLK;  // slab 0 of this item
+    // copies of the first two slabs' blocks
+    for (int sl = 0; sl < 2 && sl < g.N; ++sl) {
+      if (lane == 0) {
+        fence_proxy_async();
+        const uint32_t bar = smem_u32(&sb.full[sl]);
+        mbar_expect_tx(bar, BYTES);
+        bulk_g2s(smem_u32(sb.buf[sl]), fblk + (int64_t)sl * SB::BLK, BYTES, bar);
+      }
+      pending |= 1u << sl;
+    }
+    int vx0, vy0, px0, py0;
+    block_origin(g, bs, blk, vx0, vy0, px0, py0);
+    for (int s = lane; s < MS; s += 32) sm.sidx[s] = decode_slot(g, bs, blk, s).sp;
+    int cx0, cx1, cy0, cy1;
+    own_cells(g, bs, vx0, cx0, cx1);
+    own_cells(g, bs, vy0, cy0, cy1);
+    for (int e = lane; e < NVG * NVG; e += 32) {
+      const int i = e / NVG, j = e % NVG;
+      const int xi = vx0 + i, xj = vx0 + j, yi = vy0 + i, yj = vy0 + j;
+      const bool okx = i < nvg && j < nvg && xi >= 1 && xi <= g.nv - 2 && xj >= 1 && xj <= g.nv - 2;
+      const bool oky = i < nvg && j < nvg && yi >= 1 && yi <= g.nv - 2 && yj >= 1 && yj <= g.nv - 2;
+      sm.mx[i][j] = okx ? (CT)(g.h * vv1<K>(T.m1, g.n, xi, xj, cx0, cx1)) : (CT)0;
+      sm.my[i][j] = oky ? (CT)(g.h * vv1<K>(T.m1, g.n, yi, yj, cy0, cy1)) : (CT)0;
+    }
+    const bool carry = v.prev != nullptr;
+    for (int e = lane; e < 2 * pd::NVG2; e += 32) {
+      const int c = e / pd::NVG2, tt = e % pd::NVG2;
+      sm.yp[c][tt] = (carry && tt < nv2g) ? (CT)v.prev[(int64_t)blk * MS + c * nv2g + tt] : (CT)0;
+    }
+    __syncwarp();
+    for (int s = lane; s < MS; s += 32) {
+      const int sp = sm.sidx[s];
+      sm.rhs[0][s] = sp >= 0 ? (CT)v.r[sp] : (CT)0;
+    }
+    for (int slab = 0; slab < g.N; ++slab) {
+      const int b = slab & 1;
+      __syncwarp();
+      if (slab > 0 || carry) {
+        for (int e = lane; e < 2 * nv2g; e += 32) {
+          const int c = e / nv2g, tt = e % nv2g, iy = tt / nvg, jx = tt % nvg;
+          CT acc = 0;
+          for (int jy = 0; jy < nvg; ++jy) acc = fma(sm.my[iy][jy], sm.yp[c][jy * nvg + jx], acc);
+          sm.tm[c][tt] = acc;
+        }
+        __syncwarp();
+        for (int e = lane; e < 2 * nv2g; e += 32) {
+          const int c = e / nv2g, tt = e % nv2g, iy = tt / nvg, ix = tt % nvg;
+          CT acc = 0;
+          for (int jx = 0; jx < nvg; ++jx) acc = fma(sm.mx[ix][jx], sm.tm[c][iy * nvg + jx], acc);
+          const int s = c * nv2g + tt;
+          if (sm.sidx[s] >= 0) sm.rhs[0][s] += (CT)T.tau0[0] * acc;
+        }
+        __syncwarp();
+      }
+      // register prefetch of the next slab's right-hand side
+      CT pf[RP];
+#pragma unroll
+      for (int u = 0; u < RP; ++u) {
+        const int e = lane + 32 * u;
+        pf[u] = 0;
+        if (e < MS && slab + 1 < g.N) {
+          const int sp = sm.sidx[e];
+          if (sp >= 0) pf[u] = (CT)v.r[(int64_t)(slab + 1) * g.S + sp];
+        }
+      }
+      // this slab's block
+      const bool got = mbar_wait_bounded(smem_u32(&sb.full[b]), (b ? used1 : used0) & 1u);
+      if (!__all_sync(FULL, got)) {
+        aborted = true;
+        break;
+      }
+      if (b) ++used1;
+      else ++used0;
+      pending &= ~(1u << b);
+      const FT* A = sb.buf[b];
+      CT acc[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = 0;
+#pragma unroll 4
+      for (int c = 0; c < MS; ++c) {
+        const CT xc = sm.rhs[0][c];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int row = lane + 32 * r;
+          if (row < MS) acc[r] = fma(widen(A[c * MS + row]), xc, acc[r]);
+        }
+      }
+      __syncwarp();
+      if (slab + 2 < g.N) {  // the buffer is free again: the block two slabs ahead
+        if (lane == 0) {
+          fence_proxy_async();
+          const uint32_t bar = smem_u32(&sb.full[b]);
+          mbar_expect_tx(bar, BYTES);
+          bulk_g2s(smem_u32(sb.buf[b]), fblk + (int64_t)(slab + 2) * SB::BLK, BYTES, bar);
+        }
+        pending |= 1u << b;
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int row = lane + 32 * r;
+        if (row < MS) sm.y[0][row] = acc[r];
+      }
+      __syncwarp();
+      for (int s = lane; s < MS; s += 32) {
+        if (bs.kind == 0) {
+          v.out[((int64_t)slab * g.npatch() + blk) * MS + s] = (double)sm.y[0][s];
+        } else if (sm.sidx[s] >= 0) {
+          v.out[(int64_t)slab * g.S + sm.sidx[s]] = (double)sm.y[0][s];
+        }
+      }
+      for (int e = lane; e < 2 * nv2g; e += 32) {
+        const int c = e / nv2g, tt = e % nv2g;
+        sm.yp[c][tt] = sm.y[0][c * nv2g + tt];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < RP; ++u) {
+        const int e = lane + 32 * u;
+        if (e < MS) sm.rhs[0][e] = pf[u];
+      }
+    }
+    __syncwarp();
+  }
+  if (aborted) {
+    // this warp's copies still in flight land before it leaves (each wait bounded)
+    if (lane == 0) {
+      if (pending & 1u) mbar_wait_bounded(smem_u32(&sb.full[0]), used0 & 1u);
+      if (pending & 2u) mbar_wait_bounded(smem_u32(&sb.full[1]), used1 & 1u);
+      atomicExch(err, 1);
+    }
+  }
+}
+
+template <typename FT>
+__global__ void __launch_bounds__(32 * kWarpBulkWarps)
+warp_bulk_apply_kernel(FeTables T, SingleItems<FT> items, int64_t nitems, int* __restrict__ err) {
+  warp_apply_bulk<FT>(T, items, nitems, err);
+}
+
+template <typename FT>
+__global__ void __launch_bounds__(32 * kWarpBulkWarps)
+bt_warp_bulk_apply_kernel(const BatchSeg* __restrict__ segs, int nseg, int64_t nitems, FeTables T,
+                          const double* __restrict__ r, double* __restrict__ yp, int* __restrict__ err) {
+  warp_apply_bulk<FT>(T, BatchItems<FT>{segs, nseg, r, yp, false}, nitems, err);
+}
+
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 __device__ __forceinline__ int ceildiv(int a, int b) { return -floordiv(-a, b); }
 
@@ -1483,12 +1682,54 @@ void run_bt_warp_apply(const BatchSeg* segs, int nseg, int64_t items, const FeTa
   WR_LAUNCH_CHECK();
 }
 
+template <typename FT>
+void run_warp_bulk_apply(const LevelGeom& g, const FeTables& T, const BlockSet& bs, const FT* factors, const double* r,
+                         double* out, int* err, const double* prev, cudaStream_t s, const ChunkPlan* cp) {
+  auto kern = warp_bulk_apply_kernel<FT>;
+  const size_t smem = sizeof(WarpBulkSmem<FT>) * kWarpBulkWarps;
+  static const int grid_cap = persistent_grid(kern, 32 * kWarpBulkWarps, smem);
+  const int nblk = g.npatch();
+  SingleItems<FT> items{g, bs, factors, r, out, prev};
+  items.nblk = nblk;
+  items.prev_mode = prev ? 2 : 0;
+  int64_t nitems = nblk;
+  if (cp && cp->nchunk > 1) {
+    items.nchunk = cp->nchunk;
+    items.Lc = cp->Lc;
+    items.c_first = cp->c_first;
+    items.prev_mode = cp->prev_mode;
+    items.prev = cp->prev;
+    nitems = (int64_t)nblk * (cp->nchunk - cp->c_first);
+  }
+  if (nitems <= 0) return;
+  const int64_t want = (nitems + kWarpBulkWarps - 1) / kWarpBulkWarps;
+  const int grid = want < grid_cap ? (int)want : grid_cap;
+  kern<<<grid, 32 * kWarpBulkWarps, smem, s>>>(T, items, nitems, err);
+  WR_LAUNCH_CHECK();
+}
+
+template <typename FT>
+void run_bt_warp_bulk_apply(const BatchSeg* segs, int nseg, int64_t items, const FeTables& T, const double* r,
+                            double* yp, int* err, cudaStream_t s) {
+  auto kern = bt_warp_bulk_apply_kernel<FT>;
+  const size_t smem = sizeof(WarpBulkSmem<FT>) * kWarpBulkWarps;
+  static const int grid_cap = persistent_grid(kern, 32 * kWarpBulkWarps, smem);
+  if (items <= 0) return;
+  const int64_t want = (items + kWarpBulkWarps - 1) / kWarpBulkWarps;
+  const int grid = want < grid_cap ? (int)want : grid_cap;
+  kern<<<grid, 32 * kWarpBulkWarps, smem, s>>>(segs, nseg, items, T, r, yp, err);
+  WR_LAUNCH_CHECK();
+}
+
 template <int K, int Q, typename FT>
 void apply_variant(int variant, const LevelGeom& g, const FeTables& T, const BlockSet& bs, const FT* factors,
                    const double* r, double* out, int* err, const double* prev, cudaStream_t s,
                    const ChunkPlan* cp) {
   if (variant < 0) variant = default_apply_variant(K);
-  if (variant == 3) run_warp_apply<K, Q, FT>(g, T, bs, factors, r, out, prev, s, cp);
+  if (variant == 4) {  // the bulk-copy warp tile exists for Q2/Q1 DG(0); elsewhere it is tile 3
+    if constexpr (K == 1 && Q == 0) run_warp_bulk_apply<FT>(g, T, bs, factors, r, out, err, prev, s, cp);
+    else run_warp_apply<K, Q, FT>(g, T, bs, factors, r, out, prev, s, cp);
+  } else if (variant == 3) run_warp_apply<K, Q, FT>(g, T, bs, factors, r, out, prev, s, cp);
   else if (variant == 0) run_apply<K, Q, FT, 2 * K - 1, 0>(g, T, bs, factors, r, out, err, prev, s, cp);
   else if (variant == 1) run_apply<K, Q, FT, 2 * K - 1, 1>(g, T, bs, factors, r, out, err, prev, s, cp);
   else run_apply<K, Q, FT, 2 * K - 1, 2>(g, T, bs, factors, r, out, err, prev, s, cp);
@@ -1498,7 +1739,10 @@ template <int K, int Q, typename FT>
 void bt_apply_variant(int variant, const BatchSeg* segs, int nseg, int64_t items, const FeTables& T,
                       const double* r, double* yp, int* err, cudaStream_t s) {
   if (variant < 0) variant = default_apply_variant(K);
-  if (variant == 3) run_bt_warp_apply<K, Q, FT>(segs, nseg, items, T, r, yp, s);
+  if (variant == 4) {
+    if constexpr (K == 1 && Q == 0) run_bt_warp_bulk_apply<FT>(segs, nseg, items, T, r, yp, err, s);
+    else run_bt_warp_apply<K, Q, FT>(segs, nseg, items, T, r, yp, s);
+  } else if (variant == 3) run_bt_warp_apply<K, Q, FT>(segs, nseg, items, T, r, yp, s);
   else if (variant == 0) run_bt_apply<K, Q, FT, 2 * K - 1, 0>(segs, nseg, items, T, r, yp, false, err, s);
   else if (variant == 1) run_bt_apply<K, Q, FT, 2 * K - 1, 1>(segs, nseg, items, T, r, yp, false, err, s);
   else run_bt_apply<K, Q, FT, 2 * K - 1, 2>(segs, nseg, items, T, r, yp, false, err, s);

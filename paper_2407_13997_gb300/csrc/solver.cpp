@@ -842,7 +842,7 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
              c->opt.store_factors == WR_STORE_AUTO,
          "store_factors must be WR_STORE, WR_RECOMPUTE or WR_STORE_AUTO");
     need(c->opt.recompute_slabs >= 0 && c->opt.memory_budget_mb >= 0, "bad recompute_slabs / memory_budget_mb");
-    need(c->opt.apply_tile >= -1 && c->opt.apply_tile < kApplyTileVariants, "apply_tile must be -1 .. 3");
+    need(c->opt.apply_tile >= -1 && c->opt.apply_tile < kApplyTileVariants, "apply_tile must be -1 .. 4");
     c->s = static_cast<cudaStream_t>(stream);
     c->k = p->k; c->q = p->q; c->N = p->n_slabs; c->T = p->T;
     c->ph.kind = p->kind; c->ph.steady = p->steady; c->ph.nu = p->nu; c->ph.conv = p->conv; c->ph.T = p->T;

@@ -229,7 +229,7 @@ void cr_gather_column(const LevelGeom& g, const BlockSet& bs, int nchunk, int Lc
 // carry[c] = e_c + T_c carry[c - 1] for c = 0 .. nchunk - 2 (e_c: chunk-end states in Yp)
 void cr_carry(const LevelGeom& g, const BlockSet& bs, int nchunk, int Lc, const double* Tm, const double* Yp,
               double* carry, cudaStream_t s);
-constexpr int kApplyTileVariants = 4;
+constexpr int kApplyTileVariants = 5;
 void launch_scatter(const LevelGeom& g, const BlockSet& bs, const double* Yp, double* y,
                     cudaStream_t s);
 void launch_restrict(const LevelGeom& gf, const LevelGeom& gc, const FeTables& T,

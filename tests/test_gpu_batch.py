@@ -128,7 +128,7 @@ def test_graph_replay_equals_eager_cycles_bitwise():
     assert all(torch.equal(a, b) for a, b in zip(Ug, Ue))
 
 
-@pytest.mark.parametrize("tile", [2, 3])
+@pytest.mark.parametrize("tile", [2, 3, 4])
 def test_batched_apply_tiles_match_single_instances(tile):
     ws = members_q2q1()
     rng = np.random.default_rng(8)

@@ -274,11 +274,12 @@ def test_time_parallel_patch_solve_matches_oracle(w):
     seq.close()
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2, 3])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("w", [CASES[0], CASES[1], CASES[2], CASES[3]], ids=[IDS[0], IDS[1], IDS[2], IDS[3]])
 def test_every_apply_tile_matches_oracle(w, tile):
     """Each smoother-apply tile the autotuner can pick (one CTA per patch at 1, 2 or 3
-    CTAs per SM, or one warp per patch) reproduces the oracle's smoother."""
+    CTAs per SM, one warp per patch, or one warp per patch with bulk-copied blocks)
+    reproduces the oracle's smoother."""
     s = Setup(w, options=wrmg.default_options(apply_tile=tile, time_parallel=0))
     s.ctx.linearise(cuda(s.W[-1]), eig=False)
     for l in range(1, len(s.discs)):
