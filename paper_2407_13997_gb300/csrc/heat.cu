@@ -55,55 +55,108 @@ __device__ __forceinline__ void stage_heat_tab(const FeTables& T, HeatTab& t) {
   for (int a = threadIdx.x; a < WR_MAX_NT; a += blockDim.x) t.tau0[a] = T.tau0[a];
 }
 
-// y = J x (RES = false) or F(x) = J x - b (RES = true: the slab-0 initial-data term).
+// y = J x (RES = false) or F(x) = J x - b (RES = true: the slab-0 initial-data term),
+// by tensor-product passes.  On slab n,
+//   y_a = sum_b Kt[a][b] M x_b + dt nu sum_b Wt[a][b] K x_b - tau_a(0) M x^-,
+// M = My (x) Mx, K = Ky (x) Mx + My (x) Kx (global 1D matrices with 2K+1 bands), x^- the
+// last temporal DoF of slab n-1 (slab 0: the initial data for F, zero for J).
+// Pass 1 (x direction), one thread per (slab, component, node), components
+// x_0 .. x_{NT-1} and x^-:  tM = Mx x_c and tK = Kx x_c along each mesh row, stored
+// [slab][c][tM, tK][node].  Pass 2 (y direction and the temporal mixing), one thread
+// per (slab, node): M x_b = My tM_b, K x_b = Ky tM_b + My tK_b, M x^- = My tM_NT, then
+// every a.  About 50 FP64 operations per DoF instead of a (2K+1)^2-tap stencil with
+// its coefficients formed per tap.
 template <int K, int Q, bool RES>
-__global__ void heat_op_kernel(LevelGeom g, FeTables Tp, PhysParams ph, const double* __restrict__ x,
-                               double* __restrict__ y) {
-  constexpr int NT = Q + 1;
+__global__ void heat_xpass_kernel(LevelGeom g, FeTables Tp, PhysParams ph, const double* __restrict__ x,
+                                  double* __restrict__ t) {
+  constexpr int NT = Q + 1, NC = NT + 1;
   __shared__ HeatTab T;
   stage_heat_tab(Tp, T);
   __syncthreads();
+  const int S = g.S, nv = g.nv;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= g.ndofs) return;
-  const int nv = g.nv, S = g.S;
-  const int64_t blk = idx / S;
-  const int sp = int(idx % S), slab = int(blk / NT), a = int(blk % NT);
+  if (idx >= (int64_t)g.N * NC * S) return;
+  const int sp = int(idx % S);
+  const int64_t sc = idx / S;
+  const int c = int(sc % NC), slab = int(sc / NC);
   const int ix = sp % nv, iy = sp / nv;
-  const double h = g.h, ih = 1.0 / h, cdt = g.dt * ph.nu;
-  double mx[2 * K + 1], kx[2 * K + 1];
+  const double h = g.h, ih = 1.0 / h;
+  double am = 0.0, ak = 0.0;
 #pragma unroll
   for (int d = 0; d <= 2 * K; ++d) {
     const int jx = ix - K + d;
-    const bool ok = jx >= 0 && jx < nv;
-    mx[d] = ok ? h * heat_1d<K>(T.m1, g.n, ix, jx) : 0.0;
-    kx[d] = ok ? ih * heat_1d<K>(T.k1, g.n, ix, jx) : 0.0;
+    if (jx < 0 || jx >= nv) continue;
+    const int64_t node = (int64_t)iy * nv + jx;
+    double v;
+    if (c < NT) {
+      v = x[((int64_t)slab * NT + c) * S + node];
+    } else if (slab > 0) {
+      v = x[((int64_t)(slab - 1) * NT + NT - 1) * S + node];
+    } else if (RES) {
+      v = ph.u0 ? ph.u0[node] : heat_initial(ph, jx * (h / K), iy * (h / K));
+    } else {
+      v = 0.0;
+    }
+    am = fma(h * heat_1d<K>(T.m1, g.n, ix, jx), v, am);
+    ak = fma(ih * heat_1d<K>(T.k1, g.n, ix, jx), v, ak);
   }
-  double acc = 0.0;
-  for (int dy = 0; dy <= 2 * K; ++dy) {
-    const int jy = iy - K + dy;
-    if (jy < 0 || jy >= nv) continue;
-    const double my = h * heat_1d<K>(T.m1, g.n, iy, jy), ky = ih * heat_1d<K>(T.k1, g.n, iy, jy);
-    if (my == 0.0 && ky == 0.0) continue;
-    for (int dx = 0; dx <= 2 * K; ++dx) {
-      const int jx = ix - K + dx;
-      if (jx < 0 || jx >= nv) continue;
-      const double m2 = my * mx[dx], k2 = ky * mx[dx] + my * kx[dx];
-      const int64_t node = (int64_t)jy * nv + jx;
+  double* tc = t + (sc * 2) * S;
+  tc[sp] = am;
+  tc[S + sp] = ak;
+}
+
+template <int K, int Q>
+__global__ void heat_ypass_kernel(LevelGeom g, FeTables Tp, PhysParams ph, const double* __restrict__ t,
+                                  double* __restrict__ y) {
+  constexpr int NT = Q + 1, NC = NT + 1;
+  __shared__ HeatTab T;
+  stage_heat_tab(Tp, T);
+  __syncthreads();
+  const int S = g.S, nv = g.nv;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)g.N * S) return;
+  const int sp = int(idx % S), slab = int(idx / S);
+  const int ix = sp % nv, iy = sp / nv;
+  const double h = g.h, ih = 1.0 / h, cdt = g.dt * ph.nu;
+  double my[2 * K + 1], ky[2 * K + 1];
 #pragma unroll
-      for (int b = 0; b < NT; ++b)
-        acc = fma(T.Kt[a][b] * m2 + cdt * T.Wt[a][b] * k2, x[((int64_t)slab * NT + b) * S + node], acc);
-      double prev;
-      if (slab > 0) {
-        prev = x[((int64_t)(slab - 1) * NT + NT - 1) * S + node];
-      } else if (RES) {
-        prev = ph.u0 ? ph.u0[node] : heat_initial(ph, jx * (h / K), jy * (h / K));
-      } else {
-        prev = 0.0;
-      }
-      acc = fma(-T.tau0[a] * m2, prev, acc);
+  for (int d = 0; d <= 2 * K; ++d) {
+    const int jy = iy - K + d;
+    const bool ok = jy >= 0 && jy < nv;
+    my[d] = ok ? h * heat_1d<K>(T.m1, g.n, iy, jy) : 0.0;
+    ky[d] = ok ? ih * heat_1d<K>(T.k1, g.n, iy, jy) : 0.0;
+  }
+  double Mb[NT], Kb[NT], Mp = 0.0;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const double* tc = t + (((int64_t)slab * NC + c) * 2) * S;
+    double m = 0.0, kk = 0.0;
+#pragma unroll
+    for (int d = 0; d <= 2 * K; ++d) {
+      const int jy = iy - K + d;
+      if (jy < 0 || jy >= nv) continue;
+      const int64_t node = (int64_t)jy * nv + ix;
+      const double tm = tc[node];
+      m = fma(my[d], tm, m);
+      if (c < NT) kk = fma(ky[d], tm, fma(my[d], tc[S + node], kk));
+    }
+    if (c < NT) {
+      Mb[c] = m;
+      Kb[c] = kk;
+    } else {
+      Mp = m;
     }
   }
-  y[idx] = acc;
+#pragma unroll
+  for (int a = 0; a < NT; ++a) {
+    double acc = -T.tau0[a] * Mp;
+#pragma unroll
+    for (int b = 0; b < NT; ++b) {
+      acc = fma(T.Kt[a][b], Mb[b], acc);
+      acc = fma(cdt * T.Wt[a][b], Kb[b], acc);
+    }
+    y[((int64_t)slab * NT + a) * S + sp] = acc;
+  }
 }
 
 // Block layout: PX x PX node window per temporal DoF, slot = a PX^2 + ly PX + lx;
@@ -467,15 +520,23 @@ bool heat_block_fits(int k, int q, int n_whole) { return heat_factor_smem(heat_b
   else if (g.k == 3 && g.q == 3) { constexpr int K = 3, Q = 3; stmt; }      \
   else throw WrError(WR_ERR_ARG, "heat: k must be 1..3 and q 0..3");
 
+size_t heat_op_scratch(const LevelGeom& g) { return (size_t)g.N * (g.nt + 1) * 2 * g.S; }
+
 void heat_jacobian(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* x, double* y,
-                   cudaStream_t s) {
-  HEAT_KQ((heat_op_kernel<K, Q, false><<<grid_of(g.ndofs), 256, 0, s>>>(g, T, ph, x, y)));
+                   double* tmp, cudaStream_t s) {
+  const int64_t n1 = (int64_t)g.N * (g.nt + 1) * g.S, n2 = (int64_t)g.N * g.S;
+  HEAT_KQ((heat_xpass_kernel<K, Q, false><<<grid_of(n1), 256, 0, s>>>(g, T, ph, x, tmp)));
+  WR_LAUNCH_CHECK();
+  HEAT_KQ((heat_ypass_kernel<K, Q><<<grid_of(n2), 256, 0, s>>>(g, T, ph, tmp, y)));
   WR_LAUNCH_CHECK();
 }
 
 void heat_residual(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* x, double* y,
-                   cudaStream_t s) {
-  HEAT_KQ((heat_op_kernel<K, Q, true><<<grid_of(g.ndofs), 256, 0, s>>>(g, T, ph, x, y)));
+                   double* tmp, cudaStream_t s) {
+  const int64_t n1 = (int64_t)g.N * (g.nt + 1) * g.S, n2 = (int64_t)g.N * g.S;
+  HEAT_KQ((heat_xpass_kernel<K, Q, true><<<grid_of(n1), 256, 0, s>>>(g, T, ph, x, tmp)));
+  WR_LAUNCH_CHECK();
+  HEAT_KQ((heat_ypass_kernel<K, Q><<<grid_of(n2), 256, 0, s>>>(g, T, ph, tmp, y)));
   WR_LAUNCH_CHECK();
 }
 

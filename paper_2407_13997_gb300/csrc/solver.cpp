@@ -117,6 +117,7 @@ struct wr_ctx {
   bool heat = false;     // the heat equation (one scalar field) instead of Navier-Stokes
   double t0 = 0.0;       // the problem's start time
   double* u0 = nullptr;  // slab-0 initial state set by wr_set_initial_state (a finest-level spatial block)
+  double* htmp = nullptr;  // heat equation: scratch of the tensor-product operator passes
   std::vector<void*> allocs;
   int64_t bytes = 0;
   bool linearised = false;
@@ -200,7 +201,7 @@ struct wr_ctx {
   double norm(int64_t n, const double* x) { return std::sqrt(dot(n, x, x)); }
 
   void jac(int l, const double* x, double* y) {
-    if (heat) heat_jacobian(L[l].g, tab, ph, x, y, s);
+    if (heat) heat_jacobian(L[l].g, tab, ph, x, y, htmp, s);
     else launch_jacobian(L[l].g, tab, ph, L[l].W, x, y, ye, s);
   }
   // J inside the preconditioner (smoother residuals, the residual restricted to the
@@ -222,7 +223,7 @@ struct wr_ctx {
     if (!heat) launch_project_pressure(g, tab, x, s);  // the heat operator has no null space
   }
   void residual(const double* U, double* Fo) {
-    if (heat) heat_residual(fine().g, tab, ph, U, Fo, s);
+    if (heat) heat_residual(fine().g, tab, ph, U, Fo, htmp, s);
     else launch_residual(fine().g, tab, ph, U, Fo, ye, s);
   }
 
@@ -795,6 +796,7 @@ static int create_heat(wr_ctx* c, const wr_problem* p) {
   c->derr = c->alloc<int>(1);
   c->fstat = c->alloc<int>(1);
   c->u0 = c->alloc<double>(c->fine().g.S);
+  c->htmp = c->alloc<double>(heat_op_scratch(c->fine().g));
   c->slots = c->alloc<int>(32);
   if (c->dry) return WR_OK;
   WR_CUDA(cudaMemsetAsync(c->derr, 0, sizeof(int), c->s));

@@ -320,10 +320,12 @@ int tune_apply_variant(const TuneKey& key, cudaStream_t s, const std::function<v
 LevelGeom make_heat_geom(int n, int k, int q, int N, double T);
 int heat_block_size(int k, int q, int n_whole);  // slots per (block, slab): (q+1) PX^2; n_whole = 0: a patch
 bool heat_block_fits(int k, int q, int n_whole);  // the block's FP64 inversion fits in shared memory
+// y = J x and F(x) by tensor-product passes; tmp: heat_op_scratch(g) doubles of device scratch
+size_t heat_op_scratch(const LevelGeom& g);
 void heat_jacobian(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* x, double* y,
-                   cudaStream_t s);
+                   double* tmp, cudaStream_t s);
 void heat_residual(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* x, double* y,
-                   cudaStream_t s);
+                   double* tmp, cudaStream_t s);
 // inverts every (patch, slab) block (coarse: the single whole-mesh block); st as in launch_block_factor
 void heat_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph, bool coarse, double* f, int* st,
                  cudaStream_t s);
