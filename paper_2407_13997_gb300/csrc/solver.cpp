@@ -51,6 +51,7 @@ int tune_apply_variant(const TuneKey& key, cudaStream_t s, const std::function<v
   int best = -1;
   float best_ms = 0.f;
   for (int v = 0; v < kApplyTileVariants; ++v) {
+    if (v == 4 && !(key.k == 1 && key.q == 0)) continue;  // tile 4 exists for Q2/Q1 DG(0) only (else it is tile 3)
     launch(v);
     WR_CUDA(cudaEventRecord(e0, s));
     launch(v);
