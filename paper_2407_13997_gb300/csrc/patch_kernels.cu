@@ -1393,6 +1393,15 @@ __device__ __forceinline__ void warp_apply_bulk(const FeTables& T, const Items& 
       const int sp = sm.sidx[s];
       sm.rhs[0][s] = sp >= 0 ? (CT)v.r[sp] : (CT)0;
     }
+    // the right-hand sides are loaded into registers two slabs ahead of their use, so
+    // that a load's latency is covered by a whole slab of work
+    static_assert(RP == 2, "two right-hand-side entries per lane");
+    const int sp0 = sm.sidx[lane], sp1 = lane + 32 < MS ? sm.sidx[lane + 32] : -1;
+    CT pa = 0, pb = 0;  // slab + 1
+    if (1 < g.N) {
+      if (sp0 >= 0) pa = (CT)v.r[(int64_t)g.S + sp0];
+      if (sp1 >= 0) pb = (CT)v.r[(int64_t)g.S + sp1];
+    }
     for (int slab = 0; slab < g.N; ++slab) {
       const int b = slab & 1;
       __syncwarp();
@@ -1413,16 +1422,10 @@ __device__ __forceinline__ void warp_apply_bulk(const FeTables& T, const Items& 
         }
         __syncwarp();
       }
-      // register prefetch of the next slab's right-hand side
-      CT pf[RP];
-#pragma unroll
-      for (int u = 0; u < RP; ++u) {
-        const int e = lane + 32 * u;
-        pf[u] = 0;
-        if (e < MS && slab + 1 < g.N) {
-          const int sp = sm.sidx[e];
-          if (sp >= 0) pf[u] = (CT)v.r[(int64_t)(slab + 1) * g.S + sp];
-        }
+      CT qa = 0, qb = 0;  // slab + 2
+      if (slab + 2 < g.N) {
+        if (sp0 >= 0) qa = (CT)v.r[(int64_t)(slab + 2) * g.S + sp0];
+        if (sp1 >= 0) qb = (CT)v.r[(int64_t)(slab + 2) * g.S + sp1];
       }
       // this slab's block
       const bool got = mbar_wait_bounded(smem_u32(&sb.full[b]), (b ? used1 : used0) & 1u);
@@ -1474,11 +1477,10 @@ __device__ __forceinline__ void warp_apply_bulk(const FeTables& T, const Items& 
         sm.yp[c][tt] = sm.y[0][c * nv2g + tt];
       }
       __syncwarp();
-#pragma unroll
-      for (int u = 0; u < RP; ++u) {
-        const int e = lane + 32 * u;
-        if (e < MS) sm.rhs[0][e] = pf[u];
-      }
+      sm.rhs[0][lane] = pa;
+      if (lane + 32 < MS) sm.rhs[0][lane + 32] = pb;
+      pa = qa;
+      pb = qb;
     }
     __syncwarp();
   }
