@@ -147,3 +147,22 @@ def test_fgmres_wrmg_reaches_the_direct_solution_in_few_iterations(k, q, nc):
     assert its <= 5, its   # the paper reports 3 on its triangle meshes
     U2, its2 = heat_solve(hier, rtol=1e-12, atol=0.0)
     assert np.abs(U2 - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("q", [0, 1, 2, 3])
+def test_all_at_once_equals_slab_by_slab_solves(q):
+    """Causality of DG(q) in time (Eq. dgintime): the space-time system is block lower
+    bidiagonal, so its solution equals N one-slab solves, each started from the
+    previous slab's end value (the last temporal DoF, the right-Radau point s = 1)."""
+    pb = HeatProblem(nu=0.7, T=0.3)
+    N = 3
+    d = HeatDiscretisation(4, 2, q, N, pb)
+    U = spla.spsolve(d.jacobian().tocsc(), d.rhs())
+    state = None
+    for n in range(N):
+        one = HeatDiscretisation(4, 2, q, 1, HeatProblem(nu=0.7, T=0.3 / N))
+        one.initial_state = state
+        u1 = spla.spsolve(one.jacobian().tocsc(), one.rhs())
+        blk = U[d.block(n, 0):d.block(n + 1, 0)]
+        assert np.abs(u1 - blk).max() < 1e-12 * np.abs(blk).max(), (q, n)
+        state = u1[one.block(0, one.nt - 1):one.block(0, one.nt - 1) + one.S]
