@@ -4,6 +4,7 @@ import pytest
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
+from oracle.basis import gauss_legendre, lagrange
 from oracle.fem import Discretisation, Problem
 from paper_2407_13997_gb300.inputs import fourier_forcing
 
@@ -124,6 +125,40 @@ def test_end_point_error_converges_at_order_2q_plus_1(q, rate):
     errs = [np.abs(end_value(N) - ref).max() for N in (3, 6, 12)]
     ratios = [errs[i] / errs[i + 1] for i in range(2)]
     assert abs(ratios[-1] / rate - 1.0) < 0.15, (errs, ratios)
+
+
+@pytest.mark.parametrize("q", [0, 1])
+def test_time_error_in_l2_converges_at_order_q_plus_1(q):
+    """DG(q) in time: the L2-in-time error of the velocity converges at O(dt^{q+1}),
+    the approximation order of degree-q polynomials in time.  Linear Stokes with
+    Taylor-Green decay data; the error is measured against N = 192 slabs on the same
+    mesh (so the spatial error cancels), with the DG polynomials evaluated at q+3
+    Gauss points per slab."""
+    pb = Problem(kind="taylor_green", nu=1.0 / np.pi ** 2, conv=0.0, T=0.25)
+
+    def solve(N):
+        d = Discretisation(2, 1, q, N, pb)
+        return d, direct_solve(d)
+
+    def velocity_at(d, U, t):
+        n = min(int(t / d.dt), d.N - 1)
+        V, _ = lagrange(d.tm.nodes, [t / d.dt - n])
+        return sum(V[a, 0] * U[d.block(n, a):d.block(n, a) + d.off_p] for a in range(d.nt))
+
+    dref, Uref = solve(192)
+    xs, ws = gauss_legendre(q + 3)
+    errs = []
+    for N in (2, 4, 8):
+        d, U = solve(N)
+        e2 = 0.0
+        for n in range(N):
+            for x, wgt in zip(xs, ws):
+                t = (n + x) * d.dt
+                diff = velocity_at(d, U, t) - velocity_at(dref, Uref, t)
+                e2 += wgt * d.dt * np.sum(diff ** 2)
+        errs.append(np.sqrt(e2))
+    ratios = [errs[i] / errs[i + 1] for i in range(2)]
+    assert abs(ratios[-1] / 2 ** (q + 1) - 1.0) < 0.15, (errs, ratios)
 
 
 def l2_velocity_error(d, U, slab, a):
