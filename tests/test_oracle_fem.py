@@ -187,6 +187,25 @@ def test_taylor_green_spatial_velocity_error_is_third_order_for_q2q1():
     assert ratios[-1] > 6.5, (errs, ratios)
 
 
+def test_taylor_green_pressure_error_is_second_order_for_q2q1():
+    """Taylor-Hood Q2/Q1: pressure L2 error O(h^{k+1}) = O(h^2), with the sign
+    reading Phi = -p (the discrete pressure approximates minus the strong-form
+    pressure of Eq. nsfem's weak form); the Taylor-Green pressure is mean-free, like
+    the discrete one."""
+    errs = []
+    for n in (4, 8, 16):
+        pb = Problem(kind="taylor_green", nu=0.05, conv=1.0, T=0.02)
+        d = Discretisation(n, 1, 1, 1, pb)
+        U = direct_solve(d)
+        t = d.time_nodes(0)[1]
+        off = d.block(0, 1) + d.off_p
+        ph = U[off:off + d.np_ ** 2][d.cell_pnodes] @ d.Vp
+        ex = pb.exact_pressure(d.qpx, d.qpy, t)
+        errs.append(np.sqrt(np.sum((ph + ex) ** 2 * d.wq2[None, :])))
+    ratios = [errs[i] / errs[i + 1] for i in range(2)]
+    assert 3.4 < ratios[-1] < 5.5, (errs, ratios)
+
+
 def test_discrete_solution_is_discretely_divergence_free():
     d = Discretisation(4, 1, 1, 2, fourier_problem())
     U = direct_solve(d)
