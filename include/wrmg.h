@@ -178,6 +178,9 @@ int wr_create(wr_ctx **out, const wr_problem *p, const wr_options *o, void *cuda
 /* Device bytes wr_create would allocate for (*p, *o), without allocating. */
 int wr_estimate_bytes(const wr_problem *p, const wr_options *o, int64_t *out);
 int wr_destroy(wr_ctx *c);
+/* Description of the last failure of context c; with c = NULL, of the last
+ * failed call of this host thread that takes no context
+ * (wr_apply_jacobian_static), or "null context" if there was none. */
 const char *wr_last_error(const wr_ctx *c);
 
 /* Levels are numbered 0 (coarsest, n_coarse) .. L (finest). */
@@ -378,20 +381,25 @@ int wr_profile_smoother(wr_ctx *c, int level, double *total_ms, int *launches);
  * allocator's implicit synchronisation).  The paper has no counterpart; this
  * is a service of the library.
  *   W, x, y: caller-owned device pointers, canonical layout, FP64, length
- *   n_slabs (q+1) (2 nv^2 + np^2); x and y must not alias.  Only n_fine, k, q,
- *   n_slabs, T, nu and conv of *p are read.  Work is enqueued on cuda_stream.
+ *   n_slabs (q+1) (2 nv^2 + np^2); x and y must not alias.  Of *p, n_fine, k,
+ *   q, n_slabs, T, nu and conv are used, and kind is checked: it must be a
+ *   Navier-Stokes kind (WR_TAYLOR_GREEN, WR_POLY, WR_FOURIER or WR_LID; the
+ *   heat kinds are refused), none of which changes J.  Work is enqueued on
+ *   cuda_stream, which must belong to the current device (else WR_ERR_ARG).
  * Scratch: a fixed 64 MiB array of this library's static device memory (8 Mi
  *   doubles), held by every GPU that loads the library until the process exits.
  *   Problems that need more, i.e. n_slabs n_fine^2 (q+1) (2 (k+2)^2 + (k+1)^2)
  *   > 8 Mi, are rejected with WR_ERR_ARG before any work is enqueued (other
- *   WR_ERR_ARG causes: null or aliased pointers, unsupported k or q).
+ *   WR_ERR_ARG causes: null or aliased pointers, unsupported k, q or kind, a
+ *   stream of another device).
  * The first call on a device looks up the array's device address on that device
  *   (cudaGetSymbolAddress); make that first call before any stream capture.
  * Every call shares the array: calls that overlap on the GPU (other streams,
  *   other threads) race and must be serialised by the caller.  The array keeps
  *   the last call's contents; each call writes every entry it reads first, so
  *   nothing needs clearing.
- * Returns WR_OK, WR_ERR_ARG, or WR_ERR_CUDA (launch failure). */
+ * Returns WR_OK, WR_ERR_ARG, or WR_ERR_CUDA (launch failure); after a failure
+ *   wr_last_error(NULL) describes it (per host thread). */
 int wr_apply_jacobian_static(const wr_problem *p, const double *W, const double *x, double *y, void *cuda_stream);
 
 /* FP64 FMA throughput of this GPU, measured by a register-only kernel

@@ -69,6 +69,12 @@ struct wr_batch {
   double *F = nullptr, *w = nullptr, *step = nullptr, *U = nullptr, *vb = nullptr, *vx = nullptr;
   double *partials = nullptr, *dres = nullptr, *hres = nullptr, *hcoef = nullptr, *dcoef = nullptr;
   int64_t* dseeds = nullptr;
+  // device-resident Krylov scalars, member-indexed: FGMRES Hessenberg ((R+1) x R),
+  // rotations (R), right-hand side (R+1) and least-squares solution (R); the Arnoldi
+  // Hessenberg of the eigen-estimate ((e+1) x e); norms, reciprocals and statuses
+  double *kH = nullptr, *kcs = nullptr, *ksn = nullptr, *kg = nullptr, *ky = nullptr, *keH = nullptr;
+  double *kbeta = nullptr, *kinv = nullptr, *kstat = nullptr;
+  double* hkH = nullptr;  // pinned host copy of keH
   int *derr = nullptr, *herr = nullptr, *fstat = nullptr;
   std::vector<char> active;
   std::vector<Table> smooth;  // per depth: members with a smoothing level there
@@ -99,6 +105,7 @@ struct wr_batch {
     for (void* p : allocs) cudaFree(p);
     if (hres) cudaFreeHost(hres);
     if (hcoef) cudaFreeHost(hcoef);
+    if (hkH) cudaFreeHost(hkH);
     if (herr) cudaFreeHost(herr);
   }
 
@@ -403,85 +410,82 @@ struct wr_batch {
     upload_chebyshev();
   }
 
-  // 10-step Arnoldi (MGS) on M^{-1} J for every member with a smoothing level at depth d
+  // 10-step Arnoldi (MGS) on M^{-1} J for every member with a smoothing level at depth
+  // d, all on the device (after a member's breakdown its basis vectors are zero); the
+  // host reads the Hessenbergs once at the end
   void eigen_depth(int d) {
     Table& t = smooth[d];
     if (!t.n) return;
-    const int mdim = opt.eig_steps;
+    const int ne = opt.eig_steps;
+    const int64_t es = (int64_t)(ne + 1) * ne;
     std::vector<int64_t> seeds(t.n);
     for (int i = 0; i < t.n; ++i) seeds[i] = mem[t.members[i]].L - d;  // seed = level index
     WR_CUDA(cudaMemcpyAsync(dseeds, seeds.data(), sizeof(int64_t) * t.n, cudaMemcpyHostToDevice, s));
     bt_splitmix(t.d, t.n, t.dofs, dseeds, V[0], s);
-    std::vector<std::vector<double>> H(t.n, std::vector<double>((mdim + 1) * mdim, 0.0));
-    std::vector<int> mm(t.n, mdim);
-    std::vector<char> live(t.n, 1);
-    std::vector<double> nrm = dots(t, V[0], V[0]), c(t.n);
-    for (int i = 0; i < t.n; ++i) c[i] = 1.0 / std::sqrt(nrm[i]);
-    bt_axpby(t.d, t.n, t.dofs, nullptr, 0.0, V[0], coefs(c), 0.0, V[0], s);
-    for (int j = 0; j < mdim; ++j) {
+    bt_axpy_norm(t.d, t.n, nullptr, 0, -1, nullptr, V[0], partials, kbeta, 1, 0, kinv, -1, nullptr, 0, s);
+    bt_scale_dev(t.d, t.n, t.dofs, kinv, V[0], V[0], s);
+    for (int j = 0; j < ne; ++j) {
       jac_inner(t, V[j], ar[d].t);
       papply(t, d, ar[d].t, V[j + 1]);
-      for (int i = 0; i <= j; ++i) {
-        std::vector<double> h = dots(t, V[j + 1], V[i]);
-        for (int e = 0; e < t.n; ++e) {
-          if (live[e]) H[e][i * mdim + j] = h[e];
-          c[e] = live[e] ? -h[e] : 0.0;
-        }
-        bt_axpby(t.d, t.n, t.dofs, coefs(c), 0.0, V[i], nullptr, 1.0, V[j + 1], s);
-      }
-      std::vector<double> hn = dots(t, V[j + 1], V[j + 1]);
-      for (int e = 0; e < t.n; ++e) {
-        const double v = std::sqrt(hn[e]);
-        if (live[e]) {
-          H[e][(j + 1) * mdim + j] = v;
-          if (v <= 1e-14 * std::fabs(H[e][j * mdim + j]) + 1e-300) {
-            mm[e] = j + 1;
-            live[e] = 0;
-          }
-        }
-        c[e] = (live[e] && v > 0.0) ? 1.0 / v : 1.0;
-      }
-      bt_axpby(t.d, t.n, t.dofs, nullptr, 0.0, V[j + 1], coefs(c), 0.0, V[j + 1], s);
+      for (int i = 0; i <= j; ++i)
+        bt_axpy_dot(t.d, t.n, keH, es, i ? (i - 1) * ne + j : -1, i ? V[i - 1] : nullptr, V[j + 1], V[i], partials,
+                    keH, es, i * ne + j, s);
+      bt_axpy_norm(t.d, t.n, keH, es, j * ne + j, V[j], V[j + 1], partials, keH, es, (j + 1) * ne + j, kinv,
+                   j * ne + j, nullptr, 0, s);
+      bt_scale_dev(t.d, t.n, t.dofs, kinv, V[j + 1], V[j + 1], s);
     }
+    WR_CUDA(cudaMemcpyAsync(hkH, keH, sizeof(double) * es * B, cudaMemcpyDeviceToHost, s));
+    WR_CUDA(cudaMemcpyAsync(herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    WR_CUDA(cudaStreamSynchronize(s));
+    if (*herr) throw WrError(WR_ERR_TIMEOUT, "a bounded wait in the smoother kernel gave up");
     for (int e = 0; e < t.n; ++e) {
       Member& M = mem[t.members[e]];
-      M.lam[M.L - d] = hessenberg_max_real_eig(H[e], mm[e], mdim);
+      std::vector<double> H(hkH + t.members[e] * es, hkH + (t.members[e] + 1) * es);
+      int mm = ne;
+      for (int j = 0; j < ne; ++j)
+        if (H[(j + 1) * ne + j] <= 1e-14 * std::fabs(H[j * ne + j]) + 1e-300) {
+          mm = j + 1;
+          break;
+        }
+      M.lam[M.L - d] = hessenberg_max_real_eig(H, mm, ne);
     }
   }
 
   // ---------------------------------------------------------------- FGMRES and Newton in lock step
-  // x = step for J x = b on the fine table's members; tol per member (indexed by member id)
+  // ||w|| of the members of table t to beta[member] (and to the device: kbeta, 1 / ||w||
+  // in kinv, the FGMRES right-hand side g_b[0]); one synchronisation
+  void member_norms(Table& t, std::vector<double>& beta) {
+    if (!t.n) return;
+    bt_axpy_norm(t.d, t.n, nullptr, 0, -1, nullptr, w, partials, kbeta, 1, 0, kinv, -1, kg, opt.gmres_restart + 1, s);
+    WR_CUDA(cudaMemcpyAsync(hres, kbeta, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+    WR_CUDA(cudaMemcpyAsync(herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    WR_CUDA(cudaStreamSynchronize(s));
+    if (*herr) throw WrError(WR_ERR_TIMEOUT, "a bounded wait in the smoother kernel gave up");
+    for (int m : t.members) beta[m] = hres[m];
+  }
+
+  // x = step for J x = b on the fine table's members; tol per member (indexed by member
+  // id).  Every member's Arnoldi (MGS) coefficients, Givens rotations, least-squares
+  // solve and solution update stay on the device; the host reads the members' residual
+  // estimates once per iteration and their true residual norms once per restart.
   std::vector<int> fgmres(const double* b, double* x, const std::vector<double>& tol) {
     const int R = opt.gmres_restart;
+    const int64_t hs = (int64_t)(R + 1) * R;
     std::vector<int> its(B, 0);
     std::vector<char> saved(active);
     Table& f = fine;
     bt_axpby(f.d, f.n, f.dofs, nullptr, 0.0, x, nullptr, 0.0, x, s);
     bt_copy(f.d, f.n, f.dofs, b, w, s);
     std::vector<double> beta(B, 0.0);
-    {
-      std::vector<double> b2 = dots(f, w, w);
-      for (int i = 0; i < f.n; ++i) beta[f.members[i]] = std::sqrt(b2[i]);
-    }
+    member_norms(f, beta);
     for (int m = 0; m < B; ++m)
       if (active[m] && !(beta[m] > tol[m])) active[m] = 0;
     build_tables();
-    std::vector<std::vector<double>> H(B), gg(B), cs(B), sn(B);
+    std::vector<int> jend(B, 0);
     while (fine.n > 0) {
       Table& t = fine;
-      std::vector<double> c(t.n);
-      for (int i = 0; i < t.n; ++i) c[i] = 1.0 / beta[t.members[i]];
-      bt_copy(t.d, t.n, t.dofs, w, V[0], s);
-      bt_axpby(t.d, t.n, t.dofs, nullptr, 0.0, V[0], coefs(c), 0.0, V[0], s);
-      for (int m : t.members) {
-        H[m].assign((R + 1) * R, 0.0);
-        gg[m].assign(R + 1, 0.0);
-        cs[m].assign(R, 0.0);
-        sn[m].assign(R, 0.0);
-        gg[m][0] = beta[m];
-      }
-      std::vector<int> jend(B, 0);
-      std::vector<char> done(B, 0);
+      bt_scale_dev(t.d, t.n, t.dofs, kinv, w, V[0], s);  // V[0] = w / beta
+      for (int m : t.members) jend[m] = 0;
       int j = 0;
       for (; j < R; ++j) {
         Table& ta = fine;
@@ -489,60 +493,39 @@ struct wr_batch {
         vcycle_via_graph(V[j], Z[j]);
         bt_project_pressure(ta.d, ta.n, ta.tblks, tab, Z[j], false, s);
         jac(ta, Z[j], V[j + 1]);
-        c.assign(ta.n, 0.0);
-        for (int i = 0; i <= j; ++i) {
-          std::vector<double> h = dots(ta, V[j + 1], V[i]);
-          for (int e = 0; e < ta.n; ++e) {
-            H[ta.members[e]][i * R + j] = h[e];
-            c[e] = -h[e];
-          }
-          bt_axpby(ta.d, ta.n, ta.dofs, coefs(c), 0.0, V[i], nullptr, 1.0, V[j + 1], s);
-        }
-        std::vector<double> hn = dots(ta, V[j + 1], V[j + 1]);
-        std::vector<double> inv(ta.n);
+        for (int i = 0; i <= j; ++i)
+          bt_axpy_dot(ta.d, ta.n, kH, hs, i ? (i - 1) * R + j : -1, i ? V[i - 1] : nullptr, V[j + 1], V[i], partials,
+                      kH, hs, i * R + j, s);
+        bt_axpy_norm(ta.d, ta.n, kH, hs, j * R + j, V[j], V[j + 1], partials, kH, hs, (j + 1) * R + j, kinv, -1,
+                     nullptr, 0, s);
+        bt_givens(ta.d, ta.n, kH, kcs, ksn, kg, R, j, kstat, s);
+        bt_scale_dev(ta.d, ta.n, ta.dofs, kinv, V[j + 1], V[j + 1], s);
+        WR_CUDA(cudaMemcpyAsync(hres, kstat, sizeof(double) * ta.n, cudaMemcpyDeviceToHost, s));
+        WR_CUDA(cudaMemcpyAsync(herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        WR_CUDA(cudaStreamSynchronize(s));
+        if (*herr) throw WrError(WR_ERR_TIMEOUT, "a bounded wait in the smoother kernel gave up");
         std::vector<int> finished;
         for (int e = 0; e < ta.n; ++e) {
           const int m = ta.members[e];
-          auto& Hm = H[m];
-          const double v = std::sqrt(hn[e]);
-          Hm[(j + 1) * R + j] = v;
-          inv[e] = v != 0.0 ? 1.0 / v : 1.0;
-          for (int i = 0; i < j; ++i) {
-            const double tt = cs[m][i] * Hm[i * R + j] + sn[m][i] * Hm[(i + 1) * R + j];
-            Hm[(i + 1) * R + j] = -sn[m][i] * Hm[i * R + j] + cs[m][i] * Hm[(i + 1) * R + j];
-            Hm[i * R + j] = tt;
-          }
-          const double den = std::hypot(Hm[j * R + j], Hm[(j + 1) * R + j]);
-          cs[m][j] = Hm[j * R + j] / den;
-          sn[m][j] = Hm[(j + 1) * R + j] / den;
-          Hm[j * R + j] = den;
-          Hm[(j + 1) * R + j] = 0.0;
-          gg[m][j + 1] = -sn[m][j] * gg[m][j];
-          gg[m][j] = cs[m][j] * gg[m][j];
           its[m]++;
           jend[m] = j + 1;
-          if (!std::isfinite(gg[m][j + 1])) throw WrError(WR_ERR_NAN, "FGMRES residual is not finite");
-          if (std::fabs(gg[m][j + 1]) <= tol[m] || its[m] >= opt.gmres_maxit) finished.push_back(m);
+          if (!std::isfinite(hres[e])) throw WrError(WR_ERR_NAN, "FGMRES residual is not finite");
+          if (std::fabs(hres[e]) <= tol[m] || its[m] >= opt.gmres_maxit) finished.push_back(m);
         }
-        bt_axpby(ta.d, ta.n, ta.dofs, nullptr, 0.0, V[j + 1], coefs(inv), 0.0, V[j + 1], s);
         if (!finished.empty()) {
-          for (int m : finished) {
-            done[m] = 1;
-            active[m] = 0;
-          }
+          for (int m : finished) active[m] = 0;
           // solution update of the members that leave now (the tables now hold the rest)
-          update_solution(x, finished, H, gg, jend, R);
+          update_solution(x, finished, jend);
         }
       }
       // restart: the members still active update their solution and residual
       std::vector<int> rest(fine.members.begin(), fine.members.end());
       if (rest.empty()) break;
-      update_solution(x, rest, H, gg, jend, R);
+      update_solution(x, rest, jend);
       Table& tr = fine;
       jac(tr, x, w);
       bt_axpby(tr.d, tr.n, tr.dofs, nullptr, 1.0, b, nullptr, -1.0, w, s);
-      std::vector<double> b2 = dots(tr, w, w);
-      for (int e = 0; e < tr.n; ++e) beta[tr.members[e]] = std::sqrt(b2[e]);
+      member_norms(tr, beta);
       bool change = false;
       for (int m : rest)
         if (!(beta[m] > tol[m]) || its[m] >= opt.gmres_maxit) {
@@ -557,36 +540,21 @@ struct wr_batch {
   }
 
   // x_m += sum_i y_i Z_i for the listed members (y from the triangular solve of their
-  // Hessenberg); leaves the active set and the tables as they were
-  void update_solution(double* x, const std::vector<int>& who, std::vector<std::vector<double>>& H,
-                       std::vector<std::vector<double>>& gg, const std::vector<int>& jend, int R) {
+  // Hessenberg, on the device); the listed members advanced in lock step, so they share
+  // one basis length.  Leaves the active set and the tables as they were.
+  void update_solution(double* x, const std::vector<int>& who, const std::vector<int>& jend) {
     std::vector<char> saved(active);
     std::fill(active.begin(), active.end(), 0);
-    int jmax = 0;
+    const int je = jend[who.front()];
     for (int m : who) {
+      if (jend[m] != je) throw WrError(WR_ERR_ARG, "FGMRES members out of lock step");
       active[m] = 1;
-      jmax = std::max(jmax, jend[m]);
     }
     build_tables();
     Table& t = fine;
-    std::vector<std::vector<double>> y(B);
-    for (int m : who) {
-      const int je = jend[m];
-      y[m].assign(je, 0.0);
-      for (int i = je - 1; i >= 0; --i) {
-        double acc = gg[m][i];
-        for (int l2 = i + 1; l2 < je; ++l2) acc -= H[m][i * R + l2] * y[m][l2];
-        y[m][i] = acc / H[m][i * R + i];
-      }
-    }
-    std::vector<double> c(t.n);
-    for (int i = 0; i < jmax; ++i) {
-      for (int e = 0; e < t.n; ++e) {
-        const int m = t.members[e];
-        c[e] = i < jend[m] ? y[m][i] : 0.0;
-      }
-      bt_axpby(t.d, t.n, t.dofs, coefs(c), 0.0, Z[i], nullptr, 1.0, x, s);
-    }
+    KrylovBasis zb{};
+    for (int i = 0; i < je; ++i) zb.p[i] = Z[i];
+    bt_krylov_update(t.d, t.n, t.dofs, kH, kg, ky, opt.gmres_restart, je, zb, x, s);
     active = saved;
     build_tables();
   }
@@ -698,6 +666,7 @@ int wr_batch_create(wr_batch** out, int n, const wr_problem* ps, const wr_option
           "bad scatter_weight");
     bneed(b->opt.cheb_steps >= 1 && 2 * b->opt.cheb_steps <= kCoefRows, "bad Chebyshev steps");
     bneed(b->opt.eig_steps >= 1 && b->opt.eig_steps <= b->opt.gmres_restart, "bad eigen-estimate steps");
+    bneed(b->opt.gmres_restart >= 1 && b->opt.gmres_restart <= kMaxKrylovBasis, "bad restart");
     b->s = static_cast<cudaStream_t>(stream);
     b->B = n;
     b->k = ps[0].k;
@@ -806,6 +775,20 @@ int wr_batch_create(wr_batch** out, int n, const wr_problem* ps, const wr_option
     b->dres = b->alloc<double>(n);
     b->dcoef = b->alloc<double>(2 * (size_t)n);
     b->dseeds = b->alloc<int64_t>(n);
+    {
+      const int R = b->opt.gmres_restart, ne = b->opt.eig_steps;
+      b->kH = b->alloc<double>((size_t)n * (R + 1) * R);
+      b->kcs = b->alloc<double>((size_t)n * R);
+      b->ksn = b->alloc<double>((size_t)n * R);
+      b->kg = b->alloc<double>((size_t)n * (R + 1));
+      b->ky = b->alloc<double>((size_t)n * R);
+      b->keH = b->alloc<double>((size_t)n * (ne + 1) * ne);
+      b->kbeta = b->alloc<double>(n);
+      b->kinv = b->alloc<double>(n);
+      b->kstat = b->alloc<double>(n);
+      WR_CUDA(cudaMemsetAsync(b->keH, 0, sizeof(double) * n * (ne + 1) * ne, b->s));
+      WR_CUDA(cudaMallocHost(&b->hkH, sizeof(double) * n * (ne + 1) * ne));
+    }
     b->derr = b->alloc<int>(1);
     b->fstat = b->alloc<int>(1);
     WR_CUDA(cudaMemsetAsync(b->derr, 0, sizeof(int), b->s));

@@ -910,6 +910,356 @@ void run_bt_element_f32(const BatchSeg* segs, int nseg, int64_t units, int64_t d
   }
 }
 
+// ---------------------------------------------------------------- J(W) x of the solver
+// The Jacobian action every Chebyshev residual, restricted residual and FGMRES
+// iteration applies.  Same weak form and quadrature as element_body<.., true>, laid out
+// for the FP64 pipe, which bounds it on GB300 (FP64 at 1/64 of the FP32 rate):
+//  * W, grad W at the Gauss points do not change between linearisations: wq_kernel
+//    tabulates them once per linearisation (reference-cell gradients), so an apply
+//    interpolates only x;
+//  * every constant factor is folded into per-level tables: the quadrature weights into
+//    the test-function tables, h, dt, nu and conv into the temporal matrices
+//    (h^2 Kt, h^2 tau(0), dt conv h T3, dt nu Wt, dt h Wt), so the pointwise stage has
+//    no scaling multiplications and gradients stay in reference coordinates;
+//  * the convection is formed once per (b, e, c) and contracted with T3 afterwards;
+//  * pressure interpolation and its test contraction are sum-factorised too, and the
+//    jump value x^- needs no derivatives.
+// Element results go to the same per-element buffer as element_body's, summed by
+// assemble_kernel.
+template <int K, int Q>
+struct JacTab {
+  using d = D<K, Q>;
+  double Bv[d::NQ][d::NVL], Dv[d::NQ][d::NVL], Bp[d::NQ][d::NPL];     // interpolation
+  double BvW[d::NQ][d::NVL], DvW[d::NQ][d::NVL], BpW[d::NQ][d::NPL];  // test functions x Gauss weight
+  double KtH[d::NT][d::NT], tauH[d::NT], T3H[d::NT][d::NT][d::NT], WtN[d::NT][d::NT], WtP[d::NT][d::NT];
+};
+
+template <int K, int Q>
+__device__ __forceinline__ void build_jac_tab(const FeTables& T, const LevelGeom& g, const PhysParams& ph,
+                                              JacTab<K, Q>& tb) {
+  using d = D<K, Q>;
+  const double h = g.h, dt = g.dt;
+  for (int e = threadIdx.x; e < d::NQ * d::NVL; e += blockDim.x) {
+    const int q = e / d::NVL, i = e % d::NVL;
+    tb.Bv[q][i] = T.Bv[q][i];
+    tb.Dv[q][i] = T.Dv[q][i];
+    tb.BvW[q][i] = T.wq[q] * T.Bv[q][i];
+    tb.DvW[q][i] = T.wq[q] * T.Dv[q][i];
+  }
+  for (int e = threadIdx.x; e < d::NQ * d::NPL; e += blockDim.x) {
+    const int q = e / d::NPL, i = e % d::NPL;
+    tb.Bp[q][i] = T.Bp[q][i];
+    tb.BpW[q][i] = T.wq[q] * T.Bp[q][i];
+  }
+  for (int e = threadIdx.x; e < d::NT * d::NT * d::NT; e += blockDim.x) {
+    const int a = e / (d::NT * d::NT), b = (e / d::NT) % d::NT, c = e % d::NT;
+    tb.T3H[a][b][c] = dt * ph.conv * h * T.T3[a][b][c];
+    if (c == 0) {
+      tb.KtH[a][b] = h * h * T.Kt[a][b];
+      tb.WtN[a][b] = dt * ph.nu * T.Wt[a][b];
+      tb.WtP[a][b] = dt * h * T.Wt[a][b];
+    }
+  }
+  for (int e = threadIdx.x; e < d::NT; e += blockDim.x) tb.tauH[e] = h * h * T.tau0[e];
+}
+
+// Per (cell, slab): W_{c,b} and its reference-cell gradient at the Gauss points,
+// field (c NT + b) 3 + {value, d/dx, d/dy}, Gauss point fastest.
+template <int K, int Q>
+struct JacSmem {
+  using d = D<K, Q>;
+  static constexpr int NF = 2 * d::NT;      // velocity fields (component c, temporal DoF b)
+  double vn[NF][d::NVE];                    // nodal x (W in wq_kernel)
+  double mn[2][d::NVE];                     // nodal x^-: the previous slab's last temporal DoF
+  double pn[d::NT][d::NPE];
+  double t1[NF][2][d::NVL][d::NQ];          // x pass (value, d/dx); then the test y pass
+  double tm[2][d::NVL][d::NQ];
+  double tp[d::NT][d::NPL][d::NQ];          // x pass of the pressure; then its test y pass
+  double vq[NF][3][d::NQ2];                 // value, d/dx, d/dy; overwritten by the coefficients
+  double mq[2][d::NQ2];
+  double pq[d::NT][d::NQ2];                 // pressure; overwritten by the divergence coefficient
+  double out[d::ELEM];
+};
+
+template <int K, int Q>
+__global__ void __launch_bounds__(32 * kWarps)
+wq_kernel(LevelGeom g, const __grid_constant__ FeTables T, const double* __restrict__ W, double* __restrict__ Wq) {
+  using d = D<K, Q>;
+  using SM = JacSmem<K, Q>;
+  constexpr int NF = SM::NF;
+  __shared__ FeTables Ts;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  stage_fe_tables(T, Ts);
+  __syncthreads();
+  const int cell = blockIdx.x * kWarps + threadIdx.x / 32, slab = blockIdx.y;
+  if (cell >= g.ncells()) return;
+  SM& s = reinterpret_cast<SM*>(smem_raw)[threadIdx.x / 32];
+  const int lane = threadIdx.x & 31;
+  const int CI = cell % g.n, CJ = cell / g.n;
+  const int64_t nv2 = (int64_t)g.nv * g.nv;
+  for (int it = lane; it < NF * d::NVE; it += 32) {
+    const int f = it / d::NVE, l = it % d::NVE, c = f / d::NT, b = f % d::NT;
+    const int gx = CI * (K + 1) + l % d::NVL, gy = CJ * (K + 1) + l / d::NVL;
+    s.vn[f][l] = W[((int64_t)slab * d::NT + b) * g.S + c * nv2 + (int64_t)gy * g.nv + gx];
+  }
+  __syncwarp();
+  for (int it = lane; it < NF * d::NVL * d::NQ; it += 32) {
+    const int f = it / (d::NVL * d::NQ), r = it % (d::NVL * d::NQ), j = r / d::NQ, qx = r % d::NQ;
+    double v = 0.0, dv = 0.0;
+#pragma unroll
+    for (int i = 0; i < d::NVL; ++i) {
+      v = fma(Ts.Bv[qx][i], s.vn[f][j * d::NVL + i], v);
+      dv = fma(Ts.Dv[qx][i], s.vn[f][j * d::NVL + i], dv);
+    }
+    s.t1[f][0][j][qx] = v;
+    s.t1[f][1][j][qx] = dv;
+  }
+  __syncwarp();
+  double* dst = Wq + ((int64_t)slab * g.ncells() + cell) * (NF * 3 * d::NQ2);
+  for (int it = lane; it < NF * d::NQ2; it += 32) {
+    const int f = it / d::NQ2, q = it % d::NQ2, qy = q / d::NQ, qx = q % d::NQ;
+    double v = 0.0, vx = 0.0, vy = 0.0;
+#pragma unroll
+    for (int j = 0; j < d::NVL; ++j) {
+      v = fma(Ts.Bv[qy][j], s.t1[f][0][j][qx], v);
+      vx = fma(Ts.Bv[qy][j], s.t1[f][1][j][qx], vx);
+      vy = fma(Ts.Dv[qy][j], s.t1[f][0][j][qx], vy);
+    }
+    dst[(f * 3 + 0) * d::NQ2 + q] = v;
+    dst[(f * 3 + 1) * d::NQ2 + q] = vx;
+    dst[(f * 3 + 2) * d::NQ2 + q] = vy;
+  }
+}
+
+// One warp: the element contribution of J(W) x on (cell, slab).
+template <int K, int Q>
+__device__ __forceinline__ void jac_body(const LevelGeom& g, const JacTab<K, Q>& tb, const double* __restrict__ Wq,
+                                         const double* __restrict__ x, double* __restrict__ ye, JacSmem<K, Q>& s,
+                                         int cell, int slab) {
+  using d = D<K, Q>;
+  using SM = JacSmem<K, Q>;
+  constexpr int NF = SM::NF, NT = d::NT, NVL = d::NVL, NPL = d::NPL, NQ = d::NQ, NQ2 = d::NQ2;
+  const int lane = threadIdx.x & 31;
+  const int CI = cell % g.n, CJ = cell / g.n;
+  const int S = g.S;
+  const int64_t nv2 = (int64_t)g.nv * g.nv;
+
+  // ---- gather x (Dirichlet velocity rows of J are the identity, set by the assembly)
+  for (int it = lane; it < 2 * d::NVE; it += 32) {
+    const int c = it / d::NVE, l = it % d::NVE;
+    const int gx = CI * (K + 1) + l % NVL, gy = CJ * (K + 1) + l / NVL;
+    const int64_t sp = c * nv2 + (int64_t)gy * g.nv + gx;
+    const bool dir = vel_dirichlet(g, gx, gy);
+#pragma unroll
+    for (int b = 0; b < NT; ++b) s.vn[c * NT + b][l] = dir ? 0.0 : x[((int64_t)slab * NT + b) * S + sp];
+    s.mn[c][l] = (slab > 0 && !dir) ? x[((int64_t)(slab - 1) * NT + (NT - 1)) * S + sp] : 0.0;
+  }
+  for (int it = lane; it < NT * d::NPE; it += 32) {
+    const int b = it / d::NPE, l = it % d::NPE;
+    const int px = CI * K + l % NPL, py = CJ * K + l / NPL;
+    s.pn[b][l] = x[((int64_t)slab * NT + b) * S + 2 * nv2 + (int64_t)py * g.np + px];
+  }
+  __syncwarp();
+
+  // ---- interpolation to the Gauss points, x pass
+  for (int it = lane; it < NF * NVL * NQ; it += 32) {
+    const int f = it / (NVL * NQ), r = it % (NVL * NQ), j = r / NQ, qx = r % NQ;
+    double v = 0.0, dv = 0.0;
+#pragma unroll
+    for (int i = 0; i < NVL; ++i) {
+      v = fma(tb.Bv[qx][i], s.vn[f][j * NVL + i], v);
+      dv = fma(tb.Dv[qx][i], s.vn[f][j * NVL + i], dv);
+    }
+    s.t1[f][0][j][qx] = v;
+    s.t1[f][1][j][qx] = dv;
+  }
+  for (int it = lane; it < 2 * NVL * NQ; it += 32) {
+    const int c = it / (NVL * NQ), r = it % (NVL * NQ), j = r / NQ, qx = r % NQ;
+    double v = 0.0;
+#pragma unroll
+    for (int i = 0; i < NVL; ++i) v = fma(tb.Bv[qx][i], s.mn[c][j * NVL + i], v);
+    s.tm[c][j][qx] = v;
+  }
+  for (int it = lane; it < NT * NPL * NQ; it += 32) {
+    const int b = it / (NPL * NQ), r = it % (NPL * NQ), j = r / NQ, qx = r % NQ;
+    double v = 0.0;
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) v = fma(tb.Bp[qx][i], s.pn[b][j * NPL + i], v);
+    s.tp[b][j][qx] = v;
+  }
+  __syncwarp();
+  // y pass
+  for (int it = lane; it < NF * NQ2; it += 32) {
+    const int f = it / NQ2, q = it % NQ2, qy = q / NQ, qx = q % NQ;
+    double v = 0.0, vx = 0.0, vy = 0.0;
+#pragma unroll
+    for (int j = 0; j < NVL; ++j) {
+      v = fma(tb.Bv[qy][j], s.t1[f][0][j][qx], v);
+      vx = fma(tb.Bv[qy][j], s.t1[f][1][j][qx], vx);
+      vy = fma(tb.Dv[qy][j], s.t1[f][0][j][qx], vy);
+    }
+    s.vq[f][0][q] = v;
+    s.vq[f][1][q] = vx;
+    s.vq[f][2][q] = vy;
+  }
+  for (int it = lane; it < 2 * NQ2; it += 32) {
+    const int c = it / NQ2, q = it % NQ2, qy = q / NQ, qx = q % NQ;
+    double v = 0.0;
+#pragma unroll
+    for (int j = 0; j < NVL; ++j) v = fma(tb.Bv[qy][j], s.tm[c][j][qx], v);
+    s.mq[c][q] = v;
+  }
+  for (int it = lane; it < NT * NQ2; it += 32) {
+    const int b = it / NQ2, q = it % NQ2, qy = q / NQ, qx = q % NQ;
+    double v = 0.0;
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) v = fma(tb.Bp[qy][j], s.tp[b][j][qx], v);
+    s.pq[b][q] = v;
+  }
+  __syncwarp();
+
+  // ---- pointwise coefficients (each lane reads and overwrites its own Gauss point)
+  const double* __restrict__ wq = Wq + ((int64_t)slab * g.ncells() + cell) * (NF * 3 * NQ2);
+  for (int q = lane; q < NQ2; q += 32) {
+    double Wv[NF][3], X[NF][3], p[NT], dv[NT], xm[2];
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        Wv[f][k] = wq[(f * 3 + k) * NQ2 + q];
+        X[f][k] = s.vq[f][k][q];
+      }
+#pragma unroll
+    for (int b = 0; b < NT; ++b) {
+      p[b] = s.pq[b][q];
+      dv[b] = X[0 * NT + b][1] + X[1 * NT + b][2];
+    }
+    xm[0] = s.mq[0][q];
+    xm[1] = s.mq[1][q];
+    // Newton convection (W_b . grad) x_{c,e} + (x_b . grad) W_{c,e}, per (b, e, c)
+    double P[NT][NT][2];
+#pragma unroll
+    for (int b = 0; b < NT; ++b)
+#pragma unroll
+      for (int e = 0; e < NT; ++e)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int fe = c * NT + e;
+          double t = Wv[0 * NT + b][0] * X[fe][1];
+          t = fma(Wv[1 * NT + b][0], X[fe][2], t);
+          t = fma(X[0 * NT + b][0], Wv[fe][1], t);
+          P[b][e][c] = fma(X[1 * NT + b][0], Wv[fe][2], t);
+        }
+#pragma unroll
+    for (int a = 0; a < NT; ++a) {
+      double pw = 0.0, dw = 0.0;
+#pragma unroll
+      for (int b = 0; b < NT; ++b) {
+        pw = fma(tb.WtP[a][b], p[b], pw);
+        dw = fma(tb.WtP[a][b], dv[b], dw);
+      }
+      s.pq[a][q] = dw;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        double val = -tb.tauH[a] * xm[c];
+        double gx = c == 0 ? pw : 0.0, gy = c == 1 ? pw : 0.0;
+#pragma unroll
+        for (int b = 0; b < NT; ++b) {
+          val = fma(tb.KtH[a][b], X[c * NT + b][0], val);
+          gx = fma(tb.WtN[a][b], X[c * NT + b][1], gx);
+          gy = fma(tb.WtN[a][b], X[c * NT + b][2], gy);
+#pragma unroll
+          for (int e = 0; e < NT; ++e) val = fma(tb.T3H[a][b][e], P[b][e][c], val);
+        }
+        s.vq[c * NT + a][0][q] = val;
+        s.vq[c * NT + a][1][q] = gx;
+        s.vq[c * NT + a][2][q] = gy;
+      }
+    }
+  }
+  __syncwarp();
+
+  // ---- test contraction, y pass (weighted test tables)
+  for (int it = lane; it < NF * NVL * NQ; it += 32) {
+    const int f = it / (NVL * NQ), r = it % (NVL * NQ), j = r / NQ, qx = r % NQ;
+    double a1 = 0.0, a2 = 0.0;
+#pragma unroll
+    for (int qy = 0; qy < NQ; ++qy) {
+      const int q = qy * NQ + qx;
+      a1 = fma(tb.BvW[qy][j], s.vq[f][0][q], a1);
+      a1 = fma(tb.DvW[qy][j], s.vq[f][2][q], a1);
+      a2 = fma(tb.BvW[qy][j], s.vq[f][1][q], a2);
+    }
+    s.t1[f][0][j][qx] = a1;
+    s.t1[f][1][j][qx] = a2;
+  }
+  for (int it = lane; it < NT * NPL * NQ; it += 32) {
+    const int a = it / (NPL * NQ), r = it % (NPL * NQ), j = r / NQ, qx = r % NQ;
+    double v = 0.0;
+#pragma unroll
+    for (int qy = 0; qy < NQ; ++qy) v = fma(tb.BpW[qy][j], s.pq[a][qy * NQ + qx], v);
+    s.tp[a][j][qx] = v;
+  }
+  __syncwarp();
+  // x pass -> element output; layout a (2 NVE + NPE) + c NVE + l, then pressure
+  for (int it = lane; it < NF * d::NVE; it += 32) {
+    const int f = it / d::NVE, l = it % d::NVE, c = f / NT, a = f % NT, j = l / NVL, i = l % NVL;
+    double v = 0.0;
+#pragma unroll
+    for (int qx = 0; qx < NQ; ++qx) {
+      v = fma(tb.BvW[qx][i], s.t1[f][0][j][qx], v);
+      v = fma(tb.DvW[qx][i], s.t1[f][1][j][qx], v);
+    }
+    s.out[a * (2 * d::NVE + d::NPE) + c * d::NVE + l] = v;
+  }
+  for (int it = lane; it < NT * d::NPE; it += 32) {
+    const int a = it / d::NPE, l = it % d::NPE, j = l / NPL, i = l % NPL;
+    double v = 0.0;
+#pragma unroll
+    for (int qx = 0; qx < NQ; ++qx) v = fma(tb.BpW[qx][i], s.tp[a][j][qx], v);
+    s.out[a * (2 * d::NVE + d::NPE) + 2 * d::NVE + l] = v;
+  }
+  __syncwarp();
+  double* dst = ye + ((int64_t)slab * g.ncells() + cell) * d::ELEM;
+  for (int it = lane; it < d::ELEM; it += 32) dst[it] = s.out[it];
+}
+
+template <int K, int Q>
+__global__ void __launch_bounds__(32 * kWarps)
+jac_kernel(LevelGeom g, const __grid_constant__ FeTables T, PhysParams ph, const double* __restrict__ Wq,
+           const double* __restrict__ x, double* __restrict__ ye) {
+  __shared__ JacTab<K, Q> tb;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  build_jac_tab<K, Q>(T, g, ph, tb);
+  __syncthreads();
+  const int cell = blockIdx.x * kWarps + threadIdx.x / 32;
+  if (cell >= g.ncells()) return;
+  jac_body<K, Q>(g, tb, Wq, x, ye, reinterpret_cast<JacSmem<K, Q>*>(smem_raw)[threadIdx.x / 32], cell, blockIdx.y);
+}
+
+template <int K, int Q>
+void run_wq(const LevelGeom& g, const FeTables& T, const double* W, double* Wq, cudaStream_t s) {
+  const size_t smem = sizeof(JacSmem<K, Q>) * kWarps;
+  auto kern = wq_kernel<K, Q>;
+  WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((g.ncells() + kWarps - 1) / kWarps, g.N);
+  kern<<<grid, 32 * kWarps, smem, s>>>(g, T, W, Wq);
+  WR_LAUNCH_CHECK();
+}
+
+template <int K, int Q>
+void run_jac(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* Wq, const double* x,
+             double* y, double* ye, cudaStream_t s) {
+  const size_t smem = sizeof(JacSmem<K, Q>) * kWarps;
+  auto kern = jac_kernel<K, Q>;
+  WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((g.ncells() + kWarps - 1) / kWarps, g.N);
+  kern<<<grid, 32 * kWarps, smem, s>>>(g, T, ph, Wq, x, ye);
+  WR_LAUNCH_CHECK();
+  assemble_kernel<K, Q, true><<<(unsigned)((g.ndofs + 255) / 256), 256, 0, s>>>(g, T, ph, ye, x, y);
+  WR_LAUNCH_CHECK();
+}
+
 template <bool LIN>
 void dispatch_bt_element(int k, int q, const BatchSeg* segs, int nseg, int64_t units, int64_t dofs,
                          const FeTables& T, const double* x, double* y, double* ye, cudaStream_t s) {
@@ -955,6 +1305,25 @@ void launch_residual(const LevelGeom& g, const FeTables& T, const PhysParams& ph
 void launch_jacobian(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* W, const double* x,
                      double* y, double* ye, cudaStream_t s) {
   dispatch_element<true>(g, T, ph, W, x, y, ye, s);
+}
+
+int64_t wq_doubles(const LevelGeom& g) { return (int64_t)g.N * g.ncells() * 6 * g.nt * (g.k + 3) * (g.k + 3); }
+
+void launch_wq(const LevelGeom& g, const FeTables& T, const double* W, double* Wq, cudaStream_t s) {
+  if (g.k == 1 && g.q == 0) run_wq<1, 0>(g, T, W, Wq, s);
+  else if (g.k == 1 && g.q == 1) run_wq<1, 1>(g, T, W, Wq, s);
+  else if (g.k == 2 && g.q == 0) run_wq<2, 0>(g, T, W, Wq, s);
+  else if (g.k == 2 && g.q == 1) run_wq<2, 1>(g, T, W, Wq, s);
+  else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
+}
+
+void launch_jacobian_wq(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* Wq,
+                        const double* x, double* y, double* ye, cudaStream_t s) {
+  if (g.k == 1 && g.q == 0) run_jac<1, 0>(g, T, ph, Wq, x, y, ye, s);
+  else if (g.k == 1 && g.q == 1) run_jac<1, 1>(g, T, ph, Wq, x, y, ye, s);
+  else if (g.k == 2 && g.q == 0) run_jac<2, 0>(g, T, ph, Wq, x, y, ye, s);
+  else if (g.k == 2 && g.q == 1) run_jac<2, 1>(g, T, ph, Wq, x, y, ye, s);
+  else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 }
 
 void launch_jacobian_f32(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* W, const double* x,
@@ -1031,30 +1400,57 @@ cudaError_t static_scratch(double** out) {
 }
 }  // namespace
 
+namespace {
+int static_fail(int code, const std::string& msg) {
+  wr_set_context_free_error("wr_apply_jacobian_static: " + msg);
+  return code;
+}
+}  // namespace
+
 extern "C" int wr_apply_jacobian_static(const wr_problem* p, const double* W, const double* x, double* y,
                                         void* cuda_stream) {
-  if (!p || !W || !x || !y || x == y) return WR_ERR_ARG;
-  if ((p->k != 1 && p->k != 2) || (p->q != 0 && p->q != 1) || p->n_fine < 1 || p->n_slabs < 1 || !(p->T > 0.0))
-    return WR_ERR_ARG;
-  const int64_t nvl = p->k + 2, npl = p->k + 1;
-  const int64_t elem = (p->q + 1) * (2 * nvl * nvl + npl * npl);
-  const int64_t need = (int64_t)p->n_slabs * p->n_fine * p->n_fine * elem;
-  if (need > kStaticScratchDoubles) return WR_ERR_ARG;  // larger than the static scratch
   try {
+    if (!p || !W || !x || !y) return static_fail(WR_ERR_ARG, "null pointer");
+    if (x == y) return static_fail(WR_ERR_ARG, "x and y alias");
+    if ((p->k != 1 && p->k != 2) || (p->q != 0 && p->q != 1))
+      return static_fail(WR_ERR_ARG, "unsupported (k, q): k must be 1 or 2 and q 0 or 1");
+    if (p->n_fine < 1 || p->n_slabs < 1 || !(p->T > 0.0))
+      return static_fail(WR_ERR_ARG, "n_fine, n_slabs and T must be positive");
+    if (p->kind != WR_TAYLOR_GREEN && p->kind != WR_POLY && p->kind != WR_FOURIER && p->kind != WR_LID)
+      return static_fail(WR_ERR_ARG, "kind is not a Navier-Stokes problem (the heat kinds have no J(W) here)");
+    const int64_t nvl = p->k + 2, npl = p->k + 1;
+    const int64_t elem = (p->q + 1) * (2 * nvl * nvl + npl * npl);
+    const int64_t need = (int64_t)p->n_slabs * p->n_fine * p->n_fine * elem;
+    if (need > kStaticScratchDoubles)
+      return static_fail(WR_ERR_ARG, "problem needs " + std::to_string(need) +
+                                         " doubles of scratch, larger than the static array of " +
+                                         std::to_string(kStaticScratchDoubles));
+    const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int dev = 0, stream_dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaStreamGetDevice(s, &stream_dev);
+    if (e != cudaSuccess) return static_fail(WR_ERR_CUDA, cudaGetErrorString(e));
+    if (stream_dev != dev)
+      return static_fail(WR_ERR_ARG, "cuda_stream belongs to device " + std::to_string(stream_dev) +
+                                         ", not to the current device " + std::to_string(dev));
     double* scratch = nullptr;
-    if (static_scratch(&scratch) != cudaSuccess) return WR_ERR_CUDA;
+    e = static_scratch(&scratch);
+    if (e != cudaSuccess) return static_fail(WR_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     const LevelGeom g = make_geom(p->n_fine, p->k, p->q, p->n_slabs, p->T);
     const FeTables T = build_tables(p->k, p->q);
-    PhysParams ph = {};
-    ph.kind = p->kind;
-    ph.steady = p->steady;
+    PhysParams ph = {};  // the Jacobian reads nu, conv and T only (Dirichlet rows are the identity)
+    ph.kind = WR_FOURIER;
     ph.nu = p->nu;
     ph.conv = p->conv;
     ph.T = p->T;
-    ph.n_modes = 0;  // the Jacobian does not read the forcing
-    dispatch_element<true>(g, T, ph, W, x, y, scratch, static_cast<cudaStream_t>(cuda_stream));
+    ph.n_modes = 0;
+    dispatch_element<true>(g, T, ph, W, x, y, scratch, s);
     return WR_OK;
   } catch (const WrError& e) {
-    return e.code;
+    return static_fail(e.code, e.what());
+  } catch (const std::exception& e) {
+    return static_fail(WR_ERR_CUDA, e.what());
+  } catch (...) {
+    return static_fail(WR_ERR_CUDA, "unknown exception");
   }
 }

@@ -77,6 +77,7 @@ struct Level {
   LevelGeom g;
   BlockSet bs;
   double* W = nullptr;
+  double* Wq = nullptr;     // W and grad W at the Gauss points (launch_wq)
   void* factors = nullptr;  // stored factors (null when the level recomputes them per apply)
   bool recompute = false;   // factors recomputed in windows of `nw` slabs at every smoother apply
   int nw = 0;
@@ -111,6 +112,22 @@ struct wr_ctx {
   std::vector<double*> V, Z;
   double *F = nullptr, *w = nullptr, *hb = nullptr, *hx = nullptr;
   double *partials = nullptr, *dres = nullptr, *hres = nullptr;
+  // device-resident Krylov scalars: FGMRES Hessenberg, rotations, right-hand side and
+  // least-squares solution, the Arnoldi Hessenberg of the eigen-estimate, and scalars
+  double* kd = nullptr;
+  unsigned* kcnt = nullptr;  // zeroed block counter of the one-launch reductions
+  double* hk = nullptr;  // pinned host copy of the eigen-estimate Hessenberg
+  double* kH() { return kd; }
+  double* kcs() { return kd + (opt.gmres_restart + 1) * opt.gmres_restart; }
+  double* ksn() { return kcs() + opt.gmres_restart; }
+  double* kg() { return ksn() + opt.gmres_restart; }
+  double* ky() { return kg() + opt.gmres_restart + 1; }
+  double* keH() { return ky() + opt.gmres_restart; }
+  double* kscal() { return keH() + (opt.eig_steps + 1) * opt.eig_steps; }
+  static int64_t krylov_doubles(const wr_options& o) {
+    return (int64_t)(o.gmres_restart + 1) * o.gmres_restart + 4 * o.gmres_restart + 1 +
+           (int64_t)(o.eig_steps + 1) * o.eig_steps + 8;
+  }
   int* herr = nullptr;
   int* slots = nullptr;
   int* derr = nullptr;   // device error flag of the bounded waits
@@ -180,6 +197,7 @@ struct wr_ctx {
       for (void* p : allocs) cudaFree(p);
     }
     if (hres) cudaFreeHost(hres);
+    if (hk) cudaFreeHost(hk);
     if (herr) cudaFreeHost(herr);
   }
 
@@ -187,7 +205,7 @@ struct wr_ctx {
   int top() const { return (int)L.size() - 1; }
 
   double dot(int64_t n, const double* x, const double* y) {
-    vec_dot_dev(n, x, y, partials, dres, s);
+    krylov_axpy_dot(n, nullptr, nullptr, const_cast<double*>(x), y, partials, kcnt, dres, s);
     WR_CUDA(cudaMemcpyAsync(hres, dres, sizeof(double), cudaMemcpyDeviceToHost, s));
     WR_CUDA(cudaMemcpyAsync(herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
     WR_CUDA(cudaStreamSynchronize(s));
@@ -200,10 +218,35 @@ struct wr_ctx {
     if (*herr) throw WrError(WR_ERR_TIMEOUT, "a bounded wait in the smoother kernel gave up");
   }
   double norm(int64_t n, const double* x) { return std::sqrt(dot(n, x, x)); }
+  // ||x|| to the host; also leaves ||x|| in kscal()[0] and 1 / ||x|| in kscal()[1] on the device
+  double norm_dev(int64_t n, double* x) {
+    krylov_axpy_norm(n, nullptr, nullptr, x, partials, kcnt, kscal(), kscal() + 1, nullptr, 0.0, 0.0, s);
+    return read_scalar(kscal());
+  }
+  double read_scalar(const double* d) {
+    WR_CUDA(cudaMemcpyAsync(hres, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    WR_CUDA(cudaMemcpyAsync(herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    WR_CUDA(cudaStreamSynchronize(s));
+    if (*herr) throw WrError(WR_ERR_TIMEOUT, "a bounded wait in the smoother kernel gave up");
+    return *hres;
+  }
+  // Modified Gram-Schmidt of V[j+1] against V[0..j] on the device: H[i][j] (row
+  // stride m) = <w, V[i]> after w -= H[i-1][j] V[i-1]; then H[j+1][j] = ||w|| and
+  // w /= H[j+1][j] (skipped if 0; with breakdown = true, w = 0 where H[j+1][j] <=
+  // 1e-14 |H[j][j]| + 1e-300).
+  void mgs_dev(int64_t n, double* H, int m, int j, bool breakdown) {
+    double* w = V[j + 1];
+    for (int i = 0; i <= j; ++i)
+      krylov_axpy_dot(n, i ? H + (i - 1) * m + j : nullptr, i ? V[i - 1] : nullptr, w, V[i], partials, kcnt,
+                      H + i * m + j, s);
+    krylov_axpy_norm(n, H + j * m + j, V[j], w, partials, kcnt, H + (j + 1) * m + j, kscal() + 2,
+                     breakdown ? H + j * m + j : nullptr, 1e-14, 1e-300, s);
+    vec_scale_dev(n, kscal() + 2, w, w, s);
+  }
 
   void jac(int l, const double* x, double* y) {
     if (heat) heat_jacobian(L[l].g, tab, ph, x, y, htmp, s);
-    else launch_jacobian(L[l].g, tab, ph, L[l].W, x, y, ye, s);
+    else launch_jacobian_wq(L[l].g, tab, ph, L[l].Wq, x, y, ye, s);
   }
   // J inside the preconditioner (smoother residuals, the residual restricted to the
   // next level, eigen-estimates): single-precision element arithmetic in the
@@ -429,6 +472,7 @@ struct wr_ctx {
     }
     vec_copy(L[T_].g.ndofs, W, L[T_].W, s);
     for (int l = T_; l >= 1; --l) launch_inject(L[l].g, L[l - 1].g, L[l].W, L[l - 1].W, s);
+    for (int l = 0; l <= T_; ++l) launch_wq(L[l].g, tab, L[l].W, L[l].Wq, s);
     for (int l = 1; l <= T_; ++l) {
       if (L[l].recompute) {  // one pass over the windows checks every block for a zero pivot
         for (int s0 = 0; s0 < L[l].g.N; s0 += L[l].nw) factor_window(l, s0, std::min(L[l].nw, L[l].g.N - s0), true);
@@ -461,28 +505,27 @@ struct wr_ctx {
     Level& lv = L[l];
     const int64_t n = lv.g.ndofs;
     const int m = opt.eig_steps;
-    std::vector<double> H((m + 1) * m, 0.0);
+    double* H = keH();
     if (heat) heat_splitmix(lv.g.ndofs, (uint64_t)l, V[0], s);
     else launch_splitmix_free(lv.g, (uint64_t)l, V[0], s);
-    vec_scale(n, 1.0 / norm(n, V[0]), V[0], s);
-    int mm = m;
+    krylov_axpy_norm(n, nullptr, nullptr, V[0], partials, kcnt, kscal(), kscal() + 1, nullptr, 0.0, 0.0, s);
+    vec_scale_dev(n, kscal() + 1, V[0], V[0], s);
+    // all m steps run on the device; after a breakdown the basis vectors are zero
     for (int j = 0; j < m; ++j) {
       jac_inner(l, V[j], lv.t);
       patch_apply(l, lv.t, V[j + 1]);
-      for (int i = 0; i <= j; ++i) {
-        const double hij = dot(n, V[j + 1], V[i]);
-        H[i * m + j] = hij;
-        vec_axpby(n, -hij, V[i], 1.0, V[j + 1], s);
-      }
-      const double hn = norm(n, V[j + 1]);
-      H[(j + 1) * m + j] = hn;
-      if (hn <= 1e-14 * std::fabs(H[j * m + j]) + 1e-300) {
+      mgs_dev(n, H, m, j, true);
+    }
+    WR_CUDA(cudaMemcpyAsync(hk, H, sizeof(double) * (m + 1) * m, cudaMemcpyDeviceToHost, s));
+    check_device();
+    std::vector<double> Hh(hk, hk + (m + 1) * m);
+    int mm = m;
+    for (int j = 0; j < m; ++j)
+      if (Hh[(j + 1) * m + j] <= 1e-14 * std::fabs(Hh[j * m + j]) + 1e-300) {
         mm = j + 1;
         break;
       }
-      vec_scale(n, 1.0 / hn, V[j + 1], s);
-    }
-    lv.lam = max_real_eigenvalue(H, mm, m);
+    lv.lam = max_real_eigenvalue(Hh, mm, m);
     lv.lam_set = true;
   }
 
@@ -543,62 +586,42 @@ struct wr_ctx {
     return best;
   }
 
-  // Right-preconditioned FGMRES with zero initial guess; returns iterations.
+  // Right-preconditioned FGMRES with zero initial guess; returns iterations.  The
+  // Arnoldi (MGS) coefficients, Givens rotations, least-squares solve and solution
+  // update stay on the device; the host reads the residual estimate once per
+  // iteration (the convergence test) and the true residual norm once per restart.
   int fgmres(const double* b, double* x, double tol) {
     Level& fl = fine();
     const int64_t n = fl.g.ndofs;
     const int m = opt.gmres_restart;
+    double *H = kH(), *cs = kcs(), *sn = ksn(), *gg = kg();
+    KrylovBasis zb{};
+    for (int i = 0; i < m; ++i) zb.p[i] = Z[i];
     vec_zero(n, x, s);
     vec_copy(n, b, w, s);
-    double beta = norm(n, w);
+    double beta = norm_dev(n, w);
     int its = 0;
-    std::vector<double> H((m + 1) * m), cs(m), sn(m), gg(m + 1), y(m);
     while (beta > tol && its < opt.gmres_maxit) {
-      vec_copy(n, w, V[0], s);
-      vec_scale(n, 1.0 / beta, V[0], s);
-      std::fill(H.begin(), H.end(), 0.0);
-      std::fill(gg.begin(), gg.end(), 0.0);
-      gg[0] = beta;
+      vec_scale_dev(n, kscal() + 1, w, V[0], s);  // V[0] = w / beta
+      WR_CUDA(cudaMemcpyAsync(gg, kscal(), sizeof(double), cudaMemcpyDeviceToDevice, s));  // g = beta e_1
       int jend = 0;
       for (int j = 0; j < m; ++j) {
         check_cancel();
         vcycle(V[j], Z[j]);
         project(fl.g, Z[j]);
         jac(top(), Z[j], V[j + 1]);
-        for (int i = 0; i <= j; ++i) {
-          const double hij = dot(n, V[j + 1], V[i]);
-          H[i * m + j] = hij;
-          vec_axpby(n, -hij, V[i], 1.0, V[j + 1], s);
-        }
-        const double hn = norm(n, V[j + 1]);
-        H[(j + 1) * m + j] = hn;
-        if (hn != 0.0) vec_scale(n, 1.0 / hn, V[j + 1], s);
-        for (int i = 0; i < j; ++i) {
-          const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
-          H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
-          H[i * m + j] = t;
-        }
-        const double den = std::hypot(H[j * m + j], H[(j + 1) * m + j]);
-        cs[j] = H[j * m + j] / den;
-        sn[j] = H[(j + 1) * m + j] / den;
-        H[j * m + j] = den;
-        H[(j + 1) * m + j] = 0.0;
-        gg[j + 1] = -sn[j] * gg[j];
-        gg[j] = cs[j] * gg[j];
+        mgs_dev(n, H, m, j, false);
+        krylov_givens(H, cs, sn, gg, j, m, kscal() + 3, s);
+        const double res = read_scalar(kscal() + 3);
         ++its;
         jend = j + 1;
-        if (!std::isfinite(gg[j + 1])) throw WrError(WR_ERR_NAN, "FGMRES residual is not finite");
-        if (std::fabs(gg[j + 1]) <= tol || its >= opt.gmres_maxit) break;
+        if (!std::isfinite(res)) throw WrError(WR_ERR_NAN, "FGMRES residual is not finite");
+        if (std::fabs(res) <= tol || its >= opt.gmres_maxit) break;
       }
-      for (int i = jend - 1; i >= 0; --i) {
-        double acc = gg[i];
-        for (int l2 = i + 1; l2 < jend; ++l2) acc -= H[i * m + l2] * y[l2];
-        y[i] = acc / H[i * m + i];
-      }
-      for (int i = 0; i < jend; ++i) vec_axpby(n, y[i], Z[i], 1.0, x, s);
+      krylov_update(n, H, gg, ky(), jend, m, zb, x, s);
       jac(top(), x, w);
       vec_axpby(n, 1.0, b, -1.0, w, s);  // w = b - J x
-      beta = norm(n, w);
+      beta = norm_dev(n, w);
     }
     return its;
   }
@@ -670,6 +693,12 @@ struct wr_ctx {
 double hessenberg_max_real_eig(const std::vector<double>& H, int mm, int ld) {
   return wr_ctx::max_real_eigenvalue(H, mm, ld);
 }
+
+namespace {
+thread_local std::string g_context_free_error;
+}  // namespace
+
+void wr_set_context_free_error(const std::string& msg) { g_context_free_error = msg; }
 
 namespace {
 
@@ -794,6 +823,8 @@ static int create_heat(wr_ctx* c, const wr_problem* p) {
   c->hx = c->alloc<double>(nfine);
   c->partials = c->alloc<double>(dot_partials_size());
   c->dres = c->alloc<double>(1);
+  c->kd = c->alloc<double>(wr_ctx::krylov_doubles(c->opt));
+  c->kcnt = c->alloc<unsigned>(1);
   c->derr = c->alloc<int>(1);
   c->fstat = c->alloc<int>(1);
   c->u0 = c->alloc<double>(c->fine().g.S);
@@ -801,9 +832,13 @@ static int create_heat(wr_ctx* c, const wr_problem* p) {
   c->slots = c->alloc<int>(32);
   if (c->dry) return WR_OK;
   WR_CUDA(cudaMemsetAsync(c->derr, 0, sizeof(int), c->s));
+  // zero Hessenbergs: the entries below the subdiagonal are never written
+  WR_CUDA(cudaMemsetAsync(c->kd, 0, sizeof(double) * wr_ctx::krylov_doubles(c->opt), c->s));
+  WR_CUDA(cudaMemsetAsync(c->kcnt, 0, sizeof(unsigned), c->s));
   WR_CUDA(cudaStreamSynchronize(c->s));
   WR_CUDA(cudaMallocHost(&c->hres, sizeof(double)));
   WR_CUDA(cudaMallocHost(&c->herr, sizeof(int)));
+  WR_CUDA(cudaMallocHost(&c->hk, sizeof(double) * (c->opt.eig_steps + 1) * c->opt.eig_steps));
   *c->herr = 0;
   return WR_OK;
 }
@@ -836,7 +871,7 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
          "precision must be WR_FP64, WR_FP32 or WR_BF16");
     need(c->opt.cheb_steps >= 1 && c->opt.eig_steps >= 1 && c->opt.eig_steps <= c->opt.gmres_restart,
          "bad Chebyshev / eigen-estimate steps");
-    need(c->opt.gmres_restart >= 1 && c->opt.gmres_restart <= 200, "bad restart");
+    need(c->opt.gmres_restart >= 1 && c->opt.gmres_restart <= kMaxKrylovBasis, "bad restart");
     need(c->opt.patch_assembly == WR_PATCH_SUBMATRIX || c->opt.patch_assembly == WR_PATCH_LOCAL,
          "patch_assembly must be WR_PATCH_SUBMATRIX or WR_PATCH_LOCAL");
     need(c->opt.scatter_weight == WR_WEIGHT_ONE || c->opt.scatter_weight == WR_WEIGHT_MULTIPLICITY,
@@ -903,6 +938,7 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
       lv.bs.weighted = c->opt.scatter_weight == WR_WEIGHT_MULTIPLICITY;
       const int64_t nd = lv.g.ndofs;
       lv.W = c->alloc<double>(nd);
+      lv.Wq = c->alloc<double>(wq_doubles(lv.g));
       lv.b = c->alloc<double>(nd);
       lv.x = c->alloc<double>(nd);
       lv.r = c->alloc<double>(nd);
@@ -982,6 +1018,8 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
     c->hx = c->alloc<double>(nfine);
     c->partials = c->alloc<double>(dot_partials_size());
     c->dres = c->alloc<double>(1);
+    c->kd = c->alloc<double>(wr_ctx::krylov_doubles(c->opt));
+    c->kcnt = c->alloc<unsigned>(1);
     c->slots = c->alloc<int>(2 * ms);
     c->derr = c->alloc<int>(1);
     c->fstat = c->alloc<int>(1);
@@ -989,9 +1027,13 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
     if (c->dry) return WR_OK;
     // on the context's stream: its memory may come from the stream-ordered pool
     WR_CUDA(cudaMemsetAsync(c->derr, 0, sizeof(int), c->s));
+    // zero Hessenbergs: the entries below the subdiagonal are never written
+    WR_CUDA(cudaMemsetAsync(c->kd, 0, sizeof(double) * wr_ctx::krylov_doubles(c->opt), c->s));
+    WR_CUDA(cudaMemsetAsync(c->kcnt, 0, sizeof(unsigned), c->s));
     WR_CUDA(cudaStreamSynchronize(c->s));
     WR_CUDA(cudaMallocHost(&c->hres, sizeof(double)));
     WR_CUDA(cudaMallocHost(&c->herr, sizeof(int)));
+    WR_CUDA(cudaMallocHost(&c->hk, sizeof(double) * (c->opt.eig_steps + 1) * c->opt.eig_steps));
     *c->herr = 0;
     return WR_OK;
   });
@@ -1003,7 +1045,10 @@ int wr_destroy(wr_ctx* c) {
   return WR_OK;
 }
 
-const char* wr_last_error(const wr_ctx* c) { return c ? c->err.c_str() : "null context"; }
+const char* wr_last_error(const wr_ctx* c) {
+  if (c) return c->err.c_str();
+  return g_context_free_error.empty() ? "null context" : g_context_free_error.c_str();
+}
 
 int wr_num_levels(const wr_ctx* c, int* out) {
   if (!c || !out) return WR_ERR_ARG;

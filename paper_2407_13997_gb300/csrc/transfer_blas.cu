@@ -231,6 +231,123 @@ __global__ void dot_stage2(const double* __restrict__ partials, double* __restri
   if (threadIdx.x == 0) *out = s[0];
 }
 
+// ---------------------------------------------------------------- device-resident Krylov scalars
+// FGMRES and the Arnoldi eigen-estimate keep every Hessenberg entry, Givens rotation
+// and least-squares coefficient in device memory (FP64); the host reads one status
+// word per FGMRES iteration.  Modified Gram-Schmidt keeps its order: step i updates
+// w -= h_{i-1} v_{i-1} with the coefficient the previous step left on the device and
+// forms <w, v_i> in the same pass.  One launch per step: every block writes its partial
+// sum (a fixed strided set, a fixed tree), and the last block to finish sums the
+// partials in a fixed order, so the result depends on n only, not on block timing.
+// The grid is sized from n (at least 4 elements per thread, at most kDotBlocks).
+inline int krylov_blocks(int64_t n) {
+  const int64_t b = (n + 4 * kDotThreads - 1) / (4 * kDotThreads);
+  return (int)(b < 1 ? 1 : b > kDotBlocks ? kDotBlocks : b);
+}
+
+// mode 0: *out = <w, y>.  mode 1 (a norm, y = w): *out = ||w|| and *inv = 1 / *out (1 if
+// *out is 0).  mode 2 (Arnoldi with a breakdown test): *out = ||w||, *inv = 1 / *out
+// unless *out <= rel |*diag| + abs, where it is 0 (the basis ends there; later vectors
+// are zero).  *count must be 0 before the launch; the last block resets it.
+__global__ void axpy_dot_kernel(int64_t n, const double* __restrict__ h, const double* __restrict__ x, double* w,
+                                const double* y, double* __restrict__ partials, unsigned* __restrict__ count,
+                                double* __restrict__ out, int mode, double* __restrict__ inv,
+                                const double* __restrict__ diag, double rel, double abs_) {
+  __shared__ double s[kDotThreads];
+  __shared__ bool last;
+  const double a = x ? -*h : 0.0;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kDotThreads) {
+    double wi = w[i];
+    if (x) {
+      wi = fma(a, x[i], wi);
+      w[i] = wi;
+    }
+    acc = fma(wi, y == w ? wi : y[i], acc);
+  }
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = kDotThreads / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = s[0];
+    __threadfence();
+    last = atomicAdd(count, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double b = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += kDotThreads) b += __ldcg(partials + i);
+  s[threadIdx.x] = b;
+  __syncthreads();
+  for (int st = kDotThreads / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *count = 0u;
+    if (mode == 0) {
+      *out = s[0];
+      return;
+    }
+    const double hn = sqrt(s[0]);
+    *out = hn;
+    if (mode == 1) *inv = hn != 0.0 ? 1.0 / hn : 1.0;
+    else *inv = hn > rel * fabs(*diag) + abs_ ? 1.0 / hn : 0.0;
+  }
+}
+
+// y = a x with the scalar a in device memory (y may be x)
+__global__ void scale_dev_kernel(int64_t n, const double* __restrict__ a, const double* x, double* y) {
+  const double av = *a;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[i] * av;
+}
+
+// One FGMRES iteration's least-squares update (one thread): the earlier rotations
+// applied to column j of H (row stride m), the new rotation that zeroes H[j+1][j],
+// and the rotated right-hand side g; status[0] = g[j+1] (the residual estimate).
+__global__ void givens_kernel(double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                              double* __restrict__ g, int j, int m, double* __restrict__ status) {
+  for (int i = 0; i < j; ++i) {
+    const double hi = H[i * m + j], hi1 = H[(i + 1) * m + j];
+    H[i * m + j] = cs[i] * hi + sn[i] * hi1;
+    H[(i + 1) * m + j] = -sn[i] * hi + cs[i] * hi1;
+  }
+  const double a = H[j * m + j], b = H[(j + 1) * m + j];
+  const double den = hypot(a, b);
+  cs[j] = a / den;
+  sn[j] = b / den;
+  H[j * m + j] = den;
+  H[(j + 1) * m + j] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  status[0] = g[j + 1];
+}
+
+// Back substitution R y = g for the leading jend x jend upper triangle of H (one thread).
+__global__ void trisolve_kernel(const double* __restrict__ H, const double* __restrict__ g, double* __restrict__ y,
+                                int jend, int m) {
+  for (int i = jend - 1; i >= 0; --i) {
+    double acc = g[i];
+    for (int l = i + 1; l < jend; ++l) acc -= H[i * m + l] * y[l];
+    y[i] = acc / H[i * m + i];
+  }
+}
+
+// x += sum_l y_l Z_l, the terms added one after another (the order of separate updates)
+__global__ void multi_axpy_kernel(int64_t n, const double* __restrict__ y, KrylovBasis z, int cnt,
+                                  double* __restrict__ x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double xi = x[i];
+    for (int l = 0; l < cnt; ++l) xi = fma(y[l], z.p[l][i], xi);
+    x[i] = xi;
+  }
+}
+
 // 8 independent FMA chains per thread, register only.
 __global__ void fp64_probe_kernel(double* out, int iters, double a, double b) {
   double x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
@@ -338,6 +455,125 @@ __global__ void bt_dot_stage2(const double* __restrict__ partials, double* __res
   if (threadIdx.x == 0) out[m] = sbuf[0];
 }
 
+// ---- batched Krylov scalars on the device, member-indexed (member = segs[seg].member):
+// the FGMRES/Arnoldi arrays of member b start at base + b * stride.
+// MGS step of every member: w -= h_b x (if hoff >= 0, h_b = hbase[b * hstride + hoff]),
+// then the partial sums of <w, y> in bt_dot_stage1's pattern and order.
+__global__ void bt_axpy_dot_stage1(const BatchSeg* __restrict__ segs, const double* __restrict__ hbase,
+                                   int64_t hstride, int hoff, const double* __restrict__ x, double* w, const double* y,
+                                   double* __restrict__ partials) {
+  __shared__ double sbuf[256];
+  const int m = blockIdx.y;
+  const int64_t n = segs[m].g.ndofs, off = segs[m].off;
+  const double a = hoff >= 0 ? -hbase[segs[m].member * hstride + hoff] : 0.0;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)kBtDotBlocks * 256) {
+    double wi = w[off + i];
+    if (hoff >= 0) {
+      wi = fma(a, x[off + i], wi);
+      w[off + i] = wi;
+    }
+    acc = fma(wi, y == w ? wi : y[off + i], acc);
+  }
+  sbuf[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sbuf[threadIdx.x] += sbuf[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[m * kBtDotBlocks + blockIdx.x] = sbuf[0];
+}
+// Per member, the sum of its partials in bt_dot_stage2's order into
+// out[b * ostride + ooff]; mode 1 (a norm): out = sqrt(sum), inv[b] = 1 / out (1 if 0),
+// and g[b * gstride] = out if g is given; mode 2 (Arnoldi breakdown test): inv[b] = 0
+// where out <= rel |out[b * ostride + doff]| + abs.
+__global__ void bt_dot_stage2_to(const BatchSeg* __restrict__ segs, const double* __restrict__ partials,
+                                 double* __restrict__ out, int64_t ostride, int ooff, int mode,
+                                 double* __restrict__ inv, int doff, double rel, double abs_, double* __restrict__ g,
+                                 int64_t gstride) {
+  __shared__ double sbuf[64];
+  const int m = blockIdx.x;
+  sbuf[threadIdx.x] = partials[m * kBtDotBlocks + threadIdx.x];
+  __syncthreads();
+  for (int st = 32; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sbuf[threadIdx.x] += sbuf[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const int64_t b = segs[m].member;
+  if (mode == 0) {
+    out[b * ostride + ooff] = sbuf[0];
+    return;
+  }
+  const double hn = sqrt(sbuf[0]);
+  out[b * ostride + ooff] = hn;
+  if (mode == 1) inv[b] = hn != 0.0 ? 1.0 / hn : 1.0;
+  else inv[b] = hn > rel * fabs(out[b * ostride + doff]) + abs_ ? 1.0 / hn : 0.0;
+  if (g) g[b * gstride] = hn;
+}
+// y = a_b x per member, a member-indexed
+__global__ void bt_scale_dev_kernel(const BatchSeg* __restrict__ segs, int nseg, int64_t dofs,
+                                    const double* __restrict__ a, const double* x, double* y) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= dofs) return;
+  const int m = batch_find<BU_DOF>(segs, nseg, u);
+  const int64_t i = segs[m].off + (u - segs[m].u_dof);
+  y[i] = x[i] * a[segs[m].member];
+}
+// The FGMRES rotations of column j, one thread per member (givens_kernel's steps);
+// status[seg] = the member's new residual estimate.
+__global__ void bt_givens_kernel(const BatchSeg* __restrict__ segs, int nseg, double* __restrict__ Hb,
+                                 double* __restrict__ csb, double* __restrict__ snb, double* __restrict__ gb, int R,
+                                 int j, double* __restrict__ status) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nseg) return;
+  const int64_t b = segs[e].member;
+  double* H = Hb + b * (int64_t)(R + 1) * R;
+  double *cs = csb + b * R, *sn = snb + b * R, *g = gb + b * (R + 1);
+  for (int i = 0; i < j; ++i) {
+    const double hi = H[i * R + j], hi1 = H[(i + 1) * R + j];
+    H[i * R + j] = cs[i] * hi + sn[i] * hi1;
+    H[(i + 1) * R + j] = -sn[i] * hi + cs[i] * hi1;
+  }
+  const double a = H[j * R + j], c = H[(j + 1) * R + j];
+  const double den = hypot(a, c);
+  cs[j] = a / den;
+  sn[j] = c / den;
+  H[j * R + j] = den;
+  H[(j + 1) * R + j] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  status[e] = g[j + 1];
+}
+// y_b = R_b^{-1} g_b (leading jend x jend triangle), one thread per member
+__global__ void bt_trisolve_kernel(const BatchSeg* __restrict__ segs, int nseg, const double* __restrict__ Hb,
+                                   const double* __restrict__ gb, double* __restrict__ yb, int R, int jend) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nseg) return;
+  const int64_t b = segs[e].member;
+  const double* H = Hb + b * (int64_t)(R + 1) * R;
+  const double* g = gb + b * (R + 1);
+  double* y = yb + b * R;
+  for (int i = jend - 1; i >= 0; --i) {
+    double acc = g[i];
+    for (int l = i + 1; l < jend; ++l) acc -= H[i * R + l] * y[l];
+    y[i] = acc / H[i * R + i];
+  }
+}
+// x += sum_{l < jend} y_{b,l} Z_l per member, the terms added one after another
+__global__ void bt_multi_axpy_kernel(const BatchSeg* __restrict__ segs, int nseg, int64_t dofs,
+                                     const double* __restrict__ yb, int R, KrylovBasis z, int jend,
+                                     double* __restrict__ x) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= dofs) return;
+  const int m = batch_find<BU_DOF>(segs, nseg, u);
+  const int64_t i = segs[m].off + (u - segs[m].u_dof);
+  const double* y = yb + (int64_t)segs[m].member * R;
+  double xi = x[i];
+  for (int l = 0; l < jend; ++l) xi = fma(y[l], z.p[l][i], xi);
+  x[i] = xi;
+}
+
 inline unsigned grid_for(int64_t n, int threads) {
   const int64_t b = (n + threads - 1) / threads;
   return (unsigned)(b < 4 * 152 * 8 ? (b > 0 ? b : 1) : 4 * 152 * 8);
@@ -390,6 +626,35 @@ void vec_dot_dev(int64_t n, const double* x, const double* y, double* partials, 
   dot_stage1<<<kDotBlocks, kDotThreads, 0, s>>>(n, x, y, partials);
   WR_LAUNCH_CHECK();
   dot_stage2<<<1, kDotThreads, 0, s>>>(partials, out);
+  WR_LAUNCH_CHECK();
+}
+
+void krylov_axpy_dot(int64_t n, const double* h, const double* x, double* w, const double* y, double* partials,
+                     unsigned* count, double* out, cudaStream_t s) {
+  axpy_dot_kernel<<<krylov_blocks(n), kDotThreads, 0, s>>>(n, h, x, w, y, partials, count, out, 0, nullptr, nullptr,
+                                                          0.0, 0.0);
+  WR_LAUNCH_CHECK();
+}
+void krylov_axpy_norm(int64_t n, const double* h, const double* x, double* w, double* partials, unsigned* count,
+                      double* out, double* inv, const double* diag, double rel, double abs_, cudaStream_t s) {
+  axpy_dot_kernel<<<krylov_blocks(n), kDotThreads, 0, s>>>(n, h, x, w, w, partials, count, out, diag ? 2 : 1, inv,
+                                                          diag, rel, abs_);
+  WR_LAUNCH_CHECK();
+}
+void vec_scale_dev(int64_t n, const double* a, const double* x, double* y, cudaStream_t s) {
+  scale_dev_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, a, x, y);
+  WR_LAUNCH_CHECK();
+}
+void krylov_givens(double* H, double* cs, double* sn, double* g, int j, int m, double* status, cudaStream_t s) {
+  givens_kernel<<<1, 1, 0, s>>>(H, cs, sn, g, j, m, status);
+  WR_LAUNCH_CHECK();
+}
+void krylov_update(int64_t n, const double* H, const double* g, double* y, int jend, int m, const KrylovBasis& z,
+                   double* x, cudaStream_t s) {
+  if (jend <= 0) return;
+  trisolve_kernel<<<1, 1, 0, s>>>(H, g, y, jend, m);
+  WR_LAUNCH_CHECK();
+  multi_axpy_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, y, z, jend, x);
   WR_LAUNCH_CHECK();
 }
 
@@ -465,5 +730,46 @@ void bt_dot(const BatchSeg* segs, int nseg, const double* x, const double* y, do
   bt_dot_stage1<<<dim3(kBtDotBlocks, nseg), 256, 0, s>>>(segs, x, y, partials);
   WR_LAUNCH_CHECK();
   bt_dot_stage2<<<nseg, kBtDotBlocks, 0, s>>>(partials, out);
+  WR_LAUNCH_CHECK();
+}
+
+void bt_axpy_dot(const BatchSeg* segs, int nseg, const double* hbase, int64_t hstride, int hoff, const double* x,
+                 double* w, const double* y, double* partials, double* out, int64_t ostride, int ooff,
+                 cudaStream_t s) {
+  if (!nseg) return;
+  bt_axpy_dot_stage1<<<dim3(kBtDotBlocks, nseg), 256, 0, s>>>(segs, hbase, hstride, hoff, x, w, y, partials);
+  WR_LAUNCH_CHECK();
+  bt_dot_stage2_to<<<nseg, kBtDotBlocks, 0, s>>>(segs, partials, out, ostride, ooff, 0, nullptr, 0, 0.0, 0.0, nullptr,
+                                                 0);
+  WR_LAUNCH_CHECK();
+}
+void bt_axpy_norm(const BatchSeg* segs, int nseg, const double* hbase, int64_t hstride, int hoff, const double* x,
+                  double* w, double* partials, double* out, int64_t ostride, int ooff, double* inv, int doff,
+                  double* g, int64_t gstride, cudaStream_t s) {
+  if (!nseg) return;
+  bt_axpy_dot_stage1<<<dim3(kBtDotBlocks, nseg), 256, 0, s>>>(segs, hbase, hstride, hoff, x, w, w, partials);
+  WR_LAUNCH_CHECK();
+  bt_dot_stage2_to<<<nseg, kBtDotBlocks, 0, s>>>(segs, partials, out, ostride, ooff, doff >= 0 ? 2 : 1, inv, doff,
+                                                 1e-14, 1e-300, g, gstride);
+  WR_LAUNCH_CHECK();
+}
+void bt_scale_dev(const BatchSeg* segs, int nseg, int64_t dofs, const double* a, const double* x, double* y,
+                  cudaStream_t s) {
+  if (!nseg || !dofs) return;
+  bt_scale_dev_kernel<<<nblocks(dofs), 256, 0, s>>>(segs, nseg, dofs, a, x, y);
+  WR_LAUNCH_CHECK();
+}
+void bt_givens(const BatchSeg* segs, int nseg, double* H, double* cs, double* sn, double* g, int R, int j,
+               double* status, cudaStream_t s) {
+  if (!nseg) return;
+  bt_givens_kernel<<<(nseg + 127) / 128, 128, 0, s>>>(segs, nseg, H, cs, sn, g, R, j, status);
+  WR_LAUNCH_CHECK();
+}
+void bt_krylov_update(const BatchSeg* segs, int nseg, int64_t dofs, const double* H, const double* g, double* y, int R,
+                      int jend, const KrylovBasis& z, double* x, cudaStream_t s) {
+  if (!nseg || jend <= 0) return;
+  bt_trisolve_kernel<<<(nseg + 127) / 128, 128, 0, s>>>(segs, nseg, H, g, y, R, jend);
+  WR_LAUNCH_CHECK();
+  bt_multi_axpy_kernel<<<nblocks(dofs), 256, 0, s>>>(segs, nseg, dofs, y, R, z, jend, x);
   WR_LAUNCH_CHECK();
 }

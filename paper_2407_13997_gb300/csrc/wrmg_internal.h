@@ -30,13 +30,20 @@ struct WrError : std::runtime_error {
   WrError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
 };
 
+// On failure the runtime's last-error slot is cleared as well, so that a failed call
+// is reported once, here, and not again by a later launch check.
 #define WR_CUDA(call)                                                                   \
   do {                                                                                  \
-    cudaError_t e_ = (call);                                                            \
-    if (e_ != cudaSuccess)                                                              \
-      throw WrError(e_ == cudaErrorMemoryAllocation ? WR_ERR_NOMEM : WR_ERR_CUDA,       \
-                    std::string(#call) + ": " + cudaGetErrorString(e_));                \
+    cudaError_t wr_cuda_rc_ = (call);                                                   \
+    if (wr_cuda_rc_ != cudaSuccess) {                                                   \
+      cudaGetLastError();                                                               \
+      throw WrError(wr_cuda_rc_ == cudaErrorMemoryAllocation ? WR_ERR_NOMEM : WR_ERR_CUDA, \
+                    std::string(#call) + ": " + cudaGetErrorString(wr_cuda_rc_));       \
+    }                                                                                   \
   } while (0)
+// Description of the last failure of a call that takes no context (this thread's);
+// wr_last_error(NULL) returns it.
+void wr_set_context_free_error(const std::string& msg);
 // Every kernel launch of the library is followed by WR_LAUNCH_CHECK, which also counts it.
 void wr_count_launch();
 void wr_count_launches(int64_t n);    // kernels of a replayed CUDA graph
@@ -186,6 +193,13 @@ void launch_jacobian(const LevelGeom& g, const FeTables& T, const PhysParams& ph
                      const double* x, double* y, double* ye, cudaStream_t s);
 // J(W) x with single-precision element arithmetic (FP64 vectors and assembly): the
 // smoother's residuals inside the V-cycle of the reduced-precision forms
+// W and its reference-cell gradient at the Gauss points of every (cell, slab), the
+// input of launch_jacobian_wq (wq_doubles(g) doubles; recomputed at every linearisation)
+int64_t wq_doubles(const LevelGeom& g);
+void launch_wq(const LevelGeom& g, const FeTables& T, const double* W, double* Wq, cudaStream_t s);
+// y = J(W) x from the tabulated W (the solver's form of launch_jacobian)
+void launch_jacobian_wq(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* Wq,
+                        const double* x, double* y, double* ye, cudaStream_t s);
 void launch_jacobian_f32(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* W,
                          const double* x, double* y, double* ye, cudaStream_t s);
 void launch_boundary_values(const LevelGeom& g, const FeTables& T, const PhysParams& ph, double* U,
@@ -253,6 +267,27 @@ void vec_dot_dev(int64_t n, const double* x, const double* y, double* partials, 
                  cudaStream_t s);
 double measure_fp64_tflops(cudaStream_t s);
 
+// Device-resident Krylov scalars (FGMRES and the Arnoldi eigen-estimate).
+constexpr int kMaxKrylovBasis = 200;  // largest FGMRES restart length (wr_create refuses more)
+struct KrylovBasis {
+  const double* p[kMaxKrylovBasis];
+};
+// w -= (*h) x (skipped if x is null), then *out = <w, y> (deterministic order; one
+// launch; partials holds dot_partials_size() doubles, *count is a zeroed counter that
+// the launch leaves zeroed)
+void krylov_axpy_dot(int64_t n, const double* h, const double* x, double* w, const double* y, double* partials,
+                     unsigned* count, double* out, cudaStream_t s);
+// w -= (*h) x (skipped if x is null), then *out = ||w|| and *inv = 1 / ||w|| (1 if 0);
+// with diag: *inv = 0 where ||w|| <= rel |*diag| + abs (Arnoldi breakdown)
+void krylov_axpy_norm(int64_t n, const double* h, const double* x, double* w, double* partials, unsigned* count,
+                      double* out, double* inv, const double* diag, double rel, double abs_, cudaStream_t s);
+void vec_scale_dev(int64_t n, const double* a, const double* x, double* y, cudaStream_t s);  // y = (*a) x
+// rotations of FGMRES column j (one thread); status[0] = the new residual estimate g[j+1]
+void krylov_givens(double* H, double* cs, double* sn, double* g, int j, int m, double* status, cudaStream_t s);
+// y = R^{-1} g (leading jend x jend triangle of H), then x += sum_l y_l z_l
+void krylov_update(int64_t n, const double* H, const double* g, double* y, int jend, int m, const KrylovBasis& z,
+                   double* x, cudaStream_t s);
+
 // batched kernels (one launch for every member in `segs`; base pointers are arenas)
 void bt_jacobian(int k, int q, const BatchSeg* segs, int nseg, int64_t units, int64_t dofs, const FeTables& T,
                  const double* x, double* y, double* ye, cudaStream_t s);
@@ -282,6 +317,24 @@ void bt_fill_abs(const BatchSeg* segs, int nseg, int64_t dofs, double v, cudaStr
 int bt_dot_blocks();
 void bt_dot(const BatchSeg* segs, int nseg, const double* x, const double* y, double* partials, double* out,
             cudaStream_t s);
+
+// Batched Krylov scalars, member-indexed (array of member b at base + b * stride):
+// w -= h_b x (if hoff >= 0, h_b = hbase[b * hstride + hoff]) and out[b * ostride + ooff] = <w, y>
+void bt_axpy_dot(const BatchSeg* segs, int nseg, const double* hbase, int64_t hstride, int hoff, const double* x,
+                 double* w, const double* y, double* partials, double* out, int64_t ostride, int ooff,
+                 cudaStream_t s);
+// the same update, then out[...] = ||w||, inv[b] = 1 / ||w|| (1 if 0; with doff >= 0, 0
+// where ||w|| <= 1e-14 |out[b * ostride + doff]| + 1e-300), g[b * gstride] = ||w|| if g
+void bt_axpy_norm(const BatchSeg* segs, int nseg, const double* hbase, int64_t hstride, int hoff, const double* x,
+                  double* w, double* partials, double* out, int64_t ostride, int ooff, double* inv, int doff,
+                  double* g, int64_t gstride, cudaStream_t s);
+void bt_scale_dev(const BatchSeg* segs, int nseg, int64_t dofs, const double* a, const double* x, double* y,
+                  cudaStream_t s);  // y = a_b x
+// FGMRES column j of every member (H: (R+1) x R, cs, sn: R, g: R+1 per member); status[seg]
+void bt_givens(const BatchSeg* segs, int nseg, double* H, double* cs, double* sn, double* g, int R, int j,
+               double* status, cudaStream_t s);
+void bt_krylov_update(const BatchSeg* segs, int nseg, int64_t dofs, const double* H, const double* g, double* y, int R,
+                      int jend, const KrylovBasis& z, double* x, cudaStream_t s);
 
 // wr_create with the option of allocating the context's device memory from the
 // stream-ordered pool on `stream` (cudaMallocAsync / cudaFreeAsync), so that

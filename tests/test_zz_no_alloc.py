@@ -6,8 +6,9 @@ allocator's implicit synchronisation) use wr_apply_jacobian_static, whose only
 scratch is a fixed static device array inside the library.  This test calls it
 through the C ABI twice in a row and compares each result with the context-based
 wr_apply_jacobian on the same inputs, at the 1e-12 relative tolerance the other
-Jacobian parity tests use; it also checks that an oversized problem is refused
-before any work is enqueued.  It lives in a file of its own that pytest collects
+Jacobian parity tests use, and checks that the second call changes neither
+torch's allocated bytes nor the device's free bytes; it also checks that an
+oversized problem and a heat problem are refused before any work is enqueued.  It lives in a file of its own that pytest collects
 last and passes both alone and after the other tests.
 """
 import ctypes
@@ -47,15 +48,25 @@ def test_static_scratch_jacobian_matches_context_entry_point_twice(w):
     keep = []
     p = problem_struct(w, keep)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    for call in range(2):
-        x = torch.from_numpy(rng.standard_normal(ctx.ndofs())).cuda()
-        ref, out = ctx.vector(), ctx.vector()
+    xs = [torch.from_numpy(rng.standard_normal(ctx.ndofs())).cuda() for _ in range(2)]
+    refs = [ctx.vector() for _ in range(2)]
+    outs = [ctx.vector() for _ in range(2)]
+    for x, ref in zip(xs, refs):
         ctx.apply_jacobian(ctx.fine, x, ref)
-        rc = lib.wr_apply_jacobian_static(ctypes.byref(p), ptr(W), ptr(x), ptr(out), stream)
-        assert rc == wrmg.WR_OK
+    torch.cuda.synchronize()
+    for call in range(2):
+        if call == 1:
+            # every buffer exists already; the first call has loaded the library's
+            # module and looked up the scratch address on this device
+            torch.cuda.synchronize()
+            before = (torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0])
+        rc = lib.wr_apply_jacobian_static(ctypes.byref(p), ptr(W), ptr(xs[call]), ptr(outs[call]), stream)
+        assert rc == wrmg.WR_OK, lib.wr_last_error(None)
         torch.cuda.synchronize()
-        err = (out - ref).abs().max().item() / ref.abs().max().item()
+        err = (outs[call] - refs[call]).abs().max().item() / refs[call].abs().max().item()
         assert err < 1e-12, (call, err)
+    # the second call allocated no device memory, through torch or otherwise
+    assert (torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]) == before
     ctx.close()
 
 
@@ -69,5 +80,19 @@ def test_static_scratch_refuses_problems_larger_than_its_array():
     rc = lib.wr_apply_jacobian_static(ctypes.byref(p), ptr(dummy), ptr(dummy), ptr(out),
                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == wrmg.WR_ERR_ARG
+    assert b"larger than the static array" in lib.wr_last_error(None)
     torch.cuda.synchronize()
     assert torch.count_nonzero(out).item() == 0
+
+
+def test_static_scratch_refuses_the_heat_kinds():
+    lib = wrmg.load()
+    w = inputs.heat(n=4, k=1, q=0, N=2)
+    keep = []
+    p = problem_struct(w, keep)
+    dummy = torch.zeros(4, dtype=torch.float64, device="cuda")
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    rc = lib.wr_apply_jacobian_static(ctypes.byref(p), ptr(dummy), ptr(dummy), ptr(out),
+                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == wrmg.WR_ERR_ARG
+    assert b"not a Navier-Stokes problem" in lib.wr_last_error(None)
