@@ -51,8 +51,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--members", type=int, default=None,
                     help="batch form: number of solves (256); serve form: number of requests (32)")
-    ap.add_argument("--rates", default="10,100,500", help="serve form: Poisson arrival rates (requests/s)")
-    ap.add_argument("--inflight", type=int, default=8, help="serve form: solves in flight at most")
+    ap.add_argument("--rates", default="10,20,50,100,200,500", help="serve form: Poisson arrival rates (requests/s)")
+    ap.add_argument("--inflight", type=int, default=8, help="serve form: solves in flight at most (per-request mode)")
+    ap.add_argument("--serve-mode", default="both", choices=["stream", "batched", "both"],
+                    help="serve form: one stream and context per request, cohorts batched per cycle, or both")
+    ap.add_argument("--cohort", type=int, default=16, help="serve form, batched mode: members per cohort at most")
+    ap.add_argument("--cohort-slots", type=int, default=2, help="serve form, batched mode: cohorts in flight at most")
     ap.add_argument("--budget-gb", type=float, default=96.0, help="serve form: device-memory budget")
     ap.add_argument("--tile", type=int, default=-1,
                     help="cycle and smoother forms: force a smoother-apply tile 0..4 (default: autotuned)")
@@ -173,24 +177,20 @@ def traffic_record(kernel, workload):
     """DRAM bytes per launch of `kernel` on `workload` from a committed ncu summary,
     valid only while the kernel source is unchanged (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_2407_13997_gb300", "csrc", "patch_kernels.cu")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     rec = d.get(f"{kernel}/{workload}")
-    if not rec:
+    if not rec or not rec.get("source"):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    sha = hashlib.sha256(open(os.path.join(ROOT, rec["source"]), "rb").read()).hexdigest()
     return rec.get("dram_bytes_per_launch") if rec.get("source_sha256") == sha else None
 
 
-def cpu_baseline(w, steps=3):
-    """The oracle (FP64 CPU, test infrastructure) timed on this host: V(2,2) cycles
-    on the 16x16, 8-slab instance of the same Q3/Q2 DG(1) Fourier problem.  The
-    oracle's cost per DoF per cycle does not depend on the mesh (fixed patch size,
-    fixed stencils), so DoF/s per cycle carries over to the 64x64 workload."""
-    import numpy as np
+def _oracle_sample(w):
+    """The oracle's V(2,2) cycle on the 16x16, 8-slab instance of the workload's
+    discretisation: (hierarchy, right-hand side)."""
     from oracle.fem import Problem
     from oracle.solver import Hierarchy, Options
     from paper_2407_13997_gb300 import inputs
@@ -202,6 +202,29 @@ def cpu_baseline(w, steps=3):
     h.linearise(W)
     b = -h.fine.residual(W)
     h.vcycle(b)
+    return h, b
+
+
+def _oracle_replica(w, steps, barrier, out):
+    """One process of the all-cores oracle run: set up, wait for every replica, time
+    `steps` cycles."""
+    h, b = _oracle_sample(w)
+    barrier.wait()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        h.vcycle(b)
+    out.put((h.fine.ndofs * steps, time.perf_counter() - t0))
+
+
+def cpu_baseline(w, steps=3, all_cores=True):
+    """The oracle (FP64 CPU, test infrastructure) timed on this host: V(2,2) cycles
+    on the 16x16, 8-slab instance of the same Q3/Q2 DG(1) Fourier problem, (1) in this
+    process and (2) on every host core, one independent replica per core (processes
+    started by spawn, one BLAS thread each), timed from a common barrier to the last
+    replica's end.  The oracle's cost per DoF per cycle does not depend on the mesh
+    (fixed patch size, fixed stencils), so DoF/s per cycle carries over to the 64x64
+    workload."""
+    h, b = _oracle_sample(w)
     r0 = resource.getrusage(resource.RUSAGE_SELF)
     t0 = time.perf_counter()
     for _ in range(steps):
@@ -210,9 +233,42 @@ def cpu_baseline(w, steps=3):
     r1 = resource.getrusage(resource.RUSAGE_SELF)
     cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
     nd = h.fine.ndofs
-    return {"value": nd * steps / dt, "unit": UNIT, "cores": max(1, round(cpu / dt)), "kind": "oracle",
-            "sample": f"{steps} oracle V(2,2) cycles on the 16x16, 8-slab instance ({nd} DoFs) of the same "
-                      f"Q3/Q2 DG(1) Fourier problem, {dt / steps:.2f} s per cycle"}, nd, dt / steps
+    single = {"value": nd * steps / dt, "unit": UNIT, "cores": max(1, round(cpu / dt)), "kind": "oracle",
+              "sample": f"{steps} oracle V(2,2) cycles on the 16x16, 8-slab instance ({nd} DoFs) of the same "
+                        f"Q3/Q2 DG(1) Fourier problem, {dt / steps:.2f} s per cycle"}
+    if not all_cores:
+        return single, nd, dt / steps
+    import multiprocessing as mp
+    ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"  # inherited by the spawned replicas: one core each
+    try:
+        ctx = mp.get_context("spawn")
+        barrier, out = ctx.Barrier(ncores + 1), ctx.Queue()
+        procs = [ctx.Process(target=_oracle_replica, args=(w, steps, barrier, out)) for _ in range(ncores)]
+        for p in procs:
+            p.start()
+        barrier.wait()
+        t0 = time.perf_counter()
+        res = [out.get() for _ in procs]
+        wall = time.perf_counter() - t0
+        for p in procs:
+            p.join()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    dofs = sum(r[0] for r in res)
+    line = {"value": dofs / wall, "unit": UNIT, "cores": ncores, "kind": "oracle",
+            "sample": f"{ncores} independent replicas (one process and one BLAS thread per host core), each "
+                      f"{steps} oracle V(2,2) cycles on the 16x16, 8-slab instance ({nd} DoFs) of the same "
+                      f"Q3/Q2 DG(1) Fourier problem; {wall:.2f} s from a common start to the last replica's end",
+            "single_thread": single}
+    return line, nd, wall / steps
 
 
 def run_reference(args):
@@ -288,6 +344,7 @@ def run_ours(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     sm_ms, sm_n = ctx.profile_smoother(ctx.fine)
+    jac_ms, jac_n, jac_flops = ctx.profile_jacobian(ctx.fine)
     ctx.profile(False)
     ms = max_over_ranks(ms, dist, "cuda")
     value = D * world * args.steps / (ms * 1e-3)
@@ -325,6 +382,22 @@ def run_ours(args):
                 "kernel": f"block_apply_kernel (finest level, {args.precision} factors)", "launches": sm_n,
                 "avg_ms": avg_s * 1e3, "peak_source": hbm_src}
 
+    # the J(W) x element kernel of the finest level (step (e)): FP64-ALU bound; its
+    # HBM figure is the method's bytes per apply, 8 (2 D + D_u)
+    javg_s = jac_ms / max(jac_n, 1) * 1e-3
+    nv = w.n_fine * (w.k + 1) + 1
+    d_u = w.N * (w.q + 1) * 2 * nv * nv
+    jac_tf = jac_flops / javg_s / 1e12 if jac_n else None
+    jac_gbs = 8.0 * (2 * D + d_u) / javg_s / 1e9 if jac_n else None
+    roof_jac = {"bound": "alu", "achieved": jac_tf, "peak": fp64_tflops, "unit": "TFLOP/s",
+                "frac": jac_tf / fp64_tflops if jac_n else None,
+                "traffic": traffic_record("jac_kernel", w.name),
+                "kernel": "jac_kernel (J(W) x element kernel, finest level)", "launches": jac_n,
+                "avg_ms": javg_s * 1e3, "flops_per_launch": jac_flops,
+                "peak_source": "FP64 FMA rate measured live by wr_measure_fp64_tflops",
+                "hbm": {"achieved": jac_gbs, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": jac_gbs / hbm_peak if jac_n else None, "peak_source": hbm_src}}
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
@@ -338,7 +411,7 @@ def run_ours(args):
                        "l2": f"no flush: {ctx.device_bytes() / 1e9:.0f} GB on the device, the stored factors "
                              "streamed every cycle >> 129 MB L2",
                        "parallelism": f"replicas x{world}"},
-            "factor_ms": factor_ms, "setup_ms": setup_ms, "roofline": roof,
+            "factor_ms": factor_ms, "setup_ms": setup_ms, "roofline": roof, "roofline_jacobian": roof_jac,
             "e2e": {"value": D * world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * D,
                     "d2h_bytes_per_step": 8 * D},
             "gpu_launches": launches, "clocks": clk}
@@ -503,9 +576,12 @@ def run_serve_form(args):
     """Serving form: a seeded Poisson stream of solve requests (Q2/Q1 DG(0) or Q3/Q2
     DG(1), nu log-uniform in [1e-3, 1e-1]) served by the native request loop with
     FP32 factors and FP64 Newton/Krylov to rtol 1e-8, against the plain FP64 method
-    run request by request.  The FP64 arm is timed request by request (context
-    set-up, solve and the host copy of the solution) and its latencies follow from
-    those service times and the same arrivals through a single FIFO server."""
+    run request by request.  The loop runs in per-request mode (a stream and context
+    per request) and in batched mode (cohorts of queued requests solved as one
+    lock-step batch per slot, per-cycle batching).  The FP64 arm is timed request by
+    request (context set-up, solve and the host copy of the solution) and its
+    latencies follow from those service times and the same arrivals through a single
+    FIFO server."""
     import numpy as np
     import torch
     from paper_2407_13997_gb300 import inputs, wrmg
@@ -517,7 +593,9 @@ def run_serve_form(args):
     o64 = wrmg.default_options(precision=wrmg.WR_FP64, newton_rtol=1e-8)
     out = {"form": "serve", "requests": len(reqs), "mesh_and_slab_grid": list(grid),
            "total_ndofs": sum(w.ndofs() for w in reqs), "inflight_cap": args.inflight,
-           "budget_bytes": int(args.budget_gb * 2 ** 30), "options": "FP32 factors, FP64 Newton/FGMRES, rtol 1e-8"}
+           "budget_bytes": int(args.budget_gb * 2 ** 30), "options": "FP32 factors, FP64 Newton/FGMRES, rtol 1e-8",
+           "cohort": args.cohort, "cohort_slots": args.cohort_slots}
+    modes = ["stream", "batched"] if args.serve_mode == "both" else [args.serve_mode]
     warm = inputs.serving_workloads(2, seed=99, ns=(16,), slabs=(16,))
     for w in warm:                                    # module loading and first-launch set-up
         for o in (o32, o64):
@@ -555,45 +633,52 @@ def run_serve_form(args):
         out["sequential_fp64"]["rates"][str(int(rate))] = {
             "solves_per_s": len(reqs) / (end - arr[0]), "p50_ms": 1e3 * float(np.percentile(lat, 50)),
             "p99_ms": 1e3 * float(np.percentile(lat, 99))}
-        sv = wrmg.Server(out["budget_bytes"], args.inflight, o32)
-        tickets = [None] * len(reqs)
+        out["rates"][str(int(rate))] = {}
+        for mode in modes:
+            if mode == "batched":
+                sv = wrmg.Server(out["budget_bytes"], args.cohort_slots, o32, batch_members=args.cohort)
+            else:
+                sv = wrmg.Server(out["budget_bytes"], args.inflight, o32)
+            tickets = [None] * len(reqs)
 
-        def feeder():
-            t0 = time.perf_counter()
-            for i, (a, w) in enumerate(zip(arr, reqs)):
-                dt = t0 + a - time.perf_counter()
-                if dt > 0:
-                    time.sleep(dt)
-                tickets[i] = sv.submit(w)
+            def feeder():
+                t0 = time.perf_counter()
+                for i, (a, w) in enumerate(zip(arr, reqs)):
+                    dt = t0 + a - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                    tickets[i] = sv.submit(w)
 
-        t_start = time.perf_counter()
-        th = threading.Thread(target=feeder)
-        th.start()
-        th.join()
-        res = [sv.poll(t) for t in tickets]
-        t_end = time.perf_counter()
-        st = sv.stats()
-        sv.close()
-        lat = [r[3] for r in res]
-        ok = sum(1 for r in res if r[0] == wrmg.WR_OK)
-        for r, ref, c64 in zip(res, refs, seq_status):
-            if r[1] is not None and r[0] == wrmg.WR_OK and c64 == wrmg.WR_OK:
-                errs.append(float(np.abs(r[1] - ref).max() / max(np.abs(ref).max(), 1e-300)))
-        out.setdefault("per_request", [{"name": w.name, "nu": w.nu, "fp64_status": c, "fp64_s": t}
-                                       for w, c, t in zip(reqs, seq_status, service)])
-        for pr, r in zip(out["per_request"], res):
-            pr[f"served_status_{int(rate)}"] = r[0]
-            pr[f"served_latency_ms_{int(rate)}"] = r[3]
-        out["rates"][str(int(rate))] = {
-            "solves_per_s": len(reqs) / (t_end - t_start - arr[0]), "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "converged": ok, "peak_inflight": st["peak_inflight"],
-            "peak_bytes": st["peak_bytes"], "newton_total": sum(r[2]["newton_its"] for r in res),
-            "fgmres_total": sum(sum(r[2]["gmres"]) for r in res)}
+            t_start = time.perf_counter()
+            th = threading.Thread(target=feeder)
+            th.start()
+            th.join()
+            res = [sv.poll(t) for t in tickets]
+            t_end = time.perf_counter()
+            st = sv.stats()
+            sv.close()
+            lat = [r[3] for r in res]
+            ok = sum(1 for r in res if r[0] == wrmg.WR_OK)
+            for r, ref, c64 in zip(res, refs, seq_status):
+                if r[1] is not None and r[0] == wrmg.WR_OK and c64 == wrmg.WR_OK:
+                    errs.append(float(np.abs(r[1] - ref).max() / max(np.abs(ref).max(), 1e-300)))
+            out.setdefault("per_request", [{"name": w.name, "nu": w.nu, "fp64_status": c, "fp64_s": t}
+                                           for w, c, t in zip(reqs, seq_status, service)])
+            for pr, r in zip(out["per_request"], res):
+                pr[f"{mode}_status_{int(rate)}"] = r[0]
+                pr[f"{mode}_latency_ms_{int(rate)}"] = r[3]
+            out["rates"][str(int(rate))][mode] = {
+                "solves_per_s": len(reqs) / (t_end - t_start - arr[0]), "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "converged": ok, "peak_inflight": st["peak_inflight"],
+                "peak_cohort": st["peak_cohort"], "peak_bytes": st["peak_bytes"],
+                "newton_total": sum(r[2]["newton_its"] for r in res),
+                "fgmres_total": sum(sum(r[2]["gmres"]) for r in res)}
     # over the requests both arms solved to 1e-8
     out["max_rel_diff_vs_fp64_solution"] = max(errs) if errs else None
     top = str(int(max(rates)))
-    out["solves_per_s_ratio_vs_sequential_fp64"] = (out["rates"][top]["solves_per_s"] /
-                                                    out["sequential_fp64"]["rates"][top]["solves_per_s"])
+    out["solves_per_s_ratio_vs_sequential_fp64"] = {
+        mode: out["rates"][top][mode]["solves_per_s"] / out["sequential_fp64"]["rates"][top]["solves_per_s"]
+        for mode in modes}
     print(json.dumps(out), flush=True)
 
 

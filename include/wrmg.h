@@ -332,6 +332,23 @@ int wr_batch_solve(wr_batch *b, double *const *U, wr_stats *st);
  *   The server uses the device current at wr_server_create. */
 typedef struct wr_server wr_server;
 int wr_server_create(wr_server **out, int64_t mem_budget_bytes, int max_inflight, const wr_options *o);
+/* The same server with per-cycle batching (continuous batching): an in-flight
+ * slot (max_cohorts of them) holds a cohort instead of one request.  When a slot
+ * is free the head request is admitted together with the queued requests of the
+ * same k and q behind it, in arrival order, up to max_members and the remaining
+ * budget, and the cohort is solved as one lock-step batch (wr_batch: one launch per
+ * stage of every V-cycle, Newton step and FGMRES iteration for all its members,
+ * V-cycles replayed as CUDA graphs) on the slot's stream.  Cohorts in different
+ * slots overlap on the device; requests that arrive meanwhile form the next cohort
+ * as soon as a slot and memory free up.  Each member completes (and is pollable)
+ * the moment it leaves its cohort, so its latency is its own; a cohort's memory is
+ * released when its last member leaves.  Results equal the solve alone up to
+ * rounding (1e-10: the apply tiles are tuned per cohort).  Heat-equation and
+ * DG(2)/DG(3) requests, which the batch engine does not take, run one per slot as
+ * in wr_server_create.  Cancelling a running member takes effect at its cohort's
+ * next Newton step.  max_members = 1 is wr_server_create. */
+int wr_server_create_batched(wr_server **out, int64_t mem_budget_bytes, int max_cohorts, int max_members,
+                             const wr_options *o);
 /* Waits for the solves in flight; requests still queued complete with WR_ERR_STATE. */
 int wr_server_destroy(wr_server *sv);
 /* Queues *p (copied, forcing modes included); U0_host is NULL (start from the
@@ -345,8 +362,11 @@ int wr_server_submit(wr_server *sv, const wr_problem *p, const double *U0_host, 
  * and returns the solve's status (WR_OK, WR_ERR_NOT_CONVERGED, WR_ERR_NOMEM...).
  * Unknown tickets: WR_ERR_ARG. */
 int wr_server_poll(wr_server *sv, uint64_t ticket, int wait, double *U_host, wr_stats *st, double *latency_ms);
-/* Largest device bytes admitted at once and largest number of solves in flight so far. */
+/* Largest device bytes admitted at once and largest number of solves in flight so far
+ * (cohorts, in batched mode). */
 int wr_server_stats(wr_server *sv, int64_t *peak_bytes, int *peak_inflight);
+/* Largest cohort solved as one batch so far (0 in per-request mode). */
+int wr_server_peak_cohort(wr_server *sv, int *out);
 /* Cancels a request: a queued one completes at once, a running one at its next
  * Newton step or FGMRES iteration; either way with WR_ERR_CANCELLED (poll it as
  * usual).  A completed request is unaffected.  Unknown tickets: WR_ERR_ARG. */
@@ -401,6 +421,13 @@ int wr_profile_smoother(wr_ctx *c, int level, double *total_ms, int *launches);
  * Returns WR_OK, WR_ERR_ARG, or WR_ERR_CUDA (launch failure); after a failure
  *   wr_last_error(NULL) describes it (per host thread). */
 int wr_apply_jacobian_static(const wr_problem *p, const double *W, const double *x, double *y, void *cuda_stream);
+
+/* Sum of the recorded durations of the J(W) x element kernel on `level` (ms; the
+ * Jacobian applications of Chebyshev residuals, restricted residuals and FGMRES, timed
+ * by CUDA events once wr_profile has enabled recording), the number of launches, and
+ * the FP64 operations of one launch (the sum-factorised algorithm's count, a
+ * multiply-add counting 2; NULL to skip).  Synchronises the stream. */
+int wr_profile_jacobian(wr_ctx *c, int level, double *total_ms, int *launches, double *flops_per_launch);
 
 /* FP64 FMA throughput of this GPU, measured by a register-only kernel
  * (TFLOP/s); the denominator for FP64-ALU-bound kernels. */

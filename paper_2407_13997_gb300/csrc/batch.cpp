@@ -15,6 +15,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <memory>
 
 #include "wrmg_internal.h"
@@ -75,6 +76,12 @@ struct wr_batch {
   double *kH = nullptr, *kcs = nullptr, *ksn = nullptr, *kg = nullptr, *ky = nullptr, *keH = nullptr;
   double *kbeta = nullptr, *kinv = nullptr, *kstat = nullptr;
   double* hkH = nullptr;  // pinned host copy of keH
+  // set for one solve by batch_solve_hooked: a member's result is copied to Uout[m]
+  // and on_done(m, status) runs as soon as it leaves the lock-step set; a member whose
+  // cancel flag is set leaves with WR_ERR_CANCELLED
+  double* const* Uout = nullptr;
+  const std::atomic<int>* const* member_cancel = nullptr;
+  std::function<void(int, int)> on_done;
   int *derr = nullptr, *herr = nullptr, *fstat = nullptr;
   std::vector<char> active;
   std::vector<Table> smooth;  // per depth: members with a smoothing level there
@@ -575,6 +582,18 @@ struct wr_batch {
     }
     int status = WR_OK;
     std::vector<int> stalls(B, 0);  // consecutive Newton steps whose FGMRES ran out of iterations
+    std::vector<char> finished(B, 0);
+    auto member_status = [&](int m) {
+      if (!std::isfinite(fnorm[m])) return (int)WR_ERR_NAN;
+      return fnorm[m] <= opt.newton_rtol * f0[m] ? (int)WR_OK : (int)WR_ERR_NOT_CONVERGED;
+    };
+    auto finish = [&](int m, int rc) {  // member m leaves: hand out its result now
+      finished[m] = 1;
+      if (Uout)
+        WR_CUDA(cudaMemcpyAsync(Uout[m], U + off[0][m], sizeof(double) * mem[m].g[mem[m].L].ndofs,
+                                cudaMemcpyDeviceToDevice, s));
+      if (on_done) on_done(m, rc);
+    };
     for (int it = 0; it < opt.newton_maxit && it < 64; ++it) {
       for (int m = 0; m < B; ++m) {
         if (!active[m]) continue;
@@ -582,7 +601,11 @@ struct wr_batch {
         // a member that diverges or whose FGMRES stagnates leaves the batch early
         const bool gave_up = (opt.newton_divtol > 0.0 && fnorm[m] > opt.newton_divtol * f0[m]) ||
                              (opt.newton_stall > 0 && stalls[m] >= opt.newton_stall);
-        if (done || gave_up) active[m] = 0;
+        const bool cancelled = member_cancel && member_cancel[m] && member_cancel[m]->load();
+        if (done || gave_up || cancelled) {
+          active[m] = 0;
+          if (Uout || on_done) finish(m, cancelled ? (int)WR_ERR_CANCELLED : member_status(m));
+        }
       }
       build_tables();
       if (!fine.n) break;
@@ -622,6 +645,9 @@ struct wr_batch {
     }
     for (int m = 0; m < B; ++m)
       if (!(fnorm[m] <= opt.newton_rtol * f0[m])) status = std::isfinite(fnorm[m]) ? WR_ERR_NOT_CONVERGED : WR_ERR_NAN;
+    if (Uout || on_done)
+      for (int m = 0; m < B; ++m)
+        if (!finished[m]) finish(m, member_status(m));
     std::fill(active.begin(), active.end(), 1);
     build_tables();
     return status;
@@ -906,6 +932,34 @@ int wr_batch_solve(wr_batch* b, double* const* U, wr_stats* st) {
 }
 
 }  // extern "C"
+
+int batch_solve_hooked(wr_batch* b, double* const* U, wr_stats* st, const std::atomic<int>* const* cancel,
+                       const std::function<void(int, int)>& on_done) {
+  return bguard(b, [&]() -> int {
+    bneed(b && U && st, "null argument");
+    for (int m = 0; m < b->B; ++m)
+      WR_CUDA(cudaMemcpyAsync(b->U + b->off[0][m], U[m], sizeof(double) * b->mem[m].g[b->mem[m].L].ndofs,
+                              cudaMemcpyDeviceToDevice, b->s));
+    std::vector<wr_stats> loc(b->B);
+    struct Reset {  // the hooks belong to this call only
+      wr_batch* b;
+      ~Reset() {
+        b->Uout = nullptr;
+        b->member_cancel = nullptr;
+        b->on_done = nullptr;
+      }
+    } reset{b};
+    b->Uout = U;
+    b->member_cancel = cancel;
+    b->on_done = [&](int m, int rc) {
+      st[m] = loc[m];
+      on_done(m, rc);
+    };
+    const int rc = b->solve(loc);
+    WR_CUDA(cudaStreamSynchronize(b->s));
+    return rc;
+  });
+}
 
 extern "C" int wr_batch_set_graphs(wr_batch* b, int enable) {
   if (!b) return WR_ERR_ARG;

@@ -850,7 +850,11 @@ void dispatch_element(const LevelGeom& g, const FeTables& T, const PhysParams& p
   else if (g.k == 1 && g.q == 1) run_element<1, 1, LIN>(g, T, ph, W, x, y, ye, s);
   else if (g.k == 2 && g.q == 0) run_element<2, 0, LIN>(g, T, ph, W, x, y, ye, s);
   else if (g.k == 2 && g.q == 1) run_element<2, 1, LIN>(g, T, ph, W, x, y, ye, s);
-  else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
+  else if constexpr (!LIN) {  // the residual of Q2/Q1 with DG(2), DG(3) (their J is launch_jacobian_wq)
+    if (g.k == 1 && g.q == 2) run_element<1, 2, false>(g, T, ph, W, x, y, ye, s);
+    else if (g.k == 1 && g.q == 3) run_element<1, 3, false>(g, T, ph, W, x, y, ye, s);
+    else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
+  } else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 }
 
 template <int K, int Q, typename CT>
@@ -1249,13 +1253,15 @@ void run_wq(const LevelGeom& g, const FeTables& T, const double* W, double* Wq, 
 
 template <int K, int Q>
 void run_jac(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* Wq, const double* x,
-             double* y, double* ye, cudaStream_t s) {
+             double* y, double* ye, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
   const size_t smem = sizeof(JacSmem<K, Q>) * kWarps;
   auto kern = jac_kernel<K, Q>;
   WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((g.ncells() + kWarps - 1) / kWarps, g.N);
+  if (ev0) WR_CUDA(cudaEventRecord(ev0, s));
   kern<<<grid, 32 * kWarps, smem, s>>>(g, T, ph, Wq, x, ye);
   WR_LAUNCH_CHECK();
+  if (ev1) WR_CUDA(cudaEventRecord(ev1, s));
   assemble_kernel<K, Q, true><<<(unsigned)((g.ndofs + 255) / 256), 256, 0, s>>>(g, T, ph, ye, x, y);
   WR_LAUNCH_CHECK();
 }
@@ -1314,16 +1320,32 @@ void launch_wq(const LevelGeom& g, const FeTables& T, const double* W, double* W
   else if (g.k == 1 && g.q == 1) run_wq<1, 1>(g, T, W, Wq, s);
   else if (g.k == 2 && g.q == 0) run_wq<2, 0>(g, T, W, Wq, s);
   else if (g.k == 2 && g.q == 1) run_wq<2, 1>(g, T, W, Wq, s);
+  else if (g.k == 1 && g.q == 2) run_wq<1, 2>(g, T, W, Wq, s);
+  else if (g.k == 1 && g.q == 3) run_wq<1, 3>(g, T, W, Wq, s);
   else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 }
 
 void launch_jacobian_wq(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* Wq,
-                        const double* x, double* y, double* ye, cudaStream_t s) {
-  if (g.k == 1 && g.q == 0) run_jac<1, 0>(g, T, ph, Wq, x, y, ye, s);
-  else if (g.k == 1 && g.q == 1) run_jac<1, 1>(g, T, ph, Wq, x, y, ye, s);
-  else if (g.k == 2 && g.q == 0) run_jac<2, 0>(g, T, ph, Wq, x, y, ye, s);
-  else if (g.k == 2 && g.q == 1) run_jac<2, 1>(g, T, ph, Wq, x, y, ye, s);
+                        const double* x, double* y, double* ye, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+  if (g.k == 1 && g.q == 0) run_jac<1, 0>(g, T, ph, Wq, x, y, ye, s, ev0, ev1);
+  else if (g.k == 1 && g.q == 1) run_jac<1, 1>(g, T, ph, Wq, x, y, ye, s, ev0, ev1);
+  else if (g.k == 2 && g.q == 0) run_jac<2, 0>(g, T, ph, Wq, x, y, ye, s, ev0, ev1);
+  else if (g.k == 2 && g.q == 1) run_jac<2, 1>(g, T, ph, Wq, x, y, ye, s, ev0, ev1);
+  else if (g.k == 1 && g.q == 2) run_jac<1, 2>(g, T, ph, Wq, x, y, ye, s, ev0, ev1);
+  else if (g.k == 1 && g.q == 3) run_jac<1, 3>(g, T, ph, Wq, x, y, ye, s, ev0, ev1);
   else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
+}
+
+// FP64 operations of one (cell, slab) of jac_kernel's sum-factorised algorithm (a
+// multiply-add counts 2): interpolation of x (values and both derivatives), x^-
+// (values) and the pressure; the pointwise weak form; the test-function contractions.
+double jac_flops_per_cell_slab(int k, int q) {
+  const double nt = q + 1, nvl = k + 2, npl = k + 1, nq = k + 3, nq2 = nq * nq, nf = 2 * nt;
+  const double interp = nf * nvl * nq * 2 * nvl + 2 * nvl * nq * nvl + nt * npl * nq * npl +  // x passes
+                        nf * nq2 * 3 * nvl + 2 * nq2 * nvl + nt * nq2 * npl;                // y passes
+  const double point = nq2 * (nt + nt * nt * 2 * 4 + nt * (2 * nt + 2 * (1 + nt + nt * nt + 2 * nt)));
+  const double test = nf * nvl * nq * 3 * nq + nt * npl * nq * nq + nf * nvl * nvl * 2 * nq + nt * npl * npl * nq;
+  return 2.0 * (interp + point + test);
 }
 
 void launch_jacobian_f32(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* W, const double* x,
@@ -1349,6 +1371,8 @@ void launch_conv_elements(const LevelGeom& g, const FeTables& T, const double* W
     else if (g.k == 1 && g.q == 1) run_conv<1, 1>(g, T, W, c, s);
     else if (g.k == 2 && g.q == 0) run_conv<2, 0>(g, T, W, c, s);
     else if (g.k == 2 && g.q == 1) run_conv<2, 1>(g, T, W, c, s);
+    else if (g.k == 1 && g.q == 2) run_conv<1, 2>(g, T, W, c, s);
+    else if (g.k == 1 && g.q == 3) run_conv<1, 3>(g, T, W, c, s);
     else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
   } else {
     float* c = static_cast<float*>(Ce);

@@ -44,6 +44,54 @@ struct PD {
   static constexpr int NVL = K + 2, NVE = NVL * NVL;
 };
 
+// Block LDU of a slab's diagonal block over its NT = q+1 temporal sub-blocks (block
+// Gaussian elimination without pivoting across sub-blocks, partial pivoting inside the
+// diagonal ones):  S_k = A_kk - sum_{m<k} C_km X_mk,  C_ik = A_ik - sum_{m<k} C_im X_mk
+// (i > k),  X_kj = S_k^{-1} (A_kj - sum_{m<k} C_km X_mj) (j > k).  The NT^2 stored
+// blocks S_k^{-1}, C_ik, X_kj are kept in the order the apply consumes them:
+//   forward, k = 0 .. NT-1:   z_k = S_k^{-1} r_k;  r_i -= C_ik z_k (i = k+1 .. NT-1)
+//   backward, k = NT-2 .. 0:  y_k -= X_kj y_j (j = k+1 .. NT-1), with y_k = z_k before.
+// DG(0) is the single inverse; DG(1) is [A00^{-1}, A10, S^{-1}, X].
+struct BlockOp {
+  int src_y, src;  // source vector: y (1) or the right-hand side r (0), temporal index
+  int dst, di;     // 0: y_di = result, 1: r_di -= result, 2: y_di -= result
+};
+template <int NT>
+__host__ __device__ constexpr BlockOp block_op(int b) {
+  constexpr int nf = NT * (NT + 1) / 2;  // forward blocks
+  BlockOp o{0, 0, 0, 0};
+  if (b < nf) {
+    int k = 0, base = 0;
+    while (b >= base + (NT - k)) {
+      base += NT - k;
+      ++k;
+    }
+    const int r = b - base;
+    if (r == 0) o = BlockOp{0, k, 0, k};
+    else o = BlockOp{1, k, 1, k + r};
+  } else {
+    int rem = b - nf, k = NT - 2;
+    while (rem >= NT - 1 - k) {
+      rem -= NT - 1 - k;
+      --k;
+    }
+    o = BlockOp{1, k + 1 + rem, 2, k};
+  }
+  return o;
+}
+// storage positions of S_k^{-1}, C_ik (i > k) and X_kj (j > k)
+template <int NT>
+__host__ __device__ constexpr int pos_diag(int k) { return k * NT - k * (k - 1) / 2; }
+template <int NT>
+__host__ __device__ constexpr int pos_low(int i, int k) { return pos_diag<NT>(k) + (i - k); }
+template <int NT>
+__host__ __device__ constexpr int pos_up(int k, int j) {
+  return NT * (NT + 1) / 2 + (NT - 2 - k) * (NT - 1 - k) / 2 + (j - k - 1);
+}
+static_assert(pos_diag<2>(1) == 2 && pos_low<2>(1, 0) == 1 && pos_up<2>(0, 1) == 3, "DG(1) block order");
+static_assert(block_op<3>(6).dst == 2 && block_op<3>(6).di == 1 && block_op<3>(6).src == 2, "DG(2) block order");
+static_assert(pos_up<4>(0, 3) == 15 && pos_up<4>(2, 3) == 10 && pos_low<4>(3, 2) == 8, "DG(3) block order");
+
 struct Slot {
   int field;   // 0, 1 velocity component, 2 pressure
   int gx, gy;  // global node
@@ -509,6 +557,21 @@ __device__ void store_colmajor(const CT* A, ST* dst) {
   }
 }
 
+// M -= P Q for an MS x MS shared-memory M (row-major, leading dimension LD) and P, Q
+// stored blocks in global memory (column-major, leading dimension MS) that this CTA
+// wrote before its last barrier.
+template <int MS, int LD, int NTH, typename CT, typename ST>
+__device__ void gemm_sub_stored(CT* M, const ST* P, const ST* Qm) {
+  for (int e = threadIdx.x; e < MS * MS; e += NTH) {
+    const int i = e / MS, j = e - i * MS;
+    CT acc = 0;
+#pragma unroll 4
+    for (int l = 0; l < MS; ++l) acc = fma((CT)P[l * MS + i], (CT)Qm[j * MS + l], acc);
+    M[i * LD + j] -= acc;
+  }
+  __syncthreads();
+}
+
 // C = sign * A B (+ C if accumulate) for MS x MS shared-memory matrices, result written over B.
 template <int MS, int LD, int NTH, typename CT>
 __device__ void gemm_into_b(const CT* A, CT* B, CT sign) {
@@ -545,9 +608,9 @@ block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const C
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT* M1 = reinterpret_cast<CT*>(smem_raw);
   CT* M2 = M1 + MS * LD;
-  CT* colbuf = M2 + (Q == 1 ? MS * LD : 0);
+  CT* colbuf = M2 + (Q >= 1 ? MS * LD : 0);
   using FT = FactorTables<K, NPGX, CT>;
-  FT& ft = *reinterpret_cast<FT*>(smem_raw + ((sizeof(CT) * ((Q == 1 ? 2 : 1) * MS * LD + MS) + 15) / 16) * 16);
+  FT& ft = *reinterpret_cast<FT*>(smem_raw + ((sizeof(CT) * ((Q >= 1 ? 2 : 1) * MS * LD + MS) + 15) / 16) * 16);
   int* perm = reinterpret_cast<int*>(&ft + 1);
   int* sh = perm + MS;
   const int blk = blockIdx.x, slab = blockIdx.y;
@@ -564,6 +627,40 @@ block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const C
     if (conv) assemble_conv<K, Q, CT, LD, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M1, 0, 0, gr);
     ok = invert_block<MS, LD, NTH>(M1, colbuf, perm, sh);
     store_colmajor<MS, LD, NTH>(M1, F);
+  } else if constexpr (Q >= 2) {
+    // left-looking block LU over the NT temporal sub-blocks (see block_op): the earlier
+    // C_km and X_mj are read back from this block's own stored factors
+    constexpr int NT = Q + 1;
+    auto assemble = [&](CT* M, int a, int b) {
+      assemble_const<K, Q, CT, LD, NPGX>(g, T, ph, ft, M, a, b, false, gr);
+      __syncthreads();
+      if (conv) assemble_conv<K, Q, CT, LD, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M, a, b, gr);
+      __syncthreads();
+    };
+    ok = true;
+    for (int k = 0; k < NT; ++k) {
+      assemble(M1, k, k);
+      for (int m = 0; m < k; ++m)
+        gemm_sub_stored<MS, LD, NTH>(M1, F + pos_low<NT>(k, m) * BLK, F + pos_up<NT>(m, k) * BLK);
+      ok = invert_block<MS, LD, NTH>(M1, colbuf, perm, sh) && ok;
+      store_colmajor<MS, LD, NTH>(M1, F + pos_diag<NT>(k) * BLK);
+      __syncthreads();
+      for (int j = k + 1; j < NT; ++j) {
+        assemble(M2, k, j);
+        for (int m = 0; m < k; ++m)
+          gemm_sub_stored<MS, LD, NTH>(M2, F + pos_low<NT>(k, m) * BLK, F + pos_up<NT>(m, j) * BLK);
+        gemm_into_b<MS, LD, NTH, CT>(M1, M2, CT(1));
+        store_colmajor<MS, LD, NTH>(M2, F + pos_up<NT>(k, j) * BLK);
+        __syncthreads();  // M2 is reassembled next; the stored block is read back later
+      }
+      for (int i = k + 1; i < NT; ++i) {
+        assemble(M2, i, k);
+        for (int m = 0; m < k; ++m)
+          gemm_sub_stored<MS, LD, NTH>(M2, F + pos_low<NT>(i, m) * BLK, F + pos_up<NT>(m, k) * BLK);
+        store_colmajor<MS, LD, NTH>(M2, F + pos_low<NT>(i, k) * BLK);
+        __syncthreads();
+      }
+    }
   } else {
     // A00^{-1}
     assemble_const<K, Q, CT, LD, NPGX>(g, T, ph, ft, M1, 0, 0, false, gr);
@@ -983,10 +1080,11 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
         const int sp = sm.sidx[tid % MS];
         if (sp >= 0) pf = (CT)r[((int64_t)(slab + 1) * NT + tid / MS) * g.S + sp];
       }
-      // (c) the slab's stored blocks: Q = 0: y0 = A^{-1} r0;  Q = 1: z0 = A00^{-1} r0,
-      //     s1 = r1 - A10 z0, y1 = S^{-1} s1, y0 = z0 - X y1
+      // (c) the slab's stored blocks in block_op order (Q = 0: y0 = A^{-1} r0;  Q = 1:
+      //     z0 = A00^{-1} r0, s1 = r1 - A10 z0, y1 = S^{-1} s1, y0 = z0 - X y1)
       for (int b = 0; b < NB; ++b) {
-        const CT* xv = (b == 0) ? sm.rhs[0] : (b == 1) ? sm.y[0] : (b == 2) ? sm.rhs[NT - 1] : sm.y[NT - 1];
+        const BlockOp op = block_op<NT>(b);
+        const CT* xv = op.src_y ? sm.y[op.src] : sm.rhs[op.src];
         CT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         for (int k = 0; k < NCH; ++k) {
           const int slot = (int)(ci % NS);
@@ -1033,10 +1131,9 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
           CT sum = sm.red[0][tid];
 #pragma unroll
           for (int h = 1; h < C::G; ++h) sum += sm.red[h][tid];
-          if (b == 0) sm.y[0][tid] = sum;
-          else if (b == 1) sm.rhs[NT - 1][tid] -= sum;
-          else if (b == 2) sm.y[NT - 1][tid] = sum;
-          else sm.y[0][tid] -= sum;
+          if (op.dst == 0) sm.y[op.di][tid] = sum;
+          else if (op.dst == 1) sm.rhs[op.di][tid] -= sum;
+          else sm.y[op.di][tid] -= sum;
         }
         consumer_sync<NCONS>();
       }
@@ -1228,9 +1325,10 @@ __device__ __forceinline__ void warp_apply(const FeTables& T, const Items& items
           if (sp >= 0) pf[u] = (CT)v.r[((int64_t)(slab + 1) * NT + e / MS) * g.S + sp];
         }
       }
-      // Q = 0: y0 = A^{-1} r0;  Q = 1: z0 = A00^{-1} r0, s1 = r1 - A10 z0, y1 = S^{-1} s1, y0 = z0 - X y1
+      // the stored blocks in block_op order
       for (int b = 0; b < NB; ++b) {
-        const CT* xv = (b == 0) ? sm.rhs[0] : (b == 1) ? sm.y[0] : (b == 2) ? sm.rhs[NT - 1] : sm.y[NT - 1];
+        const BlockOp op = block_op<NT>(b);
+        const CT* xv = op.src_y ? sm.y[op.src] : sm.rhs[op.src];
         const FT* A = v.factors + (((int64_t)blk * v.fN + v.s0 + slab) * NB + b) * C::BLK;
         CT acc[R];
 #pragma unroll
@@ -1250,10 +1348,9 @@ __device__ __forceinline__ void warp_apply(const FeTables& T, const Items& items
         for (int r = 0; r < R; ++r) {
           const int row = lane + 32 * r;
           if (row >= MS) continue;
-          if (b == 0) sm.y[0][row] = acc[r];
-          else if (b == 1) sm.rhs[NT - 1][row] -= acc[r];
-          else if (b == 2) sm.y[NT - 1][row] = acc[r];
-          else sm.y[0][row] -= acc[r];
+          if (op.dst == 0) sm.y[op.di][row] = acc[r];
+          else if (op.dst == 1) sm.rhs[op.di][row] -= acc[r];
+          else sm.y[op.di][row] -= acc[r];
         }
         __syncwarp();
       }
@@ -1571,7 +1668,7 @@ void run_factor(const LevelGeom& g, const FeTables& T, const PhysParams& ph, con
                 ST* factors, int* status, cudaStream_t s) {
   using pd = PD<K, NPGX>;
   constexpr int NTH = K == 1 ? 256 : 512;
-  const size_t mats = ((sizeof(CT) * ((Q == 1 ? 2 : 1) * pd::MS * pd::LD + pd::MS) + 15) / 16) * 16;
+  const size_t mats = ((sizeof(CT) * ((Q >= 1 ? 2 : 1) * pd::MS * pd::LD + pd::MS) + 15) / 16) * 16;
   const size_t smem = mats + sizeof(FactorTables<K, NPGX, CT>) + sizeof(int) * (pd::MS + 2);
   auto kern = block_factor_kernel<K, Q, CT, ST, NTH, NPGX>;
   WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1774,6 +1871,11 @@ void launch_block_factor(const LevelGeom& g, const FeTables& T, const PhysParams
   } else if (bs.kind == 0 && g.k == 1 && g.q == 0 && precision == WR_BF16) {
     run_factor_warp<__nv_bfloat16>(g, T, ph, bs, Cf, static_cast<__nv_bfloat16*>(factors), st, s);
   } else
+  if (g.k == 1 && (g.q == 2 || g.q == 3)) {  // Q2/Q1 with DG(2), DG(3): FP64
+    if (precision != WR_FP64) throw WrError(WR_ERR_ARG, "DG(2) and DG(3) factors are FP64 only");
+    if (g.q == 2) run_factor<1, 2, double, double>(g, T, ph, bs, Cd, static_cast<double*>(factors), st, s);
+    else run_factor<1, 3, double, double>(g, T, ph, bs, Cd, static_cast<double*>(factors), st, s);
+  } else
   WR_F(1, 0) WR_F(1, 1) WR_F(2, 0) WR_F(2, 1) throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 #undef WR_F
   if (!check) return;
@@ -1803,6 +1905,12 @@ void launch_block_apply(const LevelGeom& g, const FeTables& T, const BlockSet& b
     if (g.q == 0) run_apply<1, 0, double, 4>(g, T, bs, static_cast<const double*>(factors), r, out, err, prev, s);
     else run_apply<1, 1, double, 4>(g, T, bs, static_cast<const double*>(factors), r, out, err, prev, s);
   } else
+  if (g.k == 1 && (g.q == 2 || g.q == 3)) {  // Q2/Q1 with DG(2), DG(3): FP64, CTA tile 0
+    if (precision != WR_FP64) throw WrError(WR_ERR_ARG, "DG(2) and DG(3) factors are FP64 only");
+    const double* f = static_cast<const double*>(factors);
+    if (g.q == 2) run_apply<1, 2, double>(g, T, bs, f, r, out, err, prev, s, bs.kind == 0 ? cp : nullptr);
+    else run_apply<1, 3, double>(g, T, bs, f, r, out, err, prev, s, bs.kind == 0 ? cp : nullptr);
+  } else
   WR_A(1, 0) WR_A(1, 1) WR_A(2, 0) WR_A(2, 1) throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 #undef WR_A
 }
@@ -1814,6 +1922,8 @@ void launch_scatter(const LevelGeom& g, const BlockSet& bs, const double* Yp, do
   else if (g.k == 1 && g.q == 1) scatter_kernel<1, 1><<<blocks, threads, 0, s>>>(g, Yp, y, wt);
   else if (g.k == 2 && g.q == 0) scatter_kernel<2, 0><<<blocks, threads, 0, s>>>(g, Yp, y, wt);
   else if (g.k == 2 && g.q == 1) scatter_kernel<2, 1><<<blocks, threads, 0, s>>>(g, Yp, y, wt);
+  else if (g.k == 1 && g.q == 2) scatter_kernel<1, 2><<<blocks, threads, 0, s>>>(g, Yp, y, wt);
+  else if (g.k == 1 && g.q == 3) scatter_kernel<1, 3><<<blocks, threads, 0, s>>>(g, Yp, y, wt);
   else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
   WR_LAUNCH_CHECK();
 }

@@ -3,14 +3,29 @@
 // Requests queue in arrival order.  A scheduler thread admits the request at the
 // head of the queue as soon as an in-flight slot is free and its device memory
 // (wr_estimate_bytes plus its solution vector) fits in the remaining budget;
-// a request larger than the whole budget is refused.  Every admitted request
-// runs on a worker thread with its own CUDA stream and context, so its level
-// hierarchy, factors and Krylov state stay on the device for the whole solve,
-// and the kernels of all in-flight solves overlap on the GPU.  When a solve
-// completes its memory and slot are released and the scheduler admits the next
-// requests at once (continuous admission, no waves).  Each solve runs the same
-// deterministic kernels on its own stream, so its result does not depend on
+// a request larger than the whole budget is refused.
+//
+// Per-request mode (wr_server_create): every admitted request runs on a worker
+// thread with its own CUDA stream and context, so its level hierarchy, factors and
+// Krylov state stay on the device for the whole solve, and the kernels of all
+// in-flight solves overlap on the GPU.  When a solve completes its memory and slot
+// are released and the scheduler admits the next requests at once.  Each solve runs
+// the same deterministic kernels on its own stream, so its result does not depend on
 // what else is in flight.
+//
+// Batched mode (wr_server_create_batched): a slot holds a cohort.  When a slot is
+// free, the scheduler takes the head request and every queued request with the same
+// (k, q) behind it, in arrival order, up to max_members and the remaining budget, and
+// solves them as one lock-step batch (wr_batch: one launch per stage of every V-cycle,
+// Newton step and FGMRES iteration for all members, V-cycles replayed as CUDA
+// graphs) on the slot's stream.  Cohorts in different slots overlap on the device;
+// requests arriving while cohorts run form the next cohort as soon as a slot and
+// memory free up.  A member is handed back the moment it leaves its cohort
+// (converged, given up, failed or cancelled), so its latency is its own; the
+// cohort's memory is released when its last member leaves.  A member's result is its
+// solve alone up to rounding (the apply tiles are tuned per cohort).  Requests the
+// batch engine does not take (the heat equation, DG(2) and DG(3)) run in the
+// per-request way in a slot of their own.
 #include <chrono>
 #include <condition_variable>
 #include <atomic>
@@ -57,6 +72,8 @@ struct wr_server {
   wr_options opt;
   int64_t budget = 0, used = 0, peak_used = 0;
   int max_inflight = 1, inflight = 0, peak_inflight = 0, device = 0;
+  int max_members = 1;  // > 1: batched mode, cohorts of up to max_members requests per slot
+  int peak_cohort = 0;
   uint64_t next_id = 1;
   bool stopping = false;
   std::string err;
@@ -113,6 +130,77 @@ struct wr_server {
     cv.notify_all();
   }
 
+  static bool batchable(const wr_problem& p) {
+    return p.kind != WR_HEAT && p.kind != WR_HEAT_EIGEN && (p.q == 0 || p.q == 1);
+  }
+
+  // One cohort solved as a lock-step batch on its own stream; each member completes
+  // as soon as it leaves the batch.
+  void run_cohort(std::vector<std::shared_ptr<Request>> rs) {
+    cudaSetDevice(device);
+    const int n = (int)rs.size();
+    int64_t maxd = 0, bytes = 0;
+    for (auto& r : rs) {
+      maxd = std::max(maxd, r->ndofs);
+      bytes += r->bytes;
+      std::memset(&r->st, 0, sizeof(r->st));
+    }
+    cudaStream_t s = nullptr;
+    wr_batch* b = nullptr;
+    std::vector<double*> dU(n, nullptr);
+    std::vector<wr_stats> st(n);
+    std::vector<const std::atomic<int>*> cancel(n);
+    std::vector<wr_problem> ps(n);
+    for (int m = 0; m < n; ++m) {
+      ps[m] = rs[m]->p;
+      cancel[m] = &rs[m]->cancel;
+    }
+    std::vector<char> handed(n, 0);
+    auto complete = [&](int m, int rc) {
+      auto& r = rs[m];
+      if (rc == WR_OK || rc == WR_ERR_NOT_CONVERGED) {
+        r->U.resize(r->ndofs);
+        if (cudaMemcpyAsync(r->U.data(), dU[m], sizeof(double) * r->ndofs, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+          rc = WR_ERR_CUDA;
+      }
+      std::lock_guard<std::mutex> lock(mu);
+      r->st = st[m];
+      r->status = rc;
+      r->t_end = now_ms();
+      r->done = true;
+      handed[m] = 1;
+      cv.notify_all();
+    };
+    int rc = WR_OK;
+    if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, priority_of(maxd)) != cudaSuccess) rc = WR_ERR_CUDA;
+    if (rc == WR_OK) rc = wr_batch_create(&b, n, ps.data(), &opt, s);
+    for (int m = 0; m < n && rc == WR_OK; ++m)
+      if (cudaMallocAsync(&dU[m], sizeof(double) * rs[m]->ndofs, s) != cudaSuccess) rc = WR_ERR_NOMEM;
+    if (rc == WR_OK) rc = wr_batch_initial_guess(b, dU.data());
+    for (int m = 0; m < n && rc == WR_OK; ++m)
+      if (!rs[m]->U0.empty() && cudaMemcpyAsync(dU[m], rs[m]->U0.data(), sizeof(double) * rs[m]->ndofs,
+                                                cudaMemcpyHostToDevice, s) != cudaSuccess)
+        rc = WR_ERR_CUDA;
+    if (rc == WR_OK) {
+      const int brc = batch_solve_hooked(b, dU.data(), st.data(), cancel.data(), complete);
+      if (brc != WR_OK && brc != WR_ERR_NOT_CONVERGED && brc != WR_ERR_NAN) rc = brc;
+    }
+    for (int m = 0; m < n; ++m)
+      if (!handed[m]) complete(m, rc == WR_OK ? WR_ERR_STATE : rc);
+    for (double* p : dU)
+      if (p) cudaFreeAsync(p, s);
+    if (b) wr_batch_destroy(b);
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    used -= bytes;
+    --inflight;
+    cv.notify_all();
+  }
+
   void schedule() {
     std::unique_lock<std::mutex> lock(mu);
     while (true) {
@@ -143,10 +231,28 @@ struct wr_server {
       }
       used += r->bytes;
       ++inflight;
+      r->t_start = now_ms();
+      if (max_members > 1 && batchable(r->p)) {
+        // the cohort: r and the queued requests of the same (k, q) behind it that fit
+        std::vector<std::shared_ptr<Request>> cohort{r};
+        for (auto it = queue.begin(); it != queue.end() && (int)cohort.size() < max_members;) {
+          const auto& c = *it;
+          if (batchable(c->p) && c->p.k == r->p.k && c->p.q == r->p.q && used + c->bytes <= budget) {
+            used += c->bytes;
+            c->t_start = r->t_start;
+            cohort.push_back(c);
+            it = queue.erase(it);
+          } else {
+            ++it;
+          }
+        }
+        peak_cohort = std::max(peak_cohort, (int)cohort.size());
+        workers.emplace_back([this, cohort] { run_cohort(cohort); });
+      } else {
+        workers.emplace_back([this, r] { run_one(r); });
+      }
       peak_used = std::max(peak_used, used);
       peak_inflight = std::max(peak_inflight, inflight);
-      r->t_start = now_ms();
-      workers.emplace_back([this, r] { run_one(r); });
     }
   }
 };
@@ -173,6 +279,17 @@ int wr_server_create(wr_server** out, int64_t mem_budget_bytes, int max_inflight
   sv->scheduler = std::thread([raw] { raw->schedule(); });
   *out = sv.release();
   return WR_OK;
+}
+
+int wr_server_create_batched(wr_server** out, int64_t mem_budget_bytes, int max_cohorts, int max_members,
+                             const wr_options* o) {
+  if (!out || max_members < 1) return WR_ERR_ARG;
+  const int rc = wr_server_create(out, mem_budget_bytes, max_cohorts, o);
+  if (rc == WR_OK) {
+    std::lock_guard<std::mutex> lock((*out)->mu);
+    (*out)->max_members = max_members;
+  }
+  return rc;
 }
 
 int wr_server_destroy(wr_server* sv) {
@@ -264,6 +381,14 @@ int wr_server_stats(wr_server* sv, int64_t* peak_bytes, int* peak_inflight) {
   std::lock_guard<std::mutex> lock(sv->mu);
   if (peak_bytes) *peak_bytes = sv->peak_used;
   if (peak_inflight) *peak_inflight = sv->peak_inflight;
+  return WR_OK;
+}
+
+// Largest cohort solved as one batch so far (batched mode; 0 in per-request mode).
+int wr_server_peak_cohort(wr_server* sv, int* out) {
+  if (!sv || !out) return WR_ERR_ARG;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  *out = sv->peak_cohort;
   return WR_OK;
 }
 

@@ -143,6 +143,7 @@ struct wr_ctx {
   // CUDA-event timing of the smoother-apply kernel (per level), enabled by wr_profile
   bool prof = false;
   std::vector<std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
+  std::vector<std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> prof_jac;  // J(W)x element kernel, per level
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
 
@@ -246,7 +247,13 @@ struct wr_ctx {
 
   void jac(int l, const double* x, double* y) {
     if (heat) heat_jacobian(L[l].g, tab, ph, x, y, htmp, s);
-    else launch_jacobian_wq(L[l].g, tab, ph, L[l].Wq, x, y, ye, s);
+    else if (prof && l < (int)prof_jac.size()) {
+      cudaEvent_t e0 = next_event(), e1 = next_event();
+      launch_jacobian_wq(L[l].g, tab, ph, L[l].Wq, x, y, ye, s, e0, e1);
+      prof_jac[l].push_back({e0, e1});
+    } else {
+      launch_jacobian_wq(L[l].g, tab, ph, L[l].Wq, x, y, ye, s);
+    }
   }
   // J inside the preconditioner (smoother residuals, the residual restricted to the
   // next level, eigen-estimates): single-precision element arithmetic in the
@@ -484,7 +491,7 @@ struct wr_ctx {
     if (ph.conv != 0.0) launch_conv_elements(L[0].g, tab, L[0].W, Ce, WR_FP64, s);
     launch_block_factor(L[0].g, tab, ph, cbs, Ce, cfactors, WR_FP64, fstat, s);
     linearised = true;
-    if (opt.autotune)
+    if (opt.autotune && q <= 1)  // DG(2), DG(3) have the one CTA tile
       for (int l = 1; l <= T_; ++l)
         if (!L[l].recompute && L[l].variant < 0 && L[l].nchunk == 1) {
           Level& lv = L[l];
@@ -848,8 +855,8 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
   int rc = guarded(c, [&]() -> int {
     const bool heat = p->kind == WR_HEAT || p->kind == WR_HEAT_EIGEN;
     need(p->k == 1 || p->k == 2 || (heat && p->k == 3), "k must be 1 or 2 (1, 2 or 3 for the heat equation)");
-    need(heat ? (p->q >= 0 && p->q <= 3) : (p->q == 0 || p->q == 1),
-         "q must be 0 or 1 (0..3 for the heat equation)");
+    need(heat ? (p->q >= 0 && p->q <= 3) : (p->q == 0 || p->q == 1 || (p->k == 1 && (p->q == 2 || p->q == 3))),
+         "q must be 0 or 1 (0..3 for Q2/Q1 and for the heat equation)");
     if (heat) {
       need(p->n_coarse == 1 || p->n_coarse == 2, "the heat equation coarsens to 1x1 or 2x2");
       need(heat_block_fits(p->k, p->q, p->n_coarse),
@@ -876,6 +883,11 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
          "patch_assembly must be WR_PATCH_SUBMATRIX or WR_PATCH_LOCAL");
     need(c->opt.scatter_weight == WR_WEIGHT_ONE || c->opt.scatter_weight == WR_WEIGHT_MULTIPLICITY,
          "scatter_weight must be WR_WEIGHT_ONE or WR_WEIGHT_MULTIPLICITY");
+    if (!heat && p->q >= 2) {
+      need(c->opt.precision == WR_FP64, "DG(2) and DG(3) run with FP64 factors");
+      need(p->n_coarse == 2, "DG(2) and DG(3) coarsen to 2x2");
+      need(c->opt.time_parallel == 0, "the parallel-in-time patch solve is built for DG(0) and DG(1)");
+    }
     need(c->opt.store_factors == WR_STORE || c->opt.store_factors == WR_RECOMPUTE ||
              c->opt.store_factors == WR_STORE_AUTO,
          "store_factors must be WR_STORE, WR_RECOMPUTE or WR_STORE_AUTO");
@@ -1328,6 +1340,7 @@ int wr_profile(wr_ctx* c, int enable) {
     WR_CUDA(cudaStreamSynchronize(c->s));
     c->prof = enable != 0;
     c->prof_ev.assign(c->L.size(), {});
+    c->prof_jac.assign(c->L.size(), {});
     c->ev_used = 0;
     // create the events now so that none is created inside a timed region
     while (c->prof && c->ev_pool.size() < 4096) {
@@ -1353,6 +1366,27 @@ int wr_profile_smoother(wr_ctx* c, int level, double* total_ms, int* launches) {
     }
     *total_ms = tot;
     *launches = (int)c->prof_ev[level].size();
+    return WR_OK;
+  });
+}
+
+int wr_profile_jacobian(wr_ctx* c, int level, double* total_ms, int* launches, double* flops_per_launch) {
+  return guarded(c, [&]() -> int {
+    need(c && total_ms && launches, "null argument");
+    check_level(c, level, 0);
+    need(!c->heat, "the heat equation has no element kernel");
+    need(level < (int)c->prof_jac.size(), "profiling not enabled");
+    WR_CUDA(cudaStreamSynchronize(c->s));
+    double tot = 0.0;
+    for (auto& pr : c->prof_jac[level]) {
+      float ms = 0.f;
+      WR_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+      tot += ms;
+    }
+    *total_ms = tot;
+    *launches = (int)c->prof_jac[level].size();
+    const LevelGeom& g = c->L[level].g;
+    if (flops_per_launch) *flops_per_launch = jac_flops_per_cell_slab(g.k, g.q) * g.ncells() * g.N;
     return WR_OK;
   });
 }

@@ -198,8 +198,11 @@ void launch_jacobian(const LevelGeom& g, const FeTables& T, const PhysParams& ph
 int64_t wq_doubles(const LevelGeom& g);
 void launch_wq(const LevelGeom& g, const FeTables& T, const double* W, double* Wq, cudaStream_t s);
 // y = J(W) x from the tabulated W (the solver's form of launch_jacobian)
+// (events, if given, are recorded on s around the element kernel alone)
 void launch_jacobian_wq(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* Wq,
-                        const double* x, double* y, double* ye, cudaStream_t s);
+                        const double* x, double* y, double* ye, cudaStream_t s, cudaEvent_t ev0 = nullptr,
+                        cudaEvent_t ev1 = nullptr);
+double jac_flops_per_cell_slab(int k, int q);
 void launch_jacobian_f32(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* W,
                          const double* x, double* y, double* ye, cudaStream_t s);
 void launch_boundary_values(const LevelGeom& g, const FeTables& T, const PhysParams& ph, double* U,
@@ -341,6 +344,12 @@ void bt_krylov_update(const BatchSeg* segs, int nseg, int64_t dofs, const double
 // creating and destroying a context never synchronises the whole device while
 // other streams run.
 int create_context(wr_ctx** out, const wr_problem* p, const wr_options* o, void* stream, bool stream_ordered);
+
+// wr_batch_solve with per-member completion: as soon as member m leaves the lock-step
+// set (converged, gave up, failed, or cancelled through cancel[m]) its iterate is
+// copied to U[m], st[m] is final and on_done(m, status) runs on the calling thread.
+int batch_solve_hooked(wr_batch* b, double* const* U, wr_stats* st, const std::atomic<int>* const* cancel,
+                       const std::function<void(int, int)>& on_done);
 
 // The apply kernels' bounded wait on an mbarrier that never completes: *timed_out = 1
 // and *ns = the time waited (device pointers).

@@ -117,6 +117,9 @@ _SIGS = {
     "wr_batch_solve": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Stats)]),
     "wr_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int,
                                         ctypes.POINTER(Options)]),
+    "wr_server_create_batched": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int,
+                                                ctypes.c_int, ctypes.POINTER(Options)]),
+    "wr_server_peak_cohort": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "wr_server_destroy": (ctypes.c_int, [_P]),
     "wr_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(Problem), _P, ctypes.POINTER(ctypes.c_uint64)]),
     "wr_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int, _P, ctypes.POINTER(Stats),
@@ -126,6 +129,8 @@ _SIGS = {
     "wr_inject_alloc_failure": (ctypes.c_int, [ctypes.c_int64]),
     "wr_selftest_bounded_wait": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "wr_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "wr_profile_jacobian": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "wr_profile_smoother": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int)]),
 }
@@ -359,6 +364,13 @@ class Context:
         self._check(self._lib.wr_profile_smoother(self._h, level, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
 
+    def profile_jacobian(self, level):
+        """(total ms, launches, FP64 operations per launch) of the J(W) x element kernel."""
+        ms, n, fl = ctypes.c_double(), ctypes.c_int(), ctypes.c_double()
+        self._check(self._lib.wr_profile_jacobian(self._h, level, ctypes.byref(ms), ctypes.byref(n),
+                                                  ctypes.byref(fl)))
+        return ms.value, n.value, fl.value
+
     def solve(self, U, check=True):
         """Newton solve in place; the returned statistics carry the status code."""
         st = Stats()
@@ -491,16 +503,22 @@ class Batch:
 
 class Server:
     """A request loop over independent solves: FIFO admission under a device
-    memory budget and an in-flight cap; each admitted request runs on its own
-    native worker thread, CUDA stream and context."""
+    memory budget and an in-flight cap.  batch_members = 1: each admitted request
+    runs on its own native worker thread, CUDA stream and context; > 1: each
+    in-flight slot solves a cohort of up to batch_members queued requests (same k
+    and q) as one lock-step batch (wr_server_create_batched)."""
 
-    def __init__(self, mem_budget_bytes, max_inflight, options=None):
+    def __init__(self, mem_budget_bytes, max_inflight, options=None, batch_members=1):
         lib = load()
         self._lib = lib
         self.options = options if options is not None else default_options()
         h = ctypes.c_void_p()
-        rc = lib.wr_server_create(ctypes.byref(h), int(mem_budget_bytes), int(max_inflight),
-                                  ctypes.byref(self.options))
+        if batch_members > 1:
+            rc = lib.wr_server_create_batched(ctypes.byref(h), int(mem_budget_bytes), int(max_inflight),
+                                              int(batch_members), ctypes.byref(self.options))
+        else:
+            rc = lib.wr_server_create(ctypes.byref(h), int(mem_budget_bytes), int(max_inflight),
+                                      ctypes.byref(self.options))
         if rc != WR_OK:
             raise WrmgError(rc, "wr_server_create failed")
         self._h = h
@@ -551,6 +569,7 @@ class Server:
             raise WrmgError(rc, "wr_server_cancel failed")
 
     def stats(self):
-        b, n = ctypes.c_int64(), ctypes.c_int()
+        b, n, c = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
         self._lib.wr_server_stats(self._h, ctypes.byref(b), ctypes.byref(n))
-        return {"peak_bytes": b.value, "peak_inflight": n.value}
+        self._lib.wr_server_peak_cohort(self._h, ctypes.byref(c))
+        return {"peak_bytes": b.value, "peak_inflight": n.value, "peak_cohort": c.value}
