@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--full-mix", action="store_true",
                     help="serve form: draw n and N from {16, 32, 64} (default {16, 32})")
     ap.add_argument("--form", default="cycle", choices=["cycle", "precision", "batch", "serve", "smoother", "timestepping", "lid", "heat",
-                                                        "setup"],
+                                                        "setup", "jacobian", "transfers"],
                     help="cycle: the V(2,2) throughput line (default); precision: the FP64/FP32/BF16 "
                          "solves of the 128x128 Q2/Q1 DG(0) 128-slab workload")
     return ap.parse_args()
@@ -743,6 +743,100 @@ def run_smoother_form(args):
     print(json.dumps(out), flush=True)
 
 
+def run_jacobian_form(args):
+    """The finest-level J(W) x apply alone (element kernel and assembly), K timed
+    applications after W warm-ups, with the factors recomputed per window so that the
+    context holds little besides the vectors and W at the Gauss points: the burst
+    roofline of the element kernel, and the command its ncu captures run."""
+    import torch
+    from paper_2407_13997_gb300 import inputs, wrmg
+    torch.cuda.set_device(0)
+    w = workload(args)
+    ctx = wrmg.Context(w, wrmg.default_options(store_factors=wrmg.WR_RECOMPUTE, recompute_slabs=1))
+    W = torch.from_numpy(inputs.forcing_shaped_iterate(w)).cuda()
+    ctx.linearise(W, eig=False)
+    L = ctx.fine
+    x = torch.from_numpy(inputs.seeded_vector(3, ctx.ndofs(L))).cuda()
+    y = ctx.vector(L)
+    stream = torch.cuda.current_stream()
+    fp64_tflops = wrmg.measure_fp64_tflops(stream.cuda_stream)
+    ctx.profile(True)
+    for _ in range(args.warmup):
+        ctx.apply_jacobian(L, x, y)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.apply_jacobian(L, x, y)
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    jms, jn, jflops = ctx.profile_jacobian(L)
+    avg_s = jms / max(jn, 1) * 1e-3
+    D = ctx.ndofs(L)
+    nv = w.n_fine * (w.k + 1) + 1
+    alg_bytes = 8.0 * (2 * D + w.N * (w.q + 1) * 2 * nv * nv)
+    hbm_peak, hbm_src = measured_peaks()
+    out = {"form": "jacobian", "workload": w.name, "launches": jn, "element_kernel_ms": avg_s * 1e3,
+           "apply_ms": e0.elapsed_time(e1) / args.steps, "flops_per_launch": jflops,
+           "achieved_tflops": jflops / avg_s / 1e12, "fp64_peak_tflops": fp64_tflops,
+           "fp64_frac": jflops / avg_s / 1e12 / fp64_tflops, "algorithmic_bytes": alg_bytes,
+           "achieved_gbs": alg_bytes / avg_s / 1e9, "hbm_frac": alg_bytes / avg_s / 1e9 / hbm_peak,
+           "hbm_peak_source": hbm_src}
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
+def run_transfers_form(args):
+    """Restriction, prolongation and the smoother's scatter on the finest level alone,
+    with the factors recomputed per one-slab window so that the context holds the
+    full-size vectors (larger than L2) and little else: achieved GB/s of steps (d) and
+    (f) against their algorithmic bytes, and the command their ncu captures run."""
+    import torch
+    from paper_2407_13997_gb300 import inputs, wrmg
+    torch.cuda.set_device(0)
+    w = workload(args)
+    # no Krylov basis is needed here: the shortest restart keeps the context small
+    ctx = wrmg.Context(w, wrmg.default_options(store_factors=wrmg.WR_RECOMPUTE, recompute_slabs=1,
+                                               gmres_restart=2, eig_steps=1))
+    W = torch.from_numpy(inputs.forcing_shaped_iterate(w)).cuda()
+    ctx.linearise(W, eig=False)
+    L = ctx.fine
+    Df, Dc = ctx.ndofs(L), ctx.ndofs(L - 1)
+    xf = torch.from_numpy(inputs.seeded_vector(3, Df)).cuda()
+    xc = torch.from_numpy(inputs.seeded_vector(4, Dc)).cuda()
+    yc, yf = ctx.vector(L - 1), ctx.vector(L)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps * 1e-3
+
+    torch.cuda.nvtx.range_push("timed")
+    t_r = timed(lambda: ctx.restrict(L, xf, yc))
+    t_p = timed(lambda: ctx.prolong_add(L, xc, yf))
+    torch.cuda.nvtx.range_pop()
+    hbm_peak, hbm_src = measured_peaks()
+    b_r, b_p = 8.0 * (Df + Dc), 8.0 * (Dc + 2 * Df)   # read fine + write coarse; read coarse + update fine
+    out = {"form": "transfers", "workload": w.name, "fine_ndofs": Df, "coarse_ndofs": Dc,
+           "restrict_ms": t_r * 1e3, "restrict_gbs": b_r / t_r / 1e9, "restrict_hbm_frac": b_r / t_r / 1e9 / hbm_peak,
+           "prolong_add_ms": t_p * 1e3, "prolong_add_gbs": b_p / t_p / 1e9,
+           "prolong_add_hbm_frac": b_p / t_p / 1e9 / hbm_peak, "hbm_peak_source": hbm_src,
+           "algorithmic_bytes": {"restrict": b_r, "prolong_add": b_p}}
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_timestepping_form(args):
     """Timestepping comparator on the Chorin problem (R = 10, t in [0, 0.1]): the
     all-at-once WRMG solve against N one-slab solves in sequence (the same
@@ -950,6 +1044,10 @@ def main():
         run_batch_form(args)
     elif args.form == "serve":
         run_serve_form(args)
+    elif args.form == "jacobian":
+        run_jacobian_form(args)
+    elif args.form == "transfers":
+        run_transfers_form(args)
     elif args.form == "smoother":
         run_smoother_form(args)
     elif args.form == "timestepping":

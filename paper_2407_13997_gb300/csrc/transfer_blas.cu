@@ -116,6 +116,139 @@ __global__ void restrict_kernel(LevelGeom gf, LevelGeom gc, FeTables T, const do
   restrict_body(gf, gc, T, xf, xc, idx);
 }
 
+// ---------------------------------------------------------------- tiled tensor-product transfers
+// R = P^T and P applied per field as two 1D passes (x, then y) over a tile held in
+// shared memory.  The equispaced nodes are nested: fine node 2C is coarse node C, and
+// the fine nodes strictly inside a coarse cell (odd local index r) carry the degree-p
+// Lagrange weights pv[r][l] of the cell's p+1 coarse nodes.  So coarse node C takes
+// fine node 2C with weight 1 plus the 2p odd nodes of its (at most two) cells, and a
+// fine node takes either one coarse value (even r) or p+1 weighted ones (odd r).
+// Velocity Dirichlet nodes are zero on both sides, as in the oracle's P.
+constexpr int kTrBX = 32, kTrBY = 16;  // restriction: coarse nodes per tile (x, y)
+constexpr int kTpBX = 64, kTpBY = 32;  // prolongation: fine nodes per tile (x, y)
+
+template <int P>
+__device__ __forceinline__ int tr_cell_lo(int C) { return C == 0 ? 0 : (C - 1) / P; }
+
+// sum over the 1D support of coarse node C of wts(f, C) v(f), f fine (coincident + odd)
+template <int P, int LD, class V>
+__device__ __forceinline__ double tr_restrict_1d(const double (*pv)[LD], int nc, int C, V v) {
+  double acc = v(2 * C);
+  const int c0 = tr_cell_lo<P>(C), c1 = min(C / P, nc - 1);
+  for (int cc = c0; cc <= c1; ++cc) {
+    const int l = C - P * cc;
+#pragma unroll
+    for (int r = 1; r < 2 * P; r += 2) acc = fma(pv[r][l], v(2 * P * cc + r), acc);
+  }
+  return acc;
+}
+
+// value at fine node f of the coarse interpolant of u
+template <int P, int LD, class U>
+__device__ __forceinline__ double tr_prolong_1d(const double (*pv)[LD], int nc, int f, U u) {
+  const int cc = min(f / (2 * P), nc - 1), r = f - 2 * P * cc;
+  if ((r & 1) == 0) return u(P * cc + r / 2);
+  double acc = 0.0;
+#pragma unroll
+  for (int l = 0; l <= P; ++l) acc = fma(pv[r][l], u(P * cc + l), acc);
+  return acc;
+}
+
+template <int P, bool VEL, int LD>
+__device__ void restrict_tile(const double (*pv)[LD], int ncf, const double* __restrict__ xf,
+                              double* __restrict__ xc, double* smem) {
+  const int nc = ncf / 2, nvf = ncf * P + 1, nvc = nc * P + 1;
+  const int X0 = blockIdx.x * kTrBX, Y0 = blockIdx.y * kTrBY;
+  if (X0 >= nvc || Y0 >= nvc) return;
+  const int X1 = min(X0 + kTrBX, nvc), Y1 = min(Y0 + kTrBY, nvc);
+  const int fx0 = 2 * P * tr_cell_lo<P>(X0), fx1 = min(2 * P * (min((X1 - 1) / P, nc - 1) + 1), nvf - 1);
+  const int fy0 = 2 * P * tr_cell_lo<P>(Y0), fy1 = min(2 * P * (min((Y1 - 1) / P, nc - 1) + 1), nvf - 1);
+  const int W = fx1 - fx0 + 1, H = fy1 - fy0 + 1, BW = X1 - X0;
+  double* tf = smem;        // fine tile, H x W
+  double* tt = smem + H * W;  // after the x pass, H x BW
+  for (int e = threadIdx.x; e < H * W; e += blockDim.x) {
+    const int fy = fy0 + e / W, fx = fx0 + e % W;
+    const bool dir = VEL && (fx == 0 || fy == 0 || fx == nvf - 1 || fy == nvf - 1);
+    tf[e] = dir ? 0.0 : xf[(int64_t)fy * nvf + fx];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < H * BW; e += blockDim.x) {
+    const int row = e / BW, X = X0 + e % BW;
+    const double* rowp = tf + row * W - fx0;
+    tt[e] = tr_restrict_1d<P, LD>(pv, nc, X, [&](int f) { return rowp[f]; });
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < (Y1 - Y0) * BW; e += blockDim.x) {
+    const int Y = Y0 + e / BW, xi = e % BW, X = X0 + xi;
+    double v = tr_restrict_1d<P, LD>(pv, nc, Y, [&](int f) { return tt[(f - fy0) * BW + xi]; });
+    if (VEL && (X == 0 || Y == 0 || X == nvc - 1 || Y == nvc - 1)) v = 0.0;
+    xc[(int64_t)Y * nvc + X] = v;
+  }
+}
+
+template <int P, bool VEL, int LD>
+__device__ void prolong_tile(const double (*pv)[LD], int ncf, const double* __restrict__ xc,
+                             double* __restrict__ xf, double* smem) {
+  const int nc = ncf / 2, nvf = ncf * P + 1, nvc = nc * P + 1;
+  const int F0x = blockIdx.x * kTpBX, F0y = blockIdx.y * kTpBY;
+  if (F0x >= nvf || F0y >= nvf) return;
+  const int F1x = min(F0x + kTpBX, nvf), F1y = min(F0y + kTpBY, nvf);
+  const int cx0 = P * min(F0x / (2 * P), nc - 1), cx1 = P * min((F1x - 1) / (2 * P), nc - 1) + P;
+  const int cy0 = P * min(F0y / (2 * P), nc - 1), cy1 = P * min((F1y - 1) / (2 * P), nc - 1) + P;
+  const int W = cx1 - cx0 + 1, H = cy1 - cy0 + 1, FW = F1x - F0x;
+  double* tc = smem;          // coarse tile, H x W
+  double* tt = smem + H * W;  // after the x pass, H x FW
+  for (int e = threadIdx.x; e < H * W; e += blockDim.x) {
+    const int Y = cy0 + e / W, X = cx0 + e % W;
+    const bool dir = VEL && (X == 0 || Y == 0 || X == nvc - 1 || Y == nvc - 1);
+    tc[e] = dir ? 0.0 : xc[(int64_t)Y * nvc + X];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < H * FW; e += blockDim.x) {
+    const int row = e / FW, fx = F0x + e % FW;
+    const double* rowp = tc + row * W - cx0;
+    tt[e] = tr_prolong_1d<P, LD>(pv, nc, fx, [&](int C) { return rowp[C]; });
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < (F1y - F0y) * FW; e += blockDim.x) {
+    const int fy = F0y + e / FW, xi = e % FW, fx = F0x + xi;
+    if (VEL && (fx == 0 || fy == 0 || fx == nvf - 1 || fy == nvf - 1)) continue;  // P row is zero
+    xf[(int64_t)fy * nvf + fx] += tr_prolong_1d<P, LD>(pv, nc, fy, [&](int C) { return tt[(C - cy0) * FW + xi]; });
+  }
+}
+
+// grid: (x tiles, y tiles, temporal blocks x 3 fields); the fields u_x, u_y (degree
+// k+1, Dirichlet) and the pressure (degree k) of one temporal block
+template <int K>
+__global__ void __launch_bounds__(256) restrict_tiled_kernel(LevelGeom gf, LevelGeom gc,
+                                                             const __grid_constant__ FeTables T,
+                                                             const double* __restrict__ xf,
+                                                             double* __restrict__ xc) {
+  extern __shared__ double trs[];
+  const int64_t blk = blockIdx.z / 3;
+  const int field = blockIdx.z % 3;
+  const int64_t nvf2 = (int64_t)gf.nv * gf.nv, nvc2 = (int64_t)gc.nv * gc.nv;
+  const double* src = xf + blk * gf.S;
+  double* dst = xc + blk * gc.S;
+  if (field < 2) restrict_tile<K + 1, true>(T.pv, gf.n, src + field * nvf2, dst + field * nvc2, trs);
+  else restrict_tile<K, false>(T.pp, gf.n, src + 2 * nvf2, dst + 2 * nvc2, trs);
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) prolong_tiled_kernel(LevelGeom gf, LevelGeom gc,
+                                                            const __grid_constant__ FeTables T,
+                                                            const double* __restrict__ xc,
+                                                            double* __restrict__ xf) {
+  extern __shared__ double trs[];
+  const int64_t blk = blockIdx.z / 3;
+  const int field = blockIdx.z % 3;
+  const int64_t nvf2 = (int64_t)gf.nv * gf.nv, nvc2 = (int64_t)gc.nv * gc.nv;
+  const double* src = xc + blk * gc.S;
+  double* dst = xf + blk * gf.S;
+  if (field < 2) prolong_tile<K + 1, true>(T.pv, gf.n, src + field * nvc2, dst + field * nvf2, trs);
+  else prolong_tile<K, false>(T.pp, gf.n, src + 2 * nvc2, dst + 2 * nvf2, trs);
+}
+
 // Pressure weight int chi_j of node g in 1D: h sum over cells containing g of mp1.
 __device__ __forceinline__ double pw1(const FeTables& T, int k, int n, double h, int g) {
   const int lo = g == 0 ? 0 : (g - 1) / k, hi = min(g / k, n - 1);
@@ -581,14 +714,32 @@ inline unsigned grid_for(int64_t n, int threads) {
 
 }  // namespace
 
+// shared memory of the tiled transfers (the velocity field, degree k+1, is the larger)
+static size_t restrict_smem(int k) {
+  const int P = k + 1, W = 2 * kTrBX + 4 * P + 1, H = 2 * kTrBY + 4 * P + 1;
+  return sizeof(double) * (size_t)(H * W + H * kTrBX);
+}
+static size_t prolong_smem(int k) {
+  const int P = k + 1, W = kTpBX / 2 + 2 * P + 1, H = kTpBY / 2 + 2 * P + 1;
+  return sizeof(double) * (size_t)(H * W + H * kTpBX);
+}
+
 void launch_restrict(const LevelGeom& gf, const LevelGeom& gc, const FeTables& T, const double* xf, double* xc,
                      cudaStream_t s) {
-  restrict_kernel<<<(unsigned)((gc.ndofs + 255) / 256), 256, 0, s>>>(gf, gc, T, xf, xc);
+  const dim3 grid((gc.nv + kTrBX - 1) / kTrBX, (gc.nv + kTrBY - 1) / kTrBY, (unsigned)(3 * gf.N * gf.nt));
+  const size_t smem = restrict_smem(gf.k);
+  if (gf.k == 1) restrict_tiled_kernel<1><<<grid, 256, smem, s>>>(gf, gc, T, xf, xc);
+  else if (gf.k == 2) restrict_tiled_kernel<2><<<grid, 256, smem, s>>>(gf, gc, T, xf, xc);
+  else restrict_kernel<<<(unsigned)((gc.ndofs + 255) / 256), 256, 0, s>>>(gf, gc, T, xf, xc);
   WR_LAUNCH_CHECK();
 }
 void launch_prolong_add(const LevelGeom& gf, const LevelGeom& gc, const FeTables& T, const double* xc, double* xf,
                         cudaStream_t s) {
-  prolong_add_kernel<<<(unsigned)((gf.ndofs + 255) / 256), 256, 0, s>>>(gf, gc, T, xc, xf);
+  const dim3 grid((gf.nv + kTpBX - 1) / kTpBX, (gf.nv + kTpBY - 1) / kTpBY, (unsigned)(3 * gf.N * gf.nt));
+  const size_t smem = prolong_smem(gf.k);
+  if (gf.k == 1) prolong_tiled_kernel<1><<<grid, 256, smem, s>>>(gf, gc, T, xc, xf);
+  else if (gf.k == 2) prolong_tiled_kernel<2><<<grid, 256, smem, s>>>(gf, gc, T, xc, xf);
+  else prolong_add_kernel<<<(unsigned)((gf.ndofs + 255) / 256), 256, 0, s>>>(gf, gc, T, xc, xf);
   WR_LAUNCH_CHECK();
 }
 void launch_project_pressure(const LevelGeom& g, const FeTables& T, double* x, cudaStream_t s) {
