@@ -64,6 +64,8 @@ def parse():
                     help="cycle and smoother forms: force a smoother-apply tile 0..4 (default: autotuned)")
     ap.add_argument("--time-parallel", type=int, default=None,
                     help="smoother form: also time the parallel-in-time patch solve (1 = auto, 2 = forced)")
+    ap.add_argument("--grid", default=None,
+                    help="serve form: comma-separated meshes and slab counts to draw from (overrides --full-mix)")
     ap.add_argument("--full-mix", action="store_true",
                     help="serve form: draw n and N from {16, 32, 64} (default {16, 32})")
     ap.add_argument("--form", default="cycle", choices=["cycle", "precision", "batch", "serve", "smoother", "timestepping", "lid", "heat",
@@ -597,7 +599,7 @@ def run_serve_form(args):
     import torch
     from paper_2407_13997_gb300 import inputs, wrmg
     torch.cuda.set_device(0)
-    grid = (16, 32, 64) if args.full_mix else (16, 32)
+    grid = tuple(int(v) for v in args.grid.split(",")) if args.grid else ((16, 32, 64) if args.full_mix else (16, 32))
     reqs = inputs.serving_workloads(args.members or 32, seed=2, ns=grid, slabs=grid)
     rates = [float(r) for r in args.rates.split(",")]
     o32 = wrmg.default_options(precision=wrmg.WR_FP32, newton_rtol=1e-8)

@@ -850,9 +850,11 @@ void dispatch_element(const LevelGeom& g, const FeTables& T, const PhysParams& p
   else if (g.k == 1 && g.q == 1) run_element<1, 1, LIN>(g, T, ph, W, x, y, ye, s);
   else if (g.k == 2 && g.q == 0) run_element<2, 0, LIN>(g, T, ph, W, x, y, ye, s);
   else if (g.k == 2 && g.q == 1) run_element<2, 1, LIN>(g, T, ph, W, x, y, ye, s);
-  else if constexpr (!LIN) {  // the residual of Q2/Q1 with DG(2), DG(3) (their J is launch_jacobian_wq)
+  else if constexpr (!LIN) {  // the residual with DG(2), DG(3) (their J is launch_jacobian_wq)
     if (g.k == 1 && g.q == 2) run_element<1, 2, false>(g, T, ph, W, x, y, ye, s);
     else if (g.k == 1 && g.q == 3) run_element<1, 3, false>(g, T, ph, W, x, y, ye, s);
+    else if (g.k == 2 && g.q == 2) run_element<2, 2, false>(g, T, ph, W, x, y, ye, s);
+    else if (g.k == 2 && g.q == 3) run_element<2, 3, false>(g, T, ph, W, x, y, ye, s);
     else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
   } else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 }
@@ -1322,6 +1324,8 @@ void launch_wq(const LevelGeom& g, const FeTables& T, const double* W, double* W
   else if (g.k == 2 && g.q == 1) run_wq<2, 1>(g, T, W, Wq, s);
   else if (g.k == 1 && g.q == 2) run_wq<1, 2>(g, T, W, Wq, s);
   else if (g.k == 1 && g.q == 3) run_wq<1, 3>(g, T, W, Wq, s);
+  else if (g.k == 2 && g.q == 2) run_wq<2, 2>(g, T, W, Wq, s);
+  else if (g.k == 2 && g.q == 3) run_wq<2, 3>(g, T, W, Wq, s);
   else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 }
 
@@ -1333,6 +1337,8 @@ void launch_jacobian_wq(const LevelGeom& g, const FeTables& T, const PhysParams&
   else if (g.k == 2 && g.q == 1) run_jac<2, 1>(g, T, ph, Wq, x, y, ye, s, ev0, ev1);
   else if (g.k == 1 && g.q == 2) run_jac<1, 2>(g, T, ph, Wq, x, y, ye, s, ev0, ev1);
   else if (g.k == 1 && g.q == 3) run_jac<1, 3>(g, T, ph, Wq, x, y, ye, s, ev0, ev1);
+  else if (g.k == 2 && g.q == 2) run_jac<2, 2>(g, T, ph, Wq, x, y, ye, s, ev0, ev1);
+  else if (g.k == 2 && g.q == 3) run_jac<2, 3>(g, T, ph, Wq, x, y, ye, s, ev0, ev1);
   else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 }
 
@@ -1373,6 +1379,8 @@ void launch_conv_elements(const LevelGeom& g, const FeTables& T, const double* W
     else if (g.k == 2 && g.q == 1) run_conv<2, 1>(g, T, W, c, s);
     else if (g.k == 1 && g.q == 2) run_conv<1, 2>(g, T, W, c, s);
     else if (g.k == 1 && g.q == 3) run_conv<1, 3>(g, T, W, c, s);
+    else if (g.k == 2 && g.q == 2) run_conv<2, 2>(g, T, W, c, s);
+    else if (g.k == 2 && g.q == 3) run_conv<2, 3>(g, T, W, c, s);
     else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
   } else {
     float* c = static_cast<float*>(Ce);

@@ -879,6 +879,11 @@ struct ApplySmem {
   int decision;    // abort decision of the consumers, published by consumer thread 0 before a barrier
   int issued;
   int sidx[C::MS];
+  // the columns of real (non-padding) slots, in order, and where each chunk's start in
+  // that list; dense = 1 when the block has no padding slot
+  int cols[C::MS];
+  int cst[C::NCH + 1];
+  int dense;
   CT rhs[C::NT][C::MS];
   CT y[C::NT][C::MS];
   CT red[C::G][C::MS];
@@ -1047,6 +1052,21 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
                          : (CT)0;
     }
     consumer_sync<NCONS>();
+    // Padding slots (off the domain, Dirichlet, the coarse block's pinned pressure) hold
+    // zero in every block's input vector, so their columns contribute nothing: blocks of
+    // boundary patches skip them (the output rows of padding slots stay zero).
+    if (tid == 0) {
+      int n = 0;
+      for (int k = 0; k < NCH; ++k) {
+        sm.cst[k] = n;
+        for (int c = k * C::CC; c < min(MS, (k + 1) * C::CC); ++c)
+          if (sm.sidx[c] >= 0) sm.cols[n++] = c;
+      }
+      sm.cst[NCH] = n;
+      sm.dense = n == MS;
+    }
+    consumer_sync<NCONS>();
+    const bool dense = sm.dense != 0;
     // (a) gather of slab 0; later slabs come from the register prefetch
     for (int e = tid; e < NT * MS; e += NCONS) {
       const int a = e / MS, s = e % MS, sp = sm.sidx[s];
@@ -1093,7 +1113,18 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
             aborted = true;
             *abort_flag = 1;
           }
-          if (ok && gemv_thread) {
+          if (ok && gemv_thread && !dense) {
+            // the chunk's real columns, split evenly over the G column groups
+            const FT* A = ring + (size_t)slot * C::SLOT_ELEMS;
+            const CT* xk = xv + k * C::CC;
+            const int t0 = sm.cst[k], cnt = sm.cst[k + 1] - t0, sub = (cnt + C::G - 1) / C::G;
+            const int tb = t0 + grp * sub, te = min(t0 + cnt, tb + sub);
+#pragma unroll 4
+            for (int t = tb; t < te; ++t) {
+              const int c = sm.cols[t] - k * C::CC;
+              a0 = fma(widen(A[c * MS + row]), xk[c], a0);
+            }
+          } else if (ok && gemv_thread) {
             const FT* A = ring + (size_t)slot * C::SLOT_ELEMS;
             const int c0 = grp * C::SUB;
             const int ncol = min(C::CC, MS - k * C::CC);
@@ -1871,10 +1902,13 @@ void launch_block_factor(const LevelGeom& g, const FeTables& T, const PhysParams
   } else if (bs.kind == 0 && g.k == 1 && g.q == 0 && precision == WR_BF16) {
     run_factor_warp<__nv_bfloat16>(g, T, ph, bs, Cf, static_cast<__nv_bfloat16*>(factors), st, s);
   } else
-  if (g.k == 1 && (g.q == 2 || g.q == 3)) {  // Q2/Q1 with DG(2), DG(3): FP64
+  if (g.q == 2 || g.q == 3) {  // DG(2), DG(3): FP64
     if (precision != WR_FP64) throw WrError(WR_ERR_ARG, "DG(2) and DG(3) factors are FP64 only");
-    if (g.q == 2) run_factor<1, 2, double, double>(g, T, ph, bs, Cd, static_cast<double*>(factors), st, s);
-    else run_factor<1, 3, double, double>(g, T, ph, bs, Cd, static_cast<double*>(factors), st, s);
+    double* f = static_cast<double*>(factors);
+    if (g.k == 1 && g.q == 2) run_factor<1, 2, double, double>(g, T, ph, bs, Cd, f, st, s);
+    else if (g.k == 1) run_factor<1, 3, double, double>(g, T, ph, bs, Cd, f, st, s);
+    else if (g.q == 2) run_factor<2, 2, double, double>(g, T, ph, bs, Cd, f, st, s);
+    else run_factor<2, 3, double, double>(g, T, ph, bs, Cd, f, st, s);
   } else
   WR_F(1, 0) WR_F(1, 1) WR_F(2, 0) WR_F(2, 1) throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 #undef WR_F
@@ -1905,11 +1939,14 @@ void launch_block_apply(const LevelGeom& g, const FeTables& T, const BlockSet& b
     if (g.q == 0) run_apply<1, 0, double, 4>(g, T, bs, static_cast<const double*>(factors), r, out, err, prev, s);
     else run_apply<1, 1, double, 4>(g, T, bs, static_cast<const double*>(factors), r, out, err, prev, s);
   } else
-  if (g.k == 1 && (g.q == 2 || g.q == 3)) {  // Q2/Q1 with DG(2), DG(3): FP64, CTA tile 0
+  if (g.q == 2 || g.q == 3) {  // DG(2), DG(3): FP64, CTA tile 0
     if (precision != WR_FP64) throw WrError(WR_ERR_ARG, "DG(2) and DG(3) factors are FP64 only");
     const double* f = static_cast<const double*>(factors);
-    if (g.q == 2) run_apply<1, 2, double>(g, T, bs, f, r, out, err, prev, s, bs.kind == 0 ? cp : nullptr);
-    else run_apply<1, 3, double>(g, T, bs, f, r, out, err, prev, s, bs.kind == 0 ? cp : nullptr);
+    const ChunkPlan* c2 = bs.kind == 0 ? cp : nullptr;
+    if (g.k == 1 && g.q == 2) run_apply<1, 2, double>(g, T, bs, f, r, out, err, prev, s, c2);
+    else if (g.k == 1) run_apply<1, 3, double>(g, T, bs, f, r, out, err, prev, s, c2);
+    else if (g.q == 2) run_apply<2, 2, double>(g, T, bs, f, r, out, err, prev, s, c2);
+    else run_apply<2, 3, double>(g, T, bs, f, r, out, err, prev, s, c2);
   } else
   WR_A(1, 0) WR_A(1, 1) WR_A(2, 0) WR_A(2, 1) throw WrError(WR_ERR_ARG, "unsupported (k, q)");
 #undef WR_A
@@ -1924,6 +1961,8 @@ void launch_scatter(const LevelGeom& g, const BlockSet& bs, const double* Yp, do
   else if (g.k == 2 && g.q == 1) scatter_kernel<2, 1><<<blocks, threads, 0, s>>>(g, Yp, y, wt);
   else if (g.k == 1 && g.q == 2) scatter_kernel<1, 2><<<blocks, threads, 0, s>>>(g, Yp, y, wt);
   else if (g.k == 1 && g.q == 3) scatter_kernel<1, 3><<<blocks, threads, 0, s>>>(g, Yp, y, wt);
+  else if (g.k == 2 && g.q == 2) scatter_kernel<2, 2><<<blocks, threads, 0, s>>>(g, Yp, y, wt);
+  else if (g.k == 2 && g.q == 3) scatter_kernel<2, 3><<<blocks, threads, 0, s>>>(g, Yp, y, wt);
   else throw WrError(WR_ERR_ARG, "unsupported (k, q)");
   WR_LAUNCH_CHECK();
 }

@@ -237,6 +237,12 @@ struct wr_ctx {
   // 1e-14 |H[j][j]| + 1e-300).
   void mgs_dev(int64_t n, double* H, int m, int j, bool breakdown) {
     double* w = V[j + 1];
+    if (n <= mgs_small_limit()) {  // short vectors: the whole column in one launch
+      KrylovBasis vb{};
+      for (int i = 0; i <= j; ++i) vb.p[i] = V[i];
+      krylov_mgs_small(n, vb, j, w, H, m, j, breakdown, s);
+      return;
+    }
     for (int i = 0; i <= j; ++i)
       krylov_axpy_dot(n, i ? H + (i - 1) * m + j : nullptr, i ? V[i - 1] : nullptr, w, V[i], partials, kcnt,
                       H + i * m + j, s);
@@ -855,8 +861,7 @@ static int create_impl(wr_ctx* cptr, const wr_problem* p, const wr_options* o, v
   int rc = guarded(c, [&]() -> int {
     const bool heat = p->kind == WR_HEAT || p->kind == WR_HEAT_EIGEN;
     need(p->k == 1 || p->k == 2 || (heat && p->k == 3), "k must be 1 or 2 (1, 2 or 3 for the heat equation)");
-    need(heat ? (p->q >= 0 && p->q <= 3) : (p->q == 0 || p->q == 1 || (p->k == 1 && (p->q == 2 || p->q == 3))),
-         "q must be 0 or 1 (0..3 for Q2/Q1 and for the heat equation)");
+    need(p->q >= 0 && p->q <= 3, "q must be 0..3");
     if (heat) {
       need(p->n_coarse == 1 || p->n_coarse == 2, "the heat equation coarsens to 1x1 or 2x2");
       need(heat_block_fits(p->k, p->q, p->n_coarse),

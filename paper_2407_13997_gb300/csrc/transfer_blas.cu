@@ -433,6 +433,45 @@ __global__ void axpy_dot_kernel(int64_t n, const double* __restrict__ h, const d
   }
 }
 
+// A whole modified Gram-Schmidt column in one launch, for short vectors (one CTA):
+// for i = 0..j in order, H[i m + col] = <w, v_i> and w -= H[i m + col] v_i; then
+// H[(j+1) m + col] = ||w|| and w /= ||w|| (mode 1: unless 0; mode 2: w = 0 where
+// ||w|| <= rel |H[j m + col]| + abs, the Arnoldi breakdown).  Every thread owns the same
+// strided elements in every pass, so w needs no barrier; the sums are fixed trees.
+constexpr int kMgsThreads = 1024;
+__device__ __forceinline__ double block_sum_fixed(double a, double* s) {
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int st = kMgsThreads / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
+    __syncthreads();
+  }
+  const double r = s[0];
+  __syncthreads();
+  return r;
+}
+__global__ void __launch_bounds__(kMgsThreads)
+mgs_small_kernel(int64_t n, KrylovBasis V, int j, double* __restrict__ w, double* __restrict__ H, int m, int col,
+                 int mode, double rel, double abs_) {
+  __shared__ double s[kMgsThreads];
+  for (int i = 0; i <= j; ++i) {
+    const double* __restrict__ v = V.p[i];
+    double acc = 0.0;
+    for (int64_t t = threadIdx.x; t < n; t += kMgsThreads) acc = fma(w[t], v[t], acc);
+    const double h = block_sum_fixed(acc, s);
+    if (threadIdx.x == 0) H[i * m + col] = h;
+    for (int64_t t = threadIdx.x; t < n; t += kMgsThreads) w[t] = fma(-h, v[t], w[t]);
+  }
+  double acc = 0.0;
+  for (int64_t t = threadIdx.x; t < n; t += kMgsThreads) acc = fma(w[t], w[t], acc);
+  const double hn = sqrt(block_sum_fixed(acc, s));
+  double inv;
+  if (mode == 1) inv = hn != 0.0 ? 1.0 / hn : 1.0;
+  else inv = hn > rel * fabs(H[j * m + col]) + abs_ ? 1.0 / hn : 0.0;
+  if (threadIdx.x == 0) H[(j + 1) * m + col] = hn;
+  for (int64_t t = threadIdx.x; t < n; t += kMgsThreads) w[t] *= inv;
+}
+
 // y = a x with the scalar a in device memory (y may be x)
 __global__ void scale_dev_kernel(int64_t n, const double* __restrict__ a, const double* x, double* y) {
   const double av = *a;
@@ -790,6 +829,12 @@ void krylov_axpy_norm(int64_t n, const double* h, const double* x, double* w, do
                       double* out, double* inv, const double* diag, double rel, double abs_, cudaStream_t s) {
   axpy_dot_kernel<<<krylov_blocks(n), kDotThreads, 0, s>>>(n, h, x, w, w, partials, count, out, diag ? 2 : 1, inv,
                                                           diag, rel, abs_);
+  WR_LAUNCH_CHECK();
+}
+int64_t mgs_small_limit() { return 16384; }
+void krylov_mgs_small(int64_t n, const KrylovBasis& V, int j, double* w, double* H, int m, int col, bool breakdown,
+                      cudaStream_t s) {
+  mgs_small_kernel<<<1, kMgsThreads, 0, s>>>(n, V, j, w, H, m, col, breakdown ? 2 : 1, 1e-14, 1e-300);
   WR_LAUNCH_CHECK();
 }
 void vec_scale_dev(int64_t n, const double* a, const double* x, double* y, cudaStream_t s) {

@@ -285,6 +285,12 @@ void krylov_axpy_dot(int64_t n, const double* h, const double* x, double* w, con
 void krylov_axpy_norm(int64_t n, const double* h, const double* x, double* w, double* partials, unsigned* count,
                       double* out, double* inv, const double* diag, double rel, double abs_, cudaStream_t s);
 void vec_scale_dev(int64_t n, const double* a, const double* x, double* y, cudaStream_t s);  // y = (*a) x
+// the whole MGS column j (w against V.p[0..j], H column col, row stride m, then the
+// normalisation; breakdown as in krylov_axpy_norm) in one single-CTA launch, for
+// n <= mgs_small_limit()
+int64_t mgs_small_limit();
+void krylov_mgs_small(int64_t n, const KrylovBasis& V, int j, double* w, double* H, int m, int col, bool breakdown,
+                      cudaStream_t s);
 // rotations of FGMRES column j (one thread); status[0] = the new residual estimate g[j+1]
 void krylov_givens(double* H, double* cs, double* sn, double* g, int j, int m, double* status, cudaStream_t s);
 // y = R^{-1} g (leading jend x jend triangle of H), then x += sum_l y_l z_l

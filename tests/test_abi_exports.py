@@ -93,8 +93,8 @@ def test_heat_degrees_and_coarse_mesh_checks_on_the_host(libpath):
     """The heat equation takes Q_k x DG(q) for k = 1..3, q = 0..3 (Sec. 5); its stored
     factors are one (q+1)(2k-1)^2 block per patch and slab, FP64.  The k = q = 3 coarse
     block of a 2x2 mesh (196 x 196) does not fit the direct solve and is refused; the 1x1
-    coarse mesh is taken instead.  Navier-Stokes takes DG(2) and DG(3) with Q2/Q1 and
-    FP64 factors only; Q3/Q2 stays at q <= 1."""
+    coarse mesh is taken instead.  Navier-Stokes takes DG(2) and DG(3) with FP64 factors
+    only."""
     from paper_2407_13997_gb300 import inputs, wrmg
     for k in (1, 2, 3):
         for q in (0, 1, 2, 3):
@@ -114,5 +114,9 @@ def test_heat_degrees_and_coarse_mesh_checks_on_the_host(libpath):
             wrmg.estimate_bytes(ns, wrmg.default_options(precision=wrmg.WR_FP32))
     ns3 = inputs.fourier_small(n=8, k=2, q=0, N=3)
     ns3.q = 2
+    assert wrmg.estimate_bytes(ns3) > 0
+    with pytest.raises(wrmg.WrmgError):
+        wrmg.estimate_bytes(ns3, wrmg.default_options(precision=wrmg.WR_BF16))
+    ns3.q = 4
     with pytest.raises(wrmg.WrmgError):
         wrmg.estimate_bytes(ns3)

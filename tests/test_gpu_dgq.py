@@ -1,6 +1,6 @@
 """Navier-Stokes with the higher temporal orders DG(2) and DG(3) (Sec. 2's DG(q) in
-time; the paper's higher-order experiments), Taylor-Hood Q2/Q1, on the GPU path
-through the C ABI against the FP64 oracle.
+time; the paper's higher-order experiments), Taylor-Hood Q2/Q1 and Q3/Q2, on the GPU
+path through the C ABI against the FP64 oracle.
 
 The slab blocks are (q+1) x (q+1) block matrices of the patch's spatial blocks,
 factored as a block LDU (left-looking, pivoting inside the diagonal blocks) and
@@ -24,7 +24,8 @@ from tests.oracle_problems import oracle_problem
 from tests.test_gpu_parity import Setup, cuda, rel
 
 CASES = [inputs.fourier_small(n=4, k=1, q=2, N=2, nu=0.02), inputs.fourier_small(n=4, k=1, q=3, N=2, nu=0.02),
-         inputs.fourier_small(n=8, k=1, q=2, N=3, nu=0.01)]
+         inputs.fourier_small(n=8, k=1, q=2, N=3, nu=0.01), inputs.fourier_small(n=4, k=2, q=2, N=2, nu=0.02),
+         inputs.fourier_small(n=4, k=2, q=3, N=2, nu=0.02)]
 IDS = [w.name for w in CASES]
 
 
@@ -96,7 +97,8 @@ def test_eigen_estimates_chebyshev_and_vcycle_match_oracle(setup):
 
 
 @pytest.mark.parametrize("w", [inputs.fourier_small(n=4, k=1, q=2, N=3, nu=0.02),
-                               inputs.poly_small(n=4, k=1, q=3, N=2)], ids=["fourier_dg2", "poly_dg3"])
+                               inputs.poly_small(n=4, k=1, q=3, N=2), inputs.poly_small(n=4, k=2, q=2, N=2)],
+                         ids=["fourier_q2q1_dg2", "poly_q2q1_dg3", "poly_q3q2_dg2"])
 def test_full_solve_matches_oracle(w):
     # the polynomial solution is solved to 1e-12 so that its exactness shows
     rtol = 1e-12 if w.kind == inputs.KIND_POLY else 1e-8
