@@ -597,8 +597,11 @@ __device__ void gemm_into_b(const CT* A, CT* B, CT sign) {
   __syncthreads();
 }
 
+// Two CTAs per SM for the reduced-precision Q3/Q2 blocks (64 registers; the register-
+// tiled inversion is latency-bound, so a second CTA hides its barriers); FP64 Q3/Q2
+// needs 183 KB of shared memory and runs one.
 template <int K, int Q, typename CT, typename ST, int NTH, int NPGX>
-__global__ void __launch_bounds__(NTH, 1)
+__global__ void __launch_bounds__(NTH, (sizeof(CT) == 4 && K == 2) ? 2 : 1)
 block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const CT* __restrict__ Ce,
                     ST* __restrict__ factors, int* __restrict__ status) {
   using pd = PD<K, NPGX>;
