@@ -452,68 +452,70 @@ __device__ bool gauss_jordan_reg(CT* A) {
   for (int i = tid; i < MS; i += NTH) used[i] = 0;
   if (tid == 0) zero_pivot = 0;
   __syncthreads();
+  // pivots in groups of 32 so that the register column of pivot p (p / 32) is a constant
+#pragma unroll
+  for (int vp = 0; vp < CV; ++vp) {
 #pragma unroll 1
-  for (int p = 0; p < MS; ++p) {
-    const int bsel = p & 1;
-    // column p to shared memory (owned by the lanes with lane == p % 32)
-    if (lane == (p & 31)) {
-      const int vp = p >> 5;
+    for (int p = 32 * vp; p < MS && p < 32 * vp + 32; ++p) {
+      const int bsel = p & 1;
+      // column p to shared memory (owned by the lanes with lane == p % 32), then set to
+      // -0 there: fma(-f, inv, -0) below forms the new column p, -f inv, exactly
+      if (lane == (p & 31)) {
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+          const int i = ty + TY * u;
+          if (i < MS) colb[bsel][i] = a[u][vp];
+          a[u][vp] = CT(-0.0);
+        }
+      }
+      __syncthreads();
+      // every warp finds the same pivot row
+      CT best = CT(-1);
+      int bi = MS;
+      for (int i = lane; i < MS; i += 32) {
+        const CT v = used[i] ? CT(-1) : fabs(colb[bsel][i]);
+        if (v > best) { best = v; bi = i; }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const CT ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      const int r = bi;
+      const CT inv = CT(1) / colb[bsel][r];
+      // the owner warp of row r publishes it scaled by the inverse pivot
+      if (ty == r % TY) {
+        const int ur = r / TY;
+#pragma unroll
+        for (int v = 0; v < CV; ++v) {
+          CT val = CT(0);
+#pragma unroll
+          for (int u = 0; u < RU; ++u) val = (u == ur) ? a[u][v] : val;
+          const int j = lane + 32 * v;
+          if (j < MS) rowb[bsel][j] = (j == p) ? inv : val * inv;
+        }
+      }
+      __syncthreads();
 #pragma unroll
       for (int u = 0; u < RU; ++u) {
-        CT val = CT(0);
-#pragma unroll
-        for (int v = 0; v < CV; ++v) val = (v == vp) ? a[u][v] : val;
         const int i = ty + TY * u;
-        if (i < MS) colb[bsel][i] = val;
+        const CT f = i < MS ? colb[bsel][i] : CT(0);
+        const bool pivot_row = i == r;
+#pragma unroll
+        for (int v = 0; v < CV; ++v) {
+          const int j = lane + 32 * v;
+          const CT rj = j < MS ? rowb[bsel][j] : CT(0);
+          a[u][v] = pivot_row ? rj : fma(-f, rj, a[u][v]);
+        }
       }
-    }
-    __syncthreads();
-    // every warp finds the same pivot row
-    CT best = CT(-1);
-    int bi = MS;
-    for (int i = lane; i < MS; i += 32) {
-      const CT v = used[i] ? CT(-1) : fabs(colb[bsel][i]);
-      if (v > best) { best = v; bi = i; }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const CT ob = __shfl_xor_sync(0xffffffffu, best, off);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-    }
-    const int r = bi;
-    const CT inv = CT(1) / colb[bsel][r];
-    // the owner warp of row r publishes it scaled by the inverse pivot
-    if (ty == r % TY) {
-      const int ur = r / TY;
-#pragma unroll
-      for (int v = 0; v < CV; ++v) {
-        CT val = CT(0);
-#pragma unroll
-        for (int u = 0; u < RU; ++u) val = (u == ur) ? a[u][v] : val;
-        const int j = lane + 32 * v;
-        if (j < MS) rowb[bsel][j] = (j == p) ? inv : val * inv;
+      // bookkeeping after the second barrier, so that no warp's search of this pivot sees it
+      if (tid == 0) {
+        used[r] = 1;
+        prow[p] = r;
+        pstep[r] = p;
+        if (!(best > CT(0))) zero_pivot = 1;
       }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < RU; ++u) {
-      const int i = ty + TY * u;
-      const CT f = i < MS ? colb[bsel][i] : CT(0);
-#pragma unroll
-      for (int v = 0; v < CV; ++v) {
-        const int j = lane + 32 * v;
-        const CT rj = j < MS ? rowb[bsel][j] : CT(0);
-        const CT nv = (i == r) ? rj : ((j == p) ? -f * rj : fma(-f, rj, a[u][v]));
-        a[u][v] = nv;
-      }
-    }
-    // bookkeeping after the second barrier, so that no warp's search of this pivot sees it
-    if (tid == 0) {
-      used[r] = 1;
-      prow[p] = r;
-      pstep[r] = p;
-      if (!(best > CT(0))) zero_pivot = 1;
     }
   }
   __syncthreads();
