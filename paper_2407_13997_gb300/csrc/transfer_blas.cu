@@ -438,22 +438,29 @@ __global__ void axpy_dot_kernel(int64_t n, const double* __restrict__ h, const d
 // H[(j+1) m + col] = ||w|| and w /= ||w|| (mode 1: unless 0; mode 2: w = 0 where
 // ||w|| <= rel |H[j m + col]| + abs, the Arnoldi breakdown).  Every thread owns the same
 // strided elements in every pass, so w needs no barrier; the sums are fixed trees.
-constexpr int kMgsThreads = 1024;
+constexpr int kMgsThreads = 256;
+// Sum over the CTA in a fixed order: a butterfly in each warp (lane 0's result), then
+// one warp over the warps' sums; every thread gets the total.
 __device__ __forceinline__ double block_sum_fixed(double a, double* s) {
-  s[threadIdx.x] = a;
+  constexpr int NW = kMgsThreads / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+  if (lane == 0) s[wid] = a;
   __syncthreads();
-  for (int st = kMgsThreads / 2; st > 0; st >>= 1) {
-    if (threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
-    __syncthreads();
+  if (wid == 0) {
+    double b = lane < NW ? s[lane] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) b += __shfl_xor_sync(0xffffffffu, b, off);
+    if (lane == 0) s[NW] = b;
   }
-  const double r = s[0];
   __syncthreads();
-  return r;
+  return s[NW];
 }
 __global__ void __launch_bounds__(kMgsThreads)
 mgs_small_kernel(int64_t n, KrylovBasis V, int j, double* __restrict__ w, double* __restrict__ H, int m, int col,
                  int mode, double rel, double abs_) {
-  __shared__ double s[kMgsThreads];
+  __shared__ double s[kMgsThreads / 32 + 1];
   for (int i = 0; i <= j; ++i) {
     const double* __restrict__ v = V.p[i];
     double acc = 0.0;
@@ -831,7 +838,7 @@ void krylov_axpy_norm(int64_t n, const double* h, const double* x, double* w, do
                                                           diag, rel, abs_);
   WR_LAUNCH_CHECK();
 }
-int64_t mgs_small_limit() { return 16384; }
+int64_t mgs_small_limit() { return 8192; }
 void krylov_mgs_small(int64_t n, const KrylovBasis& V, int j, double* w, double* H, int m, int col, bool breakdown,
                       cudaStream_t s) {
   mgs_small_kernel<<<1, kMgsThreads, 0, s>>>(n, V, j, w, H, m, col, breakdown ? 2 : 1, 1e-14, 1e-300);
