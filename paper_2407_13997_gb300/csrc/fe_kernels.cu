@@ -1037,124 +1037,146 @@ wq_kernel(LevelGeom g, const __grid_constant__ FeTables T, const double* __restr
   }
 }
 
-// One warp: the element contribution of J(W) x on (cell, slab).
+// Elements per warp of jac_kernel (cells cell0 .. cell0+E-1 of one slab).  Q3/Q2 fills
+// the warp's lanes with one element's stage items (25 Gauss points, 80 to 200
+// interpolation items).  Q2/Q1 has 16 Gauss points and 8 to 72 items per stage: DG(0)
+// and DG(1) take four elements (the shared-memory footprint, 2.3 or 4 KB per element,
+// still leaves 24 or 12 warps per SM), DG(2) and DG(3) two, so that their larger
+// footprint and register count leave 8 to 12 warps per SM.
 template <int K, int Q>
+struct JacE {
+  static constexpr int E = K == 2 ? 1 : (Q <= 1 ? 4 : 2);
+};
+
+// One warp: the element contributions of J(W) x on E cells (cell0 + e) of one slab.
+// Every stage loop runs over the items of all E elements, so that short stages fill
+// the warp; elements beyond the mesh are skipped.
+template <int K, int Q, int E>
 __device__ __forceinline__ void jac_body(const LevelGeom& g, const JacTab<K, Q>& tb, const double* __restrict__ Wq,
-                                         const double* __restrict__ x, double* __restrict__ ye, JacSmem<K, Q>& s,
-                                         int cell, int slab) {
+                                         const double* __restrict__ x, double* __restrict__ ye, JacSmem<K, Q>* s,
+                                         int cell0, int slab) {
   using d = D<K, Q>;
   using SM = JacSmem<K, Q>;
   constexpr int NF = SM::NF, NT = d::NT, NVL = d::NVL, NPL = d::NPL, NQ = d::NQ, NQ2 = d::NQ2;
   const int lane = threadIdx.x & 31;
-  const int CI = cell % g.n, CJ = cell / g.n;
-  const int S = g.S;
+  const int S = g.S, nc = g.ncells();
+  const int nin = E == 1 ? 1 : min(E, nc - cell0);  // elements of this warp inside the mesh
+  constexpr int ne = E;  // every stage runs all E elements; those beyond the mesh see zero input
   const int64_t nv2 = (int64_t)g.nv * g.nv;
 
   // ---- gather x (Dirichlet velocity rows of J are the identity, set by the assembly)
-  for (int it = lane; it < 2 * d::NVE; it += 32) {
-    const int c = it / d::NVE, l = it % d::NVE;
+  for (int it = lane; it < ne * 2 * d::NVE; it += 32) {
+    const int e = E == 1 ? 0 : it / (2 * d::NVE), r = E == 1 ? it : it % (2 * d::NVE), c = r / d::NVE, l = r % d::NVE;
+    const int cell = min(cell0 + e, nc - 1), CI = cell % g.n, CJ = cell / g.n;
     const int gx = CI * (K + 1) + l % NVL, gy = CJ * (K + 1) + l / NVL;
     const int64_t sp = c * nv2 + (int64_t)gy * g.nv + gx;
-    const bool dir = vel_dirichlet(g, gx, gy);
+    const bool dir = vel_dirichlet(g, gx, gy) || e >= nin;
 #pragma unroll
-    for (int b = 0; b < NT; ++b) s.vn[c * NT + b][l] = dir ? 0.0 : x[((int64_t)slab * NT + b) * S + sp];
-    s.mn[c][l] = (slab > 0 && !dir) ? x[((int64_t)(slab - 1) * NT + (NT - 1)) * S + sp] : 0.0;
+    for (int b = 0; b < NT; ++b) s[e].vn[c * NT + b][l] = dir ? 0.0 : x[((int64_t)slab * NT + b) * S + sp];
+    s[e].mn[c][l] = (slab > 0 && !dir) ? x[((int64_t)(slab - 1) * NT + (NT - 1)) * S + sp] : 0.0;
   }
-  for (int it = lane; it < NT * d::NPE; it += 32) {
-    const int b = it / d::NPE, l = it % d::NPE;
+  for (int it = lane; it < ne * NT * d::NPE; it += 32) {
+    const int e = E == 1 ? 0 : it / (NT * d::NPE), r = E == 1 ? it : it % (NT * d::NPE), b = r / d::NPE, l = r % d::NPE;
+    const int cell = min(cell0 + e, nc - 1), CI = cell % g.n, CJ = cell / g.n;
     const int px = CI * K + l % NPL, py = CJ * K + l / NPL;
-    s.pn[b][l] = x[((int64_t)slab * NT + b) * S + 2 * nv2 + (int64_t)py * g.np + px];
+    s[e].pn[b][l] = e < nin ? x[((int64_t)slab * NT + b) * S + 2 * nv2 + (int64_t)py * g.np + px] : 0.0;
   }
   __syncwarp();
 
   // ---- interpolation to the Gauss points, x pass
-  for (int it = lane; it < NF * NVL * NQ; it += 32) {
-    const int f = it / (NVL * NQ), r = it % (NVL * NQ), j = r / NQ, qx = r % NQ;
+  for (int it = lane; it < ne * NF * NVL * NQ; it += 32) {
+    const int e = E == 1 ? 0 : it / (NF * NVL * NQ), r0 = E == 1 ? it : it % (NF * NVL * NQ);
+    const int f = r0 / (NVL * NQ), r = r0 % (NVL * NQ), j = r / NQ, qx = r % NQ;
     double v = 0.0, dv = 0.0;
 #pragma unroll
     for (int i = 0; i < NVL; ++i) {
-      v = fma(tb.Bv[qx][i], s.vn[f][j * NVL + i], v);
-      dv = fma(tb.Dv[qx][i], s.vn[f][j * NVL + i], dv);
+      v = fma(tb.Bv[qx][i], s[e].vn[f][j * NVL + i], v);
+      dv = fma(tb.Dv[qx][i], s[e].vn[f][j * NVL + i], dv);
     }
-    s.t1[f][0][j][qx] = v;
-    s.t1[f][1][j][qx] = dv;
+    s[e].t1[f][0][j][qx] = v;
+    s[e].t1[f][1][j][qx] = dv;
   }
-  for (int it = lane; it < 2 * NVL * NQ; it += 32) {
-    const int c = it / (NVL * NQ), r = it % (NVL * NQ), j = r / NQ, qx = r % NQ;
+  for (int it = lane; it < ne * 2 * NVL * NQ; it += 32) {
+    const int e = E == 1 ? 0 : it / (2 * NVL * NQ), r0 = E == 1 ? it : it % (2 * NVL * NQ);
+    const int c = r0 / (NVL * NQ), r = r0 % (NVL * NQ), j = r / NQ, qx = r % NQ;
     double v = 0.0;
 #pragma unroll
-    for (int i = 0; i < NVL; ++i) v = fma(tb.Bv[qx][i], s.mn[c][j * NVL + i], v);
-    s.tm[c][j][qx] = v;
+    for (int i = 0; i < NVL; ++i) v = fma(tb.Bv[qx][i], s[e].mn[c][j * NVL + i], v);
+    s[e].tm[c][j][qx] = v;
   }
-  for (int it = lane; it < NT * NPL * NQ; it += 32) {
-    const int b = it / (NPL * NQ), r = it % (NPL * NQ), j = r / NQ, qx = r % NQ;
+  for (int it = lane; it < ne * NT * NPL * NQ; it += 32) {
+    const int e = E == 1 ? 0 : it / (NT * NPL * NQ), r0 = E == 1 ? it : it % (NT * NPL * NQ);
+    const int b = r0 / (NPL * NQ), r = r0 % (NPL * NQ), j = r / NQ, qx = r % NQ;
     double v = 0.0;
 #pragma unroll
-    for (int i = 0; i < NPL; ++i) v = fma(tb.Bp[qx][i], s.pn[b][j * NPL + i], v);
-    s.tp[b][j][qx] = v;
+    for (int i = 0; i < NPL; ++i) v = fma(tb.Bp[qx][i], s[e].pn[b][j * NPL + i], v);
+    s[e].tp[b][j][qx] = v;
   }
   __syncwarp();
   // y pass
-  for (int it = lane; it < NF * NQ2; it += 32) {
-    const int f = it / NQ2, q = it % NQ2, qy = q / NQ, qx = q % NQ;
+  for (int it = lane; it < ne * NF * NQ2; it += 32) {
+    const int e = E == 1 ? 0 : it / (NF * NQ2), r0 = E == 1 ? it : it % (NF * NQ2);
+    const int f = r0 / NQ2, q = r0 % NQ2, qy = q / NQ, qx = q % NQ;
     double v = 0.0, vx = 0.0, vy = 0.0;
 #pragma unroll
     for (int j = 0; j < NVL; ++j) {
-      v = fma(tb.Bv[qy][j], s.t1[f][0][j][qx], v);
-      vx = fma(tb.Bv[qy][j], s.t1[f][1][j][qx], vx);
-      vy = fma(tb.Dv[qy][j], s.t1[f][0][j][qx], vy);
+      v = fma(tb.Bv[qy][j], s[e].t1[f][0][j][qx], v);
+      vx = fma(tb.Bv[qy][j], s[e].t1[f][1][j][qx], vx);
+      vy = fma(tb.Dv[qy][j], s[e].t1[f][0][j][qx], vy);
     }
-    s.vq[f][0][q] = v;
-    s.vq[f][1][q] = vx;
-    s.vq[f][2][q] = vy;
+    s[e].vq[f][0][q] = v;
+    s[e].vq[f][1][q] = vx;
+    s[e].vq[f][2][q] = vy;
   }
-  for (int it = lane; it < 2 * NQ2; it += 32) {
-    const int c = it / NQ2, q = it % NQ2, qy = q / NQ, qx = q % NQ;
+  for (int it = lane; it < ne * 2 * NQ2; it += 32) {
+    const int e = E == 1 ? 0 : it / (2 * NQ2), r0 = E == 1 ? it : it % (2 * NQ2), c = r0 / NQ2, q = r0 % NQ2, qy = q / NQ, qx = q % NQ;
     double v = 0.0;
 #pragma unroll
-    for (int j = 0; j < NVL; ++j) v = fma(tb.Bv[qy][j], s.tm[c][j][qx], v);
-    s.mq[c][q] = v;
+    for (int j = 0; j < NVL; ++j) v = fma(tb.Bv[qy][j], s[e].tm[c][j][qx], v);
+    s[e].mq[c][q] = v;
   }
-  for (int it = lane; it < NT * NQ2; it += 32) {
-    const int b = it / NQ2, q = it % NQ2, qy = q / NQ, qx = q % NQ;
+  for (int it = lane; it < ne * NT * NQ2; it += 32) {
+    const int e = E == 1 ? 0 : it / (NT * NQ2), r0 = E == 1 ? it : it % (NT * NQ2), b = r0 / NQ2, q = r0 % NQ2, qy = q / NQ, qx = q % NQ;
     double v = 0.0;
 #pragma unroll
-    for (int j = 0; j < NPL; ++j) v = fma(tb.Bp[qy][j], s.tp[b][j][qx], v);
-    s.pq[b][q] = v;
+    for (int j = 0; j < NPL; ++j) v = fma(tb.Bp[qy][j], s[e].tp[b][j][qx], v);
+    s[e].pq[b][q] = v;
   }
   __syncwarp();
 
   // ---- pointwise coefficients (each lane reads and overwrites its own Gauss point)
-  const double* __restrict__ wq = Wq + ((int64_t)slab * g.ncells() + cell) * (NF * 3 * NQ2);
-  for (int q = lane; q < NQ2; q += 32) {
+  for (int it = lane; it < ne * NQ2; it += 32) {
+    const int e = E == 1 ? 0 : it / NQ2, q = E == 1 ? it : it % NQ2;
+    SM& se = s[e];
+    const double* __restrict__ wq = Wq + ((int64_t)slab * nc + min(cell0 + e, nc - 1)) * (NF * 3 * NQ2) + q;
     double Wv[NF][3], X[NF][3], p[NT], dv[NT], xm[2];
 #pragma unroll
     for (int f = 0; f < NF; ++f)
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        Wv[f][k] = wq[(f * 3 + k) * NQ2 + q];
-        X[f][k] = s.vq[f][k][q];
+        Wv[f][k] = wq[(f * 3 + k) * NQ2];
+        X[f][k] = se.vq[f][k][q];
       }
 #pragma unroll
     for (int b = 0; b < NT; ++b) {
-      p[b] = s.pq[b][q];
+      p[b] = se.pq[b][q];
       dv[b] = X[0 * NT + b][1] + X[1 * NT + b][2];
     }
-    xm[0] = s.mq[0][q];
-    xm[1] = s.mq[1][q];
+    xm[0] = se.mq[0][q];
+    xm[1] = se.mq[1][q];
     // Newton convection (W_b . grad) x_{c,e} + (x_b . grad) W_{c,e}, per (b, e, c)
     double P[NT][NT][2];
 #pragma unroll
     for (int b = 0; b < NT; ++b)
 #pragma unroll
-      for (int e = 0; e < NT; ++e)
+      for (int ee = 0; ee < NT; ++ee)
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          const int fe = c * NT + e;
+          const int fe = c * NT + ee;
           double t = Wv[0 * NT + b][0] * X[fe][1];
           t = fma(Wv[1 * NT + b][0], X[fe][2], t);
           t = fma(X[0 * NT + b][0], Wv[fe][1], t);
-          P[b][e][c] = fma(X[1 * NT + b][0], Wv[fe][2], t);
+          P[b][ee][c] = fma(X[1 * NT + b][0], Wv[fe][2], t);
         }
 #pragma unroll
     for (int a = 0; a < NT; ++a) {
@@ -1164,7 +1186,7 @@ __device__ __forceinline__ void jac_body(const LevelGeom& g, const JacTab<K, Q>&
         pw = fma(tb.WtP[a][b], p[b], pw);
         dw = fma(tb.WtP[a][b], dv[b], dw);
       }
-      s.pq[a][q] = dw;
+      se.pq[a][q] = dw;
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         double val = -tb.tauH[a] * xm[c];
@@ -1175,59 +1197,63 @@ __device__ __forceinline__ void jac_body(const LevelGeom& g, const JacTab<K, Q>&
           gx = fma(tb.WtN[a][b], X[c * NT + b][1], gx);
           gy = fma(tb.WtN[a][b], X[c * NT + b][2], gy);
 #pragma unroll
-          for (int e = 0; e < NT; ++e) val = fma(tb.T3H[a][b][e], P[b][e][c], val);
+          for (int ee = 0; ee < NT; ++ee) val = fma(tb.T3H[a][b][ee], P[b][ee][c], val);
         }
-        s.vq[c * NT + a][0][q] = val;
-        s.vq[c * NT + a][1][q] = gx;
-        s.vq[c * NT + a][2][q] = gy;
+        se.vq[c * NT + a][0][q] = val;
+        se.vq[c * NT + a][1][q] = gx;
+        se.vq[c * NT + a][2][q] = gy;
       }
     }
   }
   __syncwarp();
 
   // ---- test contraction, y pass (weighted test tables)
-  for (int it = lane; it < NF * NVL * NQ; it += 32) {
-    const int f = it / (NVL * NQ), r = it % (NVL * NQ), j = r / NQ, qx = r % NQ;
+  for (int it = lane; it < ne * NF * NVL * NQ; it += 32) {
+    const int e = E == 1 ? 0 : it / (NF * NVL * NQ), r0 = E == 1 ? it : it % (NF * NVL * NQ);
+    const int f = r0 / (NVL * NQ), r = r0 % (NVL * NQ), j = r / NQ, qx = r % NQ;
     double a1 = 0.0, a2 = 0.0;
 #pragma unroll
     for (int qy = 0; qy < NQ; ++qy) {
       const int q = qy * NQ + qx;
-      a1 = fma(tb.BvW[qy][j], s.vq[f][0][q], a1);
-      a1 = fma(tb.DvW[qy][j], s.vq[f][2][q], a1);
-      a2 = fma(tb.BvW[qy][j], s.vq[f][1][q], a2);
+      a1 = fma(tb.BvW[qy][j], s[e].vq[f][0][q], a1);
+      a1 = fma(tb.DvW[qy][j], s[e].vq[f][2][q], a1);
+      a2 = fma(tb.BvW[qy][j], s[e].vq[f][1][q], a2);
     }
-    s.t1[f][0][j][qx] = a1;
-    s.t1[f][1][j][qx] = a2;
+    s[e].t1[f][0][j][qx] = a1;
+    s[e].t1[f][1][j][qx] = a2;
   }
-  for (int it = lane; it < NT * NPL * NQ; it += 32) {
-    const int a = it / (NPL * NQ), r = it % (NPL * NQ), j = r / NQ, qx = r % NQ;
+  for (int it = lane; it < ne * NT * NPL * NQ; it += 32) {
+    const int e = E == 1 ? 0 : it / (NT * NPL * NQ), r0 = E == 1 ? it : it % (NT * NPL * NQ);
+    const int a = r0 / (NPL * NQ), r = r0 % (NPL * NQ), j = r / NQ, qx = r % NQ;
     double v = 0.0;
 #pragma unroll
-    for (int qy = 0; qy < NQ; ++qy) v = fma(tb.BpW[qy][j], s.pq[a][qy * NQ + qx], v);
-    s.tp[a][j][qx] = v;
+    for (int qy = 0; qy < NQ; ++qy) v = fma(tb.BpW[qy][j], s[e].pq[a][qy * NQ + qx], v);
+    s[e].tp[a][j][qx] = v;
   }
   __syncwarp();
   // x pass -> element output; layout a (2 NVE + NPE) + c NVE + l, then pressure
-  for (int it = lane; it < NF * d::NVE; it += 32) {
-    const int f = it / d::NVE, l = it % d::NVE, c = f / NT, a = f % NT, j = l / NVL, i = l % NVL;
+  for (int it = lane; it < ne * NF * d::NVE; it += 32) {
+    const int e = E == 1 ? 0 : it / (NF * d::NVE), r0 = E == 1 ? it : it % (NF * d::NVE);
+    const int f = r0 / d::NVE, l = r0 % d::NVE, c = f / NT, a = f % NT, j = l / NVL, i = l % NVL;
     double v = 0.0;
 #pragma unroll
     for (int qx = 0; qx < NQ; ++qx) {
-      v = fma(tb.BvW[qx][i], s.t1[f][0][j][qx], v);
-      v = fma(tb.DvW[qx][i], s.t1[f][1][j][qx], v);
+      v = fma(tb.BvW[qx][i], s[e].t1[f][0][j][qx], v);
+      v = fma(tb.DvW[qx][i], s[e].t1[f][1][j][qx], v);
     }
-    s.out[a * (2 * d::NVE + d::NPE) + c * d::NVE + l] = v;
+    s[e].out[a * (2 * d::NVE + d::NPE) + c * d::NVE + l] = v;
   }
-  for (int it = lane; it < NT * d::NPE; it += 32) {
-    const int a = it / d::NPE, l = it % d::NPE, j = l / NPL, i = l % NPL;
+  for (int it = lane; it < ne * NT * d::NPE; it += 32) {
+    const int e = E == 1 ? 0 : it / (NT * d::NPE), r0 = E == 1 ? it : it % (NT * d::NPE);
+    const int a = r0 / d::NPE, l = r0 % d::NPE, j = l / NPL, i = l % NPL;
     double v = 0.0;
 #pragma unroll
-    for (int qx = 0; qx < NQ; ++qx) v = fma(tb.BpW[qx][i], s.tp[a][j][qx], v);
-    s.out[a * (2 * d::NVE + d::NPE) + 2 * d::NVE + l] = v;
+    for (int qx = 0; qx < NQ; ++qx) v = fma(tb.BpW[qx][i], s[e].tp[a][j][qx], v);
+    s[e].out[a * (2 * d::NVE + d::NPE) + 2 * d::NVE + l] = v;
   }
   __syncwarp();
-  double* dst = ye + ((int64_t)slab * g.ncells() + cell) * d::ELEM;
-  for (int it = lane; it < d::ELEM; it += 32) dst[it] = s.out[it];
+  double* dst = ye + ((int64_t)slab * g.ncells() + cell0) * d::ELEM;  // the E elements are consecutive
+  for (int it = lane; it < nin * d::ELEM; it += 32) dst[it] = E == 1 ? s[0].out[it] : s[it / d::ELEM].out[it % d::ELEM];
 }
 
 template <int K, int Q>
@@ -1238,9 +1264,11 @@ jac_kernel(LevelGeom g, const __grid_constant__ FeTables T, PhysParams ph, const
   extern __shared__ __align__(16) unsigned char smem_raw[];
   build_jac_tab<K, Q>(T, g, ph, tb);
   __syncthreads();
-  const int cell = blockIdx.x * kWarps + threadIdx.x / 32;
-  if (cell >= g.ncells()) return;
-  jac_body<K, Q>(g, tb, Wq, x, ye, reinterpret_cast<JacSmem<K, Q>*>(smem_raw)[threadIdx.x / 32], cell, blockIdx.y);
+  constexpr int E = JacE<K, Q>::E;
+  const int cell0 = (blockIdx.x * kWarps + threadIdx.x / 32) * E;
+  if (cell0 >= g.ncells()) return;
+  jac_body<K, Q, E>(g, tb, Wq, x, ye, reinterpret_cast<JacSmem<K, Q>*>(smem_raw) + (threadIdx.x / 32) * E, cell0,
+                    blockIdx.y);
 }
 
 template <int K, int Q>
@@ -1256,10 +1284,11 @@ void run_wq(const LevelGeom& g, const FeTables& T, const double* W, double* Wq, 
 template <int K, int Q>
 void run_jac(const LevelGeom& g, const FeTables& T, const PhysParams& ph, const double* Wq, const double* x,
              double* y, double* ye, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
-  const size_t smem = sizeof(JacSmem<K, Q>) * kWarps;
+  constexpr int E = JacE<K, Q>::E;
+  const size_t smem = sizeof(JacSmem<K, Q>) * kWarps * E;
   auto kern = jac_kernel<K, Q>;
   WR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((g.ncells() + kWarps - 1) / kWarps, g.N);
+  dim3 grid((g.ncells() + kWarps * E - 1) / (kWarps * E), g.N);
   if (ev0) WR_CUDA(cudaEventRecord(ev0, s));
   kern<<<grid, 32 * kWarps, smem, s>>>(g, T, ph, Wq, x, ye);
   WR_LAUNCH_CHECK();
