@@ -428,16 +428,18 @@ __device__ bool gauss_jordan(CT* A, CT* colbuf, int* perm, int* sh) {
 // as gauss_jordan above without moving rows: thread (ty, tx) of a (NTH/32) x 32 grid
 // holds rows ty + TY u and columns tx + 32 v of A in registers for the whole
 // inversion.  Per pivot column p: the column goes to shared memory, every warp picks
-// the pivot row (largest |.| among rows not yet used, lowest row on ties), the warp
-// that owns that row publishes it scaled, and every thread updates its own entries
-// (two block barriers per pivot; the column and row buffers alternate between
-// pivots, and the used-row flags change only after the second barrier).  The inverse is read back with the pivot order undone:
+// the pivot row (largest |.| among rows not yet used, compared to 16 mantissa bits,
+// lowest row on ties), the warp that owns that row publishes it scaled, and every
+// thread updates its own entries (two block barriers per pivot; the column and row
+// buffers alternate between pivots, and the used-row flags change only after the
+// second barrier).  The inverse is read back with the pivot order undone:
 // inv(A)[i][r_q] = X[r_i][q] for the pivot rows r.  A is MS x MS row-major with
 // leading dimension LD in shared memory, overwritten with inv(A).  Returns false (to
 // all threads) if a zero pivot was met.
 template <int MS, int LD, int NTH, typename CT>
 __device__ bool gauss_jordan_reg(CT* A) {
   constexpr int TY = NTH / 32, RU = (MS + TY - 1) / TY, CV = (MS + 31) / 32;
+  static_assert(sizeof(CT) == 4 && MS <= 128, "pivot keys hold an FP32 |x| and a row below 128");
   __shared__ CT colb[2][MS], rowb[2][MS];
   __shared__ int used[MS], prow[MS], pstep[MS], zero_pivot;
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
@@ -469,21 +471,15 @@ __device__ bool gauss_jordan_reg(CT* A) {
         }
       }
       __syncthreads();
-      // every warp finds the same pivot row
-      CT best = CT(-1);
-      int bi = MS;
-      for (int i = lane; i < MS; i += 32) {
-        const CT v = used[i] ? CT(-1) : fabs(colb[bsel][i]);
-        if (v > best) { best = v; bi = i; }
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const CT ob = __shfl_xor_sync(0xffffffffu, best, off);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      const int r = bi;
-      const CT inv = CT(1) / colb[bsel][r];
+      // every warp finds the same pivot row: one integer max over keys that hold |x|
+      // to 16 mantissa bits above 127 - row (rows already used have key 0)
+      unsigned key = 0u;
+      for (int i = lane; i < MS; i += 32)
+        if (!used[i]) key = max(key, (abs_key(colb[bsel][i]) & 0x7fffff80u) | (unsigned)(127 - i));
+      key = __reduce_max_sync(0xffffffffu, key);
+      const int r = 127 - (int)(key & 127u);
+      const CT pv = colb[bsel][r];
+      const CT inv = CT(1) / pv;
       // the owner warp of row r publishes it scaled by the inverse pivot
       if (ty == r % TY) {
         const int ur = r / TY;
@@ -497,24 +493,34 @@ __device__ bool gauss_jordan_reg(CT* A) {
         }
       }
       __syncthreads();
+      // rank-one update of every row but the pivot row (its multiplier is zero), which
+      // its owner warp then overwrites with the published row
+      CT rj[CV];
+#pragma unroll
+      for (int v = 0; v < CV; ++v) {
+        const int j = lane + 32 * v;
+        rj[v] = j < MS ? rowb[bsel][j] : CT(0);
+      }
 #pragma unroll
       for (int u = 0; u < RU; ++u) {
         const int i = ty + TY * u;
-        const CT f = i < MS ? colb[bsel][i] : CT(0);
-        const bool pivot_row = i == r;
+        const CT f = (i < MS && i != r) ? colb[bsel][i] : CT(0);
 #pragma unroll
-        for (int v = 0; v < CV; ++v) {
-          const int j = lane + 32 * v;
-          const CT rj = j < MS ? rowb[bsel][j] : CT(0);
-          a[u][v] = pivot_row ? rj : fma(-f, rj, a[u][v]);
-        }
+        for (int v = 0; v < CV; ++v) a[u][v] = fma(-f, rj[v], a[u][v]);
+      }
+      if (ty == r % TY) {
+        const int ur = r / TY;
+#pragma unroll
+        for (int u = 0; u < RU; ++u)
+#pragma unroll
+          for (int v = 0; v < CV; ++v) a[u][v] = (u == ur) ? rj[v] : a[u][v];
       }
       // bookkeeping after the second barrier, so that no warp's search of this pivot sees it
       if (tid == 0) {
         used[r] = 1;
         prow[p] = r;
         pstep[r] = p;
-        if (!(best > CT(0))) zero_pivot = 1;
+        if (!(fabs(pv) > CT(0))) zero_pivot = 1;
       }
     }
   }
@@ -599,6 +605,63 @@ __device__ void gemm_into_b(const CT* A, CT* B, CT sign) {
   __syncthreads();
 }
 
+// The same product for the reduced-precision forms, register-tiled like gauss_jordan_reg:
+// thread (ty, tx) of the (NTH/32) x 32 grid accumulates rows ty + TY u and columns
+// tx + 32 v, so per k it loads RU entries of A (one address per warp) and CV of B (32
+// consecutive entries per warp) for RU x CV FMAs, at offsets fixed at compile time.  Each
+// output entry is the same FMA chain over k = 0 .. MS-1 as in gemm_into_b (bitwise the
+// same result); rows and columns past MS read row / column MS-1 and are not stored.
+template <int MS, int LD, int NTH, typename CT>
+__device__ void gemm_into_b_reg(const CT* A, CT* B, CT sign) {
+  constexpr int TY = NTH / 32, RU = (MS + TY - 1) / TY, CV = (MS + 31) / 32;
+  const int lane = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  CT acc[RU][CV];
+  const CT* arow[RU];
+  int bcol[CV];
+#pragma unroll
+  for (int u = 0; u < RU; ++u) {
+    const int i = ty + TY * u;
+    arow[u] = A + (i < MS ? i : MS - 1) * LD;
+#pragma unroll
+    for (int v = 0; v < CV; ++v) acc[u][v] = CT(0);
+  }
+#pragma unroll
+  for (int v = 0; v < CV; ++v) {
+    const int j = lane + 32 * v;
+    bcol[v] = j < MS ? j : MS - 1;
+  }
+#pragma unroll 2
+  for (int l = 0; l < MS; ++l) {
+    CT av[RU], bv[CV];
+#pragma unroll
+    for (int u = 0; u < RU; ++u) av[u] = arow[u][l];
+#pragma unroll
+    for (int v = 0; v < CV; ++v) bv[v] = B[l * LD + bcol[v]];
+#pragma unroll
+    for (int u = 0; u < RU; ++u)
+#pragma unroll
+      for (int v = 0; v < CV; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < RU; ++u)
+#pragma unroll
+    for (int v = 0; v < CV; ++v) {
+      const int i = ty + TY * u, j = lane + 32 * v;
+      if (i < MS && j < MS) B[i * LD + j] = sign * acc[u][v];
+    }
+  __syncthreads();
+}
+
+// B = sign A B for the factor kernel: FP64 keeps gemm_into_b (its 128-register budget
+// holds the per-entry indices, and the FP64 pipe bounds it); FP32 takes the register tile,
+// which under the 64-register budget of two CTAs per SM needs no index recomputation.
+template <int MS, int LD, int NTH, typename CT>
+__device__ void gemm_block(const CT* A, CT* B, CT sign) {
+  if constexpr (sizeof(CT) == 8) gemm_into_b<MS, LD, NTH, CT>(A, B, sign);
+  else gemm_into_b_reg<MS, LD, NTH, CT>(A, B, sign);
+}
+
 // Two CTAs per SM for the reduced-precision Q3/Q2 blocks (64 registers; the register-
 // tiled inversion is latency-bound, so a second CTA hides its barriers); FP64 Q3/Q2
 // needs 183 KB of shared memory and runs one.
@@ -654,7 +717,7 @@ block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const C
         assemble(M2, k, j);
         for (int m = 0; m < k; ++m)
           gemm_sub_stored<MS, LD, NTH>(M2, F + pos_low<NT>(k, m) * BLK, F + pos_up<NT>(m, j) * BLK);
-        gemm_into_b<MS, LD, NTH, CT>(M1, M2, CT(1));
+        gemm_block<MS, LD, NTH, CT>(M1, M2, CT(1));
         store_colmajor<MS, LD, NTH>(M2, F + pos_up<NT>(k, j) * BLK);
         __syncthreads();  // M2 is reassembled next; the stored block is read back later
       }
@@ -677,7 +740,7 @@ block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const C
     assemble_const<K, Q, CT, LD, NPGX>(g, T, ph, ft, M2, 0, 1, false, gr);
     __syncthreads();
     if (conv) assemble_conv<K, Q, CT, LD, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M2, 0, 1, gr);
-    gemm_into_b<MS, LD, NTH, CT>(M1, M2, CT(1));
+    gemm_block<MS, LD, NTH, CT>(M1, M2, CT(1));
     store_colmajor<MS, LD, NTH>(M2, F + 3 * BLK);
     // A10
     assemble_const<K, Q, CT, LD, NPGX>(g, T, ph, ft, M1, 1, 0, false, gr);
@@ -685,7 +748,7 @@ block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const C
     if (conv) assemble_conv<K, Q, CT, LD, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M1, 1, 0, gr);
     store_colmajor<MS, LD, NTH>(M1, F + 1 * BLK);
     // S = A11 - A10 X
-    gemm_into_b<MS, LD, NTH, CT>(M1, M2, CT(-1));
+    gemm_block<MS, LD, NTH, CT>(M1, M2, CT(-1));
     assemble_const<K, Q, CT, LD, NPGX>(g, T, ph, ft, M2, 1, 1, true, gr);
     __syncthreads();
     if (conv) assemble_conv<K, Q, CT, LD, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M2, 1, 1, gr);
@@ -830,7 +893,7 @@ __device__ __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162floa
 // Tile variants of the smoother apply (chosen per level by the autotuner): column
 // groups per chunk G, CTAs per SM and the shared-memory ring that streams the
 // factor chunks.  Variants of one K with the same G sum in the same order.
-//   Q2/Q1 (K = 1): G = 5 with 1, 2 or 3 CTAs per SM (176 / 96 / 64 KB rings);
+//   Q2/Q1 (K = 1): G = 5 with 1, 4 or 3 CTAs per SM (176 / 43 / 64 KB rings);
 //   Q3/Q2 (K = 2): G = 4 with one 480-thread CTA per SM (176 KB), or G = 2 with
 //                  two or three 256-thread CTAs per SM (96 / 64 KB).
 // The coarse 3x3 block (NPGX != 2K - 1) always takes variant 0.
@@ -840,8 +903,11 @@ inline int default_apply_variant(int k) { return k == 1 ? 2 : 0; }
 template <int K, int V>
 struct ApplyTile {
   static constexpr int G = K == 1 ? 5 : (V == 0 ? 4 : 2);
-  static constexpr int MINB = V + 1;
-  static constexpr int RING_KB = V == 0 ? 176 : V == 1 ? 96 : 64;
+  // Q2/Q1 tile 1: four CTAs per SM with a two-block FP64 ring (47 KB each), so that
+  // three other CTAs' GEMVs keep the FP64 pipe busy while one is in its serial phases
+  // (jump coupling, group reduction)
+  static constexpr int MINB = (K == 1 && V == 1) ? 4 : V + 1;
+  static constexpr int RING_KB = V == 0 ? 176 : V == 1 ? (K == 1 ? 43 : 96) : 64;
 };
 
 template <int K, int Q, typename FT, int NPGX = 2 * K - 1, int V = 0>
