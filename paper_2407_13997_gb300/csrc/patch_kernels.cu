@@ -763,7 +763,7 @@ block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const C
 // its tables and assembles its block in FP32 in its own shared-memory tile (the
 // same assembly as the CTA kernel, lane-strided), then inverts it in registers by
 // the Gauss-Jordan elimination of gauss_jordan_reg (no row moves; pivot = largest
-// |.| among the rows not yet used, lowest row on ties): lane l holds rows l and
+// |.| among the rows not yet used, compared to 16 mantissa bits, lowest row on ties): lane l holds rows l and
 // l + 32.  Each step eliminates the current first column and appends the new
 // column of the inverse at the end (every row shifts left by one), so the pivot
 // column is always register 0, the column loop unrolls with constant register
@@ -815,42 +815,36 @@ block_factor_warp_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, co
   bool zero = false;
 #pragma unroll 1
   for (int p = 0; p < MS; ++p) {
-    const float v0 = (used & 1u) ? -1.f : fabsf(a0[0]);
-    const float v1 = (used & 2u) ? -1.f : fabsf(a1[0]);
-    float best = v0;
-    int bi = lane;
-    if (v1 > v0) {
-      best = v1;
-      bi = lane + 32;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const float ob = __shfl_xor_sync(FULL, best, off);
-      const int oi = __shfl_xor_sync(FULL, bi, off);
-      if (ob > best || (ob == best && oi < bi)) {
-        best = ob;
-        bi = oi;
-      }
-    }
-    zero |= !(best > 0.f);
+    // pivot: one integer max over keys that hold |x| to 16 mantissa bits above 127 - row
+    // (rows already used have key 0)
+    const unsigned k0 = (used & 1u) ? 0u : ((abs_key(a0[0]) & 0x7fffff80u) | (unsigned)(127 - lane));
+    const unsigned k1 = (used & 2u) ? 0u : ((abs_key(a1[0]) & 0x7fffff80u) | (unsigned)(95 - lane));
+    const int bi = 127 - (int)(__reduce_max_sync(FULL, max(k0, k1)) & 127u);
     const int owner = bi & 31;
     const bool hi = bi >= 32;
     const bool r0 = !hi && lane == owner, r1 = hi && lane == owner;
-    const float f0 = a0[0], f1 = a1[0];
-    const float inv = 1.f / __shfl_sync(FULL, hi ? f1 : f0, owner);
+    const float pv = __shfl_sync(FULL, hi ? a1[0] : a0[0], owner);
+    zero |= !(fabsf(pv) > 0.f);
+    const float inv = 1.f / pv;
+    // the pivot row keeps its entries (zero multiplier) and is scaled by its owner below
+    const float f0 = r0 ? 0.f : a0[0], f1 = r1 ? 0.f : a1[0];
 #pragma unroll
     for (int j = 1; j < MS; ++j) {
       const float rj = __shfl_sync(FULL, hi ? a1[j] : a0[j], owner) * inv;
-      a0[j - 1] = r0 ? rj : fmaf(-f0, rj, a0[j]);
-      a1[j - 1] = r1 ? rj : fmaf(-f1, rj, a1[j]);
+      a0[j - 1] = fmaf(-f0, rj, a0[j]);
+      a1[j - 1] = fmaf(-f1, rj, a1[j]);
     }
     a0[MS - 1] = r0 ? inv : -f0 * inv;
     a1[MS - 1] = r1 ? inv : -f1 * inv;
     if (r0) {
+#pragma unroll
+      for (int j = 0; j < MS - 1; ++j) a0[j] *= inv;
       used |= 1u;
       step0 = p;
     }
     if (r1) {
+#pragma unroll
+      for (int j = 0; j < MS - 1; ++j) a1[j] *= inv;
       used |= 2u;
       step1 = p;
     }
