@@ -916,11 +916,15 @@ struct ApplyCfg {
   static constexpr int GR = 16 / (int)sizeof(FT);                 // elements per 16-byte granule
   static constexpr int BLK = (MS * MS + GR - 1) / GR * GR;        // padded block elements
   static constexpr int BLK_BYTES = BLK * (int)sizeof(FT);
-  // chunk width: whole block for k = 1, 28 columns for k = 2 (a multiple of GR columns keeps
-  // every chunk boundary on a 16-byte granule)
-  static constexpr int CC = K == 1 ? (MS + GR - 1) / GR * GR : (28 + GR - 1) / GR * GR;
+  // chunk width: whole block for k = 1; for k = 2, 28 columns (FP64, FP32) or 64 (BF16, whose
+  // two-byte entries need twice the FMAs per byte: the wider chunk halves the per-chunk ring
+  // work per FMA).  A multiple of GR columns keeps every chunk boundary on a 16-byte granule.
+  static constexpr int CC = K == 1 ? (MS + GR - 1) / GR * GR : (sizeof(FT) == 2 ? 64 : (28 + GR - 1) / GR * GR);
   static constexpr int NCH = (MS + CC - 1) / CC;                  // chunks per block
   static constexpr int SUB = (CC + G - 1) / G;                    // columns per group and chunk
+  static constexpr int MSX = (MS + 3) / 4 * 4;                    // padded rows of rhs / y in shared memory
+  // four-wide loads of the input vector when every group's first column is 16-byte aligned
+  static constexpr bool XV = sizeof(CT) == 4 && SUB % 4 == 0 && CC % 4 == 0;
   static constexpr int LAST = BLK - (NCH - 1) * CC * MS;          // last chunk carries the padding
   static constexpr int SLOT = CC * MS > LAST ? CC * MS : LAST;
   static constexpr int SLOT_ELEMS = (SLOT + GR - 1) / GR * GR;
@@ -949,8 +953,8 @@ struct ApplySmem {
   int cols[C::MS];
   int cst[C::NCH + 1];
   int dense;
-  CT rhs[C::NT][C::MS];
-  CT y[C::NT][C::MS];
+  alignas(16) CT rhs[C::NT][C::MSX];
+  alignas(16) CT y[C::NT][C::MSX];
   CT red[C::G][C::MS];
   CT yp[2][pd::NVG2];
   CT tm[2][pd::NVG2];
@@ -1084,7 +1088,8 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
   }
 
   // ---------------- consumer warps
-  int64_t ci = 0;  // next chunk to consume
+  int cslot = 0;          // ring slot of the next chunk to consume
+  uint32_t cphase = 0u;   // its mbarrier phase parity
   const bool gemv_thread = tid < C::G * MS;
   const int row = tid % MS, grp = tid / MS;
   bool aborted = false;
@@ -1172,8 +1177,8 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
         const CT* xv = op.src_y ? sm.y[op.src] : sm.rhs[op.src];
         CT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         for (int k = 0; k < NCH; ++k) {
-          const int slot = (int)(ci % NS);
-          const bool ok = !aborted && mbar_wait_bounded(smem_u32(&sm.full[slot]), (uint32_t)((ci / NS) & 1));
+          const int slot = cslot;
+          const bool ok = !aborted && mbar_wait_bounded(smem_u32(&sm.full[slot]), cphase);
           if (!ok) {
             aborted = true;
             *abort_flag = 1;
@@ -1203,18 +1208,31 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
 #pragma unroll 4
               for (; c < c1; ++c) a0 = fma(widen(A[c * MS + row]), xk[c], a0);
             } else {
-              for (; c + 3 < c1; c += 4) {
-                a0 = fma(widen(A[(c + 0) * MS + row]), xk[c + 0], a0);
-                a1 = fma(widen(A[(c + 1) * MS + row]), xk[c + 1], a1);
-                a2 = fma(widen(A[(c + 2) * MS + row]), xk[c + 2], a2);
-                a3 = fma(widen(A[(c + 3) * MS + row]), xk[c + 3], a3);
+              // columns c0 + 4i + j accumulate in a_j, the tail in a0; the column pointer
+              // steps by four columns, so the four loads take fixed offsets
+              const FT* Ac = A + c * MS + row;
+              for (; c + 3 < c1; c += 4, Ac += 4 * MS) {
+                CT x0, x1, x2, x3;
+                if constexpr (C::XV) {
+                  const float4 xq = *reinterpret_cast<const float4*>(xk + c);
+                  x0 = xq.x; x1 = xq.y; x2 = xq.z; x3 = xq.w;
+                } else {
+                  x0 = xk[c]; x1 = xk[c + 1]; x2 = xk[c + 2]; x3 = xk[c + 3];
+                }
+                a0 = fma(widen(Ac[0]), x0, a0);
+                a1 = fma(widen(Ac[MS]), x1, a1);
+                a2 = fma(widen(Ac[2 * MS]), x2, a2);
+                a3 = fma(widen(Ac[3 * MS]), x3, a3);
               }
-              for (; c < c1; ++c) a0 = fma(widen(A[c * MS + row]), xk[c], a0);
+              for (; c < c1; ++c, Ac += MS) a0 = fma(widen(Ac[0]), xk[c], a0);
             }
           }
           __syncwarp();
           if (ok && lane == 0) mbar_arrive(smem_u32(&sm.empty[slot]));  // this warp is done with the slot
-          ++ci;
+          if (++cslot == NS) {
+            cslot = 0;
+            cphase ^= 1u;
+          }
         }
         if (gemv_thread) sm.red[grp][row] = sizeof(CT) == 8 ? a0 : (a0 + a1) + (a2 + a3);
         if (tid == 0) sm.decision = *abort_flag;  // one reader, so every consumer decides alike
