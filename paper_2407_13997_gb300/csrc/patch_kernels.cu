@@ -44,6 +44,37 @@ struct PD {
   static constexpr int NVL = K + 2, NVE = NVL * NVL;
 };
 
+// Layout of one stored factor block (MS x MS): column-major with leading dimension MS,
+// padded to a 16-byte granule, except the BF16 blocks of Q2/Q1 patches (MS = 51), whose
+// first C8 = 48 columns are stored by octets -- entry (i, j) at ((j / 8) MS + i) 8 + j % 8,
+// the entries of row i in columns 8o .. 8o+7 in one 16-byte word (one load for eight FMAs
+// in the warp tiles) -- and whose last MS - C8 columns follow column-major.
+template <typename FT, int MS>
+struct Stored {
+  static constexpr bool OCT = sizeof(FT) == 2 && MS < 64;
+  static constexpr int GR = 16 / (int)sizeof(FT);
+  static constexpr int C8 = OCT ? MS / 8 * 8 : 0;  // columns stored by octets
+  static constexpr int BLK = (MS * MS + GR - 1) / GR * GR;
+  __host__ __device__ static constexpr int at(int i, int j) {
+    if constexpr (!OCT) return j * MS + i;
+    else return j < C8 ? ((j >> 3) * MS + i) * 8 + (j & 7) : C8 * MS + (j - C8) * MS + i;
+  }
+};
+// the two BF16 entries of a 32-bit word, widened exactly to FP32
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+// acc + sum_j A_j x_j over one octet of a row, in column order (one FMA chain)
+__device__ __forceinline__ float oct_fma(const uint4 w, const float4 xa, const float4 xb, float acc) {
+  acc = fmaf(bf16_lo(w.x), xa.x, acc);
+  acc = fmaf(bf16_hi(w.x), xa.y, acc);
+  acc = fmaf(bf16_lo(w.y), xa.z, acc);
+  acc = fmaf(bf16_hi(w.y), xa.w, acc);
+  acc = fmaf(bf16_lo(w.z), xb.x, acc);
+  acc = fmaf(bf16_hi(w.z), xb.y, acc);
+  acc = fmaf(bf16_lo(w.w), xb.z, acc);
+  return fmaf(bf16_hi(w.w), xb.w, acc);
+}
+
 // Block LDU of a slab's diagonal block over its NT = q+1 temporal sub-blocks (block
 // Gaussian elimination without pivoting across sub-blocks, partial pivoting inside the
 // diagonal ones):  S_k = A_kk - sum_{m<k} C_km X_mk,  C_ik = A_ik - sum_{m<k} C_im X_mk
@@ -559,9 +590,26 @@ __device__ __forceinline__ void narrow(float v, __nv_bfloat16& d) { d = __float2
 
 template <int MS, int LD, int NTH, typename CT, typename ST>
 __device__ void store_colmajor(const CT* A, ST* dst) {
-  for (int e = threadIdx.x; e < MS * MS; e += NTH) {
-    const int j = e / MS, i = e - j * MS;
-    narrow(A[i * LD + j], dst[e]);
+  using SL = Stored<ST, MS>;
+  if constexpr (SL::OCT) {
+    for (int e = threadIdx.x; e < MS * MS; e += NTH) {
+      int i, j;
+      if (e < SL::C8 * MS) {
+        const int o = e / (MS * 8), rem = e - o * (MS * 8);
+        i = rem >> 3;
+        j = o * 8 + (rem & 7);
+      } else {
+        const int t = e - SL::C8 * MS;
+        j = SL::C8 + t / MS;
+        i = t - (j - SL::C8) * MS;
+      }
+      narrow(A[i * LD + j], dst[e]);
+    }
+  } else {
+    for (int e = threadIdx.x; e < MS * MS; e += NTH) {
+      const int j = e / MS, i = e - j * MS;
+      narrow(A[i * LD + j], dst[e]);
+    }
   }
 }
 
@@ -570,6 +618,7 @@ __device__ void store_colmajor(const CT* A, ST* dst) {
 // wrote before its last barrier.
 template <int MS, int LD, int NTH, typename CT, typename ST>
 __device__ void gemm_sub_stored(CT* M, const ST* P, const ST* Qm) {
+  static_assert(!Stored<ST, MS>::OCT, "stored blocks read back column-major");
   for (int e = threadIdx.x; e < MS * MS; e += NTH) {
     const int i = e / MS, j = e - i * MS;
     CT acc = 0;
@@ -671,8 +720,7 @@ block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const C
                     ST* __restrict__ factors, int* __restrict__ status) {
   using pd = PD<K, NPGX>;
   constexpr int MS = pd::MS, LD = pd::LD;
-  constexpr int G = 16 / (int)sizeof(ST);
-  constexpr int64_t BLK = (MS * MS + G - 1) / G * G;
+  constexpr int64_t BLK = Stored<ST, MS>::BLK;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT* M1 = reinterpret_cast<CT*>(smem_raw);
   CT* M2 = M1 + MS * LD;
@@ -786,8 +834,8 @@ block_factor_warp_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, co
   using SM = FactorWarpSmem<ST>;
   constexpr int MS = SM::MS, LD = SM::LD;
   static_assert(MS > 32 && MS <= 64, "two rows per lane");
-  constexpr int G = 16 / (int)sizeof(ST);
-  constexpr int64_t BLK = (MS * MS + G - 1) / G * G;
+  using SL = Stored<ST, MS>;
+  constexpr int64_t BLK = SL::BLK;
   constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -855,8 +903,8 @@ block_factor_warp_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, co
 #pragma unroll
   for (int j = 0; j < MS; ++j) {
     const int col = sm.prow[j];
-    narrow(a0[j], F[col * MS + step0]);
-    if (two) narrow(a1[j], F[col * MS + step1]);
+    narrow(a0[j], F[SL::at(step0, col)]);
+    if (two) narrow(a1[j], F[SL::at(step1, col)]);
   }
   if (zero && lane == 0) atomicExch(status, 1);
 }
@@ -914,15 +962,17 @@ struct ApplyCfg {
   static constexpr int NCONS = (G * MS + 31) / 32 * 32;           // consumer threads
   static constexpr int NTH = NCONS + 32;                          // + one producer warp
   static constexpr int GR = 16 / (int)sizeof(FT);                 // elements per 16-byte granule
-  static constexpr int BLK = (MS * MS + GR - 1) / GR * GR;        // padded block elements
+  using SL = Stored<FT, MS>;
+  static constexpr int BLK = SL::BLK;                             // stored block elements
   static constexpr int BLK_BYTES = BLK * (int)sizeof(FT);
   // chunk width: whole block for k = 1; for k = 2, 28 columns (FP64, FP32) or 64 (BF16, whose
   // two-byte entries need twice the FMAs per byte: the wider chunk halves the per-chunk ring
   // work per FMA).  A multiple of GR columns keeps every chunk boundary on a 16-byte granule.
   static constexpr int CC = K == 1 ? (MS + GR - 1) / GR * GR : (sizeof(FT) == 2 ? 64 : (28 + GR - 1) / GR * GR);
   static constexpr int NCH = (MS + CC - 1) / CC;                  // chunks per block
-  static constexpr int SUB = (CC + G - 1) / G;                    // columns per group and chunk
-  static constexpr int MSX = (MS + 3) / 4 * 4;                    // padded rows of rhs / y in shared memory
+  // columns per group and chunk (whole octets for the BF16 Q2/Q1 blocks)
+  static constexpr int SUB = SL::OCT ? ((CC + G - 1) / G + 7) / 8 * 8 : (CC + G - 1) / G;
+  static constexpr int MSX = (MS + 3) / 4 * 4;                    // 16-byte rows of rhs / y in shared memory
   // four-wide loads of the input vector when every group's first column is 16-byte aligned
   static constexpr bool XV = sizeof(CT) == 4 && SUB % 4 == 0 && CC % 4 == 0;
   static constexpr int LAST = BLK - (NCH - 1) * CC * MS;          // last chunk carries the padding
@@ -934,6 +984,7 @@ struct ApplyCfg {
                                 ? RING_BYTES / (SLOT_ELEMS * (int)sizeof(FT))
                                 : 16;
   static_assert((CC * MS * (int)sizeof(FT)) % 16 == 0, "chunk boundary off the 16-byte granule");
+  static_assert(!SL::OCT || NCH == 1, "octet-stored blocks stream as one chunk");
   static_assert(NS >= 2, "ring too small");
 };
 
@@ -1192,7 +1243,7 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
 #pragma unroll 4
             for (int t = tb; t < te; ++t) {
               const int c = sm.cols[t] - k * C::CC;
-              a0 = fma(widen(A[c * MS + row]), xk[c], a0);
+              a0 = fma(widen(A[C::SL::at(row, c)]), xk[c], a0);
             }
           } else if (ok && gemv_thread) {
             const FT* A = ring + (size_t)slot * C::SLOT_ELEMS;
@@ -1207,6 +1258,25 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
               // three combining additions per block
 #pragma unroll 4
               for (; c < c1; ++c) a0 = fma(widen(A[c * MS + row]), xk[c], a0);
+            } else if constexpr (C::SL::OCT) {
+              // BF16 octets: one 16-byte load holds this row's entries of eight columns;
+              // columns 8i + j accumulate in a_(j mod 4), the column-major tail in a0
+              const int c8 = min(c1, C::SL::C8);
+              const uint4* Ao = reinterpret_cast<const uint4*>(A + ((c >> 3) * MS + row) * 8);
+              for (; c < c8; c += 8, Ao += MS) {
+                const uint4 w = *Ao;
+                const float4 xa = *reinterpret_cast<const float4*>(xk + c);
+                const float4 xb = *reinterpret_cast<const float4*>(xk + c + 4);
+                a0 = fma(bf16_lo(w.x), xa.x, a0);
+                a1 = fma(bf16_hi(w.x), xa.y, a1);
+                a2 = fma(bf16_lo(w.y), xa.z, a2);
+                a3 = fma(bf16_hi(w.y), xa.w, a3);
+                a0 = fma(bf16_lo(w.z), xb.x, a0);
+                a1 = fma(bf16_hi(w.z), xb.y, a1);
+                a2 = fma(bf16_lo(w.w), xb.z, a2);
+                a3 = fma(bf16_hi(w.w), xb.w, a3);
+              }
+              for (c = max(c, C::SL::C8); c < c1; ++c) a0 = fma(widen(A[C::SL::at(row, c)]), xk[c], a0);
             } else {
               // columns c0 + 4i + j accumulate in a_j, the tail in a0; the column pointer
               // steps by four columns, so the four loads take fixed offsets
@@ -1360,8 +1430,11 @@ struct WarpSmem {
   using pd = PD<K>;
   using CT = typename ComputeType<FT>::type;
   static constexpr int MS = pd::MS, NT = Q + 1;
-  CT rhs[NT][MS];
-  CT y[NT][MS];
+  // 16-byte rows where the octet loops load the input four-wide
+  static constexpr bool OCT = Stored<FT, MS>::OCT;
+  static constexpr int MSW = OCT ? (MS + 3) / 4 * 4 : MS;
+  alignas(OCT ? 16 : alignof(CT)) CT rhs[NT][MSW];
+  alignas(OCT ? 16 : alignof(CT)) CT y[NT][MSW];
   CT yp[2][pd::NVG2];
   CT tm[2][pd::NVG2];
   CT mx[pd::NVG][pd::NVG];
@@ -1447,14 +1520,41 @@ __device__ __forceinline__ void warp_apply(const FeTables& T, const Items& items
         CT acc[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] = 0;
-#pragma unroll 4
-        for (int c = 0; c < MS; ++c) {
-          const CT xc = xv[c];
-          const FT* col = A + (int64_t)c * MS;
+        if constexpr (Stored<FT, MS>::OCT) {
+          // one 16-byte load per row and octet of columns, then the column-major tail;
+          // the FMAs of a row in column order
+          using SL = Stored<FT, MS>;
+#pragma unroll 2
+          for (int o = 0; o < SL::C8 / 8; ++o) {
+            const float4 xa = *reinterpret_cast<const float4*>(xv + 8 * o);
+            const float4 xb = *reinterpret_cast<const float4*>(xv + 8 * o + 4);
+            const uint4* Ao = reinterpret_cast<const uint4*>(A) + (int64_t)o * MS;
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const int row = lane + 32 * r;
-            if (row < MS) acc[r] = fma(widen(__ldg(col + row)), xc, acc[r]);
+            for (int r = 0; r < R; ++r) {
+              const int row = lane + 32 * r;
+              if (row < MS) acc[r] = oct_fma(__ldg(Ao + row), xa, xb, acc[r]);
+            }
+          }
+#pragma unroll
+          for (int c = SL::C8; c < MS; ++c) {
+            const CT xc = xv[c];
+            const FT* col = A + SL::at(0, c);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              const int row = lane + 32 * r;
+              if (row < MS) acc[r] = fma(widen(__ldg(col + row)), xc, acc[r]);
+            }
+          }
+        } else {
+#pragma unroll 4
+          for (int c = 0; c < MS; ++c) {
+            const CT xc = xv[c];
+            const FT* col = A + (int64_t)c * MS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              const int row = lane + 32 * r;
+              if (row < MS) acc[r] = fma(widen(__ldg(col + row)), xc, acc[r]);
+            }
           }
         }
         __syncwarp();
@@ -1530,8 +1630,7 @@ constexpr int kWarpBulkWarps = 4;
 template <typename FT>
 struct alignas(16) WarpBulkSmem {
   static constexpr int MS = PD<1>::MS;
-  static constexpr int GR = 16 / (int)sizeof(FT);
-  static constexpr int BLK = (MS * MS + GR - 1) / GR * GR;  // the stored block, padded to 16 bytes
+  static constexpr int BLK = Stored<FT, MS>::BLK;  // the stored block (a multiple of 16 bytes)
   FT buf[2][BLK];
   unsigned long long full[2];
   WarpSmem<1, 0, FT> w;
@@ -1651,13 +1750,37 @@ __device__ __forceinline__ void warp_apply_bulk(const FeTables& T, const Items& 
       CT acc[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) acc[r] = 0;
-#pragma unroll 4
-      for (int c = 0; c < MS; ++c) {
-        const CT xc = sm.rhs[0][c];
+      if constexpr (Stored<FT, MS>::OCT) {  // tile 3's loops on the shared-memory copy
+        using SL = Stored<FT, MS>;
+#pragma unroll 2
+        for (int o = 0; o < SL::C8 / 8; ++o) {
+          const float4 xa = *reinterpret_cast<const float4*>(&sm.rhs[0][8 * o]);
+          const float4 xb = *reinterpret_cast<const float4*>(&sm.rhs[0][8 * o + 4]);
+          const uint4* Ao = reinterpret_cast<const uint4*>(A) + o * MS;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const int row = lane + 32 * r;
-          if (row < MS) acc[r] = fma(widen(A[c * MS + row]), xc, acc[r]);
+          for (int r = 0; r < R; ++r) {
+            const int row = lane + 32 * r;
+            if (row < MS) acc[r] = oct_fma(Ao[row], xa, xb, acc[r]);
+          }
+        }
+#pragma unroll
+        for (int c = SL::C8; c < MS; ++c) {
+          const CT xc = sm.rhs[0][c];
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int row = lane + 32 * r;
+            if (row < MS) acc[r] = fma(widen(A[SL::at(row, c)]), xc, acc[r]);
+          }
+        }
+      } else {
+#pragma unroll 4
+        for (int c = 0; c < MS; ++c) {
+          const CT xc = sm.rhs[0][c];
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int row = lane + 32 * r;
+            if (row < MS) acc[r] = fma(widen(A[c * MS + row]), xc, acc[r]);
+          }
         }
       }
       __syncwarp();
