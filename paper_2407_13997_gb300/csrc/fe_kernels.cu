@@ -1037,15 +1037,16 @@ wq_kernel(LevelGeom g, const __grid_constant__ FeTables T, const double* __restr
   }
 }
 
-// Elements per warp of jac_kernel (cells cell0 .. cell0+E-1 of one slab).  Q3/Q2 fills
-// the warp's lanes with one element's stage items (25 Gauss points, 80 to 200
-// interpolation items).  Q2/Q1 has 16 Gauss points and 8 to 72 items per stage: DG(0)
-// and DG(1) take four elements (the shared-memory footprint, 2.3 or 4 KB per element,
-// still leaves 24 or 12 warps per SM), DG(2) and DG(3) two, so that their larger
-// footprint and register count leave 8 to 12 warps per SM.
+// Elements per warp of jac_kernel (cells cell0 .. cell0+E-1 of one slab).  Q3/Q2 DG(0)
+// and DG(1) take two elements (stages of 25 Gauss points and 30 to 100 interpolation
+// items per element fill 32-lane warps better in pairs; 6.6 KB per element leaves 16
+// warps per SM), DG(2) and DG(3) one.  Q2/Q1 has 16 Gauss points and 8 to 72 items per
+// stage: DG(0) and DG(1) take four elements (2.3 or 4 KB per element, 24 or 12 warps
+// per SM), DG(2) and DG(3) two, so that their larger footprint and register count
+// leave 8 to 12 warps per SM.
 template <int K, int Q>
 struct JacE {
-  static constexpr int E = K == 2 ? 1 : (Q <= 1 ? 4 : 2);
+  static constexpr int E = Q <= 1 ? (K == 2 ? 2 : 4) : (K == 2 ? 1 : 2);
 };
 
 // One warp: the element contributions of J(W) x on E cells (cell0 + e) of one slab.
