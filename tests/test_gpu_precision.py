@@ -48,6 +48,31 @@ def test_reduced_precision_smoother_close_to_fp64_oracle(w, prec, lo, hi):
     ctx.close()
 
 
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("prec,lo,hi", [("fp32", 1e-12, 2e-5), ("bf16", 1e-5, 0.25)])
+@pytest.mark.parametrize("w", [inputs.fourier_small(n=8, k=1, q=0, N=3, nu=0.02),
+                               inputs.fourier_small(n=8, k=1, q=1, N=2, nu=0.02)], ids=["q2q1_dg0", "q2q1_dg1"])
+def test_reduced_precision_every_tile_close_to_fp64_oracle(w, prec, lo, hi, tile):
+    """Every apply tile on every smoothed level of Q2/Q1, in FP32 and BF16.  The BF16
+    Q2/Q1 blocks are stored by column octets (written by the warp factor kernel for DG(0)
+    and by the CTA factor kernel for DG(1)); the warp tiles read them one 16-byte word per
+    row and octet and the CTA tiles one octet per thread, the last three columns column by
+    column.  A misplaced entry would put the smoother far outside the precision's band."""
+    from tests.test_gpu_parity import Setup
+    p = {"fp32": wrmg.WR_FP32, "bf16": wrmg.WR_BF16}[prec]
+    s = Setup(w, seed=3, options=wrmg.default_options(precision=p, apply_tile=tile, time_parallel=0))
+    s.ctx.linearise(torch.from_numpy(s.W[-1]).cuda(), eig=False)
+    for l in range(1, len(s.discs)):
+        d = s.discs[l]
+        assert s.ctx.apply_tile(l) == tile
+        r = s.rng.standard_normal(d.ndofs)
+        y = s.ctx.vector(l)
+        s.ctx.patch_apply(l, torch.from_numpy(r).cuda(), y)
+        err = rel(y.cpu().numpy(), PatchSmoother(d, d.jacobian(s.W[l])).apply(r))
+        assert lo < err < hi, (l, err)
+    s.ctx.close()
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("w", [inputs.taylor_green_8x8(), inputs.fourier_small(n=8, k=2, q=1, N=4, nu=1e-2)],
                          ids=["tg_q2q1_dg0_n8_N8", "fourier_q3q2_dg1_n8_N4"])
