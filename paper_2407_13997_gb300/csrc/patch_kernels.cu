@@ -45,34 +45,53 @@ struct PD {
 };
 
 // Layout of one stored factor block (MS x MS): column-major with leading dimension MS,
-// padded to a 16-byte granule, except the BF16 blocks of Q2/Q1 patches (MS = 51), whose
-// first C8 = 48 columns are stored by octets -- entry (i, j) at ((j / 8) MS + i) 8 + j % 8,
-// the entries of row i in columns 8o .. 8o+7 in one 16-byte word (one load for eight FMAs
-// in the warp tiles) -- and whose last MS - C8 columns follow column-major.
+// padded to a 16-byte granule, except the FP32 and BF16 blocks of Q2/Q1 patches
+// (MS = 51): their first CG = 48 columns are stored by groups of GV = 16 bytes / entry
+// (4 FP32 or 8 BF16 entries) -- entry (i, j) at ((j / GV) MS + i) GV + j % GV, so that the
+// entries of row i in one group of columns share one 16-byte word (one load for GV FMAs
+// in the warp tiles) -- and their last MS - CG columns follow column-major.
 template <typename FT, int MS>
 struct Stored {
-  static constexpr bool OCT = sizeof(FT) == 2 && MS < 64;
+  static constexpr int GV = (sizeof(FT) <= 4 && MS < 64) ? 16 / (int)sizeof(FT) : 1;
+  static constexpr bool GRP = GV > 1;
   static constexpr int GR = 16 / (int)sizeof(FT);
-  static constexpr int C8 = OCT ? MS / 8 * 8 : 0;  // columns stored by octets
+  static constexpr int CG = GRP ? MS / GV * GV : 0;  // columns stored by groups
   static constexpr int BLK = (MS * MS + GR - 1) / GR * GR;
   __host__ __device__ static constexpr int at(int i, int j) {
-    if constexpr (!OCT) return j * MS + i;
-    else return j < C8 ? ((j >> 3) * MS + i) * 8 + (j & 7) : C8 * MS + (j - C8) * MS + i;
+    if constexpr (!GRP) return j * MS + i;
+    else return j < CG ? ((j / GV) * MS + i) * GV + j % GV : CG * MS + (j - CG) * MS + i;
   }
 };
 // the two BF16 entries of a 32-bit word, widened exactly to FP32
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
-// acc + sum_j A_j x_j over one octet of a row, in column order (one FMA chain)
-__device__ __forceinline__ float oct_fma(const uint4 w, const float4 xa, const float4 xb, float acc) {
-  acc = fmaf(bf16_lo(w.x), xa.x, acc);
-  acc = fmaf(bf16_hi(w.x), xa.y, acc);
-  acc = fmaf(bf16_lo(w.y), xa.z, acc);
-  acc = fmaf(bf16_hi(w.y), xa.w, acc);
-  acc = fmaf(bf16_lo(w.z), xb.x, acc);
-  acc = fmaf(bf16_hi(w.z), xb.y, acc);
-  acc = fmaf(bf16_lo(w.w), xb.z, acc);
-  return fmaf(bf16_hi(w.w), xb.w, acc);
+// acc + sum_j A_j x_j over one 16-byte group of a row, in column order (one FMA chain):
+// 8 BF16 entries against xa, xb, or 4 FP32 entries against xa
+template <typename FT>
+__device__ __forceinline__ float grp_fma(const uint4 w, const float4 xa, const float4 xb, float acc) {
+  if constexpr (sizeof(FT) == 2) {
+    acc = fmaf(bf16_lo(w.x), xa.x, acc);
+    acc = fmaf(bf16_hi(w.x), xa.y, acc);
+    acc = fmaf(bf16_lo(w.y), xa.z, acc);
+    acc = fmaf(bf16_hi(w.y), xa.w, acc);
+    acc = fmaf(bf16_lo(w.z), xb.x, acc);
+    acc = fmaf(bf16_hi(w.z), xb.y, acc);
+    acc = fmaf(bf16_lo(w.w), xb.z, acc);
+    return fmaf(bf16_hi(w.w), xb.w, acc);
+  } else {
+    (void)xb;
+    acc = fmaf(__uint_as_float(w.x), xa.x, acc);
+    acc = fmaf(__uint_as_float(w.y), xa.y, acc);
+    acc = fmaf(__uint_as_float(w.z), xa.z, acc);
+    return fmaf(__uint_as_float(w.w), xa.w, acc);
+  }
+}
+// the input entries of one group of columns (x 16-byte aligned)
+template <typename FT>
+__device__ __forceinline__ void grp_x(const float* x, float4& xa, float4& xb) {
+  xa = *reinterpret_cast<const float4*>(x);
+  if constexpr (sizeof(FT) == 2) xb = *reinterpret_cast<const float4*>(x + 4);
+  else xb = xa;
 }
 
 // Block LDU of a slab's diagonal block over its NT = q+1 temporal sub-blocks (block
@@ -591,17 +610,17 @@ __device__ __forceinline__ void narrow(float v, __nv_bfloat16& d) { d = __float2
 template <int MS, int LD, int NTH, typename CT, typename ST>
 __device__ void store_colmajor(const CT* A, ST* dst) {
   using SL = Stored<ST, MS>;
-  if constexpr (SL::OCT) {
+  if constexpr (SL::GRP) {
     for (int e = threadIdx.x; e < MS * MS; e += NTH) {
       int i, j;
-      if (e < SL::C8 * MS) {
-        const int o = e / (MS * 8), rem = e - o * (MS * 8);
-        i = rem >> 3;
-        j = o * 8 + (rem & 7);
+      if (e < SL::CG * MS) {
+        const int o = e / (MS * SL::GV), rem = e - o * (MS * SL::GV);
+        i = rem / SL::GV;
+        j = o * SL::GV + rem % SL::GV;
       } else {
-        const int t = e - SL::C8 * MS;
-        j = SL::C8 + t / MS;
-        i = t - (j - SL::C8) * MS;
+        const int t = e - SL::CG * MS;
+        j = SL::CG + t / MS;
+        i = t - (j - SL::CG) * MS;
       }
       narrow(A[i * LD + j], dst[e]);
     }
@@ -618,7 +637,7 @@ __device__ void store_colmajor(const CT* A, ST* dst) {
 // wrote before its last barrier.
 template <int MS, int LD, int NTH, typename CT, typename ST>
 __device__ void gemm_sub_stored(CT* M, const ST* P, const ST* Qm) {
-  static_assert(!Stored<ST, MS>::OCT, "stored blocks read back column-major");
+  static_assert(!Stored<ST, MS>::GRP, "stored blocks read back column-major");
   for (int e = threadIdx.x; e < MS * MS; e += NTH) {
     const int i = e / MS, j = e - i * MS;
     CT acc = 0;
@@ -970,8 +989,8 @@ struct ApplyCfg {
   // work per FMA).  A multiple of GR columns keeps every chunk boundary on a 16-byte granule.
   static constexpr int CC = K == 1 ? (MS + GR - 1) / GR * GR : (sizeof(FT) == 2 ? 64 : (28 + GR - 1) / GR * GR);
   static constexpr int NCH = (MS + CC - 1) / CC;                  // chunks per block
-  // columns per group and chunk (whole octets for the BF16 Q2/Q1 blocks)
-  static constexpr int SUB = SL::OCT ? ((CC + G - 1) / G + 7) / 8 * 8 : (CC + G - 1) / G;
+  // columns per group and chunk (whole 16-byte column groups for the FP32 / BF16 Q2/Q1 blocks)
+  static constexpr int SUB = SL::GRP ? ((CC + G - 1) / G + SL::GV - 1) / SL::GV * SL::GV : (CC + G - 1) / G;
   static constexpr int MSX = (MS + 3) / 4 * 4;                    // 16-byte rows of rhs / y in shared memory
   // four-wide loads of the input vector when every group's first column is 16-byte aligned
   static constexpr bool XV = sizeof(CT) == 4 && SUB % 4 == 0 && CC % 4 == 0;
@@ -984,7 +1003,7 @@ struct ApplyCfg {
                                 ? RING_BYTES / (SLOT_ELEMS * (int)sizeof(FT))
                                 : 16;
   static_assert((CC * MS * (int)sizeof(FT)) % 16 == 0, "chunk boundary off the 16-byte granule");
-  static_assert(!SL::OCT || NCH == 1, "octet-stored blocks stream as one chunk");
+  static_assert(!SL::GRP || NCH == 1, "group-stored blocks stream as one chunk");
   static_assert(NS >= 2, "ring too small");
 };
 
@@ -1262,25 +1281,33 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
               // three combining additions per block
 #pragma unroll 4
               for (; c < c1; ++c) a0 = fma(widen(A[c * MS + row]), xk[c], a0);
-            } else if constexpr (C::SL::OCT) {
-              // BF16 octets: one 16-byte load holds this row's entries of eight columns;
-              // columns 8i + j accumulate in a_(j mod 4), the column-major tail in a0
-              const int c8 = min(c1, C::SL::C8);
-              const uint4* Ao = reinterpret_cast<const uint4*>(A + ((c >> 3) * MS + row) * 8);
-              for (; c < c8; c += 8, Ao += MS) {
+            } else if constexpr (C::SL::GRP) {
+              // Q2/Q1 FP32 / BF16: one 16-byte load holds this row's entries of a group of
+              // GV columns; columns c0 + 4i + j accumulate in a_j, the column-major tail in a0
+              constexpr int GV = C::SL::GV;
+              const int cg = min(c1, C::SL::CG);
+              const uint4* Ao = reinterpret_cast<const uint4*>(A + ((c / GV) * MS + row) * GV);
+              for (; c < cg; c += GV, Ao += MS) {
                 const uint4 w = *Ao;
                 const float4 xa = *reinterpret_cast<const float4*>(xk + c);
-                const float4 xb = *reinterpret_cast<const float4*>(xk + c + 4);
-                a0 = fma(bf16_lo(w.x), xa.x, a0);
-                a1 = fma(bf16_hi(w.x), xa.y, a1);
-                a2 = fma(bf16_lo(w.y), xa.z, a2);
-                a3 = fma(bf16_hi(w.y), xa.w, a3);
-                a0 = fma(bf16_lo(w.z), xb.x, a0);
-                a1 = fma(bf16_hi(w.z), xb.y, a1);
-                a2 = fma(bf16_lo(w.w), xb.z, a2);
-                a3 = fma(bf16_hi(w.w), xb.w, a3);
+                if constexpr (GV == 8) {
+                  const float4 xb = *reinterpret_cast<const float4*>(xk + c + 4);
+                  a0 = fma(bf16_lo(w.x), xa.x, a0);
+                  a1 = fma(bf16_hi(w.x), xa.y, a1);
+                  a2 = fma(bf16_lo(w.y), xa.z, a2);
+                  a3 = fma(bf16_hi(w.y), xa.w, a3);
+                  a0 = fma(bf16_lo(w.z), xb.x, a0);
+                  a1 = fma(bf16_hi(w.z), xb.y, a1);
+                  a2 = fma(bf16_lo(w.w), xb.z, a2);
+                  a3 = fma(bf16_hi(w.w), xb.w, a3);
+                } else {
+                  a0 = fma(__uint_as_float(w.x), xa.x, a0);
+                  a1 = fma(__uint_as_float(w.y), xa.y, a1);
+                  a2 = fma(__uint_as_float(w.z), xa.z, a2);
+                  a3 = fma(__uint_as_float(w.w), xa.w, a3);
+                }
               }
-              for (c = max(c, C::SL::C8); c < c1; ++c) a0 = fma(widen(A[C::SL::at(row, c)]), xk[c], a0);
+              for (c = max(c, C::SL::CG); c < c1; ++c) a0 = fma(widen(A[C::SL::at(row, c)]), xk[c], a0);
             } else {
               // columns c0 + 4i + j accumulate in a_j, the tail in a0; the column pointer
               // steps by four columns, so the four loads take fixed offsets
@@ -1435,10 +1462,10 @@ struct WarpSmem {
   using CT = typename ComputeType<FT>::type;
   static constexpr int MS = pd::MS, NT = Q + 1;
   // 16-byte rows where the octet loops load the input four-wide
-  static constexpr bool OCT = Stored<FT, MS>::OCT;
-  static constexpr int MSW = OCT ? (MS + 3) / 4 * 4 : MS;
-  alignas(OCT ? 16 : alignof(CT)) CT rhs[NT][MSW];
-  alignas(OCT ? 16 : alignof(CT)) CT y[NT][MSW];
+  static constexpr bool GRP = Stored<FT, MS>::GRP;
+  static constexpr int MSW = GRP ? (MS + 3) / 4 * 4 : MS;
+  alignas(GRP ? 16 : alignof(CT)) CT rhs[NT][MSW];
+  alignas(GRP ? 16 : alignof(CT)) CT y[NT][MSW];
   CT yp[2][pd::NVG2];
   CT tm[2][pd::NVG2];
   CT mx[pd::NVG][pd::NVG];
@@ -1524,23 +1551,23 @@ __device__ __forceinline__ void warp_apply(const FeTables& T, const Items& items
         CT acc[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] = 0;
-        if constexpr (Stored<FT, MS>::OCT) {
-          // one 16-byte load per row and octet of columns, then the column-major tail;
+        if constexpr (Stored<FT, MS>::GRP) {
+          // one 16-byte load per row and group of columns, then the column-major tail;
           // the FMAs of a row in column order
           using SL = Stored<FT, MS>;
 #pragma unroll 2
-          for (int o = 0; o < SL::C8 / 8; ++o) {
-            const float4 xa = *reinterpret_cast<const float4*>(xv + 8 * o);
-            const float4 xb = *reinterpret_cast<const float4*>(xv + 8 * o + 4);
+          for (int o = 0; o < SL::CG / SL::GV; ++o) {
+            float4 xa, xb;
+            grp_x<FT>(xv + SL::GV * o, xa, xb);
             const uint4* Ao = reinterpret_cast<const uint4*>(A) + (int64_t)o * MS;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
               const int row = lane + 32 * r;
-              if (row < MS) acc[r] = oct_fma(__ldg(Ao + row), xa, xb, acc[r]);
+              if (row < MS) acc[r] = grp_fma<FT>(__ldg(Ao + row), xa, xb, acc[r]);
             }
           }
 #pragma unroll
-          for (int c = SL::C8; c < MS; ++c) {
+          for (int c = SL::CG; c < MS; ++c) {
             const CT xc = xv[c];
             const FT* col = A + SL::at(0, c);
 #pragma unroll
@@ -1754,21 +1781,21 @@ __device__ __forceinline__ void warp_apply_bulk(const FeTables& T, const Items& 
       CT acc[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) acc[r] = 0;
-      if constexpr (Stored<FT, MS>::OCT) {  // tile 3's loops on the shared-memory copy
+      if constexpr (Stored<FT, MS>::GRP) {  // tile 3's loops on the shared-memory copy
         using SL = Stored<FT, MS>;
 #pragma unroll 2
-        for (int o = 0; o < SL::C8 / 8; ++o) {
-          const float4 xa = *reinterpret_cast<const float4*>(&sm.rhs[0][8 * o]);
-          const float4 xb = *reinterpret_cast<const float4*>(&sm.rhs[0][8 * o + 4]);
+        for (int o = 0; o < SL::CG / SL::GV; ++o) {
+          float4 xa, xb;
+          grp_x<FT>(&sm.rhs[0][SL::GV * o], xa, xb);
           const uint4* Ao = reinterpret_cast<const uint4*>(A) + o * MS;
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const int row = lane + 32 * r;
-            if (row < MS) acc[r] = oct_fma(Ao[row], xa, xb, acc[r]);
+            if (row < MS) acc[r] = grp_fma<FT>(Ao[row], xa, xb, acc[r]);
           }
         }
 #pragma unroll
-        for (int c = SL::C8; c < MS; ++c) {
+        for (int c = SL::CG; c < MS; ++c) {
           const CT xc = sm.rhs[0][c];
 #pragma unroll
           for (int r = 0; r < R; ++r) {
