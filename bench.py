@@ -163,18 +163,48 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _a10_nonzeros(w, patch, sp):
+    """Nonzeros of the off-diagonal temporal block A10 of a DG(1) patch block among its
+    real slots (spatial indices sp, in slot order): two slots couple iff they share one
+    of the patch's 2 x 2 cells and are not both pressure slots."""
+    import numpy as np
+    k, n = w.k, w.n_fine
+    nv, npr = n * (k + 1) + 1, n * k + 1
+    I, J = patch % (n + 1), patch // (n + 1)
+    vel = sp < 2 * nv * nv
+    t = np.where(vel, sp % (nv * nv), sp - 2 * nv * nv)
+    gx = np.where(vel, t % nv, t % npr)
+    gy = np.where(vel, t // nv, t // npr)
+    ix = np.where(vel, gx - (I - 1) * (k + 1), gx - (I * k - (k - 1)))
+    iy = np.where(vel, gy - (J - 1) * (k + 1), gy - (J * k - (k - 1)))
+
+    def cells(c):
+        lim = np.where(vel, k + 1, k - 1)
+        return (c <= lim).astype(np.int64) | 2 * (c >= lim).astype(np.int64)
+
+    cx, cy = cells(ix), cells(iy)
+    pair = ((cx[:, None] & cx[None, :]) != 0) & ((cy[:, None] & cy[None, :]) != 0) & (vel[:, None] | vel[None, :])
+    return int(pair.sum())
+
+
 def smoother_algorithmic(ctx, w, factor_bytes=8):
     """Algorithmic bytes and flops of one finest-level smoother-apply launch:
-    every (patch, slab) streams its (q+1)^2 m^2 factor entries once (m = the
-    patch's true size, padding excluded; factor_bytes per entry), reads its
-    m (q+1) FP64 right-hand side values and writes as many FP64 outputs;
-    2 flops per factor entry."""
+    every (patch, slab) streams its factor entries once (m = the patch's true
+    size, padding excluded; factor_bytes per entry): (q+1)^2 m^2, except that FP64
+    DG(1) blocks stream A10 by its nonzeros (3 m^2 + nnz(A10)); it reads its m (q+1)
+    FP64 right-hand side values and writes as many FP64 outputs; 2 flops per
+    factor entry."""
     L = ctx.fine
     n1 = w.n_fine + 1
-    sizes = [len(ctx.patch_dofs(L, p, 0)) for p in range(n1 * n1)]  # (q+1) * m per slab
-    ent = sum(s * s for s in sizes) * w.N
-    vec = sum(sizes) * w.N
-    return factor_bytes * ent + 16.0 * vec, 2.0 * ent
+    nt = w.q + 1
+    sparse_a10 = factor_bytes == 8 and w.q == 1
+    ent = vec = 0
+    for p in range(n1 * n1):
+        idx = ctx.patch_dofs(L, p, 0)  # (q+1) * m per slab, temporal index first
+        m = len(idx) // nt
+        vec += len(idx)
+        ent += 3 * m * m + _a10_nonzeros(w, p, idx[:m]) if sparse_a10 else (nt * m) ** 2
+    return factor_bytes * ent * w.N + 16.0 * vec * w.N, 2.0 * ent * w.N
 
 
 def traffic_record(kernel, workload):

@@ -44,6 +44,88 @@ struct PD {
   static constexpr int NVL = K + 2, NVE = NVL * NVL;
 };
 
+// Sparsity of the off-diagonal temporal block A10 of a DG(1) patch block (kind 0), the
+// one stored block that is not a factor but an assembled Jacobian block: two slots couple
+// only if some cell contains both, and the slot grid spans exactly the patch's 2 x 2 cells
+// (velocity slot x in the first cell along an axis if x <= K+1, in the second if x >= K+1;
+// pressure slot x in the first if x <= K-1, in the second if x >= K-1), so two slots
+// couple iff they share a cell along both axes and are not both pressure slots (the
+// Taylor-Hood pressure block is zero): 41% of a Q3/Q2 block, 48% of a Q2/Q1 block.  Its
+// rows are cut into segments of at most L entries; FP64 A10 blocks are stored by
+// segments, item i of segment t at i * NSEGP + t (consecutive segments adjacent, so that
+// a warp reads 32 consecutive values), items past a segment's end zero.
+template <int K>
+struct SpA10 {
+  static constexpr int NVG = 2 * K + 3, NPG = 2 * K - 1, NV2 = NVG * NVG, MS = 2 * NV2 + NPG * NPG;
+  static constexpr int L = K == 2 ? 36 : 19;  // entries per segment at most
+  __host__ __device__ static constexpr bool vel(int s) { return s < 2 * NV2; }
+  __host__ __device__ static constexpr int sx(int s) { return vel(s) ? s % NV2 % NVG : (s - 2 * NV2) % NPG; }
+  __host__ __device__ static constexpr int sy(int s) { return vel(s) ? s % NV2 / NVG : (s - 2 * NV2) / NPG; }
+  // bit 0: in the patch's first cell along an axis; bit 1: in its second
+  __host__ __device__ static constexpr unsigned cells(bool v, int c) {
+    return v ? ((c <= K + 1 ? 1u : 0u) | (c >= K + 1 ? 2u : 0u)) : ((c <= K - 1 ? 1u : 0u) | (c >= K - 1 ? 2u : 0u));
+  }
+  __host__ __device__ static constexpr bool couple(int a, int b) {
+    return (vel(a) || vel(b)) && (cells(vel(a), sx(a)) & cells(vel(b), sx(b))) != 0u &&
+           (cells(vel(a), sy(a)) & cells(vel(b), sy(b))) != 0u;
+  }
+  __host__ __device__ static constexpr int len(int r) {
+    int n = 0;
+    for (int c = 0; c < MS; ++c) n += couple(r, c) ? 1 : 0;
+    return n;
+  }
+  __host__ __device__ static constexpr int count(bool segments) {
+    int n = 0;
+    for (int r = 0; r < MS; ++r) n += segments ? (len(r) + L - 1) / L : len(r);
+    return n;
+  }
+  static constexpr int NSEG = count(true), NNZ = count(false);
+  static constexpr int NSEGP = (NSEG + 31) / 32 * 32;  // segments padded to whole warps
+  static constexpr int ELEMS = L * NSEGP;              // stored entries
+};
+static_assert(SpA10<2>::MS == 107 && SpA10<1>::MS == 51, "patch slot counts");
+static_assert(SpA10<2>::NNZ == 4744 && SpA10<2>::NSEG == 141, "Q3/Q2 A10 pattern");
+static_assert(SpA10<1>::NNZ == 1256 && SpA10<1>::NSEG == 73, "Q2/Q1 A10 pattern");
+
+// The segment tables: row and length of each segment, column of each item (0 past the
+// segment's end), first segment and segment count of each row.
+template <int K>
+struct SpTab {
+  short col[SpA10<K>::ELEMS];
+  short seg_row[SpA10<K>::NSEGP], seg_len[SpA10<K>::NSEGP];
+  short start[SpA10<K>::MS], nseg[SpA10<K>::MS];
+};
+template <int K>
+constexpr SpTab<K> make_sp_tab() {
+  using S = SpA10<K>;
+  SpTab<K> t{};
+  int acc = 0;
+  for (int r = 0; r < S::MS; ++r) {
+    const int n = S::len(r), ns = (n + S::L - 1) / S::L;
+    t.start[r] = (short)acc;
+    t.nseg[r] = (short)ns;
+    for (int j = 0; j < ns; ++j) {
+      t.seg_row[acc + j] = (short)r;
+      t.seg_len[acc + j] = (short)(n - j * S::L < S::L ? n - j * S::L : S::L);
+    }
+    int k = 0;
+    for (int c = 0; c < S::MS; ++c)
+      if (S::couple(r, c)) {
+        t.col[(k % S::L) * S::NSEGP + acc + k / S::L] = (short)c;
+        ++k;
+      }
+    acc += ns;
+  }
+  return t;
+}
+__device__ const SpTab<1> g_sp1 = make_sp_tab<1>();
+__device__ const SpTab<2> g_sp2 = make_sp_tab<2>();
+template <int K>
+__device__ __forceinline__ const SpTab<K>& sp_tab() {
+  if constexpr (K == 1) return g_sp1;
+  else return g_sp2;
+}
+
 // Layout of one stored factor block (MS x MS): column-major with leading dimension MS,
 // padded to a 16-byte granule, except the FP32 and BF16 blocks of Q2/Q1 patches
 // (MS = 51): their first CG = 48 columns are stored by groups of GV = 16 bytes / entry
@@ -632,6 +714,18 @@ __device__ void store_colmajor(const CT* A, ST* dst) {
   }
 }
 
+// A (MS x MS, row-major, leading dimension LD) stored by the segments of SpA10<K>.
+template <int K, int MS, int LD, int NTH, typename CT, typename ST>
+__device__ void store_sparse_a10(const CT* A, ST* dst) {
+  using S = SpA10<K>;
+  static_assert(S::MS == MS, "A10 slot count");
+  const SpTab<K>& tb = sp_tab<K>();
+  for (int e = threadIdx.x; e < S::ELEMS; e += NTH) {
+    const int i = e / S::NSEGP, t = e - i * S::NSEGP;
+    narrow(i < tb.seg_len[t] ? A[tb.seg_row[t] * LD + tb.col[e]] : CT(0), dst[e]);
+  }
+}
+
 // M -= P Q for an MS x MS shared-memory M (row-major, leading dimension LD) and P, Q
 // stored blocks in global memory (column-major, leading dimension MS) that this CTA
 // wrote before its last barrier.
@@ -809,11 +903,16 @@ block_factor_kernel(LevelGeom g, FeTables T, PhysParams ph, BlockSet bs, const C
     if (conv) assemble_conv<K, Q, CT, LD, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M2, 0, 1, gr);
     gemm_block<MS, LD, NTH, CT>(M1, M2, CT(1));
     store_colmajor<MS, LD, NTH>(M2, F + 3 * BLK);
-    // A10
+    // A10 (FP64 patch blocks: by the segments of its sparsity pattern)
     assemble_const<K, Q, CT, LD, NPGX>(g, T, ph, ft, M1, 1, 0, false, gr);
     __syncthreads();
     if (conv) assemble_conv<K, Q, CT, LD, NPGX>(g, T, ph, bs, Ce, blk, slab, ft, M1, 1, 0, gr);
-    store_colmajor<MS, LD, NTH>(M1, F + 1 * BLK);
+    if constexpr (sizeof(ST) == 8 && NPGX == 2 * K - 1) {
+      if (bs.kind == 0) store_sparse_a10<K, MS, LD, NTH>(M1, F + 1 * BLK);
+      else store_colmajor<MS, LD, NTH>(M1, F + 1 * BLK);
+    } else {
+      store_colmajor<MS, LD, NTH>(M1, F + 1 * BLK);
+    }
     // S = A11 - A10 X
     gemm_block<MS, LD, NTH, CT>(M1, M2, CT(-1));
     assemble_const<K, Q, CT, LD, NPGX>(g, T, ph, ft, M2, 1, 1, true, gr);
@@ -1005,6 +1104,14 @@ struct ApplyCfg {
   static_assert((CC * MS * (int)sizeof(FT)) % 16 == 0, "chunk boundary off the 16-byte granule");
   static_assert(!SL::GRP || NCH == 1, "group-stored blocks stream as one chunk");
   static_assert(NS >= 2, "ring too small");
+  // FP64 DG(1) patch blocks store A10 by segments (SpA10): its chunks hold IPC items of
+  // every segment, NCH_SP of them per block
+  static constexpr bool SPA = sizeof(FT) == 8 && Q == 1 && NPGX == 2 * K - 1;
+  using SP = SpA10<K>;
+  static constexpr int IPC = SPA ? SLOT_ELEMS / SP::NSEGP : 1;
+  static constexpr int NCH_SP = SPA ? (SP::L + IPC - 1) / IPC : 1;
+  static_assert(!SPA || (IPC >= 1 && SP::NSEGP <= NCONS && SP::ELEMS <= BLK && SP::MS == MS),
+                "A10 segments do not fit the tile");
 };
 
 template <int K, int Q, typename FT, int NPGX = 2 * K - 1, int V = 0>
@@ -1026,6 +1133,7 @@ struct ApplySmem {
   alignas(16) CT rhs[C::NT][C::MSX];
   alignas(16) CT y[C::NT][C::MSX];
   CT red[C::G][C::MS];
+  CT red_sp[C::SPA ? C::SP::NSEGP : 1];  // A10 segment sums
   CT yp[2][pd::NVG2];
   CT tm[2][pd::NVG2];
   CT mx[pd::NVG][pd::NVG];
@@ -1128,29 +1236,40 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
       bool stop = false;
       for (int64_t it = blockIdx.x; it < nitems && !stop; it += gridDim.x) {
         const ApplyItem<FT> v = items(it);
-        const int64_t per_item = (int64_t)v.g.N * NB * NCH;
-        for (int64_t q = 0; q < per_item; ++q, ++s) {
-          const int slot = (int)(s % NS);
-          const int64_t u = s / NS;
-          if (u > 0 && !mbar_wait_bounded(smem_u32(&sm.empty[slot]), (uint32_t)((u - 1) & 1))) {
-            *abort_flag = 1;
-            atomicExch(err, 1);
-            stop = true;
-            break;
+        const bool sp = C::SPA && v.bs.kind == 0;
+        const int64_t nblk = (int64_t)v.g.N * NB;
+        for (int64_t bi = 0; bi < nblk && !stop; ++bi) {  // block index within the item
+          const bool spb = sp && bi % NB == 1;  // the A10 block, stored by segments
+          const int nch = spb ? C::NCH_SP : NCH;
+          for (int k = 0; k < nch; ++k, ++s) {
+            const int slot = (int)(s % NS);
+            const int64_t u = s / NS;
+            if (u > 0 && !mbar_wait_bounded(smem_u32(&sm.empty[slot]), (uint32_t)((u - 1) & 1))) {
+              *abort_flag = 1;
+              atomicExch(err, 1);
+              stop = true;
+              break;
+            }
+            if (*abort_flag) {
+              stop = true;
+              break;
+            }
+            const int64_t base = (((int64_t)v.blk * v.fN + v.s0) * NB + bi) * C::BLK;
+            int64_t off;
+            int elems;
+            if (spb) {
+              off = base + (int64_t)k * C::IPC * C::SP::NSEGP;
+              elems = (min(C::SP::L, (k + 1) * C::IPC) - k * C::IPC) * C::SP::NSEGP;
+            } else {
+              off = base + (int64_t)k * C::CC * MS;
+              elems = (k == NCH - 1) ? C::BLK - k * C::CC * MS : C::CC * MS;
+            }
+            const uint32_t bar = smem_u32(&sm.full[slot]);
+            const uint32_t bytes = (uint32_t)(elems * sizeof(FT));
+            mbar_expect_tx(bar, bytes);
+            bulk_g2s(smem_u32(ring + (size_t)slot * C::SLOT_ELEMS), v.factors + off, bytes, bar);
+            *(volatile int*)&sm.issued = (int)(s + 1 < 0x7fffffff ? s + 1 : 0x7fffffff);
           }
-          if (*abort_flag) {
-            stop = true;
-            break;
-          }
-          const int64_t bi = q / NCH;  // block index within the item
-          const int k = (int)(q - bi * NCH);
-          const int64_t off = (((int64_t)v.blk * v.fN + v.s0) * NB + bi) * C::BLK + (int64_t)k * C::CC * MS;
-          const int elems = (k == NCH - 1) ? C::BLK - k * C::CC * MS : C::CC * MS;
-          const uint32_t bar = smem_u32(&sm.full[slot]);
-          const uint32_t bytes = (uint32_t)(elems * sizeof(FT));
-          mbar_expect_tx(bar, bytes);
-          bulk_g2s(smem_u32(ring + (size_t)slot * C::SLOT_ELEMS), v.factors + off, bytes, bar);
-          *(volatile int*)&sm.issued = (int)(s + 1 < 0x7fffffff ? s + 1 : 0x7fffffff);
         }
       }
     }
@@ -1217,6 +1336,7 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
       sm.rhs[a][s] = sp >= 0 ? (CT)r[(int64_t)a * g.S + sp] : (CT)0;
     }
     const bool carry = v.prev != nullptr && bs.kind == 0;  // jump state from before the window
+    const bool sparse = C::SPA && bs.kind == 0;             // A10 stored by segments
     for (int slab = 0; slab < g.N && !aborted; ++slab) {
       if (slab > 0 || carry) {
         // jump coupling: rhs_a += tau_a(0) M_u y_{n-1, last} (tensor-product mass on the slot grid)
@@ -1249,15 +1369,28 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
       for (int b = 0; b < NB; ++b) {
         const BlockOp op = block_op<NT>(b);
         const CT* xv = op.src_y ? sm.y[op.src] : sm.rhs[op.src];
+        const bool spb = sparse && b == 1;
         CT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        for (int k = 0; k < NCH; ++k) {
+        for (int k = 0; k < (spb ? C::NCH_SP : NCH); ++k) {
           const int slot = cslot;
           const bool ok = !aborted && mbar_wait_bounded(smem_u32(&sm.full[slot]), cphase);
           if (!ok) {
             aborted = true;
             *abort_flag = 1;
           }
-          if (ok && gemv_thread && !dense) {
+          if (ok && spb) {
+            if constexpr (C::SPA) {
+              if (tid < C::SP::NSEGP) {
+                // A10 by segments: this thread's segment, the chunk's items k IPC ..
+                const FT* A = ring + (size_t)slot * C::SLOT_ELEMS;
+                const short* cl = sp_tab<K>().col + tid;  // column of item i at cl[i NSEGP]
+                const int i0 = k * C::IPC, i1 = min(C::SP::L, i0 + C::IPC);
+#pragma unroll 4
+                for (int i = i0; i < i1; ++i)
+                  a0 = fma(widen(A[(i - i0) * C::SP::NSEGP + tid]), xv[__ldg(cl + i * C::SP::NSEGP)], a0);
+              }
+            }
+          } else if (ok && gemv_thread && !dense) {
             // the chunk's real columns, split evenly over the G column groups
             const FT* A = ring + (size_t)slot * C::SLOT_ELEMS;
             const CT* xk = xv + k * C::CC;
@@ -1335,7 +1468,12 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
             cphase ^= 1u;
           }
         }
-        if (gemv_thread) sm.red[grp][row] = sizeof(CT) == 8 ? a0 : (a0 + a1) + (a2 + a3);
+        if (spb) {
+          if constexpr (C::SPA)
+            if (tid < C::SP::NSEGP) sm.red_sp[tid] = a0;
+        } else if (gemv_thread) {
+          sm.red[grp][row] = sizeof(CT) == 8 ? a0 : (a0 + a1) + (a2 + a3);
+        }
         if (tid == 0) sm.decision = *abort_flag;  // one reader, so every consumer decides alike
         consumer_sync<NCONS>();
         if (sm.decision) {
@@ -1343,9 +1481,20 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
           break;
         }
         if (tid < MS) {
-          CT sum = sm.red[0][tid];
+          CT sum = CT(0);
+          if constexpr (C::SPA) {
+            if (spb) {  // the row's segment sums in column order
+              const SpTab<K>& tb = sp_tab<K>();
+              const int j0 = __ldg(&tb.start[tid]), nj = __ldg(&tb.nseg[tid]);
+              sum = sm.red_sp[j0];
+              for (int j = 1; j < nj; ++j) sum += sm.red_sp[j0 + j];
+            }
+          }
+          if (!spb) {
+            sum = sm.red[0][tid];
 #pragma unroll
-          for (int h = 1; h < C::G; ++h) sum += sm.red[h][tid];
+            for (int h = 1; h < C::G; ++h) sum += sm.red[h][tid];
+          }
           if (op.dst == 0) sm.y[op.di][tid] = sum;
           else if (op.dst == 1) sm.rhs[op.di][tid] -= sum;
           else sm.y[op.di][tid] -= sum;
@@ -2093,6 +2242,10 @@ void apply_variant(int variant, const LevelGeom& g, const FeTables& T, const Blo
                    const double* r, double* out, int* err, const double* prev, cudaStream_t s,
                    const ChunkPlan* cp) {
   if (variant < 0) variant = default_apply_variant(K);
+  // FP64 DG(1) patch blocks store A10 by segments, which only the CTA tiles read: the warp
+  // tiles run as tile 2 there
+  if constexpr (ApplyCfg<K, Q, FT>::SPA)
+    if (variant == 3 || variant == 4) variant = 2;
   if (variant == 4) {  // the bulk-copy warp tile exists for Q2/Q1 DG(0); elsewhere it is tile 3
     if constexpr (K == 1 && Q == 0) run_warp_bulk_apply<FT>(g, T, bs, factors, r, out, err, prev, s, cp);
     else run_warp_apply<K, Q, FT>(g, T, bs, factors, r, out, prev, s, cp);
@@ -2106,6 +2259,8 @@ template <int K, int Q, typename FT>
 void bt_apply_variant(int variant, const BatchSeg* segs, int nseg, int64_t items, const FeTables& T,
                       const double* r, double* yp, int* err, cudaStream_t s) {
   if (variant < 0) variant = default_apply_variant(K);
+  if constexpr (ApplyCfg<K, Q, FT>::SPA)  // A10 by segments: CTA tiles only (as apply_variant)
+    if (variant == 3 || variant == 4) variant = 2;
   if (variant == 4) {
     if constexpr (K == 1 && Q == 0) run_bt_warp_bulk_apply<FT>(segs, nseg, items, T, r, yp, err, s);
     else run_bt_warp_apply<K, Q, FT>(segs, nseg, items, T, r, yp, s);

@@ -52,6 +52,8 @@ int tune_apply_variant(const TuneKey& key, cudaStream_t s, const std::function<v
   float best_ms = 0.f;
   for (int v = 0; v < kApplyTileVariants; ++v) {
     if (v == 4 && !(key.k == 1 && key.q == 0)) continue;  // tile 4 exists for Q2/Q1 DG(0) only (else it is tile 3)
+    // FP64 DG(1): A10 is stored by segments and the warp tiles run as tile 2
+    if (v >= 3 && key.q == 1 && key.precision == WR_FP64) continue;
     launch(v);
     WR_CUDA(cudaEventRecord(e0, s));
     launch(v);
