@@ -1110,7 +1110,8 @@ struct ApplyCfg {
   using SP = SpA10<K>;
   static constexpr int IPC = SPA ? SLOT_ELEMS / SP::NSEGP : 1;
   static constexpr int NCH_SP = SPA ? (SP::L + IPC - 1) / IPC : 1;
-  static_assert(!SPA || (IPC >= 1 && SP::NSEGP <= NCONS && SP::ELEMS <= BLK && SP::MS == MS),
+  static_assert(!SPA || (IPC >= 1 && SP::NSEGP <= NCONS && SP::ELEMS <= BLK && SP::MS == MS &&
+                          SP::NSEGP <= G * MS),
                 "A10 segments do not fit the tile");
 };
 
@@ -1132,8 +1133,7 @@ struct ApplySmem {
   int dense;
   alignas(16) CT rhs[C::NT][C::MSX];
   alignas(16) CT y[C::NT][C::MSX];
-  CT red[C::G][C::MS];
-  CT red_sp[C::SPA ? C::SP::NSEGP : 1];  // A10 segment sums
+  CT red[C::G][C::MS];  // group sums of a dense block; segment sums of a sparse A10 block
   CT yp[2][pd::NVG2];
   CT tm[2][pd::NVG2];
   CT mx[pd::NVG][pd::NVG];
@@ -1470,7 +1470,7 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
         }
         if (spb) {
           if constexpr (C::SPA)
-            if (tid < C::SP::NSEGP) sm.red_sp[tid] = a0;
+            if (tid < C::SP::NSEGP) (&sm.red[0][0])[tid] = a0;
         } else if (gemv_thread) {
           sm.red[grp][row] = sizeof(CT) == 8 ? a0 : (a0 + a1) + (a2 + a3);
         }
@@ -1486,8 +1486,9 @@ __device__ __forceinline__ void apply_persistent(const FeTables& T, const Items&
             if (spb) {  // the row's segment sums in column order
               const SpTab<K>& tb = sp_tab<K>();
               const int j0 = __ldg(&tb.start[tid]), nj = __ldg(&tb.nseg[tid]);
-              sum = sm.red_sp[j0];
-              for (int j = 1; j < nj; ++j) sum += sm.red_sp[j0 + j];
+              const CT* seg = &sm.red[0][0];
+              sum = seg[j0];
+              for (int j = 1; j < nj; ++j) sum += seg[j0 + j];
             }
           }
           if (!spb) {
