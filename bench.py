@@ -163,10 +163,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _a10_nonzeros(w, patch, sp):
-    """Nonzeros of the off-diagonal temporal block A10 of a DG(1) patch block among its
-    real slots (spatial indices sp, in slot order): two slots couple iff they share one
-    of the patch's 2 x 2 cells and are not both pressure slots."""
+def _a10_pattern(w, patch, sp):
+    """Sparsity pattern of the off-diagonal temporal block A10 of a DG(1) patch block
+    among its real slots (spatial indices sp, in slot order), as a boolean matrix: two
+    slots couple iff they share one of the patch's 2 x 2 cells and are not both pressure
+    slots."""
     import numpy as np
     k, n = w.k, w.n_fine
     nv, npr = n * (k + 1) + 1, n * k + 1
@@ -183,8 +184,12 @@ def _a10_nonzeros(w, patch, sp):
         return (c <= lim).astype(np.int64) | 2 * (c >= lim).astype(np.int64)
 
     cx, cy = cells(ix), cells(iy)
-    pair = ((cx[:, None] & cx[None, :]) != 0) & ((cy[:, None] & cy[None, :]) != 0) & (vel[:, None] | vel[None, :])
-    return int(pair.sum())
+    return ((cx[:, None] & cx[None, :]) != 0) & ((cy[:, None] & cy[None, :]) != 0) & (vel[:, None] | vel[None, :])
+
+
+def _a10_nonzeros(w, patch, sp):
+    """Nonzeros of a DG(1) patch block's A10 among its real slots."""
+    return int(_a10_pattern(w, patch, sp).sum())
 
 
 def smoother_algorithmic(ctx, w, factor_bytes=8):
