@@ -1703,17 +1703,24 @@ __device__ __forceinline__ void warp_apply(const FeTables& T, const Items& items
         for (int r = 0; r < R; ++r) acc[r] = 0;
         if constexpr (Stored<FT, MS>::GRP) {
           // one 16-byte load per row and group of columns, then the column-major tail;
-          // the FMAs of a row in column order
+          // even groups and the tail accumulate in acc, odd groups in acc2 (two chains)
           using SL = Stored<FT, MS>;
-#pragma unroll 2
-          for (int o = 0; o < SL::CG / SL::GV; ++o) {
-            float4 xa, xb;
+          static_assert(SL::CG / SL::GV % 2 == 0, "groups in pairs");
+          CT acc2[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc2[r] = 0;
+          for (int o = 0; o < SL::CG / SL::GV; o += 2) {
+            float4 xa, xb, xc, xd;
             grp_x<FT>(xv + SL::GV * o, xa, xb);
+            grp_x<FT>(xv + SL::GV * (o + 1), xc, xd);
             const uint4* Ao = reinterpret_cast<const uint4*>(A) + (int64_t)o * MS;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
               const int row = lane + 32 * r;
-              if (row < MS) acc[r] = grp_fma<FT>(__ldg(Ao + row), xa, xb, acc[r]);
+              if (row < MS) {
+                acc[r] = grp_fma<FT>(__ldg(Ao + row), xa, xb, acc[r]);
+                acc2[r] = grp_fma<FT>(__ldg(Ao + MS + row), xc, xd, acc2[r]);
+              }
             }
           }
 #pragma unroll
@@ -1726,6 +1733,8 @@ __device__ __forceinline__ void warp_apply(const FeTables& T, const Items& items
               if (row < MS) acc[r] = fma(widen(__ldg(col + row)), xc, acc[r]);
             }
           }
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc[r] += acc2[r];
         } else {
 #pragma unroll 4
           for (int c = 0; c < MS; ++c) {
@@ -1931,17 +1940,23 @@ __device__ __forceinline__ void warp_apply_bulk(const FeTables& T, const Items& 
       CT acc[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) acc[r] = 0;
-      if constexpr (Stored<FT, MS>::GRP) {  // tile 3's loops on the shared-memory copy
+      if constexpr (Stored<FT, MS>::GRP) {  // tile 3's loops and chains on the shared-memory copy
         using SL = Stored<FT, MS>;
-#pragma unroll 2
-        for (int o = 0; o < SL::CG / SL::GV; ++o) {
-          float4 xa, xb;
+        CT acc2[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc2[r] = 0;
+        for (int o = 0; o < SL::CG / SL::GV; o += 2) {
+          float4 xa, xb, xc, xd;
           grp_x<FT>(&sm.rhs[0][SL::GV * o], xa, xb);
+          grp_x<FT>(&sm.rhs[0][SL::GV * (o + 1)], xc, xd);
           const uint4* Ao = reinterpret_cast<const uint4*>(A) + o * MS;
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const int row = lane + 32 * r;
-            if (row < MS) acc[r] = grp_fma<FT>(Ao[row], xa, xb, acc[r]);
+            if (row < MS) {
+              acc[r] = grp_fma<FT>(Ao[row], xa, xb, acc[r]);
+              acc2[r] = grp_fma<FT>(Ao[MS + row], xc, xd, acc2[r]);
+            }
           }
         }
 #pragma unroll
@@ -1953,6 +1968,8 @@ __device__ __forceinline__ void warp_apply_bulk(const FeTables& T, const Items& 
             if (row < MS) acc[r] = fma(widen(A[SL::at(row, c)]), xc, acc[r]);
           }
         }
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] += acc2[r];
       } else {
 #pragma unroll 4
         for (int c = 0; c < MS; ++c) {
